@@ -1,0 +1,487 @@
+"""Pins of the FP64 CPU oracle against facts it does not compute itself: finite differences,
+textbook linear elasticity, closed-form mesh counts, brute-force closest points, library
+eigen-solvers and linear solvers, closed-form ACCD impact times, and physical invariants."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_04776_gb300 import workloads as W
+
+E_, NU_, RHO_ = W.YOUNG, W.POISSON, W.DENSITY
+MU = E_ / (2 * (1 + NU_))
+LAM = E_ * NU_ / ((1 + NU_) * (1 - 2 * NU_))
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rand_rot(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+# ------------------------------------------------------------------ elasticity
+def test_rest_tensor_is_isotropic_linear_elasticity():
+    """At F = I the Hessian of any consistent hyperelastic model is the linear-elasticity tensor
+    C_ijkl = mu (d_ik d_jl + d_il d_jk) + lambda d_ij d_kl (textbook), and Psi = P = 0."""
+    s, psi, P, C = O.psi(np.eye(3).ravel(), MU, LAM)
+    assert s == 0 and psi == 0.0 and np.all(P == 0.0)
+    d = np.eye(3)
+    ref = np.zeros((9, 9))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    ref[3 * i + j, 3 * k + l] = MU * (d[i, k] * d[j, l] + d[i, l] * d[j, k]) + LAM * d[i, j] * d[k, l]
+    np.testing.assert_allclose(C, ref, rtol=1e-12, atol=1e-9 * MU)
+
+
+def test_rest_tensor_recovers_young_and_poisson():
+    """Uniaxial stress through the rest tensor gives back E and nu (checks the Lame conversion)."""
+    _, _, _, C = O.psi(np.eye(3).ravel(), MU, LAM)
+    sym = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    Cv = np.array([[C[3 * a + b, 3 * c + d] for (c, d) in sym] for (a, b) in sym])
+    Cv[:, 3:] *= 2.0  # engineering shear strains
+    S = np.linalg.inv(Cv)
+    assert abs(1.0 / S[0, 0] - E_) < 1e-6 * E_
+    assert abs(-S[1, 0] / S[0, 0] - NU_) < 1e-9
+
+
+def test_small_strain_energy_matches_linear_elasticity():
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        A = rng.normal(size=(3, 3))
+        eps = 1e-5 * 0.5 * (A + A.T)
+        _, psi, _, _ = O.psi((np.eye(3) + eps).ravel(), MU, LAM)
+        lin = MU * np.sum(eps * eps) + 0.5 * LAM * np.trace(eps) ** 2
+        assert abs(psi - lin) < 1e-4 * abs(lin)
+
+
+def test_frame_indifference_and_inversion():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        F = np.eye(3) + 0.3 * rng.normal(size=(3, 3))
+        if np.linalg.det(F) <= 0.1:
+            continue
+        R = rand_rot(rng)
+        _, a, _, _ = O.psi(F.ravel(), MU, LAM)
+        _, b, _, _ = O.psi((R @ F).ravel(), MU, LAM)
+        assert abs(a - b) <= 1e-10 * abs(a)
+    F = np.diag([1.0, 1.0, -0.5])
+    s, _, _, _ = O.psi(F.ravel(), MU, LAM)
+    assert s == 1  # det F <= 0 has no energy
+
+
+def random_tet(rng, scale=1e-3, strain=0.2):
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float) * scale
+    X += rng.normal(scale=0.1 * scale, size=(4, 3))
+    if np.linalg.det(np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], axis=1)) < 0:
+        X[[2, 3]] = X[[3, 2]]
+    F = np.eye(3) + strain * rng.normal(size=(3, 3))
+    while np.linalg.det(F) < 0.3:
+        F = np.eye(3) + strain * rng.normal(size=(3, 3))
+    x = X @ F.T + rng.normal(scale=scale, size=3)
+    return X, x
+
+
+def test_tet_gradient_and_hessian_central_differences():
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        X, x = random_tet(rng)
+        s, e, g, H = O.tet(X, x, MU, LAM, project=False)
+        assert s == 0
+        h = 1e-9
+        gfd = np.zeros(12)
+        Hfd = np.zeros((12, 12))
+        for k in range(12):
+            xp = x.ravel().copy()
+            xm = x.ravel().copy()
+            xp[k] += h
+            xm[k] -= h
+            ep = O.tet(X, xp.reshape(4, 3), MU, LAM, derivs=False)[1]
+            em = O.tet(X, xm.reshape(4, 3), MU, LAM, derivs=False)[1]
+            gfd[k] = (ep - em) / (2 * h)
+            Hfd[:, k] = (O.tet(X, xp.reshape(4, 3), MU, LAM, project=False)[2] -
+                         O.tet(X, xm.reshape(4, 3), MU, LAM, project=False)[2]) / (2 * h)
+        assert np.max(np.abs(g - gfd)) <= 1e-6 * np.max(np.abs(g))
+        assert np.max(np.abs(H - Hfd)) <= 1e-5 * np.max(np.abs(H))
+        # translation invariance: forces of one element sum to zero
+        assert np.max(np.abs(g.reshape(4, 3).sum(0))) <= 1e-9 * np.max(np.abs(g))
+
+
+def test_tet_projection_is_psd_and_exact_when_already_psd():
+    rng = np.random.default_rng(4)
+    n_clamped = 0
+    for _ in range(20):
+        X, x = random_tet(rng, strain=0.35)
+        _, _, _, Hr = O.tet(X, x, MU, LAM, project=False)
+        _, _, _, Hp = O.tet(X, x, MU, LAM, project=True)
+        w = np.linalg.eigvalsh(Hp)
+        assert w.min() >= -1e-10 * w.max()
+        if np.linalg.eigvalsh(Hr).min() < -1e-8 * w.max():
+            n_clamped += 1
+    assert n_clamped > 0  # compression cases exercise the clamp
+    X, x = random_tet(rng, strain=0.0)  # pure rigid motion: rest Hessian is PSD
+    _, _, _, Hr = O.tet(X, x, MU, LAM, project=False)
+    _, _, _, Hp = O.tet(X, x, MU, LAM, project=True)
+    np.testing.assert_allclose(Hp, Hr, atol=1e-9 * np.abs(Hr).max())
+
+
+# ------------------------------------------------------------------ eigen / projection / solver
+def test_psd_projection_matches_library_eigh():
+    rng = np.random.default_rng(5)
+    for n in (3, 6, 9, 12):
+        A = rng.normal(size=(n, n))
+        A = A + A.T
+        w, V = np.linalg.eigh(A)
+        ref = (V * np.maximum(w, 0)) @ V.T
+        P = O.psd_project(A)
+        np.testing.assert_allclose(P, ref, atol=1e-12 * np.abs(A).max())
+        np.testing.assert_allclose(O.psd_project(P), P, atol=1e-12 * np.abs(A).max())  # idempotent
+        wo, _ = O.eigh(A)
+        np.testing.assert_allclose(np.sort(wo), w, atol=1e-12 * np.abs(A).max())
+
+
+def test_pcg_matches_dense_solve():
+    import scipy.sparse as sp
+    rng = np.random.default_rng(6)
+    n = 60
+    B = sp.random(n, n, density=0.1, random_state=7, format="csr")
+    A = (B @ B.T + sp.eye(n) * 2.0).tocsr()
+    b = rng.normal(size=n)
+    it, x = O.pcg_csr(A.indptr, A.indices, A.data, b, tol=1e-13)
+    assert it > 0
+    np.testing.assert_allclose(x, np.linalg.solve(A.toarray(), b), rtol=1e-9, atol=1e-11)
+
+
+# ------------------------------------------------------------------ distances
+def brute_pt(P, n=240):
+    p, t0, t1, t2 = P
+    u = np.linspace(0, 1, n)
+    a, b = np.meshgrid(u, u)
+    m = a + b <= 1
+    q = t0 + a[m, None] * (t1 - t0) + b[m, None] * (t2 - t0)
+    return np.min(np.sum((q - p) ** 2, 1))
+
+
+def brute_ee(P, n=600):
+    a0, a1, b0, b1 = P
+    u = np.linspace(0, 1, n)
+    s, t = np.meshgrid(u, u)
+    pa = a0 + s.ravel()[:, None] * (a1 - a0)
+    pb = b0 + t.ravel()[:, None] * (b1 - b0)
+    return np.min(np.sum((pa - pb) ** 2, 1))
+
+
+def refine_min(fun, x0, bounds, cons=()):
+    from scipy.optimize import minimize
+    r = minimize(fun, x0, bounds=bounds, constraints=cons, method="SLSQP",
+                 options=dict(ftol=1e-30, maxiter=500))
+    return r.fun
+
+
+def test_point_triangle_distance_against_brute_force():
+    rng = np.random.default_rng(8)
+    types = set()
+    for k in range(60):
+        P = rng.normal(size=(4, 3))
+        d2, ty = O.distance2(0, P)
+        types.add(ty[0])
+        bf = brute_pt(P)
+        p, t0, t1, t2 = P
+
+        def f(l):
+            q = t0 + l[0] * (t1 - t0) + l[1] * (t2 - t0)
+            return float(np.sum((q - p) ** 2))
+        ex = refine_min(f, [1 / 3, 1 / 3], [(0, 1), (0, 1)],
+                        ({"type": "ineq", "fun": lambda l: 1 - l[0] - l[1]},))
+        assert d2 <= bf + 1e-12
+        assert abs(d2 - min(ex, bf)) <= 1e-7 * max(1.0, d2)
+    assert types == {0, 1, 2}  # PP, PE and PT regions all reached
+
+
+def test_edge_edge_distance_against_brute_force():
+    rng = np.random.default_rng(9)
+    types = set()
+    for k in range(60):
+        P = rng.normal(size=(4, 3))
+        d2, ty = O.distance2(1, P)
+        types.add(ty[0])
+        a0, a1, b0, b1 = P
+
+        def f(st):
+            return float(np.sum((a0 + st[0] * (a1 - a0) - b0 - st[1] * (b1 - b0)) ** 2))
+        bf = brute_ee(P)
+        ex = refine_min(f, [0.5, 0.5], [(0, 1), (0, 1)])
+        assert d2 <= bf + 1e-12
+        assert abs(d2 - min(ex, bf)) <= 1e-7 * max(1.0, d2)
+    assert types == {0, 1, 3}
+    # exactly parallel edges never use the (singular) line-line formula
+    P = np.array([[0, 0, 0], [1, 0, 0], [0.2, 0.3, 0.0], [1.4, 0.3, 0.0]], float)
+    d2, ty = O.distance2(1, P)
+    assert ty[0] != 3 and abs(d2 - 0.09) < 1e-15
+
+
+# ------------------------------------------------------------------ barrier
+def fd_pair(kind, P, dhat, eps_x, h=1e-10):
+    s, b, g, H = O.pair_barrier(kind, P, dhat, eps_x)
+    gfd = np.zeros(12)
+    Hfd = np.zeros((12, 12))
+    for k in range(12):
+        Pp = P.ravel().copy()
+        Pm = P.ravel().copy()
+        Pp[k] += h
+        Pm[k] -= h
+        rp = O.pair_barrier(kind, Pp.reshape(4, 3), dhat, eps_x)
+        rm = O.pair_barrier(kind, Pm.reshape(4, 3), dhat, eps_x)
+        gfd[k] = (rp[1] - rm[1]) / (2 * h)
+        Hfd[:, k] = (rp[2] - rm[2]) / (2 * h)
+    return s, b, g, H, gfd, Hfd
+
+
+PAIR_CASES = {
+    # kind, points (metres), expected formula
+    "PT": (0, [[0.3e-3, 0.3e-3, 5e-5], [0, 0, 0], [1e-3, 0, 0], [0, 1e-3, 0]], 2),
+    "PE": (0, [[0.5e-3, -4e-5, 3e-5], [0, 0, 0], [1e-3, 0, 0], [0, 1e-3, 0]], 1),
+    "PP": (0, [[-3e-5, -4e-5, 2e-5], [0, 0, 0], [1e-3, 0, 0], [0, 1e-3, 0]], 0),
+    "LL": (1, [[0, 0, 0], [1e-3, 0.1e-3, 0], [0.5e-3, -0.5e-3, 6e-5], [0.4e-3, 0.5e-3, 6e-5]], 3),
+    "EE-PE": (1, [[0, 0, 0], [1e-3, 0, 0], [1.02e-3, -0.5e-3, 5e-5], [1.03e-3, 0.5e-3, 6e-5]], 1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PAIR_CASES))
+def test_barrier_central_differences(name):
+    kind, P, ftype = PAIR_CASES[name]
+    P = np.asarray(P, float)
+    d2, ty = O.distance2(kind, P)
+    assert ty[0] == ftype and d2 < W.DHAT ** 2
+    for eps_x in ([0.0] if kind == 0 else [1e-30, 1e-3 * 1e-6 * 1e-6]):
+        s, b, g, H, gfd, Hfd = fd_pair(kind, P, W.DHAT, eps_x)
+        assert s == 0 and b > 0
+        assert np.max(np.abs(g - gfd)) <= 1e-5 * np.max(np.abs(g))
+        assert np.max(np.abs(H - Hfd)) <= 1e-4 * np.max(np.abs(H))
+        assert np.max(np.abs(g.reshape(4, 3).sum(0))) <= 1e-9 * np.max(np.abs(g))
+
+
+def test_barrier_vanishes_smoothly_at_dhat_and_blows_up_at_contact():
+    base = np.array([[0.3e-3, 0.3e-3, 0.0], [0, 0, 0], [1e-3, 0, 0], [0, 1e-3, 0]])
+    vals = []
+    for hgt in (W.DHAT * (1 + 1e-9), W.DHAT * (1 - 1e-4), W.DHAT * 1e-3, W.DHAT * 1e-9):
+        P = base.copy()
+        P[0, 2] = hgt
+        s, b, g, H = O.pair_barrier(0, P, W.DHAT)
+        vals.append((s, b, np.abs(g).max()))
+    assert vals[0][0] == 1 and vals[0][1] == 0.0
+    assert vals[1][1] < 1e-8 * W.DHAT ** 2 and vals[1][2] < 1e-3 * W.DHAT  # C1 at dhat
+    assert vals[3][1] > vals[2][1] > 0  # grows toward contact
+    P = base.copy()
+    P[0, 2] = 0.0
+    assert O.pair_barrier(0, P, W.DHAT)[0] == 2
+
+
+def test_edge_mollifier_kills_parallel_and_leaves_crossing_edges():
+    par = np.array([[0, 0, 0], [1e-3, 0, 0], [0.2e-3, 0, 5e-5], [0.8e-3, 1e-12, 5e-5]])
+    eps = 1e-3 * 1e-6 * 0.36e-6
+    assert O.pair_barrier(1, par, W.DHAT, eps)[1] < 1e-12 * O.pair_barrier(1, par, W.DHAT, 0.0)[1]
+    cross = PAIR_CASES["LL"][1]
+    a = O.pair_barrier(1, np.asarray(cross), W.DHAT, eps)[1]
+    b = O.pair_barrier(1, np.asarray(cross), W.DHAT, 0.0)[1]
+    assert a == b
+
+
+# ------------------------------------------------------------------ ACCD
+def test_accd_head_on_closed_form():
+    """Point-point head-on approach at speed v from gap d0: the first additive step covers
+    (1-s) d0 = 0.9 d0 and the next one would cross below s d0, so toi = 0.9 d0 / v exactly."""
+    P = np.array([[0, 0, 1e-4], [0, 0, 0], [1, 0, 0], [0, 1, 0]])  # point above vertex t0
+    P[2:] = [[-1e-3, -1e-3, -1e-3], [-1e-3, 1e-3, -1e-3]]  # triangle far below except t0
+    P = np.array([[0, 0, 1e-4], [0, 0, 0], [1e-3, -1e-3, -1e-3], [-1e-3, 1e-3, -1e-3]])
+    dP = np.zeros((4, 3))
+    dP[0, 2] = -2e-4  # closes the 1e-4 gap at t = 0.5
+    r, t = O.accd(0, P, dP)
+    assert r == 1 and abs(t - 0.9 * 0.5) < 1e-12
+
+
+def min_dist_along(kind, P, dP, t1, n=2000):
+    return min(math.sqrt(O.distance2(kind, P + t * dP)[0]) for t in np.linspace(0, t1, n))
+
+
+def test_accd_is_conservative():
+    rng = np.random.default_rng(10)
+    hits = 0
+    for k in range(60):
+        kind = k % 2
+        P = rng.normal(size=(4, 3)) * 1e-3
+        dP = rng.normal(size=(4, 3)) * 2e-3
+        r, t = O.accd(kind, P, dP)
+        assert r in (0, 1)
+        if r == 1:
+            hits += 1
+            assert 0 <= t <= 1
+            assert min_dist_along(kind, P, dP, t) > 0
+        else:
+            assert min_dist_along(kind, P, dP, 1.0) > 0
+    assert hits > 5
+
+
+# ------------------------------------------------------------------ mesh and scene
+def load_counts():
+    rows = []
+    with open(os.path.join(HERE, "golden", "grid_counts.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return rows
+
+
+@pytest.mark.parametrize("row", load_counts())
+def test_surface_counts_and_mass(row):
+    nx, ny, nz, nv, nt, sv, st, se = row
+    size = (0.02, 0.025, 0.004)
+    gel = W.gel_grid(nx, ny, nz, size)
+    assert gel.verts.shape[0] == nv and gel.tets.shape[0] == nt
+    ind = W.icosphere(0.002, 1)
+    og = O.OracleGel(gel.verts, gel.tets, gel.dirichlet, (E_, NU_, RHO_), ind.verts, ind.tris,
+                     W.pose((0.01, 0.01, 0.1)))
+    info = og.info()
+    assert (info["surf_verts"], info["surf_tris"], info["surf_edges"]) == (sv, st, se)
+    assert abs(info["total_mass"] - RHO_ * np.prod(size)) < 1e-12 * RHO_ * np.prod(size)
+    assert info["ind_edges"] == 120  # icosphere level 1: 80 faces -> 120 edges
+    assert abs(info["bbox_diag"] - math.sqrt(sum(s * s for s in size))) < 1e-15
+
+
+def test_inverted_and_bad_meshes_are_rejected():
+    gel = W.gel_grid(3, 3, 2, (0.002, 0.002, 0.001))
+    ind = W.icosphere(0.001, 0)
+    bad = gel.tets.copy()
+    bad[0, [2, 3]] = bad[0, [3, 2]]
+    with pytest.raises(O.OracleError) as e:
+        O.OracleGel(gel.verts, bad, gel.dirichlet, (E_, NU_, RHO_), ind.verts, ind.tris, W.pose((0, 0, 1)))
+    assert e.value.status == 3
+    bad = gel.tets.copy()
+    bad[0, 0] = 10 ** 6
+    with pytest.raises(O.OracleError) as e:
+        O.OracleGel(gel.verts, bad, gel.dirichlet, (E_, NU_, RHO_), ind.verts, ind.tris, W.pose((0, 0, 1)))
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ whole-step invariants
+def small_scene(depth=0.3e-3, steps=6, seed=0, grid=(6, 6, 3), size=(0.01, 0.01, 0.003), r=0.004):
+    gel = W.gel_grid(*grid, size)
+    ind = W.icosphere(r, 1)
+    c = (0.5 * size[0] + 0.3e-3 * seed, 0.5 * size[1])
+    p0, poses = W.press_slide_poses(ind, gel, c, depth, steps)
+    return W.Workload("tiny", gel, ind, p0, poses, W.DT)
+
+
+def test_rest_state_is_a_fixed_point():
+    wl = small_scene()
+    og = O.OracleGel.from_workload(wl)
+    far = W.pose((0.005, 0.005, 0.05))
+    og.set_state(wl.gel.verts, np.zeros_like(wl.gel.verts), far)
+    info = og.step(far, W.DT)
+    x, v, fc, _ = og.state()
+    assert info["status"] == 0 and info["newton_iters"] == 0
+    assert np.array_equal(x, wl.gel.verts) and np.all(v == 0) and np.all(fc == 0)
+
+
+def test_step_invariants_and_minimiser():
+    """Each step: status OK, no penetration, no inversion, dirichlet vertices untouched, and the
+    result is a stationary point of E (free-DOF gradient tiny against the inertia scale)."""
+    wl = small_scene()
+    og = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    m = og.mass()
+    for s in range(len(wl.poses)):
+        x0, v0, _, _ = og.state()
+        info = og.step(wl.poses[s], wl.dt)
+        assert info["status"] == 0
+        x, v, fc, pose = og.state()
+        assert np.array_equal(x[wl.gel.dirichlet == 1], wl.gel.verts[wl.gel.dirichlet == 1])
+        assert info["min_distance"] > 0
+        t = wl.gel.tets
+        J = np.linalg.det(np.stack([x[t[:, 1]] - x[t[:, 0]], x[t[:, 2]] - x[t[:, 0]], x[t[:, 3]] - x[t[:, 0]]], 2))
+        assert J.min() > 0
+        h = wl.dt / (2 ** 0)
+        if info["substeps"] == 1:
+            xt = x0 + h * v0
+            g, _ = og.gradient(x, xt, h, pose)
+            free = wl.gel.dirichlet == 0
+            # stationarity: residual force below the force of moving a vertex by 1e-9 m
+            assert np.abs(g[free]).max() <= 1e-9 * (m.max() / h ** 2 + 1e3) + 1e-9
+    assert fc[2] < 0  # the indenter pushes the gel down
+
+
+def test_elastic_forces_are_balanced_by_supports():
+    """Translation invariance of the elastic energy: the support reactions at the fixed bottom
+    face balance the sum of all other forces at a converged quasi-static state."""
+    wl = small_scene(depth=0.2e-3, steps=12)
+    og = O.OracleGel.from_workload(wl, newton_tol=1e-10)
+    # quasi-static: huge time steps so inertia is negligible
+    for p in wl.poses:
+        info = og.step(p, 100.0)
+        assert info["status"] == 0
+    x, v, fc, pose = og.state()
+    xt = x.copy()  # inertia term zero at xt = x
+    g, fcon = og.gradient(x, xt, 100.0, pose)
+    fixed = wl.gel.dirichlet == 1
+    reaction = g[fixed].sum(0)  # force the supports exert on the gel (= dE/dx at fixed nodes)
+    np.testing.assert_allclose(reaction + fcon, 0.0, atol=1e-6 * abs(fcon[2]))
+    assert fcon[2] < 0
+
+
+def test_affine_patch_test():
+    """Linear tets reproduce an affine deformation prescribed on the whole boundary."""
+    gel = W.gel_grid(5, 5, 5, (0.004, 0.004, 0.004))
+    X = gel.verts
+    onb = np.any((X <= 1e-12) | (X >= 0.004 - 1e-12), axis=1).astype(np.uint8)
+    A = np.array([[1.02, 0.01, -0.005], [0.0, 0.99, 0.01], [0.003, 0.0, 1.01]])
+    xa = X @ A.T + np.array([1e-4, 0, 0])
+    ind = W.icosphere(0.001, 0)
+    far = W.pose((0.0, 0.0, 1.0))
+    og = O.OracleGel(X, gel.tets, onb, (E_, NU_, RHO_), ind.verts, ind.tris, far, newton_tol=1e-9)
+    x0 = np.where(onb[:, None] == 1, xa, X)
+    og.set_state(x0, np.zeros_like(X), far)
+    info = og.step(far, 1e4)
+    x, _, _, _ = og.state()
+    assert info["status"] == 0
+    assert np.abs(x - xa).max() < 1e-10  # vs affine displacements of ~1e-4 m
+
+
+def test_newton_matches_direct_minimisation():
+    """The oracle's Newton step reaches the same minimiser as a general-purpose quasi-Newton
+    minimiser (scipy L-BFGS-B) applied to the oracle's own energy and gradient."""
+    from scipy.optimize import minimize
+    wl = small_scene(depth=0.25e-3, steps=12, grid=(4, 4, 3), size=(0.006, 0.006, 0.003), r=0.003)
+    og = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    for s in range(12):
+        x0, v0, _, p_prev = og.state()
+        info = og.step(wl.poses[s], wl.dt)
+        assert info["status"] == 0
+        if s >= 6 and info["substeps"] == 1 and info["active_pairs"] > 0:
+            break
+    x, v, _, pose = og.state()
+    # replay that step with L-BFGS from x_n on the same energy
+    assert info["substeps"] == 1 and info["active_pairs"] > 0
+    h = wl.dt
+    xt = x0 + h * v0
+    free = wl.gel.dirichlet == 0
+
+    S = 1e-6  # optimise in micrometres around the oracle's answer, energies in micro-joules
+
+    def f(z):
+        y = x0.copy()
+        y[free] = x[free] + S * z.reshape(-1, 3)
+        e, _ = og.energy(y, xt, h, pose)
+        if not np.isfinite(e):
+            return 1e30, np.zeros_like(z)
+        g, _ = og.gradient(y, xt, h, pose)
+        return e * 1e6, g[free].ravel() * S * 1e6
+    z0 = np.full(3 * int(free.sum()), 0.1)  # start 0.1 um away along every coordinate
+    r = minimize(f, z0, jac=True, method="L-BFGS-B",
+                 options=dict(maxiter=5000, ftol=1e-30, gtol=1e-16, maxcor=50))
+    assert np.abs(r.x).max() * S < 1e-10
