@@ -1,0 +1,215 @@
+/*
+ * tx_gel.h -- C ABI of the GB300 gelpad IPC step library (libtxgel.so).
+ *
+ * One implicit time step of a GelSight gelpad pressed by a kinematic rigid indenter, solved as an
+ * incremental-potential-contact minimisation.  TacEx (arXiv 2411.04776), Sec. "General GIPC
+ * Simulation Pipeline": each GIPC step first sets the kinematic targets (here: the indenter pose)
+ * and then runs the solver that computes the new positions of the free gel vertices; the solver
+ * is IPC [Li et al. 2020] (TacEx App. A "Choice of the Simulation Methods": intersection- and
+ * inversion-free).  Per step the library minimises
+ *
+ *   E(x) = sum_i m_i |x_i - xt_i|^2 / (2 h^2) + sum_t V_t Psi_NH(F_t) + kappa sum_k b(d_k),
+ *   Psi_NH(F) = mu/2 (tr F^T F - 3) - mu ln J + lambda/2 ln^2 J,   b(d) = -(d - dhat)^2 ln(d/dhat),
+ *
+ * (xt = x_n + h v_n) by projected Newton: PSD-projected per-tet and per-contact Hessians, a
+ * block-Jacobi PCG direction, a step capped by additive CCD and det F > 0, and backtracking.
+ *
+ * Conventions (all entry points):
+ *   - SI units, FP64 at the boundary; arrays are row-major AoS (vertex k at [3k, 3k+3)).
+ *   - Host pointers unless an argument says "device".  The library copies every input it keeps;
+ *     the caller keeps ownership of all arrays it passes.
+ *   - A `stream` argument is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *     device work of a handle is ordered on that stream.  Calls on one handle must not overlap
+ *     (thread-compatible, not thread-safe); distinct handles are independent.
+ *   - Errors are returned as tx_status; no exception crosses the ABI.  A failed step leaves the
+ *     state at x_n (steps are transactional).  TX_ERR_CUDA reports a CUDA runtime error; its text
+ *     is available from tx_last_error().
+ */
+#ifndef TX_GEL_H
+#define TX_GEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tx_status {
+  TX_OK = 0,
+  TX_ERR_ARG = 1,            /* invalid argument (null pointer, size, index out of range)      */
+  TX_ERR_OOM = 2,            /* device or host allocation failed                               */
+  TX_ERR_MESH_INVERTED = 3,  /* a rest tetrahedron has non-positive volume                     */
+  TX_ERR_INFEASIBLE = 4,     /* indenter placement penetrates the gel even after step splitting */
+  TX_ERR_NEWTON_MAXIT = 5,   /* Newton iteration cap reached                                   */
+  TX_ERR_PCG_MAXIT = 6,      /* PCG iteration cap reached (only if params ask to fail on it)   */
+  TX_ERR_LINESEARCH = 7,     /* backtracking found no energy decrease above 1e-12 alpha_0       */
+  TX_ERR_CCD_MAXIT = 8,      /* ACCD iteration cap reached                                     */
+  TX_ERR_CUDA = 9,           /* CUDA runtime error (see tx_last_error)                         */
+  TX_ERR_DEVICE_TIMEOUT = 10 /* a bounded device-side wait gave up (kernel returned early)     */
+} tx_status;
+
+typedef enum tx_precision {
+  TX_PREC_FP64 = 0,  /* every step of the solve in FP64                                         */
+  TX_PREC_MIXED = 1  /* elastic Hessian blocks + PCG matvecs in FP32 with FP64 residual
+                        refinement; gradient, barrier, CCD and line-search energy stay FP64      */
+} tx_precision;
+
+/* Solver parameters.  tx_params_default() fills the values used by the GelSight workloads. */
+typedef struct tx_params {
+  double dhat;          /* barrier activation distance d_hat [m] (default 1e-4)                 */
+  double kappa;         /* barrier stiffness [N/m]; <= 0 selects E * mean gel surface edge length */
+  double newton_tol;    /* stop when ||p||_inf / h < newton_tol * (rest bbox diagonal) [1/s]     */
+  double pcg_rel_tol;   /* PCG stops at ||r|| <= pcg_rel_tol * ||g|| (inexact Newton, 1e-3)      */
+  double gravity[3];    /* body acceleration [m/s^2] (default 0)                                 */
+  int32_t newton_max_iter;  /* default 200                                                     */
+  int32_t pcg_max_iter;     /* default 2000; hitting it keeps the direction (still descent)     */
+  int32_t ls_max_halvings;  /* default 60                                                      */
+  int32_t accd_max_iter;    /* default 1000000                                                 */
+  int32_t max_split_depth;  /* infeasible indenter moves are halved up to this depth (4)       */
+  int32_t precision;        /* tx_precision                                                     */
+  int32_t refine_max;       /* mixed precision: max FP64 residual refinement rounds (3)         */
+  int32_t reserved;
+} tx_params;
+
+void tx_params_default(tx_params* p);
+
+/* One gel + indenter scene.  The gel is a tet mesh (rest positions, positively oriented tets,
+ * Dirichlet mask: 1 = vertex held at its rest position).  The indenter is a rigid triangle mesh
+ * given in its own frame, placed in the world by a pose (qw, qx, qy, qz, tx, ty, tz). */
+typedef struct tx_gel_desc {
+  int32_t n_verts;
+  const double* verts;       /* n_verts x 3 rest positions [m]                                  */
+  int32_t n_tets;
+  const int32_t* tets;       /* n_tets x 4 vertex ids                                           */
+  const uint8_t* dirichlet;  /* n_verts; may be NULL (no fixed vertex)                          */
+  double young;              /* Young's modulus E [Pa]                                          */
+  double poisson;            /* Poisson ratio nu (< 0.5)                                        */
+  double density;            /* rho [kg/m^3]                                                    */
+  int32_t n_ind_verts;
+  const double* ind_verts;   /* n_ind_verts x 3, indenter frame [m]                             */
+  int32_t n_ind_tris;
+  const int32_t* ind_tris;   /* n_ind_tris x 3                                                  */
+  double ind_pose[7];        /* initial indenter pose                                           */
+  tx_params params;
+} tx_gel_desc;
+
+/* Per-step record (last completed step of a gel). */
+typedef struct tx_step_stats {
+  int32_t newton_iters;     /* accepted Newton updates over all substeps                        */
+  int32_t pcg_iters;        /* total PCG iterations                                             */
+  int32_t ls_halvings;      /* total line-search halvings                                       */
+  int32_t substeps;         /* solves run (1 unless the indenter move had to be split)           */
+  int32_t active_pairs;     /* contact pairs with d < d_hat at the final state                  */
+  int32_t candidate_pairs;  /* broad-phase candidates at the final state                        */
+  int32_t refine_rounds;    /* mixed precision: FP64 refinement rounds used                      */
+  int32_t status;           /* tx_status of the step                                            */
+  double energy;            /* E at the final state                                             */
+  double min_distance;      /* smallest candidate-pair distance at the final state [m]          */
+  double contact_force[3];  /* force of the indenter on the gel, -kappa sum grad b [N]           */
+  double mean_position[3];  /* mean of the gel vertex positions (TacEx "object position") [m]    */
+} tx_step_stats;
+
+typedef struct tx_gel tx_gel;     /* opaque single-gel handle                                  */
+typedef struct tx_batch tx_batch; /* opaque many-gel handle                                    */
+
+const char* tx_status_str(tx_status s);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* tx_last_error(void);
+
+/* ---------------- single gel ---------------- */
+
+/* Validates and copies the description, precomputes rest data (Dm^-1, volumes, lumped masses,
+ * surface, BSR pattern), allocates device memory and uploads.  Returns TX_ERR_MESH_INVERTED if a
+ * rest tet has det(Dm) <= 0, TX_ERR_ARG on bad sizes/indices. */
+tx_status tx_gel_create(const tx_gel_desc* desc, void* stream, tx_gel** out);
+
+/* Advances one time step of length dt with the indenter moving (linearly in position, along the
+ * short arc in rotation) from its current pose to `pose`.  Blocks until the step has finished. */
+tx_status tx_gel_step(tx_gel* g, const double pose[7], double dt);
+
+/* Reads the state: x, v (n_verts x 3, may be NULL), contact force (3, may be NULL) and the last
+ * step's statistics (may be NULL).  If device_ptrs != 0, x and v are device pointers and the copy
+ * is enqueued on the gel's stream (ordered after the last step); otherwise host pointers and the
+ * call returns after the copy. */
+tx_status tx_gel_state(const tx_gel* g, double* x, double* v, double f_contact[3],
+                       tx_step_stats* stats, int32_t device_ptrs);
+
+/* Checkpoint / restore of x, v (host arrays, n_verts x 3) and the indenter pose. */
+tx_status tx_gel_get_state(const tx_gel* g, double* x, double* v, double pose[7]);
+tx_status tx_gel_set_state(tx_gel* g, const double* x, const double* v, const double pose[7]);
+
+/* TacEx Sec. "General GIPC Simulation Pipeline" (reset for RL): x = rest positions, v = 0, the
+ * indenter back at its initial pose. */
+tx_status tx_gel_reset(tx_gel* g);
+
+void tx_gel_destroy(tx_gel* g);
+
+/* Device bytes a gel created from `desc` will hold (for admission control). */
+size_t tx_gel_footprint_bytes(const tx_gel_desc* desc);
+
+/* Evaluates E at the positions x (host, n_verts x 3) with predictor xt (host), step h and the
+ * indenter at `pose`, on the device.  parts = [inertia, elastic, barrier, min distance, active
+ * pairs] (may be NULL).  Does not change the state. */
+tx_status tx_gel_energy(tx_gel* g, const double* x, const double* xt, double h,
+                        const double pose[7], double* energy, double parts[5]);
+
+/* Gradient of E (host out, n_verts x 3, Dirichlet rows included) and contact force at x. */
+tx_status tx_gel_gradient(tx_gel* g, const double* x, const double* xt, double h,
+                          const double pose[7], double* grad, double f_contact[3]);
+
+/* ---------------- many gels (batched, continuous) ---------------- */
+
+/* Creates one handle over n gels of any sizes; all state stays resident on the device. */
+tx_status tx_batch_create(const tx_gel_desc* descs, int32_t n, void* stream, tx_batch** out);
+void tx_batch_destroy(tx_batch* b);
+int32_t tx_batch_size(const tx_batch* b);
+
+/* Steps every gel once (poses: n x 7, dts: n) and blocks until all finished.  statuses: n. */
+tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_status* statuses);
+
+/* Continuous batching.  submit() queues one step request for each listed gel (a gel may hold
+ * at most one request in flight: TX_ERR_ARG otherwise); the request is admitted at the next
+ * Newton-iteration boundary.  advance() runs one Newton iteration for every admitted gel and
+ * reports the gels whose step finished (done_ids/done_status: capacity n each). */
+tx_status tx_batch_submit(tx_batch* b, int32_t count, const int32_t* ids, const double* poses,
+                          const double* dts);
+tx_status tx_batch_advance(tx_batch* b, int32_t* n_done, int32_t* done_ids,
+                           tx_status* done_status);
+/* Number of gels with a request submitted or in flight. */
+int32_t tx_batch_pending(const tx_batch* b);
+
+tx_status tx_batch_state(const tx_batch* b, int32_t gel, double* x, double* v,
+                         double f_contact[3], tx_step_stats* stats);
+tx_status tx_batch_set_state(tx_batch* b, int32_t gel, const double* x, const double* v,
+                             const double pose[7]);
+tx_status tx_batch_reset(tx_batch* b, int32_t gel);
+
+/* ---------------- unit-level kernels (device pointers, for parity checks and reuse) --------- */
+
+/* Per-tet elastic energy V Psi, gradient (12) and Hessian (144, row-major; PSD-projected in the
+ * deformation-gradient space if project != 0).  X, x: n x 12 (4 corners x 3), rest and current.
+ * e: n, g: n x 12, H: n x 144; g and H may be NULL (energy only).  All device pointers. */
+tx_status tx_eval_tets(int32_t n, const double* X, const double* x, double mu, double lambda,
+                       int32_t project, double* e, double* g, double* H, void* stream);
+
+/* Per-pair barrier b (without kappa), gradient (12) and Hessian (144) w.r.t. the 4 points of
+ * each pair; kind 0: point P0 vs triangle P1..P3, kind 1: segment P0P1 vs segment P2P3 (IPC
+ * edge-edge mollifier with threshold eps_x[i]).  If free_mask[i] != 0, the Hessian block on the
+ * points whose bit is set is PSD-projected.  dtype[i] = [formula, i0..i3] (5 ints) of the closest
+ * feature pair.  All device pointers; free_mask, dtype may be NULL. */
+tx_status tx_eval_pairs(int32_t n, const int32_t* kind, const double* P, double dhat,
+                        const double* eps_x, const int32_t* free_mask, double* b, double* g,
+                        double* H, int32_t* dtype, void* stream);
+
+/* Additive CCD per pair along P + t dP (n x 12 each), s = gap fraction (0.1), t in [0, tc].
+ * hit[i]: 0 no hit, 1 hit (toi[i] set), 2 iteration cap.  Device pointers. */
+tx_status tx_eval_accd(int32_t n, const int32_t* kind, const double* P, const double* dP,
+                       double s, double tc, int32_t max_iter, double* toi, int32_t* hit,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TX_GEL_H */

@@ -1,0 +1,288 @@
+// Elastic term of the incremental potential: compressible Neo-Hookean tetrahedra (IPC's variant,
+// Li et al. 2020, which the GIPC solver embedded by TacEx builds on):
+//   Psi(F) = mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2,   F = Ds Dm^-1,  J = det F.
+//
+// Per tet (one thread each): energy V Psi, gradient V P D_a (P = dPsi/dF = mu F + (lambda ln J -
+// mu) F^-T) and the 12x12 Hessian PSD-projected in deformation-gradient space with the analytic
+// eigensystem of isotropic energies (Smith, de Goes & Kim 2019, "Analytic Eigensystems for
+// Isotropic Distortion Energies"): in the frame of the SVD F = U S V^T the tangent is block
+// diagonal -- a 3x3 "scaling" block d2Psi/dsigma2 on the diagonal entries and, for every pair
+// i < j, a 2x2 block on (F_ij, F_ji) whose eigenvalues are
+//   twist  (antisymmetric mode):  mu - (mu - lambda ln J) / (s_i s_j)
+//   flip   (symmetric mode):      mu + (mu - lambda ln J) / (s_i s_j)
+// Negative eigenvalues are clamped to zero and the clamped tangent is mapped to the vertex
+// blocks  H_ab = V U Hhat_ab U^T  with  Hhat_ab[i][l] = sum_{jm} Dhat_a[j] Dhat_b[m] Chat[(ij),(lm)],
+// Dhat_a = V^T D_a.  Only the 10 blocks a <= b are written.
+//
+// The energy used by the line search is evaluated in the displacement-gradient form
+// (H = F - I from u = x - X, j = J - 1 = tr H + c2 + c3) to avoid the O(1) cancellation of the
+// literal formula near rest; it is the same function.
+#pragma once
+#include "txgel_common.cuh"
+
+namespace txg {
+
+// ---------------------------------------------------------------- small dense linear algebra
+template <typename R>
+__device__ __forceinline__ void jacobi3(R a[3][3], R w[3], R V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? R(1) : R(0);
+  const R tiny = sizeof(R) == 8 ? R(1e-30) : R(1e-13);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    R off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    R dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (!(off > tiny * dg)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const int r = 3 - p - q;
+      R apq = a[p][q];
+      if (apq == R(0)) continue;
+      R theta = (a[q][q] - a[p][p]) / (R(2) * apq);
+      R t = (theta >= R(0) ? R(1) : R(-1)) / (fabs(theta) + sqrt(theta * theta + R(1)));
+      R c = R(1) / sqrt(t * t + R(1));
+      R s = t * c;
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = R(0);
+      R arp = a[r][p], arq = a[r][q];
+      a[r][p] = a[p][r] = c * arp - s * arq;
+      a[r][q] = a[q][r] = s * arp + c * arq;
+      for (int k = 0; k < 3; ++k) {
+        R vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  w[0] = a[0][0];
+  w[1] = a[1][1];
+  w[2] = a[2][2];
+}
+
+template <typename R>
+__device__ __forceinline__ R det3(const R F[3][3]) {
+  return F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+         F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+}
+
+// j - ln(1 + j): alternating series for |j| < 0.1 (22 terms, error < 1e-23 j^2), else direct
+__device__ __forceinline__ double j_minus_log1p(double j) {
+  if (fabs(j) < 0.1) {
+    double s = 0.0;
+    for (int k = 22; k >= 2; --k) s = s * j + ((k & 1) ? -1.0 : 1.0) / k;
+    return s * j * j;
+  }
+  return j - log1p(j);
+}
+
+// V Psi from the displacement gradient H = F - I; +inf when J <= 0
+__device__ __forceinline__ double psi_disp(const double H[3][3], double mu, double lam) {
+  double tr = H[0][0] + H[1][1] + H[2][2];
+  double n2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) n2 += H[i][k] * H[i][k];
+  double c2 = H[0][0] * H[1][1] - H[0][1] * H[1][0] + H[0][0] * H[2][2] - H[0][2] * H[2][0] +
+              H[1][1] * H[2][2] - H[1][2] * H[2][1];
+  double c3 = det3(H);
+  double j = tr + c2 + c3;
+  if (!(j > -1.0)) return CUDART_INF;
+  double L = log1p(j);
+  return 0.5 * mu * n2 - mu * (c2 + c3) + mu * j_minus_log1p(j) + 0.5 * lam * L * L;
+}
+
+// dF/dx_a = D[a] (outer structure): D[a] = row a-1 of Dm^-1, D[0] = -sum
+__device__ __forceinline__ void tet_D(const double* Dmi, double D[4][3]) {
+  for (int j = 0; j < 3; ++j) {
+    D[1][j] = Dmi[j];
+    D[2][j] = Dmi[3 + j];
+    D[3][j] = Dmi[6 + j];
+    D[0][j] = -(D[1][j] + D[2][j] + D[3][j]);
+  }
+}
+
+// F (and H = F - I through displacements when X given) of one tet
+__device__ __forceinline__ void tet_F(const double xs[4][3], const double Xs[4][3], const double D[4][3],
+                                      double F[3][3], double Hd[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double f = 0.0, h = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        f += xs[a][i] * D[a][j];
+        h += (xs[a][i] - Xs[a][i]) * D[a][j];
+      }
+      F[i][j] = f;
+      Hd[i][j] = h;
+    }
+}
+
+__host__ __device__ __forceinline__ int ublk(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
+
+// Projected Hessian blocks (10 x 9 values, block (a<=b) at ublk(a,b)*9, row-major 3x3) in
+// precision R.  F, J and ln J come in FP64 (the gradient needs them there anyway).
+template <typename R, typename OutT>
+__device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, double lnJd, double mu_d, double lam_d,
+                          double vol_d, const double Dd[4][3], bool project, OutT* out) {
+  R F[3][3], D[4][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) F[i][j] = (R)Fd[i][j];
+  for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < 3; ++j) D[a][j] = (R)Dd[a][j];
+  const R mu = (R)mu_d, lam = (R)lam_d, vol = (R)vol_d;
+  // SVD of F through the eigen-decomposition of F^T F
+  R C[3][3], s2[3], V[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+  jacobi3<R>(C, s2, V);
+  int o0 = 0, o1 = 1, o2 = 2;  // descending order of s2
+  if (s2[o0] < s2[o1]) { int t = o0; o0 = o1; o1 = t; }
+  if (s2[o1] < s2[o2]) { int t = o1; o1 = o2; o2 = t; }
+  if (s2[o0] < s2[o1]) { int t = o0; o0 = o1; o1 = t; }
+  R sg[3];
+  sg[o0] = sqrt(fmax(s2[o0], R(0)));
+  sg[o1] = sqrt(fmax(s2[o1], R(0)));
+  R U[3][3];
+  {
+    R u0[3], u1[3];
+    for (int i = 0; i < 3; ++i) {
+      u0[i] = F[i][0] * V[0][o0] + F[i][1] * V[1][o0] + F[i][2] * V[2][o0];
+      u1[i] = F[i][0] * V[0][o1] + F[i][1] * V[1][o1] + F[i][2] * V[2][o1];
+    }
+    R n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    for (int i = 0; i < 3; ++i) u0[i] /= n0;
+    R d = u0[0] * u1[0] + u0[1] * u1[1] + u0[2] * u1[2];
+    for (int i = 0; i < 3; ++i) u1[i] -= d * u0[i];
+    R n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    for (int i = 0; i < 3; ++i) u1[i] /= n1;
+    R u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2],
+               u0[0] * u1[1] - u0[1] * u1[0]};
+    for (int i = 0; i < 3; ++i) {
+      U[i][o0] = u0[i];
+      U[i][o1] = u1[i];
+      U[i][o2] = u2[i];
+    }
+    // det U must equal det V (J > 0)
+    if ((det3(U) > R(0)) != (det3(V) > R(0)))
+      for (int i = 0; i < 3; ++i) U[i][o2] = -U[i][o2];
+  }
+  sg[o2] = (R)Jd / (sg[o0] * sg[o1]);
+  const R m = mu - lam * (R)lnJd;  // mu - lambda ln J
+  // scaling block
+  R A[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      A[i][j] = (i == j) ? mu + (m + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
+  R Ap[3][3];
+  if (project) {
+    R w[3], Q[3][3];
+    R Ac[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ac[i][j] = A[i][j];
+    jacobi3<R>(Ac, w, Q);
+    for (int i = 0; i < 3; ++i) w[i] = fmax(w[i], R(0));
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ap[i][j] = Q[i][0] * w[0] * Q[j][0] + Q[i][1] * w[1] * Q[j][1] + Q[i][2] * w[2] * Q[j][2];
+  } else {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ap[i][j] = A[i][j];
+  }
+  // pair blocks: pq[i][j] (i != j): diagonal p and off-diagonal q of the 2x2 block
+  R P2[3][3], Q2[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      if (i == j) { P2[i][j] = Q2[i][j] = R(0); continue; }
+      R k = m / (sg[i] * sg[j]);
+      R lt = mu - k, lf = mu + k;  // twist (antisymmetric), flip (symmetric)
+      if (project) { lt = fmax(lt, R(0)); lf = fmax(lf, R(0)); }
+      P2[i][j] = R(0.5) * (lf + lt);
+      Q2[i][j] = R(0.5) * (lf - lt);
+    }
+  // Dhat_a = V^T D_a
+  R Dh[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i) Dh[a][i] = V[0][i] * D[a][0] + V[1][i] * D[a][1] + V[2][i] * D[a][2];
+  for (int a = 0; a < 4; ++a)
+    for (int b = a; b < 4; ++b) {
+      R Hh[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l) {
+          if (i == l) {
+            R s = Dh[a][i] * Dh[b][i] * Ap[i][i];
+            for (int j = 0; j < 3; ++j)
+              if (j != i) s += Dh[a][j] * Dh[b][j] * P2[i][j];
+            Hh[i][i] = s;
+          } else {
+            Hh[i][l] = Dh[a][i] * Dh[b][l] * Ap[i][l] + Dh[a][l] * Dh[b][i] * Q2[i][l];
+          }
+        }
+      // U Hh U^T
+      R T[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l) T[i][l] = Hh[i][0] * U[l][0] + Hh[i][1] * U[l][1] + Hh[i][2] * U[l][2];
+      OutT* o = out + ublk(a, b) * 9;
+      for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l)
+          o[3 * i + l] = (OutT)(vol * (U[i][0] * T[0][l] + U[i][1] * T[1][l] + U[i][2] * T[2][l]));
+    }
+}
+
+// Gradient of V Psi (12) and energy; returns false if J <= 0
+__device__ __forceinline__ bool nh_grad(const double F[3][3], const double Hd[3][3], double mu,
+                                        double lam, double vol, const double D[4][3], double g[12],
+                                        double* e, double* Jo, double* lnJo) {
+  double tr = Hd[0][0] + Hd[1][1] + Hd[2][2];
+  double c2 = Hd[0][0] * Hd[1][1] - Hd[0][1] * Hd[1][0] + Hd[0][0] * Hd[2][2] - Hd[0][2] * Hd[2][0] +
+              Hd[1][1] * Hd[2][2] - Hd[1][2] * Hd[2][1];
+  double j = tr + c2 + det3(Hd);
+  if (!(j > -1.0)) return false;
+  double J = 1.0 + j, lnJ = log1p(j);
+  // F^-T = cof(F) / J
+  double cof[3][3];
+  cof[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+  cof[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+  cof[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+  cof[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+  cof[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+  cof[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+  cof[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+  cof[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+  cof[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  const double k = (lam * lnJ - mu) / J;
+  double P[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int l = 0; l < 3; ++l) P[i][l] = mu * F[i][l] + k * cof[i][l];
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i) g[3 * a + i] = vol * (P[i][0] * D[a][0] + P[i][1] * D[a][1] + P[i][2] * D[a][2]);
+  if (e) *e = vol * psi_disp(Hd, mu, lam);
+  *Jo = J;
+  *lnJo = lnJ;
+  return true;
+}
+
+// Energy of one tet at x + alpha p (the line-search trial point); used by the energy kernel.
+__device__ __forceinline__ double tet_energy_at(const Dev& d, int t, double alpha, double mu, double lam) {
+  const int4 tv = d.tets[t];
+  const int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+  double D[4][3], Hd[3][3];
+  tet_D(d.Dminv + 9 * t, D);
+  double u[4][3];
+  for (int a = 0; a < 4; ++a) {
+    const double4_32a x = d.x[ids[a]], X = d.X[ids[a]];
+    u[a][0] = x.x - X.x;
+    u[a][1] = x.y - X.y;
+    u[a][2] = x.z - X.z;
+    if (alpha != 0.0) {
+      const double4_32a p = d.p[ids[a]];
+      u[a][0] += alpha * p.x;
+      u[a][1] += alpha * p.y;
+      u[a][2] += alpha * p.z;
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Hd[i][j] = u[0][i] * D[0][j] + u[1][i] * D[1][j] + u[2][i] * D[2][j] + u[3][i] * D[3][j];
+  return d.vol[t] * psi_disp(Hd, mu, lam);
+}
+
+}  // namespace txg

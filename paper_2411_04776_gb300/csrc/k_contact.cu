@@ -1,0 +1,512 @@
+// Contact kernels: indenter placement, spatial-hash broad phase, barrier assembly, ACCD.
+//
+// Broad phase.  Per gel, the indenter's primitives (triangles, vertices, edges: three tables)
+// are inserted into a spatial hash (Teschner et al. 2003): every primitive goes into each cell
+// of a uniform grid its bounding box overlaps, cells are hashed into a power-of-two bucket array
+// (counting sort, then each bucket sorted by (primitive, cell) so the table is deterministic).
+// The gel surface primitives query it: vertices -> indenter triangles, triangles -> indenter
+// vertices, edges -> indenter edges.  A pair is a candidate when the two bounding boxes (each
+// swept over the motion under test) come within dhat of each other along every axis; it is
+// reported from exactly one cell (the lowest cell of the two boxes' common cell range), counted
+// first, prefix-summed, then written, so the candidate list is ordered and identical run to run.
+#include "dev_contact.cuh"
+
+namespace txg {
+
+constexpr int HMAXC = 1023;       // cell coordinates are clamped to [0, HMAXC]
+constexpr int QUERY_CELL_LIMIT = 4096;
+constexpr int BUILD_CELL_LIMIT = 512;  // a primitive spanning more cells turns the table brute-force
+
+__device__ __forceinline__ int cell_of(double v, double org, double inv_cell) {
+  double c = floor((v - org) * inv_cell);
+  c = fmin(fmax(c, 0.0), (double)HMAXC);
+  return (int)c;
+}
+__device__ __forceinline__ unsigned hash_cell(int ix, int iy, int iz) {
+  return ((unsigned)ix * 73856093u) ^ ((unsigned)iy * 19349663u) ^ ((unsigned)iz * 83492791u);
+}
+__device__ __forceinline__ int pack_cell(int ix, int iy, int iz) { return ix | (iy << 10) | (iz << 20); }
+
+struct Box {
+  double lo[3], hi[3];
+};
+__device__ __forceinline__ void box_init(Box& b) {
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] = CUDART_INF;
+    b.hi[c] = -CUDART_INF;
+  }
+}
+__device__ __forceinline__ void box_add(Box& b, double x, double y, double z) {
+  b.lo[0] = fmin(b.lo[0], x); b.hi[0] = fmax(b.hi[0], x);
+  b.lo[1] = fmin(b.lo[1], y); b.hi[1] = fmax(b.hi[1], y);
+  b.lo[2] = fmin(b.lo[2], z); b.hi[2] = fmax(b.hi[2], z);
+}
+__device__ __forceinline__ bool near_boxes(const Box& a, const Box& b, double pad) {
+  for (int c = 0; c < 3; ++c)
+    if (a.lo[c] - pad > b.hi[c] || b.lo[c] - pad > a.hi[c]) return false;
+  return true;
+}
+
+// bounding box of indenter primitive k of table `tab` (global index), optionally swept
+__device__ __forceinline__ Box ind_box(const Dev& d, int tab, int k, bool swept) {
+  Box b;
+  box_init(b);
+  int ids[3], n;
+  if (tab == 0) {
+    const int4 t = d.it[k];
+    ids[0] = t.x; ids[1] = t.y; ids[2] = t.z; n = 3;
+  } else if (tab == 1) {
+    ids[0] = k; n = 1;
+  } else {
+    const int2 e = d.ie[k];
+    ids[0] = e.x; ids[1] = e.y; n = 2;
+  }
+  for (int m = 0; m < n; ++m) {
+    const double4_32a q = d.iv_cur[ids[m]];
+    box_add(b, q.x, q.y, q.z);
+    if (swept) {
+      const double4_32a r = d.iv_prev[ids[m]];
+      box_add(b, r.x, r.y, r.z);
+    }
+  }
+  return b;
+}
+
+// bounding box of gel surface primitive (type, global index), optionally swept by p
+__device__ __forceinline__ Box gel_box(const Dev& d, int type, int k, bool swept) {
+  Box b;
+  box_init(b);
+  int rows[3], n;
+  if (type == PAIR_PT) {
+    rows[0] = d.sv[k]; n = 1;
+  } else if (type == PAIR_TP) {
+    const int4 t = d.st[k];
+    rows[0] = t.x; rows[1] = t.y; rows[2] = t.z; n = 3;
+  } else {
+    const int2 e = d.se[k];
+    rows[0] = e.x; rows[1] = e.y; n = 2;
+  }
+  for (int m = 0; m < n; ++m) {
+    const double4_32a x = d.x[rows[m]];
+    box_add(b, x.x, x.y, x.z);
+    if (swept) {
+      const double4_32a p = d.p[rows[m]];
+      box_add(b, x.x + p.x, x.y + p.y, x.z + p.z);
+    }
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------- indenter placement
+__global__ void k_indenter_pose(Dev d, int phase) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.niv_total) return;
+  const int g = d.iv_gel[k];
+  if (d.gc[g].phase != phase) return;
+  const GelCtl& c = d.gc[g];
+  const double4_32a v = d.iv_loc[k];
+  double4_32a a, b;
+  a.x = c.R[0] * v.x + c.R[1] * v.y + c.R[2] * v.z + c.t[0];
+  a.y = c.R[3] * v.x + c.R[4] * v.y + c.R[5] * v.z + c.t[1];
+  a.z = c.R[6] * v.x + c.R[7] * v.y + c.R[8] * v.z + c.t[2];
+  a.w = 0.0;
+  b.x = c.Rp[0] * v.x + c.Rp[1] * v.y + c.Rp[2] * v.z + c.tp[0];
+  b.y = c.Rp[3] * v.x + c.Rp[4] * v.y + c.Rp[5] * v.z + c.tp[1];
+  b.z = c.Rp[6] * v.x + c.Rp[7] * v.y + c.Rp[8] * v.z + c.tp[2];
+  b.w = 0.0;
+  d.iv_cur[k] = a;
+  d.iv_prev[k] = b;
+}
+
+// ---------------------------------------------------------------- hash build (one CTA per table)
+constexpr int HB_THREADS = 256;
+
+__global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int swept) {
+  const int g = blockIdx.x / NTAB, tab = blockIdx.x % NTAB;
+  if (d.gc[g].phase != phase) return;
+  const GelInfo& G = d.gi[g];
+  const int nb = G.hnb[tab], hb = G.hb0[tab], he = G.he0[tab], cap = G.hcap[tab];
+  const int n = tab == 0 ? G.nit : (tab == 1 ? G.niv : G.nie);
+  const int p0 = tab == 0 ? G.it0 : (tab == 1 ? G.iv0 : G.ie0);
+  const double ic = 1.0 / G.cell;
+  int* cnt = d.hcount + hb;
+  int* start = d.hstart + hb;
+  __shared__ int s_carry;
+  __shared__ int s_brute;
+  __shared__ int s_part[HB_THREADS];
+  if (threadIdx.x == 0) s_brute = 0;
+  for (int b = threadIdx.x; b <= nb; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const Box bx = ind_box(d, tab, p0 + k, swept != 0);
+    const int x0 = cell_of(bx.lo[0], G.org[0], ic), x1 = cell_of(bx.hi[0], G.org[0], ic);
+    const int y0 = cell_of(bx.lo[1], G.org[1], ic), y1 = cell_of(bx.hi[1], G.org[1], ic);
+    const int z0 = cell_of(bx.lo[2], G.org[2], ic), z1 = cell_of(bx.hi[2], G.org[2], ic);
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1) > BUILD_CELL_LIMIT) {
+      s_brute = 1;
+      continue;
+    }
+    for (int iz = z0; iz <= z1; ++iz)
+      for (int iy = y0; iy <= y1; ++iy)
+        for (int ix = x0; ix <= x1; ++ix) atomicAdd(&cnt[hash_cell(ix, iy, iz) & (nb - 1)], 1);
+  }
+  __syncthreads();
+  if (s_brute) {  // oversized primitive: every query of this table tests all primitives directly
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) start[b] = 0;
+    if (threadIdx.x == 0) d.gv[g].hent[tab] = -1;
+    return;
+  }
+  // exclusive scan of the bucket counts (fixed order)
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += HB_THREADS) {
+    const int b = base + threadIdx.x;
+    const int v = b < nb ? cnt[b] : 0;
+    s_part[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < HB_THREADS; off <<= 1) {
+      int t = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
+      __syncthreads();
+      s_part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (b < nb) start[b] = s_carry + s_part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == HB_THREADS - 1) s_carry += s_part[HB_THREADS - 1];
+    __syncthreads();
+  }
+  const int total = s_carry;
+  if (threadIdx.x == 0) {
+    start[nb] = total;
+    d.gv[g].hent[tab] = total;
+    if (total > cap) atomicOr(&d.gv[g].flags, 1);
+  }
+  if (total > cap) {  // leave an empty table; the host grows the capacity and rebuilds
+    __syncthreads();
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) start[b] = 0;
+    return;
+  }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = start[b];
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const Box bx = ind_box(d, tab, p0 + k, swept != 0);
+    const int x0 = cell_of(bx.lo[0], G.org[0], ic), x1 = cell_of(bx.hi[0], G.org[0], ic);
+    const int y0 = cell_of(bx.lo[1], G.org[1], ic), y1 = cell_of(bx.hi[1], G.org[1], ic);
+    const int z0 = cell_of(bx.lo[2], G.org[2], ic), z1 = cell_of(bx.hi[2], G.org[2], ic);
+    for (int iz = z0; iz <= z1; ++iz)
+      for (int iy = y0; iy <= y1; ++iy)
+        for (int ix = x0; ix <= x1; ++ix) {
+          const int pos = atomicAdd(&cnt[hash_cell(ix, iy, iz) & (nb - 1)], 1);
+          d.hent[he + pos] = make_int2(p0 + k, pack_cell(ix, iy, iz));
+        }
+  }
+  __syncthreads();
+  // deterministic order inside every bucket
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int s = start[b], e = start[b + 1];
+    for (int i = s + 1; i < e; ++i) {
+      const int2 key = d.hent[he + i];
+      int j = i - 1;
+      while (j >= s) {
+        const int2 o = d.hent[he + j];
+        if (o.x < key.x || (o.x == key.x && o.y <= key.y)) break;
+        d.hent[he + j + 1] = o;
+        --j;
+      }
+      d.hent[he + j + 1] = key;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- hash query
+// mode bit 0: write (else count); bit 1: gel boxes swept by p; bit 2: indenter boxes swept;
+// bit 3: skip gels whose Newton iteration converged.  Counts of gels outside `phase` are left
+// untouched: every gel only uses the offsets of its own queries relative to its first one.
+__global__ void k_query(Dev d, int phase, int mode) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= d.nq) return;
+  const bool write = mode & 1, gsw = (mode >> 1) & 1, isw = (mode >> 2) & 1, skc = (mode >> 3) & 1;
+  const int g = d.q_gel[q];
+  if (d.gc[g].phase != phase) return;
+  if (skc && d.gv[g].converged) return;
+  const GelInfo& G = d.gi[g];
+  const int tp = d.q_tp[q];
+  const int type = tp >> 28, loc = tp & ((1 << 28) - 1);
+  const int gk = (type == PAIR_PT ? G.sv0 : (type == PAIR_TP ? G.st0 : G.se0)) + loc;
+  const int tab = type;
+  const Box qb = gel_box(d, type, gk, gsw);
+  const double pad = G.dhat, ic = 1.0 / G.cell;
+  int lo[3], hi[3];
+  for (int c = 0; c < 3; ++c) {
+    lo[c] = cell_of(qb.lo[c] - pad, G.org[c], ic);
+    hi[c] = cell_of(qb.hi[c] + pad, G.org[c], ic);
+  }
+  const long long ncell = (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+  int count = 0;
+  const int base = write ? d.qoff[q] - d.qoff[G.q0] : 0;
+  auto emit = [&](int P) {
+    if (write && base + count < G.pcap) d.pairs[G.pbase + base + count] = make_int4(type, gk, P, g);
+    ++count;
+  };
+  if (ncell > QUERY_CELL_LIMIT || d.gv[g].hent[tab] < 0) {
+    // enormous sweep: test every primitive of the table directly
+    const int n = tab == 0 ? G.nit : (tab == 1 ? G.niv : G.nie);
+    const int p0 = tab == 0 ? G.it0 : (tab == 1 ? G.iv0 : G.ie0);
+    for (int k = 0; k < n; ++k) {
+      const Box pb = ind_box(d, tab, p0 + k, isw);
+      if (near_boxes(qb, pb, pad)) emit(p0 + k);
+    }
+  } else {
+    const int nb = G.hnb[tab], hb = G.hb0[tab], he = G.he0[tab];
+    for (int iz = lo[2]; iz <= hi[2]; ++iz)
+      for (int iy = lo[1]; iy <= hi[1]; ++iy)
+        for (int ix = lo[0]; ix <= hi[0]; ++ix) {
+          const int key = pack_cell(ix, iy, iz);
+          const int bk = hash_cell(ix, iy, iz) & (nb - 1);
+          const int s = d.hstart[hb + bk], e = d.hstart[hb + bk + 1];
+          for (int m = s; m < e; ++m) {
+            const int2 ent = d.hent[he + m];
+            if (ent.y != key) continue;
+            const Box pb = ind_box(d, tab, ent.x, isw);
+            const int px = cell_of(pb.lo[0], G.org[0], ic), py = cell_of(pb.lo[1], G.org[1], ic),
+                      pz = cell_of(pb.lo[2], G.org[2], ic);
+            if (ix != max(lo[0], px) || iy != max(lo[1], py) || iz != max(lo[2], pz)) continue;
+            if (!near_boxes(qb, pb, pad)) continue;
+            emit(ent.x);
+          }
+        }
+  }
+  if (!write) d.qcount[q] = count;
+}
+
+__global__ void k_pair_ranges(Dev d, int phase, int skip_conv) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.n_gels) return;
+  if (d.gc[g].phase != phase) return;
+  if (skip_conv && d.gv[g].converged) return;
+  const GelInfo& G = d.gi[g];
+  const int n = d.qoff[G.q0 + G.nq] - d.qoff[G.q0];
+  d.gv[g].pair0 = G.pbase;
+  d.gv[g].npair = n;
+  if (n > G.pcap) atomicOr(&d.gv[g].flags, 32);
+}
+
+// the pair in slot i, if its gel is in `phase` (and, optionally, not converged)
+__device__ __forceinline__ bool pair_slot(const Dev& d, int i, int phase, bool skip_conv, int4& pr) {
+  const int g = d.pslot_gel[i];
+  if (d.gc[g].phase != phase) return false;
+  if (skip_conv && d.gv[g].converged) return false;
+  if (i - d.gi[g].pbase >= min(d.gv[g].npair, d.gi[g].pcap)) return false;
+  pr = d.pairs[i];
+  return true;
+}
+
+// ---------------------------------------------------------------- barrier assembly
+__device__ __forceinline__ int find_block(const Dev& d, int row, int col) {
+  const int s = row >> 5, lane = row & 31;
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    if (d.colidx[bp] == col) return bp;
+  }
+  return -1;
+}
+__device__ __forceinline__ size_t val_addr(int bp, int e) {
+  return (size_t)9 * (bp & ~31) + 32 * e + (bp & 31);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_contact_assemble(Dev d, int phase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.npslots) return;
+  int4 pr;
+  if (!pair_slot(d, i, phase, false, pr)) return;
+  const int g = pr.w;
+  const GelInfo& G = d.gi[g];
+  double P[4][3];
+  int rows[4];
+  pair_points(d, pr, 0.0, false, P, rows);
+  const int kind = pr.x == PAIR_EE ? 1 : 0;
+  double b, gr[12], H[144];
+  if (!pair_barrier_derivs(kind, P, G.dhat, pair_eps_x(d, pr), &b, gr, H, nullptr)) return;
+  atomicAdd(&d.gv[g].active_pairs, 1);
+  const double kap = G.kappa;
+  int slots[4], ns = 0;
+  for (int k = 0; k < 4; ++k)
+    if (rows[k] >= 0) slots[ns++] = k;
+  const int nf = 3 * ns;
+  double Hf[81];
+  for (int a = 0; a < nf; ++a)
+    for (int c = 0; c < nf; ++c)
+      Hf[a * nf + c] = kap * H[(3 * slots[a / 3] + a % 3) * 12 + 3 * slots[c / 3] + c % 3];
+  psd_clamp(nf, Hf);
+  for (int a = 0; a < ns; ++a) {
+    const int ra = rows[slots[a]];
+    for (int c = 0; c < 3; ++c) atomicAdd(&d.gv[g].fc[c], -kap * gr[3 * slots[a] + c]);
+    if (d.fixed[ra]) continue;
+    atomicAdd(&d.grad[ra].x, kap * gr[3 * slots[a] + 0]);
+    atomicAdd(&d.grad[ra].y, kap * gr[3 * slots[a] + 1]);
+    atomicAdd(&d.grad[ra].z, kap * gr[3 * slots[a] + 2]);
+    for (int c = 0; c < ns; ++c) {
+      const int rc = rows[slots[c]];
+      if (d.fixed[rc]) continue;
+      const int bp = find_block(d, ra, rc);
+      if (bp < 0) {
+        atomicOr(&d.gv[g].flags, 16);
+        continue;
+      }
+      for (int e = 0; e < 9; ++e) {
+        const double v = Hf[(3 * a + e / 3) * nf + 3 * c + e % 3];
+        if (MIXED)
+          atomicAdd(&d.vals32[val_addr(bp, e)], (float)v);
+        else
+          atomicAdd(&d.vals[val_addr(bp, e)], v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- ACCD and distances
+// mode 0: Newton step (gel moves by p, indenter fixed at cur); mode 1: indenter sweep prev -> cur
+// with the gel fixed at x.
+__global__ void __launch_bounds__(128) k_accd(Dev d, int phase, int mode, int maxit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.npslots) return;
+  int4 pr;
+  if (!pair_slot(d, i, phase, mode == 0, pr)) return;
+  const int g = pr.w;
+  double P[4][3], dP[4][3];
+  int rows[4];
+  pair_points(d, pr, 0.0, mode == 1, P, rows);
+  if (mode == 0) {
+    for (int k = 0; k < 4; ++k) {
+      if (rows[k] >= 0) {
+        const double4_32a p = d.p[rows[k]];
+        dP[k][0] = p.x; dP[k][1] = p.y; dP[k][2] = p.z;
+      } else {
+        dP[k][0] = dP[k][1] = dP[k][2] = 0.0;
+      }
+    }
+  } else {
+    double Q[4][3];
+    int r2[4];
+    pair_points(d, pr, 0.0, false, Q, r2);
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) dP[k][c] = Q[k][c] - P[k][c];
+  }
+  double toi = 1.0;
+  const int r = accd_pair(pr.x == PAIR_EE ? 1 : 0, P, dP, ACCD_S, 1.0, maxit, &toi);
+  if (r == 1) {
+    atomic_min_pos(&d.gv[g].toi_bits, toi);
+    atomicOr(&d.gv[g].flags, 8);
+  } else if (r == 2) {
+    atomicOr(&d.gv[g].flags, 2);
+  }
+}
+
+// smallest pair distance at (x, indenter cur)
+__global__ void k_min_dist(Dev d, int phase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.npslots) return;
+  int4 pr;
+  if (!pair_slot(d, i, phase, false, pr)) return;
+  const int g = pr.w;
+  double P[4][3];
+  int rows[4];
+  pair_points(d, pr, 0.0, false, P, rows);
+  DType ty;
+  const double D = pair_d2(pr.x == PAIR_EE ? 1 : 0, P, &ty);
+  atomic_min_pos(&d.gv[g].dmin_bits, sqrt(fmax(D, 0.0)));
+  if (D < d.gi[g].dhat * d.gi[g].dhat) atomicAdd(&d.gv[g].active_pairs, 1);
+}
+
+// ---------------------------------------------------------------- unit-level entries
+__global__ void k_eval_pairs(int n, const int* kind, const double* Pin, double dhat, const double* eps_x,
+                             const int* free_mask, double* bo, double* go, double* Ho, int* dtype) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double P[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int c = 0; c < 3; ++c) P[k][c] = Pin[12 * i + 3 * k + c];
+  double b = 0.0, g[12], H[144];
+  for (int k = 0; k < 12; ++k) g[k] = 0.0;
+  for (int k = 0; k < 144; ++k) H[k] = 0.0;
+  DType ty;
+  const bool act = pair_barrier_derivs(kind[i], P, dhat, eps_x ? eps_x[i] : 0.0, &b, g, H, &ty);
+  if (dtype) {
+    dtype[5 * i] = ty.f;
+    for (int k = 0; k < 4; ++k) dtype[5 * i + 1 + k] = ty.i[k];
+  }
+  const int fm = free_mask ? free_mask[i] : 0;
+  if (act && fm) {
+    int idx[12], nf = 0;
+    for (int k = 0; k < 4; ++k)
+      if (fm & (1 << k))
+        for (int c = 0; c < 3; ++c) idx[nf++] = 3 * k + c;
+    double S[81];
+    for (int a = 0; a < nf; ++a)
+      for (int c = 0; c < nf; ++c) S[a * nf + c] = H[idx[a] * 12 + idx[c]];
+    psd_clamp(nf, S);
+    for (int a = 0; a < nf; ++a)
+      for (int c = 0; c < nf; ++c) H[idx[a] * 12 + idx[c]] = S[a * nf + c];
+  }
+  bo[i] = b;
+  if (go)
+    for (int k = 0; k < 12; ++k) go[12 * i + k] = g[k];
+  if (Ho)
+    for (int k = 0; k < 144; ++k) Ho[144 * i + k] = H[k];
+}
+
+__global__ void k_eval_accd(int n, const int* kind, const double* Pin, const double* dPin, double s,
+                            double tc, int maxit, double* toi, int* hit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double P[4][3], dP[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int c = 0; c < 3; ++c) {
+      P[k][c] = Pin[12 * i + 3 * k + c];
+      dP[k][c] = dPin[12 * i + 3 * k + c];
+    }
+  double t = 1.0;
+  hit[i] = accd_pair(kind[i], P, dP, s, tc, maxit, &t);
+  toi[i] = t;
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t st) {
+  if (n_ind_verts > 0) k_indenter_pose<<<nblk(n_ind_verts, 128), 128, 0, st>>>(d, phase);
+}
+void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st) {
+  k_hash_build<<<d.n_gels * NTAB, HB_THREADS, 0, st>>>(d, phase, swept);
+}
+void launch_query(const Dev& d, int phase, int mode, cudaStream_t st) {
+  if (d.nq > 0) k_query<<<nblk(d.nq, 128), 128, 0, st>>>(d, phase, mode);
+}
+void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st) {
+  k_pair_ranges<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, skip_conv);
+}
+void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
+  if (d.npslots <= 0) return;
+  if (mixed)
+    k_contact_assemble<true><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+  else
+    k_contact_assemble<false><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+}
+void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st) {
+  if (d.npslots > 0) k_accd<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode, maxit);
+}
+void launch_min_dist(const Dev& d, int phase, cudaStream_t st) {
+  if (d.npslots > 0) k_min_dist<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+}
+void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
+                       const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st) {
+  if (n > 0) k_eval_pairs<<<nblk(n, 64), 64, 0, st>>>(n, kind, P, dhat, eps_x, free_mask, b, g, H, dtype);
+}
+void launch_eval_accd(int n, const int* kind, const double* P, const double* dP, double s, double tc,
+                      int maxit, double* toi, int* hit, cudaStream_t st) {
+  if (n > 0) k_eval_accd<<<nblk(n, 128), 128, 0, st>>>(n, kind, P, dP, s, tc, maxit, toi, hit);
+}
+
+}  // namespace txg

@@ -1,0 +1,559 @@
+// Newton-system assembly, block-Jacobi PCG, incremental-potential energy and the per-gel
+// Newton / line-search bookkeeping.
+//
+//   * gather: every 3x3 block of the sliced BSR sums its per-tet contributions in a fixed order
+//     (plus M/h^2 on the diagonal); diagonal blocks also gather the gradient
+//     g = M (x - xt) / h^2 + sum_t V_t P_t D_a.  Dirichlet rows get g = 0.
+//   * PCG: one persistent cooperative kernel per Newton iteration runs every PCG iteration of
+//     every gel of the batch (Chronopoulos-Gear single-reduction CG: two grid barriers per
+//     iteration; dot products as per-slice partials summed per gel in a fixed order by every CTA
+//     that needs them, so all CTAs take identical decisions and results are reproducible).
+//   * energy: E(x + alpha p) per gel = inertia + elastic + barrier, as per-piece partial sums
+//     (pieces never straddle gels) reduced per gel in a fixed order; the reduction kernel also
+//     takes the line-search decision (accept on E <= E_cur, else halve alpha).
+#include "dev_contact.cuh"
+#include "dev_elastic.cuh"
+
+namespace txg {
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+// ---------------------------------------------------------------- exclusive scan (int)
+constexpr int SCAN_T = 1024;
+
+__global__ void k_scan_blocks(const int* in, int* out, int* bsum, int n) {
+  __shared__ int s[SCAN_T];
+  const int i = blockIdx.x * SCAN_T + threadIdx.x;
+  const int v = i < n ? in[i] : 0;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < SCAN_T; off <<= 1) {
+    int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = s[threadIdx.x] - v;
+  if (threadIdx.x == SCAN_T - 1) bsum[blockIdx.x] = s[SCAN_T - 1];
+}
+
+__global__ void k_scan_sums(int* bsum, int nb, int* total_out) {
+  __shared__ int s[SCAN_T];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += SCAN_T) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? bsum[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < SCAN_T; off <<= 1) {
+      int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == SCAN_T - 1) carry += s[SCAN_T - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int* out, const int* bsum, int n, const int* total, int* out_end) {
+  const int i = blockIdx.x * SCAN_T + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+  if (i == 0) *out_end = *total;
+}
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total.  tmp: >= nblk(n)+1 ints.
+void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
+  const int nb = nblk(n, SCAN_T);
+  if (n == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int), st);
+    return;
+  }
+  k_scan_blocks<<<nb, SCAN_T, 0, st>>>(in, out, tmp, n);
+  k_scan_sums<<<1, SCAN_T, 0, st>>>(tmp, nb, tmp + nb);
+  k_scan_add<<<nb, SCAN_T, 0, st>>>(out, tmp, n, tmp + nb, out + n);
+}
+
+// ---------------------------------------------------------------- gather (assembly)
+__device__ __forceinline__ size_t vaddr(int bp, int e) { return (size_t)9 * (bp & ~31) + 32 * e + (bp & 31); }
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
+  const int bp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bp >= nbp) return;
+  const int r = d.bp_row[bp];
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase) return;
+  const int c = d.colidx[bp];
+  const bool diag = d.diag_pos[r] == bp;
+  double h[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) h[e] = 0.0;
+  double gr[3] = {0.0, 0.0, 0.0};
+  const int c0 = d.ctr_ptr[bp], c1 = d.ctr_ptr[bp + 1];
+  for (int k = c0; k < c1; ++k) {
+    const int code = d.ctr[k];
+    const int t = code >> 4, a = (code >> 2) & 3, b = code & 3;
+    const bool tr = a > b;
+    const int blk = tr ? ublk(b, a) : ublk(a, b);
+    if (MIXED) {
+      const float* s = d.tscr32 + (size_t)t * TS32 + 9 * blk;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) h[3 * i + j] += (double)(tr ? s[3 * j + i] : s[3 * i + j]);
+    } else {
+      const double* s = d.tscr + (size_t)t * TS + 9 * blk;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) h[3 * i + j] += tr ? s[3 * j + i] : s[3 * i + j];
+    }
+    if (diag) {
+      const double* s = d.tscr + (size_t)t * TS + 90 + 3 * a;
+      gr[0] += s[0];
+      gr[1] += s[1];
+      gr[2] += s[2];
+    }
+  }
+  if (diag) {
+    const double h2 = d.gc[g].h * d.gc[g].h;
+    const double m = d.mass[r] / h2;
+    h[0] += m;
+    h[4] += m;
+    h[8] += m;
+    const double4_32a x = d.x[r], xt = d.xt[r];
+    double4_32a go;
+    if (d.fixed[r]) {
+      go = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    } else {
+      go.x = gr[0] + m * (x.x - xt.x);
+      go.y = gr[1] + m * (x.y - xt.y);
+      go.z = gr[2] + m * (x.z - xt.z);
+      go.w = 0.0;
+    }
+    d.grad[r] = go;
+  }
+  (void)c;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    if (MIXED)
+      d.vals32[vaddr(bp, e)] = (float)h[e];
+    else
+      d.vals[vaddr(bp, e)] = h[e];
+  }
+}
+
+void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st) {
+  if (mixed)
+    k_gather<true><<<nblk(nbp, 256), 256, 0, st>>>(d, phase, nbp);
+  else
+    k_gather<false><<<nblk(nbp, 256), 256, 0, st>>>(d, phase, nbp);
+}
+
+// block-Jacobi preconditioner: inverse of every free row's 3x3 diagonal block
+template <bool MIXED>
+__global__ void k_precond(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase) return;
+  double A[9], R[9];
+  const int bp = d.diag_pos[r];
+  for (int e = 0; e < 9; ++e) A[e] = MIXED ? (double)d.vals32[vaddr(bp, e)] : d.vals[vaddr(bp, e)];
+  if (d.fixed[r]) {
+    for (int e = 0; e < 9; ++e) R[e] = 0.0;
+  } else {
+    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    const double id = 1.0 / det;
+    R[0] = c00 * id;
+    R[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    R[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    R[3] = c01 * id;
+    R[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    R[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    R[6] = c02 * id;
+    R[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    R[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+  }
+  for (int e = 0; e < 9; ++e) {
+    if (MIXED)
+      d.Minv32[9 * r + e] = (float)R[e];
+    else
+      d.Minv[9 * r + e] = R[e];
+  }
+}
+
+void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
+  if (mixed)
+    k_precond<true><<<nblk(d.nrows, 128), 128, 0, st>>>(d, phase);
+  else
+    k_precond<false><<<nblk(d.nrows, 128), 128, 0, st>>>(d, phase);
+}
+
+// ---------------------------------------------------------------- persistent PCG
+constexpr int PCG_T = 256;  // threads per CTA (8 warps)
+constexpr int PCG_MAXG = 64; // gels one CTA may touch
+
+
+__device__ __forceinline__ double4_32a mul3(const double* M, const double4_32a v) {
+  return make_double4_32a(M[0] * v.x + M[1] * v.y + M[2] * v.z, M[3] * v.x + M[4] * v.y + M[5] * v.z,
+                      M[6] * v.x + M[7] * v.y + M[8] * v.z, 0.0);
+}
+__device__ __forceinline__ double dot4(const double4_32a a, const double4_32a b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// totals of the per-slice partials of gel g (arrays part + k*ns), fixed order, whole CTA
+__device__ __forceinline__ void gel_totals(const Dev& d, int g, int nk, double* out, double* sm) {
+  const GelInfo& G = d.gi[g];
+  for (int k = 0; k < nk; ++k) {
+    const double* p = d.part + (size_t)k * d.nslices + G.s0;
+    double v = 0.0;
+    for (int s = threadIdx.x; s < G.ns; s += PCG_T) v += p[s];
+    v = block_sum<PCG_T>(v, sm);
+    if (threadIdx.x == 0) out[k] = v;
+  }
+  __syncthreads();
+}
+
+// SpMV of one slice (row = lane of the warp): y = A u, FP64
+__device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane, const double4_32a* u) {
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    const int c = d.colidx[bp];
+    const double4_32a uc = u[c];
+    const double* v = d.vals + (size_t)9 * (o + 32 * k) + lane;
+    a0 += v[0] * uc.x + v[32] * uc.y + v[64] * uc.z;
+    a1 += v[96] * uc.x + v[128] * uc.y + v[160] * uc.z;
+    a2 += v[192] * uc.x + v[224] * uc.y + v[256] * uc.z;
+  }
+  return make_double4_32a(a0, a1, a2, 0.0);
+}
+
+__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, double eta2, int maxit) {
+  __shared__ double sm[PCG_T / 32];
+  __shared__ double tot[PCG_MAXG][4];
+  __shared__ int s_exit;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s0 = plan.cta_s0[blockIdx.x], s1 = plan.cta_s0[blockIdx.x + 1];
+  const int g0 = plan.cta_g0[blockIdx.x], ng = plan.cta_ng[blockIdx.x];
+  const int ns = d.nslices;
+  double* part = d.part;
+  unsigned epoch = 0;
+  // ---- init: r = -grad, x = 0, u = M^-1 r, pp = s = 0; partial |b|^2
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    if (d.gc[g].phase != phase) continue;
+    const int r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    d.r[r] = b;
+    d.p[r] = z;
+    d.pp[r] = z;
+    d.s[r] = z;
+    d.u[r] = mul3(d.Minv + 9 * r, b);
+    const double bb = warp_sum(dot4(b, b));
+    if (lane == 0) part[3 * (size_t)ns + s] = bb;
+  }
+  if (!grid_barrier(d.bar, epoch, d.err)) return;
+  int k = 0;
+  while (true) {
+    // ---- Y: w = A u, partials gamma = (r,u), delta = (w,u), rr = (r,r)
+    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+      const int g = plan.slice_gel[s];
+      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+      const int r = 32 * s + lane;
+      double4_32a w = spmv_row64(d, s, lane, d.u);
+      if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      d.w[r] = w;
+      const double4_32a rv = d.r[r], uv = d.u[r];
+      const double ga = warp_sum(dot4(rv, uv)), de = warp_sum(dot4(w, uv)), rr = warp_sum(dot4(rv, rv));
+      if (lane == 0) {
+        part[s] = ga;
+        part[(size_t)ns + s] = de;
+        part[2 * (size_t)ns + s] = rr;
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.act[(k + 1) & 1] = 0;
+    if (!grid_barrier(d.bar, epoch, d.err)) return;
+    k += 1;
+    // ---- X: per-gel scalars, convergence, vector updates
+    for (int j = 0; j < ng; ++j) gel_totals(d, g0 + j, 4, tot[j], sm);
+    int my_active = 0;
+    for (int j = 0; j < ng; ++j) {
+      const int g = g0 + j;
+      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2], bb = tot[j][3];
+      const bool conv = !(rr > eta2 * bb) || k > maxit;
+      if (conv) {
+        // every CTA touching g reaches the same decision in this iteration
+        if (threadIdx.x == 0) {
+          d.gv[g].pcg_it = k - 1;
+          d.gv[g].bb = bb;
+          d.gv[g].pcg_done = 1;
+        }
+        continue;
+      }
+      ++my_active;
+      const int par = k & 1, prv = (k - 1) & 1;
+      double beta, alpha;
+      if (k == 1) {
+        beta = 0.0;
+        alpha = ga / de;
+      } else {
+        const double gprev = d.gsc[(size_t)(prv * 4 + 0) * d.n_gels + g];
+        const double aprev = d.gsc[(size_t)(prv * 4 + 1) * d.n_gels + g];
+        beta = ga / gprev;
+        alpha = ga / (de - beta * ga / aprev);
+      }
+      if (threadIdx.x == 0) {
+        d.gsc[(size_t)(par * 4 + 0) * d.n_gels + g] = ga;
+        d.gsc[(size_t)(par * 4 + 1) * d.n_gels + g] = alpha;
+      }
+      const GelInfo& G = d.gi[g];
+      const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
+      for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
+        const int r = 32 * s + lane;
+        const double4_32a u = d.u[r], w = d.w[r];
+        double4_32a pp = d.pp[r], sv = d.s[r], x = d.p[r], rv = d.r[r];
+        pp.x = u.x + beta * pp.x; pp.y = u.y + beta * pp.y; pp.z = u.z + beta * pp.z;
+        sv.x = w.x + beta * sv.x; sv.y = w.y + beta * sv.y; sv.z = w.z + beta * sv.z;
+        x.x += alpha * pp.x; x.y += alpha * pp.y; x.z += alpha * pp.z;
+        rv.x -= alpha * sv.x; rv.y -= alpha * sv.y; rv.z -= alpha * sv.z;
+        d.pp[r] = pp;
+        d.s[r] = sv;
+        d.p[r] = x;
+        d.r[r] = rv;
+        d.u[r] = mul3(d.Minv + 9 * r, rv);
+      }
+    }
+    if (threadIdx.x == 0 && my_active) atomicAdd(&d.act[k & 1], my_active);
+    if (!grid_barrier(d.bar, epoch, d.err)) return;
+    if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[k & 1]) == 0);
+    __syncthreads();
+    if (s_exit) break;
+  }
+  // ---- ||p||_inf per gel
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    if (d.gc[g].phase != phase) continue;
+    const double4_32a x = d.p[32 * s + lane];
+    const double m = warp_max(fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z))));
+    if (lane == 0) atomic_max_pos(&d.gv[g].pnorm_bits, m);
+  }
+}
+
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta,
+                         int maxit, cudaStream_t st) {
+  double eta2 = eta * eta;
+  Dev dd = d;
+  PcgPlan pp = plan;
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, 0, st);
+}
+
+int pcg_max_ctas_per_sm() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64, PCG_T, 0);
+  return nb;
+}
+
+// ---------------------------------------------------------------- energy
+constexpr int EN_T = 256;
+constexpr int PIECE = 2048;
+
+// pieces: (gel, kind, begin, end), kind 0 tets, 1 rows, 2 pairs (range read from gv)
+// mode 0: at x (alpha = 0); mode 1: line search at x + alpha p (gels still searching)
+__global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* pieces, double* part_e,
+                                                 int mode) {
+  __shared__ double sm[EN_T / 32];
+  const int4 pc = pieces[blockIdx.x];
+  const int g = pc.x;
+  if (d.gc[g].phase != phase) return;
+  if (mode == 1 && (d.gv[g].ls_state != 0 || d.gv[g].converged)) return;
+  const GelInfo& G = d.gi[g];
+  const double alpha = mode == 1 ? d.gv[g].alpha : 0.0;
+  double acc = 0.0;
+  if (pc.y == 0) {
+    for (int t = pc.z + threadIdx.x; t < pc.w; t += EN_T) acc += tet_energy_at(d, t, alpha, G.mu, G.lam);
+  } else if (pc.y == 1) {
+    const double ih2 = 0.5 / (d.gc[g].h * d.gc[g].h);
+    for (int r = pc.z + threadIdx.x; r < pc.w; r += EN_T) {
+      const double4_32a x = d.x[r], xt = d.xt[r];
+      double ex = x.x - xt.x, ey = x.y - xt.y, ez = x.z - xt.z;
+      if (alpha != 0.0) {
+        const double4_32a p = d.p[r];
+        ex = x.x + alpha * p.x - xt.x;
+        ey = x.y + alpha * p.y - xt.y;
+        ez = x.z + alpha * p.z - xt.z;
+      }
+      acc += d.mass[r] * (ex * ex + ey * ey + ez * ez) * ih2;
+    }
+  } else {
+    const int p0 = G.pbase, np = min(d.gv[g].npair, G.pcap);
+    for (int i = threadIdx.x; i < np; i += EN_T) {
+      const int4 pr = d.pairs[p0 + i];
+      double P[4][3];
+      int rows[4];
+      pair_points(d, pr, alpha, false, P, rows);
+      double dist;
+      const double b = pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+      acc += G.kappa * b;
+    }
+  }
+  acc = block_sum<EN_T>(acc, sm);
+  if (threadIdx.x == 0) part_e[blockIdx.x] = acc;
+}
+
+// per gel: E = sum of its pieces in order; mode 0: E_cur = E; 1: line-search decision; 2: E_try = E
+__global__ void k_energy_reduce(Dev d, int phase, const int* gel_piece, const double* part_e, int mode) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.n_gels) return;
+  if (d.gc[g].phase != phase) return;
+  GelVar& v = d.gv[g];
+  if (mode == 1 && (v.ls_state != 0 || v.converged)) return;
+  double E = 0.0;
+  for (int k = gel_piece[g]; k < gel_piece[g + 1]; ++k) E += part_e[k];
+  if (mode == 0) {
+    v.E_cur = E;
+  } else if (mode == 2) {
+    v.E_try = E;
+  } else {
+    v.E_try = E;
+    if (E <= v.E_cur) {
+      v.ls_state = 1;
+      v.E_cur = E;
+    } else {
+      v.alpha *= 0.5;
+      v.ls_total += 1;
+      if (v.alpha < 1e-12 * v.alpha0) v.ls_state = 2;
+    }
+  }
+}
+
+void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
+                   double* part_e, int mode, cudaStream_t st) {
+  if (npieces > 0) k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, part_e, mode);
+  k_energy_reduce<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, gel_piece, part_e, mode);
+}
+
+// ---------------------------------------------------------------- per-row / per-gel steps
+// step begin: x_n = x, xt = x + h v + h^2 g on free rows (xt = x on fixed rows)
+__global__ void k_predictor(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase) return;
+  const GelCtl& c = d.gc[g];
+  const double4_32a x = d.x[r], v = d.v[r];
+  d.xn[r] = x;
+  double4_32a xt = x;
+  if (!d.fixed[r]) {
+    const double h = c.h;
+    xt.x = x.x + h * v.x + h * h * c.grav[0];
+    xt.y = x.y + h * v.y + h * h * c.grav[1];
+    xt.z = x.z + h * v.z + h * h * c.grav[2];
+  }
+  d.xt[r] = xt;
+}
+
+// x += alpha p for gels whose line search accepted
+__global__ void k_update(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase || d.gv[g].ls_state != 1) return;
+  const double a = d.gv[g].alpha;
+  double4_32a x = d.x[r];
+  const double4_32a p = d.p[r];
+  x.x += a * p.x;
+  x.y += a * p.y;
+  x.z += a * p.z;
+  d.x[r] = x;
+}
+
+// v = (x - x_n) / h
+__global__ void k_finalize(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase) return;
+  const double ih = 1.0 / d.gc[g].h;
+  const double4_32a x = d.x[r], xn = d.xn[r];
+  d.v[r] = make_double4_32a((x.x - xn.x) * ih, (x.y - xn.y) * ih, (x.z - xn.z) * ih, 0.0);
+}
+
+// restore x_n (failed step)
+__global__ void k_restore(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  if (d.gc[g].phase != phase) return;
+  d.x[r] = d.xn[r];
+}
+
+// per gel bookkeeping: op 0 = reset the assembly / PCG accumulators; 1 = after the PCG:
+// converged = ||p||_inf < tol, prepare the ACCD minimum; 2 = after the ACCD: alpha0 = min(1,
+// toi), start the line search; 3 = reset the per-step feasibility state
+__global__ void k_gel_op(Dev d, int phase, int op) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.n_gels) return;
+  if (d.gc[g].phase != phase) return;
+  GelVar& v = d.gv[g];
+  if (op == 0) {
+    v.fc[0] = v.fc[1] = v.fc[2] = 0.0;
+    v.active_pairs = 0;
+    v.pnorm_bits = 0ull;
+    v.pcg_done = 0;
+    v.pcg_it = 0;
+    v.flags &= ~(4 | 16);
+  } else if (op == 1) {
+    v.converged = bitsd(v.pnorm_bits) < d.gc[g].tol_p ? 1 : 0;
+    v.toi_bits = dbits(1.0);
+    v.flags &= ~8;
+  } else if (op == 2) {
+    if (v.converged) {
+      v.ls_state = 3;
+    } else if (v.flags & 32) {
+      v.ls_state = 4;  // candidate segment overflowed: the host grows it and redoes this part
+    } else {
+      v.alpha0 = fmin(1.0, bitsd(v.toi_bits));
+      v.alpha = v.alpha0;
+      v.ls_state = 0;
+    }
+  } else if (op == 3) {
+    v.toi_bits = dbits(1.0);
+    v.dmin_bits = dbits(CUDART_INF);
+    v.flags = 0;
+    v.ls_total = 0;
+    v.active_pairs = 0;
+  } else if (op == 4) {
+    v.dmin_bits = dbits(CUDART_INF);
+  } else if (op == 5) {
+    if (v.ls_state == 1) v.ls_state = 3;  // the accepted step has been applied
+  } else if (op == 6) {
+    v.flags &= ~32;
+    v.toi_bits = dbits(1.0);
+  }
+}
+
+void launch_rows(int which, const Dev& d, int phase, cudaStream_t st) {
+  const int nb = nblk(d.nrows, 256);
+  if (which == 0) k_predictor<<<nb, 256, 0, st>>>(d, phase);
+  if (which == 1) k_update<<<nb, 256, 0, st>>>(d, phase);
+  if (which == 2) k_finalize<<<nb, 256, 0, st>>>(d, phase);
+  if (which == 3) k_restore<<<nb, 256, 0, st>>>(d, phase);
+}
+void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st) {
+  k_gel_op<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, op);
+}
+
+}  // namespace txg

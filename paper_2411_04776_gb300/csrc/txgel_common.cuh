@@ -1,0 +1,255 @@
+// Shared declarations of the GB300 gelpad IPC step library: device data layout, small
+// fixed-size linear algebra, reductions and the bounded grid barrier.
+//
+// Data layout (all gels of a handle are concatenated; a single gel is a batch of one):
+//   * vertex rows: each gel owns rows [v0, v0 + nv), v0 a multiple of 32 so every 32-row slice
+//     (one warp) belongs to one gel; rows past nv up to the next multiple of 32 are inert
+//     padding (fixed, zero mass).  Positions and all solver vectors are double4_32a (x, y, z, 0):
+//     one 32-byte sector per vertex gather.
+//   * Hessian: 3x3-block sparse, sliced ELL ("SELL-32") over the rows: slice s holds rows
+//     [32 s, 32 s + 32) with width w_s = longest row; block k of lane l lives at position
+//     slice_off[s] + 32 k + l; its 9 values are stored entry-major inside the slice column
+//     (value e of lane l at 9 (slice_off[s] + 32 k) + 32 e + l) so a warp loads each entry
+//     of 32 rows with one coalesced 256-byte access.  Padding entries point at the row itself
+//     with zero values.
+//   * per-tet scratch: the 10 upper 3x3 blocks of the 12x12 element Hessian and the 12-vector
+//     gradient, gathered into the rows by fixed per-block contribution lists (deterministic,
+//     no atomics).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace txg {
+
+constexpr int SLICE = 32;
+constexpr int TS = 104;        // per-tet scratch stride (90 Hessian + 12 gradient + 2 pad), doubles
+constexpr int TS32 = 96;       // per-tet FP32 Hessian scratch stride (90 + 6 pad), floats
+constexpr int NTAB = 3;        // hash tables per gel: indenter tris, indenter verts, indenter edges
+constexpr int PAIR_PT = 0;     // gel surface vertex   vs indenter triangle
+constexpr int PAIR_TP = 1;     // indenter vertex      vs gel surface triangle
+constexpr int PAIR_EE = 2;     // gel surface edge     vs indenter edge
+constexpr double ACCD_S = 0.1; // ACCD: the gap may shrink to this fraction per sweep
+
+// phases of a gel inside a batch
+enum Phase : int { PH_IDLE = 0, PH_BEGIN = 1, PH_NEWTON = 2 };
+
+struct GelInfo {  // per gel, read-only after create
+  int v0, nv;     // rows
+  int s0, ns;     // slices
+  int t0, nt;     // tets
+  int q0, nq;     // query primitives: [surface verts | surface tris | surface edges]
+  int nsv, nst, nse;
+  int sv0, st0, se0;
+  int iv0, niv, it0, nit, ie0, nie;
+  int hb0[NTAB], hnb[NTAB];  // hash bucket ranges (power-of-two sizes)
+  int he0[NTAB], hcap[NTAB]; // hash entry ranges
+  int pbase, pcap;           // candidate-pair segment
+  int fixed_count;
+  double mu, lam, kappa, dhat, cell, bbox_diag, newton_tol;
+  double org[3];             // hash grid origin
+};
+
+struct GelCtl {  // per gel, written by the host before the launches of an iteration
+  int phase;
+  int pad_;
+  double h;                  // current (sub)step length
+  double tol_p;              // ||p||_inf tolerance = newton_tol * bbox_diag * h
+  double grav[3];
+  double R[9], t[3];         // indenter pose at the end of the (sub)step
+  double Rp[9], tp[3];       // indenter pose at its start
+};
+
+struct GelVar {  // per gel, written by the device
+  double E_cur, E_try;
+  double alpha, alpha0;
+  double bb;                 // |b|^2 of the PCG right-hand side
+  double fc[3];              // contact force on the gel
+  unsigned long long toi_bits;    // min ACCD time of impact (non-negative double bits)
+  unsigned long long pnorm_bits;  // ||p||_inf of the last Newton direction
+  unsigned long long dmin_bits;   // min pair distance
+  int ls_state;              // 0 searching, 1 accepted, 2 failed
+  int ls_total;              // halvings this step
+  int converged;             // Newton converged at the last check
+  int pcg_it;                // PCG iterations of the last solve
+  int pcg_done;              // set inside the PCG kernel once the gel's solve converged
+  int pair0, npair;          // candidate pair range
+  int hent[NTAB];            // hash entries used
+  int active_pairs;
+  int flags;                 // 1 hash overflow, 2 ACCD cap, 4 inverted tet, 8 ACCD hit, 16 pattern miss
+};
+
+// Everything the kernels touch, passed by value.
+struct Dev {
+  int n_gels;
+  const GelInfo* gi;
+  const GelCtl* gc;
+  GelVar* gv;
+  int niv_total;
+  // rows
+  int nrows;
+  double4_32a *X, *x, *xn, *v, *xt, *p, *grad;
+  double* mass;
+  uint8_t* fixed;
+  int* vgel;
+  // tets
+  int ntets;
+  int4* tets;
+  double* Dminv;  // 9 per tet
+  double* vol;
+  int* tgel;
+  double* tscr;   // TS per tet
+  float* tscr32;  // TS32 per tet (mixed precision Hessian)
+  // sliced BSR
+  int nslices;
+  int* slice_off;  // nslices + 1 (block positions)
+  int* colidx;     // per block position
+  double* vals;    // 9 per block position (FP64)
+  float* vals32;   // 9 per block position (mixed)
+  int* bp_row;     // per block position: its row
+  int* ctr_ptr;    // per block position + 1: contribution list range
+  int* ctr;        // (tet << 4) | (4 a + b)
+  int* diag_pos;   // per row: block position of the diagonal block
+  double* Minv;    // 9 per row
+  float* Minv32;
+  // PCG
+  double4_32a *r, *u, *w, *pp, *s;
+  float4 *u32, *w32, *pp32, *s32, *r32, *x32;
+  double* part;    // per slice partial sums: 4 arrays of nslices
+  double* gsc;     // per gel PCG scalars: [2][4][n_gels] (gamma, alpha for parity 0/1)
+  unsigned* bar;   // grid barrier counter
+  int* act;        // active counters (2)
+  // surface primitives (global)
+  int* sv;
+  int4* st;
+  int2* se;
+  double* se_len2;
+  int* q_gel;
+  int* q_tp;       // (type << 28) | local primitive index within the gel's surface list
+  // indenter
+  double4_32a *iv_loc, *iv_cur, *iv_prev;
+  int4* it;
+  int2* ie;
+  double* ie_len2;
+  int* iv_gel;
+  int* it_gel;
+  int* ie_gel;
+  // hash
+  int* hstart;     // bucket starts (global, per table segment nb + 1)
+  int* hcount;     // bucket fill cursors
+  int2* hent;      // entries (prim, packed cell)
+  // candidate pairs
+  int nq;
+  int* qcount;     // nq + 1
+  int* qoff;       // nq + 1 (exclusive scan)
+  int4* pairs;     // (type, gel prim, indenter prim, gel), per-gel segments [pbase, pbase + pcap)
+  int* pslot_gel;  // gel of every pair slot
+  int npslots;
+  double* pe;      // per pair scratch (energy)
+  int* err;
+};
+
+// Static partition of the slices over the CTAs of the persistent PCG kernel.
+struct PcgPlan {
+  const int* cta_s0;     // per CTA: first slice (n + 1 entries)
+  const int* cta_g0;     // per CTA: first gel touched
+  const int* cta_ng;     // per CTA: number of gels touched
+  const int* slice_gel;  // per slice: its gel
+};
+
+// ------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v));
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
+// min/max of non-negative doubles through their order-preserving bit patterns
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* a, double v) {
+  atomicMin(a, dbits(v));
+}
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+  atomicMax(a, dbits(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Fixed-order block sum (deterministic): every thread gets the total.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < NT / 32; ++k) t += sm[k];
+  return t;
+}
+
+__device__ __forceinline__ void quat_to_R(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double n = rsqrt(w * w + x * x + y * y + z * z);
+  w *= n; x *= n; y *= n; z *= n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+__device__ __forceinline__ void ld3(const double4_32a& a, double r[3]) {
+  r[0] = a.x; r[1] = a.y; r[2] = a.z;
+}
+
+// Bounded grid barrier for cooperative launches: a monotonic arrival counter; `epoch` counts the
+// barriers passed so far.  A wait that exceeds the spin limit sets *err and returns, so a kernel
+// can never hang the device.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, int* err) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    epoch += 1;
+    const unsigned target = epoch * gridDim.x;
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    while (true) {
+      unsigned cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+      if (cur >= target) break;
+      if (++spins > (1u << 22)) {
+        atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  } else {
+    epoch += 1;
+  }
+  __syncthreads();
+  if (*((volatile int*)err) != 0) ok = false;
+  return ok;
+}
+
+}  // namespace txg

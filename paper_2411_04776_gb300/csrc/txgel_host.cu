@@ -1,0 +1,1582 @@
+// Host side of the gelpad IPC step library: rest-state preprocessing, device layout, the
+// per-gel Newton state machine (continuous batching at Newton-iteration granularity) and the C ABI.
+//
+// One time step of a gel (TacEx, Sec. "General GIPC Simulation Pipeline"): the indenter is moved
+// to the requested pose (kinematic target), then the free gel vertices are found by minimising the
+// incremental potential with projected Newton.  Per gel and step:
+//   begin   : indenter placed at the target pose; spatial hash of its primitives swept from the
+//             previous pose; candidates against the gel at x_n; ACCD sweep of the indenter motion
+//             and distances after placement.  Any hit (or distance <= 0) splits the step into two
+//             half steps (midpoint pose, dt/2), recursively, up to max_split_depth; otherwise
+//             x_n = x, xt = x_n + h v_n (+ h^2 g), E(x_n) and the static hash at the target pose.
+//   newton  : assemble (elastic scratch + gather + barrier + inertia), block-Jacobi PCG, test
+//             ||p||_inf / h < tol * bbox diagonal; else candidates swept along p, ACCD cap
+//             alpha_0 = min(1, toi), backtracking E(x + alpha p) <= E(x) (det F <= 0 or d <= 0
+//             give E = +inf), x += alpha p.
+//   finish  : v = (x - x_n) / h.
+// Every gel of a handle runs this machine independently; each host round admits new requests
+// (begin) and advances every running gel by one Newton iteration, with one device->host read of
+// the per-gel state per round.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "tx_gel.h"
+#include "txgel_common.cuh"
+
+namespace txg {
+void launch_tet_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st);
+void launch_eval_tets(int n, const double* X, const double* x, double mu, double lam, int project,
+                      double* e, double* g, double* H, cudaStream_t st);
+void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t st);
+void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st);
+void launch_query(const Dev& d, int phase, int mode, cudaStream_t st);
+void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st);
+void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st);
+void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
+void launch_min_dist(const Dev& d, int phase, cudaStream_t st);
+void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
+                       const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st);
+void launch_eval_accd(int n, const int* kind, const double* P, const double* dP, double s, double tc,
+                      int maxit, double* toi, int* hit, cudaStream_t st);
+void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st);
+void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st);
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
+                         cudaStream_t st);
+int pcg_max_ctas_per_sm();
+void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
+                   double* part_e, int mode, cudaStream_t st);
+void launch_rows(int which, const Dev& d, int phase, cudaStream_t st);
+void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st);
+}  // namespace txg
+
+using namespace txg;
+
+namespace {
+
+thread_local std::string g_err;
+
+// phases beyond the ones the kernels name
+enum : int { PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6, PH_PARK = 7, PH_FAIL = 8 };
+constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
+constexpr int PIECE_HOST = 2048;
+
+#define CK(call)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      g_err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+      return TX_ERR_CUDA;                                                 \
+    }                                                                     \
+  } while (0)
+
+double bitsd_host(unsigned long long u) {
+  double v;
+  std::memcpy(&v, &u, sizeof(v));
+  return v;
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+void quat_R(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double n = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= n; x /= n; y /= n; z /= n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+void pose_mid(const double a[7], const double b[7], double m[7]) {
+  double dq = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+  double sg = dq < 0 ? -1.0 : 1.0, nn = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    m[i] = a[i] + sg * b[i];
+    nn += m[i] * m[i];
+  }
+  nn = std::sqrt(nn);
+  for (int i = 0; i < 4; ++i) m[i] /= nn;
+  for (int i = 4; i < 7; ++i) m[i] = 0.5 * (a[i] + b[i]);
+}
+
+// ---------------------------------------------------------------- rest-state preprocessing
+struct Mesh {
+  int nv = 0, nt = 0, niv = 0, nit = 0;
+  std::vector<double> X;
+  std::vector<int> tets;
+  std::vector<uint8_t> fixed;
+  std::vector<double> Dminv, vol, mass;
+  std::vector<int> sv;
+  std::vector<std::array<int, 3>> st;
+  std::vector<std::array<int, 2>> se;
+  std::vector<double> se_len2;
+  std::vector<double> IV;
+  std::vector<std::array<int, 3>> it;
+  std::vector<std::array<int, 2>> ie;
+  std::vector<double> ie_len2;
+  std::vector<std::vector<int>> adj;  // sorted neighbour lists (incl. self)
+  double mu = 0, lam = 0, kappa = 0, bbox = 0, cell = 0, org[3] = {0, 0, 0};
+  tx_params prm{};
+  double pose0[7];
+};
+
+tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
+  if (!d || d->n_verts <= 0 || d->n_tets < 0 || !d->verts || (d->n_tets > 0 && !d->tets) ||
+      d->n_ind_verts < 0 || d->n_ind_tris < 0 || (d->n_ind_verts > 0 && !d->ind_verts) ||
+      (d->n_ind_tris > 0 && !d->ind_tris))
+    return TX_ERR_ARG;
+  if (!(d->young > 0) || !(d->poisson > -1.0 && d->poisson < 0.5) || !(d->density > 0)) return TX_ERR_ARG;
+  const tx_params& p = d->params;
+  if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || p.newton_max_iter < 1 ||
+      p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0)
+    return TX_ERR_ARG;
+  m.nv = d->n_verts;
+  m.nt = d->n_tets;
+  m.niv = d->n_ind_verts;
+  m.nit = d->n_ind_tris;
+  m.prm = p;
+  std::memcpy(m.pose0, d->ind_pose, sizeof(m.pose0));
+  m.X.assign(d->verts, d->verts + 3 * m.nv);
+  m.tets.assign(d->tets, d->tets + 4 * m.nt);
+  for (int v : m.tets)
+    if (v < 0 || v >= m.nv) return TX_ERR_ARG;
+  for (int k = 0; k < 3 * m.nit; ++k)
+    if (d->ind_tris[k] < 0 || d->ind_tris[k] >= m.niv) return TX_ERR_ARG;
+  m.fixed.assign(m.nv, 0);
+  if (d->dirichlet)
+    for (int i = 0; i < m.nv; ++i) m.fixed[i] = d->dirichlet[i] ? 1 : 0;
+  m.mu = d->young / (2.0 * (1.0 + d->poisson));
+  m.lam = d->young * d->poisson / ((1.0 + d->poisson) * (1.0 - 2.0 * d->poisson));
+  m.Dminv.resize(9 * (size_t)m.nt);
+  m.vol.resize(m.nt);
+  m.mass.assign(m.nv, 0.0);
+  for (int t = 0; t < m.nt; ++t) {
+    const int* v = &m.tets[4 * t];
+    double A[9];
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a) A[3 * i + a] = m.X[3 * v[a + 1] + i] - m.X[3 * v[0] + i];
+    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(det > 0.0)) return TX_ERR_MESH_INVERTED;
+    const double id = 1.0 / det;
+    double* R = &m.Dminv[9 * (size_t)t];
+    R[0] = c00 * id;
+    R[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    R[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    R[3] = c01 * id;
+    R[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    R[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    R[6] = c02 * id;
+    R[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    R[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    m.vol[t] = det / 6.0;
+    for (int a = 0; a < 4; ++a) m.mass[v[a]] += d->density * m.vol[t] / 4.0;
+  }
+  // boundary faces (faces of exactly one tet), their vertices and edges
+  std::map<std::array<int, 3>, std::pair<std::array<int, 3>, int>> faces;
+  const int FI[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+  for (int t = 0; t < m.nt; ++t)
+    for (auto& f : FI) {
+      std::array<int, 3> tri = {m.tets[4 * t + f[0]], m.tets[4 * t + f[1]], m.tets[4 * t + f[2]]};
+      std::array<int, 3> key = tri;
+      std::sort(key.begin(), key.end());
+      auto& e = faces[key];
+      if (e.second == 0) e.first = tri;
+      e.second++;
+    }
+  std::vector<char> on(m.nv, 0);
+  std::map<std::pair<int, int>, int> edges;
+  for (auto& kv : faces) {
+    if (kv.second.second != 1) continue;
+    m.st.push_back(kv.second.first);
+    for (int c = 0; c < 3; ++c) {
+      const int a = kv.second.first[c], b = kv.second.first[(c + 1) % 3];
+      on[a] = 1;
+      edges[{std::min(a, b), std::max(a, b)}] = 1;
+    }
+  }
+  for (int i = 0; i < m.nv; ++i)
+    if (on[i]) m.sv.push_back(i);
+  double lsum = 0.0;
+  for (auto& kv : edges) {
+    m.se.push_back({kv.first.first, kv.first.second});
+    double l2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double dd = m.X[3 * kv.first.first + c] - m.X[3 * kv.first.second + c];
+      l2 += dd * dd;
+    }
+    m.se_len2.push_back(l2);
+    lsum += std::sqrt(l2);
+  }
+  const double mean_se = edges.empty() ? 0.0 : lsum / edges.size();
+  m.IV.assign(d->ind_verts, d->ind_verts + 3 * m.niv);
+  std::map<std::pair<int, int>, int> iedges;
+  for (int k = 0; k < m.nit; ++k) {
+    m.it.push_back({d->ind_tris[3 * k], d->ind_tris[3 * k + 1], d->ind_tris[3 * k + 2]});
+    for (int c = 0; c < 3; ++c) {
+      const int a = d->ind_tris[3 * k + c], b = d->ind_tris[3 * k + (c + 1) % 3];
+      iedges[{std::min(a, b), std::max(a, b)}] = 1;
+    }
+  }
+  double isum = 0.0;
+  for (auto& kv : iedges) {
+    m.ie.push_back({kv.first.first, kv.first.second});
+    double l2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double dd = m.IV[3 * kv.first.first + c] - m.IV[3 * kv.first.second + c];
+      l2 += dd * dd;
+    }
+    m.ie_len2.push_back(l2);
+    isum += std::sqrt(l2);
+  }
+  const double mean_ie = iedges.empty() ? 0.0 : isum / iedges.size();
+  m.kappa = p.kappa > 0 ? p.kappa : d->young * mean_se;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = 0; i < m.nv; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], m.X[3 * i + c]);
+      hi[c] = std::max(hi[c], m.X[3 * i + c]);
+    }
+  m.bbox = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                     (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  m.cell = std::max(std::max(mean_se, mean_ie), 4.0 * p.dhat);
+  for (int c = 0; c < 3; ++c) m.org[c] = lo[c] - 64.0 * m.cell;
+  // vertex adjacency through tets
+  m.adj.assign(m.nv, {});
+  for (int i = 0; i < m.nv; ++i) m.adj[i].push_back(i);
+  for (int t = 0; t < m.nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) m.adj[m.tets[4 * t + a]].push_back(m.tets[4 * t + b]);
+  for (auto& l : m.adj) {
+    std::sort(l.begin(), l.end());
+    l.erase(std::unique(l.begin(), l.end()), l.end());
+  }
+  return TX_OK;
+}
+
+// ---------------------------------------------------------------- device allocation
+struct DevMem {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <class T>
+  T* get(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    bytes += n * sizeof(T);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+struct Task {
+  double pa[7], pb[7];
+  double dt;
+  int depth;
+  bool first;
+};
+
+struct Run {
+  std::vector<Task> stack;  // back = next substep
+  bool in_request = false;
+  int phase = PH_IDLE;
+  tx_status status = TX_OK;
+  int newton_sub = 0;       // Newton updates in the current substep
+  tx_step_stats acc{};      // accumulating stats of the request
+  tx_step_stats last{};     // last finished request
+  double pose[7];           // indenter pose at the end of the last finished substep
+  double pose_req[7];       // pose at the start of the request (for rollback)
+};
+
+}  // namespace
+
+struct tx_batch {
+  int n = 0;
+  cudaStream_t st = nullptr;
+  bool mixed = false;
+  std::vector<Mesh> mesh;
+  std::vector<GelInfo> gi;
+  std::vector<Run> run;
+  GelCtl* gc_h = nullptr;   // pinned
+  GelVar* gv_h = nullptr;   // pinned
+  Dev d{};
+  DevMem mem;
+  DevMem pair_mem;          // pairs + slot map (regrown on overflow)
+  DevMem hash_mem;          // hash entries (regrown on overflow)
+  int nbp = 0;
+  // PCG
+  PcgPlan plan{};
+  int nctas = 0;
+  // energy pieces
+  int4* pieces = nullptr;
+  int npieces = 0;
+  int* gel_piece = nullptr;
+  std::vector<int4> pieces_h;
+  std::vector<int> gel_piece_h;
+  double* part_e = nullptr;
+  int* scan_tmp = nullptr;
+  double4_32a *x0 = nullptr, *v0 = nullptr;  // request start state (rollback)
+  double4_32a *ex = nullptr, *ext = nullptr; // evaluation save area
+  int total_rows = 0;
+  std::vector<int> done_queue;
+};
+
+struct tx_gel {
+  tx_batch* b;
+};
+
+namespace {
+
+// per-gel pair capacity and hash sizes (initial guesses; grown on overflow)
+int initial_pcap(const Mesh& m) {
+  return std::max(4096, 2 * (int)(m.sv.size() + m.st.size() + m.se.size()));
+}
+
+tx_status upload_ctl(tx_batch* b) {
+  CK(cudaMemcpyAsync((void*)b->d.gc, b->gc_h, sizeof(GelCtl) * b->n, cudaMemcpyHostToDevice, b->st));
+  return TX_OK;
+}
+tx_status download_var(tx_batch* b) {
+  CK(cudaMemcpyAsync(b->gv_h, b->d.gv, sizeof(GelVar) * b->n, cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+tx_status upload_info(tx_batch* b) {
+  CK(cudaMemcpyAsync((void*)b->d.gi, b->gi.data(), sizeof(GelInfo) * b->n, cudaMemcpyHostToDevice, b->st));
+  return TX_OK;
+}
+
+// (Re)allocate the candidate-pair segments with the capacities in gi[].pcap.
+tx_status alloc_pairs(tx_batch* b) {
+  CK(cudaStreamSynchronize(b->st));
+  b->pair_mem.release();
+  int total = 0;
+  for (int g = 0; g < b->n; ++g) {
+    b->gi[g].pbase = total;
+    total += b->gi[g].pcap;
+  }
+  b->d.pairs = b->pair_mem.get<int4>(total);
+  b->d.pslot_gel = b->pair_mem.get<int>(total);
+  if (!b->d.pairs || !b->d.pslot_gel) return TX_ERR_OOM;
+  b->d.npslots = total;
+  std::vector<int> slot(total);
+  for (int g = 0; g < b->n; ++g)
+    for (int k = 0; k < b->gi[g].pcap; ++k) slot[b->gi[g].pbase + k] = g;
+  CK(cudaMemcpy(b->d.pslot_gel, slot.data(), sizeof(int) * total, cudaMemcpyHostToDevice));
+  return upload_info(b);
+}
+
+tx_status alloc_hash(tx_batch* b) {
+  CK(cudaStreamSynchronize(b->st));
+  b->hash_mem.release();
+  int total = 0;
+  for (int g = 0; g < b->n; ++g)
+    for (int t = 0; t < NTAB; ++t) {
+      b->gi[g].he0[t] = total;
+      total += b->gi[g].hcap[t];
+    }
+  b->d.hent = b->hash_mem.get<int2>(total);
+  if (!b->d.hent) return TX_ERR_OOM;
+  return upload_info(b);
+}
+
+// ---------------------------------------------------------------- creation
+tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch** out) {
+  if (!descs || n <= 0 || !out) return TX_ERR_ARG;
+  tx_batch* b = new tx_batch();
+  b->n = n;
+  b->st = (cudaStream_t)stream;
+  b->mesh.resize(n);
+  for (int g = 0; g < n; ++g) {
+    tx_status s = build_mesh(&descs[g], b->mesh[g]);
+    if (s != TX_OK) {
+      delete b;
+      return s;
+    }
+  }
+  b->mixed = descs[0].params.precision == TX_PREC_MIXED;
+  if (b->mixed) {  // FP32 Krylov path not wired yet
+    g_err = "mixed precision is not available in this build";
+    delete b;
+    return TX_ERR_ARG;
+  }
+  for (int g = 1; g < n; ++g)
+    if ((descs[g].params.precision == TX_PREC_MIXED) != b->mixed) {
+      delete b;
+      return TX_ERR_ARG;
+    }
+  // ---- offsets
+  b->gi.resize(n);
+  int rows = 0, tets = 0, nsv = 0, nst = 0, nse = 0, nq = 0, niv = 0, nit = 0, nie = 0, hb = 0;
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    GelInfo& G = b->gi[g];
+    std::memset(&G, 0, sizeof(G));
+    G.v0 = rows;
+    G.nv = m.nv;
+    G.s0 = rows / SLICE;
+    G.ns = (m.nv + SLICE - 1) / SLICE;
+    rows += G.ns * SLICE;
+    G.t0 = tets;
+    G.nt = m.nt;
+    tets += m.nt;
+    G.q0 = nq;
+    G.nsv = (int)m.sv.size();
+    G.nst = (int)m.st.size();
+    G.nse = (int)m.se.size();
+    G.nq = G.nsv + G.nst + G.nse;
+    nq += G.nq;
+    G.sv0 = nsv;
+    G.st0 = nst;
+    G.se0 = nse;
+    nsv += G.nsv;
+    nst += G.nst;
+    nse += G.nse;
+    G.iv0 = niv;
+    G.niv = m.niv;
+    G.it0 = nit;
+    G.nit = m.nit;
+    G.ie0 = nie;
+    G.nie = (int)m.ie.size();
+    niv += G.niv;
+    nit += G.nit;
+    nie += G.nie;
+    const int np[NTAB] = {G.nit, G.niv, G.nie};
+    for (int t = 0; t < NTAB; ++t) {
+      G.hnb[t] = next_pow2(std::max(16, 2 * np[t]));
+      G.hb0[t] = hb;
+      hb += G.hnb[t] + 1;
+      G.hcap[t] = std::max(256, 8 * np[t]);
+    }
+    G.pcap = initial_pcap(m);
+    G.mu = m.mu;
+    G.lam = m.lam;
+    G.kappa = m.kappa;
+    G.dhat = m.prm.dhat;
+    G.cell = m.cell;
+    G.bbox_diag = m.bbox;
+    G.newton_tol = m.prm.newton_tol;
+    for (int c = 0; c < 3; ++c) G.org[c] = m.org[c];
+    int fc = 0;
+    for (auto f : m.fixed) fc += f;
+    G.fixed_count = fc;
+  }
+  b->total_rows = rows;
+  const int nslices = rows / SLICE;
+  // ---- sliced BSR pattern
+  std::vector<int> slice_off(nslices + 1, 0);
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    const GelInfo& G = b->gi[g];
+    for (int s = 0; s < G.ns; ++s) {
+      int w = 1;
+      for (int l = 0; l < SLICE; ++l) {
+        const int i = s * SLICE + l;
+        if (i < m.nv) w = std::max(w, (int)m.adj[i].size());
+      }
+      slice_off[G.s0 + s + 1] = w * SLICE;
+    }
+  }
+  for (int s = 0; s < nslices; ++s) slice_off[s + 1] += slice_off[s];
+  const int nbp = slice_off[nslices];
+  b->nbp = nbp;
+  std::vector<int> colidx(nbp), bp_row(nbp), diag_pos(rows), ctr_cnt(nbp + 1, 0);
+  std::vector<int> vgel(rows), slice_gel(nslices);
+  std::vector<uint8_t> fixed(rows, 1);
+  std::vector<double> mass(rows, 0.0);
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    const GelInfo& G = b->gi[g];
+    for (int s = 0; s < G.ns; ++s) slice_gel[G.s0 + s] = g;
+    for (int l = 0; l < G.ns * SLICE; ++l) {
+      const int r = G.v0 + l;
+      vgel[r] = g;
+      const int s = r / SLICE, lane = r % SLICE;
+      const int w = (slice_off[s + 1] - slice_off[s]) / SLICE;
+      for (int k = 0; k < w; ++k) {
+        const int bp = slice_off[s] + SLICE * k + lane;
+        bp_row[bp] = r;
+        if (l < m.nv && k < (int)m.adj[l].size()) {
+          colidx[bp] = G.v0 + m.adj[l][k];
+          if (m.adj[l][k] == l) diag_pos[r] = bp;
+        } else {
+          colidx[bp] = r;
+          if (l >= m.nv && k == 0) diag_pos[r] = bp;
+        }
+      }
+      if (l < m.nv) {
+        fixed[r] = m.fixed[l];
+        mass[r] = m.mass[l];
+      }
+    }
+  }
+  auto bp_of = [&](int g, int li, int lj) {
+    const Mesh& m = b->mesh[g];
+    const auto& a = m.adj[li];
+    const int k = (int)(std::lower_bound(a.begin(), a.end(), lj) - a.begin());
+    const int r = b->gi[g].v0 + li;
+    return slice_off[r / SLICE] + SLICE * k + r % SLICE;
+  };
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    for (int t = 0; t < m.nt; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) ctr_cnt[bp_of(g, m.tets[4 * t + a], m.tets[4 * t + c]) + 1]++;
+  }
+  for (int k = 0; k < nbp; ++k) ctr_cnt[k + 1] += ctr_cnt[k];
+  std::vector<int> ctr(ctr_cnt[nbp]), fillp(ctr_cnt.begin(), ctr_cnt.end() - 1);
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    for (int t = 0; t < m.nt; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) {
+          const int bp = bp_of(g, m.tets[4 * t + a], m.tets[4 * t + c]);
+          ctr[fillp[bp]++] = ((b->gi[g].t0 + t) << 4) | (a << 2) | c;
+        }
+  }
+  // ---- host arrays of the concatenated gels
+  std::vector<double4_32a> X(rows);
+  std::vector<int4> tet4(std::max(tets, 1));
+  std::vector<int> tgel(std::max(tets, 1));
+  std::vector<double> Dminv(9 * (size_t)std::max(tets, 1)), vol(std::max(tets, 1));
+  std::vector<int> sv(std::max(nsv, 1)), q_gel(std::max(nq, 1)), q_tp(std::max(nq, 1));
+  std::vector<int4> st4(std::max(nst, 1));
+  std::vector<int2> se2(std::max(nse, 1));
+  std::vector<double> se_len2(std::max(nse, 1));
+  std::vector<double4_32a> ivl(std::max(niv, 1));
+  std::vector<int4> it4(std::max(nit, 1));
+  std::vector<int2> ie2(std::max(nie, 1));
+  std::vector<double> ie_len2(std::max(nie, 1));
+  std::vector<int> iv_gel(std::max(niv, 1)), it_gel(std::max(nit, 1)), ie_gel(std::max(nie, 1));
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    const GelInfo& G = b->gi[g];
+    for (int r = 0; r < G.ns * SLICE; ++r)
+      X[G.v0 + r] = r < m.nv ? make_double4_32a(m.X[3 * r], m.X[3 * r + 1], m.X[3 * r + 2], 0.0)
+                             : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    for (int t = 0; t < m.nt; ++t) {
+      tet4[G.t0 + t] = make_int4(G.v0 + m.tets[4 * t], G.v0 + m.tets[4 * t + 1], G.v0 + m.tets[4 * t + 2],
+                                 G.v0 + m.tets[4 * t + 3]);
+      tgel[G.t0 + t] = g;
+      for (int k = 0; k < 9; ++k) Dminv[9 * (size_t)(G.t0 + t) + k] = m.Dminv[9 * (size_t)t + k];
+      vol[G.t0 + t] = m.vol[t];
+    }
+    for (int k = 0; k < G.nsv; ++k) sv[G.sv0 + k] = G.v0 + m.sv[k];
+    for (int k = 0; k < G.nst; ++k) st4[G.st0 + k] = make_int4(G.v0 + m.st[k][0], G.v0 + m.st[k][1], G.v0 + m.st[k][2], 0);
+    for (int k = 0; k < G.nse; ++k) {
+      se2[G.se0 + k] = make_int2(G.v0 + m.se[k][0], G.v0 + m.se[k][1]);
+      se_len2[G.se0 + k] = m.se_len2[k];
+    }
+    for (int k = 0; k < G.nq; ++k) {
+      q_gel[G.q0 + k] = g;
+      if (k < G.nsv)
+        q_tp[G.q0 + k] = (PAIR_PT << 28) | k;
+      else if (k < G.nsv + G.nst)
+        q_tp[G.q0 + k] = (PAIR_TP << 28) | (k - G.nsv);
+      else
+        q_tp[G.q0 + k] = (PAIR_EE << 28) | (k - G.nsv - G.nst);
+    }
+    for (int k = 0; k < G.niv; ++k) {
+      ivl[G.iv0 + k] = make_double4_32a(m.IV[3 * k], m.IV[3 * k + 1], m.IV[3 * k + 2], 0.0);
+      iv_gel[G.iv0 + k] = g;
+    }
+    for (int k = 0; k < G.nit; ++k) {
+      it4[G.it0 + k] = make_int4(G.iv0 + m.it[k][0], G.iv0 + m.it[k][1], G.iv0 + m.it[k][2], 0);
+      it_gel[G.it0 + k] = g;
+    }
+    for (int k = 0; k < G.nie; ++k) {
+      ie2[G.ie0 + k] = make_int2(G.iv0 + m.ie[k][0], G.iv0 + m.ie[k][1]);
+      ie_len2[G.ie0 + k] = m.ie_len2[k];
+      ie_gel[G.ie0 + k] = g;
+    }
+  }
+  // ---- PCG plan
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    g_err = "no CUDA device";
+    delete b;
+    return TX_ERR_CUDA;
+  }
+  const int occ = std::max(1, pcg_max_ctas_per_sm());
+  int nctas = std::min(nsm * std::min(occ, 2), nslices);
+  nctas = std::max(nctas, 1);
+  std::vector<int> cta_s0(nctas + 1), cta_g0(nctas), cta_ng(nctas);
+  for (int c = 0; c <= nctas; ++c) cta_s0[c] = (int)((long long)c * nslices / nctas);
+  for (int c = 0; c < nctas; ++c) {
+    if (cta_s0[c + 1] > cta_s0[c]) {
+      cta_g0[c] = slice_gel[cta_s0[c]];
+      cta_ng[c] = slice_gel[cta_s0[c + 1] - 1] - cta_g0[c] + 1;
+    } else {
+      cta_g0[c] = 0;
+      cta_ng[c] = 0;
+    }
+    if (cta_ng[c] > PCG_MAXG_HOST) {
+      g_err = "too many small gels for one handle";
+      delete b;
+      return TX_ERR_ARG;
+    }
+  }
+  b->nctas = nctas;
+  // ---- energy pieces
+  for (int g = 0; g < n; ++g) {
+    const GelInfo& G = b->gi[g];
+    b->gel_piece_h.push_back((int)b->pieces_h.size());
+    for (int t = G.t0; t < G.t0 + G.nt; t += PIECE_HOST)
+      b->pieces_h.push_back(make_int4(g, 0, t, std::min(t + PIECE_HOST, G.t0 + G.nt)));
+    for (int r = G.v0; r < G.v0 + G.nv; r += PIECE_HOST)
+      b->pieces_h.push_back(make_int4(g, 1, r, std::min(r + PIECE_HOST, G.v0 + G.nv)));
+    b->pieces_h.push_back(make_int4(g, 2, 0, 0));
+  }
+  b->gel_piece_h.push_back((int)b->pieces_h.size());
+  b->npieces = (int)b->pieces_h.size();
+  // ---- device allocation
+  DevMem& M = b->mem;
+  Dev& d = b->d;
+  d.n_gels = n;
+  d.nrows = rows;
+  d.ntets = tets;
+  d.nslices = nslices;
+  d.nq = nq;
+  d.niv_total = niv;
+  d.gi = M.get<GelInfo>(n);
+  d.gc = M.get<GelCtl>(n);
+  d.gv = M.get<GelVar>(n);
+  d.X = M.get<double4_32a>(rows);
+  d.x = M.get<double4_32a>(rows);
+  d.xn = M.get<double4_32a>(rows);
+  d.v = M.get<double4_32a>(rows);
+  d.xt = M.get<double4_32a>(rows);
+  d.p = M.get<double4_32a>(rows);
+  d.grad = M.get<double4_32a>(rows);
+  b->x0 = M.get<double4_32a>(rows);
+  b->v0 = M.get<double4_32a>(rows);
+  b->ex = M.get<double4_32a>(rows);
+  b->ext = M.get<double4_32a>(rows);
+  d.mass = M.get<double>(rows);
+  d.fixed = M.get<uint8_t>(rows);
+  d.vgel = M.get<int>(rows);
+  d.tets = M.get<int4>(tets);
+  d.Dminv = M.get<double>(9 * (size_t)tets);
+  d.vol = M.get<double>(tets);
+  d.tgel = M.get<int>(tets);
+  d.tscr = M.get<double>((size_t)TS * tets);
+  d.tscr32 = b->mixed ? M.get<float>((size_t)TS32 * tets) : nullptr;
+  d.slice_off = M.get<int>(nslices + 1);
+  d.colidx = M.get<int>(nbp);
+  d.bp_row = M.get<int>(nbp);
+  d.vals = b->mixed ? nullptr : M.get<double>(9 * (size_t)nbp);
+  d.vals32 = b->mixed ? M.get<float>(9 * (size_t)nbp) : nullptr;
+  d.ctr_ptr = M.get<int>(nbp + 1);
+  d.ctr = M.get<int>(ctr.size());
+  d.diag_pos = M.get<int>(rows);
+  d.Minv = b->mixed ? nullptr : M.get<double>(9 * (size_t)rows);
+  d.Minv32 = b->mixed ? M.get<float>(9 * (size_t)rows) : nullptr;
+  d.r = M.get<double4_32a>(rows);
+  d.u = M.get<double4_32a>(rows);
+  d.w = M.get<double4_32a>(rows);
+  d.pp = M.get<double4_32a>(rows);
+  d.s = M.get<double4_32a>(rows);
+  d.part = M.get<double>(4 * (size_t)nslices);
+  d.gsc = M.get<double>(8 * (size_t)n);
+  d.bar = M.get<unsigned>(4);
+  d.act = M.get<int>(4);
+  d.sv = M.get<int>(nsv);
+  d.st = M.get<int4>(nst);
+  d.se = M.get<int2>(nse);
+  d.se_len2 = M.get<double>(nse);
+  d.q_gel = M.get<int>(nq);
+  d.q_tp = M.get<int>(nq);
+  d.iv_loc = M.get<double4_32a>(niv);
+  d.iv_cur = M.get<double4_32a>(niv);
+  d.iv_prev = M.get<double4_32a>(niv);
+  d.it = M.get<int4>(nit);
+  d.ie = M.get<int2>(nie);
+  d.ie_len2 = M.get<double>(nie);
+  d.iv_gel = M.get<int>(niv);
+  d.it_gel = M.get<int>(nit);
+  d.ie_gel = M.get<int>(nie);
+  d.hstart = M.get<int>(hb);
+  d.hcount = M.get<int>(hb);
+  d.qcount = M.get<int>(nq + 1);
+  d.qoff = M.get<int>(nq + 1);
+  d.err = M.get<int>(4);
+  b->pieces = M.get<int4>(b->npieces);
+  b->gel_piece = M.get<int>(n + 1);
+  b->part_e = M.get<double>(b->npieces);
+  b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
+  int* cta_buf = M.get<int>(3 * (size_t)nctas + 1 + nslices);
+  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !cta_buf || (b->mixed ? !d.vals32 : !d.vals)) {
+    M.release();
+    delete b;
+    return TX_ERR_OOM;
+  }
+  b->plan.cta_s0 = cta_buf;
+  b->plan.cta_g0 = cta_buf + nctas + 1;
+  b->plan.cta_ng = cta_buf + 2 * nctas + 1;
+  b->plan.slice_gel = cta_buf + 3 * nctas + 1;
+  if (b->mixed) {  // FP32 PCG vectors live in the upper half of dedicated buffers
+    d.u32 = (float4*)M.get<float4>(rows);
+    d.w32 = (float4*)M.get<float4>(rows);
+    d.pp32 = (float4*)M.get<float4>(rows);
+    d.s32 = (float4*)M.get<float4>(rows);
+    d.r32 = (float4*)M.get<float4>(rows);
+    d.x32 = (float4*)M.get<float4>(rows);
+  }
+  cudaHostAlloc((void**)&b->gc_h, sizeof(GelCtl) * n, cudaHostAllocDefault);
+  cudaHostAlloc((void**)&b->gv_h, sizeof(GelVar) * n, cudaHostAllocDefault);
+  if (!b->gc_h || !b->gv_h) {
+    M.release();
+    delete b;
+    return TX_ERR_OOM;
+  }
+  std::memset(b->gc_h, 0, sizeof(GelCtl) * n);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  auto U = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = up(dst, src, bytes);
+  };
+  U((void*)d.gi, b->gi.data(), sizeof(GelInfo) * n);
+  U((void*)d.gc, b->gc_h, sizeof(GelCtl) * n);
+  U(d.X, X.data(), sizeof(double4_32a) * rows);
+  U(d.x, X.data(), sizeof(double4_32a) * rows);
+  U(d.xn, X.data(), sizeof(double4_32a) * rows);
+  U(d.xt, X.data(), sizeof(double4_32a) * rows);
+  U(d.mass, mass.data(), sizeof(double) * rows);
+  U(d.fixed, fixed.data(), rows);
+  U(d.vgel, vgel.data(), sizeof(int) * rows);
+  U(d.tets, tet4.data(), sizeof(int4) * tets);
+  U(d.Dminv, Dminv.data(), sizeof(double) * 9 * (size_t)tets);
+  U(d.vol, vol.data(), sizeof(double) * tets);
+  U(d.tgel, tgel.data(), sizeof(int) * tets);
+  U(d.slice_off, slice_off.data(), sizeof(int) * (nslices + 1));
+  U(d.colidx, colidx.data(), sizeof(int) * nbp);
+  U(d.bp_row, bp_row.data(), sizeof(int) * nbp);
+  U(d.ctr_ptr, ctr_cnt.data(), sizeof(int) * (nbp + 1));
+  U(d.ctr, ctr.data(), sizeof(int) * ctr.size());
+  U(d.diag_pos, diag_pos.data(), sizeof(int) * rows);
+  U(d.sv, sv.data(), sizeof(int) * nsv);
+  U(d.st, st4.data(), sizeof(int4) * nst);
+  U(d.se, se2.data(), sizeof(int2) * nse);
+  U(d.se_len2, se_len2.data(), sizeof(double) * nse);
+  U(d.q_gel, q_gel.data(), sizeof(int) * nq);
+  U(d.q_tp, q_tp.data(), sizeof(int) * nq);
+  U(d.iv_loc, ivl.data(), sizeof(double4_32a) * niv);
+  U(d.it, it4.data(), sizeof(int4) * nit);
+  U(d.ie, ie2.data(), sizeof(int2) * nie);
+  U(d.ie_len2, ie_len2.data(), sizeof(double) * nie);
+  U(d.iv_gel, iv_gel.data(), sizeof(int) * niv);
+  U(d.it_gel, it_gel.data(), sizeof(int) * nit);
+  U(d.ie_gel, ie_gel.data(), sizeof(int) * nie);
+  U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
+  U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
+  U((void*)b->plan.cta_s0, cta_s0.data(), sizeof(int) * (nctas + 1));
+  U((void*)b->plan.cta_g0, cta_g0.data(), sizeof(int) * nctas);
+  U((void*)b->plan.cta_ng, cta_ng.data(), sizeof(int) * nctas);
+  U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
+  if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(double4_32a) * rows);
+  if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
+  if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
+  if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(d.qcount, 0, sizeof(int) * (nq + 1));
+  if (e == cudaSuccess) e = cudaMemset(d.tscr, 0, sizeof(double) * TS * (size_t)std::max(tets, 1));
+  if (e != cudaSuccess) {
+    g_err = cudaGetErrorString(e);
+    M.release();
+    delete b;
+    return TX_ERR_CUDA;
+  }
+  tx_status s = alloc_pairs(b);
+  if (s == TX_OK) s = alloc_hash(b);
+  if (s == TX_OK && cudaDeviceSynchronize() != cudaSuccess) s = TX_ERR_CUDA;
+  if (s != TX_OK) {
+    b->pair_mem.release();
+    b->hash_mem.release();
+    M.release();
+    delete b;
+    return s;
+  }
+  b->run.resize(n);
+  for (int g = 0; g < n; ++g) {
+    std::memcpy(b->run[g].pose, b->mesh[g].pose0, sizeof(double) * 7);
+    b->run[g].last.status = TX_OK;
+  }
+  *out = b;
+  return TX_OK;
+}
+
+void fill_ctl(tx_batch* b, int g, int phase, const Task& t) {
+  GelCtl& c = b->gc_h[g];
+  const Mesh& m = b->mesh[g];
+  c.phase = phase;
+  c.h = t.dt;
+  c.tol_p = m.prm.newton_tol * m.bbox * t.dt;
+  for (int k = 0; k < 3; ++k) c.grav[k] = m.prm.gravity[k];
+  quat_R(t.pb, c.R);
+  quat_R(t.pa, c.Rp);
+  for (int k = 0; k < 3; ++k) {
+    c.t[k] = t.pb[4 + k];
+    c.tp[k] = t.pa[4 + k];
+  }
+}
+
+void finish_request(tx_batch* b, int g, tx_status s) {
+  Run& R = b->run[g];
+  R.acc.status = s;
+  R.last = R.acc;
+  R.in_request = false;
+  R.stack.clear();
+  R.phase = PH_IDLE;
+  b->gc_h[g].phase = PH_IDLE;
+  b->done_queue.push_back(g);
+}
+
+// a failed request leaves the gel at the state it had when the request started
+tx_status rollback(tx_batch* b, const std::vector<int>& gels) {
+  for (int g : gels) {
+    const GelInfo& G = b->gi[g];
+    CK(cudaMemcpyAsync(b->d.x + G.v0, b->x0 + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+    CK(cudaMemcpyAsync(b->d.v + G.v0, b->v0 + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+    std::memcpy(b->run[g].pose, b->run[g].pose_req, sizeof(double) * 7);
+  }
+  return TX_OK;
+}
+
+// ---------------------------------------------------------------- begin (admission of substeps)
+tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
+  if (set.empty()) return TX_OK;
+  Dev& d = b->d;
+  cudaStream_t st = b->st;
+  // save the request start state of gels starting a new request
+  for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = (b->run[g].phase == PH_NEWTON) ? PH_PARK : b->gc_h[g].phase;
+  for (int g : set) {
+    const Task& t = b->run[g].stack.back();
+    if (t.first) {
+      const GelInfo& G = b->gi[g];
+      CK(cudaMemcpyAsync(b->x0 + G.v0, d.x + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(b->v0 + G.v0, d.v + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, st));
+    }
+    fill_ctl(b, g, PH_BEGIN, t);
+  }
+  tx_status s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  launch_gel_op(d, PH_BEGIN, 3, st);
+  launch_indenter_pose(d, PH_BEGIN, d.niv_total, st);
+  launch_hash_build(d, PH_BEGIN, 1, st);
+  launch_query(d, PH_BEGIN, 4, st);
+  launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
+  launch_query(d, PH_BEGIN, 1 | 4, st);
+  launch_pair_ranges(d, PH_BEGIN, 0, st);
+  const int accd_max = b->mesh[set[0]].prm.accd_max_iter;
+  launch_accd(d, PH_BEGIN, 1, accd_max, st);
+  launch_min_dist(d, PH_BEGIN, st);
+  CK(cudaGetLastError());
+  s = download_var(b);
+  if (s != TX_OK) return s;
+  std::vector<int> retry, start;
+  bool regrow_pairs = false, regrow_hash = false;
+  for (int g : set) {
+    const GelVar& v = b->gv_h[g];
+    Run& R = b->run[g];
+    if (v.flags & 1) {
+      for (int t = 0; t < NTAB; ++t) b->gi[g].hcap[t] = std::max(b->gi[g].hcap[t], 2 * v.hent[t] + 64);
+      regrow_hash = true;
+      retry.push_back(g);
+      continue;
+    }
+    if (v.flags & 32) {
+      b->gi[g].pcap = std::max(2 * b->gi[g].pcap, v.npair + v.npair / 2 + 64);
+      regrow_pairs = true;
+      retry.push_back(g);
+      continue;
+    }
+    if (v.flags & 2) {
+      std::vector<int> one{g};
+      finish_request(b, g, TX_ERR_CCD_MAXIT);
+      s = rollback(b, one);
+      if (s != TX_OK) return s;
+      continue;
+    }
+    const bool hit = (v.flags & 8) != 0;
+    const double dmin = bitsd_host(v.dmin_bits);
+    if (hit || !(dmin > 0.0)) {
+      Task t = R.stack.back();
+      if (t.depth >= b->mesh[g].prm.max_split_depth) {
+        std::vector<int> one{g};
+        finish_request(b, g, TX_ERR_INFEASIBLE);
+        s = rollback(b, one);
+        if (s != TX_OK) return s;
+        continue;
+      }
+      R.stack.pop_back();
+      Task a = t, c = t;
+      double mid[7];
+      pose_mid(t.pa, t.pb, mid);
+      std::memcpy(a.pb, mid, sizeof(mid));
+      std::memcpy(c.pa, mid, sizeof(mid));
+      a.dt = c.dt = 0.5 * t.dt;
+      a.depth = c.depth = t.depth + 1;
+      c.first = false;
+      R.stack.push_back(c);
+      R.stack.push_back(a);
+      R.phase = PH_IDLE;
+      b->gc_h[g].phase = PH_IDLE;
+      continue;
+    }
+    start.push_back(g);
+  }
+  for (int g = 0; g < b->n; ++g)
+    if (b->gc_h[g].phase == PH_BEGIN) b->gc_h[g].phase = PH_PARK;
+  if (!start.empty()) {
+    for (int g : start) b->gc_h[g].phase = PH_START;
+    s = upload_ctl(b);
+    if (s != TX_OK) return s;
+    launch_rows(0, d, PH_START, st);         // x_n, predictor
+    launch_hash_build(d, PH_START, 0, st);   // static tables at the target pose
+    launch_energy(d, PH_START, b->pieces, b->npieces, b->gel_piece, b->part_e, 0, st);
+    CK(cudaGetLastError());
+    for (int g : start) {
+      Run& R = b->run[g];
+      R.phase = PH_NEWTON;
+      R.newton_sub = 0;
+      R.acc.substeps += 1;
+    }
+  }
+  for (int g = 0; g < b->n; ++g) {
+    if (b->run[g].phase == PH_NEWTON) b->gc_h[g].phase = PH_NEWTON;
+    else if (b->gc_h[g].phase == PH_PARK || b->gc_h[g].phase == PH_START) b->gc_h[g].phase = PH_IDLE;
+  }
+  s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  if (!retry.empty()) {
+    if (retries > 4) {
+      for (int g : retry) finish_request(b, g, TX_ERR_OOM);
+      return TX_OK;
+    }
+    if (regrow_pairs) {
+      s = alloc_pairs(b);
+      if (s != TX_OK) return s;
+    }
+    if (regrow_hash) {
+      s = alloc_hash(b);
+      if (s != TX_OK) return s;
+    }
+    return do_begin(b, retry, retries + 1);
+  }
+  return TX_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- one Newton iteration
+// The part after the PCG: candidates along p, ACCD, line search.  Runs for the gels whose
+// control phase is PH_NEWTON.
+tx_status post_pcg(tx_batch* b) {
+  Dev& d = b->d;
+  cudaStream_t st = b->st;
+  launch_query(d, PH_NEWTON, 2 | 8, st);
+  launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
+  launch_query(d, PH_NEWTON, 1 | 2 | 8, st);
+  launch_pair_ranges(d, PH_NEWTON, 1, st);
+  int accd_max = 1, ls_max = 1;
+  for (int g = 0; g < b->n; ++g)
+    if (b->gc_h[g].phase == PH_NEWTON) {
+      accd_max = std::max(accd_max, b->mesh[g].prm.accd_max_iter);
+      ls_max = std::max(ls_max, b->mesh[g].prm.ls_max_halvings);
+    }
+  launch_accd(d, PH_NEWTON, 0, accd_max, st);
+  launch_gel_op(d, PH_NEWTON, 2, st);
+  // first trial; usually accepted
+  launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
+  launch_rows(1, d, PH_NEWTON, st);
+  launch_gel_op(d, PH_NEWTON, 5, st);
+  CK(cudaGetLastError());
+  tx_status s = download_var(b);
+  if (s != TX_OK) return s;
+  for (int trial = 1; trial <= ls_max + 1; ++trial) {
+    bool searching = false;
+    for (int g = 0; g < b->n; ++g)
+      if (b->gc_h[g].phase == PH_NEWTON && !b->gv_h[g].converged && b->gv_h[g].ls_state == 0) searching = true;
+    if (!searching) break;
+    for (int k = 0; k < 4; ++k) {  // a few halvings per host round trip
+      launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
+      launch_rows(1, d, PH_NEWTON, st);
+      launch_gel_op(d, PH_NEWTON, 5, st);
+    }
+    CK(cudaGetLastError());
+    s = download_var(b);
+    if (s != TX_OK) return s;
+  }
+  return TX_OK;
+}
+
+tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
+  if (fin.empty()) return TX_OK;
+  Dev& d = b->d;
+  for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = PH_PARK;
+  for (int g : fin) b->gc_h[g].phase = PH_FINAL;
+  tx_status s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  launch_rows(2, d, PH_FINAL, b->st);      // v = (x - x_n) / h
+  launch_gel_op(d, PH_FINAL, 4, b->st);    // distance minimum at the final state
+  launch_min_dist(d, PH_FINAL, b->st);
+  CK(cudaGetLastError());
+  s = download_var(b);
+  if (s != TX_OK) return s;
+  for (int g : fin) {
+    Run& R = b->run[g];
+    const GelVar& v = b->gv_h[g];
+    Task t = R.stack.back();
+    R.stack.pop_back();
+    R.acc.newton_iters += R.newton_sub;
+    R.acc.ls_halvings += v.ls_total;
+    R.acc.energy = v.E_cur;
+    R.acc.active_pairs = v.active_pairs;
+    R.acc.candidate_pairs = v.npair;
+    R.acc.min_distance = bitsd_host(v.dmin_bits);
+    for (int c = 0; c < 3; ++c) R.acc.contact_force[c] = v.fc[c];
+    std::memcpy(R.pose, t.pb, sizeof(double) * 7);
+    R.phase = PH_IDLE;
+    if (R.stack.empty()) finish_request(b, g, TX_OK);
+  }
+  for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = b->run[g].phase == PH_NEWTON ? PH_NEWTON : PH_IDLE;
+  return upload_ctl(b);
+}
+
+tx_status do_newton(tx_batch* b) {
+  std::vector<int> set;
+  for (int g = 0; g < b->n; ++g) {
+    b->gc_h[g].phase = b->run[g].phase == PH_NEWTON ? PH_NEWTON : PH_IDLE;
+    if (b->run[g].phase == PH_NEWTON) set.push_back(g);
+  }
+  if (set.empty()) return TX_OK;
+  Dev& d = b->d;
+  cudaStream_t st = b->st;
+  tx_status s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  double eta = 1e-3;
+  int pcg_max = 1;
+  for (int g : set) {
+    eta = std::min(eta, b->mesh[g].prm.pcg_rel_tol);
+    pcg_max = std::max(pcg_max, b->mesh[g].prm.pcg_max_iter);
+  }
+  launch_gel_op(d, PH_NEWTON, 0, st);
+  launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
+  launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
+  launch_contact_assemble(d, PH_NEWTON, b->mixed, st);
+  launch_precond(d, PH_NEWTON, b->mixed, st);
+  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * 4, st));
+  CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+  launch_gel_op(d, PH_NEWTON, 1, st);
+  CK(cudaGetLastError());
+  s = post_pcg(b);
+  if (s != TX_OK) return s;
+  int derr = 0;
+  CK(cudaMemcpy(&derr, d.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    CK(cudaMemset(d.err, 0, sizeof(int)));
+    std::vector<int> fail;
+    for (int g : set) {
+      finish_request(b, g, TX_ERR_DEVICE_TIMEOUT);
+      fail.push_back(g);
+    }
+    return rollback(b, fail);
+  }
+  // pair-segment overflow: grow and redo the line-search part for those gels
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    std::vector<int> over;
+    for (int g : set)
+      if (b->gv_h[g].ls_state == 4) over.push_back(g);
+    if (over.empty()) break;
+    for (int g : over) b->gi[g].pcap = std::max(2 * b->gi[g].pcap, b->gv_h[g].npair + b->gv_h[g].npair / 2 + 64);
+    s = alloc_pairs(b);
+    if (s != TX_OK) return s;
+    for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = PH_PARK;
+    for (int g : over) b->gc_h[g].phase = PH_NEWTON;
+    s = upload_ctl(b);
+    if (s != TX_OK) return s;
+    launch_gel_op(d, PH_NEWTON, 6, st);  // clear the overflow flag
+    s = post_pcg(b);
+    if (s != TX_OK) return s;
+  }
+  std::vector<int> fin, fail;
+  for (int g : set) {
+    Run& R = b->run[g];
+    const GelVar& v = b->gv_h[g];
+    R.acc.pcg_iters += v.pcg_it;
+    if (v.converged) {
+      fin.push_back(g);
+    } else if (v.ls_state == 2) {
+      finish_request(b, g, TX_ERR_LINESEARCH);
+      fail.push_back(g);
+    } else if (v.ls_state == 3) {
+      R.newton_sub += 1;
+      if (R.newton_sub >= b->mesh[g].prm.newton_max_iter) {
+        finish_request(b, g, TX_ERR_NEWTON_MAXIT);
+        fail.push_back(g);
+      }
+    } else {
+      finish_request(b, g, TX_ERR_OOM);
+      fail.push_back(g);
+    }
+  }
+  s = rollback(b, fail);
+  if (s != TX_OK) return s;
+  return finalize_substeps(b, fin);
+}
+
+tx_status advance(tx_batch* b) {
+  std::vector<int> begin;
+  for (int g = 0; g < b->n; ++g) {
+    Run& R = b->run[g];
+    if (R.in_request && R.phase == PH_IDLE && !R.stack.empty()) begin.push_back(g);
+  }
+  tx_status s = do_begin(b, begin);
+  if (s != TX_OK) return s;
+  return do_newton(b);
+}
+
+tx_status submit_one(tx_batch* b, int g, const double pose[7], double dt) {
+  if (g < 0 || g >= b->n || !pose || !(dt > 0.0) || !std::isfinite(dt)) return TX_ERR_ARG;
+  double qn = 0.0;
+  for (int k = 0; k < 7; ++k)
+    if (!std::isfinite(pose[k])) return TX_ERR_ARG;
+  for (int k = 0; k < 4; ++k) qn += pose[k] * pose[k];
+  if (!(qn > 0.0)) return TX_ERR_ARG;
+  Run& R = b->run[g];
+  if (R.in_request) return TX_ERR_ARG;
+  R.in_request = true;
+  R.acc = tx_step_stats{};
+  R.newton_sub = 0;
+  std::memcpy(R.pose_req, R.pose, sizeof(double) * 7);
+  Task t;
+  std::memcpy(t.pa, R.pose, sizeof(double) * 7);
+  std::memcpy(t.pb, pose, sizeof(double) * 7);
+  t.dt = dt;
+  t.depth = 0;
+  t.first = true;
+  R.stack.clear();
+  R.stack.push_back(t);
+  return TX_OK;
+}
+
+tx_status copy_rows_out(tx_batch* b, int g, const double4_32a* src, double* dst, bool device_ptrs) {
+  const GelInfo& G = b->gi[g];
+  CK(cudaMemcpy2DAsync(dst, 3 * sizeof(double), src + G.v0, sizeof(double4_32a), 3 * sizeof(double), G.nv,
+                       device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st));
+  if (!device_ptrs) CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+
+tx_status copy_rows_in(tx_batch* b, int g, double4_32a* dst, const double* src) {
+  const GelInfo& G = b->gi[g];
+  CK(cudaMemcpy2DAsync(dst + G.v0, sizeof(double4_32a), src, 3 * sizeof(double), 3 * sizeof(double), G.nv,
+                       cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+
+// positions at which to evaluate: x, xt (host), indenter at pose; leaves the state untouched
+tx_status eval_setup(tx_batch* b, int g, const double* x, const double* xt, double h, const double pose[7]) {
+  if (!x || !xt || !pose || !(h > 0.0)) return TX_ERR_ARG;
+  for (int k = 0; k < b->n; ++k)
+    if (b->run[k].in_request) return TX_ERR_ARG;
+  const GelInfo& G = b->gi[g];
+  Dev& d = b->d;
+  CK(cudaMemcpyAsync(b->ex + G.v0, d.x + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+  CK(cudaMemcpyAsync(b->ext + G.v0, d.xt + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+  tx_status s = copy_rows_in(b, g, d.x, x);
+  if (s == TX_OK) s = copy_rows_in(b, g, d.xt, xt);
+  if (s != TX_OK) return s;
+  for (int k = 0; k < b->n; ++k) b->gc_h[k].phase = PH_IDLE;
+  Task t;
+  std::memcpy(t.pa, pose, sizeof(double) * 7);
+  std::memcpy(t.pb, pose, sizeof(double) * 7);
+  t.dt = h;
+  fill_ctl(b, g, PH_EVAL, t);
+  s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  launch_gel_op(d, PH_EVAL, 3, b->st);
+  launch_indenter_pose(d, PH_EVAL, d.niv_total, b->st);
+  launch_hash_build(d, PH_EVAL, 0, b->st);
+  launch_query(d, PH_EVAL, 0, b->st);
+  launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, b->st);
+  launch_query(d, PH_EVAL, 1, b->st);
+  launch_pair_ranges(d, PH_EVAL, 0, b->st);
+  CK(cudaGetLastError());
+  s = download_var(b);
+  if (s != TX_OK) return s;
+  if (b->gv_h[g].flags & (1 | 32)) {  // grow and redo
+    const GelVar& v = b->gv_h[g];
+    for (int tb = 0; tb < NTAB; ++tb) b->gi[g].hcap[tb] = std::max(b->gi[g].hcap[tb], 2 * v.hent[tb] + 64);
+    b->gi[g].pcap = std::max(b->gi[g].pcap, v.npair + v.npair / 2 + 64);
+    s = alloc_hash(b);
+    if (s == TX_OK) s = alloc_pairs(b);
+    if (s != TX_OK) return s;
+    launch_gel_op(d, PH_EVAL, 3, b->st);
+    launch_hash_build(d, PH_EVAL, 0, b->st);
+    launch_query(d, PH_EVAL, 0, b->st);
+    launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, b->st);
+    launch_query(d, PH_EVAL, 1, b->st);
+    launch_pair_ranges(d, PH_EVAL, 0, b->st);
+  }
+  return TX_OK;
+}
+
+tx_status eval_restore(tx_batch* b, int g) {
+  const GelInfo& G = b->gi[g];
+  Dev& d = b->d;
+  CK(cudaMemcpyAsync(d.x + G.v0, b->ex + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+  CK(cudaMemcpyAsync(d.xt + G.v0, b->ext + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+  b->gc_h[g].phase = PH_IDLE;
+  tx_status s = upload_ctl(b);
+  if (s != TX_OK) return s;
+  CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+
+void destroy_batch(tx_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  b->mem.release();
+  b->pair_mem.release();
+  b->hash_mem.release();
+  if (b->gc_h) cudaFreeHost(b->gc_h);
+  if (b->gv_h) cudaFreeHost(b->gv_h);
+  delete b;
+}
+
+}  // namespace
+
+// ======================================================================================= C ABI
+extern "C" {
+
+void tx_params_default(tx_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dhat = 1e-4;
+  p->kappa = 0.0;
+  p->newton_tol = 1e-5;
+  p->pcg_rel_tol = 1e-3;
+  p->newton_max_iter = 200;
+  p->pcg_max_iter = 2000;
+  p->ls_max_halvings = 60;
+  p->accd_max_iter = 1000000;
+  p->max_split_depth = 4;
+  p->precision = TX_PREC_FP64;
+  p->refine_max = 3;
+}
+
+const char* tx_status_str(tx_status s) {
+  switch (s) {
+    case TX_OK: return "TX_OK";
+    case TX_ERR_ARG: return "TX_ERR_ARG";
+    case TX_ERR_OOM: return "TX_ERR_OOM";
+    case TX_ERR_MESH_INVERTED: return "TX_ERR_MESH_INVERTED";
+    case TX_ERR_INFEASIBLE: return "TX_ERR_INFEASIBLE";
+    case TX_ERR_NEWTON_MAXIT: return "TX_ERR_NEWTON_MAXIT";
+    case TX_ERR_PCG_MAXIT: return "TX_ERR_PCG_MAXIT";
+    case TX_ERR_LINESEARCH: return "TX_ERR_LINESEARCH";
+    case TX_ERR_CCD_MAXIT: return "TX_ERR_CCD_MAXIT";
+    case TX_ERR_CUDA: return "TX_ERR_CUDA";
+    case TX_ERR_DEVICE_TIMEOUT: return "TX_ERR_DEVICE_TIMEOUT";
+  }
+  return "TX_ERR_UNKNOWN";
+}
+
+const char* tx_last_error(void) { return g_err.c_str(); }
+
+tx_status tx_batch_create(const tx_gel_desc* descs, int32_t n, void* stream, tx_batch** out) {
+  if (!out) return TX_ERR_ARG;
+  *out = nullptr;
+  return create_batch(descs, n, stream, out);
+}
+
+void tx_batch_destroy(tx_batch* b) { destroy_batch(b); }
+
+int32_t tx_batch_size(const tx_batch* b) { return b ? b->n : 0; }
+
+tx_status tx_batch_submit(tx_batch* b, int32_t count, const int32_t* ids, const double* poses,
+                          const double* dts) {
+  if (!b || count < 0 || (count > 0 && (!ids || !poses || !dts))) return TX_ERR_ARG;
+  for (int k = 0; k < count; ++k) {
+    const int g = ids[k];
+    if (g < 0 || g >= b->n || b->run[g].in_request) return TX_ERR_ARG;
+  }
+  for (int k = 0; k < count; ++k) {
+    tx_status s = submit_one(b, ids[k], poses + 7 * k, dts[k]);
+    if (s != TX_OK) return s;
+  }
+  return TX_OK;
+}
+
+tx_status tx_batch_advance(tx_batch* b, int32_t* n_done, int32_t* done_ids, tx_status* done_status) {
+  if (!b || !n_done) return TX_ERR_ARG;
+  b->done_queue.clear();
+  tx_status s = advance(b);
+  *n_done = (int32_t)b->done_queue.size();
+  for (size_t k = 0; k < b->done_queue.size(); ++k) {
+    if (done_ids) done_ids[k] = b->done_queue[k];
+    if (done_status) done_status[k] = (tx_status)b->run[b->done_queue[k]].last.status;
+  }
+  return s;
+}
+
+int32_t tx_batch_pending(const tx_batch* b) {
+  if (!b) return 0;
+  int c = 0;
+  for (const Run& R : b->run) c += R.in_request ? 1 : 0;
+  return c;
+}
+
+tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_status* statuses) {
+  if (!b || !poses || !dts) return TX_ERR_ARG;
+  for (int g = 0; g < b->n; ++g)
+    if (b->run[g].in_request) return TX_ERR_ARG;
+  for (int g = 0; g < b->n; ++g) {
+    tx_status s = submit_one(b, g, poses + 7 * g, dts[g]);
+    if (s != TX_OK) {
+      for (int k = 0; k < g; ++k) {
+        b->run[k].in_request = false;
+        b->run[k].stack.clear();
+      }
+      return s;
+    }
+  }
+  while (tx_batch_pending(b) > 0) {
+    b->done_queue.clear();
+    tx_status s = advance(b);
+    if (s != TX_OK) return s;
+  }
+  tx_status worst = TX_OK;
+  for (int g = 0; g < b->n; ++g) {
+    const tx_status s = (tx_status)b->run[g].last.status;
+    if (statuses) statuses[g] = s;
+    if (s != TX_OK && worst == TX_OK) worst = s;
+  }
+  return worst;
+}
+
+tx_status tx_batch_state(const tx_batch* bc, int32_t g, double* x, double* v, double f_contact[3],
+                         tx_step_stats* stats) {
+  tx_batch* b = const_cast<tx_batch*>(bc);
+  if (!b || g < 0 || g >= b->n) return TX_ERR_ARG;
+  tx_status s = TX_OK;
+  if (x) s = copy_rows_out(b, g, b->d.x, x, false);
+  if (s == TX_OK && v) s = copy_rows_out(b, g, b->d.v, v, false);
+  if (s != TX_OK) return s;
+  const tx_step_stats& L = b->run[g].last;
+  if (f_contact)
+    for (int c = 0; c < 3; ++c) f_contact[c] = L.contact_force[c];
+  if (stats) {
+    *stats = L;
+    std::vector<double> xs(3 * (size_t)b->gi[g].nv);
+    s = copy_rows_out(b, g, b->d.x, xs.data(), false);
+    if (s != TX_OK) return s;
+    for (int c = 0; c < 3; ++c) {
+      double m = 0.0;
+      for (int i = 0; i < b->gi[g].nv; ++i) m += xs[3 * i + c];
+      stats->mean_position[c] = m / b->gi[g].nv;
+    }
+  }
+  return TX_OK;
+}
+
+tx_status tx_batch_set_state(tx_batch* b, int32_t g, const double* x, const double* v, const double pose[7]) {
+  if (!b || g < 0 || g >= b->n || b->run[g].in_request) return TX_ERR_ARG;
+  tx_status s = TX_OK;
+  if (x) s = copy_rows_in(b, g, b->d.x, x);
+  if (s == TX_OK && v) s = copy_rows_in(b, g, b->d.v, v);
+  if (s != TX_OK) return s;
+  if (pose) std::memcpy(b->run[g].pose, pose, sizeof(double) * 7);
+  return TX_OK;
+}
+
+tx_status tx_batch_reset(tx_batch* b, int32_t g) {
+  if (!b || g < 0 || g >= b->n || b->run[g].in_request) return TX_ERR_ARG;
+  const GelInfo& G = b->gi[g];
+  CK(cudaMemcpyAsync(b->d.x + G.v0, b->d.X + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+  CK(cudaMemsetAsync(b->d.v + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  std::memcpy(b->run[g].pose, b->mesh[g].pose0, sizeof(double) * 7);
+  b->run[g].last = tx_step_stats{};
+  return TX_OK;
+}
+
+// ---- single gel = batch of one
+tx_status tx_gel_create(const tx_gel_desc* desc, void* stream, tx_gel** out) {
+  if (!out) return TX_ERR_ARG;
+  *out = nullptr;
+  tx_batch* b = nullptr;
+  tx_status s = create_batch(desc, 1, stream, &b);
+  if (s != TX_OK) return s;
+  *out = new tx_gel{b};
+  return TX_OK;
+}
+
+void tx_gel_destroy(tx_gel* g) {
+  if (!g) return;
+  destroy_batch(g->b);
+  delete g;
+}
+
+tx_status tx_gel_step(tx_gel* g, const double pose[7], double dt) {
+  if (!g || !pose) return TX_ERR_ARG;
+  tx_status st = TX_OK;
+  tx_status s = tx_batch_step(g->b, pose, &dt, &st);
+  return s != TX_OK ? s : st;
+}
+
+tx_status tx_gel_state(const tx_gel* g, double* x, double* v, double f_contact[3], tx_step_stats* stats,
+                       int32_t device_ptrs) {
+  if (!g) return TX_ERR_ARG;
+  tx_batch* b = g->b;
+  if (device_ptrs) {
+    tx_status s = TX_OK;
+    if (x) s = copy_rows_out(b, 0, b->d.x, x, true);
+    if (s == TX_OK && v) s = copy_rows_out(b, 0, b->d.v, v, true);
+    if (s != TX_OK) return s;
+    return tx_batch_state(b, 0, nullptr, nullptr, f_contact, stats);
+  }
+  return tx_batch_state(b, 0, x, v, f_contact, stats);
+}
+
+tx_status tx_gel_get_state(const tx_gel* g, double* x, double* v, double pose[7]) {
+  if (!g) return TX_ERR_ARG;
+  tx_status s = tx_batch_state(g->b, 0, x, v, nullptr, nullptr);
+  if (s == TX_OK && pose) std::memcpy(pose, g->b->run[0].pose, sizeof(double) * 7);
+  return s;
+}
+
+tx_status tx_gel_set_state(tx_gel* g, const double* x, const double* v, const double pose[7]) {
+  if (!g) return TX_ERR_ARG;
+  return tx_batch_set_state(g->b, 0, x, v, pose);
+}
+
+tx_status tx_gel_reset(tx_gel* g) {
+  if (!g) return TX_ERR_ARG;
+  return tx_batch_reset(g->b, 0);
+}
+
+size_t tx_gel_footprint_bytes(const tx_gel_desc* desc) {
+  Mesh m;
+  if (build_mesh(desc, m) != TX_OK) return 0;
+  const bool mixed = desc->params.precision == TX_PREC_MIXED;
+  const size_t rows = (size_t)((m.nv + SLICE - 1) / SLICE) * SLICE;
+  size_t nbp = 0;
+  for (size_t s = 0; s < rows / SLICE; ++s) {
+    size_t w = 1;
+    for (int l = 0; l < SLICE; ++l) {
+      const size_t i = s * SLICE + l;
+      if (i < (size_t)m.nv) w = std::max(w, m.adj[i].size());
+    }
+    nbp += w * SLICE;
+  }
+  const size_t nt = m.nt, nq = m.sv.size() + m.st.size() + m.se.size();
+  size_t bytes = rows * (16 * sizeof(double4_32a) + 8 + 1 + 4 + 4 + 72);
+  if (mixed) bytes += rows * (6 * sizeof(float4) + 36);
+  bytes += nt * (16 + 72 + 8 + 4 + 64 + TS * 8 + (mixed ? TS32 * 4 : 0));
+  bytes += nbp * (4 + 4 + 4 + (mixed ? 36 : 72));
+  bytes += nq * (4 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;
+  bytes += (size_t)initial_pcap(m) * 20;
+  return bytes;
+}
+
+tx_status tx_gel_energy(tx_gel* gl, const double* x, const double* xt, double h, const double pose[7],
+                        double* energy, double parts[5]) {
+  if (!gl) return TX_ERR_ARG;
+  tx_batch* b = gl->b;
+  tx_status s = eval_setup(b, 0, x, xt, h, pose);
+  if (s != TX_OK) return s;
+  Dev& d = b->d;
+  launch_energy(d, PH_EVAL, b->pieces, b->npieces, b->gel_piece, b->part_e, 2, b->st);
+  launch_min_dist(d, PH_EVAL, b->st);
+  CK(cudaGetLastError());
+  std::vector<double> pe(b->npieces);
+  CK(cudaMemcpyAsync(pe.data(), b->part_e, sizeof(double) * b->npieces, cudaMemcpyDeviceToHost, b->st));
+  s = download_var(b);
+  if (s != TX_OK) return s;
+  if (energy) *energy = b->gv_h[0].E_try;
+  if (parts) {
+    double p3[3] = {0.0, 0.0, 0.0};
+    for (int k = b->gel_piece_h[0]; k < b->gel_piece_h[1]; ++k) {
+      const int kind = b->pieces_h[k].y;
+      p3[kind == 0 ? 1 : (kind == 1 ? 0 : 2)] += pe[k];
+    }
+    parts[0] = p3[0];
+    parts[1] = p3[1];
+    parts[2] = p3[2];
+    parts[3] = bitsd_host(b->gv_h[0].dmin_bits);
+    parts[4] = b->gv_h[0].active_pairs;
+  }
+  return eval_restore(b, 0);
+}
+
+tx_status tx_gel_gradient(tx_gel* gl, const double* x, const double* xt, double h, const double pose[7],
+                          double* grad, double f_contact[3]) {
+  if (!gl || !grad) return TX_ERR_ARG;
+  tx_batch* b = gl->b;
+  tx_status s = eval_setup(b, 0, x, xt, h, pose);
+  if (s != TX_OK) return s;
+  Dev& d = b->d;
+  launch_gel_op(d, PH_EVAL, 0, b->st);
+  launch_tet_assemble(d, PH_EVAL, b->mixed, b->st);
+  launch_gather(d, PH_EVAL, b->nbp, b->mixed, b->st);
+  launch_contact_assemble(d, PH_EVAL, b->mixed, b->st);
+  CK(cudaGetLastError());
+  s = copy_rows_out(b, 0, d.grad, grad, false);
+  if (s != TX_OK) return s;
+  s = download_var(b);
+  if (s != TX_OK) return s;
+  if (f_contact)
+    for (int c = 0; c < 3; ++c) f_contact[c] = b->gv_h[0].fc[c];
+  return eval_restore(b, 0);
+}
+
+tx_status tx_eval_tets(int32_t n, const double* X, const double* x, double mu, double lambda, int32_t project,
+                       double* e, double* g, double* H, void* stream) {
+  if (n < 0 || (n > 0 && (!X || !x || !e))) return TX_ERR_ARG;
+  launch_eval_tets(n, X, x, mu, lambda, project, e, g, H, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return TX_OK;
+}
+
+tx_status tx_eval_pairs(int32_t n, const int32_t* kind, const double* P, double dhat, const double* eps_x,
+                        const int32_t* free_mask, double* bo, double* g, double* H, int32_t* dtype, void* stream) {
+  if (n < 0 || (n > 0 && (!kind || !P || !bo)) || !(dhat > 0)) return TX_ERR_ARG;
+  launch_eval_pairs(n, kind, P, dhat, eps_x, free_mask, bo, g, H, dtype, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return TX_OK;
+}
+
+tx_status tx_eval_accd(int32_t n, const int32_t* kind, const double* P, const double* dP, double s, double tc,
+                       int32_t max_iter, double* toi, int32_t* hit, void* stream) {
+  if (n < 0 || (n > 0 && (!kind || !P || !dP || !toi || !hit)) || !(s > 0 && s < 1) || max_iter < 1)
+    return TX_ERR_ARG;
+  launch_eval_accd(n, kind, P, dP, s, tc, max_iter, toi, hit, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return TX_OK;
+}
+
+}  // extern "C"

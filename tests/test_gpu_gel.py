@@ -1,0 +1,120 @@
+"""Gel-level parity of the CUDA path against the FP64 oracle: energy and gradient of the
+incremental potential at seeded states, whole-step trajectories, invariants and error paths."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2411_04776_gb300 import binding as B  # noqa: E402
+from paper_2411_04776_gb300 import workloads as W  # noqa: E402
+from tests.gpu_util import POS_TOL, smooth_state  # noqa: E402
+
+
+def contact_pose(wl, depth):
+    p = wl.poses[-1].copy()
+    p[6] += (0.6e-3 - depth) if wl.name.startswith("gel10") else 0.0
+    return p
+
+
+@pytest.mark.parametrize("make", [lambda: W.small_gel_sphere(0), lambda: W.small_gel_sphere(3),
+                                  lambda: W.mini_gel(1, kind="cylinder", n_press=60, n_slide=0)])
+def test_energy_and_gradient_match_oracle(make):
+    wl = make()
+    gel = B.Gel.from_workload(wl)
+    ref = O.OracleGel.from_workload(wl)
+    x, xt, h = smooth_state(wl, 5)
+    # indenter lowered so that it overlaps the barrier zone but not the (displaced) gel
+    pose = wl.pose0.copy()
+    pose[6] -= 0.95 * W.DHAT
+    eg, pg = gel.energy(x, xt, h, pose)
+    eo, po = ref.energy(x, xt, h, pose)
+    assert np.isfinite(eo) and po["active"] > 0
+    assert pg["active"] == po["active"]
+    assert abs(eg - eo) <= 1e-12 * abs(eo)
+    for k in ("inertia", "elastic", "barrier"):
+        assert abs(pg[k] - po[k]) <= 1e-11 * abs(po[k]) + 1e-30, k
+    gg, fg = gel.gradient(x, xt, h, pose)
+    go, fo = ref.gradient(x, xt, h, pose)
+    free = wl.gel.dirichlet == 0
+    scale = np.abs(go[free]).max()
+    assert np.abs(gg[free] - go[free]).max() <= 1e-10 * scale
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max()
+
+
+def test_rest_state_is_a_fixed_point():
+    wl = W.small_gel_sphere(0)
+    gel = B.Gel.from_workload(wl)
+    far = W.pose((0.009, 0.012, 0.05))
+    gel.set_state(wl.gel.verts, np.zeros_like(wl.gel.verts), far)
+    assert gel.step(far, wl.dt) == 0
+    x, v, fc, st = gel.state()
+    assert st.newton_iters == 0 and np.array_equal(x, wl.gel.verts) and np.all(v == 0)
+
+
+def run_pair(wl, steps, tol=1e-7):
+    gel = B.Gel.from_workload(wl, newton_tol=tol)
+    ref = O.OracleGel.from_workload(wl, newton_tol=tol)
+    errs = []
+    for s in range(steps):
+        st = gel.step(wl.poses[s], wl.dt)
+        info = ref.step(wl.poses[s], wl.dt)
+        assert st == 0, B.STATUS_NAMES[st]
+        assert info["status"] == 0
+        xg, vg, fg, sg = gel.state()
+        xo, vo, fo, _ = ref.state()
+        errs.append(np.abs(xg - xo).max())
+        assert sg.substeps == info["substeps"]
+        assert sg.min_distance > 0
+    return gel, ref, np.array(errs), fg, fo
+
+
+def test_small_gel_trajectory_matches_oracle():
+    """All 30 steps of the 10x13x4 gel pressed 0.6 mm by the r = 5 mm sphere."""
+    wl = W.small_gel_sphere(0)
+    gel, ref, errs, fg, fo = run_pair(wl, 30)
+    assert errs.max() <= POS_TOL, errs
+    assert np.abs(fg - fo).max() <= 1e-4 * np.abs(fo).max()
+
+
+def test_batch_equals_alone():
+    wls = [W.small_gel_sphere(s, n_steps=12) for s in range(3)]
+    descs = [B.GelDesc.from_workload(w, newton_tol=1e-7) for w in wls]
+    b = B.tx_batch_create(descs)
+    alone = [B.Gel.from_workload(w, newton_tol=1e-7) for w in wls]
+    try:
+        for s in range(8):
+            poses = np.stack([w.poses[s] for w in wls])
+            st, sts = B.tx_batch_step(b, poses, np.full(3, wls[0].dt))
+            assert st == 0 and np.all(sts == 0)
+            for g, w in enumerate(wls):
+                assert alone[g].step(w.poses[s], w.dt) == 0
+                xb = B.tx_batch_state(b, g, len(w.gel.verts))[0]
+                xa = alone[g].state()[0]
+                assert np.abs(xb - xa).max() <= POS_TOL
+    finally:
+        B.tx_batch_destroy(b)
+
+
+def test_error_paths():
+    wl = W.small_gel_sphere(0)
+    bad = wl.gel.tets.copy()
+    bad[0, [2, 3]] = bad[0, [3, 2]]
+    with pytest.raises(B.TxError) as e:
+        B.Gel(B.GelDesc(wl.gel.verts, bad, wl.gel.dirichlet, wl.material, wl.indenter.verts, wl.indenter.tris, wl.pose0))
+    assert e.value.status == 3
+    bad = wl.gel.tets.copy()
+    bad[1, 1] = 99999
+    with pytest.raises(B.TxError) as e:
+        B.Gel(B.GelDesc(wl.gel.verts, bad, wl.gel.dirichlet, wl.material, wl.indenter.verts, wl.indenter.tris, wl.pose0))
+    assert e.value.status == 1
+    # indenter teleported deep into the gel: no split depth can make this feasible
+    gel = B.Gel.from_workload(wl)
+    deep = wl.pose0.copy()
+    deep[6] -= 3e-3
+    st = gel.step(deep, wl.dt)
+    assert st == 4
+    x, v, _, _ = gel.state()
+    assert np.array_equal(x, wl.gel.verts)  # transactional
+    assert gel.step(wl.poses[0], wl.dt) == 0
