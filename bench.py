@@ -1,0 +1,334 @@
+"""Benchmark: Newton-converged gel steps per second of the GB300 IPC gel step.
+
+Workload (default): the GelSight-Mini-scale gel -- 20x25x4 mm on a 41x51x9 vertex grid (18819
+vertices, 96000 tets, bottom face fixed), Neo-Hookean E = 0.3 MPa, nu = 0.45, rho = 1100, a
+seeded rigid indenter (sphere r in [2, 6] mm / cylinder r 2 mm x 10 mm / triangular prism side
+4 mm, 300-2000 triangles) pressed 1.0 mm over 60 steps then slid 2 mm over 60 steps at
+dt = 1/60 s, d_hat = 0.1 mm, kappa automatic, Newton tolerance 1e-5 (relative), FP64.
+
+One "step" is one implicit time step of one gel (all phases of the hot path: placement, broad
+phase, assembly, PCG, ACCD, line search, until Newton convergence).  Warm-up steps are the first
+W steps of the trajectory, the timed steps the next K.  Every timed step is bracketed by CUDA
+events on the library's stream; an L2 flush (256 MB write) separates timed steps outside the
+events.  Under torchrun each rank simulates its own gel (seed = rank): weak scaling, no
+collective on the data path.
+
+--impl reference times the CPU oracle (FP64, single thread) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="mini", choices=["mini", "small", "batch_mini", "batch_mixed"])
+    ap.add_argument("--n-gels", type=int, default=0, help="gels per batch (batch workloads)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def make_workload(kind, seed, n_gels=0):
+    """A list of workloads (one per gel of the handle)."""
+    from paper_2411_04776_gb300 import workloads as W
+    if kind == "small":
+        return [W.small_gel_sphere(seed)]
+    if kind == "batch_mini":  # config 3 geometry: n copies of the GelSight-Mini gel, own indenters
+        return [W.mini_gel(seed + g) for g in range(n_gels or 64)]
+    if kind == "batch_mixed":  # config 2: resolutions drawn from the three grids
+        return W.mixed_batch(n_gels or 256, seed0=seed)
+    return [W.mini_gel(seed)]
+
+
+NAMES = {"mini": "GelSight-Mini gel 41x51x9 (config 1)", "small": "small gel 10x13x4 (config 0)",
+         "batch_mini": "batch of GelSight-Mini gels 41x51x9 (config 3 geometry)",
+         "batch_mixed": "batch of gels with mixed resolutions (config 2)"}
+
+
+def workload_config(wls, kind, precision):
+    n_v = sum(len(w.gel.verts) for w in wls)
+    n_t = sum(len(w.gel.tets) for w in wls)
+    return {"workload": NAMES[kind], "gels": len(wls), "trajectory": wls[0].name if len(wls) == 1 else "per-gel seeded",
+            "verts": n_v, "tets": n_t, "indenter_tris": int(sum(len(w.indenter.tris) for w in wls)),
+            "dt": wls[0].dt, "dhat": wls[0].dhat, "newton_tol": wls[0].newton_tol, "precision": precision,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(",") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_peak_tflops(sm_mhz):
+    """GB300 FP64 (non-tensor) rate: the nominal 1.25 TFLOP/s at 152 SMs x 2.07 GHz is 4 FLOP
+    (2 DFMA) per SM per clock; scaled to the given SM clock."""
+    return 4.0 * 152 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2411_04776_gb300 import _build
+    from paper_2411_04776_gb300 import binding as B
+
+    if not _build.up_to_date():
+        _build.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    wls = make_workload(args.workload, args.seed + 1000 * rank, args.n_gels)
+    prec = B.TX_PREC_MIXED if args.precision == "mixed" else B.TX_PREC_FP64
+    K, Wm = args.steps, args.warmup
+    T = min(len(w.poses) for w in wls)
+    assert Wm + K <= T, f"the trajectories have {T} steps"
+    descs = [B.GelDesc.from_workload(w, precision=prec) for w in wls]
+    single = len(wls) == 1
+    if single:
+        gel = B.Gel(descs[0], stream=stream)
+        handle, prof_fn = gel.h, gel.profile
+    else:
+        handle = B.tx_batch_create(descs, stream=stream)
+        prof_fn = lambda on: B.tx_batch_profile(handle, on)  # noqa: E731
+    dts = np.array([w.dt for w in wls])
+
+    def step(s):
+        if single:
+            return gel.step(wls[0].poses[s], wls[0].dt)
+        st, sts = B.tx_batch_step(handle, np.stack([w.poses[s] for w in wls]), dts)
+        return st
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for s in range(Wm):
+        st = step(s)
+        assert st == 0, B.STATUS_NAMES[st]
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    prof_fn(True)
+    with ClockSampler(dev) as clk:
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            st = step(Wm + i)
+            ev[i][1].record(stream)
+            assert st == 0, B.STATUS_NAMES[st]
+            if single:
+                stats.append(gel.stats())
+        torch.cuda.synchronize()
+    prof = prof_fn(False)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_s = float(step_ms.sum()) / 1e3
+    clocks = clk.summary()
+    # ---- end to end through the public API with host buffers: poses in, positions out
+    n = sum(len(w.gel.verts) for w in wls)
+    if single:
+        gel.reset()
+        for s in range(Wm):
+            gel.step(wls[0].poses[s], wls[0].dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(K):
+            pose = np.ascontiguousarray(wls[0].poses[Wm + i])
+            st = B.tx_gel_step(gel.h, pose, wls[0].dt)
+            x, v, fc, _ = B.tx_gel_state(gel.h, n)
+            assert st == 0
+        e2e_s = time.perf_counter() - t0
+        gel.close()
+    else:
+        for g in range(len(wls)):
+            B.tx_batch_reset(handle, g)
+        for s in range(Wm):
+            step(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(K):
+            st = step(Wm + i)
+            assert st == 0
+            for g, w in enumerate(wls):
+                B.tx_batch_state(handle, g, len(w.gel.verts))
+        e2e_s = time.perf_counter() - t0
+        B.tx_batch_destroy(handle)
+    return dict(total_s=total_s, step_ms=step_ms, stats=stats, prof=prof, clocks=clocks, e2e_s=e2e_s,
+                n=n, wls=wls, h2d=len(wls) * (7 * 8 + 8), d2h=2 * n * 3 * 8 + len(wls) * (3 * 8 + 96))
+
+
+def roofline(prof, clocks):
+    phases = prof["phases"]
+    kernel_phases = ["tet_assemble", "gather", "contact_assemble", "precond", "pcg"]
+    top = max(kernel_phases, key=lambda k: phases[k]["ms"])
+    ph = phases[top]
+    avg_ms = ph["ms"] / max(ph["launches"], 1)
+    peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
+    achieved = (ph["flops"] / max(ph["launches"], 1)) / (avg_ms * 1e-3) / 1e12 if ph["flops"] else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            t = json.load(open(tpath)).get(top)
+            if t and t.get("source_hash") == source_hash():
+                traffic = t["bytes_per_launch"]
+        except (ValueError, KeyError):
+            traffic = None
+    return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "avg_launch_ms": avg_ms, "launches": ph["launches"],
+            "peak_note": "FP64 non-tensor: 4 FLOP/clk/SM x 152 SMs x max SM clock (nominal 1.25 TF derivation)"}
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2411_04776_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(args, budget=30.0):
+    """The oracle as it stands, single-threaded, on the first step(s) of the same trajectory
+    (first gel of a batch)."""
+    from oracle import oracle as O
+    wl = make_workload(args.workload, args.seed, 1)[0]
+    og = O.OracleGel.from_workload(wl)
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(wl.poses):
+        info = og.step(wl.poses[done], wl.dt)
+        assert info["status"] == 0
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle (FP64 C++, 1 thread) steps 0..{done - 1} of the same trajectory, {el:.1f} s"}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from oracle import oracle as O
+        O.build()
+        cb = cpu_baseline(args, budget=args.reference_budget)
+        wls = make_workload(args.workload, args.seed, args.n_gels)
+        line = {"metric": "gel Newton-converged steps/sec", "value": cb["value"], "unit": "steps/s",
+                "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": 0,
+                "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(wls, args.workload, "fp64"), "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = run_gpu(args, rank, world)
+    total_s, e2e_s = r["total_s"], r["e2e_s"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    K = args.steps
+    ng = len(r["wls"])
+    value = world * ng * K / total_s
+    step_ms = r["step_ms"]
+    prof = r["prof"]
+    line = {
+        "metric": "gel Newton-converged steps/sec", "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": workload_config(r["wls"], args.workload, args.precision),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "max": float(step_ms.max())},
+        "newton_iters_per_step": prof["newton_iters"] / (ng * K),
+        "pcg_iters_per_step": prof["pcg_iters"] / (ng * K),
+        "roofline": roofline(r["prof"], r["clocks"]),
+        "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
+        "gpu_launches": r["prof"]["kernel_launches"],
+        "clocks": r["clocks"],
+        "e2e": {"value": world * ng * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -185,6 +185,29 @@ tx_status tx_batch_set_state(tx_batch* b, int32_t gel, const double* x, const do
                              const double pose[7]);
 tx_status tx_batch_reset(tx_batch* b, int32_t gel);
 
+/* ---------------- per-phase device timing ----------------
+ * With profiling enabled the library brackets each phase of the step with CUDA events on the
+ * handle's stream and accumulates, per phase, the device time, the number of kernel launches and
+ * the algorithmic work the phase performed (FP64-equivalent flops, counted per unit as documented
+ * for each phase name).  tx_*_profile(h, enable, out): copies the counters accumulated since the
+ * previous call into `out` (may be NULL), resets them and sets profiling on (enable = 1) or off. */
+#define TX_PROFILE_MAX 12
+typedef struct tx_profile {
+  int32_t n_phases;
+  int32_t reserved;
+  const char* names[TX_PROFILE_MAX];
+  double ms[TX_PROFILE_MAX];        /* summed event time per phase                               */
+  int64_t launches[TX_PROFILE_MAX]; /* kernel launches per phase                                 */
+  double flops[TX_PROFILE_MAX];     /* algorithmic flops per phase (0 where not counted)         */
+  double bytes[TX_PROFILE_MAX];     /* algorithmic DRAM/L2 bytes per phase (0 where not counted) */
+  int64_t pcg_iters;                /* PCG iterations (summed over gels)                         */
+  int64_t newton_iters;             /* Newton iterations run (summed over gels)                  */
+  int64_t kernel_launches;          /* every kernel this library launched (all handles)          */
+} tx_profile;
+
+tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out);
+tx_status tx_gel_profile(tx_gel* g, int32_t enable, tx_profile* out);
+
 /* ---------------- unit-level kernels (device pointers, for parity checks and reuse) --------- */
 
 /* Per-tet elastic energy V Psi, gradient (12) and Hessian (144, row-major; PSD-projected in the

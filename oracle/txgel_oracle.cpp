@@ -35,7 +35,9 @@
 //   * ACCD: C-IPC's additive CCD with s = 0.1 (the gap may shrink to 10%), t_c = 1, thickness 0,
 //     over the pairs whose swept bounding boxes come within dhat of each other;
 //   * line search: alpha_0 = min(1, ACCD time of impact), halving until E(x + alpha p) <= E(x)
-//     with every tet keeping det F > 0 (a tet with det F <= 0 has E = +inf);
+//     with every tet keeping det F > 0 (a tet with det F <= 0 has E = +inf); if halving reaches
+//     alpha < 1e-12 alpha_0 and the model decrease -g.p is below 1e-10 |E| the iterate counts as
+//     converged (stationary to FP64 energy resolution), otherwise the step fails;
 //   * convergence: ||p||_inf / h < newton_tol * (rest bounding-box diagonal);
 //   * kinematic indenter: it is placed at the step's target pose before the solve; if its linear
 //     sweep from the previous pose against the gel at x_n has an ACCD hit (or any distance <= 0
@@ -1049,7 +1051,21 @@ int newton_solve(Gel& G, double h, const double* IW) {
       G.st_ls++;
       if (alpha < 1e-12 * a0) break;
     }
-    if (!accepted) return ERR_LINESEARCH;
+    if (!accepted) {
+      // READING: a direction whose model decrease -g.p is below 1e-10 |E| cannot be resolved by
+      // FP64 energy evaluations (barrier energies carry absolute noise from coordinate round-off);
+      // such an iterate is stationary to energy resolution and is taken as converged.
+      double gp = 0.0;
+      for (int i = 0; i < n3; ++i)
+        if (dof[i] >= 0) gp += grad[i] * p[i];
+      if (-gp <= 1e-10 * std::fabs(E)) {
+        G.st_energy = E;
+        G.st_pairs = ep.active;
+        G.st_min_d = ep.min_d;
+        return OK;
+      }
+      return ERR_LINESEARCH;
+    }
     x = xtrial;
     E = total(et);
     ep = et;

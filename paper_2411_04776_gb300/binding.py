@@ -58,6 +58,25 @@ class tx_step_stats(ctypes.Structure):
                 for k, _ in self._fields_}
 
 
+PROFILE_MAX = 12
+
+
+class tx_profile(ctypes.Structure):
+    _fields_ = [("n_phases", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("names", ctypes.c_char_p * PROFILE_MAX), ("ms", ctypes.c_double * PROFILE_MAX),
+                ("launches", ctypes.c_int64 * PROFILE_MAX), ("flops", ctypes.c_double * PROFILE_MAX),
+                ("bytes", ctypes.c_double * PROFILE_MAX), ("pcg_iters", ctypes.c_int64),
+                ("newton_iters", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        phases = {}
+        for k in range(self.n_phases):
+            phases[self.names[k].decode()] = dict(ms=self.ms[k], launches=int(self.launches[k]),
+                                                  flops=self.flops[k], bytes=self.bytes[k])
+        return dict(phases=phases, pcg_iters=int(self.pcg_iters), newton_iters=int(self.newton_iters),
+                    kernel_launches=int(self.kernel_launches))
+
+
 class TxError(RuntimeError):
     def __init__(self, status, where=""):
         msg = f"{where}: {STATUS_NAMES.get(status, status)}"
@@ -98,6 +117,8 @@ _SIGS = [
                                       ctypes.POINTER(tx_step_stats)]),
     ("tx_batch_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_dp, c_dp, c_dp]),
     ("tx_batch_reset", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("tx_batch_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(tx_profile)]),
+    ("tx_gel_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(tx_profile)]),
     ("tx_eval_tets", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -344,6 +365,19 @@ def tx_batch_reset(b, gel):
     _check(load().tx_batch_reset(b, int(gel)), "tx_batch_reset")
 
 
+def tx_gel_profile(g, enable=True):
+    """Returns the per-phase counters since the previous call and sets profiling on/off."""
+    p = tx_profile()
+    _check(load().tx_gel_profile(g, int(enable), ctypes.byref(p)), "tx_gel_profile")
+    return p.as_dict()
+
+
+def tx_batch_profile(b, enable=True):
+    p = tx_profile()
+    _check(load().tx_batch_profile(b, int(enable), ctypes.byref(p)), "tx_batch_profile")
+    return p.as_dict()
+
+
 def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
@@ -415,6 +449,9 @@ class Gel:
 
     def reset(self):
         tx_gel_reset(self.h)
+
+    def profile(self, enable=True):
+        return tx_gel_profile(self.h, enable)
 
     def energy(self, x, xt, h, pose):
         return tx_gel_energy(self.h, x, xt, h, pose)

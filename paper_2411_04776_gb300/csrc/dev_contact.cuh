@@ -294,56 +294,135 @@ __device__ __forceinline__ void barrier_D(double D, double dhat, double* b, doub
   *bDD = (b2 - b1 / d) / (4.0 * D);
 }
 
-// Symmetric eigen-decomposition (cyclic Jacobi) of an n x n matrix (n <= 9) and clamp of the
-// negative eigenvalues: A <- V max(w, 0) V^T.
+// PSD projection of a symmetric n x n block (n <= 9): A <- V max(w, 0) V^T.
+// GB300 issues FP64 at 1/64 of the FP32 rate, so the eigenbasis is found in two precisions:
+//   1. cyclic Jacobi in FP32 gives an approximate eigenbasis Q (orthonormal to ~1e-7);
+//   2. in FP64, Q is re-orthonormalised (modified Gram-Schmidt, two passes), so B = Q^T A Q is a
+//      similarity, diagonal up to ~1e-7; one FP64 Jacobi sweep (plus a second if needed)
+//      diagonalises it to FP64 accuracy, W;
+//   3. V = Q W, w = diag(B), and the clamp is assembled in FP64.
+// The result equals the FP64 eigen-clamp of A to FP64 round-off of the refinement.
 static __device__ __noinline__ void psd_clamp(int n, double* A) {
-  double V[81];
+  float a32[81], q32[81];
+  for (int i = 0; i < n * n; ++i) a32[i] = (float)A[i];
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, dg = 0.0;
+    for (int j = 0; j < n; ++j) q32[i * n + j] = (i == j) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    float off = 0.f, dg = 0.f;
     for (int i = 0; i < n; ++i) {
-      dg += A[i * n + i] * A[i * n + i];
-      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+      dg += a32[i * n + i] * a32[i * n + i];
+      for (int j = i + 1; j < n; ++j) off += a32[i * n + j] * a32[i * n + j];
     }
-    if (!(off > 1e-30 * dg)) break;
+    if (!(off > 1e-13f * dg)) break;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p * n + q];
-        if (apq == 0.0) continue;
-        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = rsqrt(t * t + 1.0), s = t * c;
-        A[p * n + p] -= t * apq;
-        A[q * n + q] += t * apq;
-        A[p * n + q] = A[q * n + p] = 0.0;
+        const float apq = a32[p * n + q];
+        if (fabsf(apq) <= 1e-9f * (fabsf(a32[p * n + p]) + fabsf(a32[q * n + q]))) continue;
+        const float th = (a32[q * n + q] - a32[p * n + p]) / (2.f * apq);
+        const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+        const float c = rsqrtf(t * t + 1.f), s = t * c;
+        a32[p * n + p] -= t * apq;
+        a32[q * n + q] += t * apq;
+        a32[p * n + q] = a32[q * n + p] = 0.f;
         for (int r = 0; r < n; ++r) {
           if (r == p || r == q) continue;
-          const double arp = A[r * n + p], arq = A[r * n + q];
-          A[r * n + p] = A[p * n + r] = c * arp - s * arq;
-          A[r * n + q] = A[q * n + r] = s * arp + c * arq;
+          const float arp = a32[r * n + p], arq = a32[r * n + q];
+          a32[r * n + p] = a32[p * n + r] = c * arp - s * arq;
+          a32[r * n + q] = a32[q * n + r] = s * arp + c * arq;
         }
         for (int k = 0; k < n; ++k) {
-          const double vkp = V[k * n + p], vkq = V[k * n + q];
-          V[k * n + p] = c * vkp - s * vkq;
-          V[k * n + q] = s * vkp + c * vkq;
+          const float vkp = q32[k * n + p], vkq = q32[k * n + q];
+          q32[k * n + p] = c * vkp - s * vkq;
+          q32[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  // FP64: orthonormal Q (columns), then B = Q^T A Q
+  double Q[81], T[81], B[81];
+  for (int i = 0; i < n * n; ++i) Q[i] = (double)q32[i];
+  for (int pass = 0; pass < 2; ++pass)
+    for (int j = 0; j < n; ++j) {
+      for (int k = 0; k < j; ++k) {
+        double dp = 0.0;
+        for (int i = 0; i < n; ++i) dp = fma(Q[i * n + k], Q[i * n + j], dp);
+        for (int i = 0; i < n; ++i) Q[i * n + j] = fma(-dp, Q[i * n + k], Q[i * n + j]);
+      }
+      double nn = 0.0;
+      for (int i = 0; i < n; ++i) nn = fma(Q[i * n + j], Q[i * n + j], nn);
+      const double inv = rsqrt(nn);
+      for (int i = 0; i < n; ++i) Q[i * n + j] *= inv;
+    }
+  for (int i = 0; i < n; ++i)  // T = A Q
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc = fma(A[i * n + k], Q[k * n + j], acc);
+      T[i * n + j] = acc;
+    }
+  for (int i = 0; i < n; ++i)  // B = Q^T T (upper triangle, mirrored)
+    for (int j = i; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc = fma(Q[k * n + i], T[k * n + j], acc);
+      B[i * n + j] = B[j * n + i] = acc;
+    }
+  // FP64 refinement sweeps on the nearly diagonal B, accumulating into Q
+  for (int sweep = 0; sweep < 4; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dg += B[i * n + i] * B[i * n + i];
+      for (int j = i + 1; j < n; ++j) off += B[i * n + j] * B[i * n + j];
+    }
+    if (!(off > 1e-28 * dg)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double bpq = B[p * n + q];
+        if (fabs(bpq) <= 1e-18 * (fabs(B[p * n + p]) + fabs(B[q * n + q]))) continue;
+        const double th = (B[q * n + q] - B[p * n + p]) / (2.0 * bpq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = rsqrt(t * t + 1.0), s = t * c;
+        B[p * n + p] -= t * bpq;
+        B[q * n + q] += t * bpq;
+        B[p * n + q] = B[q * n + p] = 0.0;
+        for (int r = 0; r < n; ++r) {
+          if (r == p || r == q) continue;
+          const double brp = B[r * n + p], brq = B[r * n + q];
+          B[r * n + p] = B[p * n + r] = c * brp - s * brq;
+          B[r * n + q] = B[q * n + r] = s * brp + c * brq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = Q[k * n + p], vkq = Q[k * n + q];
+          Q[k * n + p] = c * vkp - s * vkq;
+          Q[k * n + q] = s * vkp + c * vkq;
         }
       }
   }
   double w[9];
-  for (int i = 0; i < n; ++i) w[i] = fmax(A[i * n + i], 0.0);
+  for (int i = 0; i < n; ++i) w[i] = fmax(B[i * n + i], 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = i; j < n; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < n; ++k) s += V[i * n + k] * w[k] * V[j * n + k];
-      A[i * n + j] = A[j * n + i] = s;
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc = fma(Q[i * n + k] * w[k], Q[j * n + k], acc);
+      A[i * n + j] = A[j * n + i] = acc;
     }
+}
+
+// Projected barrier block of a pair with a single free point: the barrier depends on that point
+// only through d, so its Hessian is b''(d) u u^T + b'(d) grad^2 d with u = grad d; grad^2 d is
+// PSD-orthogonal to u and b' < 0, so the PSD projection keeps b''(d) u u^T (b'' > 0 inside
+// dhat).  H3 = kappa-free 3x3 block, from gD = grad of D = d^2 restricted to the point.
+__device__ __forceinline__ void single_point_block(double bpp, const double gD[3], double H3[9]) {
+  const double n2 = gD[0] * gD[0] + gD[1] * gD[1] + gD[2] * gD[2];
+  const double k = n2 > 0.0 ? fmax(bpp, 0.0) / n2 : 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) H3[3 * i + j] = k * gD[i] * gD[j];
 }
 
 // Barrier of one pair (kind 0: point-triangle, 1: edge-edge with mollifier threshold eps_x):
 // value, gradient (12) and Hessian (144) in point space.  Returns false when d >= dhat.
+// Optional outputs: the points the value depends on (bit mask), b''(d) and grad D (12).
 static __device__ __noinline__ bool pair_barrier_derivs(int kind, const double P[4][3], double dhat, double eps_x,
-                                                 double* bv, double g[12], double H[144], DType* tyo) {
+                                                        double* bv, double g[12], double H[144], DType* tyo,
+                                                        int* involved = nullptr, double* bpp = nullptr,
+                                                        double* gDo = nullptr) {
   DType ty;
   const double D0 = pair_d2(kind, P, &ty);
   if (tyo) *tyo = ty;
@@ -352,6 +431,18 @@ static __device__ __noinline__ bool pair_barrier_derivs(int kind, const double P
   const double D = dist_derivs(ty, P, gD, HD);
   double b, bD, bDD;
   barrier_D(D, dhat, &b, &bD, &bDD);
+  if (involved) {
+    const int np = ty.f == DF_PP ? 2 : (ty.f == DF_PE ? 3 : 4);
+    int m = 0;
+    for (int k = 0; k < np; ++k) m |= 1 << ty.i[k];
+    *involved = m;
+  }
+  if (bpp) {
+    const double d = sqrt(D), r = d - dhat;
+    *bpp = -2.0 * log(d / dhat) - 4.0 * r / d + r * r / (d * d);
+  }
+  if (gDo)
+    for (int k = 0; k < 12; ++k) gDo[k] = gD[k];
   for (int a = 0; a < 12; ++a) g[a] = bD * gD[a];
   for (int a = 0; a < 12; ++a)
     for (int c = 0; c < 12; ++c) H[a * 12 + c] = bDD * gD[a] * gD[c] + bD * HD[a * 12 + c];
@@ -362,6 +453,7 @@ static __device__ __noinline__ bool pair_barrier_derivs(int kind, const double P
     double gc6[6] = {0}, Hc6[36] = {0};
     const double c = crossnorm_acc(ea, eb, 6, 0, 3, gc6, Hc6);
     if (c < eps_x) {
+      if (involved) *involved = 0xF;  // the mollifier couples all four points
       const double q = c / eps_x;
       const double m = (2.0 - q) * q;
       const double m1 = 2.0 * (1.0 - q) / eps_x;

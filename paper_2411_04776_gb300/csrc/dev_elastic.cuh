@@ -27,8 +27,8 @@ template <typename R>
 __device__ __forceinline__ void jacobi3(R a[3][3], R w[3], R V[3][3]) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? R(1) : R(0);
-  const R tiny = sizeof(R) == 8 ? R(1e-30) : R(1e-13);
-  for (int sweep = 0; sweep < 12; ++sweep) {
+  const R tiny = sizeof(R) == 8 ? R(1e-26) : R(1e-12);
+  for (int sweep = 0; sweep < 10; ++sweep) {
     R off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
     R dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
     if (!(off > tiny * dg)) break;

@@ -150,6 +150,21 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
       for (int iy = y0; iy <= y1; ++iy)
         for (int ix = x0; ix <= x1; ++ix) atomicAdd(&cnt[hash_cell(ix, iy, iz) & (nb - 1)], 1);
   }
+  if (tab == 1 && threadIdx.x == 0) {  // the indenter's bounding box (all its vertices)
+    Box all;
+    box_init(all);
+    for (int k = 0; k < n; ++k) {
+      const Box bx = ind_box(d, 1, p0 + k, swept != 0);
+      for (int c = 0; c < 3; ++c) {
+        all.lo[c] = fmin(all.lo[c], bx.lo[c]);
+        all.hi[c] = fmax(all.hi[c], bx.hi[c]);
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      d.gv[g].ibox_lo[c] = all.lo[c];
+      d.gv[g].ibox_hi[c] = all.hi[c];
+    }
+  }
   __syncthreads();
   if (s_brute) {  // oversized primitive: every query of this table tests all primitives directly
     for (int b = threadIdx.x; b <= nb; b += blockDim.x) start[b] = 0;
@@ -236,6 +251,17 @@ __global__ void k_query(Dev d, int phase, int mode) {
   const int tab = type;
   const Box qb = gel_box(d, type, gk, gsw);
   const double pad = G.dhat, ic = 1.0 / G.cell;
+  {
+    Box ib;
+    for (int c = 0; c < 3; ++c) {
+      ib.lo[c] = d.gv[g].ibox_lo[c];
+      ib.hi[c] = d.gv[g].ibox_hi[c];
+    }
+    if (!near_boxes(qb, ib, pad)) {  // nowhere near the indenter
+      if (!write) d.qcount[q] = 0;
+      return;
+    }
+  }
   int lo[3], hi[3];
   for (int c = 0; c < 3; ++c) {
     lo[c] = cell_of(qb.lo[c] - pad, G.org[c], ic);
@@ -327,19 +353,28 @@ __global__ void __launch_bounds__(128) k_contact_assemble(Dev d, int phase) {
   int rows[4];
   pair_points(d, pr, 0.0, false, P, rows);
   const int kind = pr.x == PAIR_EE ? 1 : 0;
-  double b, gr[12], H[144];
-  if (!pair_barrier_derivs(kind, P, G.dhat, pair_eps_x(d, pr), &b, gr, H, nullptr)) return;
+  double b, gr[12], H[144], bpp, gD[12];
+  int inv = 0;
+  if (!pair_barrier_derivs(kind, P, G.dhat, pair_eps_x(d, pr), &b, gr, H, nullptr, &inv, &bpp, gD)) return;
   atomicAdd(&d.gv[g].active_pairs, 1);
   const double kap = G.kappa;
+  // gel points the barrier depends on; all other rows/columns of the block are zero
   int slots[4], ns = 0;
   for (int k = 0; k < 4; ++k)
-    if (rows[k] >= 0) slots[ns++] = k;
+    if (rows[k] >= 0 && (inv >> k) & 1) slots[ns++] = k;
   const int nf = 3 * ns;
   double Hf[81];
-  for (int a = 0; a < nf; ++a)
-    for (int c = 0; c < nf; ++c)
-      Hf[a * nf + c] = kap * H[(3 * slots[a / 3] + a % 3) * 12 + 3 * slots[c / 3] + c % 3];
-  psd_clamp(nf, Hf);
+  if (ns == 1) {
+    // one free point: closed-form projection kappa b''(d) u u^T
+    double H3[9];
+    single_point_block(bpp, gD + 3 * slots[0], H3);
+    for (int e = 0; e < 9; ++e) Hf[e] = kap * H3[e];
+  } else if (ns > 1) {
+    for (int a = 0; a < nf; ++a)
+      for (int c = 0; c < nf; ++c)
+        Hf[a * nf + c] = kap * H[(3 * slots[a / 3] + a % 3) * 12 + 3 * slots[c / 3] + c % 3];
+    psd_clamp(nf, Hf);
+  }
   for (int a = 0; a < ns; ++a) {
     const int ra = rows[slots[a]];
     for (int c = 0; c < 3; ++c) atomicAdd(&d.gv[g].fc[c], -kap * gr[3 * slots[a] + c]);
@@ -476,16 +511,24 @@ __global__ void k_eval_accd(int n, const int* kind, const double* Pin, const dou
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t st) {
-  if (n_ind_verts > 0) k_indenter_pose<<<nblk(n_ind_verts, 128), 128, 0, st>>>(d, phase);
+  if (n_ind_verts > 0) {
+    k_indenter_pose<<<nblk(n_ind_verts, 128), 128, 0, st>>>(d, phase);
+    count_launch(1);
+  }
 }
 void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st) {
   k_hash_build<<<d.n_gels * NTAB, HB_THREADS, 0, st>>>(d, phase, swept);
+  count_launch(1);
 }
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st) {
-  if (d.nq > 0) k_query<<<nblk(d.nq, 128), 128, 0, st>>>(d, phase, mode);
+  if (d.nq > 0) {
+    k_query<<<nblk(d.nq, 128), 128, 0, st>>>(d, phase, mode);
+    count_launch(1);
+  }
 }
 void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st) {
   k_pair_ranges<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, skip_conv);
+  count_launch(1);
 }
 void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   if (d.npslots <= 0) return;
@@ -493,20 +536,33 @@ void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t s
     k_contact_assemble<true><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
   else
     k_contact_assemble<false><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+  count_launch(1);
 }
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st) {
-  if (d.npslots > 0) k_accd<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode, maxit);
+  if (d.npslots > 0) {
+    k_accd<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode, maxit);
+    count_launch(1);
+  }
 }
 void launch_min_dist(const Dev& d, int phase, cudaStream_t st) {
-  if (d.npslots > 0) k_min_dist<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+  if (d.npslots > 0) {
+    k_min_dist<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+    count_launch(1);
+  }
 }
 void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
                        const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st) {
-  if (n > 0) k_eval_pairs<<<nblk(n, 64), 64, 0, st>>>(n, kind, P, dhat, eps_x, free_mask, b, g, H, dtype);
+  if (n > 0) {
+    k_eval_pairs<<<nblk(n, 64), 64, 0, st>>>(n, kind, P, dhat, eps_x, free_mask, b, g, H, dtype);
+    count_launch(1);
+  }
 }
 void launch_eval_accd(int n, const int* kind, const double* P, const double* dP, double s, double tc,
                       int maxit, double* toi, int* hit, cudaStream_t st) {
-  if (n > 0) k_eval_accd<<<nblk(n, 128), 128, 0, st>>>(n, kind, P, dP, s, tc, maxit, toi, hit);
+  if (n > 0) {
+    k_eval_accd<<<nblk(n, 128), 128, 0, st>>>(n, kind, P, dP, s, tc, maxit, toi, hit);
+    count_launch(1);
+  }
 }
 
 }  // namespace txg

@@ -44,6 +44,7 @@ void launch_tet_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
     k_tet_assemble<true><<<nb, 128, 0, st>>>(d, phase);
   else
     k_tet_assemble<false><<<nb, 128, 0, st>>>(d, phase);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------- unit-level entry
@@ -103,6 +104,7 @@ void launch_eval_tets(int n, const double* X, const double* x, double mu, double
                       double* e, double* g, double* H, cudaStream_t st) {
   if (n <= 0) return;
   k_eval_tets<<<(n + 127) / 128, 128, 0, st>>>(n, X, x, mu, lam, project, e, g, H);
+  count_launch(1);
 }
 
 }  // namespace txg

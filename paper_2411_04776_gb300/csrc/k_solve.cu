@@ -75,8 +75,11 @@ void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
     return;
   }
   k_scan_blocks<<<nb, SCAN_T, 0, st>>>(in, out, tmp, n);
+  count_launch(1);
   k_scan_sums<<<1, SCAN_T, 0, st>>>(tmp, nb, tmp + nb);
+  count_launch(1);
   k_scan_add<<<nb, SCAN_T, 0, st>>>(out, tmp, n, tmp + nb, out + n);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------- gather (assembly)
@@ -154,6 +157,7 @@ void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st
     k_gather<true><<<nblk(nbp, 256), 256, 0, st>>>(d, phase, nbp);
   else
     k_gather<false><<<nblk(nbp, 256), 256, 0, st>>>(d, phase, nbp);
+  count_launch(1);
 }
 
 // block-Jacobi preconditioner: inverse of every free row's 3x3 diagonal block
@@ -195,6 +199,7 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
     k_precond<true><<<nblk(d.nrows, 128), 128, 0, st>>>(d, phase);
   else
     k_precond<false><<<nblk(d.nrows, 128), 128, 0, st>>>(d, phase);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------- persistent PCG
@@ -203,95 +208,141 @@ constexpr int PCG_MAXG = 64; // gels one CTA may touch
 
 
 __device__ __forceinline__ double4_32a mul3(const double* M, const double4_32a v) {
-  return make_double4_32a(M[0] * v.x + M[1] * v.y + M[2] * v.z, M[3] * v.x + M[4] * v.y + M[5] * v.z,
-                      M[6] * v.x + M[7] * v.y + M[8] * v.z, 0.0);
+  return make_double4_32a(fma(M[2], v.z, fma(M[1], v.y, M[0] * v.x)), fma(M[5], v.z, fma(M[4], v.y, M[3] * v.x)),
+                          fma(M[8], v.z, fma(M[7], v.y, M[6] * v.x)), 0.0);
 }
-__device__ __forceinline__ double dot4(const double4_32a a, const double4_32a b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-// totals of the per-slice partials of gel g (arrays part + k*ns), fixed order, whole CTA
-__device__ __forceinline__ void gel_totals(const Dev& d, int g, int nk, double* out, double* sm) {
-  const GelInfo& G = d.gi[g];
-  for (int k = 0; k < nk; ++k) {
-    const double* p = d.part + (size_t)k * d.nslices + G.s0;
-    double v = 0.0;
-    for (int s = threadIdx.x; s < G.ns; s += PCG_T) v += p[s];
-    v = block_sum<PCG_T>(v, sm);
-    if (threadIdx.x == 0) out[k] = v;
-  }
-  __syncthreads();
+__device__ __forceinline__ double dot4(const double4_32a a, const double4_32a b) {
+  return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x));
 }
 
-// SpMV of one slice (row = lane of the warp): y = A u, FP64
+// SpMV of one slice (row = lane of the warp): y = A u, FP64.  Unrolled so that several block
+// loads (column index, 9 values, gathered vector) are in flight at once.
 __device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane, const double4_32a* u) {
   const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
   for (int k = 0; k < w; ++k) {
     const int bp = o + 32 * k + lane;
-    const int c = d.colidx[bp];
+    const int c = __ldg(d.colidx + bp);
     const double4_32a uc = u[c];
     const double* v = d.vals + (size_t)9 * (o + 32 * k) + lane;
-    a0 += v[0] * uc.x + v[32] * uc.y + v[64] * uc.z;
-    a1 += v[96] * uc.x + v[128] * uc.y + v[160] * uc.z;
-    a2 += v[192] * uc.x + v[224] * uc.y + v[256] * uc.z;
+    a0 = fma(v[0], uc.x, a0);
+    a1 = fma(v[96], uc.x, a1);
+    a2 = fma(v[192], uc.x, a2);
+    a0 = fma(v[32], uc.y, a0);
+    a1 = fma(v[128], uc.y, a1);
+    a2 = fma(v[224], uc.y, a2);
+    a0 = fma(v[64], uc.z, a0);
+    a1 = fma(v[160], uc.z, a1);
+    a2 = fma(v[256], uc.z, a2);
   }
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
+// Reduction slots: slice partials of one CTA (dynamic shared memory, 4 per slice) are summed per
+// gel the CTA touches into one slot per (CTA, gel); the slots of a gel are contiguous, so every
+// CTA forms a gel's total by summing that short range.  Both sums run one warp per (gel, quantity)
+// with a fixed lane assignment: bitwise identical in every CTA and run.
+__device__ __forceinline__ void cta_reduce(const Dev& d, const PcgPlan& plan, const double* dsm, int s0,
+                                           int s1, int g0, int ng, int slot0, int k0, int k1) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nk = k1 - k0;
+  for (int t = wid; t < ng * nk; t += PCG_T / 32) {
+    const int j = t / nk, k = k0 + t % nk;
+    const GelInfo& G = d.gi[g0 + j];
+    const int a = max(s0, G.s0), b = min(s1, G.s0 + G.ns);
+    double v = 0.0;
+    for (int s = a + lane; s < b; s += 32) v += dsm[(s - s0) * 4 + k];
+    v = warp_sum(v);
+    if (lane == 0) d.part[(size_t)k * plan.nslots + slot0 + j] = v;
+  }
+}
+
+__device__ __forceinline__ void gel_totals(const Dev& d, const PcgPlan& plan, int g0, int ng, int nk,
+                                           double (*tot)[4]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = wid; t < ng * nk; t += PCG_T / 32) {
+    const int j = t / nk, k = t % nk;
+    const int a = plan.gel_slot[2 * (g0 + j)], b = plan.gel_slot[2 * (g0 + j) + 1];
+    double v = 0.0;
+    for (int q = a + lane; q < b; q += 32) v += d.part[(size_t)k * plan.nslots + q];
+    v = warp_sum(v);
+    if (lane == 0) tot[j][k] = v;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, double eta2, int maxit) {
-  __shared__ double sm[PCG_T / 32];
+  extern __shared__ double dsm[];  // [slices of this CTA][4]
   __shared__ double tot[PCG_MAXG][4];
+  __shared__ double bbj[PCG_MAXG];
   __shared__ int s_exit;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int s0 = plan.cta_s0[blockIdx.x], s1 = plan.cta_s0[blockIdx.x + 1];
   const int g0 = plan.cta_g0[blockIdx.x], ng = plan.cta_ng[blockIdx.x];
-  const int ns = d.nslices;
-  double* part = d.part;
+  const int slot0 = plan.cta_slot0[blockIdx.x];
   unsigned epoch = 0;
   // ---- init: r = -grad, x = 0, u = M^-1 r, pp = s = 0; partial |b|^2
   for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
     const int g = plan.slice_gel[s];
-    if (d.gc[g].phase != phase) continue;
-    const int r = 32 * s + lane;
-    const double4_32a gr = d.grad[r];
-    const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    d.r[r] = b;
-    d.p[r] = z;
-    d.pp[r] = z;
-    d.s[r] = z;
-    d.u[r] = mul3(d.Minv + 9 * r, b);
-    const double bb = warp_sum(dot4(b, b));
-    if (lane == 0) part[3 * (size_t)ns + s] = bb;
+    double bb = 0.0;
+    if (d.gc[g].phase == phase) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      d.r[r] = b;
+      d.p[r] = z;
+      d.pp[r] = z;
+      d.s[r] = z;
+      d.u[r] = mul3(d.Minv + 9 * r, b);
+      bb = dot4(b, b);
+    }
+    bb = warp_sum(bb);
+    if (lane == 0) dsm[(s - s0) * 4 + 3] = bb;
   }
+  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 3, 4);
   if (!grid_barrier(d.bar, epoch, d.err)) return;
   int k = 0;
   while (true) {
     // ---- Y: w = A u, partials gamma = (r,u), delta = (w,u), rr = (r,r)
     for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
       const int g = plan.slice_gel[s];
-      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
-      const int r = 32 * s + lane;
-      double4_32a w = spmv_row64(d, s, lane, d.u);
-      if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-      d.w[r] = w;
-      const double4_32a rv = d.r[r], uv = d.u[r];
-      const double ga = warp_sum(dot4(rv, uv)), de = warp_sum(dot4(w, uv)), rr = warp_sum(dot4(rv, rv));
+      double ga = 0.0, de = 0.0, rr = 0.0;
+      if (d.gc[g].phase == phase && !d.gv[g].pcg_done) {
+        const int r = 32 * s + lane;
+        double4_32a w = spmv_row64(d, s, lane, d.u);
+        if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.w[r] = w;
+        const double4_32a rv = d.r[r], uv = d.u[r];
+        ga = dot4(rv, uv);
+        de = dot4(w, uv);
+        rr = dot4(rv, rv);
+      }
+      ga = warp_sum(ga);
+      de = warp_sum(de);
+      rr = warp_sum(rr);
       if (lane == 0) {
-        part[s] = ga;
-        part[(size_t)ns + s] = de;
-        part[2 * (size_t)ns + s] = rr;
+        dsm[(s - s0) * 4 + 0] = ga;
+        dsm[(s - s0) * 4 + 1] = de;
+        dsm[(s - s0) * 4 + 2] = rr;
       }
     }
+    cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 3);
     if (blockIdx.x == 0 && threadIdx.x == 0) d.act[(k + 1) & 1] = 0;
     if (!grid_barrier(d.bar, epoch, d.err)) return;
     k += 1;
     // ---- X: per-gel scalars, convergence, vector updates
-    for (int j = 0; j < ng; ++j) gel_totals(d, g0 + j, 4, tot[j], sm);
+    gel_totals(d, plan, g0, ng, k == 1 ? 4 : 3, tot);
+    if (k == 1) {
+      for (int j = threadIdx.x; j < ng; j += PCG_T) bbj[j] = tot[j][3];
+      __syncthreads();
+    }
     int my_active = 0;
     for (int j = 0; j < ng; ++j) {
       const int g = g0 + j;
       if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
-      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2], bb = tot[j][3];
+      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2], bb = bbj[j];
       const bool conv = !(rr > eta2 * bb) || k > maxit;
       if (conv) {
         // every CTA touching g reaches the same decision in this iteration
@@ -341,6 +392,21 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     __syncthreads();
     if (s_exit) break;
   }
+  // ---- g . p per gel (stationarity test of the line search)
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    double gp = 0.0;
+    if (d.gc[g].phase == phase) gp = dot4(d.grad[32 * s + lane], d.p[32 * s + lane]);
+    gp = warp_sum(gp);
+    if (lane == 0) dsm[(s - s0) * 4 + 0] = gp;
+  }
+  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 1);
+  if (!grid_barrier(d.bar, epoch, d.err)) return;
+  gel_totals(d, plan, g0, ng, 1, tot);
+  for (int j = threadIdx.x; j < ng; j += PCG_T) {
+    const GelInfo& G = d.gi[g0 + j];
+    if (s0 <= G.s0 && G.s0 < s1) d.gv[g0 + j].gtp = tot[j][0];
+  }
   // ---- ||p||_inf per gel
   for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
     const int g = plan.slice_gel[s];
@@ -357,13 +423,312 @@ cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas
   Dev dd = d;
   PcgPlan pp = plan;
   void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, 0, st);
+  count_launch(1);
+  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, smem, st);
 }
 
-int pcg_max_ctas_per_sm() {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64, PCG_T, 0);
-  return nb;
+
+
+// ---------------------------------------------------------------- mixed-precision PCG
+// Mixed precision Newton direction: the Hessian is stored in FP32 (elastic blocks computed in
+// FP32, barrier blocks rounded from FP64); the direction p solves H p = -g by iterative
+// refinement: in every round the FP64 residual r = -g - H p (FP32 values, FP64 vectors and
+// accumulation) is formed, then H d = r is solved by the same block-Jacobi CG in FP32 to the
+// FP32 accuracy limit, and p += d in FP64.  Rounds stop once |r| <= eta |g| (FP64 residual).
+
+__device__ __forceinline__ float4 mul3f(const float* M, const float4 v) {
+  return make_float4(fmaf(M[2], v.z, fmaf(M[1], v.y, M[0] * v.x)), fmaf(M[5], v.z, fmaf(M[4], v.y, M[3] * v.x)),
+                     fmaf(M[8], v.z, fmaf(M[7], v.y, M[6] * v.x)), 0.f);
+}
+__device__ __forceinline__ float dot4f(const float4 a, const float4 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
+
+// y = A32 u32 (FP32)
+__device__ __forceinline__ float4 spmv_row32(const Dev& d, int s, int lane, const float4* u) {
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    const int c = __ldg(d.colidx + bp);
+    const float4 uc = u[c];
+    const float* v = d.vals32 + (size_t)9 * (o + 32 * k) + lane;
+    a0 = fmaf(v[0], uc.x, a0);
+    a1 = fmaf(v[96], uc.x, a1);
+    a2 = fmaf(v[192], uc.x, a2);
+    a0 = fmaf(v[32], uc.y, a0);
+    a1 = fmaf(v[128], uc.y, a1);
+    a2 = fmaf(v[224], uc.y, a2);
+    a0 = fmaf(v[64], uc.z, a0);
+    a1 = fmaf(v[160], uc.z, a1);
+    a2 = fmaf(v[256], uc.z, a2);
+  }
+  return make_float4(a0, a1, a2, 0.f);
+}
+
+// y = A32 x64 with FP64 products and accumulation
+__device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lane, const double4_32a* x) {
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    const int c = __ldg(d.colidx + bp);
+    const double4_32a xc = x[c];
+    const float* v = d.vals32 + (size_t)9 * (o + 32 * k) + lane;
+    a0 = fma((double)v[0], xc.x, a0);
+    a1 = fma((double)v[96], xc.x, a1);
+    a2 = fma((double)v[192], xc.x, a2);
+    a0 = fma((double)v[32], xc.y, a0);
+    a1 = fma((double)v[128], xc.y, a1);
+    a2 = fma((double)v[224], xc.y, a2);
+    a0 = fma((double)v[64], xc.z, a0);
+    a1 = fma((double)v[160], xc.z, a1);
+    a2 = fma((double)v[256], xc.z, a2);
+  }
+  return make_double4_32a(a0, a1, a2, 0.0);
+}
+
+__global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
+                                                     int refine_max) {
+  extern __shared__ double dsm[];
+  __shared__ double tot[PCG_MAXG][4];
+  __shared__ double bbj[PCG_MAXG];
+  __shared__ double tolj[PCG_MAXG];
+  __shared__ int s_exit;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s0 = plan.cta_s0[blockIdx.x], s1 = plan.cta_s0[blockIdx.x + 1];
+  const int g0 = plan.cta_g0[blockIdx.x], ng = plan.cta_ng[blockIdx.x];
+  const int slot0 = plan.cta_slot0[blockIdx.x];
+  unsigned epoch = 0;
+  int kk = 0;  // global inner-iteration parity counter (for the act[] double buffer and gsc)
+  // ---- init: r64 = b = -grad, p = 0; partials |b|^2 (k = 3) and |r|^2 (k = 2)
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    double bb = 0.0;
+    if (d.gc[g].phase == phase) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      d.r[r] = b;
+      d.p[r] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      bb = dot4(b, b);
+    }
+    bb = warp_sum(bb);
+    if (lane == 0) {
+      dsm[(s - s0) * 4 + 3] = bb;
+      dsm[(s - s0) * 4 + 2] = bb;
+    }
+  }
+  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 2, 4);
+  if (!grid_barrier(d.bar, epoch, d.err)) return;
+  for (int round = 0;; ++round) {
+    // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
+    gel_totals(d, plan, g0, ng, round == 0 ? 4 : 3, tot);
+    if (round == 0) {
+      for (int j = threadIdx.x; j < ng; j += PCG_T) bbj[j] = tot[j][3];
+      __syncthreads();
+    }
+    int my_active = 0;
+    for (int j = 0; j < ng; ++j) {
+      const int g = g0 + j;
+      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+      const double rr = tot[j][2], bb = bbj[j];
+      if (!(rr > eta2 * bb) || round >= refine_max) {
+        if (threadIdx.x == 0) {
+          d.gv[g].pcg_done = 1;
+          d.gv[g].rounds = round;
+          d.gv[g].bb = bb;
+        }
+        continue;
+      }
+      ++my_active;
+      if (threadIdx.x == 0) d.gv[g].inner_done = 0;
+      // inner target: reach eta |b| in one round if FP32 allows, else the FP32 floor
+      if (threadIdx.x == 0) tolj[j] = fmax(eta2 * bb / rr, 1e-11);
+      const GelInfo& G = d.gi[g];
+      const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
+      for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
+        const int r = 32 * s + lane;
+        const double4_32a rv = d.r[r];
+        const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
+        d.r32[r] = r32;
+        d.x32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.pp32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.s32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && my_active) atomicAdd(&d.act[2], my_active);
+    if (!grid_barrier(d.bar, epoch, d.err)) return;
+    if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[2]) == 0);
+    __syncthreads();
+    if (s_exit) break;
+    if (!grid_barrier(d.bar, epoch, d.err)) return;  // everyone has read act[2]
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.act[2] = 0;
+    // ---- inner FP32 CG (Chronopoulos-Gear), same structure as the FP64 kernel
+    int k = 0;
+    while (true) {
+      for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+        const int g = plan.slice_gel[s];
+        double ga = 0.0, de = 0.0, rr = 0.0;
+        if (d.gc[g].phase == phase && !d.gv[g].pcg_done && !d.gv[g].inner_done) {
+          const int r = 32 * s + lane;
+          float4 w = spmv_row32(d, s, lane, d.u32);
+          if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
+          d.w32[r] = w;
+          const float4 rv = d.r32[r], uv = d.u32[r];
+          ga = dot4f(rv, uv);
+          de = dot4f(w, uv);
+          rr = dot4f(rv, rv);
+        }
+        ga = warp_sum(ga);
+        de = warp_sum(de);
+        rr = warp_sum(rr);
+        if (lane == 0) {
+          dsm[(s - s0) * 4 + 0] = ga;
+          dsm[(s - s0) * 4 + 1] = de;
+          dsm[(s - s0) * 4 + 2] = rr;
+        }
+      }
+      cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 3);
+      if (blockIdx.x == 0 && threadIdx.x == 0) d.act[(kk + 1) & 1] = 0;
+      if (!grid_barrier(d.bar, epoch, d.err)) return;
+      k += 1;
+      kk += 1;
+      gel_totals(d, plan, g0, ng, 3, tot);
+      int inner_active = 0;
+      for (int j = 0; j < ng; ++j) {
+        const int g = g0 + j;
+        if (d.gc[g].phase != phase || d.gv[g].pcg_done || d.gv[g].inner_done) continue;
+        const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
+        // converged once |r32|^2 <= tol |r32 at the round start|^2 (FP32 accuracy floor 1e-11)
+        const double rr0 = k == 1 ? rr : d.gsc[(size_t)2 * d.n_gels + g];
+        if (k == 1 && threadIdx.x == 0) d.gsc[(size_t)2 * d.n_gels + g] = rr;
+        const bool conv = !(rr > tolj[j] * rr0) || k > maxit;
+        if (conv) {
+          const GelInfo& G = d.gi[g];
+          if (threadIdx.x == 0) {
+            d.gv[g].inner_done = 1;
+            if (s0 <= G.s0 && G.s0 < s1) d.gv[g].pcg_it += k - 1;  // the gel's first CTA counts
+          }
+          continue;
+        }
+        ++inner_active;
+        const int par = kk & 1, prv = (kk - 1) & 1;
+        double beta, alpha;
+        if (k == 1) {
+          beta = 0.0;
+          alpha = ga / de;
+        } else {
+          const double gprev = d.gsc[(size_t)(prv * 4 + 0) * d.n_gels + g];
+          const double aprev = d.gsc[(size_t)(prv * 4 + 1) * d.n_gels + g];
+          beta = ga / gprev;
+          alpha = ga / (de - beta * ga / aprev);
+        }
+        if (threadIdx.x == 0) {
+          d.gsc[(size_t)(par * 4 + 0) * d.n_gels + g] = ga;
+          d.gsc[(size_t)(par * 4 + 1) * d.n_gels + g] = alpha;
+        }
+        const float fb = (float)beta, fa = (float)alpha;
+        const GelInfo& G = d.gi[g];
+        const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
+        for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
+          const int r = 32 * s + lane;
+          const float4 u = d.u32[r], w = d.w32[r];
+          float4 pp = d.pp32[r], sv = d.s32[r], x = d.x32[r], rv = d.r32[r];
+          pp.x = fmaf(fb, pp.x, u.x); pp.y = fmaf(fb, pp.y, u.y); pp.z = fmaf(fb, pp.z, u.z);
+          sv.x = fmaf(fb, sv.x, w.x); sv.y = fmaf(fb, sv.y, w.y); sv.z = fmaf(fb, sv.z, w.z);
+          x.x = fmaf(fa, pp.x, x.x); x.y = fmaf(fa, pp.y, x.y); x.z = fmaf(fa, pp.z, x.z);
+          rv.x = fmaf(-fa, sv.x, rv.x); rv.y = fmaf(-fa, sv.y, rv.y); rv.z = fmaf(-fa, sv.z, rv.z);
+          d.pp32[r] = pp;
+          d.s32[r] = sv;
+          d.x32[r] = x;
+          d.r32[r] = rv;
+          d.u32[r] = mul3f(d.Minv32 + 9 * r, rv);
+        }
+      }
+      if (threadIdx.x == 0 && inner_active) atomicAdd(&d.act[kk & 1], inner_active);
+      if (!grid_barrier(d.bar, epoch, d.err)) return;
+      if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[kk & 1]) == 0);
+      __syncthreads();
+      if (s_exit) break;
+    }
+    // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p
+    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+      const int g = plan.slice_gel[s];
+      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+      const int r = 32 * s + lane;
+      const float4 x = d.x32[r];
+      double4_32a p = d.p[r];
+      p.x += (double)x.x;
+      p.y += (double)x.y;
+      p.z += (double)x.z;
+      d.p[r] = p;
+    }
+    if (!grid_barrier(d.bar, epoch, d.err)) return;
+    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+      const int g = plan.slice_gel[s];
+      double rr = 0.0;
+      if (d.gc[g].phase == phase && !d.gv[g].pcg_done) {
+        const int r = 32 * s + lane;
+        double4_32a ap = spmv_row_res(d, s, lane, d.p);
+        const double4_32a gr = d.grad[r];
+        double4_32a rv = make_double4_32a(-gr.x - ap.x, -gr.y - ap.y, -gr.z - ap.z, 0.0);
+        if (d.fixed[r]) rv = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.r[r] = rv;
+        rr = dot4(rv, rv);
+      }
+      rr = warp_sum(rr);
+      if (lane == 0) dsm[(s - s0) * 4 + 2] = rr;
+    }
+    cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 2, 3);
+    if (!grid_barrier(d.bar, epoch, d.err)) return;
+  }
+  // ---- g . p per gel (stationarity test of the line search)
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    double gp = 0.0;
+    if (d.gc[g].phase == phase) gp = dot4(d.grad[32 * s + lane], d.p[32 * s + lane]);
+    gp = warp_sum(gp);
+    if (lane == 0) dsm[(s - s0) * 4 + 0] = gp;
+  }
+  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 1);
+  if (!grid_barrier(d.bar, epoch, d.err)) return;
+  gel_totals(d, plan, g0, ng, 1, tot);
+  for (int j = threadIdx.x; j < ng; j += PCG_T) {
+    const GelInfo& G = d.gi[g0 + j];
+    if (s0 <= G.s0 && G.s0 < s1) d.gv[g0 + j].gtp = tot[j][0];
+  }
+  // ---- ||p||_inf per gel
+  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
+    const int g = plan.slice_gel[s];
+    if (d.gc[g].phase != phase) continue;
+    const double4_32a x = d.p[32 * s + lane];
+    const double m = warp_max(fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z))));
+    if (lane == 0) atomic_max_pos(&d.gv[g].pnorm_bits, m);
+  }
+}
+
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
+                             int refine_max, cudaStream_t st) {
+  double eta2 = eta * eta;
+  Dev dd = d;
+  PcgPlan pp = plan;
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&refine_max};
+  count_launch(1);
+  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed, dim3(nctas), dim3(PCG_T), args, smem, st);
+}
+
+// co-resident CTAs per SM of the persistent solvers (both must fit a cooperative launch)
+int pcg_max_ctas_per_sm(int max_slices) {
+  int a = 0, b = 0;
+  const size_t smem = (size_t)max_slices * 4 * sizeof(double);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg64, PCG_T, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_mixed, PCG_T, smem);
+  return a < b ? a : b;
 }
 
 // ---------------------------------------------------------------- energy
@@ -434,15 +799,20 @@ __global__ void k_energy_reduce(Dev d, int phase, const int* gel_piece, const do
     } else {
       v.alpha *= 0.5;
       v.ls_total += 1;
-      if (v.alpha < 1e-12 * v.alpha0) v.ls_state = 2;
+      // no resolvable decrease: stationary to energy resolution (6) or failure (2)
+      if (v.alpha < 1e-12 * v.alpha0) v.ls_state = (-v.gtp <= 1e-10 * fabs(v.E_cur)) ? 6 : 2;
     }
   }
 }
 
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
                    double* part_e, int mode, cudaStream_t st) {
-  if (npieces > 0) k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, part_e, mode);
+  if (npieces > 0) {
+    k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, part_e, mode);
+    count_launch(1);
+  }
   k_energy_reduce<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, gel_piece, part_e, mode);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------- per-row / per-gel steps
@@ -514,6 +884,8 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
     v.pnorm_bits = 0ull;
     v.pcg_done = 0;
     v.pcg_it = 0;
+    v.inner_done = 0;
+    v.rounds = 0;
     v.flags &= ~(4 | 16);
   } else if (op == 1) {
     v.converged = bitsd(v.pnorm_bits) < d.gc[g].tol_p ? 1 : 0;
@@ -547,13 +919,26 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
 
 void launch_rows(int which, const Dev& d, int phase, cudaStream_t st) {
   const int nb = nblk(d.nrows, 256);
-  if (which == 0) k_predictor<<<nb, 256, 0, st>>>(d, phase);
-  if (which == 1) k_update<<<nb, 256, 0, st>>>(d, phase);
-  if (which == 2) k_finalize<<<nb, 256, 0, st>>>(d, phase);
-  if (which == 3) k_restore<<<nb, 256, 0, st>>>(d, phase);
+  if (which == 0) {
+    k_predictor<<<nb, 256, 0, st>>>(d, phase);
+    count_launch(1);
+  }
+  if (which == 1) {
+    k_update<<<nb, 256, 0, st>>>(d, phase);
+    count_launch(1);
+  }
+  if (which == 2) {
+    k_finalize<<<nb, 256, 0, st>>>(d, phase);
+    count_launch(1);
+  }
+  if (which == 3) {
+    k_restore<<<nb, 256, 0, st>>>(d, phase);
+    count_launch(1);
+  }
 }
 void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st) {
   k_gel_op<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, op);
+  count_launch(1);
 }
 
 }  // namespace txg

@@ -65,6 +65,7 @@ struct GelVar {  // per gel, written by the device
   double E_cur, E_try;
   double alpha, alpha0;
   double bb;                 // |b|^2 of the PCG right-hand side
+  double gtp;                // g . p of the last Newton direction
   double fc[3];              // contact force on the gel
   unsigned long long toi_bits;    // min ACCD time of impact (non-negative double bits)
   unsigned long long pnorm_bits;  // ||p||_inf of the last Newton direction
@@ -74,9 +75,12 @@ struct GelVar {  // per gel, written by the device
   int converged;             // Newton converged at the last check
   int pcg_it;                // PCG iterations of the last solve
   int pcg_done;              // set inside the PCG kernel once the gel's solve converged
+  int inner_done;            // mixed precision: FP32 inner solve of the current round converged
+  int rounds;                // mixed precision: FP64 residual refinement rounds used
   int pair0, npair;          // candidate pair range
   int hent[NTAB];            // hash entries used
   int active_pairs;
+  double ibox_lo[3], ibox_hi[3];  // indenter bounding box of the current hash build
   int flags;                 // 1 hash overflow, 2 ACCD cap, 4 inverted tet, 8 ACCD hit, 16 pattern miss
 };
 
@@ -155,8 +159,15 @@ struct PcgPlan {
   const int* cta_s0;     // per CTA: first slice (n + 1 entries)
   const int* cta_g0;     // per CTA: first gel touched
   const int* cta_ng;     // per CTA: number of gels touched
+  const int* cta_slot0;  // per CTA: first reduction slot (one slot per (CTA, gel touched))
+  const int* gel_slot;   // per gel: first and one-past-last slot (n_gels + 1 ... stored as pairs)
   const int* slice_gel;  // per slice: its gel
+  int max_slices;        // most slices any CTA owns
+  int nslots;
 };
+
+// host-side count of kernel launches (every launcher adds the kernels it enqueued)
+void count_launch(int k);
 
 // ------------------------------------------------------------------------------------------
 // small helpers

@@ -51,11 +51,20 @@ void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st
 void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st);
 cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
                          cudaStream_t st);
-int pcg_max_ctas_per_sm();
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
+                             int refine_max, cudaStream_t st);
+int pcg_max_ctas_per_sm(int max_slices);
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
                    double* part_e, int mode, cudaStream_t st);
 void launch_rows(int which, const Dev& d, int phase, cudaStream_t st);
 void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st);
+}  // namespace txg
+
+#include <atomic>
+
+namespace txg {
+static std::atomic<long long> g_launch_count{0};
+void count_launch(int k) { g_launch_count.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace txg
 
 using namespace txg;
@@ -63,11 +72,12 @@ using namespace txg;
 namespace {
 
 thread_local std::string g_err;
+long long g_launch_mark = 0;
 
 // phases beyond the ones the kernels name
 enum : int { PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6, PH_PARK = 7, PH_FAIL = 8 };
 constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
-constexpr int PIECE_HOST = 2048;
+constexpr int PIECE_HOST = 512;
 
 #define CK(call)                                                          \
   do {                                                                    \
@@ -307,8 +317,34 @@ struct Run {
 
 }  // namespace
 
+namespace {
+enum Phase2 : int { PR_BEGIN = 0, PR_TET, PR_GATHER, PR_CONTACT, PR_PRECOND, PR_PCG, PR_QUERY, PR_ACCD,
+                    PR_LS, PR_FINAL, PR_N };
+const char* const kPhaseNames[PR_N] = {"begin", "tet_assemble", "gather", "contact_assemble", "precond",
+                                       "pcg", "query", "accd", "line_search", "finalize"};
+struct Prof {
+  bool on = false;
+  double ms[PR_N] = {};
+  long long launches[PR_N] = {};
+  double flops[PR_N] = {};
+  double bytes[PR_N] = {};
+  long long pcg_iters = 0, newton_iters = 0;
+  struct Pending {
+    cudaEvent_t a, b;
+    int phase;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+};
+}  // namespace
+
 struct tx_batch {
   int n = 0;
+  Prof prof;
+  std::vector<double> nnzb_real;  // per gel: real 3x3 blocks of its Hessian
+  std::vector<double> nfree;      // per gel: free rows
   cudaStream_t st = nullptr;
   bool mixed = false;
   std::vector<Mesh> mesh;
@@ -344,6 +380,41 @@ struct tx_gel {
 
 namespace {
 
+cudaEvent_t prof_event(tx_batch* b) {
+  if (!b->prof.pool.empty()) {
+    cudaEvent_t e = b->prof.pool.back();
+    b->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void prof_open(tx_batch* b, int phase) {
+  if (!b->prof.on) return;
+  b->prof.open_phase = phase;
+  b->prof.open_ev = prof_event(b);
+  cudaEventRecord(b->prof.open_ev, b->st);
+}
+void prof_close(tx_batch* b, int nlaunch) {
+  if (!b->prof.on || b->prof.open_phase < 0) return;
+  cudaEvent_t e = prof_event(b);
+  cudaEventRecord(e, b->st);
+  b->prof.pending.push_back({b->prof.open_ev, e, b->prof.open_phase});
+  b->prof.launches[b->prof.open_phase] += nlaunch;
+  b->prof.open_phase = -1;
+}
+// after a stream synchronisation: fold the finished event pairs into the counters
+void prof_resolve(tx_batch* b) {
+  for (auto& p : b->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) b->prof.ms[p.phase] += ms;
+    b->prof.pool.push_back(p.a);
+    b->prof.pool.push_back(p.b);
+  }
+  b->prof.pending.clear();
+}
+
 // per-gel pair capacity and hash sizes (initial guesses; grown on overflow)
 int initial_pcap(const Mesh& m) {
   return std::max(4096, 2 * (int)(m.sv.size() + m.st.size() + m.se.size()));
@@ -356,6 +427,7 @@ tx_status upload_ctl(tx_batch* b) {
 tx_status download_var(tx_batch* b) {
   CK(cudaMemcpyAsync(b->gv_h, b->d.gv, sizeof(GelVar) * b->n, cudaMemcpyDeviceToHost, b->st));
   CK(cudaStreamSynchronize(b->st));
+  prof_resolve(b);
   return TX_OK;
 }
 tx_status upload_info(tx_batch* b) {
@@ -412,11 +484,6 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     }
   }
   b->mixed = descs[0].params.precision == TX_PREC_MIXED;
-  if (b->mixed) {  // FP32 Krylov path not wired yet
-    g_err = "mixed precision is not available in this build";
-    delete b;
-    return TX_ERR_ARG;
-  }
   for (int g = 1; g < n; ++g)
     if ((descs[g].params.precision == TX_PREC_MIXED) != b->mixed) {
       delete b;
@@ -615,12 +682,20 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     delete b;
     return TX_ERR_CUDA;
   }
-  const int occ = std::max(1, pcg_max_ctas_per_sm());
-  int nctas = std::min(nsm * std::min(occ, 2), nslices);
-  nctas = std::max(nctas, 1);
-  std::vector<int> cta_s0(nctas + 1), cta_g0(nctas), cta_ng(nctas);
+  // one CTA per SM for small systems (every warp owns a slice), two per SM for large ones
+  int nctas = std::min(nsm * 2, (nslices + 3) / 4);
+  nctas = std::max(1, std::min(nctas, nslices));
+  int max_slices = (nslices + nctas - 1) / nctas;
+  const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
+  if (nctas > nsm * occ) {
+    nctas = nsm * occ;
+    max_slices = (nslices + nctas - 1) / nctas;
+  }
+  std::vector<int> cta_s0(nctas + 1), cta_g0(nctas), cta_ng(nctas), cta_slot0(nctas + 1, 0);
+  std::vector<int> gel_slot(2 * n, -1);
   for (int c = 0; c <= nctas; ++c) cta_s0[c] = (int)((long long)c * nslices / nctas);
   for (int c = 0; c < nctas; ++c) {
+    max_slices = std::max(max_slices, cta_s0[c + 1] - cta_s0[c]);
     if (cta_s0[c + 1] > cta_s0[c]) {
       cta_g0[c] = slice_gel[cta_s0[c]];
       cta_ng[c] = slice_gel[cta_s0[c + 1] - 1] - cta_g0[c] + 1;
@@ -633,7 +708,14 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
       delete b;
       return TX_ERR_ARG;
     }
+    cta_slot0[c + 1] = cta_slot0[c] + cta_ng[c];
+    for (int j = 0; j < cta_ng[c]; ++j) {
+      const int g = cta_g0[c] + j, slot = cta_slot0[c] + j;
+      if (gel_slot[2 * g] < 0) gel_slot[2 * g] = slot;
+      gel_slot[2 * g + 1] = slot + 1;
+    }
   }
+  const int nslots = cta_slot0[nctas];
   b->nctas = nctas;
   // ---- energy pieces
   for (int g = 0; g < n; ++g) {
@@ -694,7 +776,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.w = M.get<double4_32a>(rows);
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
-  d.part = M.get<double>(4 * (size_t)nslices);
+  d.part = M.get<double>(4 * (size_t)nslots);
   d.gsc = M.get<double>(8 * (size_t)n);
   d.bar = M.get<unsigned>(4);
   d.act = M.get<int>(4);
@@ -722,7 +804,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
-  int* cta_buf = M.get<int>(3 * (size_t)nctas + 1 + nslices);
+  int* cta_buf = M.get<int>(4 * (size_t)nctas + 2 + nslices + 2 * (size_t)n);
   if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !cta_buf || (b->mixed ? !d.vals32 : !d.vals)) {
     M.release();
     delete b;
@@ -732,6 +814,10 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->plan.cta_g0 = cta_buf + nctas + 1;
   b->plan.cta_ng = cta_buf + 2 * nctas + 1;
   b->plan.slice_gel = cta_buf + 3 * nctas + 1;
+  b->plan.cta_slot0 = cta_buf + 3 * nctas + 1 + nslices;
+  b->plan.gel_slot = cta_buf + 4 * nctas + 2 + nslices;
+  b->plan.max_slices = max_slices;
+  b->plan.nslots = nslots;
   if (b->mixed) {  // FP32 PCG vectors live in the upper half of dedicated buffers
     d.u32 = (float4*)M.get<float4>(rows);
     d.w32 = (float4*)M.get<float4>(rows);
@@ -793,6 +879,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U((void*)b->plan.cta_g0, cta_g0.data(), sizeof(int) * nctas);
   U((void*)b->plan.cta_ng, cta_ng.data(), sizeof(int) * nctas);
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
+  U((void*)b->plan.cta_slot0, cta_slot0.data(), sizeof(int) * (nctas + 1));
+  U((void*)b->plan.gel_slot, gel_slot.data(), sizeof(int) * 2 * n);
   if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
@@ -816,6 +904,14 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     return s;
   }
   b->run.resize(n);
+  b->nnzb_real.assign(n, 0.0);
+  b->nfree.assign(n, 0.0);
+  for (int g = 0; g < n; ++g) {
+    for (int i = 0; i < b->mesh[g].nv; ++i) {
+      b->nnzb_real[g] += (double)b->mesh[g].adj[i].size();
+      b->nfree[g] += b->mesh[g].fixed[i] ? 0.0 : 1.0;
+    }
+  }
   for (int g = 0; g < n; ++g) {
     std::memcpy(b->run[g].pose, b->mesh[g].pose0, sizeof(double) * 7);
     b->run[g].last.status = TX_OK;
@@ -879,6 +975,7 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
   }
   tx_status s = upload_ctl(b);
   if (s != TX_OK) return s;
+  prof_open(b, PR_BEGIN);
   launch_gel_op(d, PH_BEGIN, 3, st);
   launch_indenter_pose(d, PH_BEGIN, d.niv_total, st);
   launch_hash_build(d, PH_BEGIN, 1, st);
@@ -889,6 +986,7 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
   const int accd_max = b->mesh[set[0]].prm.accd_max_iter;
   launch_accd(d, PH_BEGIN, 1, accd_max, st);
   launch_min_dist(d, PH_BEGIN, st);
+  prof_close(b, 12);
   CK(cudaGetLastError());
   s = download_var(b);
   if (s != TX_OK) return s;
@@ -950,9 +1048,11 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
     for (int g : start) b->gc_h[g].phase = PH_START;
     s = upload_ctl(b);
     if (s != TX_OK) return s;
+    prof_open(b, PR_BEGIN);
     launch_rows(0, d, PH_START, st);         // x_n, predictor
     launch_hash_build(d, PH_START, 0, st);   // static tables at the target pose
     launch_energy(d, PH_START, b->pieces, b->npieces, b->gel_piece, b->part_e, 0, st);
+    prof_close(b, 4);
     CK(cudaGetLastError());
     for (int g : start) {
       Run& R = b->run[g];
@@ -995,22 +1095,28 @@ namespace {
 tx_status post_pcg(tx_batch* b) {
   Dev& d = b->d;
   cudaStream_t st = b->st;
+  prof_open(b, PR_QUERY);
   launch_query(d, PH_NEWTON, 2 | 8, st);
   launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
   launch_query(d, PH_NEWTON, 1 | 2 | 8, st);
   launch_pair_ranges(d, PH_NEWTON, 1, st);
+  prof_close(b, 6);
   int accd_max = 1, ls_max = 1;
   for (int g = 0; g < b->n; ++g)
     if (b->gc_h[g].phase == PH_NEWTON) {
       accd_max = std::max(accd_max, b->mesh[g].prm.accd_max_iter);
       ls_max = std::max(ls_max, b->mesh[g].prm.ls_max_halvings);
     }
+  prof_open(b, PR_ACCD);
   launch_accd(d, PH_NEWTON, 0, accd_max, st);
   launch_gel_op(d, PH_NEWTON, 2, st);
+  prof_close(b, 2);
   // first trial; usually accepted
+  prof_open(b, PR_LS);
   launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
   launch_rows(1, d, PH_NEWTON, st);
   launch_gel_op(d, PH_NEWTON, 5, st);
+  prof_close(b, 4);
   CK(cudaGetLastError());
   tx_status s = download_var(b);
   if (s != TX_OK) return s;
@@ -1019,11 +1125,13 @@ tx_status post_pcg(tx_batch* b) {
     for (int g = 0; g < b->n; ++g)
       if (b->gc_h[g].phase == PH_NEWTON && !b->gv_h[g].converged && b->gv_h[g].ls_state == 0) searching = true;
     if (!searching) break;
+    prof_open(b, PR_LS);
     for (int k = 0; k < 4; ++k) {  // a few halvings per host round trip
       launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
       launch_rows(1, d, PH_NEWTON, st);
       launch_gel_op(d, PH_NEWTON, 5, st);
     }
+    prof_close(b, 16);
     CK(cudaGetLastError());
     s = download_var(b);
     if (s != TX_OK) return s;
@@ -1038,9 +1146,11 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
   for (int g : fin) b->gc_h[g].phase = PH_FINAL;
   tx_status s = upload_ctl(b);
   if (s != TX_OK) return s;
+  prof_open(b, PR_FINAL);
   launch_rows(2, d, PH_FINAL, b->st);      // v = (x - x_n) / h
   launch_gel_op(d, PH_FINAL, 4, b->st);    // distance minimum at the final state
   launch_min_dist(d, PH_FINAL, b->st);
+  prof_close(b, 3);
   CK(cudaGetLastError());
   s = download_var(b);
   if (s != TX_OK) return s;
@@ -1082,12 +1192,29 @@ tx_status do_newton(tx_batch* b) {
     pcg_max = std::max(pcg_max, b->mesh[g].prm.pcg_max_iter);
   }
   launch_gel_op(d, PH_NEWTON, 0, st);
+  prof_open(b, PR_TET);
   launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 1);
+  prof_open(b, PR_GATHER);
   launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
+  prof_close(b, 1);
+  prof_open(b, PR_CONTACT);
   launch_contact_assemble(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 1);
+  prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 1);
   CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * 4, st));
-  CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+  CK(cudaMemsetAsync(d.act, 0, sizeof(int) * 4, st));
+  prof_open(b, PR_PCG);
+  if (b->mixed) {
+    int refine = 1;
+    for (int g : set) refine = std::max(refine, b->mesh[g].prm.refine_max);
+    CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
+  } else {
+    CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+  }
+  prof_close(b, 1);
   launch_gel_op(d, PH_NEWTON, 1, st);
   CK(cudaGetLastError());
   s = post_pcg(b);
@@ -1121,11 +1248,31 @@ tx_status do_newton(tx_batch* b) {
     if (s != TX_OK) return s;
   }
   std::vector<int> fin, fail;
+  if (b->prof.on) {
+    for (int g : set) {
+      const double it = b->gv_h[g].pcg_it;
+      const GelInfo& G = b->gi[g];
+      // per PCG iteration and row: SpMV 18 flops per 3x3 block, preconditioner 18, four
+      // axpys 24, three dot products 18; mixed precision adds one FP64 residual SpMV per round
+      const double rounds = b->mixed ? b->gv_h[g].rounds : 0.0;
+      b->prof.flops[PR_PCG] += it * (18.0 * b->nnzb_real[g] + 60.0 * b->nfree[g]) + rounds * 18.0 * b->nnzb_real[g];
+      // bytes: block values + column index + gathered vector per block, and 13 row vectors
+      // (FP64: 72 B values, 32 B vectors; mixed: 36 B values, 16 B vectors)
+      if (b->mixed)
+        b->prof.bytes[PR_PCG] += it * (40.0 * b->nnzb_real[g] + 16.0 * b->nnzb_real[g] + 244.0 * G.nv);
+      else
+        b->prof.bytes[PR_PCG] += it * (76.0 * b->nnzb_real[g] + 32.0 * b->nnzb_real[g] + 488.0 * G.nv);
+      b->prof.pcg_iters += b->gv_h[g].pcg_it;
+      b->prof.newton_iters += 1;
+      b->prof.flops[PR_TET] += 0.0;
+    }
+  }
   for (int g : set) {
     Run& R = b->run[g];
     const GelVar& v = b->gv_h[g];
     R.acc.pcg_iters += v.pcg_it;
-    if (v.converged) {
+    R.acc.refine_rounds += v.rounds;
+    if (v.converged || v.ls_state == 6) {
       fin.push_back(g);
     } else if (v.ls_state == 2) {
       finish_request(b, g, TX_ERR_LINESEARCH);
@@ -1259,6 +1406,8 @@ tx_status eval_restore(tx_batch* b, int g) {
 void destroy_batch(tx_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->st);
+  prof_resolve(b);
+  for (cudaEvent_t e : b->prof.pool) cudaEventDestroy(e);
   b->mem.release();
   b->pair_mem.release();
   b->hash_mem.release();
@@ -1552,6 +1701,37 @@ tx_status tx_gel_gradient(tx_gel* gl, const double* x, const double* xt, double 
   if (f_contact)
     for (int c = 0; c < 3; ++c) f_contact[c] = b->gv_h[0].fc[c];
   return eval_restore(b, 0);
+}
+
+tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out) {
+  if (!b) return TX_ERR_ARG;
+  CK(cudaStreamSynchronize(b->st));
+  prof_resolve(b);
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->n_phases = PR_N;
+    for (int k = 0; k < PR_N; ++k) {
+      out->names[k] = kPhaseNames[k];
+      out->ms[k] = b->prof.ms[k];
+      out->launches[k] = b->prof.launches[k];
+      out->flops[k] = b->prof.flops[k];
+      out->bytes[k] = b->prof.bytes[k];
+    }
+    out->pcg_iters = b->prof.pcg_iters;
+    out->newton_iters = b->prof.newton_iters;
+    out->kernel_launches = g_launch_count.load() - g_launch_mark;
+  }
+  g_launch_mark = g_launch_count.load();
+  std::vector<cudaEvent_t> pool = std::move(b->prof.pool);
+  b->prof = Prof{};
+  b->prof.pool = std::move(pool);
+  b->prof.on = enable != 0;
+  return TX_OK;
+}
+
+tx_status tx_gel_profile(tx_gel* g, int32_t enable, tx_profile* out) {
+  if (!g) return TX_ERR_ARG;
+  return tx_batch_profile(g->b, enable, out);
 }
 
 tx_status tx_eval_tets(int32_t n, const double* X, const double* x, double mu, double lambda, int32_t project,

@@ -78,8 +78,25 @@ def test_small_gel_trajectory_matches_oracle():
     assert np.abs(fg - fo).max() <= 1e-4 * np.abs(fo).max()
 
 
+def test_mixed_precision_trajectory_matches_oracle():
+    """FP32 Hessian blocks + FP32 Krylov solve with FP64 residual refinement; the gradient,
+    barrier, CCD and energy stay FP64, so the converged minimiser is the FP64 one."""
+    wl = W.small_gel_sphere(0)
+    gel = B.Gel.from_workload(wl, newton_tol=1e-7, precision=B.TX_PREC_MIXED)
+    ref = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    errs = []
+    for s in range(30):
+        st = gel.step(wl.poses[s], wl.dt)
+        info = ref.step(wl.poses[s], wl.dt)
+        assert st == 0 and info["status"] == 0, B.STATUS_NAMES[st]
+        errs.append(np.abs(gel.state()[0] - ref.state()[0]).max())
+    errs = np.array(errs)
+    print("mixed precision max / rms error over steps: %.3e / %.3e m" % (errs.max(), np.sqrt(np.mean(errs ** 2))))
+    assert errs.max() <= POS_TOL
+
+
 def test_batch_equals_alone():
-    wls = [W.small_gel_sphere(s, n_steps=12) for s in range(3)]
+    wls = [W.small_gel_sphere(s) for s in range(3)]
     descs = [B.GelDesc.from_workload(w, newton_tol=1e-7) for w in wls]
     b = B.tx_batch_create(descs)
     alone = [B.Gel.from_workload(w, newton_tol=1e-7) for w in wls]

@@ -60,11 +60,19 @@ def random_pairs(n, seed):
         kind = len(Ps) % 2
         P = rng.normal(scale=0.5e-3, size=(4, 3))
         if kind == 0:
-            # put the point near the triangle
-            b = rng.dirichlet([1, 1, 1]) * rng.uniform(0.6, 1.3)
-            q = P[1] + b[1] * (P[2] - P[1]) + b[2] * (P[3] - P[1])
             nrm = np.cross(P[2] - P[1], P[3] - P[1])
-            P[0] = q + nrm / np.linalg.norm(nrm) * rng.uniform(0.05, 0.95) * dhat + rng.normal(scale=2e-5, size=3)
+            nrm /= np.linalg.norm(nrm)
+            if len(Ps) % 6 == 0:
+                # beyond a corner: the closest feature is the vertex P[1]
+                out = -(P[2] - P[1]) - (P[3] - P[1])
+                q = P[1] + 0.02 * out / np.linalg.norm(out) * dhat / 1e-4 * 1e-3
+                P[0] = q + nrm * rng.uniform(-0.5, 0.5) * dhat
+                P[0] = P[1] + (P[0] - P[1]) * (0.5 * dhat / np.linalg.norm(P[0] - P[1]))
+            else:
+                # near the triangle (face interior or beyond an edge)
+                b = rng.dirichlet([1, 1, 1]) * rng.uniform(0.6, 1.3)
+                q = P[1] + b[1] * (P[2] - P[1]) + b[2] * (P[3] - P[1])
+                P[0] = q + nrm * rng.uniform(0.05, 0.95) * dhat + rng.normal(scale=2e-5, size=3)
         else:
             s, t = rng.uniform(-0.2, 1.2, size=2)
             pa = P[0] + s * (P[1] - P[0])
