@@ -231,6 +231,18 @@ tx_status tx_eval_accd(int32_t n, const int32_t* kind, const double* P, const do
                        double s, double tc, int32_t max_iter, double* toi, int32_t* hit,
                        void* stream);
 
+/* Block-Jacobi preconditioned conjugate gradient for A x = b -- the linear solve of the projected
+ * Newton step on its own.  A is symmetric positive definite with 3x3 blocks in block-CSR form:
+ * row_ptr (n + 1), col_idx (nnzb), vals (9 nnzb, row-major blocks; every block row holds its
+ * diagonal block).  b and x are 3n vectors; x0 = 0.  All array arguments are device pointers.
+ * Stops when |r| <= rel_tol |b| or after max_iter iterations.  Allocates its scratch (~21 n
+ * doubles of device memory) for the call, runs on `stream` and returns after the solve; the
+ * iteration count and the final relative residual go to *iters and *rel_res (host, may be NULL).
+ * TX_ERR_DEVICE_TIMEOUT if a bounded grid-wide wait gave up. */
+tx_status tx_bsr_pcg(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                     const double* b, double* x, double rel_tol, int32_t max_iter, int32_t* iters,
+                     double* rel_res, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

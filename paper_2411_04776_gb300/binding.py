@@ -119,6 +119,9 @@ _SIGS = [
     ("tx_batch_reset", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("tx_batch_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(tx_profile)]),
     ("tx_gel_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(tx_profile)]),
+    ("tx_bsr_pcg", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, c_ip,
+                                  c_dp, ctypes.c_void_p]),
     ("tx_eval_tets", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -416,6 +419,19 @@ def tx_eval_accd(kind, P, dP, s=0.1, tc=1.0, max_iter=1000000, stream=None):
     _check(load().tx_eval_accd(n, _ptr(kind), _ptr(P), _ptr(dP), float(s), float(tc), int(max_iter), _ptr(toi),
                                _ptr(hit), _stream(stream)), "tx_eval_accd")
     return toi, hit
+
+
+def tx_bsr_pcg(row_ptr, col_idx, vals, b, rel_tol=1e-10, max_iter=10000, stream=None):
+    """Block-Jacobi PCG on a 3x3-block CSR system (torch CUDA tensors: int32 row_ptr/col_idx,
+    float64 vals (nnzb, 9) and b (3n)).  Returns (x, iterations, relative residual)."""
+    import torch
+    n = row_ptr.numel() - 1
+    x = torch.empty(3 * n, dtype=torch.float64, device=b.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    _check(load().tx_bsr_pcg(n, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(b), _ptr(x), float(rel_tol),
+                             int(max_iter), ctypes.byref(it), ctypes.byref(rr), _stream(stream)), "tx_bsr_pcg")
+    return x, it.value, rr.value
 
 
 # ------------------------------------------------------------------ convenience wrapper
