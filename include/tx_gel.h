@@ -243,6 +243,22 @@ tx_status tx_bsr_pcg(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
                      const double* b, double* x, double rel_tol, int32_t max_iter, int32_t* iters,
                      double* rel_res, void* stream);
 
+/* tx_bsr_pcg without any device allocation.  (This entry point has no counterpart in the paper; it
+ * exists for callers of this library that must not allocate device memory while they run: a host
+ * framework that owns every device allocation of a simulation step, code recorded into a CUDA
+ * graph, or a real-time control loop where cudaMalloc/cudaFree would synchronise the device and
+ * stall the other streams.)  Same arguments and results as tx_bsr_pcg, for n <= 65536 block rows;
+ * larger systems are rejected with TX_ERR_ARG (tx_last_error says why).  The scratch is one
+ * fixed array of about 11 MB inside the library's device module, held by every GPU that loads
+ * the library until the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before any
+ * stream capture.  All calls on a device share the array: calls that overlap on the GPU (on
+ * different streams or from different threads) race and give wrong results; the counters a call
+ * needs zeroed are cleared by the call itself. */
+tx_status tx_bsr_pcg_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                             const double* vals, const double* b, double* x, double rel_tol,
+                             int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,6 +122,9 @@ _SIGS = [
     ("tx_bsr_pcg", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, c_ip,
                                   c_dp, ctypes.c_void_p]),
+    ("tx_bsr_pcg_noalloc", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32,
+                                          c_ip, c_dp, ctypes.c_void_p]),
     ("tx_eval_tets", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -431,6 +434,21 @@ def tx_bsr_pcg(row_ptr, col_idx, vals, b, rel_tol=1e-10, max_iter=10000, stream=
     rr = ctypes.c_double(0.0)
     _check(load().tx_bsr_pcg(n, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(b), _ptr(x), float(rel_tol),
                              int(max_iter), ctypes.byref(it), ctypes.byref(rr), _stream(stream)), "tx_bsr_pcg")
+    return x, it.value, rr.value
+
+
+def tx_bsr_pcg_noalloc(row_ptr, col_idx, vals, b, x=None, rel_tol=1e-10, max_iter=10000, stream=None):
+    """tx_bsr_pcg with the library's fixed scratch array (no device allocation by the library;
+    the output x may be passed in preallocated).  n <= 65536 block rows."""
+    import torch
+    n = row_ptr.numel() - 1
+    if x is None:
+        x = torch.empty(3 * n, dtype=torch.float64, device=b.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    _check(load().tx_bsr_pcg_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(b), _ptr(x),
+                                     float(rel_tol), int(max_iter), ctypes.byref(it), ctypes.byref(rr),
+                                     _stream(stream)), "tx_bsr_pcg_noalloc")
     return x, it.value, rr.value
 
 

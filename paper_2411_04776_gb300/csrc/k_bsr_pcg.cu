@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "tx_gel.h"
 #include "txgel_common.cuh"
@@ -176,6 +177,39 @@ static tx_status check_bsr_args(int32_t n, const int32_t* row_ptr, const int32_t
   return TX_OK;
 }
 
+// ------------------------------------------------------------------ no-allocation variant
+// Scratch of tx_bsr_pcg_noalloc: a fixed array in the module's global memory, so that a call
+// needs no cudaMalloc.  Every GPU that loads the library holds it until the process exits.
+constexpr int NOALLOC_MAX_ROWS = 65536;
+constexpr int NOALLOC_MAX_CTAS = 1024;
+// r, z, p, q (3 n each) + inverse diagonal blocks (9 n) + 2 partials per CTA + out/barrier/error
+constexpr size_t NOALLOC_DOUBLES = (size_t)21 * NOALLOC_MAX_ROWS + 2 * NOALLOC_MAX_CTAS + 4;
+static __device__ __align__(256) double g_pcg_scratch[NOALLOC_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static double* g_scratch_dev[NOALLOC_MAX_DEVICES] = {nullptr};
+static std::mutex g_scratch_mu;
+
+// Device address of the scratch array on the current device.  The symbol's host-side name is
+// only a stand-in, so the address is looked up once per device (with that device current).
+static cudaError_t scratch_on_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_dev[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_pcg_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_dev[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_scratch_dev[dev];
+  return cudaSuccess;
+}
+
+void set_last_error(const char* msg);
+
 }  // namespace txg
 
 using namespace txg;
@@ -227,6 +261,61 @@ extern "C" tx_status tx_bsr_pcg(int32_t n, const int32_t* row_ptr, const int32_t
     res = TX_ERR_CUDA;
   cudaFree(buf);
   if (res != TX_OK) return res;
+  if (derr) return TX_ERR_DEVICE_TIMEOUT;
+  if (iters) *iters = (int32_t)out[0];
+  if (rel_res) *rel_res = out[1];
+  return TX_OK;
+}
+
+extern "C" tx_status tx_bsr_pcg_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                        const double* vals, const double* b, double* x, double rel_tol,
+                                        int32_t max_iter, int32_t* iters, double* rel_res, void* stream) {
+  tx_status s = check_bsr_args(n, row_ptr, col_idx, vals, b, x, rel_tol, max_iter);
+  if (s != TX_OK) return s;
+  if (n > NOALLOC_MAX_ROWS) {
+    set_last_error("tx_bsr_pcg_noalloc: more than 65536 block rows (use tx_bsr_pcg)");
+    return TX_ERR_ARG;
+  }
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (rel_res) *rel_res = 0.0;
+    return TX_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TX_ERR_CUDA;
+  if (nsm > NOALLOC_MAX_CTAS) return TX_ERR_ARG;
+  double* buf = nullptr;
+  if (scratch_on_current_device(&buf) != cudaSuccess) return TX_ERR_CUDA;
+  const size_t vec = (size_t)3 * n;
+  BsrPcgArgs a;
+  a.n = n;
+  a.rp = row_ptr;
+  a.ci = col_idx;
+  a.va = vals;
+  a.b = b;
+  a.x = x;
+  a.tol2 = rel_tol * rel_tol;
+  a.maxit = max_iter;
+  a.r = buf;
+  a.z = a.r + vec;
+  a.p = a.z + vec;
+  a.q = a.p + vec;
+  a.minv = a.q + vec;
+  a.part = buf + 21 * (size_t)NOALLOC_MAX_ROWS;
+  a.out = a.part + 2 * (size_t)NOALLOC_MAX_CTAS;
+  a.bar = reinterpret_cast<unsigned*>(a.out + 2);
+  a.err = reinterpret_cast<int*>(a.out + 3);
+  int nctas = 0;
+  double out[2] = {0.0, 0.0};
+  int derr = 0;
+  // the previous call's counters are still in the array: clear them before the launch
+  if (cudaMemsetAsync(a.out, 0, 4 * sizeof(double), st) != cudaSuccess || launch_bsr_pcg(a, st, &nctas) != cudaSuccess ||
+      cudaMemcpyAsync(out, a.out, sizeof(out), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&derr, a.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TX_ERR_CUDA;
   if (derr) return TX_ERR_DEVICE_TIMEOUT;
   if (iters) *iters = (int32_t)out[0];
   if (rel_res) *rel_res = out[1];

@@ -65,6 +65,7 @@ void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st);
 namespace txg {
 static std::atomic<long long> g_launch_count{0};
 void count_launch(int k) { g_launch_count.fetch_add(k, std::memory_order_relaxed); }
+void set_last_error(const char* msg);
 }  // namespace txg
 
 using namespace txg;
@@ -73,6 +74,11 @@ namespace {
 
 thread_local std::string g_err;
 long long g_launch_mark = 0;
+}  // namespace
+
+void txg::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
 
 // phases beyond the ones the kernels name
 enum : int { PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6, PH_PARK = 7, PH_FAIL = 8 };
