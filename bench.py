@@ -43,7 +43,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="mini", choices=["mini", "small", "batch_mini", "batch_mixed"])
+    ap.add_argument("--workload", default="mini", choices=["mini", "small", "batch_mini", "batch_mixed", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: total request rate [1/s]")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM admission budget")
     ap.add_argument("--n-gels", type=int, default=0, help="gels per batch (batch workloads)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=0)
@@ -59,14 +62,15 @@ def make_workload(kind, seed, n_gels=0):
         return [W.small_gel_sphere(seed)]
     if kind == "batch_mini":  # config 3 geometry: n copies of the GelSight-Mini gel, own indenters
         return [W.mini_gel(seed + g) for g in range(n_gels or 64)]
-    if kind == "batch_mixed":  # config 2: resolutions drawn from the three grids
-        return W.mixed_batch(n_gels or 256, seed0=seed)
+    if kind in ("batch_mixed", "serve"):  # config 2 / 4: resolutions drawn from the three grids
+        return W.mixed_batch(n_gels or (1024 if kind == "serve" else 256), seed0=seed)
     return [W.mini_gel(seed)]
 
 
 NAMES = {"mini": "GelSight-Mini gel 41x51x9 (config 1)", "small": "small gel 10x13x4 (config 0)",
          "batch_mini": "batch of GelSight-Mini gels 41x51x9 (config 3 geometry)",
-         "batch_mixed": "batch of gels with mixed resolutions (config 2)"}
+         "batch_mixed": "batch of gels with mixed resolutions (config 2)",
+         "serve": "serving: RL envs with mixed-resolution gels, Poisson step requests (config 4)"}
 
 
 def workload_config(wls, kind, precision):
@@ -271,8 +275,46 @@ def cpu_baseline(args, budget=30.0):
             "sample": f"oracle (FP64 C++, 1 thread) steps 0..{done - 1} of the same trajectory, {el:.1f} s"}
 
 
+def run_serve(args):
+    """Continuous-batching server over resident gels (config 4): Poisson step requests from the
+    environments, admission by HBM footprint, one Newton iteration per round for all admitted."""
+    import torch
+    from paper_2411_04776_gb300 import binding as B
+    from paper_2411_04776_gb300 import serving as S
+    torch.cuda.set_device(0)
+    wls = make_workload("serve", args.seed, args.n_gels)
+    prec = B.TX_PREC_MIXED if args.precision == "mixed" else B.TX_PREC_FP64
+    t0 = time.perf_counter()
+    srv = S.GelServer(wls, args.budget_gb * 1e9, precision=prec, stream=torch.cuda.current_stream())
+    t_create = time.perf_counter() - t0
+    # warm-up: every environment takes its first steps
+    srv.run_schedule([list(range(srv.n))] * max(1, args.warmup))
+    srv.completed.clear()
+    arrivals = S.poisson_arrivals(srv.n, args.rate, args.duration, args.seed + 1)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        done = srv.serve(arrivals, drain=True)
+        wall = time.perf_counter() - t0
+    ok = [r for r in done if r.status == 0]
+    lat = S.latency_summary(done)
+    line = {"metric": "gel Newton-converged steps/sec", "value": len(ok) / wall, "unit": "steps/s", "n_gpus": 1,
+            "steps": len(ok), "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(len(ok), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": dict(workload_config(wls, "serve", args.precision), rate=args.rate, duration=args.duration,
+                           budget_gb=args.budget_gb),
+            "latency_ms": lat, "requests": len(arrivals), "failed": len(done) - len(ok),
+            "failed_status": sorted({B.STATUS_NAMES.get(r.status, r.status) for r in done if r.status != 0}),
+            "max_inflight": srv.max_inflight, "max_inflight_gb": srv.max_inflight_bytes / 1e9,
+            "resident_gb": float(srv.footprint.sum() / 1e9), "create_s": t_create, "clocks": clk.summary()}
+    srv.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
+    if args.workload == "serve" and args.impl == "gpu":
+        return run_serve(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -144,11 +144,13 @@ struct Mesh {
   std::vector<double> ie_len2;
   std::vector<std::vector<int>> adj;  // sorted neighbour lists (incl. self)
   double mu = 0, lam = 0, kappa = 0, bbox = 0, cell = 0, org[3] = {0, 0, 0};
+  double mean_se = 0, lo[3] = {0, 0, 0};
   tx_params prm{};
   double pose0[7];
 };
 
-tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
+// common argument validation of a description
+tx_status check_desc(const tx_gel_desc* d) {
   if (!d || d->n_verts <= 0 || d->n_tets < 0 || !d->verts || (d->n_tets > 0 && !d->tets) ||
       d->n_ind_verts < 0 || d->n_ind_tris < 0 || (d->n_ind_verts > 0 && !d->ind_verts) ||
       (d->n_ind_tris > 0 && !d->ind_tris))
@@ -158,23 +160,23 @@ tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0)
     return TX_ERR_ARG;
+  for (int k = 0; k < 4 * d->n_tets; ++k)
+    if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
+  for (int k = 0; k < 3 * d->n_ind_tris; ++k)
+    if (d->ind_tris[k] < 0 || d->ind_tris[k] >= d->n_ind_verts) return TX_ERR_ARG;
+  return TX_OK;
+}
+
+// Rest data of the gel itself (depends on its vertices, tets, Dirichlet mask and density):
+// Dm^-1, volumes, lumped masses, boundary triangles / vertices / edges, vertex adjacency.
+tx_status build_gel_part(const tx_gel_desc* d, Mesh& m) {
   m.nv = d->n_verts;
   m.nt = d->n_tets;
-  m.niv = d->n_ind_verts;
-  m.nit = d->n_ind_tris;
-  m.prm = p;
-  std::memcpy(m.pose0, d->ind_pose, sizeof(m.pose0));
   m.X.assign(d->verts, d->verts + 3 * m.nv);
   m.tets.assign(d->tets, d->tets + 4 * m.nt);
-  for (int v : m.tets)
-    if (v < 0 || v >= m.nv) return TX_ERR_ARG;
-  for (int k = 0; k < 3 * m.nit; ++k)
-    if (d->ind_tris[k] < 0 || d->ind_tris[k] >= m.niv) return TX_ERR_ARG;
   m.fixed.assign(m.nv, 0);
   if (d->dirichlet)
     for (int i = 0; i < m.nv; ++i) m.fixed[i] = d->dirichlet[i] ? 1 : 0;
-  m.mu = d->young / (2.0 * (1.0 + d->poisson));
-  m.lam = d->young * d->poisson / ((1.0 + d->poisson) * (1.0 - 2.0 * d->poisson));
   m.Dminv.resize(9 * (size_t)m.nt);
   m.vol.resize(m.nt);
   m.mass.assign(m.nv, 0.0);
@@ -200,75 +202,59 @@ tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
     m.vol[t] = det / 6.0;
     for (int a = 0; a < 4; ++a) m.mass[v[a]] += d->density * m.vol[t] / 4.0;
   }
-  // boundary faces (faces of exactly one tet), their vertices and edges
-  std::map<std::array<int, 3>, std::pair<std::array<int, 3>, int>> faces;
+  // boundary faces (faces of exactly one tet): sort the 4T faces by their vertex set
   const int FI[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+  std::vector<std::pair<std::array<int, 3>, std::array<int, 3>>> faces;
+  faces.reserve(4 * (size_t)m.nt);
   for (int t = 0; t < m.nt; ++t)
     for (auto& f : FI) {
       std::array<int, 3> tri = {m.tets[4 * t + f[0]], m.tets[4 * t + f[1]], m.tets[4 * t + f[2]]};
       std::array<int, 3> key = tri;
       std::sort(key.begin(), key.end());
-      auto& e = faces[key];
-      if (e.second == 0) e.first = tri;
-      e.second++;
+      faces.push_back({key, tri});
     }
+  std::sort(faces.begin(), faces.end());
   std::vector<char> on(m.nv, 0);
-  std::map<std::pair<int, int>, int> edges;
-  for (auto& kv : faces) {
-    if (kv.second.second != 1) continue;
-    m.st.push_back(kv.second.first);
-    for (int c = 0; c < 3; ++c) {
-      const int a = kv.second.first[c], b = kv.second.first[(c + 1) % 3];
-      on[a] = 1;
-      edges[{std::min(a, b), std::max(a, b)}] = 1;
+  std::vector<std::pair<int, int>> edges;
+  for (size_t k = 0; k < faces.size();) {
+    size_t e = k;
+    while (e < faces.size() && faces[e].first == faces[k].first) ++e;
+    if (e - k == 1) {
+      const auto& tri = faces[k].second;
+      m.st.push_back(tri);
+      for (int c = 0; c < 3; ++c) {
+        const int a = tri[c], b = tri[(c + 1) % 3];
+        on[a] = 1;
+        edges.push_back({std::min(a, b), std::max(a, b)});
+      }
     }
+    k = e;
   }
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
   for (int i = 0; i < m.nv; ++i)
     if (on[i]) m.sv.push_back(i);
   double lsum = 0.0;
-  for (auto& kv : edges) {
-    m.se.push_back({kv.first.first, kv.first.second});
+  for (auto& ed : edges) {
+    m.se.push_back({ed.first, ed.second});
     double l2 = 0.0;
     for (int c = 0; c < 3; ++c) {
-      const double dd = m.X[3 * kv.first.first + c] - m.X[3 * kv.first.second + c];
+      const double dd = m.X[3 * ed.first + c] - m.X[3 * ed.second + c];
       l2 += dd * dd;
     }
     m.se_len2.push_back(l2);
     lsum += std::sqrt(l2);
   }
-  const double mean_se = edges.empty() ? 0.0 : lsum / edges.size();
-  m.IV.assign(d->ind_verts, d->ind_verts + 3 * m.niv);
-  std::map<std::pair<int, int>, int> iedges;
-  for (int k = 0; k < m.nit; ++k) {
-    m.it.push_back({d->ind_tris[3 * k], d->ind_tris[3 * k + 1], d->ind_tris[3 * k + 2]});
-    for (int c = 0; c < 3; ++c) {
-      const int a = d->ind_tris[3 * k + c], b = d->ind_tris[3 * k + (c + 1) % 3];
-      iedges[{std::min(a, b), std::max(a, b)}] = 1;
-    }
-  }
-  double isum = 0.0;
-  for (auto& kv : iedges) {
-    m.ie.push_back({kv.first.first, kv.first.second});
-    double l2 = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      const double dd = m.IV[3 * kv.first.first + c] - m.IV[3 * kv.first.second + c];
-      l2 += dd * dd;
-    }
-    m.ie_len2.push_back(l2);
-    isum += std::sqrt(l2);
-  }
-  const double mean_ie = iedges.empty() ? 0.0 : isum / iedges.size();
-  m.kappa = p.kappa > 0 ? p.kappa : d->young * mean_se;
+  m.mean_se = edges.empty() ? 0.0 : lsum / edges.size();
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int i = 0; i < m.nv; ++i)
     for (int c = 0; c < 3; ++c) {
       lo[c] = std::min(lo[c], m.X[3 * i + c]);
       hi[c] = std::max(hi[c], m.X[3 * i + c]);
     }
+  for (int c = 0; c < 3; ++c) m.lo[c] = lo[c];
   m.bbox = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
-  m.cell = std::max(std::max(mean_se, mean_ie), 4.0 * p.dhat);
-  for (int c = 0; c < 3; ++c) m.org[c] = lo[c] - 64.0 * m.cell;
   // vertex adjacency through tets
   m.adj.assign(m.nv, {});
   for (int i = 0; i < m.nv; ++i) m.adj[i].push_back(i);
@@ -280,6 +266,59 @@ tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
     l.erase(std::unique(l.begin(), l.end()), l.end());
   }
   return TX_OK;
+}
+
+// Material constants, the indenter (edges, lengths) and the per-gel solver constants.
+void build_rest_part(const tx_gel_desc* d, Mesh& m) {
+  const tx_params& p = d->params;
+  m.niv = d->n_ind_verts;
+  m.nit = d->n_ind_tris;
+  m.prm = p;
+  std::memcpy(m.pose0, d->ind_pose, sizeof(m.pose0));
+  m.mu = d->young / (2.0 * (1.0 + d->poisson));
+  m.lam = d->young * d->poisson / ((1.0 + d->poisson) * (1.0 - 2.0 * d->poisson));
+  m.IV.assign(d->ind_verts, d->ind_verts + 3 * m.niv);
+  std::vector<std::pair<int, int>> iedges;
+  for (int k = 0; k < m.nit; ++k) {
+    m.it.push_back({d->ind_tris[3 * k], d->ind_tris[3 * k + 1], d->ind_tris[3 * k + 2]});
+    for (int c = 0; c < 3; ++c) {
+      const int a = d->ind_tris[3 * k + c], b = d->ind_tris[3 * k + (c + 1) % 3];
+      iedges.push_back({std::min(a, b), std::max(a, b)});
+    }
+  }
+  std::sort(iedges.begin(), iedges.end());
+  iedges.erase(std::unique(iedges.begin(), iedges.end()), iedges.end());
+  double isum = 0.0;
+  for (auto& ed : iedges) {
+    m.ie.push_back({ed.first, ed.second});
+    double l2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double dd = m.IV[3 * ed.first + c] - m.IV[3 * ed.second + c];
+      l2 += dd * dd;
+    }
+    m.ie_len2.push_back(l2);
+    isum += std::sqrt(l2);
+  }
+  const double mean_ie = iedges.empty() ? 0.0 : isum / iedges.size();
+  m.kappa = p.kappa > 0 ? p.kappa : d->young * m.mean_se;
+  m.cell = std::max(std::max(m.mean_se, mean_ie), 4.0 * p.dhat);
+  for (int c = 0; c < 3; ++c) m.org[c] = m.lo[c] - 64.0 * m.cell;
+}
+
+tx_status build_mesh(const tx_gel_desc* d, Mesh& m) {
+  tx_status s = check_desc(d);
+  if (s != TX_OK) return s;
+  s = build_gel_part(d, m);
+  if (s != TX_OK) return s;
+  build_rest_part(d, m);
+  return TX_OK;
+}
+
+// 64-bit FNV-1a over a byte range
+uint64_t fnv(const void* p, size_t n, uint64_t h) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
+  return h;
 }
 
 // ---------------------------------------------------------------- device allocation
@@ -482,12 +521,51 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->n = n;
   b->st = (cudaStream_t)stream;
   b->mesh.resize(n);
+  // gels with identical rest meshes (vertices, tets, Dirichlet mask, density) share one
+  // preprocessing pass; only the indenter part is per gel
+  std::map<uint64_t, int> seen;
   for (int g = 0; g < n; ++g) {
-    tx_status s = build_mesh(&descs[g], b->mesh[g]);
+    const tx_gel_desc* d = &descs[g];
+    tx_status s = check_desc(d);
     if (s != TX_OK) {
       delete b;
       return s;
     }
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(&d->n_verts, sizeof(d->n_verts), h);
+    h = fnv(&d->n_tets, sizeof(d->n_tets), h);
+    h = fnv(&d->density, sizeof(d->density), h);
+    h = fnv(d->verts, sizeof(double) * 3 * d->n_verts, h);
+    h = fnv(d->tets, sizeof(int32_t) * 4 * d->n_tets, h);
+    if (d->dirichlet) h = fnv(d->dirichlet, d->n_verts, h);
+    auto it = seen.find(h);
+    bool reused = false;
+    if (it != seen.end()) {
+      const tx_gel_desc* o = &descs[it->second];
+      const bool same = o->n_verts == d->n_verts && o->n_tets == d->n_tets && o->density == d->density &&
+                        std::memcmp(o->verts, d->verts, sizeof(double) * 3 * d->n_verts) == 0 &&
+                        std::memcmp(o->tets, d->tets, sizeof(int32_t) * 4 * d->n_tets) == 0 &&
+                        ((!o->dirichlet && !d->dirichlet) ||
+                         (o->dirichlet && d->dirichlet && std::memcmp(o->dirichlet, d->dirichlet, d->n_verts) == 0));
+      if (same) {
+        b->mesh[g] = b->mesh[it->second];  // copies the gel part (and a stale indenter part)
+        Mesh& m = b->mesh[g];
+        m.IV.clear();
+        m.it.clear();
+        m.ie.clear();
+        m.ie_len2.clear();
+        reused = true;
+      }
+    }
+    if (!reused) {
+      s = build_gel_part(d, b->mesh[g]);
+      if (s != TX_OK) {
+        delete b;
+        return s;
+      }
+      seen[h] = g;
+    }
+    build_rest_part(d, b->mesh[g]);
   }
   b->mixed = descs[0].params.precision == TX_PREC_MIXED;
   for (int g = 1; g < n; ++g)

@@ -23,6 +23,7 @@ All lengths are metres, poses are (qw, qx, qy, qz, tx, ty, tz).
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 
 import numpy as np
@@ -80,37 +81,41 @@ class Workload:
 # ----------------------------------------------------------------------------------------------
 def gel_grid(nx: int, ny: int, nz: int, size) -> GelMesh:
     """Box gel on an nx*ny*nz vertex grid, 6 Kuhn tets per cube, bottom face (z = 0) fixed."""
+    verts, tets, dirichlet = _gel_grid_arrays(int(nx), int(ny), int(nz), tuple(float(v) for v in size))
+    return GelMesh(verts.copy(), tets.copy(), dirichlet.copy())
+
+
+@functools.lru_cache(maxsize=16)
+def _gel_grid_arrays(nx, ny, nz, size):
     lx, ly, lz = size
     xs = np.linspace(0.0, lx, nx)
     ys = np.linspace(0.0, ly, ny)
     zs = np.linspace(0.0, lz, nz)
     zz, yy, xx = np.meshgrid(zs, ys, xs, indexing="ij")
     verts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(np.float64)
-
-    def vid(i, j, k):
-        return i + nx * (j + ny * k)
-
-    tets = []
+    # cube origins (i, j, k), ordered k-major then j then i (x fastest)
+    kk, jj, ii = np.meshgrid(np.arange(nz - 1), np.arange(ny - 1), np.arange(nx - 1), indexing="ij")
+    base = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
     axes = np.eye(3, dtype=np.int64)
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    for k in range(nz - 1):
-        for j in range(ny - 1):
-            for i in range(nx - 1):
-                base = np.array([i, j, k])
-                for p in perms:
-                    c0 = base
-                    c1 = c0 + axes[p[0]]
-                    c2 = c1 + axes[p[1]]
-                    c3 = c2 + axes[p[2]]
-                    t = [vid(*c0), vid(*c1), vid(*c2), vid(*c3)]
-                    # orientation of this path tet = sign of the axis permutation
-                    parity = np.linalg.det(np.stack([axes[p[0]], axes[p[1]], axes[p[2]]]))
-                    if parity < 0:
-                        t[2], t[3] = t[3], t[2]
-                    tets.append(t)
-    tets = np.asarray(tets, dtype=np.int32)
+
+    def vid(c):
+        return c[:, 0] + nx * (c[:, 1] + ny * c[:, 2])
+
+    per_cube = []
+    for p in perms:
+        c0 = base
+        c1 = c0 + axes[p[0]]
+        c2 = c1 + axes[p[1]]
+        c3 = c2 + axes[p[2]]
+        t = np.stack([vid(c0), vid(c1), vid(c2), vid(c3)], axis=1)
+        # orientation of this path tet = sign of the axis permutation
+        if np.linalg.det(np.stack([axes[p[0]], axes[p[1]], axes[p[2]]])) < 0:
+            t = t[:, [0, 1, 3, 2]]
+        per_cube.append(t)
+    tets = np.stack(per_cube, axis=1).reshape(-1, 4).astype(np.int32)
     dirichlet = (verts[:, 2] <= 1e-12).astype(np.uint8)
-    return GelMesh(verts, tets, dirichlet)
+    return verts, tets, dirichlet
 
 
 # ----------------------------------------------------------------------------------------------
