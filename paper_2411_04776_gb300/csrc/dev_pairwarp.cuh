@@ -1,0 +1,428 @@
+// Barrier derivatives of one contact pair on the 32 lanes of a warp, and the PSD projection of
+// its Hessian block by a warp-parallel Jacobi eigen-solve.
+//
+// The squared distance D of every closest-feature form is a function of nd <= 3 difference
+// vectors v_a = P[pl_a] - P[mi_a] (see dev_contact.cuh).  Its gradient over the v_a is cheap and
+// is formed once per pair (struct DV); every entry of its Hessian over the v_a has a closed form
+// (cross norm c(x, y) = |x|^2 |y|^2 - (x.y)^2, triple product s = w.(e1 x e2), quotient rule), so
+// the lanes of a warp compute the entries of the point-space block they own independently:
+//   d2D/dP_I dP_J = sum_{a,b} sigma(I, a) sigma(J, b) d2D/dv_a dv_b,  sigma = +1 (plus point),
+//   -1 (minus point), 0.
+// The barrier on D and the IPC edge-edge mollifier are then applied entry by entry.
+//
+// Projection (Li et al. 2020: per-pair Hessians are projected to PSD before assembly).  Cyclic
+// Jacobi with the round-robin ("parallel") ordering of Brent & Luk: each round applies m/2
+// disjoint rotations at once; lane k owns the 2x2 block (pair a, pair b) of the matrix it
+// transforms, so no two lanes write the same entry.  GB300 issues FP64 at 1/64 of the FP32
+// rate, so the eigenbasis is found in FP32 first, made orthonormal in FP64 by two Newton-Schulz
+// steps Q <- Q (3 I - Q^T Q) / 2, and refined by FP64 Jacobi sweeps on B = Q^T A Q (nearly
+// diagonal); the clamp Q max(B, 0) Q^T is assembled in FP64.
+#pragma once
+#include "dev_contact.cuh"
+
+namespace txg {
+
+// closest-feature data of a pair in difference-vector space
+struct DV {
+  int form, nd;
+  int pl[3], mi[3];
+  double v[3][3];
+  double D;
+  double s, W;     // PT / LL: s = w.(e1 x e2), W = c(e1, e2);  PE: s = c(w, e), W = |e|^2
+  double gD[9];    // dD/dv
+  double gs[9];    // PT / LL: ds/dv;  PE: d c(w, e)/dv
+  double gW[9];    // dW/dv
+};
+
+__device__ __forceinline__ void cn_grad(const double* x, const double* y, double* gx, double* gy) {
+  const double xx = dot3(x, x), yy = dot3(y, y), xy = dot3(x, y);
+  for (int c = 0; c < 3; ++c) {
+    gx[c] = 2.0 * yy * x[c] - 2.0 * xy * y[c];
+    gy[c] = 2.0 * xx * y[c] - 2.0 * xy * x[c];
+  }
+}
+
+__device__ __forceinline__ void dv_setup(const DType& t, const double P[4][3], DV& o) {
+  o.form = t.f;
+  for (int k = 0; k < 9; ++k) o.gD[k] = o.gs[k] = o.gW[k] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    o.pl[a] = o.mi[a] = -1;
+    o.v[a][0] = o.v[a][1] = o.v[a][2] = 0.0;
+  }
+  o.s = 0.0;
+  o.W = 1.0;
+  if (t.f == DF_PP) {
+    o.nd = 1;
+    o.pl[0] = t.i[0];
+    o.mi[0] = t.i[1];
+    sub3(P[t.i[0]], P[t.i[1]], o.v[0]);
+    o.D = dot3(o.v[0], o.v[0]);
+    for (int c = 0; c < 3; ++c) o.gD[c] = 2.0 * o.v[0][c];
+    return;
+  }
+  if (t.f == DF_PE) {
+    o.nd = 2;
+    o.pl[0] = t.i[0]; o.mi[0] = t.i[1];
+    o.pl[1] = t.i[2]; o.mi[1] = t.i[1];
+    sub3(P[t.i[0]], P[t.i[1]], o.v[0]);
+    sub3(P[t.i[2]], P[t.i[1]], o.v[1]);
+    const double* w = o.v[0];
+    const double* e = o.v[1];
+    const double we = dot3(w, e);
+    o.s = dot3(w, w) * dot3(e, e) - we * we;
+    o.W = dot3(e, e);
+    cn_grad(w, e, o.gs, o.gs + 3);
+    for (int c = 0; c < 3; ++c) o.gW[3 + c] = 2.0 * e[c];
+    o.D = o.s / o.W;
+    for (int k = 0; k < 6; ++k) o.gD[k] = (o.gs[k] - o.D * o.gW[k]) / o.W;
+    return;
+  }
+  o.nd = 3;
+  if (t.f == DF_PT) {
+    o.pl[0] = t.i[0]; o.mi[0] = t.i[1];
+    o.pl[1] = t.i[2]; o.mi[1] = t.i[1];
+    o.pl[2] = t.i[3]; o.mi[2] = t.i[1];
+  } else {  // LL
+    o.pl[0] = t.i[2]; o.mi[0] = t.i[0];
+    o.pl[1] = t.i[1]; o.mi[1] = t.i[0];
+    o.pl[2] = t.i[3]; o.mi[2] = t.i[2];
+  }
+  for (int a = 0; a < 3; ++a) sub3(P[o.pl[a]], P[o.mi[a]], o.v[a]);
+  const double* w = o.v[0];
+  const double* e1 = o.v[1];
+  const double* e2 = o.v[2];
+  double n[3];
+  cross3(e1, e2, n);
+  cross3(e2, w, o.gs + 3);
+  cross3(w, e1, o.gs + 6);
+  for (int c = 0; c < 3; ++c) o.gs[c] = n[c];
+  o.s = dot3(w, n);
+  const double ee = dot3(e1, e2);
+  o.W = dot3(e1, e1) * dot3(e2, e2) - ee * ee;
+  cn_grad(e1, e2, o.gW + 3, o.gW + 6);
+  o.D = o.s * o.s / o.W;
+  for (int k = 0; k < 9; ++k) o.gD[k] = (2.0 * o.s * o.gs[k] - o.D * o.gW[k]) / o.W;
+}
+
+// sign of point p in difference vector a
+__device__ __forceinline__ double dv_sigma(const DV& o, int p, int a) {
+  return (o.pl[a] == p ? 1.0 : 0.0) - (o.mi[a] == p ? 1.0 : 0.0);
+}
+
+// Hessian entry of the cross norm c(x, y): variables a, b in {0: x, 1: y}, components c, e
+__device__ __forceinline__ double cn_entry(const double* x, const double* y, int a, int c, int b, int e) {
+  const double dl = c == e ? 1.0 : 0.0;
+  if (a == 0 && b == 0) return 2.0 * dot3(y, y) * dl - 2.0 * y[c] * y[e];
+  if (a == 1 && b == 1) return 2.0 * dot3(x, x) * dl - 2.0 * x[c] * x[e];
+  if (a == 0) return 4.0 * x[c] * y[e] - 2.0 * y[c] * x[e] - 2.0 * dot3(x, y) * dl;
+  return 4.0 * x[e] * y[c] - 2.0 * y[e] * x[c] - 2.0 * dot3(x, y) * dl;
+}
+
+// entry (i, j) of the cross-product matrix [v]x
+__device__ __forceinline__ double skew_entry(const double* v, int i, int j) {
+  if (i == j) return 0.0;
+  const int k = 3 - i - j;
+  return j == (i + 1) % 3 ? -v[k] : v[k];
+}
+
+// d2D / dv_a,c dv_b,e
+__device__ __forceinline__ double hD_dv(const DV& o, int a, int c, int b, int e) {
+  if (o.form == DF_PP) return c == e ? 2.0 : 0.0;
+  const int ia = 3 * a + c, ib = 3 * b + e;
+  if (o.form == DF_PE) {
+    const double HN = cn_entry(o.v[0], o.v[1], a, c, b, e);
+    const double HL = (a == 1 && b == 1 && c == e) ? 2.0 : 0.0;
+    return (HN - o.D * HL - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) / o.W;
+  }
+  // second derivatives of the triple product w.(e1 x e2) (zero within one vector)
+  double Hs = 0.0;
+  if (a != b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const int r = a < b ? c : e, q = a < b ? e : c;  // component of the lower / higher vector
+    if (lo == 0 && hi == 1) Hs = -skew_entry(o.v[2], r, q);
+    else if (lo == 0 && hi == 2) Hs = skew_entry(o.v[1], r, q);
+    else Hs = -skew_entry(o.v[0], r, q);
+  }
+  const double HW = (a >= 1 && b >= 1) ? cn_entry(o.v[1], o.v[2], a - 1, c, b - 1, e) : 0.0;
+  return (2.0 * o.gs[ia] * o.gs[ib] + 2.0 * o.s * Hs - o.D * HW - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) / o.W;
+}
+
+// d2D / dP_I dP_J (point-space dofs I, J in [0, 12))
+__device__ __forceinline__ double hD_point(const DV& o, int I, int J) {
+  const int p = I / 3, c = I % 3, q = J / 3, e = J % 3;
+  double h = 0.0;
+  for (int a = 0; a < o.nd; ++a) {
+    const double sa = dv_sigma(o, p, a);
+    if (sa == 0.0) continue;
+    for (int b = 0; b < o.nd; ++b) {
+      const double sb = dv_sigma(o, q, b);
+      if (sb == 0.0) continue;
+      h += sa * sb * hD_dv(o, a, c, b, e);
+    }
+  }
+  return h;
+}
+
+// point-space gradient of D
+__device__ __forceinline__ void gD_point(const DV& o, double g[12]) {
+  for (int k = 0; k < 12; ++k) g[k] = 0.0;
+  for (int a = 0; a < o.nd; ++a)
+    for (int c = 0; c < 3; ++c) {
+      g[3 * o.pl[a] + c] += o.gD[3 * a + c];
+      g[3 * o.mi[a] + c] -= o.gD[3 * a + c];
+    }
+}
+
+// Barrier of a pair in point space (without kappa).  kind 1 (edge-edge) carries the IPC mollifier
+// m(c) = (2 - c/eps) c/eps of the edges' cross norm c below eps_x.
+struct PairBarrier {
+  DV dv;
+  double b0, bD, bDD;     // b(D), db/dD, d2b/dD2 (unmollified)
+  double gDp[12];         // dD/dP
+  int moll;               // mollifier active
+  double m, m1, m2;       // m(c), m'(c), m''(c)
+  double ea[3], eb[3];    // edge vectors (kind 1)
+  double gcp[12];         // dc/dP (kind 1, mollified)
+  double b;               // mollified barrier value
+  int involved;           // bit mask of the points the value depends on
+};
+
+// Returns false when d >= dhat.
+__device__ __forceinline__ bool pair_barrier_setup(int kind, const double P[4][3], double dhat, double eps_x,
+                                                   PairBarrier& pb, DType* tyo = nullptr) {
+  DType ty;
+  const double D0 = pair_d2(kind, P, &ty);
+  if (tyo) *tyo = ty;
+  if (!(D0 < dhat * dhat)) return false;
+  dv_setup(ty, P, pb.dv);
+  barrier_D(pb.dv.D, dhat, &pb.b0, &pb.bD, &pb.bDD);
+  gD_point(pb.dv, pb.gDp);
+  const int np = ty.f == DF_PP ? 2 : (ty.f == DF_PE ? 3 : 4);
+  int msk = 0;
+  for (int k = 0; k < np; ++k) msk |= 1 << ty.i[k];
+  pb.involved = msk;
+  pb.moll = 0;
+  pb.m = 1.0;
+  pb.m1 = pb.m2 = 0.0;
+  pb.b = pb.b0;
+  for (int k = 0; k < 12; ++k) pb.gcp[k] = 0.0;
+  if (kind == 1) {
+    sub3(P[1], P[0], pb.ea);
+    sub3(P[3], P[2], pb.eb);
+    const double ab = dot3(pb.ea, pb.eb);
+    const double c = dot3(pb.ea, pb.ea) * dot3(pb.eb, pb.eb) - ab * ab;
+    if (c < eps_x) {
+      pb.moll = 1;
+      pb.involved = 0xF;
+      const double q = c / eps_x;
+      pb.m = (2.0 - q) * q;
+      pb.m1 = 2.0 * (1.0 - q) / eps_x;
+      pb.m2 = -2.0 / (eps_x * eps_x);
+      double ga[3], gb[3];
+      cn_grad(pb.ea, pb.eb, ga, gb);
+      for (int c3 = 0; c3 < 3; ++c3) {
+        pb.gcp[c3] = -ga[c3];
+        pb.gcp[3 + c3] = ga[c3];
+        pb.gcp[6 + c3] = -gb[c3];
+        pb.gcp[9 + c3] = gb[c3];
+      }
+      pb.b = pb.m * pb.b0;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ double pair_grad_entry(const PairBarrier& pb, int I) {
+  const double gb = pb.bD * pb.gDp[I];
+  return pb.moll ? pb.m * gb + pb.b0 * pb.m1 * pb.gcp[I] : gb;
+}
+
+// d2b/dP_I dP_J of the (mollified) barrier
+__device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, int J) {
+  double h = pb.bDD * pb.gDp[I] * pb.gDp[J] + pb.bD * hD_point(pb.dv, I, J);
+  if (pb.moll) {
+    const int p = I / 3, c = I % 3, q = J / 3, e = J % 3;
+    // cross-norm Hessian over the points: edge a = (P0 -> P1), edge b = (P2 -> P3)
+    const int ap = p < 2 ? 0 : 1, aq = q < 2 ? 0 : 1;
+    const double sp = (p == 1 || p == 3) ? 1.0 : -1.0, sq = (q == 1 || q == 3) ? 1.0 : -1.0;
+    const double Hc = sp * sq * cn_entry(pb.ea, pb.eb, ap, c, aq, e);
+    const double gbI = pb.bD * pb.gDp[I], gbJ = pb.bD * pb.gDp[J];
+    h = pb.m * h + pb.m1 * (pb.gcp[I] * gbJ + gbI * pb.gcp[J]) +
+        pb.b0 * (pb.m2 * pb.gcp[I] * pb.gcp[J] + pb.m1 * Hc);
+  }
+  return h;
+}
+
+// ---------------------------------------------------------------- warp-parallel Jacobi
+constexpr int PW_MAXN = 12;  // largest block: all four points of a pair
+
+template <typename T>
+struct RotWS {
+  T c[PW_MAXN / 2], s[PW_MAXN / 2], t[PW_MAXN / 2];
+  int p[PW_MAXN / 2], q[PW_MAXN / 2];
+};
+
+__device__ __forceinline__ float jabs(float v) { return fabsf(v); }
+__device__ __forceinline__ double jabs(double v) { return fabs(v); }
+__device__ __forceinline__ float jsqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double jsqrt(double v) { return sqrt(v); }
+
+// Cyclic Jacobi on the symmetric m x m matrix A (m even, row stride m) in shared memory,
+// accumulating the rotations into V (A <- J^T A J, V <- V J).  Stops when the squared
+// off-diagonal norm is at most rel_tol times the squared diagonal norm.  Rotations whose
+// off-diagonal entry is below skip_rel (|a_pp| + |a_qq|) are skipped (exact identity).
+// Called by all 32 lanes of a warp.
+template <typename T>
+__device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip_rel, RotWS<T>& rw, int lane) {
+  const int h = m >> 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = 0, dg = 0;
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = e / m, j = e - i * m;
+      const T v = A[e];
+      if (i == j) dg += v * v;
+      else if (i < j) off += v * v;
+    }
+    off = warp_sum(off);
+    dg = warp_sum(dg);
+    if (!(off > rel_tol * dg)) break;
+    for (int r = 0; r < m - 1; ++r) {
+      if (lane < h) {
+        // round-robin: position 0 fixed, positions 1..m-1 rotate by r
+        const int pa = lane == 0 ? 0 : lane + 1, pb = lane == 0 ? 1 : m - lane;
+        int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
+        int q = (pb - 1 + r) % (m - 1) + 1;
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        const T apq = A[p * m + q], app = A[p * m + p], aqq = A[q * m + q];
+        T c = 1, s = 0, t = 0;
+        if (apq != T(0) && jabs(apq) > skip_rel * (jabs(app) + jabs(aqq))) {
+          const T th = (aqq - app) / (T(2) * apq);
+          t = (th >= T(0) ? T(1) : T(-1)) / (jabs(th) + jsqrt(th * th + T(1)));
+          c = T(1) / jsqrt(t * t + T(1));
+          s = t * c;
+        }
+        rw.p[lane] = p;
+        rw.q[lane] = q;
+        rw.c[lane] = c;
+        rw.s[lane] = s;
+        rw.t[lane] = t;
+      }
+      __syncwarp();
+      for (int blk = lane; blk < h * h; blk += 32) {
+        const int a = blk / h, b = blk - a * h;
+        const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
+        if (a == b) {
+          const T t = rw.t[a];
+          if (t != T(0)) {
+            const T apq = A[pa * m + qa];
+            A[pa * m + pa] -= t * apq;
+            A[qa * m + qa] += t * apq;
+            A[pa * m + qa] = A[qa * m + pa] = T(0);
+          }
+        } else {
+          const T ca = rw.c[a], sa = rw.s[a], cb = rw.c[b], sb = rw.s[b];
+          const T x00 = A[pa * m + pb], x01 = A[pa * m + qb], x10 = A[qa * m + pb], x11 = A[qa * m + qb];
+          const T y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+          const T y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+          A[pa * m + pb] = cb * y00 - sb * y01;
+          A[pa * m + qb] = sb * y00 + cb * y01;
+          A[qa * m + pb] = cb * y10 - sb * y11;
+          A[qa * m + qb] = sb * y10 + cb * y11;
+        }
+      }
+      for (int task = lane; task < m * h; task += 32) {
+        const int k = task / h, a = task - k * h;
+        const int p = rw.p[a], q = rw.q[a];
+        const T c = rw.c[a], s = rw.s[a];
+        const T vp = V[k * m + p], vq = V[k * m + q];
+        V[k * m + p] = c * vp - s * vq;
+        V[k * m + q] = s * vp + c * vq;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// per-warp workspace of the projection
+struct ProjWS {
+  double H[PW_MAXN * PW_MAXN];  // in: symmetric block (stride m); out: its PSD projection
+  double Q[PW_MAXN * PW_MAXN];
+  double T[PW_MAXN * PW_MAXN];
+  double B[PW_MAXN * PW_MAXN];
+  float a32[PW_MAXN * PW_MAXN];
+  float v32[PW_MAXN * PW_MAXN];
+  RotWS<float> r32;
+  RotWS<double> r64;
+};
+
+// C = op(X) Y over m x m matrices (stride m): op = transpose when tx; lane-parallel entries
+__device__ __forceinline__ void warp_mm(const double* X, const double* Y, double* C, int m, bool tx, int lane) {
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e - i * m;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(tx ? X[k * m + i] : X[i * m + k], Y[k * m + j], acc);
+    C[e] = acc;
+  }
+  __syncwarp();
+}
+
+// PSD projection of w.H (n x n symmetric, stored with stride m = n rounded up to even, padding
+// rows / columns zero); all 32 lanes of the warp call it.
+__device__ void warp_psd_project(ProjWS& w, int n, int lane) {
+  const int m = n + (n & 1);
+  // FP32 copy scaled by a power of two so that its squares stay far from the FP32 range limits
+  double mx = 0.0;
+  for (int e = lane; e < m * m; e += 32) mx = fmax(mx, fabs(w.H[e]));
+  mx = warp_max(mx);
+  if (!(mx > 0.0)) return;  // zero block: already its own projection
+  const double sc = ldexp(1.0, -ilogb(mx));
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e - i * m;
+    w.a32[e] = (float)(w.H[e] * sc);
+    w.v32[e] = i == j ? 1.f : 0.f;
+  }
+  __syncwarp();
+  warp_jacobi<float>(w.a32, w.v32, m, 10, 1e-12f, 1e-9f, w.r32, lane);
+  for (int e = lane; e < m * m; e += 32) w.Q[e] = (double)w.v32[e];
+  __syncwarp();
+  // two Newton-Schulz steps: Q <- Q (3 I - Q^T Q) / 2 (orthogonality error 1e-7 -> 1e-14 -> eps)
+  for (int it = 0; it < 2; ++it) {
+    warp_mm(w.Q, w.Q, w.T, m, true, lane);
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = e / m, j = e - i * m;
+      double acc = 0.0;
+      for (int k = 0; k < m; ++k) acc = fma(w.Q[i * m + k], w.T[k * m + j], acc);
+      w.B[e] = 1.5 * w.Q[e] - 0.5 * acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < m * m; e += 32) w.Q[e] = w.B[e];
+    __syncwarp();
+  }
+  warp_mm(w.H, w.Q, w.T, m, false, lane);  // T = H Q
+  for (int e = lane; e < m * m; e += 32) {  // B = Q^T T, symmetric by construction
+    const int i = e / m, j = e - i * m;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(w.Q[k * m + a], w.T[k * m + b], acc);
+    w.B[e] = acc;
+  }
+  __syncwarp();
+  warp_jacobi<double>(w.B, w.Q, m, 4, 1e-30, 1e-18, w.r64, lane);
+  for (int e = lane; e < m * m; e += 32) {  // H = Q max(diag B, 0) Q^T
+    const int i = e / m, j = e - i * m;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double lk = w.B[k * m + k];
+      if (lk > 0.0) acc = fma(w.Q[a * m + k] * lk, w.Q[b * m + k], acc);
+    }
+    w.H[e] = acc;
+  }
+  __syncwarp();
+}
+
+}  // namespace txg

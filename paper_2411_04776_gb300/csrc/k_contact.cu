@@ -9,9 +9,13 @@
 // swept over the motion under test) come within dhat of each other along every axis; it is
 // reported from exactly one cell (the lowest cell of the two boxes' common cell range), counted
 // first, prefix-summed, then written, so the candidate list is ordered and identical run to run.
-#include "dev_contact.cuh"
+#include <algorithm>
+
+#include "dev_pairwarp.cuh"
 
 namespace txg {
+
+static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 constexpr int HMAXC = 1023;       // cell coordinates are clamped to [0, HMAXC]
 constexpr int QUERY_CELL_LIMIT = 4096;
@@ -118,6 +122,39 @@ __global__ void k_indenter_pose(Dev d, int phase) {
   d.iv_prev[k] = b;
 }
 
+// ---------------------------------------------------------------- indenter primitive boxes
+__device__ __forceinline__ int pbox_base(const Dev& d, int tab) {
+  return tab == 0 ? 0 : (tab == 1 ? d.nit_total : d.nit_total + d.niv_total);
+}
+__device__ __forceinline__ Box load_pbox(const Dev& d, int tab, int k, int* cell) {
+  const int i = pbox_base(d, tab) + k;
+  const double4_32a lo = d.pbox[2 * i], hi = d.pbox[2 * i + 1];
+  *cell = (int)__double_as_longlong(lo.w);
+  Box b;
+  b.lo[0] = lo.x; b.lo[1] = lo.y; b.lo[2] = lo.z;
+  b.hi[0] = hi.x; b.hi[1] = hi.y; b.hi[2] = hi.z;
+  return b;
+}
+
+// one thread per indenter primitive of the gels in `phase`: its box (swept from the previous pose
+// when asked) and lowest grid cell, read by the hash build and every query until the next build
+__global__ void k_ind_boxes(Dev d, int phase, int swept) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = d.nit_total, nv = d.niv_total;
+  if (i >= nt + nv + d.nie_total) return;
+  const int tab = i < nt ? 0 : (i < nt + nv ? 1 : 2);
+  const int k = i - (tab == 0 ? 0 : (tab == 1 ? nt : nt + nv));
+  const int g = tab == 0 ? d.it_gel[k] : (tab == 1 ? d.iv_gel[k] : d.ie_gel[k]);
+  if (d.gc[g].phase != phase) return;
+  const GelInfo& G = d.gi[g];
+  const Box b = ind_box(d, tab, k, swept != 0);
+  const double ic = 1.0 / G.cell;
+  const int c = pack_cell(cell_of(b.lo[0], G.org[0], ic), cell_of(b.lo[1], G.org[1], ic),
+                          cell_of(b.lo[2], G.org[2], ic));
+  d.pbox[2 * i] = make_double4_32a(b.lo[0], b.lo[1], b.lo[2], __longlong_as_double((long long)c));
+  d.pbox[2 * i + 1] = make_double4_32a(b.hi[0], b.hi[1], b.hi[2], 0.0);
+}
+
 // ---------------------------------------------------------------- hash build (one CTA per table)
 constexpr int HB_THREADS = 256;
 
@@ -137,11 +174,18 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
   if (threadIdx.x == 0) s_brute = 0;
   for (int b = threadIdx.x; b <= nb; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
+  Box all;  // the indenter's bounding box (vertex table only)
+  box_init(all);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const Box bx = ind_box(d, tab, p0 + k, swept != 0);
-    const int x0 = cell_of(bx.lo[0], G.org[0], ic), x1 = cell_of(bx.hi[0], G.org[0], ic);
-    const int y0 = cell_of(bx.lo[1], G.org[1], ic), y1 = cell_of(bx.hi[1], G.org[1], ic);
-    const int z0 = cell_of(bx.lo[2], G.org[2], ic), z1 = cell_of(bx.hi[2], G.org[2], ic);
+    int c0;
+    const Box bx = load_pbox(d, tab, p0 + k, &c0);
+    for (int c = 0; c < 3; ++c) {
+      all.lo[c] = fmin(all.lo[c], bx.lo[c]);
+      all.hi[c] = fmax(all.hi[c], bx.hi[c]);
+    }
+    const int x0 = c0 & HMAXC, x1 = cell_of(bx.hi[0], G.org[0], ic);
+    const int y0 = (c0 >> 10) & HMAXC, y1 = cell_of(bx.hi[1], G.org[1], ic);
+    const int z0 = c0 >> 20, z1 = cell_of(bx.hi[2], G.org[2], ic);
     if ((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1) > BUILD_CELL_LIMIT) {
       s_brute = 1;
       continue;
@@ -150,19 +194,28 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
       for (int iy = y0; iy <= y1; ++iy)
         for (int ix = x0; ix <= x1; ++ix) atomicAdd(&cnt[hash_cell(ix, iy, iz) & (nb - 1)], 1);
   }
-  if (tab == 1 && threadIdx.x == 0) {  // the indenter's bounding box (all its vertices)
-    Box all;
-    box_init(all);
-    for (int k = 0; k < n; ++k) {
-      const Box bx = ind_box(d, 1, p0 + k, swept != 0);
-      for (int c = 0; c < 3; ++c) {
-        all.lo[c] = fmin(all.lo[c], bx.lo[c]);
-        all.hi[c] = fmax(all.hi[c], bx.hi[c]);
-      }
-    }
+  if (tab == 1) {  // min / max are exact: any reduction order gives the same box
+    __shared__ double s_box[HB_THREADS / 32][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = 0; c < 3; ++c) {
-      d.gv[g].ibox_lo[c] = all.lo[c];
-      d.gv[g].ibox_hi[c] = all.hi[c];
+      all.lo[c] = warp_min(all.lo[c]);
+      all.hi[c] = warp_max(all.hi[c]);
+    }
+    if (lane == 0)
+      for (int c = 0; c < 3; ++c) {
+        s_box[wid][c] = all.lo[c];
+        s_box[wid][3 + c] = all.hi[c];
+      }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int c = threadIdx.x;
+      double lo = s_box[0][c], hi = s_box[0][3 + c];
+      for (int w = 1; w < HB_THREADS / 32; ++w) {
+        lo = fmin(lo, s_box[w][c]);
+        hi = fmax(hi, s_box[w][3 + c]);
+      }
+      d.gv[g].ibox_lo[c] = lo;
+      d.gv[g].ibox_hi[c] = hi;
     }
   }
   __syncthreads();
@@ -204,10 +257,11 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
   for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = start[b];
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const Box bx = ind_box(d, tab, p0 + k, swept != 0);
-    const int x0 = cell_of(bx.lo[0], G.org[0], ic), x1 = cell_of(bx.hi[0], G.org[0], ic);
-    const int y0 = cell_of(bx.lo[1], G.org[1], ic), y1 = cell_of(bx.hi[1], G.org[1], ic);
-    const int z0 = cell_of(bx.lo[2], G.org[2], ic), z1 = cell_of(bx.hi[2], G.org[2], ic);
+    int c0;
+    const Box bx = load_pbox(d, tab, p0 + k, &c0);
+    const int x0 = c0 & HMAXC, x1 = cell_of(bx.hi[0], G.org[0], ic);
+    const int y0 = (c0 >> 10) & HMAXC, y1 = cell_of(bx.hi[1], G.org[1], ic);
+    const int z0 = c0 >> 20, z1 = cell_of(bx.hi[2], G.org[2], ic);
     for (int iz = z0; iz <= z1; ++iz)
       for (int iy = y0; iy <= y1; ++iy)
         for (int ix = x0; ix <= x1; ++ix) {
@@ -240,7 +294,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
 __global__ void k_query(Dev d, int phase, int mode) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.nq) return;
-  const bool write = mode & 1, gsw = (mode >> 1) & 1, isw = (mode >> 2) & 1, skc = (mode >> 3) & 1;
+  // indenter boxes (swept or not, bit 2) were stored by the last hash build of the gel
+  const bool write = mode & 1, gsw = (mode >> 1) & 1, skc = (mode >> 3) & 1;
   const int g = d.q_gel[q];
   if (d.gc[g].phase != phase) return;
   if (skc && d.gv[g].converged) return;
@@ -279,7 +334,8 @@ __global__ void k_query(Dev d, int phase, int mode) {
     const int n = tab == 0 ? G.nit : (tab == 1 ? G.niv : G.nie);
     const int p0 = tab == 0 ? G.it0 : (tab == 1 ? G.iv0 : G.ie0);
     for (int k = 0; k < n; ++k) {
-      const Box pb = ind_box(d, tab, p0 + k, isw);
+      int c0;
+      const Box pb = load_pbox(d, tab, p0 + k, &c0);
       if (near_boxes(qb, pb, pad)) emit(p0 + k);
     }
   } else {
@@ -293,9 +349,9 @@ __global__ void k_query(Dev d, int phase, int mode) {
           for (int m = s; m < e; ++m) {
             const int2 ent = d.hent[he + m];
             if (ent.y != key) continue;
-            const Box pb = ind_box(d, tab, ent.x, isw);
-            const int px = cell_of(pb.lo[0], G.org[0], ic), py = cell_of(pb.lo[1], G.org[1], ic),
-                      pz = cell_of(pb.lo[2], G.org[2], ic);
+            int c0;
+            const Box pb = load_pbox(d, tab, ent.x, &c0);
+            const int px = c0 & HMAXC, py = (c0 >> 10) & HMAXC, pz = c0 >> 20;
             if (ix != max(lo[0], px) || iy != max(lo[1], py) || iz != max(lo[2], pz)) continue;
             if (!near_boxes(qb, pb, pad)) continue;
             emit(ent.x);
@@ -341,8 +397,14 @@ __device__ __forceinline__ size_t val_addr(int bp, int e) {
   return (size_t)9 * (bp & ~31) + 32 * e + (bp & 31);
 }
 
+// Contact assembly, part 1: one thread per candidate slot.  Active pairs (d < dhat) add their
+// barrier gradient and the contact force; a pair whose value depends on a single gel point adds
+// its projected block in closed form (the Hessian of b(d(P)) in the one free point is
+// b'' u u^T + b' grad^2 d with u = grad d, grad^2 d PSD and orthogonal to u, b' < 0, so the
+// projection keeps max(b'', 0) u u^T); pairs with two or three free gel points are listed for
+// the warp kernel below.
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_contact_assemble(Dev d, int phase) {
+__global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.npslots) return;
   int4 pr;
@@ -352,52 +414,111 @@ __global__ void __launch_bounds__(128) k_contact_assemble(Dev d, int phase) {
   double P[4][3];
   int rows[4];
   pair_points(d, pr, 0.0, false, P, rows);
-  const int kind = pr.x == PAIR_EE ? 1 : 0;
-  double b, gr[12], H[144], bpp, gD[12];
-  int inv = 0;
-  if (!pair_barrier_derivs(kind, P, G.dhat, pair_eps_x(d, pr), &b, gr, H, nullptr, &inv, &bpp, gD)) return;
+  PairBarrier pb;
+  if (!pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), pb)) return;
   atomicAdd(&d.gv[g].active_pairs, 1);
   const double kap = G.kappa;
-  // gel points the barrier depends on; all other rows/columns of the block are zero
   int slots[4], ns = 0;
   for (int k = 0; k < 4; ++k)
-    if (rows[k] >= 0 && (inv >> k) & 1) slots[ns++] = k;
-  const int nf = 3 * ns;
-  double Hf[81];
-  if (ns == 1) {
-    // one free point: closed-form projection kappa b''(d) u u^T
-    double H3[9];
-    single_point_block(bpp, gD + 3 * slots[0], H3);
-    for (int e = 0; e < 9; ++e) Hf[e] = kap * H3[e];
-  } else if (ns > 1) {
-    for (int a = 0; a < nf; ++a)
-      for (int c = 0; c < nf; ++c)
-        Hf[a * nf + c] = kap * H[(3 * slots[a / 3] + a % 3) * 12 + 3 * slots[c / 3] + c % 3];
-    psd_clamp(nf, Hf);
-  }
+    if (rows[k] >= 0 && (pb.involved >> k) & 1) slots[ns++] = k;
   for (int a = 0; a < ns; ++a) {
     const int ra = rows[slots[a]];
-    for (int c = 0; c < 3; ++c) atomicAdd(&d.gv[g].fc[c], -kap * gr[3 * slots[a] + c]);
-    if (d.fixed[ra]) continue;
-    atomicAdd(&d.grad[ra].x, kap * gr[3 * slots[a] + 0]);
-    atomicAdd(&d.grad[ra].y, kap * gr[3 * slots[a] + 1]);
-    atomicAdd(&d.grad[ra].z, kap * gr[3 * slots[a] + 2]);
-    for (int c = 0; c < ns; ++c) {
-      const int rc = rows[slots[c]];
-      if (d.fixed[rc]) continue;
-      const int bp = find_block(d, ra, rc);
-      if (bp < 0) {
-        atomicOr(&d.gv[g].flags, 16);
-        continue;
-      }
-      for (int e = 0; e < 9; ++e) {
-        const double v = Hf[(3 * a + e / 3) * nf + 3 * c + e % 3];
-        if (MIXED)
-          atomicAdd(&d.vals32[val_addr(bp, e)], (float)v);
-        else
-          atomicAdd(&d.vals[val_addr(bp, e)], v);
-      }
+    double gr[3];
+    for (int c = 0; c < 3; ++c) {
+      gr[c] = kap * pair_grad_entry(pb, 3 * slots[a] + c);
+      atomicAdd(&d.gv[g].fc[c], -gr[c]);
     }
+    if (d.fixed[ra]) continue;
+    atomicAdd(&d.grad[ra].x, gr[0]);
+    atomicAdd(&d.grad[ra].y, gr[1]);
+    atomicAdd(&d.grad[ra].z, gr[2]);
+  }
+  if (ns == 1) {
+    const int ra = rows[slots[0]];
+    if (d.fixed[ra]) return;
+    const double dd = sqrt(pb.dv.D), r = dd - G.dhat;
+    const double bpp = -2.0 * log(dd / G.dhat) - 4.0 * r / dd + r * r / (dd * dd);
+    double H3[9];
+    single_point_block(bpp, pb.gDp + 3 * slots[0], H3);
+    const int bp = d.diag_pos[ra];
+    for (int e = 0; e < 9; ++e) {
+      if (MIXED)
+        atomicAdd(&d.vals32[val_addr(bp, e)], (float)(kap * H3[e]));
+      else
+        atomicAdd(&d.vals[val_addr(bp, e)], kap * H3[e]);
+    }
+  } else if (ns > 1) {
+    d.cwork[atomicAdd(d.cwork_n, 1)] = i;
+  }
+}
+
+// Contact assembly, part 2: one warp per listed pair.  The lanes form the barrier Hessian block
+// on the pair's free gel points entry by entry, the warp projects it to PSD, and the lanes add it
+// to the sliced BSR.
+constexpr int CW_WARPS = 4;
+
+struct ContactWS {
+  PairBarrier pb;
+  ProjWS pj;
+  double P[4][3];
+  int rows[4], slots[4], bp[16];
+  int ns, g;
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d) {
+  __shared__ ContactWS sws[CW_WARPS];
+  ContactWS& w = sws[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int n = *d.cwork_n;
+  for (int k = blockIdx.x * CW_WARPS + (threadIdx.x >> 5); k < n; k += gridDim.x * CW_WARPS) {
+    const int i = d.cwork[k];
+    if (lane == 0) {
+      const int4 pr = d.pairs[i];
+      pair_points(d, pr, 0.0, false, w.P, w.rows);
+      const GelInfo& G = d.gi[pr.w];
+      pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, w.P, G.dhat, pair_eps_x(d, pr), w.pb);
+      int ns = 0;
+      for (int q = 0; q < 4; ++q)
+        if (w.rows[q] >= 0 && (w.pb.involved >> q) & 1) w.slots[ns++] = q;
+      w.ns = ns;
+      w.g = pr.w;
+    }
+    __syncwarp();
+    const int ns = w.ns, nf = 3 * ns, m = nf + (nf & 1);
+    for (int e = lane; e < m * m; e += 32) {
+      const int r = e / m, c = e - r * m;
+      const int a = r < c ? r : c, b = r < c ? c : r;  // same formula order for (r, c) and (c, r)
+      double v = 0.0;
+      if (b < nf) v = pair_hess_entry(w.pb, 3 * w.slots[a / 3] + a % 3, 3 * w.slots[b / 3] + b % 3);
+      w.pj.H[e] = v;
+    }
+    __syncwarp();
+    warp_psd_project(w.pj, nf, lane);
+    const int g = w.g;
+    if (lane < ns * ns) {
+      const int a = lane / ns, c = lane - a * ns;
+      const int ra = w.rows[w.slots[a]], rc = w.rows[w.slots[c]];
+      int bp = -1;
+      if (!d.fixed[ra] && !d.fixed[rc]) {
+        bp = find_block(d, ra, rc);
+        if (bp < 0) atomicOr(&d.gv[g].flags, 16);
+      }
+      w.bp[lane] = bp;
+    }
+    __syncwarp();
+    const double kap = d.gi[g].kappa;
+    for (int e = lane; e < nf * nf; e += 32) {
+      const int r = e / nf, c = e - r * nf;
+      const int bp = w.bp[(r / 3) * ns + c / 3];
+      if (bp < 0) continue;
+      const double v = kap * w.pj.H[r * m + c];
+      if (MIXED)
+        atomicAdd(&d.vals32[val_addr(bp, 3 * (r % 3) + c % 3)], (float)v);
+      else
+        atomicAdd(&d.vals[val_addr(bp, 3 * (r % 3) + c % 3)], v);
+    }
+    __syncwarp();
   }
 }
 
@@ -455,41 +576,91 @@ __global__ void k_min_dist(Dev d, int phase) {
   if (D < d.gi[g].dhat * d.gi[g].dhat) atomicAdd(&d.gv[g].active_pairs, 1);
 }
 
-// ---------------------------------------------------------------- unit-level entries
-__global__ void k_eval_pairs(int n, const int* kind, const double* Pin, double dhat, const double* eps_x,
-                             const int* free_mask, double* bo, double* go, double* Ho, int* dtype) {
+// kappa b(d) of every candidate pair at x + alpha p (mode 1: line-search trial of the gels still
+// searching, alpha = their trial step; otherwise alpha = 0), one thread per pair slot; the energy
+// kernel sums a gel's slots in a fixed order
+__global__ void __launch_bounds__(128) k_pair_energy(Dev d, int phase, int mode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= d.npslots) return;
+  const int g = d.pslot_gel[i];
+  if (d.gc[g].phase != phase) return;
+  if (mode == 1 && (d.gv[g].ls_state != 0 || d.gv[g].converged)) return;
+  const GelInfo& G = d.gi[g];
+  if (i - G.pbase >= min(d.gv[g].npair, G.pcap)) return;
+  const int4 pr = d.pairs[i];
+  const double alpha = mode == 1 ? d.gv[g].alpha : 0.0;
   double P[4][3];
-  for (int k = 0; k < 4; ++k)
-    for (int c = 0; c < 3; ++c) P[k][c] = Pin[12 * i + 3 * k + c];
-  double b = 0.0, g[12], H[144];
-  for (int k = 0; k < 12; ++k) g[k] = 0.0;
-  for (int k = 0; k < 144; ++k) H[k] = 0.0;
-  DType ty;
-  const bool act = pair_barrier_derivs(kind[i], P, dhat, eps_x ? eps_x[i] : 0.0, &b, g, H, &ty);
-  if (dtype) {
-    dtype[5 * i] = ty.f;
-    for (int k = 0; k < 4; ++k) dtype[5 * i + 1 + k] = ty.i[k];
+  int rows[4];
+  pair_points(d, pr, alpha, false, P, rows);
+  double dist;
+  d.pe[i] = G.kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+}
+
+void launch_pair_energy(const Dev& d, int phase, int mode, cudaStream_t st) {
+  if (d.npslots > 0) {
+    k_pair_energy<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode);
+    count_launch(1);
   }
-  const int fm = free_mask ? free_mask[i] : 0;
-  if (act && fm) {
-    int idx[12], nf = 0;
+}
+
+// ---------------------------------------------------------------- unit-level entries
+// unit-level entry: one warp per pair (the same lane-parallel derivatives and projection as the
+// assembly), full 12 x 12 Hessian with the free block projected
+struct EvalWS {
+  PairBarrier pb;
+  ProjWS pj;
+  double P[4][3];
+  int act, nf;
+  int fd[PW_MAXN];
+};
+
+__global__ void __launch_bounds__(128) k_eval_pairs(int n, const int* kind, const double* Pin, double dhat,
+                                                    const double* eps_x, const int* free_mask, double* bo,
+                                                    double* go, double* Ho, int* dtype) {
+  __shared__ EvalWS sws[4];
+  EvalWS& w = sws[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (i >= n) return;  // whole warps
+  if (lane == 0) {
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) w.P[k][c] = Pin[12 * i + 3 * k + c];
+    DType ty;
+    w.act = pair_barrier_setup(kind[i], w.P, dhat, eps_x ? eps_x[i] : 0.0, w.pb, &ty) ? 1 : 0;
+    if (dtype) {
+      dtype[5 * i] = ty.f;
+      for (int k = 0; k < 4; ++k) dtype[5 * i + 1 + k] = ty.i[k];
+    }
+    const int fm = free_mask ? free_mask[i] : 0;
+    int nf = 0;
     for (int k = 0; k < 4; ++k)
       if (fm & (1 << k))
-        for (int c = 0; c < 3; ++c) idx[nf++] = 3 * k + c;
-    double S[81];
-    for (int a = 0; a < nf; ++a)
-      for (int c = 0; c < nf; ++c) S[a * nf + c] = H[idx[a] * 12 + idx[c]];
-    psd_clamp(nf, S);
-    for (int a = 0; a < nf; ++a)
-      for (int c = 0; c < nf; ++c) H[idx[a] * 12 + idx[c]] = S[a * nf + c];
+        for (int c = 0; c < 3; ++c) w.fd[nf++] = 3 * k + c;
+    w.nf = nf;
+    bo[i] = w.act ? w.pb.b : 0.0;
   }
-  bo[i] = b;
-  if (go)
-    for (int k = 0; k < 12; ++k) go[12 * i + k] = g[k];
+  __syncwarp();
+  const bool act = w.act != 0;
+  if (go && lane < 12) go[12 * i + lane] = act ? pair_grad_entry(w.pb, lane) : 0.0;
   if (Ho)
-    for (int k = 0; k < 144; ++k) Ho[144 * i + k] = H[k];
+    for (int e = lane; e < 144; e += 32) {
+      const int r = e / 12, c = e - r * 12;
+      Ho[144 * (size_t)i + e] = act ? pair_hess_entry(w.pb, r < c ? r : c, r < c ? c : r) : 0.0;
+    }
+  const int nf = w.nf;
+  if (!act || nf == 0 || !Ho) return;
+  const int m = nf + (nf & 1);
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const int a = r < c ? r : c, b = r < c ? c : r;
+    w.pj.H[e] = b < nf ? pair_hess_entry(w.pb, w.fd[a], w.fd[b]) : 0.0;
+  }
+  __syncwarp();
+  warp_psd_project(w.pj, nf, lane);
+  for (int e = lane; e < nf * nf; e += 32) {
+    const int r = e / nf, c = e - r * nf;
+    Ho[144 * (size_t)i + 12 * w.fd[r] + w.fd[c]] = w.pj.H[r * m + c];
+  }
 }
 
 __global__ void k_eval_accd(int n, const int* kind, const double* Pin, const double* dPin, double s,
@@ -508,7 +679,6 @@ __global__ void k_eval_accd(int n, const int* kind, const double* Pin, const dou
 }
 
 // ---------------------------------------------------------------- launchers
-static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t st) {
   if (n_ind_verts > 0) {
@@ -517,6 +687,11 @@ void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t
   }
 }
 void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st) {
+  const int np = d.nit_total + d.niv_total + d.nie_total;
+  if (np > 0) {
+    k_ind_boxes<<<nblk(np, 128), 128, 0, st>>>(d, phase, swept);
+    count_launch(1);
+  }
   k_hash_build<<<d.n_gels * NTAB, HB_THREADS, 0, st>>>(d, phase, swept);
   count_launch(1);
 }
@@ -532,11 +707,17 @@ void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st)
 }
 void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   if (d.npslots <= 0) return;
-  if (mixed)
-    k_contact_assemble<true><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
-  else
-    k_contact_assemble<false><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
-  count_launch(1);
+  cudaMemsetAsync(d.cwork_n, 0, sizeof(int), st);
+  const int nb = nblk(d.npslots, 128);
+  const int nw = std::min(nblk(d.npslots, CW_WARPS), 8 * 152);
+  if (mixed) {
+    k_contact_pairs<true><<<nb, 128, 0, st>>>(d, phase);
+    k_contact_hess<true><<<nw, 32 * CW_WARPS, 0, st>>>(d);
+  } else {
+    k_contact_pairs<false><<<nb, 128, 0, st>>>(d, phase);
+    k_contact_hess<false><<<nw, 32 * CW_WARPS, 0, st>>>(d);
+  }
+  count_launch(2);
 }
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st) {
   if (d.npslots > 0) {
@@ -553,7 +734,7 @@ void launch_min_dist(const Dev& d, int phase, cudaStream_t st) {
 void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
                        const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st) {
   if (n > 0) {
-    k_eval_pairs<<<nblk(n, 64), 64, 0, st>>>(n, kind, P, dhat, eps_x, free_mask, b, g, H, dtype);
+    k_eval_pairs<<<nblk(n, 4), 128, 0, st>>>(n, kind, P, dhat, eps_x, free_mask, b, g, H, dtype);
     count_launch(1);
   }
 }

@@ -763,16 +763,9 @@ __global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* p
       acc += d.mass[r] * (ex * ex + ey * ey + ez * ez) * ih2;
     }
   } else {
+    // per-pair barrier energies written by k_pair_energy
     const int p0 = G.pbase, np = min(d.gv[g].npair, G.pcap);
-    for (int i = threadIdx.x; i < np; i += EN_T) {
-      const int4 pr = d.pairs[p0 + i];
-      double P[4][3];
-      int rows[4];
-      pair_points(d, pr, alpha, false, P, rows);
-      double dist;
-      const double b = pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
-      acc += G.kappa * b;
-    }
+    for (int i = threadIdx.x; i < np; i += EN_T) acc += d.pe[p0 + i];
   }
   acc = block_sum<EN_T>(acc, sm);
   if (threadIdx.x == 0) part_e[blockIdx.x] = acc;
@@ -805,8 +798,11 @@ __global__ void k_energy_reduce(Dev d, int phase, const int* gel_piece, const do
   }
 }
 
+void launch_pair_energy(const Dev& d, int phase, int mode, cudaStream_t st);
+
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
                    double* part_e, int mode, cudaStream_t st) {
+  launch_pair_energy(d, phase, mode, st);
   if (npieces > 0) {
     k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, part_e, mode);
     count_launch(1);

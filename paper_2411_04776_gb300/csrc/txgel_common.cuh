@@ -139,6 +139,10 @@ struct Dev {
   int* iv_gel;
   int* it_gel;
   int* ie_gel;
+  int nit_total, nie_total;
+  // bounding boxes of the indenter primitives [triangles | vertices | edges] at the pose of the
+  // last hash build of their gel: (lo, hi) pairs, lo.w holds the packed lowest grid cell
+  double4_32a* pbox;
   // hash
   int* hstart;     // bucket starts (global, per table segment nb + 1)
   int* hcount;     // bucket fill cursors
@@ -150,7 +154,9 @@ struct Dev {
   int4* pairs;     // (type, gel prim, indenter prim, gel), per-gel segments [pbase, pbase + pcap)
   int* pslot_gel;  // gel of every pair slot
   int npslots;
-  double* pe;      // per pair scratch (energy)
+  double* pe;      // per pair slot: kappa b(d) at the last energy evaluation
+  int* cwork;      // contact pairs with two or more free gel points (pair slots), and their count
+  int* cwork_n;
   int* err;
 };
 

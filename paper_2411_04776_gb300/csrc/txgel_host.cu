@@ -491,7 +491,9 @@ tx_status alloc_pairs(tx_batch* b) {
   }
   b->d.pairs = b->pair_mem.get<int4>(total);
   b->d.pslot_gel = b->pair_mem.get<int>(total);
-  if (!b->d.pairs || !b->d.pslot_gel) return TX_ERR_OOM;
+  b->d.pe = b->pair_mem.get<double>(total);
+  b->d.cwork = b->pair_mem.get<int>(total);
+  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork) return TX_ERR_OOM;
   b->d.npslots = total;
   std::vector<int> slot(total);
   for (int g = 0; g < b->n; ++g)
@@ -879,11 +881,15 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.iv_gel = M.get<int>(niv);
   d.it_gel = M.get<int>(nit);
   d.ie_gel = M.get<int>(nie);
+  d.nit_total = nit;
+  d.nie_total = nie;
+  d.pbox = M.get<double4_32a>(2 * ((size_t)nit + niv + nie));
   d.hstart = M.get<int>(hb);
   d.hcount = M.get<int>(hb);
   d.qcount = M.get<int>(nq + 1);
   d.qoff = M.get<int>(nq + 1);
   d.err = M.get<int>(4);
+  d.cwork_n = M.get<int>(4);
   b->pieces = M.get<int4>(b->npieces);
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
@@ -1732,7 +1738,8 @@ size_t tx_gel_footprint_bytes(const tx_gel_desc* desc) {
   bytes += nt * (16 + 72 + 8 + 4 + 64 + TS * 8 + (mixed ? TS32 * 4 : 0));
   bytes += nbp * (4 + 4 + 4 + (mixed ? 36 : 72));
   bytes += nq * (4 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;
-  bytes += (size_t)initial_pcap(m) * 20;
+  bytes += ((size_t)m.niv + m.nit + m.ie.size()) * 2 * sizeof(double4_32a);  // primitive boxes
+  bytes += (size_t)initial_pcap(m) * 32;
   return bytes;
 }
 
