@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
+    ap.add_argument("--pcg-cta-slices", type=int, default=0,
+                    help="PCG work split: 32-row slices per CTA at least (0: library default)")
     return ap.parse_args()
 
 
@@ -146,7 +148,7 @@ def run_gpu(args, rank, world):
     K, Wm = args.steps, args.warmup
     T = min(len(w.poses) for w in wls)
     assert Wm + K <= T, f"the trajectories have {T} steps"
-    descs = [B.GelDesc.from_workload(w, precision=prec) for w in wls]
+    descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=args.pcg_cta_slices) for w in wls]
     single = len(wls) == 1
     if single:
         gel = B.Gel(descs[0], stream=stream)
@@ -285,7 +287,8 @@ def run_serve(args):
     wls = make_workload("serve", args.seed, args.n_gels)
     prec = B.TX_PREC_MIXED if args.precision == "mixed" else B.TX_PREC_FP64
     t0 = time.perf_counter()
-    srv = S.GelServer(wls, args.budget_gb * 1e9, precision=prec, stream=torch.cuda.current_stream())
+    srv = S.GelServer(wls, args.budget_gb * 1e9, precision=prec, stream=torch.cuda.current_stream(),
+                      pcg_cta_slices=args.pcg_cta_slices)
     t_create = time.perf_counter() - t0
     # warm-up: every environment takes its first steps
     srv.run_schedule([list(range(srv.n))] * max(1, args.warmup))

@@ -69,7 +69,8 @@ typedef struct tx_params {
   int32_t max_split_depth;  /* infeasible indenter moves are halved up to this depth (4)       */
   int32_t precision;        /* tx_precision                                                     */
   int32_t refine_max;       /* mixed precision: max FP64 residual refinement rounds (3)         */
-  int32_t reserved;
+  int32_t pcg_cta_slices;   /* PCG work split: at least this many 32-row slices per CTA; 0 picks
+                               the default (4)                  */
 } tx_params;
 
 void tx_params_default(tx_params* p);

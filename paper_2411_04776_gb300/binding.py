@@ -34,7 +34,7 @@ class tx_params(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
                 ("ls_max_halvings", ctypes.c_int32), ("accd_max_iter", ctypes.c_int32),
                 ("max_split_depth", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("refine_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("refine_max", ctypes.c_int32), ("pcg_cta_slices", ctypes.c_int32)]
 
 
 class tx_gel_desc(ctypes.Structure):

@@ -1,0 +1,166 @@
+// Device pieces shared by the persistent PCG kernels (k_solve.cu: matrix and vectors in global
+// memory; k_pcg_res.cu: one slice per warp with the matrix in shared memory and the row vectors
+// in registers): group barrier, deterministic group sums, the solve epilogue.
+#pragma once
+#include "txgel_common.cuh"
+
+namespace txg {
+
+// ---------------------------------------------------------------- persistent PCG
+constexpr int PCG_T = 256;  // threads per CTA (8 warps)
+constexpr int PCG_MAXG = 64; // gels one CTA may touch
+
+__device__ __forceinline__ double4_32a mul3(const double* M, const double4_32a v) {
+  return make_double4_32a(fma(M[2], v.z, fma(M[1], v.y, M[0] * v.x)), fma(M[5], v.z, fma(M[4], v.y, M[3] * v.x)),
+                          fma(M[8], v.z, fma(M[7], v.y, M[6] * v.x)), 0.0);
+}
+__device__ __forceinline__ double dot4(const double4_32a a, const double4_32a b) {
+  return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x));
+}
+
+// SpMV of one slice (row = lane of the warp): y = A u, FP64.  Unrolled so that several block
+// loads (column index, 9 values, gathered vector) are in flight at once.
+__device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane, const double4_32a* u) {
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    const int c = __ldg(d.colidx + bp);
+    const double4_32a uc = u[c];
+    const double* v = d.vals + (size_t)9 * (o + 32 * k) + lane;
+    a0 = fma(v[0], uc.x, a0);
+    a1 = fma(v[96], uc.x, a1);
+    a2 = fma(v[192], uc.x, a2);
+    a0 = fma(v[32], uc.y, a0);
+    a1 = fma(v[128], uc.y, a1);
+    a2 = fma(v[224], uc.y, a2);
+    a0 = fma(v[64], uc.z, a0);
+    a1 = fma(v[160], uc.z, a1);
+    a2 = fma(v[256], uc.z, a2);
+  }
+  return make_double4_32a(a0, a1, a2, 0.0);
+}
+
+// Barrier of the nc CTAs of one group (all co-resident: cooperative launch).  Arrival is a
+// release add on the group's counter, the wait an acquire poll bounded by a spin limit; a wait
+// that gives up sets *err and the CTA returns false (the host reports a device timeout).
+__device__ __forceinline__ bool group_barrier(unsigned* cnt, int nc, unsigned& epoch, int* err, int* s_fail) {
+  __syncthreads();
+  epoch += 1;
+  if (nc > 1 && threadIdx.x == 0) {
+    const unsigned target = epoch * (unsigned)nc;
+    __threadfence();
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
+    unsigned spins = 0, cur;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(cnt) : "memory");
+      if (cur >= target) break;
+      if (++spins > (1u << 22)) {
+        atomicExch(err, 1);
+        *s_fail = 1;
+        break;
+      }
+      __nanosleep(20);
+    }
+  }
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+// Per-CTA view of its group (gels [g0, g0 + ng), CTAs [c0, c0 + nc)).  A group of several CTAs
+// holds a single gel; a group of one CTA may hold several small gels.
+struct PcgCta {
+  int s0, s1;  // slices of this CTA
+  int c0, nc, g0, ng;
+  unsigned* bar;
+  unsigned epoch;
+};
+
+__device__ __forceinline__ PcgCta pcg_cta(const Dev& d, const PcgPlan& plan) {
+  PcgCta c;
+  c.s0 = plan.cta_s0[blockIdx.x];
+  c.s1 = plan.cta_s0[blockIdx.x + 1];
+  const int gr = plan.cta_grp[blockIdx.x];
+  const int4 G = plan.grp[gr];
+  c.c0 = G.x;
+  c.nc = G.y;
+  c.g0 = G.z;
+  c.ng = G.w;
+  c.bar = d.bar + gr;
+  c.epoch = 0;
+  return c;
+}
+
+// Group totals of quantities [k0, k1) from the per-slice partials dsm[(s - s0) * 4 + k]: every
+// CTA sums its slices of each gel (one warp per (gel, quantity), fixed lane order); a group of
+// several CTAs (one gel) exchanges the CTA sums through d.part and every CTA adds them up in CTA
+// order.  Bitwise identical in every CTA of the group and in every run.  Includes the group
+// barrier between the two levels.
+__device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double* dsm, int k0, int k1,
+                                          double (*tot)[4], int* s_fail) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nk = k1 - k0;
+  for (int t = wid; t < c.ng * nk; t += (int)(blockDim.x >> 5)) {
+    const int j = t / nk, k = k0 + t % nk;
+    const GelInfo& G = d.gi[c.g0 + j];
+    const int a = max(c.s0, G.s0), b = min(c.s1, G.s0 + G.ns);
+    double v = 0.0;
+    for (int s = a + lane; s < b; s += 32) v += dsm[(s - c.s0) * 4 + k];
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (c.nc == 1)
+        tot[j][k] = v;
+      else
+        d.part[(size_t)k * gridDim.x + blockIdx.x] = v;
+    }
+  }
+  if (c.nc > 1) {
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, s_fail)) return false;
+    for (int t = wid; t < nk; t += (int)(blockDim.x >> 5)) {
+      const int k = k0 + t;
+      double v = 0.0;
+      for (int q = c.c0 + lane; q < c.c0 + c.nc; q += 32) v += d.part[(size_t)k * gridDim.x + q];
+      v = warp_sum(v);
+      if (lane == 0) tot[0][k] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// g . p (stationarity test of the line search) and ||p||_inf per gel after a solve
+__device__ __forceinline__ void pcg_epilogue(const Dev& d, const PcgPlan& plan, PcgCta& c, double* dsm,
+                                             double (*tot)[4], const int* gact, int* s_fail) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, s_fail)) return;  // p complete, exchange slots free
+  for (int s = c.s0 + wid; s < c.s1; s += (int)(blockDim.x >> 5)) {
+    const int j = plan.slice_gel[s] - c.g0;
+    double gp = 0.0, m = 0.0;
+    if (gact[j]) {
+      const double4_32a x = d.p[32 * s + lane];
+      gp = dot4(d.grad[32 * s + lane], x);
+      m = fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z)));
+    }
+    gp = warp_sum(gp);
+    m = warp_max(m);
+    if (lane == 0) {
+      dsm[(s - c.s0) * 4 + 3] = gp;
+      if (gact[j]) atomic_max_pos(&d.gv[c.g0 + j].pnorm_bits, m);
+    }
+  }
+  if (!group_sum(d, c, dsm, 3, 4, tot, s_fail)) return;
+  if (blockIdx.x == c.c0)
+    for (int j = threadIdx.x; j < c.ng; j += blockDim.x)
+      if (gact[j]) d.gv[c.g0 + j].gtp = tot[j][3];
+}
+
+
+__device__ __forceinline__ float4 mul3f(const float* M, const float4 v) {
+  return make_float4(fmaf(M[2], v.z, fmaf(M[1], v.y, M[0] * v.x)), fmaf(M[5], v.z, fmaf(M[4], v.y, M[3] * v.x)),
+                     fmaf(M[8], v.z, fmaf(M[7], v.y, M[6] * v.x)), 0.f);
+}
+__device__ __forceinline__ float dot4f(const float4 a, const float4 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
+
+
+}  // namespace txg

@@ -13,6 +13,7 @@
 //     takes the line-search decision (accept on E <= E_cur, else halve alpha).
 #include "dev_contact.cuh"
 #include "dev_elastic.cuh"
+#include "dev_pcg.cuh"
 
 namespace txg {
 
@@ -202,91 +203,27 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   count_launch(1);
 }
 
-// ---------------------------------------------------------------- persistent PCG
-constexpr int PCG_T = 256;  // threads per CTA (8 warps)
-constexpr int PCG_MAXG = 64; // gels one CTA may touch
-
-
-__device__ __forceinline__ double4_32a mul3(const double* M, const double4_32a v) {
-  return make_double4_32a(fma(M[2], v.z, fma(M[1], v.y, M[0] * v.x)), fma(M[5], v.z, fma(M[4], v.y, M[3] * v.x)),
-                          fma(M[8], v.z, fma(M[7], v.y, M[6] * v.x)), 0.0);
-}
-__device__ __forceinline__ double dot4(const double4_32a a, const double4_32a b) {
-  return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x));
-}
-
-// SpMV of one slice (row = lane of the warp): y = A u, FP64.  Unrolled so that several block
-// loads (column index, 9 values, gathered vector) are in flight at once.
-__device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane, const double4_32a* u) {
-  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-#pragma unroll 4
-  for (int k = 0; k < w; ++k) {
-    const int bp = o + 32 * k + lane;
-    const int c = __ldg(d.colidx + bp);
-    const double4_32a uc = u[c];
-    const double* v = d.vals + (size_t)9 * (o + 32 * k) + lane;
-    a0 = fma(v[0], uc.x, a0);
-    a1 = fma(v[96], uc.x, a1);
-    a2 = fma(v[192], uc.x, a2);
-    a0 = fma(v[32], uc.y, a0);
-    a1 = fma(v[128], uc.y, a1);
-    a2 = fma(v[224], uc.y, a2);
-    a0 = fma(v[64], uc.z, a0);
-    a1 = fma(v[160], uc.z, a1);
-    a2 = fma(v[256], uc.z, a2);
-  }
-  return make_double4_32a(a0, a1, a2, 0.0);
-}
-
-// Reduction slots: slice partials of one CTA (dynamic shared memory, 4 per slice) are summed per
-// gel the CTA touches into one slot per (CTA, gel); the slots of a gel are contiguous, so every
-// CTA forms a gel's total by summing that short range.  Both sums run one warp per (gel, quantity)
-// with a fixed lane assignment: bitwise identical in every CTA and run.
-__device__ __forceinline__ void cta_reduce(const Dev& d, const PcgPlan& plan, const double* dsm, int s0,
-                                           int s1, int g0, int ng, int slot0, int k0, int k1) {
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nk = k1 - k0;
-  for (int t = wid; t < ng * nk; t += PCG_T / 32) {
-    const int j = t / nk, k = k0 + t % nk;
-    const GelInfo& G = d.gi[g0 + j];
-    const int a = max(s0, G.s0), b = min(s1, G.s0 + G.ns);
-    double v = 0.0;
-    for (int s = a + lane; s < b; s += 32) v += dsm[(s - s0) * 4 + k];
-    v = warp_sum(v);
-    if (lane == 0) d.part[(size_t)k * plan.nslots + slot0 + j] = v;
-  }
-}
-
-__device__ __forceinline__ void gel_totals(const Dev& d, const PcgPlan& plan, int g0, int ng, int nk,
-                                           double (*tot)[4]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t = wid; t < ng * nk; t += PCG_T / 32) {
-    const int j = t / nk, k = t % nk;
-    const int a = plan.gel_slot[2 * (g0 + j)], b = plan.gel_slot[2 * (g0 + j) + 1];
-    double v = 0.0;
-    for (int q = a + lane; q < b; q += 32) v += d.part[(size_t)k * plan.nslots + q];
-    v = warp_sum(v);
-    if (lane == 0) tot[j][k] = v;
-  }
-  __syncthreads();
-}
-
+// One projected-Newton direction per gel of the gels in `phase`: block-Jacobi preconditioned CG
+// on H p = -g (Chronopoulos-Gear: one reduction phase per iteration), FP64, stops per gel when
+// |r| <= eta |g| or after maxit iterations.
 __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, double eta2, int maxit) {
   extern __shared__ double dsm[];  // [slices of this CTA][4]
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG];
-  __shared__ int s_exit;
+  __shared__ double bbj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
+  __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s0 = plan.cta_s0[blockIdx.x], s1 = plan.cta_s0[blockIdx.x + 1];
-  const int g0 = plan.cta_g0[blockIdx.x], ng = plan.cta_ng[blockIdx.x];
-  const int slot0 = plan.cta_slot0[blockIdx.x];
-  unsigned epoch = 0;
+  PcgCta c = pcg_cta(d, plan);
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
+    run[j] = gact[j];
+  }
+  __syncthreads();
   // ---- init: r = -grad, x = 0, u = M^-1 r, pp = s = 0; partial |b|^2
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
     double bb = 0.0;
-    if (d.gc[g].phase == phase) {
+    if (gact[plan.slice_gel[s] - c.g0]) {
       const int r = 32 * s + lane;
       const double4_32a gr = d.grad[r];
       const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
@@ -299,17 +236,16 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
       bb = dot4(b, b);
     }
     bb = warp_sum(bb);
-    if (lane == 0) dsm[(s - s0) * 4 + 3] = bb;
+    if (lane == 0) dsm[(s - c.s0) * 4 + 3] = bb;
   }
-  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 3, 4);
-  if (!grid_barrier(d.bar, epoch, d.err)) return;
-  int k = 0;
-  while (true) {
-    // ---- Y: w = A u, partials gamma = (r,u), delta = (w,u), rr = (r,r)
-    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-      const int g = plan.slice_gel[s];
+  if (!group_sum(d, c, dsm, 3, 4, tot, &s_fail)) return;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) bbj[j] = tot[j][3];
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;  // u complete before the SpMV
+  for (int k = 1;; ++k) {
+    // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
       double ga = 0.0, de = 0.0, rr = 0.0;
-      if (d.gc[g].phase == phase && !d.gv[g].pcg_done) {
+      if (run[plan.slice_gel[s] - c.g0]) {
         const int r = 32 * s + lane;
         double4_32a w = spmv_row64(d, s, lane, d.u);
         if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
@@ -323,98 +259,58 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
       de = warp_sum(de);
       rr = warp_sum(rr);
       if (lane == 0) {
-        dsm[(s - s0) * 4 + 0] = ga;
-        dsm[(s - s0) * 4 + 1] = de;
-        dsm[(s - s0) * 4 + 2] = rr;
+        dsm[(s - c.s0) * 4 + 0] = ga;
+        dsm[(s - c.s0) * 4 + 1] = de;
+        dsm[(s - c.s0) * 4 + 2] = rr;
       }
     }
-    cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 3);
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.act[(k + 1) & 1] = 0;
-    if (!grid_barrier(d.bar, epoch, d.err)) return;
-    k += 1;
-    // ---- X: per-gel scalars, convergence, vector updates
-    gel_totals(d, plan, g0, ng, k == 1 ? 4 : 3, tot);
-    if (k == 1) {
-      for (int j = threadIdx.x; j < ng; j += PCG_T) bbj[j] = tot[j][3];
-      __syncthreads();
-    }
-    int my_active = 0;
-    for (int j = 0; j < ng; ++j) {
-      const int g = g0 + j;
-      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
-      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2], bb = bbj[j];
-      const bool conv = !(rr > eta2 * bb) || k > maxit;
-      if (conv) {
-        // every CTA touching g reaches the same decision in this iteration
-        if (threadIdx.x == 0) {
-          d.gv[g].pcg_it = k - 1;
-          d.gv[g].bb = bb;
-          d.gv[g].pcg_done = 1;
+    if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
+    // ---- per-gel scalars and convergence (identical in every CTA of the group)
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+      if (!run[j]) continue;
+      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
+      if (!(rr > eta2 * bbj[j]) || k > maxit) {
+        run[j] = 0;
+        if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + j].pcg_it = k - 1;
+          d.gv[c.g0 + j].bb = bbj[j];
+          d.gv[c.g0 + j].pcg_done = 1;
         }
         continue;
       }
-      ++my_active;
-      const int par = k & 1, prv = (k - 1) & 1;
-      double beta, alpha;
-      if (k == 1) {
-        beta = 0.0;
-        alpha = ga / de;
-      } else {
-        const double gprev = d.gsc[(size_t)(prv * 4 + 0) * d.n_gels + g];
-        const double aprev = d.gsc[(size_t)(prv * 4 + 1) * d.n_gels + g];
-        beta = ga / gprev;
-        alpha = ga / (de - beta * ga / aprev);
-      }
-      if (threadIdx.x == 0) {
-        d.gsc[(size_t)(par * 4 + 0) * d.n_gels + g] = ga;
-        d.gsc[(size_t)(par * 4 + 1) * d.n_gels + g] = alpha;
-      }
-      const GelInfo& G = d.gi[g];
-      const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
-      for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
-        const int r = 32 * s + lane;
-        const double4_32a u = d.u[r], w = d.w[r];
-        double4_32a pp = d.pp[r], sv = d.s[r], x = d.p[r], rv = d.r[r];
-        pp.x = u.x + beta * pp.x; pp.y = u.y + beta * pp.y; pp.z = u.z + beta * pp.z;
-        sv.x = w.x + beta * sv.x; sv.y = w.y + beta * sv.y; sv.z = w.z + beta * sv.z;
-        x.x += alpha * pp.x; x.y += alpha * pp.y; x.z += alpha * pp.z;
-        rv.x -= alpha * sv.x; rv.y -= alpha * sv.y; rv.z -= alpha * sv.z;
-        d.pp[r] = pp;
-        d.s[r] = sv;
-        d.p[r] = x;
-        d.r[r] = rv;
-        d.u[r] = mul3(d.Minv + 9 * r, rv);
-      }
+      s_any = 1;
+      const double beta = k == 1 ? 0.0 : ga / gprev[j];
+      const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
+      gprev[j] = ga;
+      aprev[j] = alpha;
+      alj[j] = alpha;
+      bej[j] = beta;
     }
-    if (threadIdx.x == 0 && my_active) atomicAdd(&d.act[k & 1], my_active);
-    if (!grid_barrier(d.bar, epoch, d.err)) return;
-    if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[k & 1]) == 0);
     __syncthreads();
-    if (s_exit) break;
+    if (!s_any) break;
+    // ---- vector updates
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      const int j = plan.slice_gel[s] - c.g0;
+      if (!run[j]) continue;
+      const double beta = bej[j], alpha = alj[j];
+      const int r = 32 * s + lane;
+      const double4_32a u = d.u[r], w = d.w[r];
+      double4_32a pp = d.pp[r], sv = d.s[r], x = d.p[r], rv = d.r[r];
+      pp.x = fma(beta, pp.x, u.x); pp.y = fma(beta, pp.y, u.y); pp.z = fma(beta, pp.z, u.z);
+      sv.x = fma(beta, sv.x, w.x); sv.y = fma(beta, sv.y, w.y); sv.z = fma(beta, sv.z, w.z);
+      x.x = fma(alpha, pp.x, x.x); x.y = fma(alpha, pp.y, x.y); x.z = fma(alpha, pp.z, x.z);
+      rv.x = fma(-alpha, sv.x, rv.x); rv.y = fma(-alpha, sv.y, rv.y); rv.z = fma(-alpha, sv.z, rv.z);
+      d.pp[r] = pp;
+      d.s[r] = sv;
+      d.p[r] = x;
+      d.r[r] = rv;
+      d.u[r] = mul3(d.Minv + 9 * r, rv);
+    }
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
   }
-  // ---- g . p per gel (stationarity test of the line search)
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
-    double gp = 0.0;
-    if (d.gc[g].phase == phase) gp = dot4(d.grad[32 * s + lane], d.p[32 * s + lane]);
-    gp = warp_sum(gp);
-    if (lane == 0) dsm[(s - s0) * 4 + 0] = gp;
-  }
-  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 1);
-  if (!grid_barrier(d.bar, epoch, d.err)) return;
-  gel_totals(d, plan, g0, ng, 1, tot);
-  for (int j = threadIdx.x; j < ng; j += PCG_T) {
-    const GelInfo& G = d.gi[g0 + j];
-    if (s0 <= G.s0 && G.s0 < s1) d.gv[g0 + j].gtp = tot[j][0];
-  }
-  // ---- ||p||_inf per gel
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
-    if (d.gc[g].phase != phase) continue;
-    const double4_32a x = d.p[32 * s + lane];
-    const double m = warp_max(fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z))));
-    if (lane == 0) atomic_max_pos(&d.gv[g].pnorm_bits, m);
-  }
+  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
 cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta,
@@ -428,20 +324,12 @@ cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas
   return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, smem, st);
 }
 
-
-
 // ---------------------------------------------------------------- mixed-precision PCG
 // Mixed precision Newton direction: the Hessian is stored in FP32 (elastic blocks computed in
 // FP32, barrier blocks rounded from FP64); the direction p solves H p = -g by iterative
 // refinement: in every round the FP64 residual r = -g - H p (FP32 values, FP64 vectors and
 // accumulation) is formed, then H d = r is solved by the same block-Jacobi CG in FP32 to the
 // FP32 accuracy limit, and p += d in FP64.  Rounds stop once |r| <= eta |g| (FP64 residual).
-
-__device__ __forceinline__ float4 mul3f(const float* M, const float4 v) {
-  return make_float4(fmaf(M[2], v.z, fmaf(M[1], v.y, M[0] * v.x)), fmaf(M[5], v.z, fmaf(M[4], v.y, M[3] * v.x)),
-                     fmaf(M[8], v.z, fmaf(M[7], v.y, M[6] * v.x)), 0.f);
-}
-__device__ __forceinline__ float dot4f(const float4 a, const float4 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
 
 // y = A32 u32 (FP32)
 __device__ __forceinline__ float4 spmv_row32(const Dev& d, int s, int lane, const float4* u) {
@@ -493,20 +381,23 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
                                                      int refine_max) {
   extern __shared__ double dsm[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG];
-  __shared__ double tolj[PCG_MAXG];
-  __shared__ int s_exit;
+  __shared__ double bbj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
+  __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
+  __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s0 = plan.cta_s0[blockIdx.x], s1 = plan.cta_s0[blockIdx.x + 1];
-  const int g0 = plan.cta_g0[blockIdx.x], ng = plan.cta_ng[blockIdx.x];
-  const int slot0 = plan.cta_slot0[blockIdx.x];
-  unsigned epoch = 0;
-  int kk = 0;  // global inner-iteration parity counter (for the act[] double buffer and gsc)
+  PcgCta c = pcg_cta(d, plan);
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
+    run[j] = gact[j];
+    itj[j] = 0;
+  }
+  __syncthreads();
   // ---- init: r64 = b = -grad, p = 0; partials |b|^2 (k = 3) and |r|^2 (k = 2)
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
     double bb = 0.0;
-    if (d.gc[g].phase == phase) {
+    if (gact[plan.slice_gel[s] - c.g0]) {
       const int r = 32 * s + lane;
       const double4_32a gr = d.grad[r];
       const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
@@ -516,64 +407,55 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
     }
     bb = warp_sum(bb);
     if (lane == 0) {
-      dsm[(s - s0) * 4 + 3] = bb;
-      dsm[(s - s0) * 4 + 2] = bb;
+      dsm[(s - c.s0) * 4 + 3] = bb;
+      dsm[(s - c.s0) * 4 + 2] = bb;
     }
   }
-  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 2, 4);
-  if (!grid_barrier(d.bar, epoch, d.err)) return;
+  if (!group_sum(d, c, dsm, 2, 4, tot, &s_fail)) return;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) bbj[j] = tot[j][3];
+  __syncthreads();
   for (int round = 0;; ++round) {
     // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
-    gel_totals(d, plan, g0, ng, round == 0 ? 4 : 3, tot);
-    if (round == 0) {
-      for (int j = threadIdx.x; j < ng; j += PCG_T) bbj[j] = tot[j][3];
-      __syncthreads();
-    }
-    int my_active = 0;
-    for (int j = 0; j < ng; ++j) {
-      const int g = g0 + j;
-      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+      inner[j] = 0;
+      if (!run[j]) continue;
       const double rr = tot[j][2], bb = bbj[j];
       if (!(rr > eta2 * bb) || round >= refine_max) {
-        if (threadIdx.x == 0) {
-          d.gv[g].pcg_done = 1;
-          d.gv[g].rounds = round;
-          d.gv[g].bb = bb;
+        run[j] = 0;
+        if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + j].pcg_done = 1;
+          d.gv[c.g0 + j].rounds = round;
+          d.gv[c.g0 + j].bb = bb;
+          d.gv[c.g0 + j].pcg_it = itj[j];
         }
         continue;
       }
-      ++my_active;
-      if (threadIdx.x == 0) d.gv[g].inner_done = 0;
+      s_any = 1;
+      inner[j] = 1;
       // inner target: reach eta |b| in one round if FP32 allows, else the FP32 floor
-      if (threadIdx.x == 0) tolj[j] = fmax(eta2 * bb / rr, 1e-11);
-      const GelInfo& G = d.gi[g];
-      const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
-      for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
-        const int r = 32 * s + lane;
-        const double4_32a rv = d.r[r];
-        const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
-        d.r32[r] = r32;
-        d.x32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d.pp32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d.s32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
-      }
+      tolj[j] = fmax(eta2 * bb / rr, 1e-11);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && my_active) atomicAdd(&d.act[2], my_active);
-    if (!grid_barrier(d.bar, epoch, d.err)) return;
-    if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[2]) == 0);
-    __syncthreads();
-    if (s_exit) break;
-    if (!grid_barrier(d.bar, epoch, d.err)) return;  // everyone has read act[2]
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.act[2] = 0;
+    if (!s_any) break;
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      if (!inner[plan.slice_gel[s] - c.g0]) continue;
+      const int r = 32 * s + lane;
+      const double4_32a rv = d.r[r];
+      const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
+      d.r32[r] = r32;
+      d.x32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.pp32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.s32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
+    }
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
     // ---- inner FP32 CG (Chronopoulos-Gear), same structure as the FP64 kernel
-    int k = 0;
-    while (true) {
-      for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-        const int g = plan.slice_gel[s];
+    for (int k = 1;; ++k) {
+      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
         double ga = 0.0, de = 0.0, rr = 0.0;
-        if (d.gc[g].phase == phase && !d.gv[g].pcg_done && !d.gv[g].inner_done) {
+        if (inner[plan.slice_gel[s] - c.g0]) {
           const int r = 32 * s + lane;
           float4 w = spmv_row32(d, s, lane, d.u32);
           if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -587,78 +469,56 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
         de = warp_sum(de);
         rr = warp_sum(rr);
         if (lane == 0) {
-          dsm[(s - s0) * 4 + 0] = ga;
-          dsm[(s - s0) * 4 + 1] = de;
-          dsm[(s - s0) * 4 + 2] = rr;
+          dsm[(s - c.s0) * 4 + 0] = ga;
+          dsm[(s - c.s0) * 4 + 1] = de;
+          dsm[(s - c.s0) * 4 + 2] = rr;
         }
       }
-      cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 3);
-      if (blockIdx.x == 0 && threadIdx.x == 0) d.act[(kk + 1) & 1] = 0;
-      if (!grid_barrier(d.bar, epoch, d.err)) return;
-      k += 1;
-      kk += 1;
-      gel_totals(d, plan, g0, ng, 3, tot);
-      int inner_active = 0;
-      for (int j = 0; j < ng; ++j) {
-        const int g = g0 + j;
-        if (d.gc[g].phase != phase || d.gv[g].pcg_done || d.gv[g].inner_done) continue;
+      if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+        if (!inner[j]) continue;
         const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
         // converged once |r32|^2 <= tol |r32 at the round start|^2 (FP32 accuracy floor 1e-11)
-        const double rr0 = k == 1 ? rr : d.gsc[(size_t)2 * d.n_gels + g];
-        if (k == 1 && threadIdx.x == 0) d.gsc[(size_t)2 * d.n_gels + g] = rr;
-        const bool conv = !(rr > tolj[j] * rr0) || k > maxit;
-        if (conv) {
-          const GelInfo& G = d.gi[g];
-          if (threadIdx.x == 0) {
-            d.gv[g].inner_done = 1;
-            if (s0 <= G.s0 && G.s0 < s1) d.gv[g].pcg_it += k - 1;  // the gel's first CTA counts
-          }
+        if (k == 1) rr0j[j] = rr;
+        if (!(rr > tolj[j] * rr0j[j]) || k > maxit) {
+          inner[j] = 0;
+          itj[j] += k - 1;
           continue;
         }
-        ++inner_active;
-        const int par = kk & 1, prv = (kk - 1) & 1;
-        double beta, alpha;
-        if (k == 1) {
-          beta = 0.0;
-          alpha = ga / de;
-        } else {
-          const double gprev = d.gsc[(size_t)(prv * 4 + 0) * d.n_gels + g];
-          const double aprev = d.gsc[(size_t)(prv * 4 + 1) * d.n_gels + g];
-          beta = ga / gprev;
-          alpha = ga / (de - beta * ga / aprev);
-        }
-        if (threadIdx.x == 0) {
-          d.gsc[(size_t)(par * 4 + 0) * d.n_gels + g] = ga;
-          d.gsc[(size_t)(par * 4 + 1) * d.n_gels + g] = alpha;
-        }
-        const float fb = (float)beta, fa = (float)alpha;
-        const GelInfo& G = d.gi[g];
-        const int gs0 = max(s0, G.s0), gs1 = min(s1, G.s0 + G.ns);
-        for (int s = gs0 + wid; s < gs1; s += PCG_T / 32) {
-          const int r = 32 * s + lane;
-          const float4 u = d.u32[r], w = d.w32[r];
-          float4 pp = d.pp32[r], sv = d.s32[r], x = d.x32[r], rv = d.r32[r];
-          pp.x = fmaf(fb, pp.x, u.x); pp.y = fmaf(fb, pp.y, u.y); pp.z = fmaf(fb, pp.z, u.z);
-          sv.x = fmaf(fb, sv.x, w.x); sv.y = fmaf(fb, sv.y, w.y); sv.z = fmaf(fb, sv.z, w.z);
-          x.x = fmaf(fa, pp.x, x.x); x.y = fmaf(fa, pp.y, x.y); x.z = fmaf(fa, pp.z, x.z);
-          rv.x = fmaf(-fa, sv.x, rv.x); rv.y = fmaf(-fa, sv.y, rv.y); rv.z = fmaf(-fa, sv.z, rv.z);
-          d.pp32[r] = pp;
-          d.s32[r] = sv;
-          d.x32[r] = x;
-          d.r32[r] = rv;
-          d.u32[r] = mul3f(d.Minv32 + 9 * r, rv);
-        }
+        s_any = 1;
+        const double beta = k == 1 ? 0.0 : ga / gprev[j];
+        const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
+        gprev[j] = ga;
+        aprev[j] = alpha;
+        alj[j] = (float)alpha;
+        bej[j] = (float)beta;
       }
-      if (threadIdx.x == 0 && inner_active) atomicAdd(&d.act[kk & 1], inner_active);
-      if (!grid_barrier(d.bar, epoch, d.err)) return;
-      if (threadIdx.x == 0) s_exit = (*((volatile int*)&d.act[kk & 1]) == 0);
       __syncthreads();
-      if (s_exit) break;
+      if (!s_any) break;
+      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+        const int j = plan.slice_gel[s] - c.g0;
+        if (!inner[j]) continue;
+        const float fb = bej[j], fa = alj[j];
+        const int r = 32 * s + lane;
+        const float4 u = d.u32[r], w = d.w32[r];
+        float4 pp = d.pp32[r], sv = d.s32[r], x = d.x32[r], rv = d.r32[r];
+        pp.x = fmaf(fb, pp.x, u.x); pp.y = fmaf(fb, pp.y, u.y); pp.z = fmaf(fb, pp.z, u.z);
+        sv.x = fmaf(fb, sv.x, w.x); sv.y = fmaf(fb, sv.y, w.y); sv.z = fmaf(fb, sv.z, w.z);
+        x.x = fmaf(fa, pp.x, x.x); x.y = fmaf(fa, pp.y, x.y); x.z = fmaf(fa, pp.z, x.z);
+        rv.x = fmaf(-fa, sv.x, rv.x); rv.y = fmaf(-fa, sv.y, rv.y); rv.z = fmaf(-fa, sv.z, rv.z);
+        d.pp32[r] = pp;
+        d.s32[r] = sv;
+        d.x32[r] = x;
+        d.r32[r] = rv;
+        d.u32[r] = mul3f(d.Minv32 + 9 * r, rv);
+      }
+      if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
     }
     // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p
-    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-      const int g = plan.slice_gel[s];
-      if (d.gc[g].phase != phase || d.gv[g].pcg_done) continue;
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      if (!run[plan.slice_gel[s] - c.g0]) continue;
       const int r = 32 * s + lane;
       const float4 x = d.x32[r];
       double4_32a p = d.p[r];
@@ -667,11 +527,10 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
       p.z += (double)x.z;
       d.p[r] = p;
     }
-    if (!grid_barrier(d.bar, epoch, d.err)) return;
-    for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-      const int g = plan.slice_gel[s];
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
       double rr = 0.0;
-      if (d.gc[g].phase == phase && !d.gv[g].pcg_done) {
+      if (run[plan.slice_gel[s] - c.g0]) {
         const int r = 32 * s + lane;
         double4_32a ap = spmv_row_res(d, s, lane, d.p);
         const double4_32a gr = d.grad[r];
@@ -681,34 +540,11 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
         rr = dot4(rv, rv);
       }
       rr = warp_sum(rr);
-      if (lane == 0) dsm[(s - s0) * 4 + 2] = rr;
+      if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
     }
-    cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 2, 3);
-    if (!grid_barrier(d.bar, epoch, d.err)) return;
+    if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
   }
-  // ---- g . p per gel (stationarity test of the line search)
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
-    double gp = 0.0;
-    if (d.gc[g].phase == phase) gp = dot4(d.grad[32 * s + lane], d.p[32 * s + lane]);
-    gp = warp_sum(gp);
-    if (lane == 0) dsm[(s - s0) * 4 + 0] = gp;
-  }
-  cta_reduce(d, plan, dsm, s0, s1, g0, ng, slot0, 0, 1);
-  if (!grid_barrier(d.bar, epoch, d.err)) return;
-  gel_totals(d, plan, g0, ng, 1, tot);
-  for (int j = threadIdx.x; j < ng; j += PCG_T) {
-    const GelInfo& G = d.gi[g0 + j];
-    if (s0 <= G.s0 && G.s0 < s1) d.gv[g0 + j].gtp = tot[j][0];
-  }
-  // ---- ||p||_inf per gel
-  for (int s = s0 + wid; s < s1; s += PCG_T / 32) {
-    const int g = plan.slice_gel[s];
-    if (d.gc[g].phase != phase) continue;
-    const double4_32a x = d.p[32 * s + lane];
-    const double m = warp_max(fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z))));
-    if (lane == 0) atomic_max_pos(&d.gv[g].pnorm_bits, m);
-  }
+  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
 cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,

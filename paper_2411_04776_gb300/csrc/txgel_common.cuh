@@ -120,10 +120,8 @@ struct Dev {
   // PCG
   double4_32a *r, *u, *w, *pp, *s;
   float4 *u32, *w32, *pp32, *s32, *r32, *x32;
-  double* part;    // per slice partial sums: 4 arrays of nslices
-  double* gsc;     // per gel PCG scalars: [2][4][n_gels] (gamma, alpha for parity 0/1)
-  unsigned* bar;   // grid barrier counter
-  int* act;        // active counters (2)
+  double* part;    // PCG: per-CTA partial sums exchanged inside a group, [4][nctas]
+  unsigned* bar;   // PCG: one barrier counter per group
   // surface primitives (global)
   int* sv;
   int4* st;
@@ -160,16 +158,17 @@ struct Dev {
   int* err;
 };
 
-// Static partition of the slices over the CTAs of the persistent PCG kernel.
+// Static partition of the slices over the CTAs of the persistent PCG kernels.  The gels are split
+// into independent groups: a gel with many slices forms a group alone, spread over several CTAs;
+// consecutive small gels are packed into a group of one CTA.  The CTAs of a group synchronise
+// through a barrier counter of their own, so a group never waits for another one.
 struct PcgPlan {
-  const int* cta_s0;     // per CTA: first slice (n + 1 entries)
-  const int* cta_g0;     // per CTA: first gel touched
-  const int* cta_ng;     // per CTA: number of gels touched
-  const int* cta_slot0;  // per CTA: first reduction slot (one slot per (CTA, gel touched))
-  const int* gel_slot;   // per gel: first and one-past-last slot (n_gels + 1 ... stored as pairs)
+  const int* cta_s0;     // per CTA: first slice (nctas + 1 entries)
+  const int* cta_grp;    // per CTA: its group
+  const int4* grp;       // per group: (first CTA, CTA count, first gel, gel count)
   const int* slice_gel;  // per slice: its gel
   int max_slices;        // most slices any CTA owns
-  int nslots;
+  int ngroups;
 };
 
 // host-side count of kernel launches (every launcher adds the kernels it enqueued)

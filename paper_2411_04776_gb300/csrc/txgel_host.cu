@@ -54,6 +54,9 @@ cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas
 cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
                              int refine_max, cudaStream_t st);
 int pcg_max_ctas_per_sm(int max_slices);
+int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
+cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, double eta,
+                           int maxit, int refine_max, int wmax, cudaStream_t st);
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
                    double* part_e, int mode, cudaStream_t st);
 void launch_rows(int which, const Dev& d, int phase, cudaStream_t st);
@@ -83,6 +86,10 @@ namespace {
 // phases beyond the ones the kernels name
 enum : int { PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6, PH_PARK = 7, PH_FAIL = 8 };
 constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
+// default slices (32 rows) per PCG CTA: FP64 spreads a gel over many SMs (the FP64 pipe bounds
+// the SpMV); FP32 keeps groups small so that their barriers are cheap
+constexpr int PCG_SLICES_FP64 = 4;
+constexpr int PCG_SLICES_MIXED = 4;
 constexpr int PIECE_HOST = 512;
 
 #define CK(call)                                                          \
@@ -158,7 +165,8 @@ tx_status check_desc(const tx_gel_desc* d) {
   if (!(d->young > 0) || !(d->poisson > -1.0 && d->poisson < 0.5) || !(d->density > 0)) return TX_ERR_ARG;
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || p.newton_max_iter < 1 ||
-      p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0)
+      p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
+      p.pcg_cta_slices < 0)
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
     if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
@@ -405,6 +413,8 @@ struct tx_batch {
   // PCG
   PcgPlan plan{};
   int nctas = 0;
+  bool pcg_res = false;  // resident kernels: one slice per warp, matrix in shared memory
+  int pcg_wmax = 0;      // widest slice (blocks per row)
   // energy pieces
   int4* pieces = nullptr;
   int npieces = 0;
@@ -760,7 +770,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
       ie_gel[G.ie0 + k] = g;
     }
   }
-  // ---- PCG plan
+  // ---- PCG plan: independent groups (a large gel over several CTAs, small gels packed into one)
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -768,41 +778,60 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     delete b;
     return TX_ERR_CUDA;
   }
-  // one CTA per SM for small systems (every warp owns a slice), two per SM for large ones
-  int nctas = std::min(nsm * 2, (nslices + 3) / 4);
-  nctas = std::max(1, std::min(nctas, nslices));
-  int max_slices = (nslices + nctas - 1) / nctas;
-  const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
-  if (nctas > nsm * occ) {
-    nctas = nsm * occ;
-    max_slices = (nslices + nctas - 1) / nctas;
-  }
-  std::vector<int> cta_s0(nctas + 1), cta_g0(nctas), cta_ng(nctas), cta_slot0(nctas + 1, 0);
-  std::vector<int> gel_slot(2 * n, -1);
-  for (int c = 0; c <= nctas; ++c) cta_s0[c] = (int)((long long)c * nslices / nctas);
-  for (int c = 0; c < nctas; ++c) {
-    max_slices = std::max(max_slices, cta_s0[c + 1] - cta_s0[c]);
-    if (cta_s0[c + 1] > cta_s0[c]) {
-      cta_g0[c] = slice_gel[cta_s0[c]];
-      cta_ng[c] = slice_gel[cta_s0[c + 1] - 1] - cta_g0[c] + 1;
-    } else {
-      cta_g0[c] = 0;
-      cta_ng[c] = 0;
+  int spc_min = 0;  // slices (32 rows) per CTA at least
+  for (int g = 0; g < n; ++g) spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
+  if (spc_min <= 0) spc_min = b->mixed ? PCG_SLICES_MIXED : PCG_SLICES_FP64;
+  std::vector<int> cta_s0, cta_grp;
+  std::vector<int4> grp;
+  int spc = std::max(spc_min, 1), max_slices = 1;
+  for (int attempt = 0;; ++attempt) {
+    cta_s0.clear();
+    cta_grp.clear();
+    grp.clear();
+    int g = 0;
+    while (g < n) {
+      const GelInfo& G = b->gi[g];
+      if (G.ns > spc || g + 1 == n) {  // a group of its own, over ceil(ns / spc) CTAs
+        const int nc = std::max(1, (G.ns + spc - 1) / spc);
+        grp.push_back(make_int4((int)cta_s0.size(), nc, g, 1));
+        for (int q = 0; q < nc; ++q) {
+          cta_s0.push_back(G.s0 + (int)((long long)q * G.ns / nc));
+          cta_grp.push_back((int)grp.size() - 1);
+        }
+        ++g;
+        continue;
+      }
+      int acc = 0, k = g;  // pack consecutive small gels into one CTA
+      while (k < n && k - g < PCG_MAXG_HOST && b->gi[k].ns <= spc && (k == g || acc + b->gi[k].ns <= spc)) {
+        acc += b->gi[k].ns;
+        ++k;
+      }
+      grp.push_back(make_int4((int)cta_s0.size(), 1, g, k - g));
+      cta_s0.push_back(G.s0);
+      cta_grp.push_back((int)grp.size() - 1);
+      g = k;
     }
-    if (cta_ng[c] > PCG_MAXG_HOST) {
-      g_err = "too many small gels for one handle";
+    const int nctas = (int)cta_grp.size();
+    cta_s0.push_back(nslices);
+    max_slices = 1;
+    for (int c = 0; c < nctas; ++c) max_slices = std::max(max_slices, cta_s0[c + 1] - cta_s0[c]);
+    const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
+    if (nctas <= nsm * occ) break;
+    if (attempt > 200) {
+      g_err = "PCG partition does not fit the device";
       delete b;
       return TX_ERR_ARG;
     }
-    cta_slot0[c + 1] = cta_slot0[c] + cta_ng[c];
-    for (int j = 0; j < cta_ng[c]; ++j) {
-      const int g = cta_g0[c] + j, slot = cta_slot0[c] + j;
-      if (gel_slot[2 * g] < 0) gel_slot[2 * g] = slot;
-      gel_slot[2 * g + 1] = slot + 1;
-    }
+    spc = spc + spc / 4 + 1;
   }
-  const int nslots = cta_slot0[nctas];
+  const int nctas = (int)cta_grp.size();
+  const int ngroups = (int)grp.size();
   b->nctas = nctas;
+  for (int q = 0; q < nslices; ++q) b->pcg_wmax = std::max(b->pcg_wmax, (slice_off[q + 1] - slice_off[q]) / SLICE);
+  {
+    const int occ = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
+    b->pcg_res = occ > 0 && nctas <= nsm * occ;
+  }
   // ---- energy pieces
   for (int g = 0; g < n; ++g) {
     const GelInfo& G = b->gi[g];
@@ -862,10 +891,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.w = M.get<double4_32a>(rows);
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
-  d.part = M.get<double>(4 * (size_t)nslots);
-  d.gsc = M.get<double>(8 * (size_t)n);
-  d.bar = M.get<unsigned>(4);
-  d.act = M.get<int>(4);
+  d.part = M.get<double>(4 * (size_t)nctas);
+  d.bar = M.get<unsigned>(ngroups);
   d.sv = M.get<int>(nsv);
   d.st = M.get<int4>(nst);
   d.se = M.get<int2>(nse);
@@ -894,20 +921,20 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
-  int* cta_buf = M.get<int>(4 * (size_t)nctas + 2 + nslices + 2 * (size_t)n);
-  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !cta_buf || (b->mixed ? !d.vals32 : !d.vals)) {
+  int* cta_buf = M.get<int>(2 * (size_t)nctas + 1 + nslices);
+  int4* grp_buf = M.get<int4>(ngroups);
+  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !cta_buf || !grp_buf ||
+      (b->mixed ? !d.vals32 : !d.vals)) {
     M.release();
     delete b;
     return TX_ERR_OOM;
   }
   b->plan.cta_s0 = cta_buf;
-  b->plan.cta_g0 = cta_buf + nctas + 1;
-  b->plan.cta_ng = cta_buf + 2 * nctas + 1;
-  b->plan.slice_gel = cta_buf + 3 * nctas + 1;
-  b->plan.cta_slot0 = cta_buf + 3 * nctas + 1 + nslices;
-  b->plan.gel_slot = cta_buf + 4 * nctas + 2 + nslices;
+  b->plan.cta_grp = cta_buf + nctas + 1;
+  b->plan.slice_gel = cta_buf + 2 * nctas + 1;
+  b->plan.grp = grp_buf;
   b->plan.max_slices = max_slices;
-  b->plan.nslots = nslots;
+  b->plan.ngroups = ngroups;
   if (b->mixed) {  // FP32 PCG vectors live in the upper half of dedicated buffers
     d.u32 = (float4*)M.get<float4>(rows);
     d.w32 = (float4*)M.get<float4>(rows);
@@ -966,11 +993,9 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
   U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
   U((void*)b->plan.cta_s0, cta_s0.data(), sizeof(int) * (nctas + 1));
-  U((void*)b->plan.cta_g0, cta_g0.data(), sizeof(int) * nctas);
-  U((void*)b->plan.cta_ng, cta_ng.data(), sizeof(int) * nctas);
+  U((void*)b->plan.cta_grp, cta_grp.data(), sizeof(int) * nctas);
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
-  U((void*)b->plan.cta_slot0, cta_slot0.data(), sizeof(int) * (nctas + 1));
-  U((void*)b->plan.gel_slot, gel_slot.data(), sizeof(int) * 2 * n);
+  U((void*)b->plan.grp, grp.data(), sizeof(int4) * ngroups);
   if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
@@ -1294,15 +1319,20 @@ tx_status do_newton(tx_batch* b) {
   prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
-  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * 4, st));
-  CK(cudaMemsetAsync(d.act, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
   prof_open(b, PR_PCG);
   if (b->mixed) {
     int refine = 1;
     for (int g : set) refine = std::max(refine, b->mesh[g].prm.refine_max);
-    CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
+    if (b->pcg_res)
+      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
+    else
+      CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
   } else {
-    CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+    if (b->pcg_res)
+      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
+    else
+      CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
   }
   prof_close(b, 1);
   launch_gel_op(d, PH_NEWTON, 1, st);
@@ -1525,6 +1555,7 @@ void tx_params_default(tx_params* p) {
   p->max_split_depth = 4;
   p->precision = TX_PREC_FP64;
   p->refine_max = 3;
+  p->pcg_cta_slices = 0;
 }
 
 const char* tx_status_str(tx_status s) {
