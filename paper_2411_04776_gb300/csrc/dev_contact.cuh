@@ -239,6 +239,25 @@ __device__ __forceinline__ void pair_points(const Dev& d, const int4& pr, double
   }
 }
 
+// gel row of each slot of a candidate pair (-1 for indenter slots), as in pair_points
+__device__ __forceinline__ void pair_rows(const Dev& d, const int4& pr, int rows[4]) {
+  if (pr.x == PAIR_PT) {
+    rows[0] = d.sv[pr.y];
+    rows[1] = rows[2] = rows[3] = -1;
+  } else if (pr.x == PAIR_TP) {
+    const int4 t = d.st[pr.y];
+    rows[0] = -1;
+    rows[1] = t.x;
+    rows[2] = t.y;
+    rows[3] = t.z;
+  } else {
+    const int2 e = d.se[pr.y];
+    rows[0] = e.x;
+    rows[1] = e.y;
+    rows[2] = rows[3] = -1;
+  }
+}
+
 __device__ __forceinline__ double pair_eps_x(const Dev& d, const int4& pr) {
   return pr.x == PAIR_EE ? 1e-3 * d.se_len2[pr.y] * d.ie_len2[pr.z] : 0.0;
 }

@@ -14,9 +14,8 @@
 // Jacobi with the round-robin ("parallel") ordering of Brent & Luk: each round applies m/2
 // disjoint rotations at once; lane k owns the 2x2 block (pair a, pair b) of the matrix it
 // transforms, so no two lanes write the same entry.  GB300 issues FP64 at 1/64 of the FP32
-// rate, so the eigenbasis is found in FP32 first, made orthonormal in FP64 by two Newton-Schulz
-// steps Q <- Q (3 I - Q^T Q) / 2, and refined by FP64 Jacobi sweeps on B = Q^T A Q (nearly
-// diagonal); the clamp Q max(B, 0) Q^T is assembled in FP64.
+// rate, so the eigenbasis is found in FP32 first; FP64 then re-orthonormalises it and refines
+// only what FP32 could not resolve; the clamp X max(lam, 0) X^T is assembled in FP64.
 #pragma once
 #include "dev_contact.cuh"
 
@@ -29,6 +28,7 @@ struct DV {
   double v[3][3];
   double D;
   double s, W;     // PT / LL: s = w.(e1 x e2), W = c(e1, e2);  PE: s = c(w, e), W = |e|^2
+  double iW;       // 1 / W
   double gD[9];    // dD/dv
   double gs[9];    // PT / LL: ds/dv;  PE: d c(w, e)/dv
   double gW[9];    // dW/dv
@@ -51,6 +51,7 @@ __device__ __forceinline__ void dv_setup(const DType& t, const double P[4][3], D
   }
   o.s = 0.0;
   o.W = 1.0;
+  o.iW = 1.0;
   if (t.f == DF_PP) {
     o.nd = 1;
     o.pl[0] = t.i[0];
@@ -74,6 +75,7 @@ __device__ __forceinline__ void dv_setup(const DType& t, const double P[4][3], D
     cn_grad(w, e, o.gs, o.gs + 3);
     for (int c = 0; c < 3; ++c) o.gW[3 + c] = 2.0 * e[c];
     o.D = o.s / o.W;
+    o.iW = 1.0 / o.W;
     for (int k = 0; k < 6; ++k) o.gD[k] = (o.gs[k] - o.D * o.gW[k]) / o.W;
     return;
   }
@@ -101,6 +103,7 @@ __device__ __forceinline__ void dv_setup(const DType& t, const double P[4][3], D
   o.W = dot3(e1, e1) * dot3(e2, e2) - ee * ee;
   cn_grad(e1, e2, o.gW + 3, o.gW + 6);
   o.D = o.s * o.s / o.W;
+  o.iW = 1.0 / o.W;
   for (int k = 0; k < 9; ++k) o.gD[k] = (2.0 * o.s * o.gs[k] - o.D * o.gW[k]) / o.W;
 }
 
@@ -132,7 +135,7 @@ __device__ __forceinline__ double hD_dv(const DV& o, int a, int c, int b, int e)
   if (o.form == DF_PE) {
     const double HN = cn_entry(o.v[0], o.v[1], a, c, b, e);
     const double HL = (a == 1 && b == 1 && c == e) ? 2.0 : 0.0;
-    return (HN - o.D * HL - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) / o.W;
+    return (HN - o.D * HL - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) * o.iW;
   }
   // second derivatives of the triple product w.(e1 x e2) (zero within one vector)
   double Hs = 0.0;
@@ -144,7 +147,7 @@ __device__ __forceinline__ double hD_dv(const DV& o, int a, int c, int b, int e)
     else Hs = -skew_entry(o.v[0], r, q);
   }
   const double HW = (a >= 1 && b >= 1) ? cn_entry(o.v[1], o.v[2], a - 1, c, b - 1, e) : 0.0;
-  return (2.0 * o.gs[ia] * o.gs[ib] + 2.0 * o.s * Hs - o.D * HW - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) / o.W;
+  return (2.0 * o.gs[ia] * o.gs[ib] + 2.0 * o.s * Hs - o.D * HW - o.gD[ia] * o.gW[ib] - o.gW[ia] * o.gD[ib]) * o.iW;
 }
 
 // d2D / dP_I dP_J (point-space dofs I, J in [0, 12))
@@ -237,9 +240,9 @@ __device__ __forceinline__ double pair_grad_entry(const PairBarrier& pb, int I) 
   return pb.moll ? pb.m * gb + pb.b0 * pb.m1 * pb.gcp[I] : gb;
 }
 
-// d2b/dP_I dP_J of the (mollified) barrier
-__device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, int J) {
-  double h = pb.bDD * pb.gDp[I] * pb.gDp[J] + pb.bD * hD_point(pb.dv, I, J);
+// d2b/dP_I dP_J of the (mollified) barrier, given hDp = d2D/dP_I dP_J
+__device__ __forceinline__ double pair_hess_compose(const PairBarrier& pb, int I, int J, double hDp) {
+  double h = pb.bDD * pb.gDp[I] * pb.gDp[J] + pb.bD * hDp;
   if (pb.moll) {
     const int p = I / 3, c = I % 3, q = J / 3, e = J % 3;
     // cross-norm Hessian over the points: edge a = (P0 -> P1), edge b = (P2 -> P3)
@@ -251,6 +254,49 @@ __device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, 
         pb.b0 * (pb.m2 * pb.gcp[I] * pb.gcp[J] + pb.m1 * Hc);
   }
   return h;
+}
+
+__device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, int J) {
+  return pair_hess_compose(pb, I, J, hD_point(pb.dv, I, J));
+}
+
+// The block of the barrier Hessian on the point dofs fd[0, nf) into H (row stride m, rows and
+// columns nf..m-1 zero), by the lanes of a warp: the difference-vector Hessian of D is formed
+// once (Hdv: (3 nd)^2 scratch), every point entry is then a signed sum of its entries.  Entries
+// (i, j) and (j, i) are computed in the same order, so H is exactly symmetric.
+__device__ __forceinline__ void warp_pair_block(const PairBarrier& pb, const int* fd, int nf, int m, double* Hdv,
+                                                double* H, int lane) {
+  const DV& o = pb.dv;
+  const int n3 = 3 * o.nd;
+  for (int e = lane; e < n3 * n3; e += 32) {
+    const int r = e / n3, c = e - r * n3;
+    const int a = r < c ? r : c, b = r < c ? c : r;
+    Hdv[e] = hD_dv(o, a / 3, a % 3, b / 3, b % 3);
+  }
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const int i = r < c ? r : c, j = r < c ? c : r;
+    double v = 0.0;
+    if (j < nf) {
+      const int I = fd[i], J = fd[j];
+      const int p = I / 3, ci = I - 3 * p, q = J / 3, cj = J - 3 * q;
+      double h = 0.0;
+      for (int a = 0; a < o.nd; ++a) {
+        const double sa = dv_sigma(o, p, a);
+        if (sa == 0.0) continue;
+        for (int b = 0; b < o.nd; ++b) {
+          const double sb = dv_sigma(o, q, b);
+          if (sb == 0.0) continue;
+          const double x = Hdv[(3 * a + ci) * n3 + 3 * b + cj];
+          h += sa * sb > 0.0 ? x : -x;
+        }
+      }
+      v = pair_hess_compose(pb, I, J, h);
+    }
+    H[e] = v;
+  }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------- warp-parallel Jacobi
@@ -347,80 +393,163 @@ __device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
   }
 }
 
+// FP64 refinement sweeps of cyclic Jacobi (round-robin order) on a symmetric A that an
+// orthonormal basis already nearly diagonalises.  Rotation angles come from the FP32 quotient
+// (a_qq - a_pp) / (2 a_pq); the rotation itself (c = 1 / sqrt(1 + t^2), s = t c) and every update
+// are FP64, so each sweep multiplies the off-diagonal entries by ~1e-7 and keeps V orthonormal to
+// FP64 round-off.  Entries below tau (absolute) are left alone, and a round none of whose pairs
+// needs a rotation is skipped by the whole warp; a sweep without rotations ends the refinement.
+__device__ void warp_jacobi_refine(double* A, double* V, int m, int max_sweeps, double tau, RotWS<double>& rw,
+                                   int lane) {
+  const int h = m >> 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    bool rotated = false;
+    for (int r = 0; r < m - 1; ++r) {
+      bool rot = false;
+      if (lane < h) {
+        const int pa = lane == 0 ? 0 : lane + 1, pb = lane == 0 ? 1 : m - lane;
+        int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
+        int q = (pb - 1 + r) % (m - 1) + 1;
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        const double apq = A[p * m + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > tau) {
+          const float th = (float)(A[q * m + q] - A[p * m + p]) / (2.f * (float)apq);
+          const float t32 = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+          const double t = (double)t32;
+          c = rsqrt(fma(t, t, 1.0));
+          s = t * c;
+          rot = true;
+        }
+        rw.p[lane] = p;
+        rw.q[lane] = q;
+        rw.c[lane] = c;
+        rw.s[lane] = s;
+      }
+      if (!__any_sync(0xffffffffu, rot)) continue;
+      rotated = true;
+      __syncwarp();
+      for (int blk = lane; blk < h * h; blk += 32) {
+        const int a = blk / h, b = blk - a * h;
+        const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
+        const double ca = rw.c[a], sa = rw.s[a], cb = rw.c[b], sb = rw.s[b];
+        const double x00 = A[pa * m + pb], x01 = A[pa * m + qb], x10 = A[qa * m + pb], x11 = A[qa * m + qb];
+        const double y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+        const double y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+        A[pa * m + pb] = cb * y00 - sb * y01;
+        A[pa * m + qb] = sb * y00 + cb * y01;
+        A[qa * m + pb] = cb * y10 - sb * y11;
+        A[qa * m + qb] = sb * y10 + cb * y11;
+      }
+      for (int task = lane; task < m * h; task += 32) {
+        const int k = task / h, a = task - k * h;
+        const int p = rw.p[a], q = rw.q[a];
+        const double c = rw.c[a], s = rw.s[a];
+        const double vp = V[k * m + p], vq = V[k * m + q];
+        V[k * m + p] = c * vp - s * vq;
+        V[k * m + q] = s * vp + c * vq;
+      }
+      __syncwarp();
+    }
+    if (!rotated) break;
+  }
+}
+
 // per-warp workspace of the projection
 struct ProjWS {
   double H[PW_MAXN * PW_MAXN];  // in: symmetric block (stride m); out: its PSD projection
-  double Q[PW_MAXN * PW_MAXN];
-  double T[PW_MAXN * PW_MAXN];
-  double B[PW_MAXN * PW_MAXN];
+  double X[PW_MAXN * PW_MAXN], T[PW_MAXN * PW_MAXN], B[PW_MAXN * PW_MAXN];
   float a32[PW_MAXN * PW_MAXN];
   float v32[PW_MAXN * PW_MAXN];
   RotWS<float> r32;
   RotWS<double> r64;
 };
 
-// C = op(X) Y over m x m matrices (stride m): op = transpose when tx; lane-parallel entries
-__device__ __forceinline__ void warp_mm(const double* X, const double* Y, double* C, int m, bool tx, int lane) {
-  for (int e = lane; e < m * m; e += 32) {
-    const int i = e / m, j = e - i * m;
-    double acc = 0.0;
-    for (int k = 0; k < m; ++k) acc = fma(tx ? X[k * m + i] : X[i * m + k], Y[k * m + j], acc);
-    C[e] = acc;
+// (i, j), i <= j, of the t-th entry of the upper triangle of an m x m matrix, row by row
+__device__ __forceinline__ void upper_ij(int t, int m, int& i, int& j) {
+  i = 0;
+  while (t >= m - i) {
+    t -= m - i;
+    ++i;
   }
-  __syncwarp();
+  j = i + t;
 }
 
 // PSD projection of w.H (n x n symmetric, stored with stride m = n rounded up to even, padding
 // rows / columns zero); all 32 lanes of the warp call it.
+//   1. scale by a power of two (exact): max |A| in [1, 2);
+//   2. FP32 round-robin Jacobi: eigenvector estimate X (orthonormal to ~1e-7);
+//   3. one Newton-Schulz step X <- X (3 I - X^T X) / 2 in FP64 (orthonormal to ~1e-14);
+//   4. B = X^T A X (FP64), refined by FP64 Jacobi sweeps until its off-diagonal entries are
+//      below 1e-13 max|A| -- the well-separated part needs one sweep, close or tiny eigenvalues
+//      (the barrier's Hessian spans many orders of magnitude) as many as they take;
+//   5. H = X max(diag B, 0) X^T (FP64), scaled back.
 __device__ void warp_psd_project(ProjWS& w, int n, int lane) {
-  const int m = n + (n & 1);
-  // FP32 copy scaled by a power of two so that its squares stay far from the FP32 range limits
+  const int m = n + (n & 1), mm = m * m, nu = m * (m + 1) / 2;
   double mx = 0.0;
-  for (int e = lane; e < m * m; e += 32) mx = fmax(mx, fabs(w.H[e]));
+  for (int e = lane; e < mm; e += 32) mx = fmax(mx, fabs(w.H[e]));
   mx = warp_max(mx);
   if (!(mx > 0.0)) return;  // zero block: already its own projection
-  const double sc = ldexp(1.0, -ilogb(mx));
-  for (int e = lane; e < m * m; e += 32) {
+  const int ex = ilogb(mx);
+  const double sc = ldexp(1.0, -ex);
+  for (int e = lane; e < mm; e += 32) {
     const int i = e / m, j = e - i * m;
-    w.a32[e] = (float)(w.H[e] * sc);
+    const double v = w.H[e] * sc;
+    w.H[e] = v;
+    w.a32[e] = (float)v;
     w.v32[e] = i == j ? 1.f : 0.f;
   }
   __syncwarp();
   warp_jacobi<float>(w.a32, w.v32, m, 10, 1e-12f, 1e-9f, w.r32, lane);
-  for (int e = lane; e < m * m; e += 32) w.Q[e] = (double)w.v32[e];
+  for (int e = lane; e < mm; e += 32) w.X[e] = (double)w.v32[e];
   __syncwarp();
-  // two Newton-Schulz steps: Q <- Q (3 I - Q^T Q) / 2 (orthogonality error 1e-7 -> 1e-14 -> eps)
-  for (int it = 0; it < 2; ++it) {
-    warp_mm(w.Q, w.Q, w.T, m, true, lane);
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = e / m, j = e - i * m;
-      double acc = 0.0;
-      for (int k = 0; k < m; ++k) acc = fma(w.Q[i * m + k], w.T[k * m + j], acc);
-      w.B[e] = 1.5 * w.Q[e] - 0.5 * acc;
-    }
-    __syncwarp();
-    for (int e = lane; e < m * m; e += 32) w.Q[e] = w.B[e];
-    __syncwarp();
-  }
-  warp_mm(w.H, w.Q, w.T, m, false, lane);  // T = H Q
-  for (int e = lane; e < m * m; e += 32) {  // B = Q^T T, symmetric by construction
-    const int i = e / m, j = e - i * m;
-    const int a = i < j ? i : j, b = i < j ? j : i;
+  for (int t = lane; t < nu; t += 32) {  // T = X^T X (upper, mirrored)
+    int i, j;
+    upper_ij(t, m, i, j);
     double acc = 0.0;
-    for (int k = 0; k < m; ++k) acc = fma(w.Q[k * m + a], w.T[k * m + b], acc);
-    w.B[e] = acc;
+    for (int k = 0; k < m; ++k) acc = fma(w.X[k * m + i], w.X[k * m + j], acc);
+    w.T[i * m + j] = w.T[j * m + i] = acc;
   }
   __syncwarp();
-  warp_jacobi<double>(w.B, w.Q, m, 4, 1e-30, 1e-18, w.r64, lane);
-  for (int e = lane; e < m * m; e += 32) {  // H = Q max(diag B, 0) Q^T
+  for (int e = lane; e < mm; e += 32) {  // B = X (3 I - T) / 2
     const int i = e / m, j = e - i * m;
-    const int a = i < j ? i : j, b = i < j ? j : i;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(w.X[i * m + k], w.T[k * m + j], acc);
+    w.B[e] = 1.5 * w.X[e] - 0.5 * acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < mm; e += 32) {  // T = A X
+    const int i = e / m, j = e - i * m;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(w.H[i * m + k], w.B[k * m + j], acc);
+    w.T[e] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < mm; e += 32) w.X[e] = w.B[e];
+  __syncwarp();
+  for (int t = lane; t < nu; t += 32) {  // B = X^T T (upper, mirrored)
+    int i, j;
+    upper_ij(t, m, i, j);
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(w.X[k * m + i], w.T[k * m + j], acc);
+    w.B[i * m + j] = w.B[j * m + i] = acc;
+  }
+  __syncwarp();
+  warp_jacobi_refine(w.B, w.X, m, 6, 1e-13, w.r64, lane);
+  const double isc = ldexp(1.0, ex);
+  for (int t = lane; t < nu; t += 32) {  // H = X max(diag B, 0) X^T
+    int i, j;
+    upper_ij(t, m, i, j);
     double acc = 0.0;
     for (int k = 0; k < m; ++k) {
       const double lk = w.B[k * m + k];
-      if (lk > 0.0) acc = fma(w.Q[a * m + k] * lk, w.Q[b * m + k], acc);
+      if (lk > 0.0) acc = fma(w.X[i * m + k] * lk, w.X[j * m + k], acc);
     }
-    w.H[e] = acc;
+    w.H[i * m + j] = w.H[j * m + i] = acc * isc;
   }
   __syncwarp();
 }

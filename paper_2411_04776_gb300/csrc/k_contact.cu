@@ -448,20 +448,23 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
         atomicAdd(&d.vals[val_addr(bp, e)], kap * H3[e]);
     }
   } else if (ns > 1) {
-    d.cwork[atomicAdd(d.cwork_n, 1)] = i;
+    const int pos = atomicAdd(d.cwork_n, 1);
+    d.cwork[pos] = i;
+    if (pos < d.crec_cap) d.crec[pos] = pb;  // the warp kernel starts from this setup
   }
 }
 
 // Contact assembly, part 2: one warp per listed pair.  The lanes form the barrier Hessian block
-// on the pair's free gel points entry by entry, the warp projects it to PSD, and the lanes add it
-// to the sliced BSR.
+// on the pair's free gel points (warp_pair_block), the warp projects it to PSD, and the lanes add
+// it to the sliced BSR.  The pair's setup comes from the record part 1 stored (recomputed by one
+// lane for pairs beyond the record capacity).
 constexpr int CW_WARPS = 4;
 
 struct ContactWS {
   PairBarrier pb;
   ProjWS pj;
   double P[4][3];
-  int rows[4], slots[4], bp[16];
+  int rows[4], slots[4], fd[PW_MAXN], bp[16];
   int ns, g;
 };
 
@@ -473,27 +476,33 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d) {
   const int n = *d.cwork_n;
   for (int k = blockIdx.x * CW_WARPS + (threadIdx.x >> 5); k < n; k += gridDim.x * CW_WARPS) {
     const int i = d.cwork[k];
+    if (k < d.crec_cap) {
+      const double* src = reinterpret_cast<const double*>(d.crec + k);
+      double* dst = reinterpret_cast<double*>(&w.pb);
+      for (int q = lane; q < (int)(sizeof(PairBarrier) / sizeof(double)); q += 32) dst[q] = src[q];
+    }
     if (lane == 0) {
       const int4 pr = d.pairs[i];
-      pair_points(d, pr, 0.0, false, w.P, w.rows);
       const GelInfo& G = d.gi[pr.w];
-      pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, w.P, G.dhat, pair_eps_x(d, pr), w.pb);
+      int rows[4];
+      if (k >= d.crec_cap) {
+        pair_points(d, pr, 0.0, false, w.P, rows);
+        pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, w.P, G.dhat, pair_eps_x(d, pr), w.pb);
+      } else {
+        pair_rows(d, pr, rows);
+      }
       int ns = 0;
-      for (int q = 0; q < 4; ++q)
-        if (w.rows[q] >= 0 && (w.pb.involved >> q) & 1) w.slots[ns++] = q;
+      for (int q = 0; q < 4; ++q) {
+        w.rows[q] = rows[q];
+        if (rows[q] >= 0 && (w.pb.involved >> q) & 1) w.slots[ns++] = q;
+      }
+      for (int q = 0; q < 3 * ns; ++q) w.fd[q] = 3 * w.slots[q / 3] + q % 3;
       w.ns = ns;
       w.g = pr.w;
     }
     __syncwarp();
     const int ns = w.ns, nf = 3 * ns, m = nf + (nf & 1);
-    for (int e = lane; e < m * m; e += 32) {
-      const int r = e / m, c = e - r * m;
-      const int a = r < c ? r : c, b = r < c ? c : r;  // same formula order for (r, c) and (c, r)
-      double v = 0.0;
-      if (b < nf) v = pair_hess_entry(w.pb, 3 * w.slots[a / 3] + a % 3, 3 * w.slots[b / 3] + b % 3);
-      w.pj.H[e] = v;
-    }
-    __syncwarp();
+    warp_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, lane);
     warp_psd_project(w.pj, nf, lane);
     const int g = w.g;
     if (lane < ns * ns) {
@@ -611,7 +620,7 @@ struct EvalWS {
   ProjWS pj;
   double P[4][3];
   int act, nf;
-  int fd[PW_MAXN];
+  int fd[PW_MAXN], all[PW_MAXN];
 };
 
 __global__ void __launch_bounds__(128) k_eval_pairs(int n, const int* kind, const double* Pin, double dhat,
@@ -642,20 +651,21 @@ __global__ void __launch_bounds__(128) k_eval_pairs(int n, const int* kind, cons
   __syncwarp();
   const bool act = w.act != 0;
   if (go && lane < 12) go[12 * i + lane] = act ? pair_grad_entry(w.pb, lane) : 0.0;
-  if (Ho)
-    for (int e = lane; e < 144; e += 32) {
-      const int r = e / 12, c = e - r * 12;
-      Ho[144 * (size_t)i + e] = act ? pair_hess_entry(w.pb, r < c ? r : c, r < c ? c : r) : 0.0;
-    }
-  const int nf = w.nf;
-  if (!act || nf == 0 || !Ho) return;
-  const int m = nf + (nf & 1);
-  for (int e = lane; e < m * m; e += 32) {
-    const int r = e / m, c = e - r * m;
-    const int a = r < c ? r : c, b = r < c ? c : r;
-    w.pj.H[e] = b < nf ? pair_hess_entry(w.pb, w.fd[a], w.fd[b]) : 0.0;
+  if (!act) {
+    if (Ho)
+      for (int e = lane; e < 144; e += 32) Ho[144 * (size_t)i + e] = 0.0;
+    return;
   }
-  __syncwarp();
+  if (Ho) {  // the whole 12 x 12 Hessian through the same lane-parallel block code
+    if (lane < 12) w.all[lane] = lane;
+    __syncwarp();
+    warp_pair_block(w.pb, w.all, 12, 12, w.pj.T, w.pj.H, lane);
+    for (int e = lane; e < 144; e += 32) Ho[144 * (size_t)i + e] = w.pj.H[e];
+  }
+  const int nf = w.nf;
+  if (nf == 0 || !Ho) return;
+  const int m = nf + (nf & 1);
+  warp_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, lane);
   warp_psd_project(w.pj, nf, lane);
   for (int e = lane; e < nf * nf; e += 32) {
     const int r = e / nf, c = e - r * nf;
@@ -705,6 +715,8 @@ void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st)
   k_pair_ranges<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, skip_conv);
   count_launch(1);
 }
+size_t pair_record_doubles() { return sizeof(PairBarrier) / sizeof(double); }
+
 void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   if (d.npslots <= 0) return;
   cudaMemsetAsync(d.cwork_n, 0, sizeof(int), st);

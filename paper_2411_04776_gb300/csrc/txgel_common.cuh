@@ -84,6 +84,8 @@ struct GelVar {  // per gel, written by the device
   int flags;                 // 1 hash overflow, 2 ACCD cap, 4 inverted tet, 8 ACCD hit, 16 pattern miss
 };
 
+struct PairBarrier;  // barrier setup of one contact pair (dev_pairwarp.cuh)
+
 // Everything the kernels touch, passed by value.
 struct Dev {
   int n_gels;
@@ -155,6 +157,8 @@ struct Dev {
   double* pe;      // per pair slot: kappa b(d) at the last energy evaluation
   int* cwork;      // contact pairs with two or more free gel points (pair slots), and their count
   int* cwork_n;
+  PairBarrier* crec;  // their barrier setup (the first crec_cap of them)
+  int crec_cap;
   int* err;
 };
 

@@ -54,6 +54,7 @@ cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas
 cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
                              int refine_max, cudaStream_t st);
 int pcg_max_ctas_per_sm(int max_slices);
+size_t pair_record_doubles();
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
 cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, double eta,
                            int maxit, int refine_max, int wmax, cudaStream_t st);
@@ -90,6 +91,9 @@ constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
 // the SpMV); FP32 keeps groups small so that their barriers are cheap
 constexpr int PCG_SLICES_FP64 = 4;
 constexpr int PCG_SLICES_MIXED = 4;
+// contact pairs whose barrier setup is kept for the warp Hessian kernel (others recompute it)
+constexpr int CREC_PER_GEL = 512;
+constexpr int CREC_BASE = 8192;
 constexpr int PIECE_HOST = 512;
 
 #define CK(call)                                                          \
@@ -503,7 +507,9 @@ tx_status alloc_pairs(tx_batch* b) {
   b->d.pslot_gel = b->pair_mem.get<int>(total);
   b->d.pe = b->pair_mem.get<double>(total);
   b->d.cwork = b->pair_mem.get<int>(total);
-  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork) return TX_ERR_OOM;
+  b->d.crec_cap = std::min(total, CREC_PER_GEL * b->n + CREC_BASE);
+  b->d.crec = reinterpret_cast<PairBarrier*>(b->pair_mem.get<double>((size_t)b->d.crec_cap * pair_record_doubles()));
+  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork || !b->d.crec) return TX_ERR_OOM;
   b->d.npslots = total;
   std::vector<int> slot(total);
   for (int g = 0; g < b->n; ++g)
@@ -1770,7 +1776,7 @@ size_t tx_gel_footprint_bytes(const tx_gel_desc* desc) {
   bytes += nbp * (4 + 4 + 4 + (mixed ? 36 : 72));
   bytes += nq * (4 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;
   bytes += ((size_t)m.niv + m.nit + m.ie.size()) * 2 * sizeof(double4_32a);  // primitive boxes
-  bytes += (size_t)initial_pcap(m) * 32;
+  bytes += (size_t)initial_pcap(m) * 32 + (size_t)CREC_PER_GEL * pair_record_doubles() * 8;
   return bytes;
 }
 

@@ -103,7 +103,7 @@ def test_pair_kernel_matches_oracle():
         assert s == 0
         assert abs(b[i] - bo) <= 1e-10 * abs(bo) + 1e-30
         assert np.abs(g[i] - go).max() <= 1e-8 * np.abs(go).max()
-        assert np.abs(H[i] - Ho).max() <= 1e-7 * np.abs(Ho).max(), (i, kinds[i], ty)
+        assert np.abs(H[i] - Ho).max() <= 1e-9 * np.abs(Ho).max(), (i, kinds[i], ty)
     assert {(0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 3)} <= seen
 
 
