@@ -1,16 +1,17 @@
-// Persistent PCG for groups whose CTAs own at most one 32-row slice per warp (a single gel, or
-// a few gels, spread over many SMs).  Every warp keeps its slice for the whole solve: the CTA
-// copies its slices of the sliced BSR (values and column indices) into shared memory once, the
-// row vectors of the solve (r, pp, s, the direction, the preconditioner block) stay in the
-// owning lane's registers, and only u -- the vector the SpMV gathers from neighbouring rows --
-// goes through global memory (L2).  Per iteration this leaves the gathers of u, the group sum and
-// the group barrier as the only global traffic.  Arithmetic, stopping rules and the fixed-order
-// reductions are those of the kernels in k_solve.cu.
+// Persistent PCG for groups whose CTAs own at most one 32-row slice per warp (a single gel, or a
+// few gels, spread over many SMs), as pipelined CG with one group barrier per iteration.  Every
+// warp keeps its slice for the whole solve: the CTA copies its slices of the sliced BSR (values
+// and column indices) into shared memory once, the row vectors of the solve stay in the owning
+// lane's registers, and only the vector the SpMV gathers from neighbouring rows goes through
+// global memory (L2).  Per iteration this leaves those gathers, the group sum and the group
+// barrier as the only global traffic.  Stopping rules and the fixed-order reductions are those
+// of the kernels in k_solve.cu.
 #include "dev_pcg.cuh"
 
 namespace txg {
 
-constexpr int RES_MAXW = 8;  // warps (slices) per CTA
+constexpr int RES_MAXW = 8;    // warps (slices) per CTA
+constexpr int RES_MAXNC = 256; // CTAs of one group (exchange slots a lane prefetches: 8)
 
 // warp-owned image of slice s in shared memory: values [k][9][32], column indices [k][32]
 template <typename V>
@@ -25,26 +26,39 @@ __device__ __forceinline__ int res_load(const Dev& d, int s, const V* gval, V* s
   return w;
 }
 
-// y = A u for the lane's row, values from shared memory, u gathered from global memory
 template <typename V, typename U, typename A>
-__device__ __forceinline__ void res_spmv(const V* sv, const int* sc, int w, int lane, const U* u, A& a0, A& a1,
-                                         A& a2) {
-  a0 = a1 = a2 = A(0);
-#pragma unroll 8
-  for (int k = 0; k < w; ++k) {
-    const int c = sc[32 * k + lane];
-    const U uc = u[c];
-    const V* v = sv + 288 * k + lane;
-    a0 = fma((A)v[0], (A)uc.x, a0);
-    a1 = fma((A)v[96], (A)uc.x, a1);
-    a2 = fma((A)v[192], (A)uc.x, a2);
-    a0 = fma((A)v[32], (A)uc.y, a0);
-    a1 = fma((A)v[128], (A)uc.y, a1);
-    a2 = fma((A)v[224], (A)uc.y, a2);
-    a0 = fma((A)v[64], (A)uc.z, a0);
-    a1 = fma((A)v[160], (A)uc.z, a1);
-    a2 = fma((A)v[256], (A)uc.z, a2);
+__device__ __forceinline__ void res_block(const V* sv, const int* sc, int k, int lane, const U* u, A& a0, A& a1,
+                                          A& a2) {
+  const int c = sc[32 * k + lane];
+  const U uc = u[c];
+  const V* v = sv + 288 * k + lane;
+  a0 = fma((A)v[0], (A)uc.x, a0);
+  a1 = fma((A)v[96], (A)uc.x, a1);
+  a2 = fma((A)v[192], (A)uc.x, a2);
+  a0 = fma((A)v[32], (A)uc.y, a0);
+  a1 = fma((A)v[128], (A)uc.y, a1);
+  a2 = fma((A)v[224], (A)uc.y, a2);
+  a0 = fma((A)v[64], (A)uc.z, a0);
+  a1 = fma((A)v[160], (A)uc.z, a1);
+  a2 = fma((A)v[256], (A)uc.z, a2);
+}
+
+// y = A u for the lane's row: values from shared memory, u gathered from global memory; even and
+// odd blocks accumulate separately (six independent FMA chains), then add
+template <typename V, typename U, typename A>
+__device__ __forceinline__ void res_spmv(const V* sv, const int* sc, int w, int lane, const U* u, A& y0, A& y1,
+                                         A& y2) {
+  A a0 = A(0), a1 = A(0), a2 = A(0), b0 = A(0), b1 = A(0), b2 = A(0);
+  int k = 0;
+#pragma unroll 4
+  for (; k + 1 < w; k += 2) {
+    res_block(sv, sc, k, lane, u, a0, a1, a2);
+    res_block(sv, sc, k + 1, lane, u, b0, b1, b2);
   }
+  if (k < w) res_block(sv, sc, k, lane, u, a0, a1, a2);
+  y0 = a0 + b0;
+  y1 = a1 + b1;
+  y2 = a2 + b2;
 }
 
 // CG scalars with two levels of division: beta = ga / ga_prev and t = ga / al_prev are independent
@@ -63,43 +77,131 @@ __device__ __forceinline__ void cg_scalars(int k, double ga, double de, double g
 // shared memory: [dsm: 4 per slice][values: warps x wmax x 288][columns: warps x wmax x 32]
 template <typename V>
 __device__ __forceinline__ void res_smem(double* dyn, int max_slices, int wmax, double*& dsm, V*& sv, int*& sc) {
-  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
+  const int nw = max_slices, wid = threadIdx.x >> 5;  // slice warps; the control warp has no slice
   dsm = dyn;
   V* vbase = reinterpret_cast<V*>(dyn + 4 * max_slices);
   sv = vbase + (size_t)wid * wmax * 288;
   sc = reinterpret_cast<int*>(vbase + (size_t)nw * wmax * 288) + (size_t)wid * wmax * 32;
 }
 
-__global__ void __launch_bounds__(32 * RES_MAXW) k_pcg64_res(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
+// Split group sums of the pipelined kernels (one group barrier between post and collect).
+// post: every CTA adds the per-warp partials dsm[4 w + k] of each of its gels in warp order; a
+// CTA alone in its group keeps the totals, a CTA of a multi-CTA group (one gel) publishes its sum
+// in exchange set `set` of d.part.  The prefetch / finish pair of collect adds a multi-CTA group's
+// published sums in CTA order; the prefetch loads them into registers before the SpMV so that
+// their latency overlaps it.  Bitwise identical in every CTA of the group.
+__device__ __forceinline__ void res_post(const Dev& d, const PcgCta& c, const double* dsm, int k0, int k1, int set,
+                                         double (*tot)[4]) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nk = k1 - k0;
+  for (int t = wid; t < c.ng * nk; t += (int)(blockDim.x >> 5)) {
+    const int j = t / nk, k = k0 + t % nk;
+    const GelInfo& G = d.gi[c.g0 + j];
+    const int a = max(c.s0, G.s0), b = min(c.s1, G.s0 + G.ns);
+    double v = 0.0;
+    for (int s = a + lane; s < b; s += 32) v += dsm[(s - c.s0) * 4 + k];
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (c.nc == 1)
+        tot[j][k] = v;
+      else
+        d.part[(size_t)(4 * set + k) * gridDim.x + blockIdx.x] = v;
+    }
+  }
+}
+
+struct ResPrefetch {
+  double v[RES_MAXNC / 32];
+};
+
+__device__ __forceinline__ void res_prefetch(const Dev& d, const PcgCta& c, int k0, int k1, int set, ResPrefetch& pf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < RES_MAXNC / 32; ++t) {
+    const int q = c.c0 + lane + 32 * t;
+    pf.v[t] = (c.nc > 1 && wid < k1 - k0 && q < c.c0 + c.nc) ? d.part[(size_t)(4 * set + k0 + wid) * gridDim.x + q] : 0.0;
+  }
+}
+
+__device__ __forceinline__ void res_finish(const PcgCta& c, int k0, int k1, const ResPrefetch& pf, double (*tot)[4]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (c.nc > 1 && wid < k1 - k0) {
+    double v = 0.0;
+#pragma unroll
+    for (int t = 0; t < RES_MAXNC / 32; ++t) v += pf.v[t];
+    v = warp_sum(v);
+    if (lane == 0) tot[0][k0 + wid] = v;
+  }
+  __syncthreads();
+}
+
+// The control warp's collect of quantities [k0, k1) from exchange set `set` (no block barrier): a
+// multi-CTA group's published CTA sums are added in CTA order; a one-CTA group already has them.
+__device__ __forceinline__ void ctl_collect(const Dev& d, const PcgCta& c, int k0, int k1, int set, double (*tot)[4]) {
+  if (c.nc == 1) return;
+  const int lane = threadIdx.x & 31;
+  double v[3][RES_MAXNC / 32];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int t = 0; t < RES_MAXNC / 32; ++t) {
+      const int q = c.c0 + lane + 32 * t;
+      v[k][t] = (k < k1 - k0 && q < c.c0 + c.nc) ? d.part[(size_t)(4 * set + k0 + k) * gridDim.x + q] : 0.0;
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double a = 0.0;
+#pragma unroll
+    for (int t = 0; t < RES_MAXNC / 32; ++t) a += v[k][t];
+    a = warp_sum(a);
+    if (lane == 0 && k < k1 - k0) tot[0][k0 + k] = a;
+  }
+  __syncwarp();
+}
+
+// Pipelined CG (Ghysels & Vanroose 2014, preconditioned): with m = M^-1 w and n = A m the
+// recurrences z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p, x += alpha p,
+// r -= alpha s, u -= alpha q, w -= alpha z keep u = M^-1 r and w = A u, so the dot products
+// (r, u), (w, u), (r, r) of the next iteration are formed with the vector updates and their group
+// reduction overlaps the next SpMV: one group barrier per iteration.  m is exchanged through two
+// alternating global buffers (its SpMV reads the neighbours' m of this iteration while they may
+// already write the next one).  Same scalars (alpha, beta) and stopping rule as the CG of
+// k_solve.cu: |r| <= eta |b| or maxit iterations.  One extra (control) warp per CTA collects the
+// group totals and takes the per-gel decisions while the slice warps run the SpMV, so neither is
+// on the critical path; run flags are double-buffered (the slice warps read this iteration's,
+// the control warp writes the next one's).
+__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
                                                              int wmax) {
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
-  __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[2][PCG_MAXG];
   __shared__ int s_fail, s_any;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
   PcgCta c = pcg_cta(d, plan);
   double* dsm;
   double* sv;
   int* sc;
   res_smem<double>(dyn, plan.max_slices, wmax, dsm, sv, sc);
   if (threadIdx.x == 0) s_fail = 0;
-  for (int j = threadIdx.x; j < c.ng; j += blockDim.x) {
-    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
-    run[j] = gact[j];
+  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
+    gact[q] = d.gc[c.g0 + q].phase == phase ? 1 : 0;
+    run[0][q] = gact[q];
   }
   __syncthreads();
   const int s = c.s0 + wid, row = 32 * s + lane;
   const bool has = s < c.s1;
   const int j = has ? plan.slice_gel[s] - c.g0 : 0;
   const bool mine = has && gact[j];
+  const bool fixed = mine && d.fixed[row];
+  double4_32a* mbuf[2] = {d.pp, d.s};
   int w = 0;
-  double r0 = 0, r1 = 0, r2 = 0, u0 = 0, u1 = 0, u2 = 0, p0 = 0, p1 = 0, p2 = 0;
-  double q0 = 0, q1 = 0, q2 = 0, x0 = 0, x1 = 0, x2 = 0, w0 = 0, w1 = 0, w2 = 0;
   double M[9];
   for (int e = 0; e < 9; ++e) M[e] = 0.0;
-  const bool fixed = mine && d.fixed[row];
-  // ---- init: r = -grad, x = 0, u = M^-1 r; partial |b|^2
+  double x0 = 0, x1 = 0, x2 = 0, r0 = 0, r1 = 0, r2 = 0, u0 = 0, u1 = 0, u2 = 0, w0 = 0, w1 = 0, w2 = 0;
+  double z0 = 0, z1 = 0, z2 = 0, q0 = 0, q1 = 0, q2 = 0, t0 = 0, t1 = 0, t2 = 0, p0 = 0, p1 = 0, p2 = 0;
+  double m0 = 0, m1 = 0, m2 = 0;
+  // ---- init: r = b = -grad, x = 0, u = M^-1 r; |b|^2
   if (mine) {
     w = res_load<double>(d, s, d.vals, sv, sc, lane);
     for (int e = 0; e < 9; ++e) M[e] = d.Minv[9 * row + e];
@@ -114,16 +216,90 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg64_res(Dev d, int phase, P
     const double bb = warp_sum(fma(r2, r2, fma(r1, r1, r0 * r0)));
     if (lane == 0) dsm[4 * wid + 3] = bb;
   }
-  if (!group_sum(d, c, dsm, 3, 4, tot, &s_fail)) return;
+  res_post(d, c, dsm, 3, 4, 0, tot);
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  {
+    ResPrefetch pf;
+    res_prefetch(d, c, 3, 4, 0, pf);
+    res_finish(c, 3, 4, pf, tot);
+  }
   for (int q = threadIdx.x; q < c.ng; q += blockDim.x) bbj[q] = tot[q][3];
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;  // u complete before the SpMV
-  for (int k = 1;; ++k) {
-    // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
+  // ---- w = A u, m = M^-1 w; dot products of iteration 0
+  if (has) {
+    double ga = 0.0, de = 0.0, rr = 0.0;
+    if (mine) {
+      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.u, w0, w1, w2);
+      if (fixed) w0 = w1 = w2 = 0.0;
+      m0 = fma(M[2], w2, fma(M[1], w1, M[0] * w0));
+      m1 = fma(M[5], w2, fma(M[4], w1, M[3] * w0));
+      m2 = fma(M[8], w2, fma(M[7], w1, M[6] * w0));
+      mbuf[0][row] = make_double4_32a(m0, m1, m2, 0.0);
+      ga = fma(r2, u2, fma(r1, u1, r0 * u0));
+      de = fma(w2, u2, fma(w1, u1, w0 * u0));
+      rr = fma(r2, r2, fma(r1, r1, r0 * r0));
+    }
+    ga = warp_sum(ga);
+    de = warp_sum(de);
+    rr = warp_sum(rr);
+    if (lane == 0) {
+      dsm[4 * wid + 0] = ga;
+      dsm[4 * wid + 1] = de;
+      dsm[4 * wid + 2] = rr;
+    }
+  }
+  res_post(d, c, dsm, 0, 3, 0, tot);
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  for (int i = 0;; ++i) {
+    const int par = i & 1;
+    double n0 = 0, n1 = 0, n2 = 0;
+    if (wid == ctl) {
+      ctl_collect(d, c, 0, 3, par, tot);
+      int any = 0;
+      for (int q = lane; q < c.ng; q += 32) {
+        run[par ^ 1][q] = 0;
+        if (!run[par][q]) continue;
+        const double ga = tot[q][0], de = tot[q][1], rr = tot[q][2];
+        if (!(rr > eta2 * bbj[q]) || i >= maxit) {
+          if (blockIdx.x == c.c0) {
+            d.gv[c.g0 + q].pcg_it = i;
+            d.gv[c.g0 + q].bb = bbj[q];
+            d.gv[c.g0 + q].pcg_done = 1;
+          }
+          continue;
+        }
+        any = 1;
+        run[par ^ 1][q] = 1;
+        double al, be;
+        cg_scalars(i + 1, ga, de, gprev[q], aprev[q], al, be);
+        gprev[q] = ga;
+        aprev[q] = al;
+        alj[q] = al;
+        bej[q] = be;
+      }
+      any = __any_sync(0xffffffffu, any);
+      if (lane == 0) s_any = any;
+    } else if (has && run[par][j]) {
+      res_spmv<double, double4_32a, double>(sv, sc, w, lane, mbuf[par], n0, n1, n2);
+      if (fixed) n0 = n1 = n2 = 0.0;
+    }
+    __syncthreads();
+    if (!s_any) break;
     if (has) {
       double ga = 0.0, de = 0.0, rr = 0.0;
-      if (run[j]) {
-        res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.u, w0, w1, w2);
-        if (fixed) w0 = w1 = w2 = 0.0;
+      if (run[par ^ 1][j]) {
+        const double be = bej[j], al = alj[j];
+        z0 = fma(be, z0, n0); z1 = fma(be, z1, n1); z2 = fma(be, z2, n2);
+        q0 = fma(be, q0, m0); q1 = fma(be, q1, m1); q2 = fma(be, q2, m2);
+        t0 = fma(be, t0, w0); t1 = fma(be, t1, w1); t2 = fma(be, t2, w2);
+        p0 = fma(be, p0, u0); p1 = fma(be, p1, u1); p2 = fma(be, p2, u2);
+        x0 = fma(al, p0, x0); x1 = fma(al, p1, x1); x2 = fma(al, p2, x2);
+        r0 = fma(-al, t0, r0); r1 = fma(-al, t1, r1); r2 = fma(-al, t2, r2);
+        u0 = fma(-al, q0, u0); u1 = fma(-al, q1, u1); u2 = fma(-al, q2, u2);
+        w0 = fma(-al, z0, w0); w1 = fma(-al, z1, w1); w2 = fma(-al, z2, w2);
+        m0 = fma(M[2], w2, fma(M[1], w1, M[0] * w0));
+        m1 = fma(M[5], w2, fma(M[4], w1, M[3] * w0));
+        m2 = fma(M[8], w2, fma(M[7], w1, M[6] * w0));
+        mbuf[par ^ 1][row] = make_double4_32a(m0, m1, m2, 0.0);
         ga = fma(r2, u2, fma(r1, u1, r0 * u0));
         de = fma(w2, u2, fma(w1, u1, w0 * u0));
         rr = fma(r2, r2, fma(r1, r1, r0 * r0));
@@ -137,58 +313,22 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg64_res(Dev d, int phase, P
         dsm[4 * wid + 2] = rr;
       }
     }
-    if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
-      if (!run[q]) continue;
-      const double ga = tot[q][0], de = tot[q][1], rr = tot[q][2];
-      if (!(rr > eta2 * bbj[q]) || k > maxit) {
-        run[q] = 0;
-        if (blockIdx.x == c.c0) {
-          d.gv[c.g0 + q].pcg_it = k - 1;
-          d.gv[c.g0 + q].bb = bbj[q];
-          d.gv[c.g0 + q].pcg_done = 1;
-        }
-        continue;
-      }
-      s_any = 1;
-      double al, be;
-      cg_scalars(k, ga, de, gprev[q], aprev[q], al, be);
-      gprev[q] = ga;
-      aprev[q] = al;
-      alj[q] = al;
-      bej[q] = be;
-    }
-    __syncthreads();
-    if (!s_any) break;
-    // ---- vector updates (registers); u to global memory for the neighbours' SpMV
-    if (has && run[j]) {
-      const double be = bej[j], al = alj[j];
-      p0 = fma(be, p0, u0); p1 = fma(be, p1, u1); p2 = fma(be, p2, u2);
-      q0 = fma(be, q0, w0); q1 = fma(be, q1, w1); q2 = fma(be, q2, w2);
-      x0 = fma(al, p0, x0); x1 = fma(al, p1, x1); x2 = fma(al, p2, x2);
-      r0 = fma(-al, q0, r0); r1 = fma(-al, q1, r1); r2 = fma(-al, q2, r2);
-      u0 = fma(M[2], r2, fma(M[1], r1, M[0] * r0));
-      u1 = fma(M[5], r2, fma(M[4], r1, M[3] * r0));
-      u2 = fma(M[8], r2, fma(M[7], r1, M[6] * r0));
-      d.u[row] = make_double4_32a(u0, u1, u2, 0.0);
-    }
+    res_post(d, c, dsm, 0, 3, par ^ 1, tot);
     if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
   }
   if (mine) d.p[row] = make_double4_32a(x0, x1, x2, 0.0);
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
-__global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phase, PcgPlan plan, double eta2,
+__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int phase, PcgPlan plan, double eta2,
                                                                  int maxit, int refine_max, int wmax) {
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
-  __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
-  __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG];
+  __shared__ float alj[PCG_MAXG], bej[PCG_MAXG], gprf[PCG_MAXG], aprf[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[2][PCG_MAXG], itj[PCG_MAXG];
   __shared__ int s_fail, s_any;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
   PcgCta c = pcg_cta(d, plan);
   double* dsm;
   float* sv;
@@ -206,6 +346,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phas
   const int j = has ? plan.slice_gel[s] - c.g0 : 0;
   const bool mine = has && gact[j];
   const bool fixed = mine && d.fixed[row];
+  float4* mbuf[2] = {d.pp32, d.s32};
   int w = 0;
   double g0 = 0, g1 = 0, g2 = 0, R0 = 0, R1 = 0, R2 = 0, P0 = 0, P1 = 0, P2 = 0;  // FP64: grad, r, p
   float M[9];
@@ -224,14 +365,20 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phas
       dsm[4 * wid + 2] = bb;
     }
   }
-  if (!group_sum(d, c, dsm, 2, 4, tot, &s_fail)) return;
+  res_post(d, c, dsm, 2, 4, 0, tot);
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  {
+    ResPrefetch pf;
+    res_prefetch(d, c, 2, 4, 0, pf);
+    res_finish(c, 2, 4, pf, tot);
+  }
   for (int q = threadIdx.x; q < c.ng; q += blockDim.x) bbj[q] = tot[q][3];
   __syncthreads();
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
-      inner[q] = 0;
+      inner[0][q] = 0;
       if (!run[q]) continue;
       const double rr = tot[q][2], bb = bbj[q];
       if (!(rr > eta2 * bb) || round >= refine_max) {
@@ -245,15 +392,16 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phas
         continue;
       }
       s_any = 1;
-      inner[q] = 1;
+      inner[0][q] = 1;
       tolj[q] = fmax(eta2 * bb / rr, 1e-11);
     }
     __syncthreads();
     if (!s_any) break;
-    // ---- inner init: r32 = r64, x32 = 0, u32 = M^-1 r32
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
-    const bool in = has && inner[j];
+    // ---- inner init: r = r64, x = 0, u = M^-1 r (to global), then w = A u, m = M^-1 w
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, z0 = 0.f, z1 = 0.f, z2 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    const bool in = has && inner[0][j];
     if (in) {
       r0 = (float)R0; r1 = (float)R1; r2 = (float)R2;
       u0 = fmaf(M[2], r2, fmaf(M[1], r1, M[0] * r0));
@@ -262,58 +410,95 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phas
       d.u32[row] = make_float4(u0, u1, u2, 0.f);
     }
     if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
-    for (int k = 1;; ++k) {
+    if (has) {
+      double ga = 0.0, de = 0.0, rr = 0.0;
+      if (in) {
+        res_spmv<float, float4, float>(sv, sc, w, lane, d.u32, w0, w1, w2);
+        if (fixed) w0 = w1 = w2 = 0.f;
+        m0 = fmaf(M[2], w2, fmaf(M[1], w1, M[0] * w0));
+        m1 = fmaf(M[5], w2, fmaf(M[4], w1, M[3] * w0));
+        m2 = fmaf(M[8], w2, fmaf(M[7], w1, M[6] * w0));
+        mbuf[0][row] = make_float4(m0, m1, m2, 0.f);
+        ga = warp_sum(fmaf(r2, u2, fmaf(r1, u1, r0 * u0)));
+        de = warp_sum(fmaf(w2, u2, fmaf(w1, u1, w0 * u0)));
+        rr = warp_sum(fmaf(r2, r2, fmaf(r1, r1, r0 * r0)));
+      }
+      if (lane == 0) {
+        dsm[4 * wid + 0] = ga;
+        dsm[4 * wid + 1] = de;
+        dsm[4 * wid + 2] = rr;
+      }
+    }
+    res_post(d, c, dsm, 0, 3, 0, tot);
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    // ---- inner pipelined CG in FP32
+    for (int i = 0;; ++i) {
+      const int par = i & 1;
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+      if (wid == ctl) {
+        ctl_collect(d, c, 0, 3, par, tot);
+        int any = 0;
+        for (int q = lane; q < c.ng; q += 32) {
+          inner[par ^ 1][q] = 0;
+          if (!inner[par][q]) continue;
+          const double ga = tot[q][0], de = tot[q][1], rr = tot[q][2];
+          if (i == 0) rr0j[q] = rr;
+          if (!(rr > tolj[q] * rr0j[q]) || i >= maxit) {
+            itj[q] += i;
+            continue;
+          }
+          any = 1;
+          inner[par ^ 1][q] = 1;
+          // FP32 scalars for the FP32 iteration: beta = ga / ga_prev, alpha = ga / (de - beta ga / al_prev)
+          const float gf = (float)ga, df = (float)de;
+          float al, be;
+          if (i == 0) {
+            be = 0.f;
+            al = gf / df;
+          } else {
+            be = gf / gprf[q];
+            al = gf / (df - be * (gf / aprf[q]));
+          }
+          gprf[q] = gf;
+          aprf[q] = al;
+          alj[q] = al;
+          bej[q] = be;
+        }
+        any = __any_sync(0xffffffffu, any);
+        if (lane == 0) s_any = any;
+      } else if (has && inner[par][j]) {
+        res_spmv<float, float4, float>(sv, sc, w, lane, mbuf[par], n0, n1, n2);
+        if (fixed) n0 = n1 = n2 = 0.f;
+      }
+      __syncthreads();
+      if (!s_any) break;
       if (has) {
         double ga = 0.0, de = 0.0, rr = 0.0;
-        if (inner[j]) {
-          res_spmv<float, float4, float>(sv, sc, w, lane, d.u32, w0, w1, w2);
-          if (fixed) w0 = w1 = w2 = 0.f;
-          ga = fmaf(r2, u2, fmaf(r1, u1, r0 * u0));
-          de = fmaf(w2, u2, fmaf(w1, u1, w0 * u0));
-          rr = fmaf(r2, r2, fmaf(r1, r1, r0 * r0));
+        if (inner[par ^ 1][j]) {
+          const float be = bej[j], al = alj[j];
+          z0 = fmaf(be, z0, n0); z1 = fmaf(be, z1, n1); z2 = fmaf(be, z2, n2);
+          q0 = fmaf(be, q0, m0); q1 = fmaf(be, q1, m1); q2 = fmaf(be, q2, m2);
+          t0 = fmaf(be, t0, w0); t1 = fmaf(be, t1, w1); t2 = fmaf(be, t2, w2);
+          p0 = fmaf(be, p0, u0); p1 = fmaf(be, p1, u1); p2 = fmaf(be, p2, u2);
+          x0 = fmaf(al, p0, x0); x1 = fmaf(al, p1, x1); x2 = fmaf(al, p2, x2);
+          r0 = fmaf(-al, t0, r0); r1 = fmaf(-al, t1, r1); r2 = fmaf(-al, t2, r2);
+          u0 = fmaf(-al, q0, u0); u1 = fmaf(-al, q1, u1); u2 = fmaf(-al, q2, u2);
+          w0 = fmaf(-al, z0, w0); w1 = fmaf(-al, z1, w1); w2 = fmaf(-al, z2, w2);
+          m0 = fmaf(M[2], w2, fmaf(M[1], w1, M[0] * w0));
+          m1 = fmaf(M[5], w2, fmaf(M[4], w1, M[3] * w0));
+          m2 = fmaf(M[8], w2, fmaf(M[7], w1, M[6] * w0));
+          mbuf[par ^ 1][row] = make_float4(m0, m1, m2, 0.f);
+          ga = warp_sum(fmaf(r2, u2, fmaf(r1, u1, r0 * u0)));
+          de = warp_sum(fmaf(w2, u2, fmaf(w1, u1, w0 * u0)));
+          rr = warp_sum(fmaf(r2, r2, fmaf(r1, r1, r0 * r0)));
         }
-        ga = warp_sum(ga);
-        de = warp_sum(de);
-        rr = warp_sum(rr);
         if (lane == 0) {
           dsm[4 * wid + 0] = ga;
           dsm[4 * wid + 1] = de;
           dsm[4 * wid + 2] = rr;
         }
       }
-      if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
-      if (threadIdx.x == 0) s_any = 0;
-      __syncthreads();
-      for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
-        if (!inner[q]) continue;
-        const double ga = tot[q][0], de = tot[q][1], rr = tot[q][2];
-        if (k == 1) rr0j[q] = rr;
-        if (!(rr > tolj[q] * rr0j[q]) || k > maxit) {
-          inner[q] = 0;
-          itj[q] += k - 1;
-          continue;
-        }
-        s_any = 1;
-        double al, be;
-        cg_scalars(k, ga, de, gprev[q], aprev[q], al, be);
-        gprev[q] = ga;
-        aprev[q] = al;
-        alj[q] = (float)al;
-        bej[q] = (float)be;
-      }
-      __syncthreads();
-      if (!s_any) break;
-      if (has && inner[j]) {
-        const float fb = bej[j], fa = alj[j];
-        p0 = fmaf(fb, p0, u0); p1 = fmaf(fb, p1, u1); p2 = fmaf(fb, p2, u2);
-        q0 = fmaf(fb, q0, w0); q1 = fmaf(fb, q1, w1); q2 = fmaf(fb, q2, w2);
-        x0 = fmaf(fa, p0, x0); x1 = fmaf(fa, p1, x1); x2 = fmaf(fa, p2, x2);
-        r0 = fmaf(-fa, q0, r0); r1 = fmaf(-fa, q1, r1); r2 = fmaf(-fa, q2, r2);
-        u0 = fmaf(M[2], r2, fmaf(M[1], r1, M[0] * r0));
-        u1 = fmaf(M[5], r2, fmaf(M[4], r1, M[3] * r0));
-        u2 = fmaf(M[8], r2, fmaf(M[7], r1, M[6] * r0));
-        d.u32[row] = make_float4(u0, u1, u2, 0.f);
-      }
+      res_post(d, c, dsm, 0, 3, par ^ 1, tot);
       if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
     }
     // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p (FP32 values, FP64 arithmetic)
@@ -339,7 +524,13 @@ __global__ void __launch_bounds__(32 * RES_MAXW) k_pcg_mixed_res(Dev d, int phas
       rr = warp_sum(rr);
       if (lane == 0) dsm[4 * wid + 2] = rr;
     }
-    if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
+    res_post(d, c, dsm, 2, 3, 0, tot);
+    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    {
+      ResPrefetch pf;
+      res_prefetch(d, c, 2, 3, 0, pf);
+      res_finish(c, 2, 3, pf, tot);
+    }
   }
   if (mine) d.p[row] = make_double4_32a(P0, P1, P2, 0.0);
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
@@ -354,7 +545,7 @@ size_t pcg_res_smem(bool mixed, int max_slices, int wmax) {
 
 // co-resident CTAs per SM of the resident kernel (0 if it cannot be launched so)
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax) {
-  if (max_slices > RES_MAXW) return 0;
+  if (max_slices + 1 > RES_MAXW) return 0;
   const size_t smem = pcg_res_smem(mixed, max_slices, wmax);
   const void* fn = mixed ? (const void*)k_pcg_mixed_res : (const void*)k_pcg64_res;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -362,7 +553,7 @@ int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax) {
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * max_slices, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * (max_slices + 1), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -379,11 +570,11 @@ cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nct
   if (mixed) {
     void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&refine_max,
                     (void*)&wmax};
-    return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed_res, dim3(nctas), dim3(32 * plan.max_slices), args,
+    return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed_res, dim3(nctas), dim3(32 * (plan.max_slices + 1)), args,
                                        smem, st);
   }
   void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&wmax};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg64_res, dim3(nctas), dim3(32 * plan.max_slices), args, smem,
+  return cudaLaunchCooperativeKernel((const void*)k_pcg64_res, dim3(nctas), dim3(32 * (plan.max_slices + 1)), args, smem,
                                      st);
 }
 

@@ -122,7 +122,7 @@ struct Dev {
   // PCG
   double4_32a *r, *u, *w, *pp, *s;
   float4 *u32, *w32, *pp32, *s32, *r32, *x32;
-  double* part;    // PCG: per-CTA partial sums exchanged inside a group, [4][nctas]
+  double* part;    // PCG: per-CTA partial sums exchanged inside a group, [2 sets][4][nctas]
   unsigned* bar;   // PCG: one barrier counter per group
   // surface primitives (global)
   int* sv;

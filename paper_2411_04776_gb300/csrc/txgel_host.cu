@@ -94,6 +94,7 @@ constexpr int PCG_SLICES_MIXED = 4;
 // contact pairs whose barrier setup is kept for the warp Hessian kernel (others recompute it)
 constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
+constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
 constexpr int PIECE_HOST = 512;
 
 #define CK(call)                                                          \
@@ -836,7 +837,9 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   for (int q = 0; q < nslices; ++q) b->pcg_wmax = std::max(b->pcg_wmax, (slice_off[q + 1] - slice_off[q]) / SLICE);
   {
     const int occ = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
-    b->pcg_res = occ > 0 && nctas <= nsm * occ;
+    int max_nc = 0;
+    for (const int4& q : grp) max_nc = std::max(max_nc, q.y);
+    b->pcg_res = occ > 0 && nctas <= nsm * occ && max_nc <= PCG_RES_MAXNC;
   }
   // ---- energy pieces
   for (int g = 0; g < n; ++g) {
@@ -897,7 +900,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.w = M.get<double4_32a>(rows);
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
-  d.part = M.get<double>(4 * (size_t)nctas);
+  d.part = M.get<double>(8 * (size_t)nctas);
   d.bar = M.get<unsigned>(ngroups);
   d.sv = M.get<int>(nsv);
   d.st = M.get<int4>(nst);
