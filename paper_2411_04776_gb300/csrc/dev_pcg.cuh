@@ -79,8 +79,9 @@ struct PcgCta {
 
 __device__ __forceinline__ PcgCta pcg_cta(const Dev& d, const PcgPlan& plan) {
   PcgCta c;
-  c.s0 = plan.cta_s0[blockIdx.x];
-  c.s1 = plan.cta_s0[blockIdx.x + 1];
+  const int2 r = plan.cta_rng[blockIdx.x];
+  c.s0 = r.x;
+  c.s1 = r.y;
   const int gr = plan.cta_grp[blockIdx.x];
   const int4 G = plan.grp[gr];
   c.c0 = G.x;

@@ -162,12 +162,13 @@ struct Dev {
   int* err;
 };
 
-// Static partition of the slices over the CTAs of the persistent PCG kernels.  The gels are split
-// into independent groups: a gel with many slices forms a group alone, spread over several CTAs;
-// consecutive small gels are packed into a group of one CTA.  The CTAs of a group synchronise
-// through a barrier counter of their own, so a group never waits for another one.
+// Partition of the slices of the gels being solved over the CTAs of the persistent PCG kernels
+// (rebuilt when that set of gels changes).  The gels are split into independent groups: a gel
+// with many slices forms a group alone, spread over several CTAs; runs of small gels are packed
+// into a group of one CTA.  The CTAs of a group synchronise through a barrier counter of their
+// own, so a group never waits for another one.
 struct PcgPlan {
-  const int* cta_s0;     // per CTA: first slice (nctas + 1 entries)
+  const int2* cta_rng;   // per CTA: its slices [x, y)
   const int* cta_grp;    // per CTA: its group
   const int4* grp;       // per group: (first CTA, CTA count, first gel, gel count)
   const int* slice_gel;  // per slice: its gel

@@ -95,6 +95,7 @@ constexpr int PCG_SLICES_MIXED = 4;
 constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
 constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
+constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
 constexpr int PIECE_HOST = 512;
 
 #define CK(call)                                                          \
@@ -420,6 +421,13 @@ struct tx_batch {
   int nctas = 0;
   bool pcg_res = false;  // resident kernels: one slice per warp, matrix in shared memory
   int pcg_wmax = 0;      // widest slice (blocks per row)
+  int pcg_spc_min = 4;   // slices per CTA at least
+  int pcg_cta_cap = 0;   // capacity of the device plan arrays (CTAs)
+  int nsm = 0;
+  std::vector<int> plan_key;  // active gels of the plan on the device
+  std::vector<int2> plan_rng_h;
+  std::vector<int> plan_grp_of_h;
+  std::vector<int4> plan_grp_h;
   // energy pieces
   int4* pieces = nullptr;
   int npieces = 0;
@@ -788,59 +796,11 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   int spc_min = 0;  // slices (32 rows) per CTA at least
   for (int g = 0; g < n; ++g) spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
   if (spc_min <= 0) spc_min = b->mixed ? PCG_SLICES_MIXED : PCG_SLICES_FP64;
-  std::vector<int> cta_s0, cta_grp;
-  std::vector<int4> grp;
-  int spc = std::max(spc_min, 1), max_slices = 1;
-  for (int attempt = 0;; ++attempt) {
-    cta_s0.clear();
-    cta_grp.clear();
-    grp.clear();
-    int g = 0;
-    while (g < n) {
-      const GelInfo& G = b->gi[g];
-      if (G.ns > spc || g + 1 == n) {  // a group of its own, over ceil(ns / spc) CTAs
-        const int nc = std::max(1, (G.ns + spc - 1) / spc);
-        grp.push_back(make_int4((int)cta_s0.size(), nc, g, 1));
-        for (int q = 0; q < nc; ++q) {
-          cta_s0.push_back(G.s0 + (int)((long long)q * G.ns / nc));
-          cta_grp.push_back((int)grp.size() - 1);
-        }
-        ++g;
-        continue;
-      }
-      int acc = 0, k = g;  // pack consecutive small gels into one CTA
-      while (k < n && k - g < PCG_MAXG_HOST && b->gi[k].ns <= spc && (k == g || acc + b->gi[k].ns <= spc)) {
-        acc += b->gi[k].ns;
-        ++k;
-      }
-      grp.push_back(make_int4((int)cta_s0.size(), 1, g, k - g));
-      cta_s0.push_back(G.s0);
-      cta_grp.push_back((int)grp.size() - 1);
-      g = k;
-    }
-    const int nctas = (int)cta_grp.size();
-    cta_s0.push_back(nslices);
-    max_slices = 1;
-    for (int c = 0; c < nctas; ++c) max_slices = std::max(max_slices, cta_s0[c + 1] - cta_s0[c]);
-    const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
-    if (nctas <= nsm * occ) break;
-    if (attempt > 200) {
-      g_err = "PCG partition does not fit the device";
-      delete b;
-      return TX_ERR_ARG;
-    }
-    spc = spc + spc / 4 + 1;
-  }
-  const int nctas = (int)cta_grp.size();
-  const int ngroups = (int)grp.size();
-  b->nctas = nctas;
+  b->pcg_spc_min = spc_min;
+  b->nsm = nsm;
   for (int q = 0; q < nslices; ++q) b->pcg_wmax = std::max(b->pcg_wmax, (slice_off[q + 1] - slice_off[q]) / SLICE);
-  {
-    const int occ = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
-    int max_nc = 0;
-    for (const int4& q : grp) max_nc = std::max(max_nc, q.y);
-    b->pcg_res = occ > 0 && nctas <= nsm * occ && max_nc <= PCG_RES_MAXNC;
-  }
+  const int cta_cap = PCG_CTAS_PER_SM_CAP * nsm;  // largest co-resident grid of any plan
+  b->pcg_cta_cap = cta_cap;
   // ---- energy pieces
   for (int g = 0; g < n; ++g) {
     const GelInfo& G = b->gi[g];
@@ -900,8 +860,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.w = M.get<double4_32a>(rows);
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
-  d.part = M.get<double>(8 * (size_t)nctas);
-  d.bar = M.get<unsigned>(ngroups);
+  d.part = M.get<double>(8 * (size_t)cta_cap);
+  d.bar = M.get<unsigned>(n);
   d.sv = M.get<int>(nsv);
   d.st = M.get<int4>(nst);
   d.se = M.get<int2>(nse);
@@ -930,20 +890,21 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
-  int* cta_buf = M.get<int>(2 * (size_t)nctas + 1 + nslices);
-  int4* grp_buf = M.get<int4>(ngroups);
-  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !cta_buf || !grp_buf ||
+  int2* rng_buf = M.get<int2>(cta_cap);
+  int* cta_buf = M.get<int>((size_t)cta_cap + nslices);
+  int4* grp_buf = M.get<int4>(n);
+  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !rng_buf || !cta_buf || !grp_buf ||
       (b->mixed ? !d.vals32 : !d.vals)) {
     M.release();
     delete b;
     return TX_ERR_OOM;
   }
-  b->plan.cta_s0 = cta_buf;
-  b->plan.cta_grp = cta_buf + nctas + 1;
-  b->plan.slice_gel = cta_buf + 2 * nctas + 1;
+  b->plan.cta_rng = rng_buf;
+  b->plan.cta_grp = cta_buf;
+  b->plan.slice_gel = cta_buf + cta_cap;
   b->plan.grp = grp_buf;
-  b->plan.max_slices = max_slices;
-  b->plan.ngroups = ngroups;
+  b->plan.max_slices = 1;
+  b->plan.ngroups = 0;
   if (b->mixed) {  // FP32 PCG vectors live in the upper half of dedicated buffers
     d.u32 = (float4*)M.get<float4>(rows);
     d.w32 = (float4*)M.get<float4>(rows);
@@ -1001,10 +962,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U(d.ie_gel, ie_gel.data(), sizeof(int) * nie);
   U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
   U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
-  U((void*)b->plan.cta_s0, cta_s0.data(), sizeof(int) * (nctas + 1));
-  U((void*)b->plan.cta_grp, cta_grp.data(), sizeof(int) * nctas);
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
-  U((void*)b->plan.grp, grp.data(), sizeof(int4) * ngroups);
   if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
@@ -1298,6 +1256,81 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
   return upload_ctl(b);
 }
 
+// PCG partition for the gels of `set` (in index order), rebuilt only when the set changes.
+// Groups: a gel with more than spc slices is spread over ceil(ns / spc) CTAs; runs of small gels
+// (index span <= 64, slice span <= spc) share one CTA.  spc grows from its minimum until the CTAs
+// fit co-resident on the device; the resident kernels are used when every CTA has at most a
+// slice per warp and they fit, else the streaming kernels.
+tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
+  if (set == b->plan_key && b->nctas > 0) return TX_OK;
+  int total = 0;
+  for (int g : set) total += b->gi[g].ns;
+  const int nsm = b->nsm;
+  int spc = std::max(b->pcg_spc_min, 1), max_slices = 1;
+  std::vector<int2>& rng = b->plan_rng_h;
+  std::vector<int>& cgrp = b->plan_grp_of_h;
+  std::vector<int4>& grp = b->plan_grp_h;
+  bool res = false;
+  for (int attempt = 0;; ++attempt) {
+    rng.clear();
+    cgrp.clear();
+    grp.clear();
+    size_t k = 0;
+    while (k < set.size()) {
+      const int g = set[k];
+      const GelInfo& G = b->gi[g];
+      if (G.ns > spc) {
+        const int nc = (G.ns + spc - 1) / spc;
+        grp.push_back(make_int4((int)rng.size(), nc, g, 1));
+        for (int q = 0; q < nc; ++q) {
+          rng.push_back(make_int2(G.s0 + (int)((long long)q * G.ns / nc), G.s0 + (int)((long long)(q + 1) * G.ns / nc)));
+          cgrp.push_back((int)grp.size() - 1);
+        }
+        ++k;
+        continue;
+      }
+      size_t e = k + 1;  // pack the following small gels while the spans allow
+      while (e < set.size()) {
+        const GelInfo& H = b->gi[set[e]];
+        if (H.ns > spc || set[e] - g >= PCG_MAXG_HOST || H.s0 + H.ns - G.s0 > spc) break;
+        ++e;
+      }
+      const GelInfo& L = b->gi[set[e - 1]];
+      grp.push_back(make_int4((int)rng.size(), 1, g, set[e - 1] - g + 1));
+      rng.push_back(make_int2(G.s0, L.s0 + L.ns));
+      cgrp.push_back((int)grp.size() - 1);
+      k = e;
+    }
+    const int nctas = (int)rng.size();
+    max_slices = 1;
+    int max_nc = 0;
+    for (const int2& r : rng) max_slices = std::max(max_slices, r.y - r.x);
+    for (const int4& q : grp) max_nc = std::max(max_nc, q.y);
+    const int occ_res = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
+    res = occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC;
+    const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
+    if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
+    if (attempt > 400) {
+      set_last_error("PCG partition does not fit the device");
+      return TX_ERR_ARG;
+    }
+    spc = spc + spc / 4 + 1;
+  }
+  const int nctas = (int)rng.size();
+  cudaStream_t st = b->st;
+  // the staging vectors stay untouched until the copies ran: the host waits on the stream every
+  // Newton round before it can rebuild a plan
+  CK(cudaMemcpyAsync((void*)b->plan.cta_rng, rng.data(), sizeof(int2) * nctas, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync((void*)b->plan.cta_grp, cgrp.data(), sizeof(int) * nctas, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync((void*)b->plan.grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
+  b->plan.max_slices = max_slices;
+  b->plan.ngroups = (int)grp.size();
+  b->nctas = nctas;
+  b->pcg_res = res;
+  b->plan_key = set;
+  return TX_OK;
+}
+
 tx_status do_newton(tx_batch* b) {
   std::vector<int> set;
   for (int g = 0; g < b->n; ++g) {
@@ -1328,6 +1361,8 @@ tx_status do_newton(tx_batch* b) {
   prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
+  s = prepare_pcg_plan(b, set);
+  if (s != TX_OK) return s;
   CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
   prof_open(b, PR_PCG);
   if (b->mixed) {
