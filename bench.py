@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
+    ap.add_argument("--batched-gels", type=int, default=64,
+                    help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
     ap.add_argument("--pcg-cta-slices", type=int, default=0,
                     help="PCG work split: 32-row slices per CTA at least (0: library default)")
     return ap.parse_args()
@@ -133,7 +135,7 @@ def fp64_peak_tflops(sm_mhz):
     return 4.0 * 152 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
-def run_gpu(args, rank, world):
+def run_gpu(args, rank, world, e2e=True):
     import torch
     from paper_2411_04776_gb300 import _build
     from paper_2411_04776_gb300 import binding as B
@@ -194,6 +196,13 @@ def run_gpu(args, rank, world):
     clocks = clk.summary()
     # ---- end to end through the public API with host buffers: poses in, positions out
     n = sum(len(w.gel.verts) for w in wls)
+    if not e2e:
+        if single:
+            gel.close()
+        else:
+            B.tx_batch_destroy(handle)
+        return dict(total_s=total_s, step_ms=step_ms, stats=stats, prof=prof, clocks=clocks, e2e_s=None,
+                    n=n, wls=wls, h2d=0, d2h=0)
     if single:
         gel.reset()
         for s in range(Wm):
@@ -225,27 +234,53 @@ def run_gpu(args, rank, world):
                 n=n, wls=wls, h2d=len(wls) * (7 * 8 + 8), d2h=2 * n * 3 * 8 + len(wls) * (3 * 8 + 96))
 
 
-def roofline(prof, clocks):
-    phases = prof["phases"]
-    kernel_phases = ["tet_assemble", "gather", "contact_assemble", "precond", "pcg"]
-    top = max(kernel_phases, key=lambda k: phases[k]["ms"])
-    ph = phases[top]
-    avg_ms = ph["ms"] / max(ph["launches"], 1)
-    peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
-    achieved = (ph["flops"] / max(ph["launches"], 1)) / (avg_ms * 1e-3) / 1e12 if ph["flops"] else None
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(prof, clocks, precision, kernel):
+    """Roofline of the dominant kernel (the persistent PCG, one launch per Newton round).  FP64:
+    bound by the FP64 pipe (GB300 runs FP64 at 1/64 of FP32; no tensor cores on this path), peak
+    derived from the unit count and the SM clock.  Mixed precision: the inner solve streams FP32
+    blocks, bound by HBM, peak = the measured copy bandwidth."""
+    ph = prof["phases"]["pcg"]
+    launches = max(ph["launches"], 1)
+    avg_ms = ph["ms"] / launches
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
-            t = json.load(open(tpath)).get(top)
+            t = json.load(open(tpath)).get(kernel)
             if t and t.get("source_hash") == source_hash():
                 traffic = t["bytes_per_launch"]
         except (ValueError, KeyError):
             traffic = None
-    return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    if precision == "fp64":
+        peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
+        achieved = (ph["flops"] / launches) / (avg_ms * 1e-3) / 1e12 if ph["flops"] else None
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "avg_launch_ms": avg_ms, "launches": ph["launches"],
+                "peak_note": "derived: FP64 (non-tensor) 4 FLOP/clk/SM x 152 SMs x max SM clock; "
+                             "achieved = algorithmic FLOP (18 per 3x3 block, 60 per row per iteration)"}
+    pk = measured_peaks()
+    peak = float(pk.get("hbm_gbs") or 6800.0)
+    achieved = (ph["bytes"] / launches) / (avg_ms * 1e-3) / 1e9 if ph["bytes"] else None
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "avg_launch_ms": avg_ms, "launches": ph["launches"],
-            "peak_note": "FP64 non-tensor: 4 FLOP/clk/SM x 152 SMs x max SM clock (nominal 1.25 TF derivation)"}
+            "peak_note": ("measured copy bandwidth (MEASURED_PEAKS.json)" if pk.get("hbm_gbs") else "fallback 6.8 TB/s")
+                         + "; achieved = algorithmic bytes of streaming iterations (40 B per block, 212 B per row)"}
+
+
+def pcg_kernel_name(precision, n_gels):
+    if n_gels == 1:
+        return "k_pcg64_res" if precision == "fp64" else "k_pcg_mixed_res"
+    return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
 
 
 def source_hash():
@@ -363,16 +398,73 @@ def main():
                        "max": float(step_ms.max())},
         "newton_iters_per_step": prof["newton_iters"] / (ng * K),
         "pcg_iters_per_step": prof["pcg_iters"] / (ng * K),
-        "roofline": roofline(r["prof"], r["clocks"]),
+        "roofline": roofline(r["prof"], r["clocks"], args.precision, pcg_kernel_name(args.precision, ng)),
         "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
         "gpu_launches": r["prof"]["kernel_launches"],
         "clocks": r["clocks"],
         "e2e": {"value": world * ng * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
     }
+    if world == 1 and args.workload == "mini" and args.batched_gels > 0:
+        line["batched_mixed"] = batched_mixed(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))
+
+
+def plain_fp64_sequential(wls, steps, warmup):
+    """The plain FP64 path on the same gels and the same step window, one gel at a time: each gel
+    takes its warm-up steps untimed, then its timed steps (CUDA events, L2 flushed before each)."""
+    import torch
+    from paper_2411_04776_gb300 import binding as B
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    for w in wls:
+        gel = B.Gel(B.GelDesc.from_workload(w, precision=B.TX_PREC_FP64), stream=stream)
+        for s in range(warmup):
+            assert gel.step(w.poses[s], w.dt) == 0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            assert gel.step(w.poses[warmup + i], w.dt) == 0
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        gel.close()
+    ms = np.array(ms)
+    return {"gels": len(wls), "value": len(ms) / (ms.sum() / 1e3), "unit": "steps/s",
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}
+
+
+def batched_mixed(args):
+    """Companion measurement of the same metric on the batched mixed-precision configuration:
+    args.batched_gels GelSight-Mini gels (41x51x9, each with its own seeded indenter and press/slide
+    trajectory) stepped together, FP32 elastic blocks and FP32 inner PCG with FP64 residual
+    refinement; compared with the plain FP64 path stepping the first 16 of the same gels one at a
+    time over the same steps (vs_plain_fp64 = ratio of the two steps/s)."""
+    import argparse
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.n_gels, a.precision = "batch_mini", args.batched_gels, "mixed"
+    a.steps, a.warmup = 4, 3
+    r = run_gpu(a, 0, 1, e2e=False)
+    ng = len(r["wls"])
+    value = ng * a.steps / r["total_s"]
+    prof = r["prof"]
+    plain = plain_fp64_sequential(r["wls"][:min(ng, 16)], a.steps, a.warmup)
+    return {"workload": workload_config(r["wls"], a.workload, "mixed")["workload"], "gels": ng,
+            "precision": "mixed", "value": value, "unit": "steps/s", "steps": a.steps, "warmup": a.warmup,
+            "ms_per_batch_step": r["total_s"] * 1e3 / a.steps,
+            "latency_ms": {"p50": float(np.percentile(r["step_ms"], 50)),
+                           "p99": float(np.percentile(r["step_ms"], 99))},
+            "newton_iters_per_step": prof["newton_iters"] / (ng * a.steps),
+            "pcg_iters_per_step": prof["pcg_iters"] / (ng * a.steps),
+            "plain_fp64_same_steps": plain,
+            "vs_plain_fp64": value / plain["value"],
+            "roofline": roofline(prof, r["clocks"], "mixed", pcg_kernel_name("mixed", ng)),
+            "phases_ms": {k: round(v["ms"], 3) for k, v in prof["phases"].items()},
+            "gpu_launches": prof["kernel_launches"], "clocks": r["clocks"]}
 
 
 if __name__ == "__main__":

@@ -1420,12 +1420,15 @@ tx_status do_newton(tx_batch* b) {
       // axpys 24, three dot products 18; mixed precision adds one FP64 residual SpMV per round
       const double rounds = b->mixed ? b->gv_h[g].rounds : 0.0;
       b->prof.flops[PR_PCG] += it * (18.0 * b->nnzb_real[g] + 60.0 * b->nfree[g]) + rounds * 18.0 * b->nnzb_real[g];
-      // bytes: block values + column index + gathered vector per block, and 13 row vectors
-      // (FP64: 72 B values, 32 B vectors; mixed: 36 B values, 16 B vectors)
+      // algorithmic bytes of a streaming iteration: block values + column index per block, and
+      // per row the preconditioner block, six vectors read and five written (FP64: 72 + 4 B per
+      // block, 72 + 11 x 32 B per row; mixed: 36 + 4 B per block, 36 + 11 x 16 B per row); a
+      // refinement round adds the FP64 residual SpMV (FP32 blocks, three FP64 row vectors)
       if (b->mixed)
-        b->prof.bytes[PR_PCG] += it * (40.0 * b->nnzb_real[g] + 16.0 * b->nnzb_real[g] + 244.0 * G.nv);
+        b->prof.bytes[PR_PCG] += it * (40.0 * b->nnzb_real[g] + 212.0 * G.nv) +
+                                 rounds * (40.0 * b->nnzb_real[g] + 96.0 * G.nv);
       else
-        b->prof.bytes[PR_PCG] += it * (76.0 * b->nnzb_real[g] + 32.0 * b->nnzb_real[g] + 488.0 * G.nv);
+        b->prof.bytes[PR_PCG] += it * (76.0 * b->nnzb_real[g] + 424.0 * G.nv);
       b->prof.pcg_iters += b->gv_h[g].pcg_it;
       b->prof.newton_iters += 1;
       b->prof.flops[PR_TET] += 0.0;
