@@ -61,6 +61,67 @@ __device__ __forceinline__ void jacobi3(R a[3][3], R w[3], R V[3][3]) {
   w[2] = a[2][2];
 }
 
+// Symmetric 3x3 eigen-decomposition to FP64 accuracy at a fraction of an FP64 Jacobi's cost
+// (GB300 issues FP64 at 1/64 of the FP32 rate): the basis from FP32 cyclic Jacobi, one
+// Newton-Schulz step X <- X (3 I - X^T X) / 2 to make it orthonormal in FP64, then FP64 Jacobi
+// sweeps on the nearly diagonal B = X^T C X with the rotation angle taken from the FP32 quotient
+// (the rotation itself, c = 1 / sqrt(1 + t^2), s = t c, and all updates in FP64); entries below
+// 1e-15 max|C| are left alone, a sweep without rotations ends the refinement.
+__device__ __forceinline__ void eig3_refined(const double C[3][3], double w[3], double V[3][3]) {
+  float Cf[3][3], wf[3], Vf[3][3];
+  double mx = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Cf[i][j] = (float)C[i][j];
+      mx = fmax(mx, fabs(C[i][j]));
+    }
+  jacobi3<float>(Cf, wf, Vf);
+  double X[3][3], S[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) X[i][j] = (double)Vf[i][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = fma(X[0][i], X[0][j], fma(X[1][i], X[1][j], X[2][i] * X[2][j]));
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = 1.5 * X[i][j] - 0.5 * fma(X[i][0], S[0][j], fma(X[i][1], S[1][j], X[i][2] * S[2][j]));
+  double T[3][3], B[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) T[i][j] = fma(C[i][0], V[0][j], fma(C[i][1], V[1][j], C[i][2] * V[2][j]));
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) B[i][j] = B[j][i] = fma(V[0][i], T[0][j], fma(V[1][i], T[1][j], V[2][i] * T[2][j]));
+  const double tau = 1e-15 * mx;
+  for (int sweep = 0; sweep < 4; ++sweep) {
+    bool rot = false;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const int r = 3 - p - q;
+      const double bpq = B[p][q];
+      if (!(fabs(bpq) > tau)) continue;
+      rot = true;
+      const float th = (float)(B[q][q] - B[p][p]) / (2.f * (float)bpq);
+      const double t = (double)((th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f))));
+      const double c = rsqrt(fma(t, t, 1.0)), sn = t * c;
+      const double bpp = B[p][p], bqq = B[q][q];
+      B[p][p] = c * c * bpp - 2.0 * c * sn * bpq + sn * sn * bqq;
+      B[q][q] = sn * sn * bpp + 2.0 * c * sn * bpq + c * c * bqq;
+      B[p][q] = B[q][p] = c * sn * (bpp - bqq) + (c * c - sn * sn) * bpq;
+      const double brp = B[r][p], brq = B[r][q];
+      B[r][p] = B[p][r] = c * brp - sn * brq;
+      B[r][q] = B[q][r] = sn * brp + c * brq;
+      for (int k = 0; k < 3; ++k) {
+        const double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - sn * vkq;
+        V[k][q] = sn * vkp + c * vkq;
+      }
+    }
+    if (!rot) break;
+  }
+  w[0] = B[0][0];
+  w[1] = B[1][1];
+  w[2] = B[2][2];
+}
+
 template <typename R>
 __device__ __forceinline__ R det3(const R F[3][3]) {
   return F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
@@ -135,7 +196,10 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
   R C[3][3], s2[3], V[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) C[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
-  jacobi3<R>(C, s2, V);
+  if constexpr (sizeof(R) == 8)
+    eig3_refined(C, s2, V);
+  else
+    jacobi3<R>(C, s2, V);
   int o0 = 0, o1 = 1, o2 = 2;  // descending order of s2
   if (s2[o0] < s2[o1]) { int t = o0; o0 = o1; o1 = t; }
   if (s2[o1] < s2[o2]) { int t = o1; o1 = o2; o2 = t; }
@@ -175,12 +239,19 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
     for (int j = 0; j < 3; ++j)
       A[i][j] = (i == j) ? mu + (m + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
   R Ap[3][3];
-  if (project) {
+  // A = diag(mu + m / s_i^2) + lambda s s^T with s_i = 1 / sigma_i: PSD as it stands when the
+  // diagonal part is (lambda >= 0), which holds unless the volume grows by ~25 % or more
+  const bool psd = (mu + m / (sg[0] * sg[0]) >= R(0)) && (mu + m / (sg[1] * sg[1]) >= R(0)) &&
+                   (mu + m / (sg[2] * sg[2]) >= R(0)) && lam >= R(0);
+  if (project && !psd) {
     R w[3], Q[3][3];
     R Ac[3][3];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) Ac[i][j] = A[i][j];
-    jacobi3<R>(Ac, w, Q);
+    if constexpr (sizeof(R) == 8)
+      eig3_refined(Ac, w, Q);
+    else
+      jacobi3<R>(Ac, w, Q);
     for (int i = 0; i < 3; ++i) w[i] = fmax(w[i], R(0));
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) Ap[i][j] = Q[i][0] * w[0] * Q[j][0] + Q[i][1] * w[1] * Q[j][1] + Q[i][2] * w[2] * Q[j][2];
