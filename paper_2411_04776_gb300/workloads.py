@@ -88,9 +88,11 @@ def gel_grid(nx: int, ny: int, nz: int, size) -> GelMesh:
 @functools.lru_cache(maxsize=16)
 def _gel_grid_arrays(nx, ny, nz, size):
     lx, ly, lz = size
-    xs = np.linspace(0.0, lx, nx)
-    ys = np.linspace(0.0, ly, ny)
-    zs = np.linspace(0.0, lz, nz)
+    return _tensor_grid_arrays(np.linspace(0.0, lx, nx), np.linspace(0.0, ly, ny), np.linspace(0.0, lz, nz))
+
+
+def _tensor_grid_arrays(xs, ys, zs):
+    nx, ny, nz = len(xs), len(ys), len(zs)
     zz, yy, xx = np.meshgrid(zs, ys, xs, indexing="ij")
     verts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(np.float64)
     # cube origins (i, j, k), ordered k-major then j then i (x fastest)
@@ -118,9 +120,55 @@ def _gel_grid_arrays(nx, ny, nz, size):
     return verts, tets, dirichlet
 
 
+def graded_axis(length: float, h0: float, ratio: float, centred: bool) -> np.ndarray:
+    """Node coordinates on [0, length] with cell size h0 at the centre (centred) or at the top end
+    (length), growing geometrically by `ratio` away from it; the outermost cell absorbs the rest."""
+    half = 0.5 * length if centred else length
+    cuts, x, h = [0.0], 0.0, h0
+    while x + h < half - 0.5 * h:
+        x += h
+        cuts.append(x)
+        h *= ratio
+    cuts.append(half)
+    c = np.asarray(cuts)
+    if centred:
+        return np.concatenate([half - c[::-1], half + c[1:]])
+    return length - c[::-1]
+
+
+def gel_tensor_grid(xs, ys, zs) -> GelMesh:
+    """Box gel on the tensor-product grid xs x ys x zs (Kuhn tets, bottom face fixed)."""
+    verts, tets, dirichlet = _tensor_grid_arrays(np.asarray(xs, float), np.asarray(ys, float), np.asarray(zs, float))
+    return GelMesh(verts, tets, dirichlet)
+
+
 # ----------------------------------------------------------------------------------------------
 # indenters
 # ----------------------------------------------------------------------------------------------
+def spherical_cap(radius: float, cap_radius: float, n_rings: int, n_sectors: int, grading: float = 1.0) -> Indenter:
+    """Lower cap of a sphere of `radius`, apex at the frame origin (centre at z = radius), out to
+    the ring of horizontal radius cap_radius: an apex fan and n_rings rings of n_sectors vertices
+    (ring spacing graded by `grading`, finest at the apex) -- an open triangle mesh."""
+    th_max = math.asin(min(cap_radius / radius, 1.0))
+    w = np.cumsum(grading ** np.arange(n_rings))
+    th = th_max * w / w[-1]
+    verts = [np.zeros(3)]
+    for t in th:
+        for k in range(n_sectors):
+            ph = 2.0 * math.pi * (k + 0.5 * (len(verts) % 2)) / n_sectors
+            verts.append(np.array([radius * math.sin(t) * math.cos(ph), radius * math.sin(t) * math.sin(ph),
+                                   radius * (1.0 - math.cos(t))]))
+    tris = []
+    for k in range(n_sectors):
+        tris.append((0, 1 + k, 1 + (k + 1) % n_sectors))
+    for r in range(n_rings - 1):
+        a0, b0 = 1 + r * n_sectors, 1 + (r + 1) * n_sectors
+        for k in range(n_sectors):
+            k1 = (k + 1) % n_sectors
+            tris.append((a0 + k, b0 + k, b0 + k1))
+            tris.append((a0 + k, b0 + k1, a0 + k1))
+    return Indenter(np.array(verts), np.array(tris, dtype=np.int32), "cap")
+
 def icosphere(radius: float, level: int) -> Indenter:
     """Icosahedron subdivided `level` times, vertices on the sphere (level 2: 162 verts, 320 tris)."""
     t = (1.0 + math.sqrt(5.0)) / 2.0
@@ -281,6 +329,24 @@ def mini_gel(seed: int = 0, grid=GRID_MINI, depth: float = 1.0e-3, n_press: int 
     p0, poses = press_slide_poses(ind, gel, c, depth, n_press, slide, n_slide)
     name = f"gel{nx}x{ny}x{nz}_{kind}{len(ind.tris)}_press{depth*1e3:.1f}mm_slide{slide*1e3:.1f}mm"
     return Workload(name, gel, ind, p0, poses, DT)
+
+
+def hertz_block(h0: float = 0.06e-3, ratio: float = 1.3, half: float = 3.0e-3, thick: float = 2.0e-3,
+                radius: float = 3.0e-3, depth: float = 40e-6, dhat: float = 5e-6, step: float = 4e-6,
+                n_rings: int = 24, n_sectors: int = 48) -> Workload:
+    """Hertz indentation: a 2*half x 2*half x thick block (bottom fixed, the gel material) meshed
+    with cells of size h0 at the top centre growing by `ratio` outward and downward, pressed by
+    a rigid spherical cap of `radius` to `depth` below the top face in quasi-static steps of
+    `step` (time step 1 s, so inertia is negligible), barrier distance dhat."""
+    xs = graded_axis(2 * half, h0, ratio, True)
+    zs = graded_axis(thick, h0, ratio, False)
+    gel = gel_tensor_grid(xs, xs, zs)
+    a = math.sqrt(radius * depth)
+    ind = spherical_cap(radius, min(3.0 * a, 0.9 * radius), n_rings, n_sectors, grading=1.08)
+    n = int(math.ceil((depth + dhat) / step))
+    p0, poses = press_slide_poses(ind, gel, (half, half), depth, n, dhat=dhat)
+    return Workload(f"hertz_R{radius*1e3:.1f}mm_d{depth*1e6:.0f}um_h{h0*1e6:.0f}um", gel, ind, p0, poses, 1.0,
+                    dhat=dhat)
 
 
 def mixed_batch(n_gels: int = 256, seed0: int = 0, n_press: int = 60, n_slide: int = 60):

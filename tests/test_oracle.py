@@ -485,3 +485,39 @@ def test_newton_matches_direct_minimisation():
     r = minimize(f, z0, jac=True, method="L-BFGS-B",
                  options=dict(maxiter=5000, ftol=1e-30, gtol=1e-16, maxcor=50))
     assert np.abs(r.x).max() * S < 1e-10
+
+
+# ------------------------------------------------------------------ contact mechanics
+
+
+def hertz_force(uc, radius):
+    """Hertz's solution for a rigid frictionless sphere of `radius` pressed to a depth uc into an
+    elastic half-space (Johnson, Contact Mechanics, 1985, Sec. 4.2): F = 4/3 E* sqrt(R) uc^(3/2),
+    E* = E / (1 - nu^2)."""
+    return 4.0 / 3.0 * E_ / (1.0 - NU_ ** 2) * math.sqrt(radius) * uc ** 1.5
+
+
+def test_hertz_sphere_indentation_coarse():
+    """Rigid spherical cap (R = 3 mm) pressed quasi-statically (time step 1 s) into a 16 x 16 x 8 mm
+    block (a >> the 80 um cells under the contact, a << the block): the contact force follows
+    Hertz's u^(3/2) law.  A displacement-based mesh this coarse is stiffer than the continuum
+    (a lower bound on compliance), so the force may exceed Hertz but not fall below it; the
+    refinement study that brings it within 15 % runs on the GPU library (test_gpu_hertz)."""
+    half = 8e-3
+    wl = W.hertz_block(h0=80e-6, ratio=1.5, half=half, thick=half, dhat=15e-6, step=12e-6)
+    X = wl.gel.verts
+    c = np.where((np.abs(X[:, 0] - half) < 1e-9) & (np.abs(X[:, 1] - half) < 1e-9) & (X[:, 2] > half - 1e-9))[0]
+    assert len(c) == 1
+    og = O.OracleGel.from_workload(wl)
+    u, F = [], []
+    for s in range(len(wl.poses)):
+        assert og.step(wl.poses[s], wl.dt)["status"] == 0
+        x, _, fc, _ = og.state()
+        u.append(X[c[0], 2] - x[c[0], 2])  # surface displacement under the apex
+        F.append(-fc[2])
+    u, F = np.array(u), np.array(F)
+    ratio = F / hertz_force(u, 3e-3)
+    assert np.all(ratio[-2:] > 0.95) and np.all(ratio[-2:] < 1.45), ratio
+    # the u^(3/2) law between the last two loads
+    expo = math.log(F[-1] / F[-2]) / math.log(u[-1] / u[-2])
+    assert 1.35 < expo < 1.65, expo
