@@ -78,6 +78,17 @@ def test_small_gel_trajectory_matches_oracle():
     assert np.abs(fg - fo).max() <= 1e-4 * np.abs(fo).max()
 
 
+def test_gelsight_mini_steps_match_oracle():
+    """First contact steps of the GelSight-Mini gel (41x51x9: 18,819 vertices, 96,000 tets) pressed
+    by the seeded prism indenter, in the launch configuration the bench times (one gel, FP64):
+    the prism starts d_hat above the gel and travels 33 um per step, contact from step 4 on."""
+    wl = W.mini_gel(seed=3, kind="prism", depth=0.3e-3, n_press=12, slide=0.0, n_slide=0)
+    gel, ref, errs, fg, fo = run_pair(wl, 6)
+    assert gel.state()[3].active_pairs > 0
+    assert errs.max() <= POS_TOL, errs
+    assert np.abs(fg - fo).max() <= 1e-4 * max(np.abs(fo).max(), 1e-12)
+
+
 def test_mixed_precision_trajectory_matches_oracle():
     """FP32 Hessian blocks + FP32 Krylov solve with FP64 residual refinement; the gradient,
     barrier, CCD and energy stay FP64, so the converged minimiser is the FP64 one."""
