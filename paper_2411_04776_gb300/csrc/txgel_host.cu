@@ -23,6 +23,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -391,6 +392,7 @@ struct Prof {
   struct Pending {
     cudaEvent_t a, b;
     int phase;
+    bool graph;  // events owned by a captured Newton-iteration graph (not returned to the pool)
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
@@ -425,6 +427,24 @@ struct tx_batch {
   int pcg_cta_cap = 0;   // capacity of the device plan arrays (CTAs)
   int nsm = 0;
   std::vector<int> plan_key;  // active gels of the plan on the device
+  // captured Newton iteration (launch part), replayed while its inputs stay the same
+  struct NewtonGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> key;
+    Dev dev{};
+    PcgPlan plan{};
+    int nctas = 0;
+    bool res = false, prof = false;
+    double eta = 0.0;
+    int pcg_max = 0, refine = 0, accd_max = 0;
+    long long launches = 0;
+    long long phase_launches[PR_N] = {};
+    std::vector<Prof::Pending> prof_pairs;
+  } graph;
+  int graphs = -1;  // -1 undecided, 0 off (unsupported or disabled), 1 on
+  bool capturing = false;  // profile events become event-record nodes of the graph
+  cudaStream_t gst = nullptr;          // stream the graph is captured on and replayed on
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order it after / before the caller's stream
   std::vector<int2> plan_rng_h;
   std::vector<int> plan_grp_of_h;
   std::vector<int4> plan_grp_h;
@@ -458,17 +478,26 @@ cudaEvent_t prof_event(tx_batch* b) {
   cudaEventCreate(&e);
   return e;
 }
+// inside a stream capture a plain record would only order the graph's nodes; the external
+// flag makes it a record node that fires on every replay, so the phase times stay measurable
+void prof_record(tx_batch* b, cudaEvent_t e) {
+  if (b->capturing)
+    cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, b->st);
+}
+
 void prof_open(tx_batch* b, int phase) {
   if (!b->prof.on) return;
   b->prof.open_phase = phase;
   b->prof.open_ev = prof_event(b);
-  cudaEventRecord(b->prof.open_ev, b->st);
+  prof_record(b, b->prof.open_ev);
 }
 void prof_close(tx_batch* b, int nlaunch) {
   if (!b->prof.on || b->prof.open_phase < 0) return;
   cudaEvent_t e = prof_event(b);
-  cudaEventRecord(e, b->st);
-  b->prof.pending.push_back({b->prof.open_ev, e, b->prof.open_phase});
+  prof_record(b, e);
+  b->prof.pending.push_back({b->prof.open_ev, e, b->prof.open_phase, false});
   b->prof.launches[b->prof.open_phase] += nlaunch;
   b->prof.open_phase = -1;
 }
@@ -476,7 +505,13 @@ void prof_close(tx_batch* b, int nlaunch) {
 void prof_resolve(tx_batch* b) {
   for (auto& p : b->prof.pending) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) b->prof.ms[p.phase] += ms;
+    const cudaError_t e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e == cudaSuccess)
+      b->prof.ms[p.phase] += ms;
+    else
+      g_err = std::string("profile event: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    if (p.graph) continue;
     b->prof.pool.push_back(p.a);
     b->prof.pool.push_back(p.b);
   }
@@ -1174,7 +1209,8 @@ namespace {
 // ---------------------------------------------------------------- one Newton iteration
 // The part after the PCG: candidates along p, ACCD, line search.  Runs for the gels whose
 // control phase is PH_NEWTON.
-tx_status post_pcg(tx_batch* b) {
+// The part after the PCG, launch side: candidates along p, ACCD, the first line-search trial.
+void post_pcg_launch(tx_batch* b, int accd_max) {
   Dev& d = b->d;
   cudaStream_t st = b->st;
   prof_open(b, PR_QUERY);
@@ -1183,12 +1219,6 @@ tx_status post_pcg(tx_batch* b) {
   launch_query(d, PH_NEWTON, 1 | 2 | 8, st);
   launch_pair_ranges(d, PH_NEWTON, 1, st);
   prof_close(b, 6);
-  int accd_max = 1, ls_max = 1;
-  for (int g = 0; g < b->n; ++g)
-    if (b->gc_h[g].phase == PH_NEWTON) {
-      accd_max = std::max(accd_max, b->mesh[g].prm.accd_max_iter);
-      ls_max = std::max(ls_max, b->mesh[g].prm.ls_max_halvings);
-    }
   prof_open(b, PR_ACCD);
   launch_accd(d, PH_NEWTON, 0, accd_max, st);
   launch_gel_op(d, PH_NEWTON, 2, st);
@@ -1199,6 +1229,15 @@ tx_status post_pcg(tx_batch* b) {
   launch_rows(1, d, PH_NEWTON, st);
   launch_gel_op(d, PH_NEWTON, 5, st);
   prof_close(b, 4);
+}
+
+// ... and the host side: read the per-gel state, run further halvings while gels search.
+tx_status post_pcg_finish(tx_batch* b) {
+  Dev& d = b->d;
+  cudaStream_t st = b->st;
+  int ls_max = 1;
+  for (int g = 0; g < b->n; ++g)
+    if (b->gc_h[g].phase == PH_NEWTON) ls_max = std::max(ls_max, b->mesh[g].prm.ls_max_halvings);
   CK(cudaGetLastError());
   tx_status s = download_var(b);
   if (s != TX_OK) return s;
@@ -1219,6 +1258,18 @@ tx_status post_pcg(tx_batch* b) {
     if (s != TX_OK) return s;
   }
   return TX_OK;
+}
+
+int newton_accd_max(tx_batch* b) {
+  int accd_max = 1;
+  for (int g = 0; g < b->n; ++g)
+    if (b->gc_h[g].phase == PH_NEWTON) accd_max = std::max(accd_max, b->mesh[g].prm.accd_max_iter);
+  return accd_max;
+}
+
+tx_status post_pcg(tx_batch* b) {
+  post_pcg_launch(b, newton_accd_max(b));
+  return post_pcg_finish(b);
 }
 
 tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
@@ -1331,6 +1382,154 @@ tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
   return TX_OK;
 }
 
+// Launches of one Newton iteration for the gels in PH_NEWTON, up to the first line-search trial.
+tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int accd_max) {
+  Dev& d = b->d;
+  cudaStream_t st = b->st;
+  launch_gel_op(d, PH_NEWTON, 0, st);
+  prof_open(b, PR_TET);
+  launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 1);
+  prof_open(b, PR_GATHER);
+  launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
+  prof_close(b, 1);
+  prof_open(b, PR_CONTACT);
+  launch_contact_assemble(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 2);
+  prof_open(b, PR_PRECOND);
+  launch_precond(d, PH_NEWTON, b->mixed, st);
+  prof_close(b, 1);
+  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
+  prof_open(b, PR_PCG);
+  if (b->mixed) {
+    if (b->pcg_res)
+      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
+    else
+      CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
+  } else {
+    if (b->pcg_res)
+      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
+    else
+      CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+  }
+  prof_close(b, 1);
+  launch_gel_op(d, PH_NEWTON, 1, st);
+  post_pcg_launch(b, accd_max);
+  return TX_OK;
+}
+
+void drop_newton_graph(tx_batch* b) {
+  auto& G = b->graph;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  for (auto& p : G.prof_pairs) {
+    b->prof.pool.push_back(p.a);
+    b->prof.pool.push_back(p.b);
+  }
+  G.prof_pairs.clear();
+  G.key.clear();
+}
+
+// The iteration's launches as a CUDA graph: captured on the first iteration of a given set of
+// gels (and whenever anything its kernels were captured with changes: the PCG partition, device
+// buffers, solver parameters, profiling), then replayed with one launch.  Falls back to plain
+// launches for good if capture is refused (TXG_NO_GRAPHS=1 also disables it).
+tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double eta, int pcg_max, int refine,
+                              int accd_max) {
+  if (b->graphs < 0) {
+    const char* e = std::getenv("TXG_NO_GRAPHS");
+    b->graphs = (e && e[0] == '1') ? 0 : 1;
+    // capture needs a stream of its own (the caller's may be the legacy default stream)
+    if (b->graphs && (cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&b->gev_in, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&b->gev_out, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      b->graphs = 0;
+    }
+  }
+  if (b->graphs == 0) return newton_launches(b, eta, pcg_max, refine, accd_max);
+  auto& G = b->graph;
+  const bool same = G.exec && G.key == set && G.res == b->pcg_res && G.nctas == b->nctas &&
+                    G.prof == b->prof.on && G.eta == eta && G.pcg_max == pcg_max && G.refine == refine &&
+                    G.accd_max == accd_max && std::memcmp(&G.dev, &b->d, sizeof(Dev)) == 0 &&
+                    std::memcmp(&G.plan, &b->plan, sizeof(PcgPlan)) == 0;
+  if (!same) {
+    drop_newton_graph(b);
+    const long long l0 = g_launch_count.load();
+    long long pl0[PR_N];
+    std::memcpy(pl0, b->prof.launches, sizeof(pl0));
+    const size_t pend0 = b->prof.pending.size();
+    cudaGraph_t graph = nullptr;
+    cudaStream_t user = b->st;
+    b->st = b->gst;  // every launch of the iteration goes to the capture stream
+    bool ok = cudaStreamBeginCapture(b->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    std::string why;
+    if (ok) {
+      b->capturing = true;
+      const tx_status s = newton_launches(b, eta, pcg_max, refine, accd_max);
+      b->capturing = false;
+      if (s != TX_OK) why = g_err;
+      const cudaError_t e = cudaStreamEndCapture(b->gst, &graph);
+      if (e != cudaSuccess && why.empty()) why = std::string("end capture: ") + cudaGetErrorString(e);
+      ok = e == cudaSuccess && s == TX_OK && graph;
+    } else {
+      why = "begin capture refused";
+    }
+    b->st = user;
+    if (ok) {
+      const cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+      if (e != cudaSuccess) why = std::string("instantiate: ") + cudaGetErrorString(e);
+      ok = e == cudaSuccess;
+    }
+    if (!ok) g_err = "Newton-iteration graph not used (" + why + "); plain launches";
+    if (graph) cudaGraphDestroy(graph);
+    // nothing ran during the capture: undo its launch and profile bookkeeping
+    const long long nl = g_launch_count.load() - l0;
+    count_launch((int)-nl);
+    long long dl[PR_N];
+    for (int k = 0; k < PR_N; ++k) {
+      dl[k] = b->prof.launches[k] - pl0[k];
+      b->prof.launches[k] = pl0[k];
+    }
+    std::vector<Prof::Pending> pairs(b->prof.pending.begin() + pend0, b->prof.pending.end());
+    b->prof.pending.resize(pend0);
+    cudaGetLastError();
+    if (!ok) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+      for (auto& p : pairs) {
+        b->prof.pool.push_back(p.a);
+        b->prof.pool.push_back(p.b);
+      }
+      b->graphs = 0;
+      return newton_launches(b, eta, pcg_max, refine, accd_max);
+    }
+    for (auto& p : pairs) p.graph = true;
+    G.prof_pairs = pairs;
+    G.key = set;
+    G.dev = b->d;
+    G.plan = b->plan;
+    G.nctas = b->nctas;
+    G.res = b->pcg_res;
+    G.prof = b->prof.on;
+    G.eta = eta;
+    G.pcg_max = pcg_max;
+    G.refine = refine;
+    G.accd_max = accd_max;
+    G.launches = nl;
+    std::memcpy(G.phase_launches, dl, sizeof(dl));
+  }
+  CK(cudaEventRecord(b->gev_in, b->st));
+  CK(cudaStreamWaitEvent(b->gst, b->gev_in, 0));
+  CK(cudaGraphLaunch(G.exec, b->gst));
+  CK(cudaEventRecord(b->gev_out, b->gst));
+  CK(cudaStreamWaitEvent(b->st, b->gev_out, 0));
+  count_launch((int)G.launches);
+  for (int k = 0; k < PR_N; ++k) b->prof.launches[k] += G.phase_launches[k];
+  for (const auto& p : G.prof_pairs) b->prof.pending.push_back(p);
+  return TX_OK;
+}
+
 tx_status do_newton(tx_batch* b) {
   std::vector<int> set;
   for (int g = 0; g < b->n; ++g) {
@@ -1348,40 +1547,14 @@ tx_status do_newton(tx_batch* b) {
     eta = std::min(eta, b->mesh[g].prm.pcg_rel_tol);
     pcg_max = std::max(pcg_max, b->mesh[g].prm.pcg_max_iter);
   }
-  launch_gel_op(d, PH_NEWTON, 0, st);
-  prof_open(b, PR_TET);
-  launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
-  prof_close(b, 1);
-  prof_open(b, PR_GATHER);
-  launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
-  prof_close(b, 1);
-  prof_open(b, PR_CONTACT);
-  launch_contact_assemble(d, PH_NEWTON, b->mixed, st);
-  prof_close(b, 1);
-  prof_open(b, PR_PRECOND);
-  launch_precond(d, PH_NEWTON, b->mixed, st);
-  prof_close(b, 1);
+  int refine = 1;
+  for (int g : set) refine = std::max(refine, b->mesh[g].prm.refine_max);
   s = prepare_pcg_plan(b, set);
   if (s != TX_OK) return s;
-  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
-  prof_open(b, PR_PCG);
-  if (b->mixed) {
-    int refine = 1;
-    for (int g : set) refine = std::max(refine, b->mesh[g].prm.refine_max);
-    if (b->pcg_res)
-      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
-    else
-      CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
-  } else {
-    if (b->pcg_res)
-      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
-    else
-      CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
-  }
-  prof_close(b, 1);
-  launch_gel_op(d, PH_NEWTON, 1, st);
-  CK(cudaGetLastError());
-  s = post_pcg(b);
+  const int accd_max = newton_accd_max(b);
+  s = run_newton_launches(b, set, eta, pcg_max, refine, accd_max);
+  if (s != TX_OK) return s;
+  s = post_pcg_finish(b);
   if (s != TX_OK) return s;
   int derr = 0;
   CK(cudaMemcpy(&derr, d.err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1574,6 +1747,13 @@ void destroy_batch(tx_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->st);
   prof_resolve(b);
+  drop_newton_graph(b);
+  if (b->gst) {
+    cudaStreamSynchronize(b->gst);
+    cudaStreamDestroy(b->gst);
+  }
+  if (b->gev_in) cudaEventDestroy(b->gev_in);
+  if (b->gev_out) cudaEventDestroy(b->gev_out);
   for (cudaEvent_t e : b->prof.pool) cudaEventDestroy(e);
   b->mem.release();
   b->pair_mem.release();
