@@ -343,6 +343,8 @@ def run_serve(args):
                            budget_gb=args.budget_gb),
             "latency_ms": lat, "requests": len(arrivals), "failed": len(done) - len(ok),
             "failed_status": sorted({B.STATUS_NAMES.get(r.status, r.status) for r in done if r.status != 0}),
+            "failed_requests": [[r.env, r.step % len(wls[r.env].poses), B.STATUS_NAMES.get(r.status, r.status)]
+                                for r in done if r.status != 0][:32],
             "max_inflight": srv.max_inflight, "max_inflight_gb": srv.max_inflight_bytes / 1e9,
             "resident_gb": float(srv.footprint.sum() / 1e9), "create_s": t_create, "clocks": clk.summary()}
     srv.close()
