@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
-    ap.add_argument("--pcg-cta-slices", type=int, default=0,
-                    help="PCG work split: 32-row slices per CTA at least (0: library default)")
+    ap.add_argument("--pcg-cta-slices", type=int, default=None,
+                    help="PCG work split: 32-row slices per CTA at least (0: library default, -1: autotune; "
+                         "default: autotune for single gels, library default for batches)")
     return ap.parse_args()
 
 
@@ -150,7 +151,8 @@ def run_gpu(args, rank, world, e2e=True):
     K, Wm = args.steps, args.warmup
     T = min(len(w.poses) for w in wls)
     assert Wm + K <= T, f"the trajectories have {T} steps"
-    descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=args.pcg_cta_slices) for w in wls]
+    spc = args.pcg_cta_slices if args.pcg_cta_slices is not None else (-1 if len(wls) == 1 else 0)
+    descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=spc) for w in wls]
     single = len(wls) == 1
     if single:
         gel = B.Gel(descs[0], stream=stream)
@@ -323,7 +325,7 @@ def run_serve(args):
     prec = B.TX_PREC_MIXED if args.precision == "mixed" else B.TX_PREC_FP64
     t0 = time.perf_counter()
     srv = S.GelServer(wls, args.budget_gb * 1e9, precision=prec, stream=torch.cuda.current_stream(),
-                      pcg_cta_slices=args.pcg_cta_slices)
+                      pcg_cta_slices=args.pcg_cta_slices or 0)
     t_create = time.perf_counter() - t0
     # warm-up: every environment takes its first steps
     srv.run_schedule([list(range(srv.n))] * max(1, args.warmup))

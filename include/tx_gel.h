@@ -70,7 +70,9 @@ typedef struct tx_params {
   int32_t precision;        /* tx_precision                                                     */
   int32_t refine_max;       /* mixed precision: max FP64 residual refinement rounds (3)         */
   int32_t pcg_cta_slices;   /* PCG work split: at least this many 32-row slices per CTA; 0 picks
-                               the default (4)                  */
+                               the default (4); -1 autotunes it per class of active gel sets
+                               (timed on live Newton rounds; the split changes the order of the
+                               PCG's sums, so tuned runs are not bitwise reproducible)          */
 } tx_params;
 
 void tx_params_default(tx_params* p);

@@ -92,6 +92,8 @@ constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
 // the SpMV); FP32 keeps groups small so that their barriers are cheap
 constexpr int PCG_SLICES_FP64 = 4;
 constexpr int PCG_SLICES_MIXED = 4;
+constexpr int TUNE_N = 5;
+constexpr int TUNE_SPC[TUNE_N] = {4, 2, 3, 6, 8};  // candidate slices per CTA (first: the default)
 // contact pairs whose barrier setup is kept for the warp Hessian kernel (others recompute it)
 constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
@@ -173,7 +175,7 @@ tx_status check_desc(const tx_gel_desc* d) {
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
-      p.pcg_cta_slices < 0)
+      p.pcg_cta_slices < -1)
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
     if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
@@ -427,6 +429,7 @@ struct tx_batch {
   int pcg_cta_cap = 0;   // capacity of the device plan arrays (CTAs)
   int nsm = 0;
   std::vector<int> plan_key;  // active gels of the plan on the device
+  int plan_spc = 0;           // slices per CTA it was built with
   // captured Newton iteration (launch part), replayed while its inputs stay the same
   struct NewtonGraph {
     cudaGraphExec_t exec = nullptr;
@@ -434,13 +437,25 @@ struct tx_batch {
     Dev dev{};
     PcgPlan plan{};
     int nctas = 0;
-    bool res = false, prof = false;
+    bool res = false, prof = false, tune = false;
     double eta = 0.0;
     int pcg_max = 0, refine = 0, accd_max = 0;
     long long launches = 0;
     long long phase_launches[PR_N] = {};
     std::vector<Prof::Pending> prof_pairs;
   } graph;
+  // PCG work-split autotuner (opt-in: a negative pcg_cta_slices): per class of active sets
+  // (number of gels, total slices in powers of 2^(1/2)) the candidate splits are tried on
+  // successive Newton rounds, timed per PCG iteration, and the fastest is kept
+  struct Tune {
+    int idx = 0;
+    double us[8] = {};
+    int best = -1;
+  };
+  bool tune_on = false;
+  std::map<long long, Tune> tune;
+  long long tune_key = -1;  // class of the current round (-1: not timing)
+  cudaEvent_t tev0 = nullptr, tev1 = nullptr;
   int graphs = -1;  // -1 undecided, 0 off (unsupported or disabled), 1 on
   bool capturing = false;  // profile events become event-record nodes of the graph
   cudaStream_t gst = nullptr;          // stream the graph is captured on and replayed on
@@ -829,7 +844,10 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     return TX_ERR_CUDA;
   }
   int spc_min = 0;  // slices (32 rows) per CTA at least
-  for (int g = 0; g < n; ++g) spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
+  for (int g = 0; g < n; ++g) {
+    spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
+    if (b->mesh[g].prm.pcg_cta_slices < 0) b->tune_on = true;
+  }
   if (spc_min <= 0) spc_min = b->mixed ? PCG_SLICES_MIXED : PCG_SLICES_FP64;
   b->pcg_spc_min = spc_min;
   b->nsm = nsm;
@@ -1313,11 +1331,24 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
 // fit co-resident on the device; the resident kernels are used when every CTA has at most a
 // slice per warp and they fit, else the streaming kernels.
 tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
-  if (set == b->plan_key && b->nctas > 0) return TX_OK;
   int total = 0;
   for (int g : set) total += b->gi[g].ns;
+  int spc0 = b->pcg_spc_min;
+  b->tune_key = -1;
+  if (b->tune_on) {
+    const long long key = (long long)std::min<size_t>(set.size(), 64) * 1000 +
+                          (long long)std::lround(2.0 * std::log2(std::max(total, 1)));
+    tx_batch::Tune& T = b->tune[key];
+    if (T.best < 0) {
+      spc0 = TUNE_SPC[T.idx];
+      b->tune_key = key;
+    } else {
+      spc0 = TUNE_SPC[T.best];
+    }
+  }
+  if (set == b->plan_key && b->nctas > 0 && spc0 == b->plan_spc) return TX_OK;
   const int nsm = b->nsm;
-  int spc = std::max(b->pcg_spc_min, 1), max_slices = 1;
+  int spc = std::max(spc0, 1), max_slices = 1;
   std::vector<int2>& rng = b->plan_rng_h;
   std::vector<int>& cgrp = b->plan_grp_of_h;
   std::vector<int4>& grp = b->plan_grp_h;
@@ -1379,7 +1410,36 @@ tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
   b->nctas = nctas;
   b->pcg_res = res;
   b->plan_key = set;
+  b->plan_spc = spc0;
   return TX_OK;
+}
+
+// after the round's synchronisation: the PCG time per iteration of the candidate being tried
+void tune_record(tx_batch* b, const std::vector<int>& set) {
+  if (b->tune_key < 0) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, b->tev0, b->tev1) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  int it = 1;
+  for (int g : set) it = std::max(it, b->gv_h[g].pcg_it);
+  tx_batch::Tune& T = b->tune[b->tune_key];
+  T.us[T.idx] = 1e3 * ms / it;
+  if (++T.idx == TUNE_N) {
+    T.best = 0;
+    for (int k = 1; k < TUNE_N; ++k)
+      if (T.us[k] < T.us[T.best]) T.best = k;
+  }
+  b->tune_key = -1;
+}
+
+void tune_event(tx_batch* b, cudaEvent_t& e) {
+  if (!e) cudaEventCreate(&e);
+  if (b->capturing)
+    cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, b->st);
 }
 
 // Launches of one Newton iteration for the gels in PH_NEWTON, up to the first line-search trial.
@@ -1400,6 +1460,7 @@ tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int 
   launch_precond(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
   CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
+  if (b->tune_key >= 0) tune_event(b, b->tev0);
   prof_open(b, PR_PCG);
   if (b->mixed) {
     if (b->pcg_res)
@@ -1413,6 +1474,7 @@ tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int 
       CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
   }
   prof_close(b, 1);
+  if (b->tune_key >= 0) tune_event(b, b->tev1);
   launch_gel_op(d, PH_NEWTON, 1, st);
   post_pcg_launch(b, accd_max);
   return TX_OK;
@@ -1449,7 +1511,8 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
   }
   if (b->graphs == 0) return newton_launches(b, eta, pcg_max, refine, accd_max);
   auto& G = b->graph;
-  const bool same = G.exec && G.key == set && G.res == b->pcg_res && G.nctas == b->nctas &&
+  const bool same = G.exec && G.key == set && G.res == b->pcg_res && G.nctas == b->nctas && !G.tune &&
+                    b->tune_key < 0 &&
                     G.prof == b->prof.on && G.eta == eta && G.pcg_max == pcg_max && G.refine == refine &&
                     G.accd_max == accd_max && std::memcmp(&G.dev, &b->d, sizeof(Dev)) == 0 &&
                     std::memcmp(&G.plan, &b->plan, sizeof(PcgPlan)) == 0;
@@ -1512,6 +1575,7 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
     G.nctas = b->nctas;
     G.res = b->pcg_res;
     G.prof = b->prof.on;
+    G.tune = b->tune_key >= 0;
     G.eta = eta;
     G.pcg_max = pcg_max;
     G.refine = refine;
@@ -1556,6 +1620,7 @@ tx_status do_newton(tx_batch* b) {
   if (s != TX_OK) return s;
   s = post_pcg_finish(b);
   if (s != TX_OK) return s;
+  tune_record(b, set);
   int derr = 0;
   CK(cudaMemcpy(&derr, d.err, sizeof(int), cudaMemcpyDeviceToHost));
   if (derr) {
@@ -1753,6 +1818,8 @@ void destroy_batch(tx_batch* b) {
     cudaStreamDestroy(b->gst);
   }
   if (b->gev_in) cudaEventDestroy(b->gev_in);
+  if (b->tev0) cudaEventDestroy(b->tev0);
+  if (b->tev1) cudaEventDestroy(b->tev1);
   if (b->gev_out) cudaEventDestroy(b->gev_out);
   for (cudaEvent_t e : b->prof.pool) cudaEventDestroy(e);
   b->mem.release();
