@@ -146,7 +146,7 @@ def run_gpu(args, rank, world, e2e=True):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    wls = make_workload(args.workload, args.seed + 1000 * rank, args.n_gels)
+    wls = make_workload(args.workload, rank_seed(args.seed, rank), args.n_gels)
     prec = B.TX_PREC_MIXED if args.precision == "mixed" else B.TX_PREC_FP64
     K, Wm = args.steps, args.warmup
     T = min(len(w.poses) for w in wls)
@@ -353,6 +353,25 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(values, device):
+    """The job's time is the slowest rank's: element-wise maximum over the process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_throughput(world, gels_per_rank, steps, max_seconds):
+    """Whole-job gel steps per second: every rank steps its own gels (weak scaling, no exchange)."""
+    return world * gels_per_rank * steps / max_seconds
+
+
+def rank_seed(seed, rank):
+    """Each rank draws its own gels (distinct seeded workloads)."""
+    return seed + 1000 * rank
+
+
 def main():
     args = parse_args()
     if args.workload == "serve" and args.impl == "gpu":
@@ -380,16 +399,12 @@ def main():
     r = run_gpu(args, rank, world)
     total_s, e2e_s = r["total_s"], r["e2e_s"]
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([total_s, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+        total_s, e2e_s = max_over_ranks([total_s, e2e_s], "cuda")
     if rank != 0:
         return
     K = args.steps
     ng = len(r["wls"])
-    value = world * ng * K / total_s
+    value = job_throughput(world, ng, K, total_s)
     step_ms = r["step_ms"]
     prof = r["prof"]
     line = {
