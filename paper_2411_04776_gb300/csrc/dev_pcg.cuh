@@ -98,6 +98,8 @@ __device__ __forceinline__ PcgCta pcg_cta(const Dev& d, const PcgPlan& plan) {
 // several CTAs (one gel) exchanges the CTA sums through d.part and every CTA adds them up in CTA
 // order.  Bitwise identical in every CTA of the group and in every run.  Includes the group
 // barrier between the two levels.
+// (A = float: the CTA-level sum of an FP32 inner iteration's partials is taken in FP32.)
+template <typename A = double>
 __device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double* dsm, int k0, int k1,
                                           double (*tot)[4], int* s_fail) {
   __syncthreads();
@@ -106,8 +108,8 @@ __device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double*
     const int j = t / nk, k = k0 + t % nk;
     const GelInfo& G = d.gi[c.g0 + j];
     const int a = max(c.s0, G.s0), b = min(c.s1, G.s0 + G.ns);
-    double v = 0.0;
-    for (int s = a + lane; s < b; s += 32) v += dsm[(s - c.s0) * 4 + k];
+    A v = A(0);
+    for (int s = a + lane; s < b; s += 32) v += (A)dsm[(s - c.s0) * 4 + k];
     v = warp_sum(v);
     if (lane == 0) {
       if (c.nc == 1)

@@ -110,6 +110,27 @@ __device__ __forceinline__ void res_post(const Dev& d, const PcgCta& c, const do
   }
 }
 
+// res_post for the FP32 inner iteration: the per-gel CTA sums of FP32 partials in FP32
+__device__ __forceinline__ void res_post_f(const Dev& d, const PcgCta& c, const double* dsm, int k0, int k1, int set,
+                                           double (*tot)[4]) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nk = k1 - k0;
+  for (int t = wid; t < c.ng * nk; t += (int)(blockDim.x >> 5)) {
+    const int j = t / nk, k = k0 + t % nk;
+    const GelInfo& G = d.gi[c.g0 + j];
+    const int a = max(c.s0, G.s0), b = min(c.s1, G.s0 + G.ns);
+    float v = 0.f;
+    for (int s = a + lane; s < b; s += 32) v += (float)dsm[(s - c.s0) * 4 + k];
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (c.nc == 1)
+        tot[j][k] = v;
+      else
+        d.part[(size_t)(4 * set + k) * gridDim.x + blockIdx.x] = v;
+    }
+  }
+}
+
 struct ResPrefetch {
   double v[RES_MAXNC / 32];
 };
@@ -429,7 +450,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
         dsm[4 * wid + 2] = rr;
       }
     }
-    res_post(d, c, dsm, 0, 3, 0, tot);
+    res_post_f(d, c, dsm, 0, 3, 0, tot);
     if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
     // ---- inner pipelined CG in FP32
     for (int i = 0;; ++i) {
@@ -498,7 +519,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
           dsm[4 * wid + 2] = rr;
         }
       }
-      res_post(d, c, dsm, 0, 3, par ^ 1, tot);
+      res_post_f(d, c, dsm, 0, 3, par ^ 1, tot);
       if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
     }
     // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p (FP32 values, FP64 arithmetic)

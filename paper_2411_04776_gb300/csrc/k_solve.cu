@@ -11,6 +11,8 @@
 //   * energy: E(x + alpha p) per gel = inertia + elastic + barrier, as per-piece partial sums
 //     (pieces never straddle gels) reduced per gel in a fixed order; the reduction kernel also
 //     takes the line-search decision (accept on E <= E_cur, else halve alpha).
+#include <type_traits>
+
 #include "dev_contact.cuh"
 #include "dev_elastic.cuh"
 #include "dev_pcg.cuh"
@@ -95,9 +97,12 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
   if (d.gc[g].phase != phase) return;
   const int c = d.colidx[bp];
   const bool diag = d.diag_pos[r] == bp;
-  double h[9];
+  // the block sum in the precision of the stored block (FP64 adds run at 1/64 of the FP32 rate);
+  // the gradient stays FP64
+  using HT = typename std::conditional<MIXED, float, double>::type;
+  HT h[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) h[e] = 0.0;
+  for (int e = 0; e < 9; ++e) h[e] = HT(0);
   double gr[3] = {0.0, 0.0, 0.0};
   const int c0 = d.ctr_ptr[bp], c1 = d.ctr_ptr[bp + 1];
   for (int k = c0; k < c1; ++k) {
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) h[3 * i + j] += (double)(tr ? s[3 * j + i] : s[3 * i + j]);
+        for (int j = 0; j < 3; ++j) h[3 * i + j] += tr ? s[3 * j + i] : s[3 * i + j];
     } else {
       const double* s = d.tscr + (size_t)t * TS + 9 * blk;
 #pragma unroll
@@ -128,9 +133,9 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
   if (diag) {
     const double h2 = d.gc[g].h * d.gc[g].h;
     const double m = d.mass[r] / h2;
-    h[0] += m;
-    h[4] += m;
-    h[8] += m;
+    h[0] += (HT)m;
+    h[4] += (HT)m;
+    h[8] += (HT)m;
     const double4_32a x = d.x[r], xt = d.xt[r];
     double4_32a go;
     if (d.fixed[r]) {
@@ -377,7 +382,7 @@ __device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lan
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
-__global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
+__global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
                                                      int refine_max) {
   extern __shared__ double dsm[];
   __shared__ double tot[PCG_MAXG][4];
@@ -461,20 +466,19 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_mixed(Dev d, int phase, PcgPlan p
           if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
           d.w32[r] = w;
           const float4 rv = d.r32[r], uv = d.u32[r];
-          ga = dot4f(rv, uv);
-          de = dot4f(w, uv);
-          rr = dot4f(rv, rv);
+          // FP32 warp sums: the inner solve's dot products are FP32 quantities (GB300 runs FP64
+          // adds at 1/64 of the FP32 rate); slices and CTAs are then added in FP64
+          ga = warp_sum(dot4f(rv, uv));
+          de = warp_sum(dot4f(w, uv));
+          rr = warp_sum(dot4f(rv, rv));
         }
-        ga = warp_sum(ga);
-        de = warp_sum(de);
-        rr = warp_sum(rr);
         if (lane == 0) {
           dsm[(s - c.s0) * 4 + 0] = ga;
           dsm[(s - c.s0) * 4 + 1] = de;
           dsm[(s - c.s0) * 4 + 2] = rr;
         }
       }
-      if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
+      if (!group_sum<float>(d, c, dsm, 0, 3, tot, &s_fail)) return;
       if (threadIdx.x == 0) s_any = 0;
       __syncthreads();
       for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
