@@ -430,12 +430,27 @@ struct tx_batch {
   int nsm = 0;
   std::vector<int> plan_key;  // active gels of the plan on the device
   int plan_spc = 0;           // slices per CTA it was built with
+  long long plan_version = 0; // bumped whenever the device plan changes
+  // A round's solve may run as several consecutive PCG launches ("parts"), each over a subset
+  // of the gels whose FP32 matrices fit in L2 together, so that its iterations after the first
+  // read the matrix from L2 instead of HBM.  Each part has its own plan arrays.
+  struct PlanPart {
+    PcgPlan plan{};
+    int nctas = 0;
+    bool res = false;
+  };
+  std::vector<PlanPart> parts;
+  int nparts = 0;
+  std::vector<double> nbp_gel;  // per gel: block positions of its sliced BSR
+  DevMem plan_mem;
+  int plan_parts_cap = 0;
+  double l2_budget = 0.0;     // bytes of FP32 matrices and vectors one part may hold
   // captured Newton iteration (launch part), replayed while its inputs stay the same
   struct NewtonGraph {
     cudaGraphExec_t exec = nullptr;
     std::vector<int> key;
     Dev dev{};
-    PcgPlan plan{};
+    long long plan_version = -1;
     int nctas = 0;
     bool res = false, prof = false, tune = false;
     double eta = 0.0;
@@ -852,6 +867,9 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->pcg_spc_min = spc_min;
   b->nsm = nsm;
   for (int q = 0; q < nslices; ++q) b->pcg_wmax = std::max(b->pcg_wmax, (slice_off[q + 1] - slice_off[q]) / SLICE);
+  b->nbp_gel.resize(n);
+  for (int g = 0; g < n; ++g)
+    b->nbp_gel[g] = (double)(slice_off[b->gi[g].s0 + b->gi[g].ns] - slice_off[b->gi[g].s0]);
   const int cta_cap = PCG_CTAS_PER_SM_CAP * nsm;  // largest co-resident grid of any plan
   b->pcg_cta_cap = cta_cap;
   // ---- energy pieces
@@ -943,21 +961,18 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
-  int2* rng_buf = M.get<int2>(cta_cap);
-  int* cta_buf = M.get<int>((size_t)cta_cap + nslices);
-  int4* grp_buf = M.get<int4>(n);
-  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !rng_buf || !cta_buf || !grp_buf ||
-      (b->mixed ? !d.vals32 : !d.vals)) {
+  int* sg_buf = M.get<int>(nslices);
+  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !sg_buf || (b->mixed ? !d.vals32 : !d.vals)) {
     M.release();
     delete b;
     return TX_ERR_OOM;
   }
-  b->plan.cta_rng = rng_buf;
-  b->plan.cta_grp = cta_buf;
-  b->plan.slice_gel = cta_buf + cta_cap;
-  b->plan.grp = grp_buf;
+  b->plan.slice_gel = sg_buf;
   b->plan.max_slices = 1;
   b->plan.ngroups = 0;
+  // L2-sized parts measured slower than one launch over all gels on the 64-gel batch (the parts'
+  // stragglers add up and every part re-reads its matrix once): off (0 = no split)
+  b->l2_budget = 0.0;
   if (b->mixed) {  // FP32 PCG vectors live in the upper half of dedicated buffers
     d.u32 = (float4*)M.get<float4>(rows);
     d.w32 = (float4*)M.get<float4>(rows);
@@ -1330,23 +1345,35 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
 // (index span <= 64, slice span <= spc) share one CTA.  spc grows from its minimum until the CTAs
 // fit co-resident on the device; the resident kernels are used when every CTA has at most a
 // slice per warp and they fit, else the streaming kernels.
-tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
-  int total = 0;
-  for (int g : set) total += b->gi[g].ns;
-  int spc0 = b->pcg_spc_min;
-  b->tune_key = -1;
-  if (b->tune_on) {
-    const long long key = (long long)std::min<size_t>(set.size(), 64) * 1000 +
-                          (long long)std::lround(2.0 * std::log2(std::max(total, 1)));
-    tx_batch::Tune& T = b->tune[key];
-    if (T.best < 0) {
-      spc0 = TUNE_SPC[T.idx];
-      b->tune_key = key;
-    } else {
-      spc0 = TUNE_SPC[T.best];
-    }
+// device arrays for `np` plan parts (each: CTA ranges, CTA groups, groups)
+tx_status ensure_plan_parts(tx_batch* b, int np) {
+  if (np <= b->plan_parts_cap) return TX_OK;
+  CK(cudaStreamSynchronize(b->st));
+  b->plan_mem.release();
+  const int cap = std::max(np, 2 * b->plan_parts_cap);
+  const size_t C = (size_t)b->pcg_cta_cap, G = (size_t)b->n;
+  int2* rng = b->plan_mem.get<int2>(C * cap);
+  int* cg = b->plan_mem.get<int>(C * cap);
+  int4* gr = b->plan_mem.get<int4>(G * cap);
+  if (!rng || !cg || !gr) return TX_ERR_OOM;
+  b->parts.resize(cap);
+  for (int k = 0; k < cap; ++k) {
+    PcgPlan& P = b->parts[k].plan;
+    P = b->plan;
+    P.cta_rng = rng + C * k;
+    P.cta_grp = cg + C * k;
+    P.grp = gr + G * k;
   }
-  if (set == b->plan_key && b->nctas > 0 && spc0 == b->plan_spc) return TX_OK;
+  b->plan_parts_cap = cap;
+  return TX_OK;
+}
+
+// PCG partition of one subset of the gels (in index order) into the given part.
+// Groups: a gel with more than spc slices is spread over ceil(ns / spc) CTAs; runs of small gels
+// (index span <= 64, slice span <= spc) share one CTA.  spc grows from its minimum until the CTAs
+// fit co-resident on the device; the resident kernels are used when every CTA has at most a
+// slice per warp and they fit, else the streaming kernels.
+tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch::PlanPart& part) {
   const int nsm = b->nsm;
   int spc = std::max(spc0, 1), max_slices = 1;
   std::vector<int2>& rng = b->plan_rng_h;
@@ -1400,17 +1427,59 @@ tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
   }
   const int nctas = (int)rng.size();
   cudaStream_t st = b->st;
-  // the staging vectors stay untouched until the copies ran: the host waits on the stream every
-  // Newton round before it can rebuild a plan
-  CK(cudaMemcpyAsync((void*)b->plan.cta_rng, rng.data(), sizeof(int2) * nctas, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync((void*)b->plan.cta_grp, cgrp.data(), sizeof(int) * nctas, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync((void*)b->plan.grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
-  b->plan.max_slices = max_slices;
-  b->plan.ngroups = (int)grp.size();
-  b->nctas = nctas;
-  b->pcg_res = res;
+  // pageable sources: the copies take the data when enqueued, the vectors can be reused at once
+  CK(cudaMemcpyAsync((void*)part.plan.cta_rng, rng.data(), sizeof(int2) * nctas, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync((void*)part.plan.cta_grp, cgrp.data(), sizeof(int) * nctas, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync((void*)part.plan.grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
+  part.plan.max_slices = max_slices;
+  part.plan.ngroups = (int)grp.size();
+  part.nctas = nctas;
+  part.res = res;
+  return TX_OK;
+}
+
+// The round's PCG plan for the gels of `set`, rebuilt only when the set changes.  With a nonzero
+// l2_budget, mixed precision splits the set into consecutive subsets whose FP32 blocks and Krylov
+// vectors fit in that budget (one PCG launch each); by default one launch covers the whole set.
+tx_status prepare_pcg_plan(tx_batch* b, const std::vector<int>& set) {
+  int total = 0;
+  for (int g : set) total += b->gi[g].ns;
+  int spc0 = b->pcg_spc_min;
+  b->tune_key = -1;
+  if (b->tune_on) {
+    const long long key = (long long)std::min<size_t>(set.size(), 64) * 1000 +
+                          (long long)std::lround(2.0 * std::log2(std::max(total, 1)));
+    tx_batch::Tune& T = b->tune[key];
+    if (T.best < 0) {
+      spc0 = TUNE_SPC[T.idx];
+      b->tune_key = key;
+    } else {
+      spc0 = TUNE_SPC[T.best];
+    }
+  }
+  if (set == b->plan_key && b->nctas > 0 && spc0 == b->plan_spc) return TX_OK;
+  std::vector<std::vector<int>> subsets(1);
+  double acc = 0.0;
+  for (int g : set) {
+    const double bytes = b->mixed ? 40.0 * b->nbp_gel[g] + 160.0 * b->gi[g].nv : 0.0;
+    if (b->mixed && b->l2_budget > 0.0 && !subsets.back().empty() && acc + bytes > b->l2_budget) {
+      subsets.emplace_back();
+      acc = 0.0;
+    }
+    subsets.back().push_back(g);
+    acc += bytes;
+  }
+  tx_status s = ensure_plan_parts(b, (int)subsets.size());
+  if (s != TX_OK) return s;
+  for (size_t k = 0; k < subsets.size(); ++k) {
+    s = plan_part(b, subsets[k], spc0, b->parts[k]);
+    if (s != TX_OK) return s;
+  }
+  b->nparts = (int)subsets.size();
+  b->nctas = b->parts[0].nctas;
   b->plan_key = set;
   b->plan_spc = spc0;
+  b->plan_version += 1;
   return TX_OK;
 }
 
@@ -1459,21 +1528,24 @@ tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int 
   prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
-  CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * b->plan.ngroups, st));
   if (b->tune_key >= 0) tune_event(b, b->tev0);
   prof_open(b, PR_PCG);
-  if (b->mixed) {
-    if (b->pcg_res)
-      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
-    else
-      CK(launch_pcg_mixed(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, refine, st));
-  } else {
-    if (b->pcg_res)
-      CK(launch_pcg_res(d, PH_NEWTON, b->plan, b->nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
-    else
-      CK(launch_pcg64(d, PH_NEWTON, b->plan, b->nctas, eta, pcg_max, st));
+  for (int k = 0; k < b->nparts; ++k) {
+    const tx_batch::PlanPart& P = b->parts[k];
+    CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * P.plan.ngroups, st));
+    if (b->mixed) {
+      if (P.res)
+        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
+      else
+        CK(launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, eta, pcg_max, refine, st));
+    } else {
+      if (P.res)
+        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
+      else
+        CK(launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, eta, pcg_max, st));
+    }
   }
-  prof_close(b, 1);
+  prof_close(b, b->nparts);
   if (b->tune_key >= 0) tune_event(b, b->tev1);
   launch_gel_op(d, PH_NEWTON, 1, st);
   post_pcg_launch(b, accd_max);
@@ -1511,11 +1583,11 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
   }
   if (b->graphs == 0) return newton_launches(b, eta, pcg_max, refine, accd_max);
   auto& G = b->graph;
-  const bool same = G.exec && G.key == set && G.res == b->pcg_res && G.nctas == b->nctas && !G.tune &&
+  const bool same = G.exec && G.key == set && G.nctas == b->nctas && !G.tune &&
                     b->tune_key < 0 &&
                     G.prof == b->prof.on && G.eta == eta && G.pcg_max == pcg_max && G.refine == refine &&
                     G.accd_max == accd_max && std::memcmp(&G.dev, &b->d, sizeof(Dev)) == 0 &&
-                    std::memcmp(&G.plan, &b->plan, sizeof(PcgPlan)) == 0;
+                    G.plan_version == b->plan_version;
   if (!same) {
     drop_newton_graph(b);
     const long long l0 = g_launch_count.load();
@@ -1571,9 +1643,8 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
     G.prof_pairs = pairs;
     G.key = set;
     G.dev = b->d;
-    G.plan = b->plan;
+    G.plan_version = b->plan_version;
     G.nctas = b->nctas;
-    G.res = b->pcg_res;
     G.prof = b->prof.on;
     G.tune = b->tune_key >= 0;
     G.eta = eta;
@@ -1825,6 +1896,7 @@ void destroy_batch(tx_batch* b) {
   b->mem.release();
   b->pair_mem.release();
   b->hash_mem.release();
+  b->plan_mem.release();
   if (b->gc_h) cudaFreeHost(b->gc_h);
   if (b->gv_h) cudaFreeHost(b->gv_h);
   delete b;
