@@ -181,9 +181,9 @@ __device__ __forceinline__ void tet_F(const double xs[4][3], const double Xs[4][
 
 __host__ __device__ __forceinline__ int ublk(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
 
-// Projected Hessian blocks (10 x 9 values, block (a<=b) at ublk(a,b)*9, row-major 3x3) in
-// precision R.  F, J and ln J come in FP64 (the gradient needs them there anyway).
-template <typename R, typename OutT>
+// Projected Hessian blocks (10 blocks of 9 values, block (a<=b) at ublk(a,b)*BS, row-major 3x3)
+// in precision R.  F, J and ln J come in FP64 (the gradient needs them there anyway).
+template <typename R, typename OutT, int BS = 9>
 __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, double lnJd, double mu_d, double lam_d,
                           double vol_d, const double Dd[4][3], bool project, OutT* out) {
   R F[3][3], D[4][3];
@@ -292,7 +292,7 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
       R T[3][3];
       for (int i = 0; i < 3; ++i)
         for (int l = 0; l < 3; ++l) T[i][l] = Hh[i][0] * U[l][0] + Hh[i][1] * U[l][1] + Hh[i][2] * U[l][2];
-      OutT* o = out + ublk(a, b) * 9;
+      OutT* o = out + ublk(a, b) * BS;
       for (int i = 0; i < 3; ++i)
         for (int l = 0; l < 3; ++l)
           o[3 * i + l] = (OutT)(vol * (U[i][0] * T[0][l] + U[i][1] * T[1][l] + U[i][2] * T[2][l]));

@@ -224,25 +224,29 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
     if (threadIdx.x == 0) d.gv[g].hent[tab] = -1;
     return;
   }
-  // exclusive scan of the bucket counts (fixed order)
-  if (threadIdx.x == 0) s_carry = 0;
+  // exclusive scan of the bucket counts: every thread scans a contiguous chunk serially, one
+  // block-wide scan of the chunk totals
+  const int per = (nb + HB_THREADS - 1) / HB_THREADS;
+  const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+  int own = 0;
+  for (int b = b0; b < b1; ++b) own += cnt[b];
+  s_part[threadIdx.x] = own;
   __syncthreads();
-  for (int base = 0; base < nb; base += HB_THREADS) {
-    const int b = base + threadIdx.x;
-    const int v = b < nb ? cnt[b] : 0;
-    s_part[threadIdx.x] = v;
+  for (int off = 1; off < HB_THREADS; off <<= 1) {
+    const int t = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
     __syncthreads();
-    for (int off = 1; off < HB_THREADS; off <<= 1) {
-      int t = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
-      __syncthreads();
-      s_part[threadIdx.x] += t;
-      __syncthreads();
-    }
-    if (b < nb) start[b] = s_carry + s_part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == HB_THREADS - 1) s_carry += s_part[HB_THREADS - 1];
+    s_part[threadIdx.x] += t;
     __syncthreads();
   }
+  int run = s_part[threadIdx.x] - own;
+  for (int b = b0; b < b1; ++b) {
+    const int c = cnt[b];
+    start[b] = run;
+    cnt[b] = run;  // fill cursor of the scatter below
+    run += c;
+  }
+  if (threadIdx.x == HB_THREADS - 1) s_carry = s_part[HB_THREADS - 1];
+  __syncthreads();
   const int total = s_carry;
   if (threadIdx.x == 0) {
     start[nb] = total;
@@ -254,7 +258,6 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
     for (int b = threadIdx.x; b <= nb; b += blockDim.x) start[b] = 0;
     return;
   }
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = start[b];
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     int c0;
@@ -269,21 +272,29 @@ __global__ void __launch_bounds__(HB_THREADS) k_hash_build(Dev d, int phase, int
           d.hent[he + pos] = make_int2(p0 + k, pack_cell(ix, iy, iz));
         }
   }
-  __syncthreads();
-  // deterministic order inside every bucket
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const int s = start[b], e = start[b + 1];
-    for (int i = s + 1; i < e; ++i) {
-      const int2 key = d.hent[he + i];
-      int j = i - 1;
-      while (j >= s) {
-        const int2 o = d.hent[he + j];
-        if (o.x < key.x || (o.x == key.x && o.y <= key.y)) break;
-        d.hent[he + j + 1] = o;
-        --j;
-      }
-      d.hent[he + j + 1] = key;
+}
+
+// deterministic order inside every bucket (the scatter above fills them in arrival order): one
+// thread per bucket, insertion sort by (primitive, cell); blockIdx.y = gel * NTAB + table
+__global__ void k_hash_sort(Dev d, int phase) {
+  const int g = blockIdx.y / NTAB, tab = blockIdx.y % NTAB;
+  if (d.gc[g].phase != phase) return;
+  const GelInfo& G = d.gi[g];
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= G.hnb[tab] || d.gv[g].hent[tab] < 0 || d.gv[g].hent[tab] > G.hcap[tab]) return;
+  const int* start = d.hstart + G.hb0[tab];
+  int2* e = d.hent + G.he0[tab];
+  const int s = start[b], t = start[b + 1];
+  for (int i = s + 1; i < t; ++i) {
+    const int2 key = e[i];
+    int j = i - 1;
+    while (j >= s) {
+      const int2 o = e[j];
+      if (o.x < key.x || (o.x == key.x && o.y <= key.y)) break;
+      e[j + 1] = o;
+      --j;
     }
+    e[j + 1] = key;
   }
 }
 
@@ -703,6 +714,8 @@ void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st) {
     count_launch(1);
   }
   k_hash_build<<<d.n_gels * NTAB, HB_THREADS, 0, st>>>(d, phase, swept);
+  count_launch(1);
+  k_hash_sort<<<dim3(nblk(d.max_hnb, 128), d.n_gels * NTAB), 128, 0, st>>>(d, phase);
   count_launch(1);
 }
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st) {

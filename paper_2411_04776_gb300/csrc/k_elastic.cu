@@ -27,14 +27,14 @@ __global__ void __launch_bounds__(128) k_tet_assemble(Dev d, int phase) {
   if (!nh_grad(F, Hd, G.mu, G.lam, d.vol[t], D, gr, nullptr, &J, &lnJ)) {
     // inverted element (cannot happen after a successful line search): flag and zero it
     atomicOr(&d.gv[g].flags, 4);
-    for (int k = 0; k < 102; ++k) out[k] = 0.0;
+    for (int k = 0; k < TS; ++k) out[k] = 0.0;
     return;
   }
-  for (int k = 0; k < 12; ++k) out[90 + k] = gr[k];
+  for (int k = 0; k < 12; ++k) out[GOFF + k] = gr[k];
   if (MIXED)
-    nh_blocks<float, float>(F, J, lnJ, G.mu, G.lam, d.vol[t], D, true, d.tscr32 + (size_t)t * TS32);
+    nh_blocks<float, float, BLK32>(F, J, lnJ, G.mu, G.lam, d.vol[t], D, true, d.tscr32 + (size_t)t * TS32);
   else
-    nh_blocks<double, double>(F, J, lnJ, G.mu, G.lam, d.vol[t], D, true, out);
+    nh_blocks<double, double, BLK64>(F, J, lnJ, G.mu, G.lam, d.vol[t], D, true, out);
 }
 
 void launch_tet_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {

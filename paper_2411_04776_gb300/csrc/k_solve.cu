@@ -105,26 +105,38 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
   for (int e = 0; e < 9; ++e) h[e] = HT(0);
   double gr[3] = {0.0, 0.0, 0.0};
   const int c0 = d.ctr_ptr[bp], c1 = d.ctr_ptr[bp + 1];
+#pragma unroll 2
   for (int k = c0; k < c1; ++k) {
     const int code = d.ctr[k];
     const int t = code >> 4, a = (code >> 2) & 3, b = code & 3;
     const bool tr = a > b;
     const int blk = tr ? ublk(b, a) : ublk(a, b);
+    HT v[12];  // the block as stored (row-major 3x3, padded), read with 16-byte loads
     if (MIXED) {
-      const float* s = d.tscr32 + (size_t)t * TS32 + 9 * blk;
+      const float4* s = reinterpret_cast<const float4*>(d.tscr32 + (size_t)t * TS32 + BLK32 * blk);
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) h[3 * i + j] += tr ? s[3 * j + i] : s[3 * i + j];
+      for (int q = 0; q < 3; ++q) {
+        const float4 f = s[q];
+        v[4 * q] = f.x;
+        v[4 * q + 1] = f.y;
+        v[4 * q + 2] = f.z;
+        v[4 * q + 3] = f.w;
+      }
     } else {
-      const double* s = d.tscr + (size_t)t * TS + 9 * blk;
+      const double2* s = reinterpret_cast<const double2*>(d.tscr + (size_t)t * TS + BLK64 * blk);
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) h[3 * i + j] += tr ? s[3 * j + i] : s[3 * i + j];
+      for (int q = 0; q < 5; ++q) {
+        const double2 f = s[q];
+        v[2 * q] = (HT)f.x;
+        v[2 * q + 1] = (HT)f.y;
+      }
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) h[3 * i + j] += tr ? v[3 * j + i] : v[3 * i + j];
     if (diag) {
-      const double* s = d.tscr + (size_t)t * TS + 90 + 3 * a;
+      const double* s = d.tscr + (size_t)t * TS + GOFF + 3 * a;
       gr[0] += s[0];
       gr[1] += s[1];
       gr[2] += s[2];

@@ -24,8 +24,13 @@
 namespace txg {
 
 constexpr int SLICE = 32;
-constexpr int TS = 104;        // per-tet scratch stride (90 Hessian + 12 gradient + 2 pad), doubles
-constexpr int TS32 = 96;       // per-tet FP32 Hessian scratch stride (90 + 6 pad), floats
+// per-tet scratch: the 10 upper 3x3 blocks, each padded to a 16-byte multiple so the gather reads
+// it with vector loads (FP64: 10 doubles per block, FP32: 12 floats), then the 12-entry gradient
+constexpr int BLK64 = 10;      // doubles per block in the FP64 scratch
+constexpr int BLK32 = 12;      // floats per block in the FP32 scratch
+constexpr int GOFF = 100;      // gradient offset in the FP64 scratch
+constexpr int TS = 112;        // per-tet FP64 scratch stride (10 x 10 blocks + 12 gradient), doubles
+constexpr int TS32 = 120;      // per-tet FP32 block scratch stride (10 x 12), floats
 constexpr int NTAB = 3;        // hash tables per gel: indenter tris, indenter verts, indenter edges
 constexpr int PAIR_PT = 0;     // gel surface vertex   vs indenter triangle
 constexpr int PAIR_TP = 1;     // indenter vertex      vs gel surface triangle
@@ -146,6 +151,7 @@ struct Dev {
   // hash
   int* hstart;     // bucket starts (global, per table segment nb + 1)
   int* hcount;     // bucket fill cursors
+  int max_hnb;     // largest bucket count of any table
   int2* hent;      // entries (prim, packed cell)
   // candidate pairs
   int nq;

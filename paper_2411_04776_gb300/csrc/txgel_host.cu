@@ -667,7 +667,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     }
   // ---- offsets
   b->gi.resize(n);
-  int rows = 0, tets = 0, nsv = 0, nst = 0, nse = 0, nq = 0, niv = 0, nit = 0, nie = 0, hb = 0;
+  int rows = 0, tets = 0, nsv = 0, nst = 0, nse = 0, nq = 0, niv = 0, nit = 0, nie = 0, hb = 0, max_hnb = 1;
   for (int g = 0; g < n; ++g) {
     const Mesh& m = b->mesh[g];
     GelInfo& G = b->gi[g];
@@ -704,6 +704,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     const int np[NTAB] = {G.nit, G.niv, G.nie};
     for (int t = 0; t < NTAB; ++t) {
       G.hnb[t] = next_pow2(std::max(16, 2 * np[t]));
+      max_hnb = std::max(max_hnb, G.hnb[t]);
       G.hb0[t] = hb;
       hb += G.hnb[t] + 1;
       G.hcap[t] = std::max(256, 8 * np[t]);
@@ -953,6 +954,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.pbox = M.get<double4_32a>(2 * ((size_t)nit + niv + nie));
   d.hstart = M.get<int>(hb);
   d.hcount = M.get<int>(hb);
+  d.max_hnb = max_hnb;
   d.qcount = M.get<int>(nq + 1);
   d.qoff = M.get<int>(nq + 1);
   d.err = M.get<int>(4);
