@@ -299,77 +299,186 @@ __global__ void k_hash_sort(Dev d, int phase) {
 }
 
 // ---------------------------------------------------------------- hash query
-// mode bit 0: write (else count); bit 1: gel boxes swept by p; bit 2: indenter boxes swept;
-// bit 3: skip gels whose Newton iteration converged.  Counts of gels outside `phase` are left
-// untouched: every gel only uses the offsets of its own queries relative to its first one.
-__global__ void k_query(Dev d, int phase, int mode) {
+// mode bit 0: write (else count); bit 1: gel boxes swept by p; bit 3: skip gels whose Newton
+// iteration converged.  Counts of gels outside `phase` are left untouched: every gel only uses
+// the offsets of its own queries relative to its first one.  The indenter boxes (swept or not)
+// were stored by the last hash build of the gel.
+//
+// Two kernels: one thread per gel surface primitive drops those nowhere near the indenter's box
+// (count 0) and lists the others; then, for a short list (a single gel: latency matters), one
+// warp per listed primitive walks its cells, a lane per cell (a lane per indenter primitive when
+// the box is too large for the hash or the table is brute force), and a warp scan of the lanes'
+// counts places every candidate; for a long list (batches: throughput matters) one thread per
+// listed primitive walks them serially.  Either way the order is the cell order (z, y, x) and the
+// bucket order within a cell.
+
+struct QueryCtx {
+  int g, type, gk, tab;
+  Box qb;
+  double pad, ic;
+  int lo[3], hi[3];
+  long long ncell;
+  bool brute;
+};
+
+__device__ __forceinline__ bool query_ctx(const Dev& d, int q, int phase, int mode, QueryCtx& c) {
+  const bool gsw = (mode >> 1) & 1, skc = (mode >> 3) & 1;
+  c.g = d.q_gel[q];
+  if (d.gc[c.g].phase != phase) return false;
+  if (skc && d.gv[c.g].converged) return false;
+  const GelInfo& G = d.gi[c.g];
+  const int tp = d.q_tp[q];
+  c.type = tp >> 28;
+  const int loc = tp & ((1 << 28) - 1);
+  c.gk = (c.type == PAIR_PT ? G.sv0 : (c.type == PAIR_TP ? G.st0 : G.se0)) + loc;
+  c.tab = c.type;
+  c.qb = gel_box(d, c.type, c.gk, gsw);
+  c.pad = G.dhat;
+  c.ic = 1.0 / G.cell;
+  for (int k = 0; k < 3; ++k) {
+    c.lo[k] = cell_of(c.qb.lo[k] - c.pad, G.org[k], c.ic);
+    c.hi[k] = cell_of(c.qb.hi[k] + c.pad, G.org[k], c.ic);
+  }
+  c.ncell = (long long)(c.hi[0] - c.lo[0] + 1) * (c.hi[1] - c.lo[1] + 1) * (c.hi[2] - c.lo[2] + 1);
+  c.brute = c.ncell > QUERY_CELL_LIMIT || d.gv[c.g].hent[c.tab] < 0;
+  return true;
+}
+
+__global__ void k_query_near(Dev d, int phase, int mode) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.nq) return;
-  // indenter boxes (swept or not, bit 2) were stored by the last hash build of the gel
-  const bool write = mode & 1, gsw = (mode >> 1) & 1, skc = (mode >> 3) & 1;
-  const int g = d.q_gel[q];
-  if (d.gc[g].phase != phase) return;
-  if (skc && d.gv[g].converged) return;
-  const GelInfo& G = d.gi[g];
-  const int tp = d.q_tp[q];
-  const int type = tp >> 28, loc = tp & ((1 << 28) - 1);
-  const int gk = (type == PAIR_PT ? G.sv0 : (type == PAIR_TP ? G.st0 : G.se0)) + loc;
-  const int tab = type;
-  const Box qb = gel_box(d, type, gk, gsw);
-  const double pad = G.dhat, ic = 1.0 / G.cell;
-  {
-    Box ib;
-    for (int c = 0; c < 3; ++c) {
-      ib.lo[c] = d.gv[g].ibox_lo[c];
-      ib.hi[c] = d.gv[g].ibox_hi[c];
-    }
-    if (!near_boxes(qb, ib, pad)) {  // nowhere near the indenter
-      if (!write) d.qcount[q] = 0;
-      return;
-    }
+  QueryCtx c;
+  if (!query_ctx(d, q, phase, mode, c)) return;
+  Box ib;
+  for (int k = 0; k < 3; ++k) {
+    ib.lo[k] = d.gv[c.g].ibox_lo[k];
+    ib.hi[k] = d.gv[c.g].ibox_hi[k];
   }
-  int lo[3], hi[3];
-  for (int c = 0; c < 3; ++c) {
-    lo[c] = cell_of(qb.lo[c] - pad, G.org[c], ic);
-    hi[c] = cell_of(qb.hi[c] + pad, G.org[c], ic);
+  if (!near_boxes(c.qb, ib, c.pad)) {  // nowhere near the indenter
+    d.qcount[q] = 0;
+    return;
   }
-  const long long ncell = (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
-  int count = 0;
+  d.qnear[atomicAdd(d.qnear_n, 1)] = q;
+}
+
+// matches of indenter primitive entry `ent` found in cell (ix, iy, iz) of the query
+__device__ __forceinline__ bool query_match(const Dev& d, const QueryCtx& c, int2 ent, int ix, int iy, int iz) {
+  if (ent.y != pack_cell(ix, iy, iz)) return false;
+  int c0;
+  const Box pb = load_pbox(d, c.tab, ent.x, &c0);
+  const int px = c0 & HMAXC, py = (c0 >> 10) & HMAXC, pz = c0 >> 20;
+  if (ix != max(c.lo[0], px) || iy != max(c.lo[1], py) || iz != max(c.lo[2], pz)) return false;
+  return near_boxes(c.qb, pb, c.pad);
+}
+
+// one thread per listed primitive: its cells and buckets walked serially (throughput mode, for
+// lists much longer than the grid's warps)
+__device__ void query_thread(const Dev& d, int q, int phase, int mode) {
+  const bool write = mode & 1;
+  QueryCtx c;
+  query_ctx(d, q, phase, mode, c);
+  const GelInfo& G = d.gi[c.g];
   const int base = write ? d.qoff[q] - d.qoff[G.q0] : 0;
+  int count = 0;
   auto emit = [&](int P) {
-    if (write && base + count < G.pcap) d.pairs[G.pbase + base + count] = make_int4(type, gk, P, g);
+    if (write && base + count < G.pcap) d.pairs[G.pbase + base + count] = make_int4(c.type, c.gk, P, c.g);
     ++count;
   };
-  if (ncell > QUERY_CELL_LIMIT || d.gv[g].hent[tab] < 0) {
-    // enormous sweep: test every primitive of the table directly
-    const int n = tab == 0 ? G.nit : (tab == 1 ? G.niv : G.nie);
-    const int p0 = tab == 0 ? G.it0 : (tab == 1 ? G.iv0 : G.ie0);
-    for (int k = 0; k < n; ++k) {
-      int c0;
-      const Box pb = load_pbox(d, tab, p0 + k, &c0);
-      if (near_boxes(qb, pb, pad)) emit(p0 + k);
+  if (c.brute) {
+    const int np = c.tab == 0 ? G.nit : (c.tab == 1 ? G.niv : G.nie);
+    const int p0 = c.tab == 0 ? G.it0 : (c.tab == 1 ? G.iv0 : G.ie0);
+    for (int k = 0; k < np; ++k) {
+      int cc;
+      const Box pb = load_pbox(d, c.tab, p0 + k, &cc);
+      if (near_boxes(c.qb, pb, c.pad)) emit(p0 + k);
     }
   } else {
-    const int nb = G.hnb[tab], hb = G.hb0[tab], he = G.he0[tab];
-    for (int iz = lo[2]; iz <= hi[2]; ++iz)
-      for (int iy = lo[1]; iy <= hi[1]; ++iy)
-        for (int ix = lo[0]; ix <= hi[0]; ++ix) {
-          const int key = pack_cell(ix, iy, iz);
+    const int nb = G.hnb[c.tab], hb = G.hb0[c.tab], he = G.he0[c.tab];
+    for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
+      for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
+        for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) {
           const int bk = hash_cell(ix, iy, iz) & (nb - 1);
           const int s = d.hstart[hb + bk], e = d.hstart[hb + bk + 1];
           for (int m = s; m < e; ++m) {
             const int2 ent = d.hent[he + m];
-            if (ent.y != key) continue;
-            int c0;
-            const Box pb = load_pbox(d, tab, ent.x, &c0);
-            const int px = c0 & HMAXC, py = (c0 >> 10) & HMAXC, pz = c0 >> 20;
-            if (ix != max(lo[0], px) || iy != max(lo[1], py) || iz != max(lo[2], pz)) continue;
-            if (!near_boxes(qb, pb, pad)) continue;
-            emit(ent.x);
+            if (query_match(d, c, ent, ix, iy, iz)) emit(ent.x);
           }
         }
   }
   if (!write) d.qcount[q] = count;
+}
+
+__global__ void __launch_bounds__(128) k_query_list(Dev d, int phase, int mode) {
+  const bool write = mode & 1;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int n = *d.qnear_n;
+  if (n > 4 * nw) {  // long list: a thread per primitive keeps every lane busy
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      query_thread(d, d.qnear[i], phase, mode);
+    return;
+  }
+  for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
+    const int q = d.qnear[w];
+    QueryCtx c;
+    query_ctx(d, q, phase, mode, c);
+    const GelInfo& G = d.gi[c.g];
+    int base = write ? d.qoff[q] - d.qoff[G.q0] : 0;
+    int total = 0;
+    if (c.brute) {
+      const int np = c.tab == 0 ? G.nit : (c.tab == 1 ? G.niv : G.nie);
+      const int p0 = c.tab == 0 ? G.it0 : (c.tab == 1 ? G.iv0 : G.ie0);
+      for (int k0 = 0; k0 < np; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        if (k < np) {
+          int cc;
+          const Box pb = load_pbox(d, c.tab, p0 + k, &cc);
+          hit = near_boxes(c.qb, pb, c.pad);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (write && hit) {
+          const int pos = base + total + __popc(m & ((1u << lane) - 1u));
+          if (pos < G.pcap) d.pairs[G.pbase + pos] = make_int4(c.type, c.gk, p0 + k, c.g);
+        }
+        total += __popc(m);
+      }
+    } else {
+      const int nx = c.hi[0] - c.lo[0] + 1, ny = c.hi[1] - c.lo[1] + 1;
+      const int nb = G.hnb[c.tab], hb = G.hb0[c.tab], he = G.he0[c.tab];
+      for (long long ci0 = 0; ci0 < c.ncell; ci0 += 32) {
+        const long long ci = ci0 + lane;
+        int cnt = 0, s = 0, e = 0, ix = 0, iy = 0, iz = 0;
+        if (ci < c.ncell) {
+          ix = c.lo[0] + (int)(ci % nx);
+          iy = c.lo[1] + (int)((ci / nx) % ny);
+          iz = c.lo[2] + (int)(ci / ((long long)nx * ny));
+          const int bk = hash_cell(ix, iy, iz) & (nb - 1);
+          s = d.hstart[hb + bk];
+          e = d.hstart[hb + bk + 1];
+          for (int m = s; m < e; ++m)
+            if (query_match(d, c, d.hent[he + m], ix, iy, iz)) ++cnt;
+        }
+        int pre = cnt;  // inclusive warp scan of the lanes' counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, pre, o);
+          if (lane >= o) pre += t;
+        }
+        if (write && cnt) {
+          int pos = base + total + pre - cnt;
+          for (int m = s; m < e; ++m) {
+            const int2 ent = d.hent[he + m];
+            if (!query_match(d, c, ent, ix, iy, iz)) continue;
+            if (pos < G.pcap) d.pairs[G.pbase + pos] = make_int4(c.type, c.gk, ent.x, c.g);
+            ++pos;
+          }
+        }
+        total += __shfl_sync(0xffffffffu, pre, 31);
+      }
+    }
+    if (!write && lane == 0) d.qcount[q] = total;
+  }
 }
 
 __global__ void k_pair_ranges(Dev d, int phase, int skip_conv) {
@@ -719,10 +828,14 @@ void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st) {
   count_launch(1);
 }
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st) {
-  if (d.nq > 0) {
-    k_query<<<nblk(d.nq, 128), 128, 0, st>>>(d, phase, mode);
+  if (d.nq <= 0) return;
+  if (!(mode & 1)) {  // the count pass lists the primitives near the indenter; the write pass reuses it
+    cudaMemsetAsync(d.qnear_n, 0, sizeof(int), st);
+    k_query_near<<<nblk(d.nq, 128), 128, 0, st>>>(d, phase, mode);
     count_launch(1);
   }
+  k_query_list<<<std::min(nblk(d.nq, 4), 8 * 152), 128, 0, st>>>(d, phase, mode);
+  count_launch(1);
 }
 void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st) {
   k_pair_ranges<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, skip_conv);

@@ -157,6 +157,8 @@ struct Dev {
   int nq;
   int* qcount;     // nq + 1
   int* qoff;       // nq + 1 (exclusive scan)
+  int* qnear;      // queries near the indenter (listed by the count pass), and their count
+  int* qnear_n;
   int4* pairs;     // (type, gel prim, indenter prim, gel), per-gel segments [pbase, pbase + pcap)
   int* pslot_gel;  // gel of every pair slot
   int npslots;

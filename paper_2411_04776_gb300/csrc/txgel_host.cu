@@ -957,6 +957,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.max_hnb = max_hnb;
   d.qcount = M.get<int>(nq + 1);
   d.qoff = M.get<int>(nq + 1);
+  d.qnear = M.get<int>(nq + 1);
+  d.qnear_n = M.get<int>(4);
   d.err = M.get<int>(4);
   d.cwork_n = M.get<int>(4);
   b->pieces = M.get<int4>(b->npieces);
@@ -1253,7 +1255,7 @@ void post_pcg_launch(tx_batch* b, int accd_max) {
   launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
   launch_query(d, PH_NEWTON, 1 | 2 | 8, st);
   launch_pair_ranges(d, PH_NEWTON, 1, st);
-  prof_close(b, 6);
+  prof_close(b, 7);
   prof_open(b, PR_ACCD);
   launch_accd(d, PH_NEWTON, 0, accd_max, st);
   launch_gel_op(d, PH_NEWTON, 2, st);
