@@ -54,9 +54,13 @@ def parse_args():
     ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
-    ap.add_argument("--pcg-cta-slices", type=int, default=None,
+    ap.add_argument("--pcg-cta-slices", type=int, default=0,
                     help="PCG work split: 32-row slices per CTA at least (0: library default, -1: autotune; "
-                         "default: autotune for single gels, library default for batches)")
+                         "the autotuner measured no gain on the default workloads)")
+    ap.add_argument("--pcg-rel-tol", type=float, default=None,
+                    help="PCG forcing term near Newton convergence (default: the library's)")
+    ap.add_argument("--pcg-rel-tol-far", type=float, default=None,
+                    help="PCG forcing term far from Newton convergence (default: the library's)")
     return ap.parse_args()
 
 
@@ -151,8 +155,8 @@ def run_gpu(args, rank, world, e2e=True):
     K, Wm = args.steps, args.warmup
     T = min(len(w.poses) for w in wls)
     assert Wm + K <= T, f"the trajectories have {T} steps"
-    spc = args.pcg_cta_slices if args.pcg_cta_slices is not None else (-1 if len(wls) == 1 else 0)
-    descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=spc) for w in wls]
+    kw = {k: getattr(args, k) for k in ("pcg_rel_tol", "pcg_rel_tol_far") if getattr(args, k) is not None}
+    descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=args.pcg_cta_slices, **kw) for w in wls]
     single = len(wls) == 1
     if single:
         gel = B.Gel(descs[0], stream=stream)

@@ -60,7 +60,12 @@ typedef struct tx_params {
   double dhat;          /* barrier activation distance d_hat [m] (default 1e-4)                 */
   double kappa;         /* barrier stiffness [N/m]; <= 0 selects E * mean gel surface edge length */
   double newton_tol;    /* stop when ||p||_inf / h < newton_tol * (rest bbox diagonal) [1/s]     */
-  double pcg_rel_tol;   /* PCG stops at ||r|| <= pcg_rel_tol * ||g|| (inexact Newton, 1e-3)      */
+  double pcg_rel_tol;   /* PCG stops at ||r|| <= pcg_rel_tol * ||g|| (inexact Newton, 1e-3) near
+                           convergence: when the next ||p||_inf, predicted from the last one and
+                           the last contraction ratio, is below twice the Newton tolerance, and
+                           always for the direction that ends the solve                        */
+  double pcg_rel_tol_far; /* forcing term of the other Newton iterations (default 0.1); values
+                           at or below pcg_rel_tol give a fixed forcing term                  */
   double gravity[3];    /* body acceleration [m/s^2] (default 0)                                 */
   int32_t newton_max_iter;  /* default 200                                                     */
   int32_t pcg_max_iter;     /* default 2000; hitting it keeps the direction (still descent)     */

@@ -30,7 +30,8 @@ c_ip = ctypes.POINTER(ctypes.c_int32)
 
 class tx_params(ctypes.Structure):
     _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("newton_tol", ctypes.c_double),
-                ("pcg_rel_tol", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+                ("pcg_rel_tol", ctypes.c_double), ("pcg_rel_tol_far", ctypes.c_double),
+                ("gravity", ctypes.c_double * 3),
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
                 ("ls_max_halvings", ctypes.c_int32), ("accd_max_iter", ctypes.c_int32),
                 ("max_split_depth", ctypes.c_int32), ("precision", ctypes.c_int32),

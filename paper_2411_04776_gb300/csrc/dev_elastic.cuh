@@ -164,18 +164,18 @@ __device__ __forceinline__ void tet_D(const double* Dmi, double D[4][3]) {
   }
 }
 
-// F (and H = F - I through displacements when X given) of one tet
+// Displacement gradient H = sum_a (x_a - X_a) D_a^T of one tet and F = I + H
+// (sum_a X_a D_a^T = I by the definition of Dm^-1)
 __device__ __forceinline__ void tet_F(const double xs[4][3], const double Xs[4][3], const double D[4][3],
                                       double F[3][3], double Hd[3][3]) {
+  double u[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i) u[a][i] = xs[a][i] - Xs[a][i];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double f = 0.0, h = 0.0;
-      for (int a = 0; a < 4; ++a) {
-        f += xs[a][i] * D[a][j];
-        h += (xs[a][i] - Xs[a][i]) * D[a][j];
-      }
-      F[i][j] = f;
+      const double h = u[0][i] * D[0][j] + u[1][i] * D[1][j] + u[2][i] * D[2][j] + u[3][i] * D[3][j];
       Hd[i][j] = h;
+      F[i][j] = i == j ? 1.0 + h : h;
     }
 }
 
@@ -183,19 +183,73 @@ __host__ __device__ __forceinline__ int ublk(int a, int b) { return a * 4 - (a *
 
 // Projected Hessian blocks (10 blocks of 9 values, block (a<=b) at ublk(a,b)*BS, row-major 3x3)
 // in precision R.  F, J and ln J come in FP64 (the gradient needs them there anyway).
+template <typename R>
+__device__ __forceinline__ R rsqrt_r(R v) {
+  if constexpr (sizeof(R) == 8)
+    return rsqrt(v);
+  else
+    return rsqrtf(v);
+}
+
+// One vertex block H_ab = U Hhat_ab U^T (Ap, P2, Q2 already scaled by the rest volume); x =
+// Dhat_a, y = Dhat_b.  A diagonal block (x == y) is symmetric: its lower half is mirrored.
+template <typename R, bool DIAG>
+__device__ __forceinline__ void nh_vertex_block(const R U[3][3], const R Ap[3][3], const R P2[3][3],
+                                                const R Q2[3][3], const R x[3], const R y[3], R H[3][3]) {
+  R Hh[3][3];
+  const R w0 = x[0] * y[0], w1 = x[1] * y[1], w2 = x[2] * y[2];
+  Hh[0][0] = w0 * Ap[0][0] + w1 * P2[0][1] + w2 * P2[0][2];
+  Hh[1][1] = w1 * Ap[1][1] + w0 * P2[1][0] + w2 * P2[1][2];
+  Hh[2][2] = w2 * Ap[2][2] + w0 * P2[2][0] + w1 * P2[2][1];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (i != l) Hh[i][l] = (x[i] * y[l]) * Ap[i][l] + (x[l] * y[i]) * Q2[i][l];
+  R T[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) T[i][l] = Hh[i][0] * U[l][0] + Hh[i][1] * U[l][1] + Hh[i][2] * U[l][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      if (DIAG && l < i) continue;
+      H[i][l] = U[i][0] * T[0][l] + U[i][1] * T[1][l] + U[i][2] * T[2][l];
+    }
+  if (DIAG) {
+    H[1][0] = H[0][1];
+    H[2][0] = H[0][2];
+    H[2][1] = H[1][2];
+  }
+}
+
+template <typename OutT, int BS, typename R>
+__device__ __forceinline__ void nh_store_block(OutT* o, const R H[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) o[3 * i + l] = (OutT)H[i][l];
+}
+
+// Projected Hessian blocks (10 blocks of 9 values, block (a<=b) at ublk(a,b)*BS, row-major 3x3)
+// in precision R.  F, J and ln J come in FP64 (the gradient needs them there anyway).  D[0] is
+// minus the sum of D[1..3] (translation invariance), so H is bilinear in the D's and the blocks
+// of vertex 0 follow from the other six: H_0b = -sum_{a>=1} H_ab, H_00 = -sum_{b>=1} H_0b.
 template <typename R, typename OutT, int BS = 9>
 __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, double lnJd, double mu_d, double lam_d,
                           double vol_d, const double Dd[4][3], bool project, OutT* out) {
   R F[3][3], D[4][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) F[i][j] = (R)Fd[i][j];
-  for (int a = 0; a < 4; ++a)
+  for (int a = 1; a < 4; ++a)
     for (int j = 0; j < 3; ++j) D[a][j] = (R)Dd[a][j];
   const R mu = (R)mu_d, lam = (R)lam_d, vol = (R)vol_d;
   // SVD of F through the eigen-decomposition of F^T F
   R C[3][3], s2[3], V[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) C[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+    for (int j = i; j < 3; ++j) C[i][j] = C[j][i] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
   if constexpr (sizeof(R) == 8)
     eig3_refined(C, s2, V);
   else
@@ -204,7 +258,7 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
   if (s2[o0] < s2[o1]) { int t = o0; o0 = o1; o1 = t; }
   if (s2[o1] < s2[o2]) { int t = o1; o1 = o2; o2 = t; }
   if (s2[o0] < s2[o1]) { int t = o0; o0 = o1; o1 = t; }
-  R sg[3];
+  R sg[3], is[3];  // singular values and their reciprocals
   sg[o0] = sqrt(fmax(s2[o0], R(0)));
   sg[o1] = sqrt(fmax(s2[o1], R(0)));
   R U[3][3];
@@ -214,12 +268,12 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
       u0[i] = F[i][0] * V[0][o0] + F[i][1] * V[1][o0] + F[i][2] * V[2][o0];
       u1[i] = F[i][0] * V[0][o1] + F[i][1] * V[1][o1] + F[i][2] * V[2][o1];
     }
-    R n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
-    for (int i = 0; i < 3; ++i) u0[i] /= n0;
+    const R r0 = rsqrt_r(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    for (int i = 0; i < 3; ++i) u0[i] *= r0;
     R d = u0[0] * u1[0] + u0[1] * u1[1] + u0[2] * u1[2];
     for (int i = 0; i < 3; ++i) u1[i] -= d * u0[i];
-    R n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-    for (int i = 0; i < 3; ++i) u1[i] /= n1;
+    const R r1 = rsqrt_r(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    for (int i = 0; i < 3; ++i) u1[i] *= r1;
     R u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2],
                u0[0] * u1[1] - u0[1] * u1[0]};
     for (int i = 0; i < 3; ++i) {
@@ -231,72 +285,85 @@ __device__ __forceinline__ void nh_blocks(const double Fd[3][3], double Jd, doub
     if ((det3(U) > R(0)) != (det3(V) > R(0)))
       for (int i = 0; i < 3; ++i) U[i][o2] = -U[i][o2];
   }
-  sg[o2] = (R)Jd / (sg[o0] * sg[o1]);
+  {
+    const R p01 = sg[o0] * sg[o1], iJ = R(1) / (R)Jd, ip01 = R(1) / p01;
+    sg[o2] = (R)Jd * ip01;
+    is[o0] = sg[o1] * ip01;
+    is[o1] = sg[o0] * ip01;
+    is[o2] = p01 * iJ;
+  }
   const R m = mu - lam * (R)lnJd;  // mu - lambda ln J
-  // scaling block
+  // scaling block A = diag(mu + m / s_i^2) + lambda s s^T with s_i = 1 / sigma_i: PSD as it
+  // stands when the diagonal part is (lambda >= 0), which holds unless the volume grows by ~25 %
+  // or more
   R A[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      A[i][j] = (i == j) ? mu + (m + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
+    for (int j = 0; j < 3; ++j) A[i][j] = (i == j) ? mu + (m + lam) * (is[i] * is[i]) : lam * (is[i] * is[j]);
   R Ap[3][3];
-  // A = diag(mu + m / s_i^2) + lambda s s^T with s_i = 1 / sigma_i: PSD as it stands when the
-  // diagonal part is (lambda >= 0), which holds unless the volume grows by ~25 % or more
-  const bool psd = (mu + m / (sg[0] * sg[0]) >= R(0)) && (mu + m / (sg[1] * sg[1]) >= R(0)) &&
-                   (mu + m / (sg[2] * sg[2]) >= R(0)) && lam >= R(0);
+  const bool psd = (mu + m * (is[0] * is[0]) >= R(0)) && (mu + m * (is[1] * is[1]) >= R(0)) &&
+                   (mu + m * (is[2] * is[2]) >= R(0)) && lam >= R(0);
   if (project && !psd) {
     R w[3], Q[3][3];
-    R Ac[3][3];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) Ac[i][j] = A[i][j];
     if constexpr (sizeof(R) == 8)
-      eig3_refined(Ac, w, Q);
+      eig3_refined(A, w, Q);
     else
-      jacobi3<R>(Ac, w, Q);
-    for (int i = 0; i < 3; ++i) w[i] = fmax(w[i], R(0));
+      jacobi3<R>(A, w, Q);
+    for (int i = 0; i < 3; ++i) w[i] = fmax(w[i], R(0)) * vol;
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) Ap[i][j] = Q[i][0] * w[0] * Q[j][0] + Q[i][1] * w[1] * Q[j][1] + Q[i][2] * w[2] * Q[j][2];
+      for (int j = i; j < 3; ++j)
+        Ap[i][j] = Ap[j][i] = Q[i][0] * w[0] * Q[j][0] + Q[i][1] * w[1] * Q[j][1] + Q[i][2] * w[2] * Q[j][2];
   } else {
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) Ap[i][j] = A[i][j];
+      for (int j = 0; j < 3; ++j) Ap[i][j] = A[i][j] * vol;
   }
-  // pair blocks: pq[i][j] (i != j): diagonal p and off-diagonal q of the 2x2 block
+  // pair blocks: diagonal p and off-diagonal q of the 2x2 block of every pair i != j (symmetric
+  // in i, j), scaled by the volume
   R P2[3][3], Q2[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      if (i == j) { P2[i][j] = Q2[i][j] = R(0); continue; }
-      R k = m / (sg[i] * sg[j]);
+    for (int j = i + 1; j < 3; ++j) {
+      const R k = m * (is[i] * is[j]);
       R lt = mu - k, lf = mu + k;  // twist (antisymmetric), flip (symmetric)
       if (project) { lt = fmax(lt, R(0)); lf = fmax(lf, R(0)); }
-      P2[i][j] = R(0.5) * (lf + lt);
-      Q2[i][j] = R(0.5) * (lf - lt);
+      P2[i][j] = P2[j][i] = R(0.5) * vol * (lf + lt);
+      Q2[i][j] = Q2[j][i] = R(0.5) * vol * (lf - lt);
     }
-  // Dhat_a = V^T D_a
+  // Dhat_a = V^T D_a (a = 1..3)
   R Dh[4][3];
-  for (int a = 0; a < 4; ++a)
+  for (int a = 1; a < 4; ++a)
     for (int i = 0; i < 3; ++i) Dh[a][i] = V[0][i] * D[a][0] + V[1][i] * D[a][1] + V[2][i] * D[a][2];
-  for (int a = 0; a < 4; ++a)
-    for (int b = a; b < 4; ++b) {
-      R Hh[3][3];
+  // blocks of vertices 1..3, accumulating minus the column sums into the vertex-0 blocks
+  R H0[3][3][3];  // H0[b-1] = H_0b
+  for (int b = 0; b < 3; ++b)
+    for (int i = 0; i < 3; ++i)
+      for (int l = 0; l < 3; ++l) H0[b][i][l] = R(0);
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    {
+      R H[3][3];
+      nh_vertex_block<R, true>(U, Ap, P2, Q2, Dh[a], Dh[a], H);
+      nh_store_block<OutT, BS>(out + ublk(a, a) * BS, H);
+      for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l) H0[a - 1][i][l] -= H[i][l];
+    }
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b) {
+      R H[3][3];
+      nh_vertex_block<R, false>(U, Ap, P2, Q2, Dh[a], Dh[b], H);
+      nh_store_block<OutT, BS>(out + ublk(a, b) * BS, H);
       for (int i = 0; i < 3; ++i)
         for (int l = 0; l < 3; ++l) {
-          if (i == l) {
-            R s = Dh[a][i] * Dh[b][i] * Ap[i][i];
-            for (int j = 0; j < 3; ++j)
-              if (j != i) s += Dh[a][j] * Dh[b][j] * P2[i][j];
-            Hh[i][i] = s;
-          } else {
-            Hh[i][l] = Dh[a][i] * Dh[b][l] * Ap[i][l] + Dh[a][l] * Dh[b][i] * Q2[i][l];
-          }
+          H0[b - 1][i][l] -= H[i][l];  // H_ab contributes to H_0b
+          H0[a - 1][i][l] -= H[l][i];  // H_ba = H_ab^T contributes to H_0a
         }
-      // U Hh U^T
-      R T[3][3];
-      for (int i = 0; i < 3; ++i)
-        for (int l = 0; l < 3; ++l) T[i][l] = Hh[i][0] * U[l][0] + Hh[i][1] * U[l][1] + Hh[i][2] * U[l][2];
-      OutT* o = out + ublk(a, b) * BS;
-      for (int i = 0; i < 3; ++i)
-        for (int l = 0; l < 3; ++l)
-          o[3 * i + l] = (OutT)(vol * (U[i][0] * T[0][l] + U[i][1] * T[1][l] + U[i][2] * T[2][l]));
     }
+  }
+  R H00[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int l = 0; l < 3; ++l) H00[i][l] = -(H0[0][i][l] + H0[1][i][l] + H0[2][i][l]);
+  for (int i = 0; i < 3; ++i)
+    for (int l = i + 1; l < 3; ++l) H00[l][i] = H00[i][l] = R(0.5) * (H00[i][l] + H00[l][i]);
+  nh_store_block<OutT, BS>(out + ublk(0, 0) * BS, H00);
+  for (int b = 1; b < 4; ++b) nh_store_block<OutT, BS>(out + ublk(0, b) * BS, H0[b - 1]);
 }
 
 // Gradient of V Psi (12) and energy; returns false if J <= 0
@@ -320,12 +387,13 @@ __device__ __forceinline__ bool nh_grad(const double F[3][3], const double Hd[3]
   cof[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
   cof[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
   cof[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
-  const double k = (lam * lnJ - mu) / J;
-  double P[3][3];
+  const double k = vol * (lam * lnJ - mu) / J, vmu = vol * mu;
+  double P[3][3];  // V dPsi/dF
   for (int i = 0; i < 3; ++i)
-    for (int l = 0; l < 3; ++l) P[i][l] = mu * F[i][l] + k * cof[i][l];
-  for (int a = 0; a < 4; ++a)
-    for (int i = 0; i < 3; ++i) g[3 * a + i] = vol * (P[i][0] * D[a][0] + P[i][1] * D[a][1] + P[i][2] * D[a][2]);
+    for (int l = 0; l < 3; ++l) P[i][l] = vmu * F[i][l] + k * cof[i][l];
+  for (int a = 1; a < 4; ++a)
+    for (int i = 0; i < 3; ++i) g[3 * a + i] = P[i][0] * D[a][0] + P[i][1] * D[a][1] + P[i][2] * D[a][2];
+  for (int i = 0; i < 3; ++i) g[i] = -(g[3 + i] + g[6 + i] + g[9 + i]);  // D_0 = -(D_1 + D_2 + D_3)
   if (e) *e = vol * psi_disp(Hd, mu, lam);
   *Jo = J;
   *lnJo = lnJ;

@@ -191,11 +191,11 @@ __device__ __forceinline__ void ctl_collect(const Dev& d, const PcgCta& c, int k
 // group totals and takes the per-gel decisions while the slice warps run the SpMV, so neither is
 // on the critical path; run flags are double-buffered (the slice warps read this iteration's,
 // the control warp writes the next one's).
-__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
+__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase, PcgPlan plan, int maxit,
                                                              int wmax) {
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[2][PCG_MAXG];
   __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
     res_prefetch(d, c, 3, 4, 0, pf);
     res_finish(c, 3, 4, pf, tot);
   }
-  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) bbj[q] = tot[q][3];
+  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
+    bbj[q] = tot[q][3];
+    thj[q] = d.gv[c.g0 + q].eta2 * bbj[q];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+  }
   // ---- w = A u, m = M^-1 w; dot products of iteration 0
   if (has) {
     double ga = 0.0, de = 0.0, rr = 0.0;
@@ -280,10 +283,11 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
         run[par ^ 1][q] = 0;
         if (!run[par][q]) continue;
         const double ga = tot[q][0], de = tot[q][1], rr = tot[q][2];
-        if (!(rr > eta2 * bbj[q]) || i >= maxit) {
+        if (!(rr > thj[q]) || i >= maxit) {
           if (blockIdx.x == c.c0) {
             d.gv[c.g0 + q].pcg_it = i;
             d.gv[c.g0 + q].bb = bbj[q];
+            d.gv[c.g0 + q].res2 = bbj[q] > 0.0 ? rr / bbj[q] : 0.0;
             d.gv[c.g0 + q].pcg_done = 1;
           }
           continue;
@@ -341,11 +345,11 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
-__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int phase, PcgPlan plan, double eta2,
+__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int phase, PcgPlan plan,
                                                                  int maxit, int refine_max, int wmax) {
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG];
   __shared__ float alj[PCG_MAXG], bej[PCG_MAXG], gprf[PCG_MAXG], aprf[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[2][PCG_MAXG], itj[PCG_MAXG];
   __shared__ int s_fail, s_any;
@@ -393,7 +397,10 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
     res_prefetch(d, c, 2, 4, 0, pf);
     res_finish(c, 2, 4, pf, tot);
   }
-  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) bbj[q] = tot[q][3];
+  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
+    bbj[q] = tot[q][3];
+    thj[q] = d.gv[c.g0 + q].eta2 * bbj[q];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+  }
   __syncthreads();
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) s_any = 0;
@@ -402,9 +409,10 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       inner[0][q] = 0;
       if (!run[q]) continue;
       const double rr = tot[q][2], bb = bbj[q];
-      if (!(rr > eta2 * bb) || round >= refine_max) {
+      if (!(rr > thj[q]) || round >= refine_max) {
         run[q] = 0;
         if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + q].res2 = bb > 0.0 ? rr / bb : 0.0;
           d.gv[c.g0 + q].pcg_done = 1;
           d.gv[c.g0 + q].rounds = round;
           d.gv[c.g0 + q].bb = bb;
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       }
       s_any = 1;
       inner[0][q] = 1;
-      tolj[q] = fmax(eta2 * bb / rr, 1e-11);
+      tolj[q] = fmax(thj[q] / rr, 1e-11);
     }
     __syncthreads();
     if (!s_any) break;
@@ -581,20 +589,18 @@ int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax) {
   return n;
 }
 
-cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, double eta,
-                           int maxit, int refine_max, int wmax, cudaStream_t st) {
-  double eta2 = eta * eta;
+cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, int maxit,
+                           int refine_max, int wmax, cudaStream_t st) {
   Dev dd = d;
   PcgPlan pp = plan;
   const size_t smem = pcg_res_smem(mixed, plan.max_slices, wmax);
   count_launch(1);
   if (mixed) {
-    void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&refine_max,
-                    (void*)&wmax};
+    void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&refine_max, (void*)&wmax};
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed_res, dim3(nctas), dim3(32 * (plan.max_slices + 1)), args,
                                        smem, st);
   }
-  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&wmax};
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&wmax};
   return cudaLaunchCooperativeKernel((const void*)k_pcg64_res, dim3(nctas), dim3(32 * (plan.max_slices + 1)), args, smem,
                                      st);
 }

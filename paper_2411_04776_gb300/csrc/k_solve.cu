@@ -223,10 +223,10 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
 // One projected-Newton direction per gel of the gels in `phase`: block-Jacobi preconditioned CG
 // on H p = -g (Chronopoulos-Gear: one reduction phase per iteration), FP64, stops per gel when
 // |r| <= eta |g| or after maxit iterations.
-__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, double eta2, int maxit) {
+__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, int maxit) {
   extern __shared__ double dsm[];  // [slices of this CTA][4]
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
   __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -256,7 +256,10 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     if (lane == 0) dsm[(s - c.s0) * 4 + 3] = bb;
   }
   if (!group_sum(d, c, dsm, 3, 4, tot, &s_fail)) return;
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) bbj[j] = tot[j][3];
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    bbj[j] = tot[j][3];
+    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+  }
   if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;  // u complete before the SpMV
   for (int k = 1;; ++k) {
     // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
@@ -288,11 +291,12 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
       if (!run[j]) continue;
       const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
-      if (!(rr > eta2 * bbj[j]) || k > maxit) {
+      if (!(rr > thj[j]) || k > maxit) {
         run[j] = 0;
         if (blockIdx.x == c.c0) {
           d.gv[c.g0 + j].pcg_it = k - 1;
           d.gv[c.g0 + j].bb = bbj[j];
+          d.gv[c.g0 + j].res2 = bbj[j] > 0.0 ? rr / bbj[j] : 0.0;
           d.gv[c.g0 + j].pcg_done = 1;
         }
         continue;
@@ -330,12 +334,10 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
-cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta,
-                         int maxit, cudaStream_t st) {
-  double eta2 = eta * eta;
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st) {
   Dev dd = d;
   PcgPlan pp = plan;
-  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit};
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit};
   count_launch(1);
   const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
   return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, smem, st);
@@ -394,11 +396,11 @@ __device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lan
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
-__global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPlan plan, double eta2, int maxit,
+__global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPlan plan, int maxit,
                                                      int refine_max) {
   extern __shared__ double dsm[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
   __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
   __shared__ int s_fail, s_any;
@@ -429,7 +431,10 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
     }
   }
   if (!group_sum(d, c, dsm, 2, 4, tot, &s_fail)) return;
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) bbj[j] = tot[j][3];
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    bbj[j] = tot[j][3];
+    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+  }
   __syncthreads();
   for (int round = 0;; ++round) {
     // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
@@ -439,9 +444,10 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       inner[j] = 0;
       if (!run[j]) continue;
       const double rr = tot[j][2], bb = bbj[j];
-      if (!(rr > eta2 * bb) || round >= refine_max) {
+      if (!(rr > thj[j]) || round >= refine_max) {
         run[j] = 0;
         if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + j].res2 = bb > 0.0 ? rr / bb : 0.0;
           d.gv[c.g0 + j].pcg_done = 1;
           d.gv[c.g0 + j].rounds = round;
           d.gv[c.g0 + j].bb = bb;
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       s_any = 1;
       inner[j] = 1;
       // inner target: reach eta |b| in one round if FP32 allows, else the FP32 floor
-      tolj[j] = fmax(eta2 * bb / rr, 1e-11);
+      tolj[j] = fmax(thj[j] / rr, 1e-11);
     }
     __syncthreads();
     if (!s_any) break;
@@ -563,12 +569,11 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
-cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
-                             int refine_max, cudaStream_t st) {
-  double eta2 = eta * eta;
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
+                             cudaStream_t st) {
   Dev dd = d;
   PcgPlan pp = plan;
-  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&eta2, (void*)&maxit, (void*)&refine_max};
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&refine_max};
   count_launch(1);
   const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed, dim3(nctas), dim3(PCG_T), args, smem, st);
@@ -718,9 +723,21 @@ __global__ void k_restore(Dev d, int phase) {
   d.x[r] = d.xn[r];
 }
 
+constexpr double NEAR_FACTOR = 2.0;
+
 // per gel bookkeeping: op 0 = reset the assembly / PCG accumulators; 1 = after the PCG:
-// converged = ||p||_inf < tol, prepare the ACCD minimum; 2 = after the ACCD: alpha0 = min(1,
-// toi), start the line search; 3 = reset the per-step feasibility state
+// converged = ||p||_inf < tol on a direction solved to the near forcing term, next forcing term,
+// prepare the ACCD minimum; 2 = after the ACCD: alpha0 = min(1, toi), start the line search;
+// 3 = reset the per-step feasibility state and start with the far forcing term.
+//
+// Forcing terms (inexact Newton): the projected Newton iteration converges linearly (the PSD
+// projection drops curvature), so solving the linear system much more accurately than the
+// contraction of the Newton steps buys nothing while ||p|| is large.  The next solve runs to
+// eta_near when the next ||p||_inf, predicted from the last one and the last contraction
+// ratio, falls below NEAR_FACTOR tol (the direction that may end the solve), to eta_far
+// otherwise.  Convergence is only declared on a direction whose solve reached eta_near (a zero
+// right-hand side counts), so the stopping test sees the same direction quality as with a
+// fixed eta_near; a far solve that lands below tol costs one more iteration.
 __global__ void k_gel_op(Dev d, int phase, int op) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.n_gels) return;
@@ -736,7 +753,13 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
     v.rounds = 0;
     v.flags &= ~(4 | 16);
   } else if (op == 1) {
-    v.converged = bitsd(v.pnorm_bits) < d.gc[g].tol_p ? 1 : 0;
+    const GelCtl& c = d.gc[g];
+    const double pn = bitsd(v.pnorm_bits);
+    const bool near = v.eta2 <= c.eta2_near || v.res2 <= c.eta2_near;  // solved to eta_near (or capped there)
+    v.converged = (pn < c.tol_p && near) ? 1 : 0;
+    const double rho = v.pn_prev > 0.0 ? fmin(pn / v.pn_prev, 1.0) : 1.0;
+    v.eta2 = pn * rho < NEAR_FACTOR * c.tol_p ? c.eta2_near : c.eta2_far;
+    v.pn_prev = pn;
     v.toi_bits = dbits(1.0);
     v.flags &= ~8;
   } else if (op == 2) {
@@ -750,6 +773,8 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
       v.ls_state = 0;
     }
   } else if (op == 3) {
+    v.eta2 = d.gc[g].eta2_far;
+    v.pn_prev = 0.0;
     v.toi_bits = dbits(1.0);
     v.dmin_bits = dbits(CUDART_INF);
     v.flags = 0;

@@ -61,6 +61,7 @@ struct GelCtl {  // per gel, written by the host before the launches of an itera
   int pad_;
   double h;                  // current (sub)step length
   double tol_p;              // ||p||_inf tolerance = newton_tol * bbox_diag * h
+  double eta2_near, eta2_far;  // squared PCG forcing terms near convergence / far from it
   double grav[3];
   double R[9], t[3];         // indenter pose at the end of the (sub)step
   double Rp[9], tp[3];       // indenter pose at its start
@@ -71,6 +72,9 @@ struct GelVar {  // per gel, written by the device
   double alpha, alpha0;
   double bb;                 // |b|^2 of the PCG right-hand side
   double gtp;                // g . p of the last Newton direction
+  double eta2;               // squared forcing term of the next PCG solve
+  double res2;               // |r|^2 / |b|^2 reached by the last PCG solve
+  double pn_prev;            // ||p||_inf of the previous direction (0: none yet)
   double fc[3];              // contact force on the gel
   unsigned long long toi_bits;    // min ACCD time of impact (non-negative double bits)
   unsigned long long pnorm_bits;  // ||p||_inf of the last Newton direction

@@ -50,15 +50,14 @@ void launch_eval_accd(int n, const int* kind, const double* P, const double* dP,
 void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
 void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st);
 void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st);
-cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
-                         cudaStream_t st);
-cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, double eta, int maxit,
-                             int refine_max, cudaStream_t st);
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st);
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
+                             cudaStream_t st);
 int pcg_max_ctas_per_sm(int max_slices);
 size_t pair_record_doubles();
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
-cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, double eta,
-                           int maxit, int refine_max, int wmax, cudaStream_t st);
+cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, int maxit,
+                           int refine_max, int wmax, cudaStream_t st);
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
                    double* part_e, int mode, cudaStream_t st);
 void launch_rows(int which, const Dev& d, int phase, cudaStream_t st);
@@ -173,7 +172,7 @@ tx_status check_desc(const tx_gel_desc* d) {
     return TX_ERR_ARG;
   if (!(d->young > 0) || !(d->poisson > -1.0 && d->poisson < 0.5) || !(d->density > 0)) return TX_ERR_ARG;
   const tx_params& p = d->params;
-  if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || p.newton_max_iter < 1 ||
+  if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
       p.pcg_cta_slices < -1)
     return TX_ERR_ARG;
@@ -453,7 +452,6 @@ struct tx_batch {
     long long plan_version = -1;
     int nctas = 0;
     bool res = false, prof = false, tune = false;
-    double eta = 0.0;
     int pcg_max = 0, refine = 0, accd_max = 0;
     long long launches = 0;
     long long phase_launches[PR_N] = {};
@@ -1080,6 +1078,9 @@ void fill_ctl(tx_batch* b, int g, int phase, const Task& t) {
   c.phase = phase;
   c.h = t.dt;
   c.tol_p = m.prm.newton_tol * m.bbox * t.dt;
+  const double far = std::max(m.prm.pcg_rel_tol_far, m.prm.pcg_rel_tol);
+  c.eta2_near = m.prm.pcg_rel_tol * m.prm.pcg_rel_tol;
+  c.eta2_far = far * far;
   for (int k = 0; k < 3; ++k) c.grav[k] = m.prm.gravity[k];
   quat_R(t.pb, c.R);
   quat_R(t.pa, c.Rp);
@@ -1516,7 +1517,7 @@ void tune_event(tx_batch* b, cudaEvent_t& e) {
 }
 
 // Launches of one Newton iteration for the gels in PH_NEWTON, up to the first line-search trial.
-tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int accd_max) {
+tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
   Dev& d = b->d;
   cudaStream_t st = b->st;
   launch_gel_op(d, PH_NEWTON, 0, st);
@@ -1539,14 +1540,14 @@ tx_status newton_launches(tx_batch* b, double eta, int pcg_max, int refine, int 
     CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * P.plan.ngroups, st));
     if (b->mixed) {
       if (P.res)
-        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, true, eta, pcg_max, refine, b->pcg_wmax, st));
+        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, true, pcg_max, refine, b->pcg_wmax, st));
       else
-        CK(launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, eta, pcg_max, refine, st));
+        CK(launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, pcg_max, refine, st));
     } else {
       if (P.res)
-        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, eta, pcg_max, 0, b->pcg_wmax, st));
+        CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, pcg_max, 0, b->pcg_wmax, st));
       else
-        CK(launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, eta, pcg_max, st));
+        CK(launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, pcg_max, st));
     }
   }
   prof_close(b, b->nparts);
@@ -1572,7 +1573,7 @@ void drop_newton_graph(tx_batch* b) {
 // gels (and whenever anything its kernels were captured with changes: the PCG partition, device
 // buffers, solver parameters, profiling), then replayed with one launch.  Falls back to plain
 // launches for good if capture is refused (TXG_NO_GRAPHS=1 also disables it).
-tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double eta, int pcg_max, int refine,
+tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, int pcg_max, int refine,
                               int accd_max) {
   if (b->graphs < 0) {
     const char* e = std::getenv("TXG_NO_GRAPHS");
@@ -1585,11 +1586,11 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
       b->graphs = 0;
     }
   }
-  if (b->graphs == 0) return newton_launches(b, eta, pcg_max, refine, accd_max);
+  if (b->graphs == 0) return newton_launches(b, pcg_max, refine, accd_max);
   auto& G = b->graph;
   const bool same = G.exec && G.key == set && G.nctas == b->nctas && !G.tune &&
                     b->tune_key < 0 &&
-                    G.prof == b->prof.on && G.eta == eta && G.pcg_max == pcg_max && G.refine == refine &&
+                    G.prof == b->prof.on && G.pcg_max == pcg_max && G.refine == refine &&
                     G.accd_max == accd_max && std::memcmp(&G.dev, &b->d, sizeof(Dev)) == 0 &&
                     G.plan_version == b->plan_version;
   if (!same) {
@@ -1605,7 +1606,7 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
     std::string why;
     if (ok) {
       b->capturing = true;
-      const tx_status s = newton_launches(b, eta, pcg_max, refine, accd_max);
+      const tx_status s = newton_launches(b, pcg_max, refine, accd_max);
       b->capturing = false;
       if (s != TX_OK) why = g_err;
       const cudaError_t e = cudaStreamEndCapture(b->gst, &graph);
@@ -1641,7 +1642,7 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
         b->prof.pool.push_back(p.b);
       }
       b->graphs = 0;
-      return newton_launches(b, eta, pcg_max, refine, accd_max);
+      return newton_launches(b, pcg_max, refine, accd_max);
     }
     for (auto& p : pairs) p.graph = true;
     G.prof_pairs = pairs;
@@ -1651,7 +1652,6 @@ tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, double e
     G.nctas = b->nctas;
     G.prof = b->prof.on;
     G.tune = b->tune_key >= 0;
-    G.eta = eta;
     G.pcg_max = pcg_max;
     G.refine = refine;
     G.accd_max = accd_max;
@@ -1680,18 +1680,14 @@ tx_status do_newton(tx_batch* b) {
   cudaStream_t st = b->st;
   tx_status s = upload_ctl(b);
   if (s != TX_OK) return s;
-  double eta = 1e-3;
   int pcg_max = 1;
-  for (int g : set) {
-    eta = std::min(eta, b->mesh[g].prm.pcg_rel_tol);
-    pcg_max = std::max(pcg_max, b->mesh[g].prm.pcg_max_iter);
-  }
+  for (int g : set) pcg_max = std::max(pcg_max, b->mesh[g].prm.pcg_max_iter);
   int refine = 1;
   for (int g : set) refine = std::max(refine, b->mesh[g].prm.refine_max);
   s = prepare_pcg_plan(b, set);
   if (s != TX_OK) return s;
   const int accd_max = newton_accd_max(b);
-  s = run_newton_launches(b, set, eta, pcg_max, refine, accd_max);
+  s = run_newton_launches(b, set, pcg_max, refine, accd_max);
   if (s != TX_OK) return s;
   s = post_pcg_finish(b);
   if (s != TX_OK) return s;
@@ -1918,6 +1914,7 @@ void tx_params_default(tx_params* p) {
   p->kappa = 0.0;
   p->newton_tol = 1e-5;
   p->pcg_rel_tol = 1e-3;
+  p->pcg_rel_tol_far = 0.1;
   p->newton_max_iter = 200;
   p->pcg_max_iter = 2000;
   p->ls_max_halvings = 60;

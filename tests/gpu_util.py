@@ -4,6 +4,16 @@ import numpy as np
 # parity gate on positions: 1e-6 of the 4 mm gel thickness
 POS_TOL = 4e-9
 
+# Newton tolerance of the parity runs.  The projected Newton iteration converges linearly (rate
+# about 1/2), so a run stopped at ||p||_inf / h < tol * bbox sits about that far from the
+# minimiser.  At 1e-7 the oracle's own positions move by up to 2.3 nm when the tolerance is
+# tightened to 1e-9 (coarse Hertz block), inside the 4 nm gate; tighter tolerances run into the
+# FP64 resolution of the energy on the 10x13x4 gel (the line search stalls).
+PARITY_NEWTON_TOL = 1e-7
+# The contact force is far more sensitive: at 1e-7 the oracle's own force moves by up to 7e-4
+# (relative) under the same tightening, at 1e-8 by 2e-6, so force parity at 1e-4 runs at 1e-8.
+FORCE_PARITY_NEWTON_TOL = 1e-8
+
 
 def smooth_state(wl, seed, amp=2e-5):
     """Seeded smooth displacement of the free vertices (no inversion), predictor and h."""

@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 from oracle import oracle as O  # noqa: E402
 from paper_2411_04776_gb300 import binding as B  # noqa: E402
 from paper_2411_04776_gb300 import workloads as W  # noqa: E402
-from tests.gpu_util import POS_TOL, smooth_state  # noqa: E402
+from tests.gpu_util import PARITY_NEWTON_TOL, POS_TOL, smooth_state  # noqa: E402
 
 
 def contact_pose(wl, depth):
@@ -53,7 +53,7 @@ def test_rest_state_is_a_fixed_point():
     assert st.newton_iters == 0 and np.array_equal(x, wl.gel.verts) and np.all(v == 0)
 
 
-def run_pair(wl, steps, tol=1e-7):
+def run_pair(wl, steps, tol=PARITY_NEWTON_TOL):
     gel = B.Gel.from_workload(wl, newton_tol=tol)
     ref = O.OracleGel.from_workload(wl, newton_tol=tol)
     errs = []
@@ -93,8 +93,8 @@ def test_mixed_precision_trajectory_matches_oracle():
     """FP32 Hessian blocks + FP32 Krylov solve with FP64 residual refinement; the gradient,
     barrier, CCD and energy stay FP64, so the converged minimiser is the FP64 one."""
     wl = W.small_gel_sphere(0)
-    gel = B.Gel.from_workload(wl, newton_tol=1e-7, precision=B.TX_PREC_MIXED)
-    ref = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    gel = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, precision=B.TX_PREC_MIXED)
+    ref = O.OracleGel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL)
     errs = []
     for s in range(30):
         st = gel.step(wl.poses[s], wl.dt)
@@ -108,9 +108,9 @@ def test_mixed_precision_trajectory_matches_oracle():
 
 def test_batch_equals_alone():
     wls = [W.small_gel_sphere(s) for s in range(3)]
-    descs = [B.GelDesc.from_workload(w, newton_tol=1e-7) for w in wls]
+    descs = [B.GelDesc.from_workload(w, newton_tol=PARITY_NEWTON_TOL) for w in wls]
     b = B.tx_batch_create(descs)
-    alone = [B.Gel.from_workload(w, newton_tol=1e-7) for w in wls]
+    alone = [B.Gel.from_workload(w, newton_tol=PARITY_NEWTON_TOL) for w in wls]
     try:
         for s in range(8):
             poses = np.stack([w.poses[s] for w in wls])

@@ -11,6 +11,7 @@ pytestmark = pytest.mark.gpu
 from oracle import oracle as O  # noqa: E402
 from paper_2411_04776_gb300 import binding as B  # noqa: E402
 from paper_2411_04776_gb300 import workloads as W  # noqa: E402
+from tests.gpu_util import FORCE_PARITY_NEWTON_TOL, PARITY_NEWTON_TOL  # noqa: E402
 
 HALF = 8e-3
 RADIUS = 3e-3
@@ -28,10 +29,10 @@ def centre(X):
     return int(c[0])
 
 
-def run_gpu(h0, ratio):
+def run_gpu(h0, ratio, tol=PARITY_NEWTON_TOL):
     wl = W.hertz_block(h0=h0, ratio=ratio, half=HALF, thick=HALF, dhat=15e-6, step=12e-6)
     c = centre(wl.gel.verts)
-    g = B.Gel(B.GelDesc.from_workload(wl, newton_tol=1e-7), stream=torch.cuda.current_stream())
+    g = B.Gel(B.GelDesc.from_workload(wl, newton_tol=tol), stream=torch.cuda.current_stream())
     out = []
     for p in wl.poses:
         assert g.step(p, wl.dt) == 0
@@ -52,8 +53,8 @@ def test_hertz_force_converges_under_refinement():
 
 
 def test_hertz_coarse_matches_oracle():
-    wl, r = run_gpu(80e-6, 1.5)
-    og = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    wl, r = run_gpu(80e-6, 1.5, FORCE_PARITY_NEWTON_TOL)
+    og = O.OracleGel.from_workload(wl, newton_tol=FORCE_PARITY_NEWTON_TOL)
     c = centre(wl.gel.verts)
     for s, p in enumerate(wl.poses):
         assert og.step(p, wl.dt)["status"] == 0
