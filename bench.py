@@ -261,7 +261,7 @@ def roofline(prof, clocks, precision, kernel):
     if os.path.exists(tpath):
         try:
             t = json.load(open(tpath)).get(kernel)
-            if t and t.get("source_hash") == source_hash():
+            if t and t.get("source_hash") == source_hash(t["files"]):
                 traffic = t["bytes_per_launch"]
         except (ValueError, KeyError):
             traffic = None
@@ -289,13 +289,15 @@ def pcg_kernel_name(precision, n_gels):
     return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
 
 
-def source_hash():
+def source_hash(files):
+    """Hash of the CUDA sources a kernel is built from (the ncu counters in profiles/traffic.json
+    are used only while these are unchanged)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2411_04776_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in sorted(files):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
