@@ -1,25 +1,77 @@
-// Barrier derivatives of one contact pair on the 32 lanes of a warp, and the PSD projection of
-// its Hessian block by a warp-parallel Jacobi eigen-solve.
+// Barrier derivatives of one contact pair on the threads of a team (a warp or a CTA), and the
+// PSD projection of its Hessian block by a team-parallel Jacobi eigen-solve.  The contact
+// kernels use a warp per pair; the code also runs on a whole CTA (every thread calls it).
 //
 // The squared distance D of every closest-feature form is a function of nd <= 3 difference
 // vectors v_a = P[pl_a] - P[mi_a] (see dev_contact.cuh).  Its gradient over the v_a is cheap and
 // is formed once per pair (struct DV); every entry of its Hessian over the v_a has a closed form
 // (cross norm c(x, y) = |x|^2 |y|^2 - (x.y)^2, triple product s = w.(e1 x e2), quotient rule), so
-// the lanes of a warp compute the entries of the point-space block they own independently:
+// the threads of a team compute the entries of the point-space block they own independently:
 //   d2D/dP_I dP_J = sum_{a,b} sigma(I, a) sigma(J, b) d2D/dv_a dv_b,  sigma = +1 (plus point),
 //   -1 (minus point), 0.
 // The barrier on D and the IPC edge-edge mollifier are then applied entry by entry.
 //
 // Projection (Li et al. 2020: per-pair Hessians are projected to PSD before assembly).  Cyclic
 // Jacobi with the round-robin ("parallel") ordering of Brent & Luk: each round applies m/2
-// disjoint rotations at once; lane k owns the 2x2 block (pair a, pair b) of the matrix it
-// transforms, so no two lanes write the same entry.  GB300 issues FP64 at 1/64 of the FP32
+// disjoint rotations at once; thread k owns the 2x2 block (pair a, pair b) of the matrix it
+// transforms, so no two threads write the same entry.  GB300 issues FP64 at 1/64 of the FP32
 // rate, so the eigenbasis is found in FP32 first; FP64 then re-orthonormalises it and refines
 // only what FP32 could not resolve; the clamp X max(lam, 0) X^T is assembled in FP64.
 #pragma once
 #include "dev_contact.cuh"
 
 namespace txg {
+
+// The threads that work on one pair: a warp (NT = 32) or a whole CTA (NT = 64, 128, ...; every
+// thread of the CTA calls the team functions).  id is the thread's index in the team; red is
+// NT / 32 doubles of shared scratch for the CTA-wide reductions (unused by a warp).
+template <int NT>
+struct Team {
+  int id;
+  double* red;
+  __device__ __forceinline__ void sync() const {
+    if constexpr (NT == 32)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
+  __device__ __forceinline__ bool any(bool p) const {
+    if constexpr (NT == 32)
+      return __any_sync(0xffffffffu, p);
+    else
+      return __syncthreads_or(p) != 0;
+  }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v) const {
+    v = warp_sum(v);
+    if constexpr (NT == 32) {
+      return v;
+    } else {
+      __syncthreads();  // the previous reduction's readers are done with red
+      if ((id & 31) == 0) red[id >> 5] = (double)v;
+      __syncthreads();
+      T t = T(0);
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) t += (T)red[w];
+      return t;
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ T max(T v) const {
+    v = warp_max(v);
+    if constexpr (NT == 32) {
+      return v;
+    } else {
+      __syncthreads();
+      if ((id & 31) == 0) red[id >> 5] = (double)v;
+      __syncthreads();
+      T t = (T)red[0];
+#pragma unroll
+      for (int w = 1; w < NT / 32; ++w) t = t > (T)red[w] ? t : (T)red[w];
+      return t;
+    }
+  }
+};
 
 // closest-feature data of a pair in difference-vector space
 struct DV {
@@ -261,20 +313,21 @@ __device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, 
 }
 
 // The block of the barrier Hessian on the point dofs fd[0, nf) into H (row stride m, rows and
-// columns nf..m-1 zero), by the lanes of a warp: the difference-vector Hessian of D is formed
+// columns nf..m-1 zero), by the threads of a team: the difference-vector Hessian of D is formed
 // once (Hdv: (3 nd)^2 scratch), every point entry is then a signed sum of its entries.  Entries
 // (i, j) and (j, i) are computed in the same order, so H is exactly symmetric.
-__device__ __forceinline__ void warp_pair_block(const PairBarrier& pb, const int* fd, int nf, int m, double* Hdv,
-                                                double* H, int lane) {
+template <int NT>
+__device__ __forceinline__ void team_pair_block(const PairBarrier& pb, const int* fd, int nf, int m, double* Hdv,
+                                                double* H, const Team<NT>& tm) {
   const DV& o = pb.dv;
   const int n3 = 3 * o.nd;
-  for (int e = lane; e < n3 * n3; e += 32) {
+  for (int e = tm.id; e < n3 * n3; e += NT) {
     const int r = e / n3, c = e - r * n3;
     const int a = r < c ? r : c, b = r < c ? c : r;
     Hdv[e] = hD_dv(o, a / 3, a % 3, b / 3, b % 3);
   }
-  __syncwarp();
-  for (int e = lane; e < m * m; e += 32) {
+  tm.sync();
+  for (int e = tm.id; e < m * m; e += NT) {
     const int r = e / m, c = e - r * m;
     const int i = r < c ? r : c, j = r < c ? c : r;
     double v = 0.0;
@@ -296,10 +349,10 @@ __device__ __forceinline__ void warp_pair_block(const PairBarrier& pb, const int
     }
     H[e] = v;
   }
-  __syncwarp();
+  tm.sync();
 }
 
-// ---------------------------------------------------------------- warp-parallel Jacobi
+// ---------------------------------------------------------------- team-parallel Jacobi
 constexpr int PW_MAXN = 12;  // largest block: all four points of a pair
 
 template <typename T>
@@ -317,25 +370,26 @@ __device__ __forceinline__ double jsqrt(double v) { return sqrt(v); }
 // accumulating the rotations into V (A <- J^T A J, V <- V J).  Stops when the squared
 // off-diagonal norm is at most rel_tol times the squared diagonal norm.  Rotations whose
 // off-diagonal entry is below skip_rel (|a_pp| + |a_qq|) are skipped (exact identity).
-// Called by all 32 lanes of a warp.
-template <typename T>
-__device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip_rel, RotWS<T>& rw, int lane) {
+// Called by every thread of the team.
+template <typename T, int NT>
+__device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip_rel, RotWS<T>& rw,
+                            const Team<NT>& tm) {
   const int h = m >> 1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = 0, dg = 0;
-    for (int e = lane; e < m * m; e += 32) {
+    for (int e = tm.id; e < m * m; e += NT) {
       const int i = e / m, j = e - i * m;
       const T v = A[e];
       if (i == j) dg += v * v;
       else if (i < j) off += v * v;
     }
-    off = warp_sum(off);
-    dg = warp_sum(dg);
+    off = tm.sum(off);
+    dg = tm.sum(dg);
     if (!(off > rel_tol * dg)) break;
     for (int r = 0; r < m - 1; ++r) {
-      if (lane < h) {
+      if (tm.id < h) {
         // round-robin: position 0 fixed, positions 1..m-1 rotate by r
-        const int pa = lane == 0 ? 0 : lane + 1, pb = lane == 0 ? 1 : m - lane;
+        const int pa = tm.id == 0 ? 0 : tm.id + 1, pb = tm.id == 0 ? 1 : m - tm.id;
         int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
         int q = (pb - 1 + r) % (m - 1) + 1;
         if (p > q) {
@@ -351,14 +405,14 @@ __device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
           c = T(1) / jsqrt(t * t + T(1));
           s = t * c;
         }
-        rw.p[lane] = p;
-        rw.q[lane] = q;
-        rw.c[lane] = c;
-        rw.s[lane] = s;
-        rw.t[lane] = t;
+        rw.p[tm.id] = p;
+        rw.q[tm.id] = q;
+        rw.c[tm.id] = c;
+        rw.s[tm.id] = s;
+        rw.t[tm.id] = t;
       }
-      __syncwarp();
-      for (int blk = lane; blk < h * h; blk += 32) {
+      tm.sync();
+      for (int blk = tm.id; blk < h * h; blk += NT) {
         const int a = blk / h, b = blk - a * h;
         const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
         if (a == b) {
@@ -380,7 +434,7 @@ __device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
           A[qa * m + qb] = sb * y10 + cb * y11;
         }
       }
-      for (int task = lane; task < m * h; task += 32) {
+      for (int task = tm.id; task < m * h; task += NT) {
         const int k = task / h, a = task - k * h;
         const int p = rw.p[a], q = rw.q[a];
         const T c = rw.c[a], s = rw.s[a];
@@ -388,7 +442,7 @@ __device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
         V[k * m + p] = c * vp - s * vq;
         V[k * m + q] = s * vp + c * vq;
       }
-      __syncwarp();
+      tm.sync();
     }
   }
 }
@@ -398,16 +452,17 @@ __device__ void warp_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
 // (a_qq - a_pp) / (2 a_pq); the rotation itself (c = 1 / sqrt(1 + t^2), s = t c) and every update
 // are FP64, so each sweep multiplies the off-diagonal entries by ~1e-7 and keeps V orthonormal to
 // FP64 round-off.  Entries below tau (absolute) are left alone, and a round none of whose pairs
-// needs a rotation is skipped by the whole warp; a sweep without rotations ends the refinement.
-__device__ void warp_jacobi_refine(double* A, double* V, int m, int max_sweeps, double tau, RotWS<double>& rw,
-                                   int lane) {
+// needs a rotation is skipped by the whole team; a sweep without rotations ends the refinement.
+template <int NT>
+__device__ void team_jacobi_refine(double* A, double* V, int m, int max_sweeps, double tau, RotWS<double>& rw,
+                                   const Team<NT>& tm) {
   const int h = m >> 1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool rotated = false;
     for (int r = 0; r < m - 1; ++r) {
       bool rot = false;
-      if (lane < h) {
-        const int pa = lane == 0 ? 0 : lane + 1, pb = lane == 0 ? 1 : m - lane;
+      if (tm.id < h) {
+        const int pa = tm.id == 0 ? 0 : tm.id + 1, pb = tm.id == 0 ? 1 : m - tm.id;
         int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
         int q = (pb - 1 + r) % (m - 1) + 1;
         if (p > q) {
@@ -425,15 +480,15 @@ __device__ void warp_jacobi_refine(double* A, double* V, int m, int max_sweeps, 
           s = t * c;
           rot = true;
         }
-        rw.p[lane] = p;
-        rw.q[lane] = q;
-        rw.c[lane] = c;
-        rw.s[lane] = s;
+        rw.p[tm.id] = p;
+        rw.q[tm.id] = q;
+        rw.c[tm.id] = c;
+        rw.s[tm.id] = s;
       }
-      if (!__any_sync(0xffffffffu, rot)) continue;
+      if (!tm.any(rot)) continue;
       rotated = true;
-      __syncwarp();
-      for (int blk = lane; blk < h * h; blk += 32) {
+      tm.sync();
+      for (int blk = tm.id; blk < h * h; blk += NT) {
         const int a = blk / h, b = blk - a * h;
         const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
         const double ca = rw.c[a], sa = rw.s[a], cb = rw.c[b], sb = rw.s[b];
@@ -445,7 +500,7 @@ __device__ void warp_jacobi_refine(double* A, double* V, int m, int max_sweeps, 
         A[qa * m + pb] = cb * y10 - sb * y11;
         A[qa * m + qb] = sb * y10 + cb * y11;
       }
-      for (int task = lane; task < m * h; task += 32) {
+      for (int task = tm.id; task < m * h; task += NT) {
         const int k = task / h, a = task - k * h;
         const int p = rw.p[a], q = rw.q[a];
         const double c = rw.c[a], s = rw.s[a];
@@ -453,13 +508,13 @@ __device__ void warp_jacobi_refine(double* A, double* V, int m, int max_sweeps, 
         V[k * m + p] = c * vp - s * vq;
         V[k * m + q] = s * vp + c * vq;
       }
-      __syncwarp();
+      tm.sync();
     }
     if (!rotated) break;
   }
 }
 
-// per-warp workspace of the projection
+// per-team workspace of the projection
 struct ProjWS {
   double H[PW_MAXN * PW_MAXN];  // in: symmetric block (stride m); out: its PSD projection
   double X[PW_MAXN * PW_MAXN], T[PW_MAXN * PW_MAXN], B[PW_MAXN * PW_MAXN];
@@ -480,7 +535,7 @@ __device__ __forceinline__ void upper_ij(int t, int m, int& i, int& j) {
 }
 
 // PSD projection of w.H (n x n symmetric, stored with stride m = n rounded up to even, padding
-// rows / columns zero); all 32 lanes of the warp call it.
+// rows / columns zero); every thread of the team calls it.
 //   1. scale by a power of two (exact): max |A| in [1, 2);
 //   2. FP32 round-robin Jacobi: eigenvector estimate X (orthonormal to ~1e-7);
 //   3. one Newton-Schulz step X <- X (3 I - X^T X) / 2 in FP64 (orthonormal to ~1e-14);
@@ -488,60 +543,61 @@ __device__ __forceinline__ void upper_ij(int t, int m, int& i, int& j) {
 //      below 1e-13 max|A| -- the well-separated part needs one sweep, close or tiny eigenvalues
 //      (the barrier's Hessian spans many orders of magnitude) as many as they take;
 //   5. H = X max(diag B, 0) X^T (FP64), scaled back.
-__device__ void warp_psd_project(ProjWS& w, int n, int lane) {
+template <int NT>
+__device__ void team_psd_project(ProjWS& w, int n, const Team<NT>& tm) {
   const int m = n + (n & 1), mm = m * m, nu = m * (m + 1) / 2;
   double mx = 0.0;
-  for (int e = lane; e < mm; e += 32) mx = fmax(mx, fabs(w.H[e]));
-  mx = warp_max(mx);
+  for (int e = tm.id; e < mm; e += NT) mx = fmax(mx, fabs(w.H[e]));
+  mx = tm.max(mx);
   if (!(mx > 0.0)) return;  // zero block: already its own projection
   const int ex = ilogb(mx);
   const double sc = ldexp(1.0, -ex);
-  for (int e = lane; e < mm; e += 32) {
+  for (int e = tm.id; e < mm; e += NT) {
     const int i = e / m, j = e - i * m;
     const double v = w.H[e] * sc;
     w.H[e] = v;
     w.a32[e] = (float)v;
     w.v32[e] = i == j ? 1.f : 0.f;
   }
-  __syncwarp();
-  warp_jacobi<float>(w.a32, w.v32, m, 10, 1e-12f, 1e-9f, w.r32, lane);
-  for (int e = lane; e < mm; e += 32) w.X[e] = (double)w.v32[e];
-  __syncwarp();
-  for (int t = lane; t < nu; t += 32) {  // T = X^T X (upper, mirrored)
+  tm.sync();
+  team_jacobi<float, NT>(w.a32, w.v32, m, 10, 1e-12f, 1e-9f, w.r32, tm);
+  for (int e = tm.id; e < mm; e += NT) w.X[e] = (double)w.v32[e];
+  tm.sync();
+  for (int t = tm.id; t < nu; t += NT) {  // T = X^T X (upper, mirrored)
     int i, j;
     upper_ij(t, m, i, j);
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.X[k * m + i], w.X[k * m + j], acc);
     w.T[i * m + j] = w.T[j * m + i] = acc;
   }
-  __syncwarp();
-  for (int e = lane; e < mm; e += 32) {  // B = X (3 I - T) / 2
+  tm.sync();
+  for (int e = tm.id; e < mm; e += NT) {  // B = X (3 I - T) / 2
     const int i = e / m, j = e - i * m;
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.X[i * m + k], w.T[k * m + j], acc);
     w.B[e] = 1.5 * w.X[e] - 0.5 * acc;
   }
-  __syncwarp();
-  for (int e = lane; e < mm; e += 32) {  // T = A X
+  tm.sync();
+  for (int e = tm.id; e < mm; e += NT) {  // T = A X
     const int i = e / m, j = e - i * m;
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.H[i * m + k], w.B[k * m + j], acc);
     w.T[e] = acc;
   }
-  __syncwarp();
-  for (int e = lane; e < mm; e += 32) w.X[e] = w.B[e];
-  __syncwarp();
-  for (int t = lane; t < nu; t += 32) {  // B = X^T T (upper, mirrored)
+  tm.sync();
+  for (int e = tm.id; e < mm; e += NT) w.X[e] = w.B[e];
+  tm.sync();
+  for (int t = tm.id; t < nu; t += NT) {  // B = X^T T (upper, mirrored)
     int i, j;
     upper_ij(t, m, i, j);
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.X[k * m + i], w.T[k * m + j], acc);
     w.B[i * m + j] = w.B[j * m + i] = acc;
   }
-  __syncwarp();
-  warp_jacobi_refine(w.B, w.X, m, 6, 1e-13, w.r64, lane);
+  tm.sync();
+  team_jacobi_refine<NT>(w.B, w.X, m, 6, 1e-13, w.r64, tm);
   const double isc = ldexp(1.0, ex);
-  for (int t = lane; t < nu; t += 32) {  // H = X max(diag B, 0) X^T
+  for (int t = tm.id; t < nu; t += NT) {  // H = X max(diag B, 0) X^T
     int i, j;
     upper_ij(t, m, i, j);
     double acc = 0.0;
@@ -551,7 +607,7 @@ __device__ void warp_psd_project(ProjWS& w, int n, int lane) {
     }
     w.H[i * m + j] = w.H[j * m + i] = acc * isc;
   }
-  __syncwarp();
+  tm.sync();
 }
 
 }  // namespace txg

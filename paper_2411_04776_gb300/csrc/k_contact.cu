@@ -446,35 +446,53 @@ __global__ void __launch_bounds__(128) k_query_list(Dev d, int phase, int mode) 
     } else {
       const int nx = c.hi[0] - c.lo[0] + 1, ny = c.hi[1] - c.lo[1] + 1;
       const int nb = G.hnb[c.tab], hb = G.hb0[c.tab], he = G.he0[c.tab];
+      // 32 cells at a time: a lane per cell reads its bucket's range; the bucket entries of the
+      // 32 cells are then checked a lane per entry (owner cell found by a binary search over the
+      // lanes' exclusive offsets), so no lane walks a bucket serially
       for (long long ci0 = 0; ci0 < c.ncell; ci0 += 32) {
         const long long ci = ci0 + lane;
-        int cnt = 0, s = 0, e = 0, ix = 0, iy = 0, iz = 0;
+        int cnt = 0, s = 0, ix = 0, iy = 0, iz = 0;
         if (ci < c.ncell) {
           ix = c.lo[0] + (int)(ci % nx);
           iy = c.lo[1] + (int)((ci / nx) % ny);
           iz = c.lo[2] + (int)(ci / ((long long)nx * ny));
           const int bk = hash_cell(ix, iy, iz) & (nb - 1);
           s = d.hstart[hb + bk];
-          e = d.hstart[hb + bk + 1];
-          for (int m = s; m < e; ++m)
-            if (query_match(d, c, d.hent[he + m], ix, iy, iz)) ++cnt;
+          cnt = d.hstart[hb + bk + 1] - s;
         }
-        int pre = cnt;  // inclusive warp scan of the lanes' counts
+        int ex = cnt;  // inclusive, then exclusive warp scan of the entry counts
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, pre, o);
-          if (lane >= o) pre += t;
+          const int t = __shfl_up_sync(0xffffffffu, ex, o);
+          if (lane >= o) ex += t;
         }
-        if (write && cnt) {
-          int pos = base + total + pre - cnt;
-          for (int m = s; m < e; ++m) {
-            const int2 ent = d.hent[he + m];
-            if (!query_match(d, c, ent, ix, iy, iz)) continue;
-            if (pos < G.pcap) d.pairs[G.pbase + pos] = make_int4(c.type, c.gk, ent.x, c.g);
-            ++pos;
+        const int T = __shfl_sync(0xffffffffu, ex, 31);
+        ex -= cnt;
+        for (int j0 = 0; j0 < T; j0 += 32) {
+          const int j = j0 + lane;
+          int L = 0;  // the last lane whose offset is <= j: it owns entry j (its count is > 0)
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int e2 = __shfl_sync(0xffffffffu, ex, L + step);
+            if (e2 <= j) L += step;
           }
+          const int sL = __shfl_sync(0xffffffffu, s, L), eL = __shfl_sync(0xffffffffu, ex, L);
+          const int xL = __shfl_sync(0xffffffffu, ix, L), yL = __shfl_sync(0xffffffffu, iy, L);
+          const int zL = __shfl_sync(0xffffffffu, iz, L);
+          bool hit = false;
+          int P = 0;
+          if (j < T) {
+            const int2 ent = d.hent[he + sL + (j - eL)];
+            hit = query_match(d, c, ent, xL, yL, zL);
+            P = ent.x;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (write && hit) {
+            const int pos = base + total + __popc(m & ((1u << lane) - 1u));
+            if (pos < G.pcap) d.pairs[G.pbase + pos] = make_int4(c.type, c.gk, P, c.g);
+          }
+          total += __popc(m);
         }
-        total += __shfl_sync(0xffffffffu, pre, 31);
       }
     }
     if (!write && lane == 0) d.qcount[q] = total;
@@ -549,9 +567,9 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
       atomicAdd(&d.gv[g].fc[c], -gr[c]);
     }
     if (d.fixed[ra]) continue;
-    atomicAdd(&d.grad[ra].x, gr[0]);
-    atomicAdd(&d.grad[ra].y, gr[1]);
-    atomicAdd(&d.grad[ra].z, gr[2]);
+    atomicAdd(&d.cgrad[ra].x, gr[0]);
+    atomicAdd(&d.cgrad[ra].y, gr[1]);
+    atomicAdd(&d.cgrad[ra].z, gr[2]);
   }
   if (ns == 1) {
     const int ra = rows[slots[0]];
@@ -560,13 +578,9 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
     const double bpp = -2.0 * log(dd / G.dhat) - 4.0 * r / dd + r * r / (dd * dd);
     double H3[9];
     single_point_block(bpp, pb.gDp + 3 * slots[0], H3);
-    const int bp = d.diag_pos[ra];
-    for (int e = 0; e < 9; ++e) {
-      if (MIXED)
-        atomicAdd(&d.vals32[val_addr(bp, e)], (float)(kap * H3[e]));
-      else
-        atomicAdd(&d.vals[val_addr(bp, e)], kap * H3[e]);
-    }
+    C1Rec& rec = d.c1rec[atomicAdd(d.c1_n, 1)];  // at most one per slot: never past npslots
+    rec.bp = d.diag_pos[ra];
+    for (int e = 0; e < 9; ++e) rec.v[e] = kap * H3[e];
   } else if (ns > 1) {
     const int pos = atomicAdd(d.cwork_n, 1);
     d.cwork[pos] = i;
@@ -574,10 +588,15 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
   }
 }
 
-// Contact assembly, part 2: one warp per listed pair.  The lanes form the barrier Hessian block
-// on the pair's free gel points (warp_pair_block), the warp projects it to PSD, and the lanes add
-// it to the sliced BSR.  The pair's setup comes from the record part 1 stored (recomputed by one
-// lane for pairs beyond the record capacity).
+// Contact assembly, part 2: one warp per listed pair.  Its lanes form the barrier Hessian block
+// on the pair's free gel points (team_pair_block), project it to PSD and scale it by kappa.  (A
+// CTA of four warps per pair measured no faster: the projection is bound by the latency of its
+// Jacobi rounds, not by FP64 issue, and batches lose pairs in flight.)  Mode 0 (may run beside
+// the elastic assembly): the first crec_cap listed pairs, starting from the setup part 1 stored;
+// the result and its block positions go to the pair's record.  Mode 1 (after the gather wrote
+// the matrix): the recorded blocks and the single-point blocks of part 1 are added to the gel's
+// BSR; pairs beyond the record capacity are formed here (setup recomputed by one lane) and added
+// directly.
 constexpr int CW_WARPS = 4;
 
 struct ContactWS {
@@ -589,19 +608,49 @@ struct ContactWS {
 };
 
 template <bool MIXED>
-__global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d) {
+__device__ __forceinline__ void add_val(const Dev& d, int bp, int e, double v) {
+  if (MIXED)
+    atomicAdd(&d.vals32[val_addr(bp, e)], (float)v);
+  else
+    atomicAdd(&d.vals[val_addr(bp, e)], v);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d, int mode) {
   __shared__ ContactWS sws[CW_WARPS];
   ContactWS& w = sws[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+  const Team<32> tm{(int)(threadIdx.x & 31), nullptr};
+  const int wid = blockIdx.x * CW_WARPS + (threadIdx.x >> 5), nw = gridDim.x * CW_WARPS;
   const int n = *d.cwork_n;
-  for (int k = blockIdx.x * CW_WARPS + (threadIdx.x >> 5); k < n; k += gridDim.x * CW_WARPS) {
+  const int nrec = min(n, d.crec_cap);
+  if (mode == 1) {
+    // single-point blocks: a thread per record
+    const int n1 = *d.c1_n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n1; k += gridDim.x * blockDim.x) {
+      const C1Rec& r = d.c1rec[k];
+      for (int e = 0; e < 9; ++e) add_val<MIXED>(d, r.bp, e, r.v[e]);
+    }
+    // recorded pair blocks: a warp per pair
+    for (int k = wid; k < nrec; k += nw) {
+      const int* bpk = d.chbp + (size_t)k * CH_BP;
+      const int ns = bpk[0], nf = 3 * ns;
+      const double* hv = d.chv + (size_t)k * CH_STRIDE;
+      for (int e = tm.id; e < nf * nf; e += 32) {
+        const int r = e / nf, c = e - r * nf;
+        const int bp = bpk[1 + (r / 3) * ns + c / 3];
+        if (bp >= 0) add_val<MIXED>(d, bp, 3 * (r % 3) + c % 3, hv[e]);
+      }
+    }
+  }
+  const int k0 = mode == 0 ? 0 : nrec, k1 = mode == 0 ? nrec : n;
+  for (int k = k0 + wid; k < k1; k += nw) {
     const int i = d.cwork[k];
     if (k < d.crec_cap) {
       const double* src = reinterpret_cast<const double*>(d.crec + k);
       double* dst = reinterpret_cast<double*>(&w.pb);
-      for (int q = lane; q < (int)(sizeof(PairBarrier) / sizeof(double)); q += 32) dst[q] = src[q];
+      for (int q = tm.id; q < (int)(sizeof(PairBarrier) / sizeof(double)); q += 32) dst[q] = src[q];
     }
-    if (lane == 0) {
+    if (tm.id == 0) {
       const int4 pr = d.pairs[i];
       const GelInfo& G = d.gi[pr.w];
       int rows[4];
@@ -622,32 +671,34 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d) {
     }
     __syncwarp();
     const int ns = w.ns, nf = 3 * ns, m = nf + (nf & 1);
-    warp_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, lane);
-    warp_psd_project(w.pj, nf, lane);
+    team_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, tm);
+    team_psd_project(w.pj, nf, tm);
     const int g = w.g;
-    if (lane < ns * ns) {
-      const int a = lane / ns, c = lane - a * ns;
+    if (tm.id < ns * ns) {
+      const int a = tm.id / ns, c = tm.id - a * ns;
       const int ra = w.rows[w.slots[a]], rc = w.rows[w.slots[c]];
       int bp = -1;
       if (!d.fixed[ra] && !d.fixed[rc]) {
         bp = find_block(d, ra, rc);
         if (bp < 0) atomicOr(&d.gv[g].flags, 16);
       }
-      w.bp[lane] = bp;
+      w.bp[tm.id] = bp;
+      if (mode == 0) d.chbp[(size_t)k * CH_BP + 1 + tm.id] = bp;
     }
+    if (mode == 0 && tm.id == 0) d.chbp[(size_t)k * CH_BP] = ns;
     __syncwarp();
     const double kap = d.gi[g].kappa;
-    for (int e = lane; e < nf * nf; e += 32) {
+    for (int e = tm.id; e < nf * nf; e += 32) {
       const int r = e / nf, c = e - r * nf;
-      const int bp = w.bp[(r / 3) * ns + c / 3];
-      if (bp < 0) continue;
       const double v = kap * w.pj.H[r * m + c];
-      if (MIXED)
-        atomicAdd(&d.vals32[val_addr(bp, 3 * (r % 3) + c % 3)], (float)v);
-      else
-        atomicAdd(&d.vals[val_addr(bp, 3 * (r % 3) + c % 3)], v);
+      if (mode == 0) {
+        d.chv[(size_t)k * CH_STRIDE + e] = v;
+      } else {
+        const int bp = w.bp[(r / 3) * ns + c / 3];
+        if (bp >= 0) add_val<MIXED>(d, bp, 3 * (r % 3) + c % 3, v);
+      }
     }
-    __syncwarp();
+    __syncwarp();  // w is reused by the warp's next pair
   }
 }
 
@@ -733,7 +784,7 @@ void launch_pair_energy(const Dev& d, int phase, int mode, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- unit-level entries
-// unit-level entry: one warp per pair (the same lane-parallel derivatives and projection as the
+// unit-level entry: one warp per pair (the same team-parallel derivatives and projection as the
 // assembly), full 12 x 12 Hessian with the free block projected
 struct EvalWS {
   PairBarrier pb;
@@ -748,10 +799,10 @@ __global__ void __launch_bounds__(128) k_eval_pairs(int n, const int* kind, cons
                                                     double* go, double* Ho, int* dtype) {
   __shared__ EvalWS sws[4];
   EvalWS& w = sws[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+  const Team<32> tm{(int)(threadIdx.x & 31), nullptr};
   const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (i >= n) return;  // whole warps
-  if (lane == 0) {
+  if (tm.id == 0) {
     for (int k = 0; k < 4; ++k)
       for (int c = 0; c < 3; ++c) w.P[k][c] = Pin[12 * i + 3 * k + c];
     DType ty;
@@ -770,24 +821,25 @@ __global__ void __launch_bounds__(128) k_eval_pairs(int n, const int* kind, cons
   }
   __syncwarp();
   const bool act = w.act != 0;
-  if (go && lane < 12) go[12 * i + lane] = act ? pair_grad_entry(w.pb, lane) : 0.0;
+  if (go && tm.id < 12) go[12 * i + tm.id] = act ? pair_grad_entry(w.pb, tm.id) : 0.0;
   if (!act) {
     if (Ho)
-      for (int e = lane; e < 144; e += 32) Ho[144 * (size_t)i + e] = 0.0;
+      for (int e = tm.id; e < 144; e += 32) Ho[144 * (size_t)i + e] = 0.0;
     return;
   }
-  if (Ho) {  // the whole 12 x 12 Hessian through the same lane-parallel block code
-    if (lane < 12) w.all[lane] = lane;
+  if (Ho) {  // the whole 12 x 12 Hessian through the same team-parallel block code
+    if (tm.id < 12) w.all[tm.id] = tm.id;
     __syncwarp();
-    warp_pair_block(w.pb, w.all, 12, 12, w.pj.T, w.pj.H, lane);
-    for (int e = lane; e < 144; e += 32) Ho[144 * (size_t)i + e] = w.pj.H[e];
+    team_pair_block(w.pb, w.all, 12, 12, w.pj.T, w.pj.H, tm);
+    for (int e = tm.id; e < 144; e += 32) Ho[144 * (size_t)i + e] = w.pj.H[e];
+    __syncwarp();
   }
   const int nf = w.nf;
   if (nf == 0 || !Ho) return;
   const int m = nf + (nf & 1);
-  warp_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, lane);
-  warp_psd_project(w.pj, nf, lane);
-  for (int e = lane; e < nf * nf; e += 32) {
+  team_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, tm);
+  team_psd_project(w.pj, nf, tm);
+  for (int e = tm.id; e < nf * nf; e += 32) {
     const int r = e / nf, c = e - r * nf;
     Ho[144 * (size_t)i + 12 * w.fd[r] + w.fd[c]] = w.pj.H[r * m + c];
   }
@@ -843,19 +895,34 @@ void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st)
 }
 size_t pair_record_doubles() { return sizeof(PairBarrier) / sizeof(double); }
 
-void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st) {
+// Contact assembly without the matrix: contact gradient into cgrad, single-point blocks and the
+// first crec_cap projected pair Hessians into their records (independent of the elastic
+// assembly and the gather, so it may run beside them)
+void launch_contact_compute(const Dev& d, int phase, bool mixed, cudaStream_t st) {
+  cudaMemsetAsync(d.cgrad, 0, sizeof(double4_32a) * (size_t)d.nrows, st);
   if (d.npslots <= 0) return;
   cudaMemsetAsync(d.cwork_n, 0, sizeof(int), st);
+  cudaMemsetAsync(d.c1_n, 0, sizeof(int), st);
   const int nb = nblk(d.npslots, 128);
-  const int nw = std::min(nblk(d.npslots, CW_WARPS), 8 * 152);
+  const int nc = std::min(nblk(std::min(d.npslots, d.crec_cap), CW_WARPS), 8 * 152);
   if (mixed) {
     k_contact_pairs<true><<<nb, 128, 0, st>>>(d, phase);
-    k_contact_hess<true><<<nw, 32 * CW_WARPS, 0, st>>>(d);
+    k_contact_hess<true><<<nc, 32 * CW_WARPS, 0, st>>>(d, 0);
   } else {
     k_contact_pairs<false><<<nb, 128, 0, st>>>(d, phase);
-    k_contact_hess<false><<<nw, 32 * CW_WARPS, 0, st>>>(d);
+    k_contact_hess<false><<<nc, 32 * CW_WARPS, 0, st>>>(d, 0);
   }
   count_launch(2);
+}
+// ... and its blocks added to the matrix the gather wrote
+void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st) {
+  if (d.npslots <= 0) return;
+  const int nc = std::min(nblk(d.npslots, CW_WARPS), 8 * 152);
+  if (mixed)
+    k_contact_hess<true><<<nc, 32 * CW_WARPS, 0, st>>>(d, 1);
+  else
+    k_contact_hess<false><<<nc, 32 * CW_WARPS, 0, st>>>(d, 1);
+  count_launch(1);
 }
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st) {
   if (d.npslots > 0) {

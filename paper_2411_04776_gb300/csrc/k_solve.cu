@@ -153,9 +153,10 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
     if (d.fixed[r]) {
       go = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     } else {
-      go.x = gr[0] + m * (x.x - xt.x);
-      go.y = gr[1] + m * (x.y - xt.y);
-      go.z = gr[2] + m * (x.z - xt.z);
+      const double4_32a cg = d.cgrad[r];  // the contact kernels' part
+      go.x = gr[0] + m * (x.x - xt.x) + cg.x;
+      go.y = gr[1] + m * (x.y - xt.y) + cg.y;
+      go.z = gr[2] + m * (x.z - xt.z) + cg.z;
       go.w = 0.0;
     }
     d.grad[r] = go;

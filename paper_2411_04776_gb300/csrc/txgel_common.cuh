@@ -95,6 +95,15 @@ struct GelVar {  // per gel, written by the device
 
 struct PairBarrier;  // barrier setup of one contact pair (dev_pairwarp.cuh)
 
+// Barrier block of a pair with one free gel point: its diagonal block position and kappa d2b/dx2
+struct C1Rec {
+  int bp;
+  int pad_;
+  double v[9];
+};
+constexpr int CH_STRIDE = 144;  // projected pair Hessian record: 12 x 12 values (row stride 3 ns)
+constexpr int CH_BP = 17;       // and ns followed by the ns x ns block positions
+
 // Everything the kernels touch, passed by value.
 struct Dev {
   int n_gels;
@@ -171,6 +180,11 @@ struct Dev {
   int* cwork_n;
   PairBarrier* crec;  // their barrier setup (the first crec_cap of them)
   int crec_cap;
+  double* chv;     // the projected kappa-scaled Hessians of those crec_cap pairs (CH_STRIDE each)
+  int* chbp;       // their ns and block positions (CH_BP each)
+  C1Rec* c1rec;    // single-free-point barrier blocks (appended; one per pair slot at most)
+  int* c1_n;
+  double4_32a* cgrad;  // contact gradient per row: accumulated by the contact kernels, added by the gather
   int* err;
 };
 

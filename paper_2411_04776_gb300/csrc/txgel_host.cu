@@ -40,7 +40,8 @@ void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t
 void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st);
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st);
 void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st);
-void launch_contact_assemble(const Dev& d, int phase, bool mixed, cudaStream_t st);
+void launch_contact_compute(const Dev& d, int phase, bool mixed, cudaStream_t st);
+void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
 void launch_min_dist(const Dev& d, int phase, cudaStream_t st);
 void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
@@ -472,6 +473,9 @@ struct tx_batch {
   int graphs = -1;  // -1 undecided, 0 off (unsupported or disabled), 1 on
   bool capturing = false;  // profile events become event-record nodes of the graph
   cudaStream_t gst = nullptr;          // stream the graph is captured on and replayed on
+  cudaStream_t st2 = nullptr;          // side stream of the contact assembly (fork / join events)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_ok = false;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order it after / before the caller's stream
   std::vector<int2> plan_rng_h;
   std::vector<int> plan_grp_of_h;
@@ -508,23 +512,25 @@ cudaEvent_t prof_event(tx_batch* b) {
 }
 // inside a stream capture a plain record would only order the graph's nodes; the external
 // flag makes it a record node that fires on every replay, so the phase times stay measurable
-void prof_record(tx_batch* b, cudaEvent_t e) {
+void prof_record(tx_batch* b, cudaEvent_t e, cudaStream_t s = nullptr) {
+  if (!s) s = b->st;
   if (b->capturing)
-    cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
   else
-    cudaEventRecord(e, b->st);
+    cudaEventRecord(e, s);
 }
 
-void prof_open(tx_batch* b, int phase) {
+// phase timing on the stream its launches go to (the library stream unless given)
+void prof_open(tx_batch* b, int phase, cudaStream_t s = nullptr) {
   if (!b->prof.on) return;
   b->prof.open_phase = phase;
   b->prof.open_ev = prof_event(b);
-  prof_record(b, b->prof.open_ev);
+  prof_record(b, b->prof.open_ev, s);
 }
-void prof_close(tx_batch* b, int nlaunch) {
+void prof_close(tx_batch* b, int nlaunch, cudaStream_t s = nullptr) {
   if (!b->prof.on || b->prof.open_phase < 0) return;
   cudaEvent_t e = prof_event(b);
-  prof_record(b, e);
+  prof_record(b, e, s);
   b->prof.pending.push_back({b->prof.open_ev, e, b->prof.open_phase, false});
   b->prof.launches[b->prof.open_phase] += nlaunch;
   b->prof.open_phase = -1;
@@ -581,7 +587,12 @@ tx_status alloc_pairs(tx_batch* b) {
   b->d.cwork = b->pair_mem.get<int>(total);
   b->d.crec_cap = std::min(total, CREC_PER_GEL * b->n + CREC_BASE);
   b->d.crec = reinterpret_cast<PairBarrier*>(b->pair_mem.get<double>((size_t)b->d.crec_cap * pair_record_doubles()));
-  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork || !b->d.crec) return TX_ERR_OOM;
+  b->d.chv = b->pair_mem.get<double>((size_t)b->d.crec_cap * CH_STRIDE);
+  b->d.chbp = b->pair_mem.get<int>((size_t)b->d.crec_cap * CH_BP);
+  b->d.c1rec = b->pair_mem.get<C1Rec>(total);
+  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork || !b->d.crec || !b->d.chv || !b->d.chbp ||
+      !b->d.c1rec)
+    return TX_ERR_OOM;
   b->d.npslots = total;
   std::vector<int> slot(total);
   for (int g = 0; g < b->n; ++g)
@@ -902,6 +913,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.xt = M.get<double4_32a>(rows);
   d.p = M.get<double4_32a>(rows);
   d.grad = M.get<double4_32a>(rows);
+  d.cgrad = M.get<double4_32a>(rows);
   b->x0 = M.get<double4_32a>(rows);
   b->v0 = M.get<double4_32a>(rows);
   b->ex = M.get<double4_32a>(rows);
@@ -959,6 +971,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.qnear_n = M.get<int>(4);
   d.err = M.get<int>(4);
   d.cwork_n = M.get<int>(4);
+  d.c1_n = M.get<int>(4);
   b->pieces = M.get<int4>(b->npieces);
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
@@ -1521,14 +1534,27 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
   Dev& d = b->d;
   cudaStream_t st = b->st;
   launch_gel_op(d, PH_NEWTON, 0, st);
+  // the contact terms (latency-bound: a thread per candidate pair, a warp per pair Hessian) on the
+  // side stream, beside the elastic assembly; the gather waits for them.  Only for a single gel
+  // in mixed precision: the FP64 elastic assembly, or a batch's, leaves no FP64 issue slots to the
+  // contact kernels and the overlap measured no gain (FP64) or a loss (64-gel batches).
+  cudaStream_t cs = st;
+  if (b->side_ok && b->mixed && b->n == 1) {
+    CK(cudaEventRecord(b->ev_fork, st));
+    CK(cudaStreamWaitEvent(b->st2, b->ev_fork, 0));
+    cs = b->st2;
+  }
+  prof_open(b, PR_CONTACT, cs);
+  launch_contact_compute(d, PH_NEWTON, b->mixed, cs);
+  prof_close(b, 2, cs);
+  if (cs != st) CK(cudaEventRecord(b->ev_join, cs));
   prof_open(b, PR_TET);
   launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
+  if (cs != st) CK(cudaStreamWaitEvent(st, b->ev_join, 0));
   prof_open(b, PR_GATHER);
   launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
-  prof_close(b, 1);
-  prof_open(b, PR_CONTACT);
-  launch_contact_assemble(d, PH_NEWTON, b->mixed, st);
+  launch_contact_merge(d, b->mixed, st);
   prof_close(b, 2);
   prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
@@ -1575,6 +1601,12 @@ void drop_newton_graph(tx_batch* b) {
 // launches for good if capture is refused (TXG_NO_GRAPHS=1 also disables it).
 tx_status run_newton_launches(tx_batch* b, const std::vector<int>& set, int pcg_max, int refine,
                               int accd_max) {
+  if (!b->side_ok && !b->st2) {  // side stream of the contact assembly (plain sequence if refused)
+    b->side_ok = cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (!b->side_ok) cudaGetLastError();
+  }
   if (b->graphs < 0) {
     const char* e = std::getenv("TXG_NO_GRAPHS");
     b->graphs = (e && e[0] == '1') ? 0 : 1;
@@ -1884,6 +1916,12 @@ void destroy_batch(tx_batch* b) {
   cudaStreamSynchronize(b->st);
   prof_resolve(b);
   drop_newton_graph(b);
+  if (b->st2) {
+    cudaStreamSynchronize(b->st2);
+    cudaStreamDestroy(b->st2);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->gst) {
     cudaStreamSynchronize(b->gst);
     cudaStreamDestroy(b->gst);
@@ -2131,13 +2169,14 @@ size_t tx_gel_footprint_bytes(const tx_gel_desc* desc) {
     nbp += w * SLICE;
   }
   const size_t nt = m.nt, nq = m.sv.size() + m.st.size() + m.se.size();
-  size_t bytes = rows * (16 * sizeof(double4_32a) + 8 + 1 + 4 + 4 + 72);
+  size_t bytes = rows * (17 * sizeof(double4_32a) + 8 + 1 + 4 + 4 + 72);
   if (mixed) bytes += rows * (6 * sizeof(float4) + 36);
   bytes += nt * (16 + 72 + 8 + 4 + 64 + TS * 8 + (mixed ? TS32 * 4 : 0));
   bytes += nbp * (4 + 4 + 4 + (mixed ? 36 : 72));
   bytes += nq * (4 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;
   bytes += ((size_t)m.niv + m.nit + m.ie.size()) * 2 * sizeof(double4_32a);  // primitive boxes
-  bytes += (size_t)initial_pcap(m) * 32 + (size_t)CREC_PER_GEL * pair_record_doubles() * 8;
+  bytes += (size_t)initial_pcap(m) * (32 + sizeof(C1Rec)) +
+           (size_t)CREC_PER_GEL * (pair_record_doubles() * 8 + CH_STRIDE * 8 + CH_BP * 4);
   return bytes;
 }
 
@@ -2179,9 +2218,10 @@ tx_status tx_gel_gradient(tx_gel* gl, const double* x, const double* xt, double 
   if (s != TX_OK) return s;
   Dev& d = b->d;
   launch_gel_op(d, PH_EVAL, 0, b->st);
+  launch_contact_compute(d, PH_EVAL, b->mixed, b->st);
   launch_tet_assemble(d, PH_EVAL, b->mixed, b->st);
   launch_gather(d, PH_EVAL, b->nbp, b->mixed, b->st);
-  launch_contact_assemble(d, PH_EVAL, b->mixed, b->st);
+  launch_contact_merge(d, b->mixed, b->st);
   CK(cudaGetLastError());
   s = copy_rows_out(b, 0, d.grad, grad, false);
   if (s != TX_OK) return s;
