@@ -11,6 +11,7 @@
 // first, prefix-summed, then written, so the candidate list is ordered and identical run to run.
 #include <algorithm>
 
+#include "dev_elastic.cuh"
 #include "dev_pairwarp.cuh"
 
 namespace txg {
@@ -759,28 +760,90 @@ __global__ void k_min_dist(Dev d, int phase) {
 // kappa b(d) of every candidate pair at x + alpha p (mode 1: line-search trial of the gels still
 // searching, alpha = their trial step; otherwise alpha = 0), one thread per pair slot; the energy
 // kernel sums a gel's slots in a fixed order
-__global__ void __launch_bounds__(128) k_pair_energy(Dev d, int phase, int mode) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.npslots) return;
-  const int g = d.pslot_gel[i];
+// ---------------------------------------------------------------- energy
+// One launch per energy evaluation.  pieces: (gel, kind, begin, end); kind 0 tets [begin, end),
+// 1 rows [begin, end), 2 pair slots (chunk begin of end chunks over the gel's candidate list).
+// Every CTA sums its piece into part_e; the gel's last CTA to finish (a per-gel ticket) adds its
+// pieces in order and applies the result.  mode 0: E_cur at x; 1: line-search trial at
+// x + alpha p for gels still searching (accept, or halve alpha); 2: E_try at x.
+constexpr int EN_T = 256;
+
+__global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* pieces, const int* gel_piece,
+                                                 double* part_e, unsigned* ticket, int mode) {
+  __shared__ double sm[EN_T / 32];
+  __shared__ int last;
+  const int4 pc = pieces[blockIdx.x];
+  const int g = pc.x;
   if (d.gc[g].phase != phase) return;
-  if (mode == 1 && (d.gv[g].ls_state != 0 || d.gv[g].converged)) return;
+  GelVar& v = d.gv[g];
+  if (mode == 1 && (v.ls_state != 0 || v.converged)) return;
   const GelInfo& G = d.gi[g];
-  if (i - G.pbase >= min(d.gv[g].npair, G.pcap)) return;
-  const int4 pr = d.pairs[i];
-  const double alpha = mode == 1 ? d.gv[g].alpha : 0.0;
-  double P[4][3];
-  int rows[4];
-  pair_points(d, pr, alpha, false, P, rows);
-  double dist;
-  d.pe[i] = G.kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+  const double alpha = mode == 1 ? v.alpha : 0.0;
+  double acc = 0.0;
+  if (pc.y == 0) {
+    for (int t = pc.z + threadIdx.x; t < pc.w; t += EN_T) acc += tet_energy_at(d, t, alpha, G.mu, G.lam);
+  } else if (pc.y == 1) {
+    const double ih2 = 0.5 / (d.gc[g].h * d.gc[g].h);
+    for (int r = pc.z + threadIdx.x; r < pc.w; r += EN_T) {
+      const double4_32a x = d.x[r], xt = d.xt[r];
+      double ex = x.x - xt.x, ey = x.y - xt.y, ez = x.z - xt.z;
+      if (alpha != 0.0) {
+        const double4_32a p = d.p[r];
+        ex = x.x + alpha * p.x - xt.x;
+        ey = x.y + alpha * p.y - xt.y;
+        ez = x.z + alpha * p.z - xt.z;
+      }
+      acc += d.mass[r] * (ex * ex + ey * ey + ez * ez) * ih2;
+    }
+  } else {
+    const int np = min(v.npair, G.pcap);
+    for (int i = pc.z * EN_T + threadIdx.x; i < np; i += pc.w * EN_T) {
+      const int4 pr = d.pairs[G.pbase + i];
+      double P[4][3], dist;
+      int rows[4];
+      pair_points(d, pr, alpha, false, P, rows);
+      acc += G.kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+    }
+  }
+  acc = block_sum<EN_T>(acc, sm);
+  if (threadIdx.x == 0) {
+    part_e[blockIdx.x] = acc;
+    __threadfence();
+    const unsigned n = (unsigned)(gel_piece[g + 1] - gel_piece[g]);
+    last = atomicAdd(&ticket[g], 1u) == n - 1u;
+  }
+  __syncthreads();
+  if (!last) return;
+  // every piece of the gel is in part_e (each fenced before taking its ticket): a fixed-order
+  // block sum of them, read past L1
+  double E = 0.0;
+  for (int k = gel_piece[g] + threadIdx.x; k < gel_piece[g + 1]; k += EN_T) E += __ldcg(part_e + k);
+  E = block_sum<EN_T>(E, sm);
+  if (threadIdx.x != 0) return;
+  ticket[g] = 0u;
+  if (mode == 0) {
+    v.E_cur = E;
+  } else if (mode == 2) {
+    v.E_try = E;
+  } else {
+    v.E_try = E;
+    if (E <= v.E_cur) {
+      v.ls_state = 1;
+      v.E_cur = E;
+    } else {
+      v.alpha *= 0.5;
+      v.ls_total += 1;
+      // no resolvable decrease: stationary to energy resolution (6) or failure (2)
+      if (v.alpha < 1e-12 * v.alpha0) v.ls_state = (-v.gtp <= 1e-10 * fabs(v.E_cur)) ? 6 : 2;
+    }
+  }
 }
 
-void launch_pair_energy(const Dev& d, int phase, int mode, cudaStream_t st) {
-  if (d.npslots > 0) {
-    k_pair_energy<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode);
-    count_launch(1);
-  }
+void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
+                   double* part_e, unsigned* ticket, int mode, cudaStream_t st) {
+  if (npieces <= 0) return;
+  k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, gel_piece, part_e, ticket, mode);
+  count_launch(1);
 }
 
 // ---------------------------------------------------------------- unit-level entries

@@ -589,86 +589,6 @@ int pcg_max_ctas_per_sm(int max_slices) {
   return a < b ? a : b;
 }
 
-// ---------------------------------------------------------------- energy
-constexpr int EN_T = 256;
-constexpr int PIECE = 2048;
-
-// pieces: (gel, kind, begin, end), kind 0 tets, 1 rows, 2 pairs (range read from gv)
-// mode 0: at x (alpha = 0); mode 1: line search at x + alpha p (gels still searching)
-__global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* pieces, double* part_e,
-                                                 int mode) {
-  __shared__ double sm[EN_T / 32];
-  const int4 pc = pieces[blockIdx.x];
-  const int g = pc.x;
-  if (d.gc[g].phase != phase) return;
-  if (mode == 1 && (d.gv[g].ls_state != 0 || d.gv[g].converged)) return;
-  const GelInfo& G = d.gi[g];
-  const double alpha = mode == 1 ? d.gv[g].alpha : 0.0;
-  double acc = 0.0;
-  if (pc.y == 0) {
-    for (int t = pc.z + threadIdx.x; t < pc.w; t += EN_T) acc += tet_energy_at(d, t, alpha, G.mu, G.lam);
-  } else if (pc.y == 1) {
-    const double ih2 = 0.5 / (d.gc[g].h * d.gc[g].h);
-    for (int r = pc.z + threadIdx.x; r < pc.w; r += EN_T) {
-      const double4_32a x = d.x[r], xt = d.xt[r];
-      double ex = x.x - xt.x, ey = x.y - xt.y, ez = x.z - xt.z;
-      if (alpha != 0.0) {
-        const double4_32a p = d.p[r];
-        ex = x.x + alpha * p.x - xt.x;
-        ey = x.y + alpha * p.y - xt.y;
-        ez = x.z + alpha * p.z - xt.z;
-      }
-      acc += d.mass[r] * (ex * ex + ey * ey + ez * ez) * ih2;
-    }
-  } else {
-    // per-pair barrier energies written by k_pair_energy
-    const int p0 = G.pbase, np = min(d.gv[g].npair, G.pcap);
-    for (int i = threadIdx.x; i < np; i += EN_T) acc += d.pe[p0 + i];
-  }
-  acc = block_sum<EN_T>(acc, sm);
-  if (threadIdx.x == 0) part_e[blockIdx.x] = acc;
-}
-
-// per gel: E = sum of its pieces in order; mode 0: E_cur = E; 1: line-search decision; 2: E_try = E
-__global__ void k_energy_reduce(Dev d, int phase, const int* gel_piece, const double* part_e, int mode) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= d.n_gels) return;
-  if (d.gc[g].phase != phase) return;
-  GelVar& v = d.gv[g];
-  if (mode == 1 && (v.ls_state != 0 || v.converged)) return;
-  double E = 0.0;
-  for (int k = gel_piece[g]; k < gel_piece[g + 1]; ++k) E += part_e[k];
-  if (mode == 0) {
-    v.E_cur = E;
-  } else if (mode == 2) {
-    v.E_try = E;
-  } else {
-    v.E_try = E;
-    if (E <= v.E_cur) {
-      v.ls_state = 1;
-      v.E_cur = E;
-    } else {
-      v.alpha *= 0.5;
-      v.ls_total += 1;
-      // no resolvable decrease: stationary to energy resolution (6) or failure (2)
-      if (v.alpha < 1e-12 * v.alpha0) v.ls_state = (-v.gtp <= 1e-10 * fabs(v.E_cur)) ? 6 : 2;
-    }
-  }
-}
-
-void launch_pair_energy(const Dev& d, int phase, int mode, cudaStream_t st);
-
-void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
-                   double* part_e, int mode, cudaStream_t st) {
-  launch_pair_energy(d, phase, mode, st);
-  if (npieces > 0) {
-    k_energy<<<npieces, EN_T, 0, st>>>(d, phase, pieces, part_e, mode);
-    count_launch(1);
-  }
-  k_energy_reduce<<<nblk(d.n_gels, 128), 128, 0, st>>>(d, phase, gel_piece, part_e, mode);
-  count_launch(1);
-}
-
 // ---------------------------------------------------------------- per-row / per-gel steps
 // step begin: x_n = x, xt = x + h v + h^2 g on free rows (xt = x on fixed rows)
 __global__ void k_predictor(Dev d, int phase) {

@@ -175,7 +175,6 @@ struct Dev {
   int4* pairs;     // (type, gel prim, indenter prim, gel), per-gel segments [pbase, pbase + pcap)
   int* pslot_gel;  // gel of every pair slot
   int npslots;
-  double* pe;      // per pair slot: kappa b(d) at the last energy evaluation
   int* cwork;      // contact pairs with two or more free gel points (pair slots), and their count
   int* cwork_n;
   PairBarrier* crec;  // their barrier setup (the first crec_cap of them)

@@ -60,7 +60,7 @@ int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
 cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, int maxit,
                            int refine_max, int wmax, cudaStream_t st);
 void launch_energy(const Dev& d, int phase, const int4* pieces, int npieces, const int* gel_piece,
-                   double* part_e, int mode, cudaStream_t st);
+                   double* part_e, unsigned* ticket, int mode, cudaStream_t st);
 void launch_rows(int which, const Dev& d, int phase, cudaStream_t st);
 void launch_gel_op(const Dev& d, int phase, int op, cudaStream_t st);
 }  // namespace txg
@@ -100,6 +100,7 @@ constexpr int CREC_BASE = 8192;
 constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
 constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
 constexpr int PIECE_HOST = 512;
+constexpr int PAIR_PIECES = 16;  // energy pieces over a gel's candidate pairs (a few thousand: one each per thread)
 
 #define CK(call)                                                          \
   do {                                                                    \
@@ -487,6 +488,7 @@ struct tx_batch {
   std::vector<int4> pieces_h;
   std::vector<int> gel_piece_h;
   double* part_e = nullptr;
+  unsigned* en_ticket = nullptr;  // per gel: pieces of the running energy launch done
   int* scan_tmp = nullptr;
   double4_32a *x0 = nullptr, *v0 = nullptr;  // request start state (rollback)
   double4_32a *ex = nullptr, *ext = nullptr; // evaluation save area
@@ -583,14 +585,13 @@ tx_status alloc_pairs(tx_batch* b) {
   }
   b->d.pairs = b->pair_mem.get<int4>(total);
   b->d.pslot_gel = b->pair_mem.get<int>(total);
-  b->d.pe = b->pair_mem.get<double>(total);
   b->d.cwork = b->pair_mem.get<int>(total);
   b->d.crec_cap = std::min(total, CREC_PER_GEL * b->n + CREC_BASE);
   b->d.crec = reinterpret_cast<PairBarrier*>(b->pair_mem.get<double>((size_t)b->d.crec_cap * pair_record_doubles()));
   b->d.chv = b->pair_mem.get<double>((size_t)b->d.crec_cap * CH_STRIDE);
   b->d.chbp = b->pair_mem.get<int>((size_t)b->d.crec_cap * CH_BP);
   b->d.c1rec = b->pair_mem.get<C1Rec>(total);
-  if (!b->d.pairs || !b->d.pslot_gel || !b->d.pe || !b->d.cwork || !b->d.crec || !b->d.chv || !b->d.chbp ||
+  if (!b->d.pairs || !b->d.pslot_gel || !b->d.cwork || !b->d.crec || !b->d.chv || !b->d.chbp ||
       !b->d.c1rec)
     return TX_ERR_OOM;
   b->d.npslots = total;
@@ -890,7 +891,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
       b->pieces_h.push_back(make_int4(g, 0, t, std::min(t + PIECE_HOST, G.t0 + G.nt)));
     for (int r = G.v0; r < G.v0 + G.nv; r += PIECE_HOST)
       b->pieces_h.push_back(make_int4(g, 1, r, std::min(r + PIECE_HOST, G.v0 + G.nv)));
-    b->pieces_h.push_back(make_int4(g, 2, 0, 0));
+    for (int k = 0; k < PAIR_PIECES; ++k) b->pieces_h.push_back(make_int4(g, 2, k, PAIR_PIECES));
   }
   b->gel_piece_h.push_back((int)b->pieces_h.size());
   b->npieces = (int)b->pieces_h.size();
@@ -975,6 +976,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->pieces = M.get<int4>(b->npieces);
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
+  b->en_ticket = M.get<unsigned>(n);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
   int* sg_buf = M.get<int>(nslices);
   if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !sg_buf || (b->mixed ? !d.vals32 : !d.vals)) {
@@ -1046,6 +1048,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
   U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
+  if (e == cudaSuccess) e = cudaMemset(b->en_ticket, 0, sizeof(unsigned) * n);
   if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
@@ -1219,7 +1222,7 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
     prof_open(b, PR_BEGIN);
     launch_rows(0, d, PH_START, st);         // x_n, predictor
     launch_hash_build(d, PH_START, 0, st);   // static tables at the target pose
-    launch_energy(d, PH_START, b->pieces, b->npieces, b->gel_piece, b->part_e, 0, st);
+    launch_energy(d, PH_START, b->pieces, b->npieces, b->gel_piece, b->part_e, b->en_ticket, 0, st);
     prof_close(b, 4);
     CK(cudaGetLastError());
     for (int g : start) {
@@ -1276,7 +1279,7 @@ void post_pcg_launch(tx_batch* b, int accd_max) {
   prof_close(b, 2);
   // first trial; usually accepted
   prof_open(b, PR_LS);
-  launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
+  launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, b->en_ticket, 1, st);
   launch_rows(1, d, PH_NEWTON, st);
   launch_gel_op(d, PH_NEWTON, 5, st);
   prof_close(b, 4);
@@ -1299,7 +1302,7 @@ tx_status post_pcg_finish(tx_batch* b) {
     if (!searching) break;
     prof_open(b, PR_LS);
     for (int k = 0; k < 4; ++k) {  // a few halvings per host round trip
-      launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, 1, st);
+      launch_energy(d, PH_NEWTON, b->pieces, b->npieces, b->gel_piece, b->part_e, b->en_ticket, 1, st);
       launch_rows(1, d, PH_NEWTON, st);
       launch_gel_op(d, PH_NEWTON, 5, st);
     }
@@ -2187,7 +2190,7 @@ tx_status tx_gel_energy(tx_gel* gl, const double* x, const double* xt, double h,
   tx_status s = eval_setup(b, 0, x, xt, h, pose);
   if (s != TX_OK) return s;
   Dev& d = b->d;
-  launch_energy(d, PH_EVAL, b->pieces, b->npieces, b->gel_piece, b->part_e, 2, b->st);
+  launch_energy(d, PH_EVAL, b->pieces, b->npieces, b->gel_piece, b->part_e, b->en_ticket, 2, b->st);
   launch_min_dist(d, PH_EVAL, b->st);
   CK(cudaGetLastError());
   std::vector<double> pe(b->npieces);
