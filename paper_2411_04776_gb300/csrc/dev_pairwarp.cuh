@@ -371,10 +371,20 @@ __device__ __forceinline__ double jsqrt(double v) { return sqrt(v); }
 // off-diagonal norm is at most rel_tol times the squared diagonal norm.  Rotations whose
 // off-diagonal entry is below skip_rel (|a_pp| + |a_qq|) are skipped (exact identity).
 // Called by every thread of the team.
+// position of round-robin slot pa (1..m-1) in round r: slots 1..m-1 rotate by r
+__device__ __forceinline__ int rr_pos(int pa, int r, int m) {
+  int x = pa - 1 + r;  // < 2 (m - 1)
+  if (x >= m - 1) x -= m - 1;
+  return x + 1;
+}
+// v / h for v < 2^16 / h, with ih = ceil(2^16 / h) (h <= PW_MAXN / 2)
+__device__ __forceinline__ int div_small(int v, unsigned ih) { return (int)(((unsigned)v * ih) >> 16); }
+
 template <typename T, int NT>
 __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip_rel, RotWS<T>& rw,
                             const Team<NT>& tm) {
   const int h = m >> 1;
+  const unsigned ih = (65536u + h - 1) / h;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = 0, dg = 0;
     for (int e = tm.id; e < m * m; e += NT) {
@@ -390,8 +400,8 @@ __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
       if (tm.id < h) {
         // round-robin: position 0 fixed, positions 1..m-1 rotate by r
         const int pa = tm.id == 0 ? 0 : tm.id + 1, pb = tm.id == 0 ? 1 : m - tm.id;
-        int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
-        int q = (pb - 1 + r) % (m - 1) + 1;
+        int p = pa == 0 ? 0 : rr_pos(pa, r, m);
+        int q = rr_pos(pb, r, m);
         if (p > q) {
           const int x = p;
           p = q;
@@ -400,9 +410,15 @@ __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
         const T apq = A[p * m + q], app = A[p * m + p], aqq = A[q * m + q];
         T c = 1, s = 0, t = 0;
         if (apq != T(0) && jabs(apq) > skip_rel * (jabs(app) + jabs(aqq))) {
-          const T th = (aqq - app) / (T(2) * apq);
-          t = (th >= T(0) ? T(1) : T(-1)) / (jabs(th) + jsqrt(th * th + T(1)));
-          c = T(1) / jsqrt(t * t + T(1));
+          if constexpr (sizeof(T) == 4) {  // approximate quotients: the FP64 refinement follows
+            const float th = __fdividef(aqq - app, 2.f * apq);
+            t = copysignf(__fdividef(1.f, fabsf(th) + sqrtf(fmaf(th, th, 1.f))), th);
+            c = rsqrtf(fmaf(t, t, 1.f));
+          } else {
+            const T th = (aqq - app) / (T(2) * apq);
+            t = (th >= T(0) ? T(1) : T(-1)) / (jabs(th) + jsqrt(th * th + T(1)));
+            c = T(1) / jsqrt(t * t + T(1));
+          }
           s = t * c;
         }
         rw.p[tm.id] = p;
@@ -413,7 +429,7 @@ __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
       }
       tm.sync();
       for (int blk = tm.id; blk < h * h; blk += NT) {
-        const int a = blk / h, b = blk - a * h;
+        const int a = div_small(blk, ih), b = blk - a * h;
         const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
         if (a == b) {
           const T t = rw.t[a];
@@ -435,7 +451,7 @@ __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip
         }
       }
       for (int task = tm.id; task < m * h; task += NT) {
-        const int k = task / h, a = task - k * h;
+        const int k = div_small(task, ih), a = task - k * h;
         const int p = rw.p[a], q = rw.q[a];
         const T c = rw.c[a], s = rw.s[a];
         const T vp = V[k * m + p], vq = V[k * m + q];
@@ -457,14 +473,15 @@ template <int NT>
 __device__ void team_jacobi_refine(double* A, double* V, int m, int max_sweeps, double tau, RotWS<double>& rw,
                                    const Team<NT>& tm) {
   const int h = m >> 1;
+  const unsigned ih = (65536u + h - 1) / h;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool rotated = false;
     for (int r = 0; r < m - 1; ++r) {
       bool rot = false;
       if (tm.id < h) {
         const int pa = tm.id == 0 ? 0 : tm.id + 1, pb = tm.id == 0 ? 1 : m - tm.id;
-        int p = pa == 0 ? 0 : (pa - 1 + r) % (m - 1) + 1;
-        int q = (pb - 1 + r) % (m - 1) + 1;
+        int p = pa == 0 ? 0 : rr_pos(pa, r, m);
+        int q = rr_pos(pb, r, m);
         if (p > q) {
           const int x = p;
           p = q;
@@ -489,7 +506,7 @@ __device__ void team_jacobi_refine(double* A, double* V, int m, int max_sweeps, 
       rotated = true;
       tm.sync();
       for (int blk = tm.id; blk < h * h; blk += NT) {
-        const int a = blk / h, b = blk - a * h;
+        const int a = div_small(blk, ih), b = blk - a * h;
         const int pa = rw.p[a], qa = rw.q[a], pb = rw.p[b], qb = rw.q[b];
         const double ca = rw.c[a], sa = rw.s[a], cb = rw.c[b], sb = rw.s[b];
         const double x00 = A[pa * m + pb], x01 = A[pa * m + qb], x10 = A[qa * m + pb], x11 = A[qa * m + qb];
@@ -501,7 +518,7 @@ __device__ void team_jacobi_refine(double* A, double* V, int m, int max_sweeps, 
         A[qa * m + qb] = sb * y10 + cb * y11;
       }
       for (int task = tm.id; task < m * h; task += NT) {
-        const int k = task / h, a = task - k * h;
+        const int k = div_small(task, ih), a = task - k * h;
         const int p = rw.p[a], q = rw.q[a];
         const double c = rw.c[a], s = rw.s[a];
         const double vp = V[k * m + p], vq = V[k * m + q];
