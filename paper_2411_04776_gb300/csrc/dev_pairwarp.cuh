@@ -312,6 +312,15 @@ __device__ __forceinline__ double pair_hess_entry(const PairBarrier& pb, int I, 
   return pair_hess_compose(pb, I, J, hD_point(pb.dv, I, J));
 }
 
+// position of round-robin slot pa (1..m-1) in round r: slots 1..m-1 rotate by r
+__device__ __forceinline__ int rr_pos(int pa, int r, int m) {
+  int x = pa - 1 + r;  // < 2 (m - 1)
+  if (x >= m - 1) x -= m - 1;
+  return x + 1;
+}
+// v / h for v < 2^16 / h, with ih = ceil(2^16 / h) (h <= 12 here, v < 200)
+__device__ __forceinline__ int div_small(int v, unsigned ih) { return (int)(((unsigned)v * ih) >> 16); }
+
 // The block of the barrier Hessian on the point dofs fd[0, nf) into H (row stride m, rows and
 // columns nf..m-1 zero), by the threads of a team: the difference-vector Hessian of D is formed
 // once (Hdv: (3 nd)^2 scratch), every point entry is then a signed sum of its entries.  Entries
@@ -321,14 +330,15 @@ __device__ __forceinline__ void team_pair_block(const PairBarrier& pb, const int
                                                 double* H, const Team<NT>& tm) {
   const DV& o = pb.dv;
   const int n3 = 3 * o.nd;
+  const unsigned in3 = (65536u + n3 - 1) / n3, im = (65536u + m - 1) / m;
   for (int e = tm.id; e < n3 * n3; e += NT) {
-    const int r = e / n3, c = e - r * n3;
+    const int r = div_small(e, in3), c = e - r * n3;
     const int a = r < c ? r : c, b = r < c ? c : r;
     Hdv[e] = hD_dv(o, a / 3, a % 3, b / 3, b % 3);
   }
   tm.sync();
   for (int e = tm.id; e < m * m; e += NT) {
-    const int r = e / m, c = e - r * m;
+    const int r = div_small(e, im), c = e - r * m;
     const int i = r < c ? r : c, j = r < c ? c : r;
     double v = 0.0;
     if (j < nf) {
@@ -371,24 +381,15 @@ __device__ __forceinline__ double jsqrt(double v) { return sqrt(v); }
 // off-diagonal norm is at most rel_tol times the squared diagonal norm.  Rotations whose
 // off-diagonal entry is below skip_rel (|a_pp| + |a_qq|) are skipped (exact identity).
 // Called by every thread of the team.
-// position of round-robin slot pa (1..m-1) in round r: slots 1..m-1 rotate by r
-__device__ __forceinline__ int rr_pos(int pa, int r, int m) {
-  int x = pa - 1 + r;  // < 2 (m - 1)
-  if (x >= m - 1) x -= m - 1;
-  return x + 1;
-}
-// v / h for v < 2^16 / h, with ih = ceil(2^16 / h) (h <= PW_MAXN / 2)
-__device__ __forceinline__ int div_small(int v, unsigned ih) { return (int)(((unsigned)v * ih) >> 16); }
-
 template <typename T, int NT>
 __device__ void team_jacobi(T* A, T* V, int m, int max_sweeps, T rel_tol, T skip_rel, RotWS<T>& rw,
                             const Team<NT>& tm) {
   const int h = m >> 1;
-  const unsigned ih = (65536u + h - 1) / h;
+  const unsigned ih = (65536u + h - 1) / h, im = (65536u + m - 1) / m;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = 0, dg = 0;
     for (int e = tm.id; e < m * m; e += NT) {
-      const int i = e / m, j = e - i * m;
+      const int i = div_small(e, im), j = e - i * m;
       const T v = A[e];
       if (i == j) dg += v * v;
       else if (i < j) off += v * v;
@@ -563,6 +564,7 @@ __device__ __forceinline__ void upper_ij(int t, int m, int& i, int& j) {
 template <int NT>
 __device__ void team_psd_project(ProjWS& w, int n, const Team<NT>& tm) {
   const int m = n + (n & 1), mm = m * m, nu = m * (m + 1) / 2;
+  const unsigned im = (65536u + m - 1) / m;
   double mx = 0.0;
   for (int e = tm.id; e < mm; e += NT) mx = fmax(mx, fabs(w.H[e]));
   mx = tm.max(mx);
@@ -570,7 +572,7 @@ __device__ void team_psd_project(ProjWS& w, int n, const Team<NT>& tm) {
   const int ex = ilogb(mx);
   const double sc = ldexp(1.0, -ex);
   for (int e = tm.id; e < mm; e += NT) {
-    const int i = e / m, j = e - i * m;
+    const int i = div_small(e, im), j = e - i * m;
     const double v = w.H[e] * sc;
     w.H[e] = v;
     w.a32[e] = (float)v;
@@ -589,14 +591,14 @@ __device__ void team_psd_project(ProjWS& w, int n, const Team<NT>& tm) {
   }
   tm.sync();
   for (int e = tm.id; e < mm; e += NT) {  // B = X (3 I - T) / 2
-    const int i = e / m, j = e - i * m;
+    const int i = div_small(e, im), j = e - i * m;
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.X[i * m + k], w.T[k * m + j], acc);
     w.B[e] = 1.5 * w.X[e] - 0.5 * acc;
   }
   tm.sync();
   for (int e = tm.id; e < mm; e += NT) {  // T = A X
-    const int i = e / m, j = e - i * m;
+    const int i = div_small(e, im), j = e - i * m;
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc = fma(w.H[i * m + k], w.B[k * m + j], acc);
     w.T[e] = acc;
