@@ -106,6 +106,25 @@ def test_mixed_precision_trajectory_matches_oracle():
     assert errs.max() <= POS_TOL
 
 
+def test_forcing_terms_keep_the_minimiser():
+    """The loose PCG forcing term far from Newton convergence (0.1, the default) changes the
+    iterates but not the converged state: every step of the 10x13x4 gel pressed by the sphere
+    matches a fixed 1e-3 forcing term within the parity gate, with fewer PCG iterations."""
+    wl = W.small_gel_sphere(0)
+    loose = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL)
+    fixed = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, pcg_rel_tol_far=0.0)
+    it_loose = it_fixed = 0
+    for s in range(30):
+        assert loose.step(wl.poses[s], wl.dt) == 0
+        assert fixed.step(wl.poses[s], wl.dt) == 0
+        xl, _, fl, sl = loose.state()
+        xf, _, ff, sf = fixed.state()
+        it_loose += sl.pcg_iters
+        it_fixed += sf.pcg_iters
+        assert np.abs(xl - xf).max() <= POS_TOL
+    assert it_loose < it_fixed, (it_loose, it_fixed)
+
+
 def test_batch_equals_alone():
     wls = [W.small_gel_sphere(s) for s in range(3)]
     descs = [B.GelDesc.from_workload(w, newton_tol=PARITY_NEWTON_TOL) for w in wls]
