@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ double rhoj[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[2][PCG_MAXG];
   __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
@@ -222,32 +223,56 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   double x0 = 0, x1 = 0, x2 = 0, r0 = 0, r1 = 0, r2 = 0, u0 = 0, u1 = 0, u2 = 0, w0 = 0, w1 = 0, w2 = 0;
   double z0 = 0, z1 = 0, z2 = 0, q0 = 0, q1 = 0, q2 = 0, t0 = 0, t1 = 0, t2 = 0, p0 = 0, p1 = 0, p2 = 0;
   double m0 = 0, m1 = 0, m2 = 0;
-  // ---- init: r = b = -grad, x = 0, u = M^-1 r; |b|^2
+  // ---- init: r = b = -grad; start from x0 = rho p_prev, the minimiser of the quadratic model
+  // along the gel's previous Newton direction (one Galerkin step: rho = b.p / p.A p, 0 without
+  // one); the linear Newton contraction makes it a good start, and the A-norm error cannot grow
+  double xp0 = 0.0, xp1 = 0.0, xp2 = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (mine) {
     w = res_load<double>(d, s, d.vals, sv, sc, lane);
     for (int e = 0; e < 9; ++e) M[e] = d.Minv[9 * row + e];
     const double4_32a gr = d.grad[row];
     r0 = -gr.x; r1 = -gr.y; r2 = -gr.z;
+    if (!fixed) {
+      const double4_32a pv = d.p[row];
+      xp0 = pv.x; xp1 = pv.y; xp2 = pv.z;
+      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.p, a0, a1, a2);
+    }
+  }
+  if (has) {
+    const double bp = warp_sum(fma(r2, xp2, fma(r1, xp1, r0 * xp0)));
+    const double pw = warp_sum(fma(a2, xp2, fma(a1, xp1, a0 * xp0)));
+    const double bb = warp_sum(fma(r2, r2, fma(r1, r1, r0 * r0)));
+    if (lane == 0) {
+      dsm[4 * wid + 0] = bp;
+      dsm[4 * wid + 1] = pw;
+      dsm[4 * wid + 2] = bb;
+    }
+  }
+  res_post(d, c, dsm, 0, 3, 0, tot);
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  {
+    ResPrefetch pf;
+    res_prefetch(d, c, 0, 3, 0, pf);
+    res_finish(c, 0, 3, pf, tot);
+  }
+  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
+    bbj[q] = tot[q][2];
+    thj[q] = d.gv[c.g0 + q].eta2 * bbj[q];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[q][1], rho = tot[q][0] / pw;
+    rhoj[q] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
+  }
+  __syncthreads();
+  if (mine) {
+    const double rho = rhoj[j];
+    x0 = rho * xp0; x1 = rho * xp1; x2 = rho * xp2;
+    r0 = fma(-rho, a0, r0); r1 = fma(-rho, a1, r1); r2 = fma(-rho, a2, r2);
     u0 = fma(M[2], r2, fma(M[1], r1, M[0] * r0));
     u1 = fma(M[5], r2, fma(M[4], r1, M[3] * r0));
     u2 = fma(M[8], r2, fma(M[7], r1, M[6] * r0));
     d.u[row] = make_double4_32a(u0, u1, u2, 0.0);
   }
-  if (has) {
-    const double bb = warp_sum(fma(r2, r2, fma(r1, r1, r0 * r0)));
-    if (lane == 0) dsm[4 * wid + 3] = bb;
-  }
-  res_post(d, c, dsm, 3, 4, 0, tot);
+  // u complete before the SpMV; every CTA has read the start's sums before any reuses their slots
   if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
-  {
-    ResPrefetch pf;
-    res_prefetch(d, c, 3, 4, 0, pf);
-    res_finish(c, 3, 4, pf, tot);
-  }
-  for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
-    bbj[q] = tot[q][3];
-    thj[q] = d.gv[c.g0 + q].eta2 * bbj[q];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
-  }
   // ---- w = A u, m = M^-1 w; dot products of iteration 0
   if (has) {
     double ga = 0.0, de = 0.0, rr = 0.0;
