@@ -272,7 +272,8 @@ def roofline(prof, clocks, precision, kernel):
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "avg_launch_ms": avg_ms, "launches": ph["launches"],
                 "peak_note": "derived: FP64 (non-tensor) 4 FLOP/clk/SM x 152 SMs x max SM clock; "
-                             "achieved = algorithmic FLOP (18 per 3x3 block, 60 per row per iteration)"}
+                             "achieved = algorithmic FLOP (18 per 3x3 block, 60 per row per iteration; the single-gel "
+                             "solver adds its Galerkin start: one SpMV and 30 per row per solve)"}
     pk = measured_peaks()
     peak = float(pk.get("hbm_gbs") or 6800.0)
     achieved = (ph["bytes"] / launches) / (avg_ms * 1e-3) / 1e9 if ph["bytes"] else None

@@ -1757,9 +1757,13 @@ tx_status do_newton(tx_batch* b) {
   }
   std::vector<int> fin, fail;
   if (b->prof.on) {
+    // the FP64 resident solver's Galerkin start: one SpMV, three dot products and two updates
+    bool warm = !b->mixed && b->nparts > 0;
+    for (int k = 0; k < b->nparts; ++k) warm = warm && b->parts[k].res;
     for (int g : set) {
       const double it = b->gv_h[g].pcg_it;
       const GelInfo& G = b->gi[g];
+      if (warm) b->prof.flops[PR_PCG] += 18.0 * b->nnzb_real[g] + 30.0 * b->nfree[g];
       // per PCG iteration and row: SpMV 18 flops per 3x3 block, preconditioner 18, four
       // axpys 24, three dot products 18; mixed precision adds one FP64 residual SpMV per round
       const double rounds = b->mixed ? b->gv_h[g].rounds : 0.0;
