@@ -281,7 +281,8 @@ def roofline(prof, clocks, precision, kernel):
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "avg_launch_ms": avg_ms, "launches": ph["launches"],
             "peak_note": ("measured copy bandwidth (MEASURED_PEAKS.json)" if pk.get("hbm_gbs") else "fallback 6.8 TB/s")
-                         + "; achieved = algorithmic bytes of streaming iterations (40 B per block, 212 B per row)"}
+                         + "; achieved = algorithmic bytes of streaming iterations (40 B per block, 212 B per row; the "
+                            "single-gel solver adds its Galerkin start per solve)"}
 
 
 def pcg_kernel_name(precision, n_gels):

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
                                                                  int maxit, int refine_max, int wmax) {
   extern __shared__ double dyn[];
   __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], rhoj[PCG_MAXG];
   __shared__ float alj[PCG_MAXG], bej[PCG_MAXG], gprf[PCG_MAXG], aprf[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[2][PCG_MAXG], itj[PCG_MAXG];
   __shared__ int s_fail, s_any;
@@ -401,32 +401,61 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
   double g0 = 0, g1 = 0, g2 = 0, R0 = 0, R1 = 0, R2 = 0, P0 = 0, P1 = 0, P2 = 0;  // FP64: grad, r, p
   float M[9];
   for (int e = 0; e < 9; ++e) M[e] = 0.f;
+  // start from p = rho p_prev, the minimiser of the quadratic model along the gel's previous
+  // Newton direction (FP64 arithmetic on the FP32 matrix, as the residual refinement)
+  double xp0 = 0.0, xp1 = 0.0, xp2 = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (mine) {
     w = res_load<float>(d, s, d.vals32, sv, sc, lane);
     for (int e = 0; e < 9; ++e) M[e] = d.Minv32[9 * row + e];
     const double4_32a gr = d.grad[row];
     g0 = gr.x; g1 = gr.y; g2 = gr.z;
     R0 = -g0; R1 = -g1; R2 = -g2;
+    if (!fixed) {
+      const double4_32a pv = d.p[row];
+      xp0 = pv.x; xp1 = pv.y; xp2 = pv.z;
+      res_spmv<float, double4_32a, double>(sv, sc, w, lane, d.p, a0, a1, a2);
+    }
   }
   if (has) {
+    const double bp = warp_sum(fma(R2, xp2, fma(R1, xp1, R0 * xp0)));
+    const double pw = warp_sum(fma(a2, xp2, fma(a1, xp1, a0 * xp0)));
     const double bb = warp_sum(fma(R2, R2, fma(R1, R1, R0 * R0)));
     if (lane == 0) {
-      dsm[4 * wid + 3] = bb;
+      dsm[4 * wid + 0] = bp;
+      dsm[4 * wid + 1] = pw;
       dsm[4 * wid + 2] = bb;
     }
   }
-  res_post(d, c, dsm, 2, 4, 0, tot);
+  res_post(d, c, dsm, 0, 3, 0, tot);
   if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
   {
     ResPrefetch pf;
-    res_prefetch(d, c, 2, 4, 0, pf);
-    res_finish(c, 2, 4, pf, tot);
+    res_prefetch(d, c, 0, 3, 0, pf);
+    res_finish(c, 0, 3, pf, tot);
   }
   for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
-    bbj[q] = tot[q][3];
+    bbj[q] = tot[q][2];
     thj[q] = d.gv[c.g0 + q].eta2 * bbj[q];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[q][1], rho = tot[q][0] / pw;
+    rhoj[q] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
   }
   __syncthreads();
+  if (mine) {
+    const double rho = rhoj[j];
+    P0 = rho * xp0; P1 = rho * xp1; P2 = rho * xp2;
+    R0 = fma(-rho, a0, R0); R1 = fma(-rho, a1, R1); R2 = fma(-rho, a2, R2);
+  }
+  if (has) {  // |r|^2 at the start, through the other exchange set (the first one may still be read)
+    const double rr = warp_sum(fma(R2, R2, fma(R1, R1, R0 * R0)));
+    if (lane == 0) dsm[4 * wid + 2] = rr;
+  }
+  res_post(d, c, dsm, 2, 3, 1, tot);
+  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  {
+    ResPrefetch pf;
+    res_prefetch(d, c, 2, 3, 1, pf);
+    res_finish(c, 2, 3, pf, tot);
+  }
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();

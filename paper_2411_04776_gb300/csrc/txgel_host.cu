@@ -1437,7 +1437,9 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
     for (const int2& r : rng) max_slices = std::max(max_slices, r.y - r.x);
     for (const int4& q : grp) max_nc = std::max(max_nc, q.y);
     const int occ_res = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
-    res = occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC;
+    // a multi-CTA group reduces three quantities at once, one warp each: two slice warps and the
+    // control warp at least
+    res = occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC && (max_nc == 1 || max_slices >= 2);
     const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
     if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
     if (attempt > 400) {
@@ -1757,13 +1759,17 @@ tx_status do_newton(tx_batch* b) {
   }
   std::vector<int> fin, fail;
   if (b->prof.on) {
-    // the FP64 resident solver's Galerkin start: one SpMV, three dot products and two updates
-    bool warm = !b->mixed && b->nparts > 0;
+    // the resident solvers' Galerkin start: one SpMV (FP64 arithmetic), three dot products and two
+    // updates per solve
+    bool warm = b->nparts > 0;
     for (int k = 0; k < b->nparts; ++k) warm = warm && b->parts[k].res;
     for (int g : set) {
       const double it = b->gv_h[g].pcg_it;
       const GelInfo& G = b->gi[g];
-      if (warm) b->prof.flops[PR_PCG] += 18.0 * b->nnzb_real[g] + 30.0 * b->nfree[g];
+      if (warm) {
+        b->prof.flops[PR_PCG] += 18.0 * b->nnzb_real[g] + 30.0 * b->nfree[g];
+        b->prof.bytes[PR_PCG] += (b->mixed ? 40.0 : 76.0) * b->nnzb_real[g] + 96.0 * G.nv;
+      }
       // per PCG iteration and row: SpMV 18 flops per 3x3 block, preconditioner 18, four
       // axpys 24, three dot products 18; mixed precision adds one FP64 residual SpMV per round
       const double rounds = b->mixed ? b->gv_h[g].rounds : 0.0;
