@@ -240,6 +240,23 @@ def run_gpu(args, rank, world, e2e=True):
                 n=n, wls=wls, h2d=len(wls) * (7 * 8 + 8), d2h=2 * n * 3 * 8 + len(wls) * (3 * 8 + 96))
 
 
+def iteration_histogram(stats):
+    """Per-step Newton and PCG iteration counts of the timed steps: percentiles and binned counts."""
+    if not stats:
+        return None
+    out = {}
+    for key, name, edges in (("newton_iters", "newton", [0, 5, 10, 20, 50, 100, 200]),
+                             ("pcg_iters", "pcg", [0, 100, 500, 1000, 2000, 5000, 10000])):
+        v = np.array([s[key] for s in stats], dtype=float)
+        bins = []
+        for a, b in zip(edges, edges[1:] + [None]):
+            inside = (v >= a) & (v < b) if b is not None else (v >= a)
+            bins.append({"from": a, "to": b, "steps": int(inside.sum())})
+        out[name] = {"p50": float(np.percentile(v, 50)), "p90": float(np.percentile(v, 90)),
+                     "max": float(v.max()), "bins": bins}
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -428,6 +445,7 @@ def main():
         "roofline": roofline(r["prof"], r["clocks"], args.precision, pcg_kernel_name(args.precision, ng)),
         "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
         "gpu_launches": r["prof"]["kernel_launches"],
+        "iteration_histogram": iteration_histogram(r["stats"]),
         "clocks": r["clocks"],
         "e2e": {"value": world * ng * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},

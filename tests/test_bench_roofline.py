@@ -44,3 +44,13 @@ def test_traffic_follows_the_source_hash():
         current = bench.source_hash(e["files"]) == e["source_hash"]
         assert r["traffic"] == (e["bytes_per_launch"] if current else None), kernel
         assert os.path.exists(os.path.join(ROOT, "profiles", e["capture"]))
+
+
+def test_iteration_histogram_counts_every_step():
+    st = [{"newton_iters": n, "pcg_iters": p} for n, p in [(3, 50), (25, 700), (52, 1200), (300, 10650), (25, 800)]]
+    h = bench.iteration_histogram(st)
+    for name in ("newton", "pcg"):
+        assert sum(b["steps"] for b in h[name]["bins"]) == len(st)
+    assert h["newton"]["p50"] == 25.0 and h["newton"]["max"] == 300.0
+    assert h["pcg"]["bins"][-1] == {"from": 10000, "to": None, "steps": 1}
+    assert bench.iteration_histogram([]) is None
