@@ -78,6 +78,10 @@ def _declare(L):
     L.or_pcg_csr.restype = ctypes.c_int
     L.or_pcg_csr.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_double, ctypes.c_int]
     L.or_pair_counts.argtypes = [ctypes.c_void_p, dp, dp, ip]
+    L.or_set_friction.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+    L.or_friction_pair.restype = ctypes.c_int
+    L.or_friction_pair.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
     return L
 
 
@@ -102,7 +106,8 @@ class OracleGel:
 
     def __init__(self, verts, tets, dirichlet, material, ind_verts, ind_tris, pose0, dhat=1e-4,
                  kappa=0.0, newton_tol=1e-5, pcg_tol=1e-10, gravity=(0.0, 0.0, 0.0),
-                 newton_max=200, pcg_max=200000, ls_max=80, accd_max=1000000, split_depth=4):
+                 newton_max=200, pcg_max=200000, ls_max=80, accd_max=1000000, split_depth=4,
+                 friction=0.0, eps_v=1e-3):
         L = lib()
         self.N = int(len(verts))
         self.M = int(len(ind_verts))
@@ -121,6 +126,8 @@ class OracleGel:
                               fpp, ipp, ctypes.byref(st))
         if not self._h:
             raise OracleError(st.value)
+        if friction > 0.0:  # IPC lagged friction (coefficient, velocity threshold [m/s])
+            L.or_set_friction(self._h, float(friction), float(eps_v))
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -256,6 +263,21 @@ def accd(kind, P, dP, s=0.1, tc=1.0, maxit=1000000):
     dP, dPp = _d(dP)
     r = lib().or_accd(int(kind), Pp, dPp, s, tc, maxit, ctypes.byref(t))
     return r, t.value
+
+
+def friction_pair(kind, Plag, Pnow, dhat, kappa, eps_x, mu, eh):
+    """Lagged friction of one pair (IPC, Li et al. 2020 Sec. 5): set up from the points at the
+    step start, evaluated at the current points.  Returns (active, D, dD/dP (12), d2D/dP2 (12x12),
+    lagged normal force)."""
+    e = ctypes.c_double(0.0)
+    lam = ctypes.c_double(0.0)
+    g = np.zeros(12)
+    H = np.zeros(144)
+    Plag, Pl = _d(Plag)
+    Pnow, Pn = _d(Pnow)
+    a = lib().or_friction_pair(int(kind), Pl, Pn, dhat, kappa, eps_x, mu, eh, ctypes.byref(e), _d(g)[1],
+                               _d(H)[1], ctypes.byref(lam))
+    return a, e.value, g, H.reshape(12, 12), lam.value
 
 
 def psd_project(A):

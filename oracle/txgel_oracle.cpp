@@ -22,6 +22,16 @@
 //   b(d)   = -(d - dhat)^2 ln(d / dhat)
 //   m_k    = IPC edge-edge mollifier (1 for point-triangle pairs)
 //
+// plus, when a friction coefficient mu_f > 0 is set, IPC's lagged dissipative friction (Li et
+// al. 2020, Sec. 5): for every pair in contact at the start of the (sub)step (gel at x_n,
+// indenter at its previous pose)
+//   D_k(x) = mu_f lambda_k f0(|u_k(x)|),  u_k = T_k^T (relative displacement of the closest points
+//   over the step), lambda_k = kappa m_k |b'(d_k)| (the pair's normal force), T_k an orthonormal
+//   basis of the tangent plane, all taken at the start and held fixed (lagged) during the solve;
+//   f0(y) = -y^3 / (3 e^2) + y^2 / e + e / 3 below e = eps_v h and f0(y) = y above (f0' = f1 is 1
+//   when sliding faster than eps_v, so the force is mu_f lambda_k: Coulomb; below it a stiff
+//   spring: static friction).
+//
 // minimised by projected Newton: per-element PSD-projected Hessians, direction from the linear
 // system on the free degrees of freedom, step capped by additive CCD (ACCD, Li et al. 2021 "C-IPC")
 // and by det F > 0, backtracking on E.  Readings of points the paper leaves open are marked
@@ -660,6 +670,9 @@ struct Gel {
   double dhat = 1e-4, kappa = 0, newton_tol = 1e-5, pcg_tol = 1e-10, bbox_diag = 0;
   double grav[3] = {0, 0, 0};
   int newton_max = 200, pcg_max = 100000, ls_max = 60, accd_max = 100000, split_depth = 4;
+  double fric_mu = 0.0, fric_epsv = 1e-3;  // friction coefficient (0: none), velocity threshold [m/s]
+  std::vector<struct FricPair> fric;        // lagged friction pairs of the running (sub)step
+  double fric_eh = 0.0;                     // eps_v h of the running (sub)step
   // state
   std::vector<double> x, v;
   double pose[7] = {1, 0, 0, 0, 0, 0, 0};
@@ -781,14 +794,147 @@ std::vector<PairRef> candidate_pairs(const Gel& G, const double* x0, const doubl
 
 int kind_of(const PairRef& pr) { return pr.type == 2 ? K_EE : K_PT; }
 
+// ---------------- lagged friction ----------------
+struct FricPair {
+  PairRef pr;
+  double w[4];        // closest-point weights: relative displacement = sum_k w[k] (P_k - Plag_k)
+  double T[3][2];     // orthonormal tangent basis (columns) at the lagged state
+  double lam;         // lagged normal force magnitude kappa m |b'(d)|
+  double Plag[4][3];  // the pair's points at the lagged state
+};
+
+// lagged data of one pair from its points at the start of the step; false if not in contact
+bool fric_setup(int kind, const double P[4][3], double dhat, double kappa, double eps_x, FricPair* f) {
+  const DType ty = classify(kind, P);
+  const double D = d2_of_type(ty, P);
+  if (!(D > 0.0) || !(D < dhat * dhat)) return false;
+  const double d = std::sqrt(D);
+  double m = 1.0;
+  if (kind == K_EE) {  // the mollifier at the lagged state scales the normal force
+    double ea[3], eb[3], n[3];
+    sub3(P[1], P[0], ea);
+    sub3(P[3], P[2], eb);
+    cross3(ea, eb, n);
+    const double c = dot3(n, n);
+    if (c < eps_x) m = (2.0 - c / eps_x) * (c / eps_x);
+  }
+  const double bp = -2.0 * (d - dhat) * std::log(d / dhat) - (d - dhat) * (d - dhat) / d;  // b'(d) < 0
+  f->lam = kappa * m * std::fabs(bp);
+  for (int k = 0; k < 4; ++k) {
+    f->w[k] = 0.0;
+    for (int c = 0; c < 3; ++c) f->Plag[k][c] = P[k][c];
+  }
+  double nrm[3];  // a normal of the tangent plane
+  const int* i = ty.i;
+  if (ty.f == F_PP) {
+    f->w[i[0]] = 1.0;
+    f->w[i[1]] = -1.0;
+    sub3(P[i[0]], P[i[1]], nrm);
+  } else if (ty.f == F_PE) {
+    double e[3], w[3];
+    sub3(P[i[2]], P[i[1]], e);
+    sub3(P[i[0]], P[i[1]], w);
+    const double t = dot3(w, e) / dot3(e, e);
+    f->w[i[0]] = 1.0;
+    f->w[i[1]] = -(1.0 - t);
+    f->w[i[2]] = -t;
+    for (int c = 0; c < 3; ++c) nrm[c] = P[i[0]][c] - ((1.0 - t) * P[i[1]][c] + t * P[i[2]][c]);
+  } else if (ty.f == F_PT) {
+    double e1[3], e2[3], w[3];
+    sub3(P[i[2]], P[i[1]], e1);
+    sub3(P[i[3]], P[i[1]], e2);
+    sub3(P[i[0]], P[i[1]], w);
+    const double a = dot3(e1, e1), b = dot3(e1, e2), c = dot3(e2, e2), dd = dot3(e1, w), ff = dot3(e2, w);
+    const double det = a * c - b * b;
+    const double l1 = (c * dd - b * ff) / det, l2 = (a * ff - b * dd) / det;
+    f->w[i[0]] = 1.0;
+    f->w[i[1]] = -(1.0 - l1 - l2);
+    f->w[i[2]] = -l1;
+    f->w[i[3]] = -l2;
+    cross3(e1, e2, nrm);
+  } else {
+    double u[3], v[3], w[3];
+    sub3(P[i[1]], P[i[0]], u);
+    sub3(P[i[3]], P[i[2]], v);
+    sub3(P[i[0]], P[i[2]], w);
+    const double a = dot3(u, u), b = dot3(u, v), c = dot3(v, v), dd = dot3(u, w), e = dot3(v, w);
+    const double den = a * c - b * b;
+    const double s = (b * e - c * dd) / den, t = (a * e - b * dd) / den;
+    f->w[i[0]] = 1.0 - s;
+    f->w[i[1]] = s;
+    f->w[i[2]] = -(1.0 - t);
+    f->w[i[3]] = -t;
+    cross3(u, v, nrm);
+  }
+  const double nn = std::sqrt(dot3(nrm, nrm));
+  for (int c = 0; c < 3; ++c) nrm[c] /= nn;
+  // first tangent: the coordinate axis least aligned with the normal, made orthogonal to it
+  int ax = 0;
+  for (int c = 1; c < 3; ++c)
+    if (std::fabs(nrm[c]) < std::fabs(nrm[ax])) ax = c;
+  double t1[3] = {0.0, 0.0, 0.0}, t2[3];
+  t1[ax] = 1.0;
+  const double pn = dot3(t1, nrm);
+  for (int c = 0; c < 3; ++c) t1[c] -= pn * nrm[c];
+  const double n1 = std::sqrt(dot3(t1, t1));
+  for (int c = 0; c < 3; ++c) t1[c] /= n1;
+  cross3(nrm, t1, t2);
+  for (int c = 0; c < 3; ++c) {
+    f->T[c][0] = t1[c];
+    f->T[c][1] = t2[c];
+  }
+  return true;
+}
+
+// f0 as a function of s = |u|^2 (smooth at s = 0): value, d/ds, d2/ds2
+void fric_f0_s(double s, double eh, double* g0, double* g1, double* g2) {
+  const double y = std::sqrt(s);
+  if (y >= eh) {
+    *g0 = y;
+    *g1 = 0.5 / y;
+    *g2 = -0.25 / (y * s);
+    return;
+  }
+  *g0 = -s * y / (3.0 * eh * eh) + s / eh + eh / 3.0;
+  *g1 = -0.5 * y / (eh * eh) + 1.0 / eh;
+  *g2 = s > 0.0 ? -0.25 / (y * eh * eh) : 0.0;  // times (ds)^2 = 4 (u.du)^2, which is 0 at s = 0
+}
+
+double fric_value(double s, double eh) {
+  double a, b, c;
+  fric_f0_s(s, eh, &a, &b, &c);
+  return a;
+}
+template <int N>
+AD<N> fric_value(const AD<N>& s, double eh) {
+  double a, b, c;
+  fric_f0_s(s.v, eh, &a, &b, &c);
+  return ad_chain(s, a, b, c);
+}
+
+// D = mu lambda f0(|T^T sum_k w_k (P_k - Plag_k)|) for the pair's current points P
+template <class T>
+T fric_energy(const FricPair& f, const T P[4][3], double mu, double eh) {
+  T dl[3];
+  for (int c = 0; c < 3; ++c) {
+    dl[c] = f.w[0] * (P[0][c] - f.Plag[0][c]);
+    for (int k = 1; k < 4; ++k) dl[c] = dl[c] + f.w[k] * (P[k][c] - f.Plag[k][c]);
+  }
+  T u0 = dl[0] * f.T[0][0] + dl[1] * f.T[1][0] + dl[2] * f.T[2][0];
+  T u1 = dl[0] * f.T[0][1] + dl[1] * f.T[1][1] + dl[2] * f.T[2][1];
+  T s = u0 * u0 + u1 * u1;
+  return (mu * f.lam) * fric_value(s, eh);
+}
+
 // ---------------- energy ----------------
 struct EnergyParts {
   double inertia, elastic, barrier, min_d;
   int active;
+  double friction;
 };
 
 EnergyParts energy(const Gel& G, const double* x, const double* xt, double h, const double* IW) {
-  EnergyParts e{0, 0, 0, INF, 0};
+  EnergyParts e{0, 0, 0, INF, 0, 0};
   for (int i = 0; i < G.N; ++i) {
     double s = 0.0;
     for (int c = 0; c < 3; ++c) s += (x[3 * i + c] - xt[3 * i + c]) * (x[3 * i + c] - xt[3 * i + c]);
@@ -820,10 +966,19 @@ EnergyParts energy(const Gel& G, const double* x, const double* xt, double h, co
     e.active++;
     e.barrier += G.kappa * pair_barrier<double>(kind, ty, P, G.dhat, pair_eps_x(G, pr));
   }
+  for (const FricPair& f : G.fric) {  // lagged friction (empty unless mu_f > 0)
+    double P[4][3];
+    int gi[4];
+    pair_points(G, x, IW, f.pr, P, gi);
+    e.friction += fric_energy<double>(f, P, G.fric_mu, G.fric_eh);
+  }
   return e;
 }
 
-double total(const EnergyParts& e) { return e.inertia + e.elastic + e.barrier; }
+double total(const EnergyParts& e) {
+  const double s = e.inertia + e.elastic + e.barrier;
+  return e.friction != 0.0 ? s + e.friction : s;
+}
 
 // ---------------- gradient and projected Hessian ----------------
 struct Triplet {
@@ -890,6 +1045,34 @@ void assemble(const Gel& G, const double* x, const double* xt, double h, const d
       double gv = G.kappa * b.g[fidx[r]];
       grad[gr] += gv;
       fc[cr] -= gv;
+      for (int c = 0; c < nf; ++c) {
+        int kc = fidx[c] / 3, cc = fidx[c] % 3;
+        add(gr, 3 * gi[kc] + cc, Hf[r * nf + c]);
+      }
+    }
+  }
+  // lagged friction: convex in u, so its Hessian is PSD as it stands (projected all the same)
+  for (const FricPair& f : G.fric) {
+    double P[4][3];
+    int gi[4];
+    pair_points(G, x, IW, f.pr, P, gi);
+    AD<12> Pv[4][3];
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) Pv[k][c] = ad_var<12>(P[k][c], 3 * k + c);
+    AD<12> D = fric_energy<AD<12>>(f, Pv, G.fric_mu, G.fric_eh);
+    int fidx[12], nf = 0;
+    for (int k = 0; k < 4; ++k)
+      if (gi[k] >= 0)
+        for (int c = 0; c < 3; ++c) fidx[nf++] = 3 * k + c;
+    std::vector<double> Hf(nf * nf);
+    for (int r = 0; r < nf; ++r)
+      for (int c = 0; c < nf; ++c) Hf[r * nf + c] = D.h[fidx[r]][fidx[c]];
+    if (project) psd_project(nf, Hf.data());
+    for (int r = 0; r < nf; ++r) {
+      int kr = fidx[r] / 3, cr = fidx[r] % 3;
+      int gr = 3 * gi[kr] + cr;
+      grad[gr] += D.g[fidx[r]];
+      fc[cr] -= D.g[fidx[r]];
       for (int c = 0; c < nf; ++c) {
         int kc = fidx[c] / 3, cc = fidx[c] % 3;
         add(gr, 3 * gi[kc] + cc, Hf[r * nf + c]);
@@ -996,7 +1179,7 @@ int min_toi(const Gel& G, const double* x0, const double* dx, const double* I0, 
 }
 
 // ---------------- Newton solve of one (sub)step ----------------
-int newton_solve(Gel& G, double h, const double* IW) {
+int newton_iterate(Gel& G, double h, const double* IW) {
   int n3 = 3 * G.N;
   std::vector<double> xn = G.x, xt(n3);
   for (int i = 0; i < G.N; ++i)
@@ -1074,6 +1257,26 @@ int newton_solve(Gel& G, double h, const double* IW) {
   return ERR_NEWTON_MAXIT;
 }
 
+// Newton solve of one (sub)step with the indenter at IW; with friction, the lagged pairs are
+// taken first at the step's start (gel at x_n, indenter at I0) and dropped afterwards
+int newton_solve(Gel& G, double h, const double* I0, const double* IW) {
+  G.fric.clear();
+  if (G.fric_mu > 0.0) {
+    G.fric_eh = G.fric_epsv * h;
+    for (const PairRef& pr : candidate_pairs(G, G.x.data(), G.x.data(), I0, I0, G.dhat)) {
+      double P[4][3];
+      int gi[4];
+      pair_points(G, G.x.data(), I0, pr, P, gi);
+      FricPair f;
+      f.pr = pr;
+      if (fric_setup(kind_of(pr), P, G.dhat, G.kappa, pair_eps_x(G, pr), &f)) G.fric.push_back(f);
+    }
+  }
+  const int s = newton_iterate(G, h, IW);
+  G.fric.clear();
+  return s;
+}
+
 // feasibility of moving the indenter from I0 to I1 with the gel fixed at its current x
 bool placement_ok(const Gel& G, const double* I0, const double* I1, int* err) {
   std::vector<double> dI(3 * G.M), zx(3 * G.N, 0.0);
@@ -1122,7 +1325,7 @@ int substep(Gel& G, const double pa[7], const double pb[7], double dt, int depth
     return substep(G, pm, pb, 0.5 * dt, depth + 1);
   }
   std::vector<double> xn = G.x;
-  int s = newton_solve(G, dt, I1.data());
+  int s = newton_solve(G, dt, I0.data(), I1.data());
   if (s != OK) {
     G.x = xn;
     return s;
@@ -1487,6 +1690,41 @@ int or_accd(int kind, const double* Pf, const double* dPf, double s, double tc, 
 }
 
 void or_psd_project(int n, double* A) { psd_project(n, A); }
+
+// friction coefficient (0: no friction, the default) and velocity threshold eps_v [m/s]
+void or_set_friction(void* g, double mu, double eps_v) {
+  Gel& G = *static_cast<Gel*>(g);
+  G.fric_mu = mu;
+  G.fric_epsv = eps_v;
+}
+
+// Lagged friction of one pair: setup from the points Plag at the start of the step (normal
+// force from kappa, dhat, eps_x), then D, dD/dP (12) and d2D/dP2 (144) at the points Pnow;
+// eh = eps_v h.  Returns 1 if the pair is in contact at the start (else 0 and zeros), and the
+// lagged normal force in *lam.
+int or_friction_pair(int kind, const double* Plag, const double* Pnow, double dhat, double kappa,
+                     double eps_x, double mu, double eh, double* e, double* g, double* H, double* lam) {
+  double P0[4][3];
+  AD<12> Pv[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int c = 0; c < 3; ++c) {
+      P0[k][c] = Plag[3 * k + c];
+      Pv[k][c] = ad_var<12>(Pnow[3 * k + c], 3 * k + c);
+    }
+  FricPair f;
+  *e = 0.0;
+  *lam = 0.0;
+  for (int i = 0; i < 12; ++i) g[i] = 0.0;
+  for (int i = 0; i < 144; ++i) H[i] = 0.0;
+  if (!fric_setup(kind, P0, dhat, kappa, eps_x, &f)) return 0;
+  const AD<12> D = fric_energy<AD<12>>(f, Pv, mu, eh);
+  *e = D.v;
+  *lam = f.lam;
+  for (int i = 0; i < 12; ++i) g[i] = D.g[i];
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 12; ++j) H[12 * i + j] = D.h[i][j];
+  return 1;
+}
 
 void or_eigh(int n, const double* A, double* w, double* V) {
   std::vector<double> M(A, A + n * n), ww, VV;

@@ -521,3 +521,99 @@ def test_hertz_sphere_indentation_coarse():
     # the u^(3/2) law between the last two loads
     expo = math.log(F[-1] / F[-2]) / math.log(u[-1] / u[-2])
     assert 1.35 < expo < 1.65, expo
+
+
+# ------------------------------------------------------------------ lagged friction
+# IPC's lagged dissipative friction (Li et al. 2020, Sec. 5): D = mu lambda f0(|u|), u the
+# tangential relative displacement of the closest points over the step, lambda the pair's normal
+# force at the step start.  f1 = f0' is 1 above eps_v h (Coulomb) and -y^2/(eps_v h)^2 + 2y/(eps_v h)
+# below it (static friction as a stiff spring).
+def _friction_pair_points(kind, rng, d0):
+    """Lagged points of a pair at distance d0 with face-interior (PT) or edge-interior (EE)
+    closest points, randomly rotated and shifted."""
+    R = rand_rot(rng)
+    if kind == 0:
+        P = np.array([[0.05, 0.02, 0.0], [-1.0, -0.8, 0.0], [1.2, -0.6, 0.0], [0.1, 1.1, 0.0]]) * 1e-3
+        P[0, 2] = d0
+    else:
+        P = np.array([[-1.0, 0.1, 0.0], [1.1, -0.2, 0.0], [0.2, -1.0, 0.0], [-0.1, 1.2, 0.0]]) * 1e-3
+        P[2:, 2] = d0
+    return P @ R.T + rng.normal(size=3) * 1e-3
+
+
+def test_friction_force_is_coulomb_when_sliding_and_a_spring_when_sticking():
+    dhat, kappa, mu, eh = 1e-4, 30.0, 0.4, 1e-5
+    P = np.array([[0.05e-3, 0.02e-3, 0.3 * dhat], [-1e-3, -0.8e-3, 0.0], [1.2e-3, -0.6e-3, 0.0],
+                  [0.1e-3, 1.1e-3, 0.0]])
+    # the lagged normal force is the barrier's: kappa |db/dx| on the point (unit distance gradient)
+    _, _, gb, _ = O.pair_barrier(0, P, dhat)
+    lam_barrier = kappa * np.linalg.norm(gb[:3])
+    for du in (np.array([3e-5, -2e-5, 0.0]), np.array([1e-8, 2e-8, 0.0]), np.array([4e-6, 3e-6, 0.0])):
+        Pn = P.copy()
+        Pn[0] += du
+        a, e, g, H, lam = O.friction_pair(0, P, Pn, dhat, kappa, 0.0, mu, eh)
+        assert a == 1 and abs(lam - lam_barrier) <= 1e-10 * lam_barrier
+        f = -g[:3]
+        y = np.linalg.norm(du)
+        f1 = 1.0 if y >= eh else 2 * y / eh - (y / eh) ** 2
+        assert abs(np.linalg.norm(f) - mu * lam * f1) <= 1e-10 * mu * lam * f1
+        # opposite to the slip, in the tangent plane
+        assert abs(np.dot(f, du) + np.linalg.norm(f) * y) <= 1e-10 * np.linalg.norm(f) * y
+        assert abs(f[2]) <= 1e-12 * np.linalg.norm(f)
+        # the triangle takes the reaction
+        assert np.abs(g.reshape(4, 3).sum(0)).max() <= 1e-12 * np.abs(g).max()
+    # no contact at the step start: no friction
+    Pfar = P.copy()
+    Pfar[0, 2] = 1.5 * dhat
+    assert O.friction_pair(0, Pfar, Pfar + 1e-6, dhat, kappa, 0.0, mu, eh)[0] == 0
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_friction_central_differences(kind):
+    rng = np.random.default_rng(11 + kind)
+    dhat, kappa, mu, eh = 1e-4, 30.0, 0.3, 2e-5
+    for trial in range(4):
+        P = _friction_pair_points(kind, rng, rng.uniform(0.2, 0.8) * dhat)
+        for scale in (0.2 * eh, 5 * eh):  # sticking and sliding
+            Pn = P + rng.normal(size=P.shape) * scale
+            a, e, g, H, lam = O.friction_pair(kind, P, Pn, dhat, kappa, 0.0, mu, eh)
+            assert a == 1
+            h = 1e-9
+            gfd = np.zeros(12)
+            Hfd = np.zeros((12, 12))
+            for i in range(12):
+                dp = np.zeros(12)
+                dp[i] = h
+                ep = O.friction_pair(kind, P, Pn + dp.reshape(4, 3), dhat, kappa, 0.0, mu, eh)
+                em = O.friction_pair(kind, P, Pn - dp.reshape(4, 3), dhat, kappa, 0.0, mu, eh)
+                gfd[i] = (ep[1] - em[1]) / (2 * h)
+                Hfd[:, i] = (ep[2] - em[2]) / (2 * h)
+            assert np.abs(g - gfd).max() <= 1e-6 * np.abs(g).max()
+            assert np.abs(H - Hfd).max() <= 1e-6 * np.abs(H).max()
+            # convex: the Hessian of the lagged friction needs no projection
+            assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() >= -1e-9 * np.abs(H).max()
+
+
+def test_flat_plate_slides_with_coulomb_force():
+    """A rigid flat plate pressed on the gel top and slid along +x faster than eps_v: once the gel
+    top has sheared up to the friction limit, the tangential contact force is mu times the normal
+    force (every contact normal is vertical); without friction the tangential force vanishes."""
+    gel = W.gel_grid(6, 6, 3, (0.01, 0.01, 0.003))
+    L = 0.03
+    plate = W.Indenter(np.array([[-L, -L, 0.0], [L, -L, 0.0], [L, L, 0.0], [-L, L, 0.0]]),
+                       np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32), "plate")
+    p0, poses = W.press_slide_poses(plate, gel, (0.005, 0.005), 0.15e-3, 6, slide=0.9e-3, n_slide=18)
+    wl = W.Workload("plate", gel, plate, p0, poses, W.DT)
+    ratios = {}
+    for mu in (0.0, 0.5):
+        og = O.OracleGel.from_workload(wl, newton_tol=1e-7, friction=mu, eps_v=1e-3)
+        for s in range(len(poses)):
+            assert og.step(poses[s], wl.dt)["status"] == 0
+        _, _, fc, _ = og.state()
+        assert fc[2] < 0
+        ratios[mu] = (fc[0] / -fc[2], fc[1] / -fc[2])
+    # frictionless: only the plate diagonal's edge-edge pairs tilt with the gel top (1e-5 here)
+    assert abs(ratios[0.0][0]) <= 1e-4 and abs(ratios[0.0][1]) <= 1e-4
+    # with friction (0.5014 / -0.0012 here: the normal forces are lagged by a step and the gel
+    # top still creeps sideways a little as it shears)
+    assert abs(ratios[0.5][0] - 0.5) <= 0.01 and abs(ratios[0.5][1]) <= 5e-3
