@@ -451,9 +451,15 @@ def main():
                 "d2h_bytes_per_step": r["d2h"]},
     }
     if world == 1 and args.workload == "mini" and args.batched_gels > 0:
-        line["batched_mixed"] = batched_mixed(args)
+        try:  # a companion measurement: its failure is reported, the main line still prints
+            line["batched_mixed"] = batched_mixed(args)
+        except Exception as e:  # noqa: BLE001
+            line["batched_mixed"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        try:
+            line["cpu_baseline"] = cpu_baseline(args)
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
     print(json.dumps(line))
 
 
