@@ -79,6 +79,9 @@ def _declare(L):
     L.or_pcg_csr.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_double, ctypes.c_int]
     L.or_pair_counts.argtypes = [ctypes.c_void_p, dp, dp, ip]
     L.or_set_friction.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+    L.or_step_attached.restype = ctypes.c_int
+    L.or_step_attached.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ip, dp]
+    L.or_set_case_pose.argtypes = [ctypes.c_void_p, dp]
     L.or_friction_pair.restype = ctypes.c_int
     L.or_friction_pair.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
@@ -151,6 +154,19 @@ class OracleGel:
                     ls_halvings=int(stats[2]), substeps=int(stats[3]), active_pairs=int(stats[4]),
                     energy=float(fst[0]), min_distance=float(fst[1]))
         return info
+
+    def step_attached(self, pose, case_pose, dt):
+        """One step with the indenter driven to `pose` and the attached (Dirichlet) vertices driven
+        with their frame to `case_pose` (their rest positions carried by it)."""
+        P, Pp = _d(pose)
+        C, Cp = _d(case_pose)
+        stats = np.zeros(5, dtype=np.int32)
+        fst = np.zeros(2)
+        s = lib().or_step_attached(self._h, Pp, Cp, float(dt), stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   fst.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return dict(status=s, newton_iters=int(stats[0]), pcg_iters=int(stats[1]),
+                    ls_halvings=int(stats[2]), substeps=int(stats[3]), active_pairs=int(stats[4]),
+                    energy=float(fst[0]), min_distance=float(fst[1]))
 
     def state(self):
         x = np.zeros((self.N, 3))

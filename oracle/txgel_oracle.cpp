@@ -676,6 +676,7 @@ struct Gel {
   // state
   std::vector<double> x, v;
   double pose[7] = {1, 0, 0, 0, 0, 0, 0};
+  double case_pose[7] = {1, 0, 0, 0, 0, 0, 0};  // pose of the Dirichlet (attached) vertices' frame
   double fc[3] = {0, 0, 0};
   // stats of the last step
   int st_newton = 0, st_pcg = 0, st_ls = 0, st_substeps = 0, st_pairs = 0;
@@ -1310,21 +1311,43 @@ bool placement_ok(const Gel& G, const double* I0, const double* I1, int* err) {
   return true;
 }
 
-int substep(Gel& G, const double pa[7], const double pb[7], double dt, int depth) {
+// Dirichlet (attached) vertices at the case pose: their rest positions carried by it
+void place_attached(Gel& G, const double cpose[7]) {
+  std::vector<double> Xd, xd;
+  for (int i = 0; i < G.N; ++i)
+    if (G.dir[i])
+      for (int c = 0; c < 3; ++c) Xd.push_back(G.X[3 * i + c]);
+  xd.resize(Xd.size());
+  pose_apply(cpose, Xd.data(), (int)(Xd.size() / 3), xd.data());
+  for (int i = 0, k = 0; i < G.N; ++i)
+    if (G.dir[i]) {
+      for (int c = 0; c < 3; ++c) G.x[3 * i + c] = xd[3 * k + c];
+      ++k;
+    }
+}
+
+// One (sub)step moving the indenter from pose pa to pb; with case poses (ca, cb) the attached
+// vertices are also moved to their targets at cb first (kinematic attachments: the paper's GIPC
+// step sets the attachment points' targets, then solves), and a split halves both motions.
+int substep(Gel& G, const double pa[7], const double pb[7], double dt, int depth, const double* ca = nullptr,
+            const double* cb = nullptr) {
   std::vector<double> I0(3 * G.M), I1(3 * G.M);
   pose_apply(pa, G.IV.data(), G.M, I0.data());
   pose_apply(pb, G.IV.data(), G.M, I1.data());
+  std::vector<double> xn = G.x;
+  if (cb) place_attached(G, cb);
   int err = OK;
   if (!placement_ok(G, I0.data(), I1.data(), &err)) {
+    G.x = xn;
     if (err != OK) return err;
     if (depth >= G.split_depth) return ERR_INFEASIBLE;
-    double pm[7];
+    double pm[7], cm[7];
     pose_mid(pa, pb, pm);
-    int s = substep(G, pa, pm, 0.5 * dt, depth + 1);
+    if (cb) pose_mid(ca, cb, cm);
+    int s = substep(G, pa, pm, 0.5 * dt, depth + 1, ca, cb ? cm : nullptr);
     if (s != OK) return s;
-    return substep(G, pm, pb, 0.5 * dt, depth + 1);
+    return substep(G, pm, pb, 0.5 * dt, depth + 1, cb ? cm : nullptr, cb);
   }
-  std::vector<double> xn = G.x;
   int s = newton_solve(G, dt, I0.data(), I1.data());
   if (s != OK) {
     G.x = xn;
@@ -1472,19 +1495,30 @@ void* or_create(int N, const double* X, int T, const int* tets, const uint8_t* d
 void or_destroy(void* g) { delete static_cast<Gel*>(g); }
 
 // stats: [newton_iters, pcg_iters, ls_halvings, substeps, active_pairs]; fstats: [E, min_d]
+int or_step_attached(void* g, const double* pose, const double* case_pose, double dt, int* stats, double* fstats);
+
 int or_step(void* g, const double* pose, double dt, int* stats, double* fstats) {
+  return or_step_attached(g, pose, nullptr, dt, stats, fstats);
+}
+
+// One step with the indenter driven to `pose` and, if case_pose is given, the attached (Dirichlet)
+// vertices driven with their frame to case_pose (their rest positions carried by it)
+int or_step_attached(void* g, const double* pose, const double* case_pose, double dt, int* stats, double* fstats) {
   Gel& G = *static_cast<Gel*>(g);
   G.st_newton = G.st_pcg = G.st_ls = G.st_substeps = G.st_pairs = 0;
   G.st_energy = 0;
   G.st_min_d = INF;
   std::vector<double> x0 = G.x, v0 = G.v;
-  double p0[7];
+  double p0[7], c0[7];
   std::memcpy(p0, G.pose, sizeof(p0));
-  int s = substep(G, G.pose, pose, dt, 0);
+  std::memcpy(c0, G.case_pose, sizeof(c0));
+  int s = substep(G, G.pose, pose, dt, 0, case_pose ? c0 : nullptr, case_pose);
   if (s != OK) {  // transactional: leave the state at x_n
     G.x = x0;
     G.v = v0;
     std::memcpy(G.pose, p0, sizeof(p0));
+  } else if (case_pose) {
+    std::memcpy(G.case_pose, case_pose, sizeof(G.case_pose));
   }
   if (stats) {
     stats[0] = G.st_newton;
@@ -1519,6 +1553,14 @@ void or_reset(void* g) {
   Gel& G = *static_cast<Gel*>(g);
   G.x = G.X;
   G.v.assign(3 * G.N, 0.0);
+  const double id[7] = {1, 0, 0, 0, 0, 0, 0};
+  std::memcpy(G.case_pose, id, sizeof(id));
+}
+
+// pose of the attached vertices' frame (their positions are not moved until the next step)
+void or_set_case_pose(void* g, const double* pose) {
+  Gel& G = *static_cast<Gel*>(g);
+  std::memcpy(G.case_pose, pose, sizeof(G.case_pose));
 }
 
 // scalar properties: [mu, lambda, kappa, bbox_diag, total mass]; counts: [surf verts, surf tris,

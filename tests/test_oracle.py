@@ -617,3 +617,54 @@ def test_flat_plate_slides_with_coulomb_force():
     # with friction (0.5014 / -0.0012 here: the normal forces are lagged by a step and the gel
     # top still creeps sideways a little as it shears)
     assert abs(ratios[0.5][0] - 0.5) <= 0.01 and abs(ratios[0.5][1]) <= 5e-3
+
+
+# ------------------------------------------------------------------ attachment-driven gel
+# The paper's GIPC step sets the attachment points' targets (from the sensor case pose), then
+# solves: the Dirichlet vertices move kinematically with their frame.
+def test_attachment_rigid_translation_is_exact():
+    """Gel moving with its case at constant velocity, no contact: the step is a rigid translation
+    (inertia and elasticity both at rest; the Newton solve starts from the moved attachments and
+    the old free positions, so it is met to the Newton tolerance, 2.4e-9 m here)."""
+    wl = small_scene()
+    og = O.OracleGel.from_workload(wl)
+    far = W.pose((0.005, 0.005, 0.05))
+    v0 = np.array([2e-3, -1e-3, 3e-3])
+    X = wl.gel.verts
+    og.set_state(X, np.tile(v0, (len(X), 1)), far)
+    for s in range(1, 6):
+        t = v0 * wl.dt * s
+        info = og.step_attached(far, W.pose(t), wl.dt)
+        assert info["status"] == 0
+        x, v, fc, _ = og.state()
+        assert np.abs(x - (X + t)).max() <= 1e-10
+        assert np.abs(v - v0).max() <= 1e-10 / wl.dt
+        assert np.all(fc == 0)
+
+
+def test_attachment_motion_is_relative():
+    """Pressing the indenter down onto a resting gel equals carrying the gel up (case and all, at
+    the indenter's speed) against the resting indenter: the same motion in a frame moving at
+    constant velocity (Galilean invariance of the incremental potential).  The indenter sits off
+    the gel's mirror planes (a symmetric press is a bifurcation whose branch rounding picks) and
+    moves slowly enough that neither run splits its steps."""
+    gel = W.gel_grid(6, 6, 3, (0.01, 0.01, 0.003))
+    ind = W.icosphere(0.004, 1)
+    p0, poses = W.press_slide_poses(ind, gel, (0.0063, 0.0057), 0.15e-3, 20)
+    wl = W.Workload("tiny_offset", gel, ind, p0, poses, W.DT)
+    a = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    b = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+    X = wl.gel.verts
+    z0 = wl.pose0[6]
+    vz = (wl.poses[0][6] - z0) / wl.dt  # indenter velocity (downwards)
+    b.set_state(X, np.tile([0.0, 0.0, -vz], (len(X), 1)), wl.pose0)
+    for s in range(len(wl.poses)):
+        lift = z0 - wl.poses[s][6]
+        ia = a.step(wl.poses[s], wl.dt)
+        assert ia["status"] == 0 and ia["substeps"] == 1
+        assert b.step_attached(wl.pose0, W.pose((0.0, 0.0, lift)), wl.dt)["status"] == 0
+        xa, _, fa, _ = a.state()
+        xb, _, fb, _ = b.state()
+        assert np.abs(xb - np.array([0.0, 0.0, lift]) - xa).max() <= 1e-9
+        assert np.abs(fb - fa).max() <= 1e-6 * np.abs(fa).max()
+    assert fa[2] < 0
