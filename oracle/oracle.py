@@ -82,6 +82,9 @@ def _declare(L):
     L.or_step_attached.restype = ctypes.c_int
     L.or_step_attached.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ip, dp]
     L.or_set_case_pose.argtypes = [ctypes.c_void_p, dp]
+    L.or_markers.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, dp, dp, ip]
+    L.or_height_map.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, dp]
     L.or_friction_pair.restype = ctypes.c_int
     L.or_friction_pair.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
@@ -167,6 +170,25 @@ class OracleGel:
         return dict(status=s, newton_iters=int(stats[0]), pcg_iters=int(stats[1]),
                     ls_halvings=int(stats[2]), substeps=int(stats[3]), active_pairs=int(stats[4]),
                     energy=float(fst[0]), min_distance=float(fst[1]))
+
+    def markers(self, x, rest_xy):
+        """Positions of markers placed at rest points (x, y) of the top surface, carried by the gel
+        at positions x; and whether each lies on the top."""
+        x, xp = _d(x)
+        r, rp = _d(rest_xy)
+        n = len(r)
+        out = np.zeros((n, 3))
+        found = np.zeros(n, dtype=np.int32)
+        lib().or_markers(self._h, xp, n, rp, _d(out)[1], found.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return out, found.astype(bool)
+
+    def height_map(self, x, nx, ny, x0, y0, dx, dy):
+        """Top-surface height at pixel centres (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy), ny x nx,
+        NaN off the gel."""
+        x, xp = _d(x)
+        out = np.zeros((ny, nx))
+        lib().or_height_map(self._h, xp, int(nx), int(ny), float(x0), float(y0), float(dx), float(dy), _d(out)[1])
+        return out
 
     def state(self):
         x = np.zeros((self.N, 3))

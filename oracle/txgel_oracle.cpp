@@ -1733,6 +1733,75 @@ int or_accd(int kind, const double* Pf, const double* dPf, double s, double tc, 
 
 void or_psd_project(int n, double* A) { psd_project(n, A); }
 
+// ---------------- gel-surface readout (markers, height map) ----------------
+// The top surface: the boundary triangles whose rest outward normal points up (+z), the side the
+// indenter comes from.  Barycentric coordinates of the point (px, py) in the xy projection of
+// triangle (a, b, c) of positions P; false if outside (or degenerate).
+static bool xy_bary(const double* P, int a, int b, int c, double px, double py, double l[3]) {
+  const double ax = P[3 * a], ay = P[3 * a + 1], bx = P[3 * b], by = P[3 * b + 1], cx = P[3 * c], cy = P[3 * c + 1];
+  const double det = (bx - ax) * (cy - ay) - (cx - ax) * (by - ay);
+  if (det == 0.0) return false;
+  l[1] = ((px - ax) * (cy - ay) - (cx - ax) * (py - ay)) / det;
+  l[2] = ((bx - ax) * (py - ay) - (px - ax) * (by - ay)) / det;
+  l[0] = 1.0 - l[1] - l[2];
+  const double eps = -1e-12;
+  return l[0] >= eps && l[1] >= eps && l[2] >= eps;
+}
+
+static std::vector<int> top_tris(const Gel& G) {
+  std::vector<int> out;
+  for (size_t k = 0; k < G.stris.size() / 3; ++k) {
+    const int a = G.stris[3 * k], b = G.stris[3 * k + 1], c = G.stris[3 * k + 2];
+    double e1[3], e2[3], n[3];
+    sub3(&G.X[3 * b], &G.X[3 * a], e1);
+    sub3(&G.X[3 * c], &G.X[3 * a], e2);
+    cross3(e1, e2, n);
+    if (n[2] > 0.0) out.push_back((int)k);
+  }
+  return out;
+}
+
+// Markers at rest points (mx, my) of the top surface, carried by the gel at positions x: the
+// barycentric combination of the containing top triangle's vertices.  found[i] = 0 off the top.
+void or_markers(void* g, const double* x, int n, const double* rest_xy, double* out, int* found) {
+  const Gel& G = *static_cast<Gel*>(g);
+  const std::vector<int> top = top_tris(G);
+  for (int i = 0; i < n; ++i) {
+    found[i] = 0;
+    for (int c = 0; c < 3; ++c) out[3 * i + c] = 0.0;
+    for (int k : top) {
+      const int a = G.stris[3 * k], b = G.stris[3 * k + 1], c = G.stris[3 * k + 2];
+      double l[3];
+      if (!xy_bary(G.X.data(), a, b, c, rest_xy[2 * i], rest_xy[2 * i + 1], l)) continue;
+      for (int q = 0; q < 3; ++q) out[3 * i + q] = l[0] * x[3 * a + q] + l[1] * x[3 * b + q] + l[2] * x[3 * c + q];
+      found[i] = 1;
+      break;
+    }
+  }
+}
+
+// Height map of the gel's top surface at positions x: pixel (i, j) at (x0 + (i + 1/2) dx,
+// y0 + (j + 1/2) dy) gets the largest z of the top triangles covering it in the xy projection
+// (the surface seen from above), NaN where none does.  out is ny x nx, row j = y.
+void or_height_map(void* g, const double* x, int nx, int ny, double x0, double y0, double dx, double dy,
+                   double* out) {
+  const Gel& G = *static_cast<Gel*>(g);
+  const std::vector<int> top = top_tris(G);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double px = x0 + (i + 0.5) * dx, py = y0 + (j + 0.5) * dy;
+      double best = std::numeric_limits<double>::quiet_NaN();
+      for (int k : top) {
+        const int a = G.stris[3 * k], b = G.stris[3 * k + 1], c = G.stris[3 * k + 2];
+        double l[3];
+        if (!xy_bary(x, a, b, c, px, py, l)) continue;
+        const double z = l[0] * x[3 * a + 2] + l[1] * x[3 * b + 2] + l[2] * x[3 * c + 2];
+        if (!(z <= best)) best = z;  // also replaces the initial NaN
+      }
+      out[j * nx + i] = best;
+    }
+}
+
 // friction coefficient (0: no friction, the default) and velocity threshold eps_v [m/s]
 void or_set_friction(void* g, double mu, double eps_v) {
   Gel& G = *static_cast<Gel*>(g);

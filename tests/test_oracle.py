@@ -668,3 +668,67 @@ def test_attachment_motion_is_relative():
         assert np.abs(xb - np.array([0.0, 0.0, lift]) - xa).max() <= 1e-9
         assert np.abs(fb - fa).max() <= 1e-6 * np.abs(fa).max()
     assert fa[2] < 0
+
+
+# ------------------------------------------------------------------ gel-surface readout
+def _readout_gel():
+    wl = W.small_gel_sphere(0)
+    return wl, O.OracleGel.from_workload(wl)
+
+
+def test_readout_at_rest():
+    wl, og = _readout_gel()
+    X = wl.gel.verts
+    top = X[:, 2].max()
+    rng = np.random.default_rng(5)
+    m = np.column_stack([rng.uniform(0.0, 0.018, 50), rng.uniform(0.0, 0.024, 50)])
+    pos, found = og.markers(X, m)
+    assert found.all()
+    assert np.abs(pos[:, :2] - m).max() <= 1e-15 and np.abs(pos[:, 2] - top).max() <= 1e-15
+    _, f_off = og.markers(X, np.array([[0.019, 0.01], [-0.001, 0.01]]))
+    assert not f_off.any()
+    # pixel centres from -0.5 mm in 1 mm steps: rows (y) 1..24 and columns (x) 1..18 lie on the gel
+    hm = og.height_map(X, 20, 26, -0.001, -0.001, 0.001, 0.001)
+    assert np.abs(hm[1:25, 1:19] - top).max() <= 1e-15
+    assert np.isnan(hm[0, :]).all() and np.isnan(hm[:, 0]).all()
+    assert np.isnan(hm[25, :]).all() and np.isnan(hm[:, 19]).all()
+
+
+def test_readout_follows_an_affine_deformation_exactly():
+    wl, og = _readout_gel()
+    X = wl.gel.verts
+    top = X[:, 2].max()
+    rng = np.random.default_rng(6)
+    A = np.eye(3) + rng.uniform(-0.05, 0.05, size=(3, 3))
+    b = rng.uniform(-1e-3, 1e-3, size=3)
+    x = X @ A.T + b
+    m = np.column_stack([rng.uniform(0.001, 0.017, 40), rng.uniform(0.001, 0.023, 40)])
+    pos, found = og.markers(x, m)
+    assert found.all()
+    want = np.column_stack([m, np.full(len(m), top)]) @ A.T + b
+    assert np.abs(pos - want).max() <= 1e-15 * 1e3 * 0.03
+    # height of the mapped top plane at pixel centres well inside its image
+    nx, ny, x0, y0, dx, dy = 30, 40, 0.002, 0.003, 0.0004, 0.0004
+    hm = og.height_map(x, nx, ny, x0, y0, dx, dy)
+    Axy, Axz = A[:2, :2], A[:2, 2]
+    for j in range(ny):
+        for i in range(nx):
+            p = np.array([x0 + (i + 0.5) * dx, y0 + (j + 0.5) * dy])
+            Xxy = np.linalg.solve(Axy, p - b[:2] - Axz * top)
+            z = A[2, :2] @ Xxy + A[2, 2] * top + b[2]
+            assert abs(hm[j, i] - z) <= 1e-15 * 1e3 * 0.01
+
+
+def test_height_map_at_vertices_is_the_vertex_height():
+    """Top vertices displaced vertically by a smooth bump: a pixel centred on a vertex reads the
+    vertex's height (every covering triangle interpolates to it)."""
+    wl, og = _readout_gel()
+    X = wl.gel.verts.copy()
+    top = X[:, 2].max()
+    x = X.copy()
+    t = np.abs(X[:, 2] - top) < 1e-12
+    x[t, 2] -= 3e-4 * np.exp(-((X[t, 0] - 0.009) ** 2 + (X[t, 1] - 0.012) ** 2) / (4e-3) ** 2)
+    hm = og.height_map(x, 10, 13, -0.001, -0.001, 0.002, 0.002)  # pixel centres on the 2 mm grid
+    for k in np.nonzero(t)[0]:
+        i, j = int(round(X[k, 0] / 0.002)), int(round(X[k, 1] / 0.002))
+        assert abs(hm[j, i] - x[k, 2]) <= 1e-15
