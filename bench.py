@@ -13,7 +13,8 @@ events on the library's stream; an L2 flush (256 MB write) separates timed steps
 events.  Under torchrun each rank simulates its own gel (seed = rank): weak scaling, no
 collective on the data path.
 
---impl reference times the CPU oracle (FP64, single thread) on the same workload.
+--impl reference times the CPU oracle (FP64, every host core) on the same workload and the same
+window of steps (the warm-up steps run untimed first).
 """
 from __future__ import annotations
 
@@ -51,7 +52,7 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reference-budget", type=float, default=150.0, help="seconds of oracle work")
+    ap.add_argument("--reference-budget", type=float, default=200.0, help="seconds of timed oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
     ap.add_argument("--pcg-cta-slices", type=int, default=0,
@@ -135,9 +136,30 @@ class ClockSampler:
 
 
 def fp64_peak_tflops(sm_mhz):
-    """GB300 FP64 (non-tensor) rate: the nominal 1.25 TFLOP/s at 152 SMs x 2.07 GHz is 4 FLOP
-    (2 DFMA) per SM per clock; scaled to the given SM clock."""
+    """GB300 FP64 (non-tensor) rate from the datasheet: the nominal 1.25 TFLOP/s at 152 SMs x
+    2.07 GHz is 4 FLOP (2 DFMA) per SM per clock; scaled to the given SM clock.  Used only if the
+    on-device measurement below fails."""
     return 4.0 * 152 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def measure_fma_peaks(dev, target_ms=150.0):
+    """FP64 and FP32 FMA-pipe peaks measured on this device now (tx_peak_fma: every SM, eight
+    independent FMA chains per thread, CUDA-event timed), with the SM clock sampled while they
+    run.  Each is the best of three launches sized to about target_ms."""
+    from paper_2411_04776_gb300 import binding as B
+    out = {}
+    with ClockSampler(dev) as clk:
+        for bits in (64, 32):
+            f, ms = B.tx_peak_fma(bits, 2000)  # warm-up and size probe
+            iters = max(2000, int(2000 * target_ms / max(ms, 1e-3)))
+            best = 0.0
+            for _ in range(3):
+                f, ms = B.tx_peak_fma(bits, iters)
+                best = max(best, f / (ms * 1e-3) / 1e12)
+            out[f"fp{bits}_tflops"] = best
+    out["clocks"] = clk.summary()
+    out["how"] = "tx_peak_fma: 8 independent FMA chains per thread over every SM, best of 3 CUDA-event-timed launches"
+    return out
 
 
 def run_gpu(args, rank, world, e2e=True):
@@ -202,13 +224,17 @@ def run_gpu(args, rank, world, e2e=True):
     clocks = clk.summary()
     # ---- end to end through the public API with host buffers: poses in, positions out
     n = sum(len(w.gel.verts) for w in wls)
-    if not e2e:
+    if not e2e:  # companion measurements: the final states are compared across configurations
+        finals = []
+        for g, w in enumerate(wls):
+            x, _, fc, _ = (gel.state() if single else B.tx_batch_state(handle, g, len(w.gel.verts)))
+            finals.append((x, fc))
         if single:
             gel.close()
         else:
             B.tx_batch_destroy(handle)
         return dict(total_s=total_s, step_ms=step_ms, stats=stats, prof=prof, clocks=clocks, e2e_s=None,
-                    n=n, wls=wls, h2d=0, d2h=0)
+                    n=n, wls=wls, h2d=0, d2h=0, finals=finals)
     if single:
         gel.reset()
         for s in range(Wm):
@@ -265,7 +291,7 @@ def measured_peaks():
         return {}
 
 
-def roofline(prof, clocks, precision, kernel):
+def roofline(prof, clocks, precision, kernel, fma=None):
     """Roofline of the dominant kernel (the persistent PCG, one launch per Newton round).  FP64:
     bound by the FP64 pipe (GB300 runs FP64 at 1/64 of FP32; no tensor cores on this path), peak
     derived from the unit count and the SM clock.  Mixed precision: the inner solve streams FP32
@@ -283,14 +309,19 @@ def roofline(prof, clocks, precision, kernel):
         except (ValueError, KeyError):
             traffic = None
     if precision == "fp64":
-        peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
+        if fma and fma.get("fp64_tflops"):
+            peak = fma["fp64_tflops"]
+            note = "measured in this run (tx_peak_fma, FP64 FMA pipe, sampled SM clock %s MHz)" % (
+                fma.get("clocks", {}).get("sm_mhz"))
+        else:
+            peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
+            note = "derived (measurement failed): FP64 (non-tensor) 4 FLOP/clk/SM x 152 SMs x max SM clock"
         achieved = (ph["flops"] / launches) / (avg_ms * 1e-3) / 1e12 if ph["flops"] else None
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "avg_launch_ms": avg_ms, "launches": ph["launches"],
-                "peak_note": "derived: FP64 (non-tensor) 4 FLOP/clk/SM x 152 SMs x max SM clock; "
-                             "achieved = algorithmic FLOP (18 per 3x3 block, 60 per row per iteration; the single-gel "
-                             "solver adds its Galerkin start: one SpMV and 30 per row per solve)"}
+                "peak_note": note + "; achieved = algorithmic FLOP (18 per 3x3 block, 60 per row per iteration; the "
+                                    "resident solver adds its Galerkin start: one SpMV and 30 per row per solve)"}
     pk = measured_peaks()
     peak = float(pk.get("hbm_gbs") or 6800.0)
     achieved = (ph["bytes"] / launches) / (avg_ms * 1e-3) / 1e9 if ph["bytes"] else None
@@ -320,23 +351,54 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(args, budget=30.0):
-    """The oracle as it stands, single-threaded, on the first step(s) of the same trajectory
-    (first gel of a batch)."""
+def host_description():
+    """CPU model and core count of this host (the oracle's timings are quoted with them)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "arch": os.uname().machine}
+
+
+def oracle_window(wl, first, count, budget, threads):
+    """The oracle as it stands on the trajectory of workload wl: steps 0..first-1 untimed (all host
+    cores: the same state whatever the thread count, the oracle's sums do not depend on it), then
+    up to `count` steps from `first` on timed with `threads` threads until `budget` seconds of
+    oracle work are spent (at least one step).  Returns (timed steps, seconds, threads used)."""
     from oracle import oracle as O
-    wl = make_workload(args.workload, args.seed, 1)[0]
+    O.set_threads(0)
     og = O.OracleGel.from_workload(wl)
+    for s in range(first):
+        assert og.step(wl.poses[s], wl.dt)["status"] == 0
+    used = O.set_threads(threads)
     t0 = time.perf_counter()
     done = 0
-    while done < len(wl.poses):
-        info = og.step(wl.poses[done], wl.dt)
-        assert info["status"] == 0
+    while done < count and first + done < len(wl.poses):
+        assert og.step(wl.poses[first + done], wl.dt)["status"] == 0
         done += 1
         if time.perf_counter() - t0 > budget:
             break
     el = time.perf_counter() - t0
-    return {"value": done / el, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle (FP64 C++, 1 thread) steps 0..{done - 1} of the same trajectory, {el:.1f} s"}
+    O.set_threads(0)
+    return done, el, used
+
+
+def cpu_baseline(args, budget=30.0):
+    """The oracle as it stands (FP64 C++, every host core; bitwise the result of one thread) on
+    the first timed steps of the GPU arm's window: the same trajectory (first gel of a batch),
+    steps args.warmup, args.warmup + 1, ... until about `budget` seconds."""
+    wl = make_workload(args.workload, args.seed, 1)[0]
+    done, el, used = oracle_window(wl, args.warmup, args.steps, budget, 0)
+    host = host_description()
+    return {"value": done / el, "unit": "steps/s", "cores": used, "kind": "oracle",
+            "sample": f"oracle (FP64 C++, OpenMP, {used} threads) steps {args.warmup}..{args.warmup + done - 1} of "
+                      f"the GPU arm's trajectory (the start of its timed window), {el:.1f} s; steps 0..{args.warmup - 1} "
+                      f"run untimed first", "host": host}
 
 
 def run_serve(args):
@@ -408,20 +470,33 @@ def main():
             return
         from oracle import oracle as O
         O.build()
-        cb = cpu_baseline(args, budget=args.reference_budget)
         wls = make_workload(args.workload, args.seed, args.n_gels)
-        line = {"metric": "gel Newton-converged steps/sec", "value": cb["value"], "unit": "steps/s",
-                "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": 0,
-                "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(wls, args.workload, "fp64"), "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        done, el, used = oracle_window(wls[0], args.warmup, args.steps, args.reference_budget, 0)
+        value = done / el
+        host = host_description()
+        cb = {"value": value, "unit": "steps/s", "cores": used, "kind": "oracle",
+              "sample": f"oracle (FP64 C++, OpenMP, {used} threads) steps {args.warmup}..{args.warmup + done - 1} "
+                        f"of the GPU arm's trajectory, {el:.1f} s (steps 0..{args.warmup - 1} untimed first); "
+                        f"budget {args.reference_budget:.0f} s", "host": host}
+        line = {"metric": "gel Newton-converged steps/sec", "value": value, "unit": "steps/s",
+                "impl": "reference", "n_gpus": args.gpus, "steps": done, "steps_requested": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(wls[:1] if args.workload == "mini" else wls, args.workload, "fp64"),
+                "cpu_baseline": cb,
+                "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     r = run_gpu(args, rank, world)
+    fma = None
+    if rank == 0:
+        try:
+            fma = measure_fma_peaks(int(os.environ.get("LOCAL_RANK", 0)))
+        except Exception as e:  # noqa: BLE001
+            fma = {"error": f"{type(e).__name__}: {e}"}
     total_s, e2e_s = r["total_s"], r["e2e_s"]
     if world > 1:
         total_s, e2e_s = max_over_ranks([total_s, e2e_s], "cuda")
@@ -442,14 +517,18 @@ def main():
                        "max": float(step_ms.max())},
         "newton_iters_per_step": prof["newton_iters"] / (ng * K),
         "pcg_iters_per_step": prof["pcg_iters"] / (ng * K),
-        "roofline": roofline(r["prof"], r["clocks"], args.precision, pcg_kernel_name(args.precision, ng)),
+        "roofline": roofline(r["prof"], r["clocks"], args.precision, pcg_kernel_name(args.precision, ng), fma),
         "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
         "gpu_launches": r["prof"]["kernel_launches"],
+        "pcg_launches": {"resident": r["prof"]["pcg_resident_launches"],
+                         "streaming": r["prof"]["pcg_streaming_launches"]},
+        "fma_peaks": fma,
         "iteration_histogram": iteration_histogram(r["stats"]),
         "clocks": r["clocks"],
         "e2e": {"value": world * ng * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
     }
+    args.fma_peaks = fma
     if world == 1 and args.workload == "mini" and args.batched_gels > 0:
         try:  # a companion measurement: its failure is reported, the main line still prints
             line["batched_mixed"] = batched_mixed(args)
@@ -470,7 +549,7 @@ def plain_fp64_sequential(wls, steps, warmup):
     from paper_2411_04776_gb300 import binding as B
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ms = []
+    ms, finals = [], []
     for w in wls:
         gel = B.Gel(B.GelDesc.from_workload(w, precision=B.TX_PREC_FP64), stream=stream)
         for s in range(warmup):
@@ -483,18 +562,36 @@ def plain_fp64_sequential(wls, steps, warmup):
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+        x, _, fc, _ = gel.state()
+        finals.append((x, fc))
         gel.close()
     ms = np.array(ms)
     return {"gels": len(wls), "value": len(ms) / (ms.sum() / 1e3), "unit": "steps/s",
-            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}, finals
+
+
+def state_difference(a, b):
+    """Max / RMS vertex displacement difference and max relative contact-force difference between
+    two sets of final gel states (same gels, same steps)."""
+    dmax, sq, cnt, fmax = 0.0, 0.0, 0, 0.0
+    for (xa, fa), (xb, fb) in zip(a, b):
+        d = np.abs(xa - xb)
+        dmax = max(dmax, float(d.max()))
+        sq += float((d ** 2).sum())
+        cnt += d.size
+        fmax = max(fmax, float(np.abs(fa - fb).max() / max(np.abs(fb).max(), 1e-30)))
+    return {"max_disp_m": dmax, "rms_disp_m": (sq / max(cnt, 1)) ** 0.5, "max_force_rel": fmax}
 
 
 def batched_mixed(args):
-    """Companion measurement of the same metric on the batched mixed-precision configuration:
-    args.batched_gels GelSight-Mini gels (41x51x9, each with its own seeded indenter and press/slide
-    trajectory) stepped together, FP32 elastic blocks and FP32 inner PCG with FP64 residual
-    refinement; compared with the plain FP64 path stepping the first 16 of the same gels one at a
-    time over the same steps (vs_plain_fp64 = ratio of the two steps/s)."""
+    """Companion measurement of the same metric on the batched configurations: args.batched_gels
+    GelSight-Mini gels (41x51x9, each with its own seeded indenter and press/slide trajectory)
+    stepped together (one handle) in mixed precision (FP32 elastic blocks and FP32 inner PCG with
+    FP64 residual refinement) and in FP64, and the plain FP64 path stepping the same gels one at
+    a time over the same steps.  vs_plain_fp64 splits into the batching gain (batched FP64 / one
+    at a time) and the precision gain (batched mixed / batched FP64).  Accuracy: the final states
+    of the mixed batch against the one-at-a-time FP64 run (both at the workload's Newton
+    tolerance, so the difference includes where each run stopped within it)."""
     import argparse
     a = argparse.Namespace(**vars(args))
     a.workload, a.n_gels, a.precision = "batch_mini", args.batched_gels, "mixed"
@@ -503,7 +600,11 @@ def batched_mixed(args):
     ng = len(r["wls"])
     value = ng * a.steps / r["total_s"]
     prof = r["prof"]
-    plain = plain_fp64_sequential(r["wls"][:min(ng, 16)], a.steps, a.warmup)
+    a64 = argparse.Namespace(**vars(a))
+    a64.precision = "fp64"
+    r64 = run_gpu(a64, 0, 1, e2e=False)
+    value64 = ng * a.steps / r64["total_s"]
+    plain, plain_finals = plain_fp64_sequential(r["wls"], a.steps, a.warmup)
     return {"workload": workload_config(r["wls"], a.workload, "mixed")["workload"], "gels": ng,
             "precision": "mixed", "value": value, "unit": "steps/s", "steps": a.steps, "warmup": a.warmup,
             "ms_per_batch_step": r["total_s"] * 1e3 / a.steps,
@@ -511,9 +612,21 @@ def batched_mixed(args):
                            "p99": float(np.percentile(r["step_ms"], 99))},
             "newton_iters_per_step": prof["newton_iters"] / (ng * a.steps),
             "pcg_iters_per_step": prof["pcg_iters"] / (ng * a.steps),
+            "batched_fp64": {"value": value64, "unit": "steps/s", "ms_per_batch_step": r64["total_s"] * 1e3 / a.steps,
+                             "newton_iters_per_step": r64["prof"]["newton_iters"] / (ng * a.steps),
+                             "pcg_iters_per_step": r64["prof"]["pcg_iters"] / (ng * a.steps),
+                             "roofline": roofline(r64["prof"], r64["clocks"], "fp64", pcg_kernel_name("fp64", ng),
+                                                  args.fma_peaks),
+                             "pcg_launches": {"resident": r64["prof"]["pcg_resident_launches"],
+                                              "streaming": r64["prof"]["pcg_streaming_launches"]}},
             "plain_fp64_same_steps": plain,
             "vs_plain_fp64": value / plain["value"],
+            "batching_gain_fp64": value64 / plain["value"],
+            "precision_gain_batched": value / value64,
+            "accuracy_vs_plain_fp64": state_difference(r["finals"], plain_finals),
+            "accuracy_batched_fp64_vs_plain_fp64": state_difference(r64["finals"], plain_finals),
             "roofline": roofline(prof, r["clocks"], "mixed", pcg_kernel_name("mixed", ng)),
+            "pcg_launches": {"resident": prof["pcg_resident_launches"], "streaming": prof["pcg_streaming_launches"]},
             "phases_ms": {k: round(v["ms"], 3) for k, v in prof["phases"].items()},
             "gpu_launches": prof["kernel_launches"], "clocks": r["clocks"]}
 

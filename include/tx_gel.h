@@ -78,6 +78,12 @@ typedef struct tx_params {
                                the default (4); -1 autotunes it per class of active gel sets
                                (timed on live Newton rounds; the split changes the order of the
                                PCG's sums, so tuned runs are not bitwise reproducible)          */
+  int32_t pcg_plan;         /* PCG kernel family: 0 automatic (the resident kernels, which keep the
+                               matrix in shared memory, whenever the gels fit them; otherwise the
+                               streaming kernels); 1 always the streaming kernels (tests and
+                               measurements of that family).  A handle uses the streaming kernels
+                               if any of its gels asks for them.                                */
+  int32_t reserved0;        /* must be 0                                                       */
 } tx_params;
 
 void tx_params_default(tx_params* p);
@@ -211,10 +217,33 @@ typedef struct tx_profile {
   int64_t pcg_iters;                /* PCG iterations (summed over gels)                         */
   int64_t newton_iters;             /* Newton iterations run (summed over gels)                  */
   int64_t kernel_launches;          /* every kernel this library launched (all handles)          */
+  int64_t pcg_resident_launches;    /* PCG launches of the resident kernels (matrix in shared
+                                       memory; counted whether or not profiling is on)            */
+  int64_t pcg_streaming_launches;   /* PCG launches of the streaming kernels (matrix from HBM)   */
 } tx_profile;
 
 tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out);
 tx_status tx_gel_profile(tx_gel* g, int32_t enable, tx_profile* out);
+
+/* ---------------- measurement ----------------
+ * Peak rate of the plain (non-tensor) FMA pipe in FP64 (bits = 64) or FP32 (bits = 32): one launch
+ * over every SM in which each thread runs eight independent chains of `iters` FMAs, timed with
+ * CUDA events on `stream` (the call waits for it).  *flops = 2 x the FMAs executed, *ms = the
+ * launch's event time; flops / ms is the roofline denominator of the FP64-bound solver kernels.
+ * No counterpart in the paper: it measures the device the solver runs on. */
+tx_status tx_peak_fma(int32_t bits, int32_t iters, double* flops, double* ms, void* stream);
+
+/* ---------------- fault injection (test hook) ----------------
+ * Makes the library's own failure paths run without faulting the device.  kind 1: the device or
+ * pinned-host allocation `count` allocations from now fails before it reaches the CUDA runtime
+ * (the call that makes it returns TX_ERR_OOM and frees what it had allocated); kind 2: the PCG
+ * launches of the next `count` Newton iterations (any handle) wait at their group barriers for an
+ * arrival that never comes, with a short poll limit, so that every wait gives up and the step
+ * returns TX_ERR_DEVICE_TIMEOUT with the state rolled back.  count 0 disarms a kind.  Returns
+ * TX_ERR_ARG for an unknown kind or a negative count.  Process-wide; not for production use. */
+#define TX_INJECT_ALLOC_FAIL 1
+#define TX_INJECT_WAIT_TIMEOUT 2
+tx_status tx_debug_inject(int32_t kind, int32_t count);
 
 /* ---------------- unit-level kernels (device pointers, for parity checks and reuse) --------- */
 
@@ -253,16 +282,18 @@ tx_status tx_bsr_pcg(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
 
 /* tx_bsr_pcg without any device allocation.  (This entry point has no counterpart in the paper; it
  * exists for callers of this library that must not allocate device memory while they run: a host
- * framework that owns every device allocation of a simulation step, code recorded into a CUDA
- * graph, or a real-time control loop where cudaMalloc/cudaFree would synchronise the device and
- * stall the other streams.)  Same arguments and results as tx_bsr_pcg, for n <= 65536 block rows;
- * larger systems are rejected with TX_ERR_ARG (tx_last_error says why).  The scratch is one
- * fixed array of about 11 MB inside the library's device module, held by every GPU that loads
- * the library until the process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call before any
- * stream capture.  All calls on a device share the array: calls that overlap on the GPU (on
- * different streams or from different threads) race and give wrong results; the counters a call
- * needs zeroed are cleared by the call itself. */
+ * framework that owns every device allocation of a simulation step through its own pool or a
+ * fixed memory budget, or a real-time control loop where cudaMalloc/cudaFree would synchronise
+ * the device and stall the other streams.)  Same arguments and results as tx_bsr_pcg, for
+ * n <= 65536 block rows; larger systems are rejected with TX_ERR_ARG (tx_last_error says why).
+ * Like tx_bsr_pcg it waits for its stream to finish before returning (it reads the iteration
+ * count back).  The scratch is one fixed array of about 11 MB inside the library's device module,
+ * held by every GPU that loads the library until the process exits.  The first call in a CUDA
+ * context (each device's primary context; a device reset makes a new one) looks up that array's
+ * device address (cudaGetSymbolAddress) with the context current and keeps it for that context;
+ * make that first call before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU (on different streams or from different threads) race and give wrong
+ * results; the counters a call needs zeroed are cleared by the call itself. */
 tx_status tx_bsr_pcg_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                              const double* vals, const double* b, double* x, double rel_tol,
                              int32_t max_iter, int32_t* iters, double* rel_res, void* stream);

@@ -24,13 +24,28 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_MESH_INVERTED", 4: "ERR_I
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build (plain g++, -O2, portable flags)."""
+    """Compile the oracle into oracle/_build (plain g++, -O2, portable flags; OpenMP when the
+    compiler has it -- the parallel loops give bitwise the same results as one thread)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        base = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base + ["-Wno-unknown-pragmas"])
         os.replace(tmp, _OUT)
     return _OUT
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: all host cores); returns the count in use.
+    The results are bitwise independent of it."""
+    L = lib()
+    L.or_set_threads(int(n))
+    return int(L.or_get_threads())
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def lib():
@@ -85,6 +100,8 @@ def _declare(L):
     L.or_markers.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, dp, dp, ip]
     L.or_height_map.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, dp]
+    L.or_set_threads.argtypes = [ctypes.c_int]
+    L.or_get_threads.restype = ctypes.c_int
     L.or_friction_pair.restype = ctypes.c_int
     L.or_friction_pair.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]

@@ -63,6 +63,11 @@
 // which is the same function as the definition above (det(I+H) = 1 + tr H + c2 + c3) but free of
 // the O(1) cancellation the literal form has near the rest state; the line search needs E to
 // resolve energy decreases far below E itself.
+//
+// Threads: when built with OpenMP, the loops over tets, contact pairs, broad-phase primitives and
+// matrix rows run in parallel, but every such loop only writes per-element results; all sums and
+// minima over elements are then taken serially in index order.  The results are therefore
+// bitwise identical for any thread count (or_set_threads), and equal to a one-thread run.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -71,6 +76,9 @@
 #include <map>
 #include <utility>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -775,21 +783,23 @@ std::vector<PairRef> candidate_pairs(const Gel& G, const double* x0, const doubl
   for (int k = 0; k < G.K; ++k) itb[k] = ibox(&G.itris[3 * k], 3);
   for (size_t k = 0; k < iedb.size(); ++k) iedb[k] = ibox(&G.iedges[2 * k], 2);
   for (int k = 0; k < G.M; ++k) ivb[k] = ibox(&k, 1);
-  for (size_t g = 0; g < G.sverts.size(); ++g) {
-    Box b = gbox(&G.sverts[g], 1);
-    for (int k = 0; k < G.K; ++k)
-      if (near_boxes(b, itb[k], pad)) out.push_back({0, (int)g, k});
-  }
-  for (size_t g = 0; g < G.stris.size() / 3; ++g) {
-    Box b = gbox(&G.stris[3 * g], 3);
-    for (int k = 0; k < G.M; ++k)
-      if (near_boxes(b, ivb[k], pad)) out.push_back({1, (int)g, k});
-  }
-  for (size_t g = 0; g < G.sedges.size() / 2; ++g) {
-    Box b = gbox(&G.sedges[2 * g], 2);
-    for (size_t k = 0; k < iedb.size(); ++k)
-      if (near_boxes(b, iedb[k], pad)) out.push_back({2, (int)g, (int)k});
-  }
+  // every (gel primitive, indenter primitive) combination of each type, listed gel primitive by
+  // gel primitive (the scan of one gel primitive may run on any thread; the lists are joined in
+  // gel-primitive order)
+  auto scan = [&](int type, int ng, int nvert, const int* ids, const std::vector<Box>& ib) {
+    std::vector<std::vector<int>> hits(ng);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < ng; ++g) {
+      Box b = gbox(ids + (size_t)nvert * g, nvert);
+      for (int k = 0; k < (int)ib.size(); ++k)
+        if (near_boxes(b, ib[k], pad)) hits[g].push_back(k);
+    }
+    for (int g = 0; g < ng; ++g)
+      for (int k : hits[g]) out.push_back({type, g, k});
+  };
+  scan(0, (int)G.sverts.size(), 1, G.sverts.data(), itb);
+  scan(1, (int)(G.stris.size() / 3), 3, G.stris.data(), ivb);
+  scan(2, (int)(G.sedges.size() / 2), 2, G.sedges.data(), iedb);
   return out;
 }
 
@@ -941,6 +951,8 @@ EnergyParts energy(const Gel& G, const double* x, const double* xt, double h, co
     for (int c = 0; c < 3; ++c) s += (x[3 * i + c] - xt[3 * i + c]) * (x[3 * i + c] - xt[3 * i + c]);
     e.inertia += G.mass[i] * s / (2.0 * h * h);
   }
+  std::vector<double> te(G.T);
+#pragma omp parallel for schedule(static)
   for (int t = 0; t < G.T; ++t) {
     double Xl[4][3], xl[4][3];
     for (int a = 0; a < 4; ++a)
@@ -948,16 +960,25 @@ EnergyParts energy(const Gel& G, const double* x, const double* xt, double h, co
         Xl[a][c] = G.X[3 * G.tets[4 * t + a] + c];
         xl[a][c] = x[3 * G.tets[4 * t + a] + c];
       }
-    e.elastic += tet_energy(G.rest[t], Xl, xl, G.mu, G.lam);
+    te[t] = tet_energy(G.rest[t], Xl, xl, G.mu, G.lam);
   }
+  for (int t = 0; t < G.T; ++t) e.elastic += te[t];
   std::vector<PairRef> pairs = candidate_pairs(G, x, x, IW, IW, G.dhat);
-  for (const PairRef& pr : pairs) {
+  const int np = (int)pairs.size();
+  std::vector<double> pd2(np), pb(np, 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int k = 0; k < np; ++k) {
     double P[4][3];
     int gi[4];
-    pair_points(G, x, IW, pr, P, gi);
-    int kind = kind_of(pr);
+    pair_points(G, x, IW, pairs[k], P, gi);
+    int kind = kind_of(pairs[k]);
     DType ty = classify(kind, P);
     double D = d2_of_type(ty, P);
+    pd2[k] = D;
+    if (D > 0.0 && D < G.dhat * G.dhat) pb[k] = pair_barrier<double>(kind, ty, P, G.dhat, pair_eps_x(G, pairs[k]));
+  }
+  for (int k = 0; k < np; ++k) {
+    const double D = pd2[k];
     e.min_d = std::min(e.min_d, std::sqrt(D));
     if (!(D > 0.0)) {
       e.barrier = INF;
@@ -965,14 +986,18 @@ EnergyParts energy(const Gel& G, const double* x, const double* xt, double h, co
     }
     if (D >= G.dhat * G.dhat) continue;
     e.active++;
-    e.barrier += G.kappa * pair_barrier<double>(kind, ty, P, G.dhat, pair_eps_x(G, pr));
+    e.barrier += G.kappa * pb[k];
   }
-  for (const FricPair& f : G.fric) {  // lagged friction (empty unless mu_f > 0)
+  const int nfr = (int)G.fric.size();
+  std::vector<double> fe(nfr);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nfr; ++k) {  // lagged friction (empty unless mu_f > 0)
     double P[4][3];
     int gi[4];
-    pair_points(G, x, IW, f.pr, P, gi);
-    e.friction += fric_energy<double>(f, P, G.fric_mu, G.fric_eh);
+    pair_points(G, x, IW, G.fric[k].pr, P, gi);
+    fe[k] = fric_energy<double>(G.fric[k], P, G.fric_mu, G.fric_eh);
   }
+  for (int k = 0; k < nfr; ++k) e.friction += fe[k];
   return e;
 }
 
@@ -1002,83 +1027,106 @@ void assemble(const Gel& G, const double* x, const double* xt, double h, const d
       grad[3 * i + c] += G.mass[i] * (x[3 * i + c] - xt[3 * i + c]) / (h * h);
       add(3 * i + c, 3 * i + c, G.mass[i] / (h * h));
     }
-  for (int t = 0; t < G.T; ++t) {
-    double Xl[4][3], xl[4][3], e, g[12], H[144];
-    for (int a = 0; a < 4; ++a)
-      for (int c = 0; c < 3; ++c) {
-        Xl[a][c] = G.X[3 * G.tets[4 * t + a] + c];
-        xl[a][c] = x[3 * G.tets[4 * t + a] + c];
-      }
-    tet_derivs(G.rest[t], Xl, xl, G.mu, G.lam, project, &e, g, H);
-    for (int a = 0; a < 4; ++a)
-      for (int c = 0; c < 3; ++c) {
-        int gi = 3 * G.tets[4 * t + a] + c;
-        grad[gi] += g[3 * a + c];
-        for (int b = 0; b < 4; ++b)
-          for (int d = 0; d < 3; ++d) add(gi, 3 * G.tets[4 * t + b] + d, H[(3 * a + c) * 12 + 3 * b + d]);
-      }
+  {
+    // per-tet derivatives (parallel), then added in tet order
+    std::vector<double> tg(12 * (size_t)G.T), tH(144 * (size_t)G.T);
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < G.T; ++t) {
+      double Xl[4][3], xl[4][3], e;
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) {
+          Xl[a][c] = G.X[3 * G.tets[4 * t + a] + c];
+          xl[a][c] = x[3 * G.tets[4 * t + a] + c];
+        }
+      tet_derivs(G.rest[t], Xl, xl, G.mu, G.lam, project, &e, &tg[12 * (size_t)t], &tH[144 * (size_t)t]);
+    }
+    for (int t = 0; t < G.T; ++t) {
+      const double* g = &tg[12 * (size_t)t];
+      const double* H = &tH[144 * (size_t)t];
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) {
+          int gi = 3 * G.tets[4 * t + a] + c;
+          grad[gi] += g[3 * a + c];
+          for (int b = 0; b < 4; ++b)
+            for (int d = 0; d < 3; ++d) add(gi, 3 * G.tets[4 * t + b] + d, H[(3 * a + c) * 12 + 3 * b + d]);
+        }
+    }
   }
-  std::vector<PairRef> pairs = candidate_pairs(G, x, x, IW, IW, G.dhat);
-  for (const PairRef& pr : pairs) {
-    double P[4][3];
-    int gi[4];
-    pair_points(G, x, IW, pr, P, gi);
-    int kind = kind_of(pr);
-    DType ty = classify(kind, P);
-    double D = d2_of_type(ty, P);
-    if (!(D < G.dhat * G.dhat) || !(D > 0.0)) continue;
-    AD<12> Pv[4][3];
-    for (int k = 0; k < 4; ++k)
-      for (int c = 0; c < 3; ++c) Pv[k][c] = ad_var<12>(P[k][c], 3 * k + c);
-    AD<12> b = pair_barrier<AD<12>>(kind, ty, Pv, G.dhat, pair_eps_x(G, pr));
-    // free sub-block: the gel's points only
-    int fidx[12], nf = 0;
-    for (int k = 0; k < 4; ++k)
-      if (gi[k] >= 0)
-        for (int c = 0; c < 3; ++c) fidx[nf++] = 3 * k + c;
-    std::vector<double> Hf(nf * nf);
-    for (int r = 0; r < nf; ++r)
-      for (int c = 0; c < nf; ++c) Hf[r * nf + c] = G.kappa * b.h[fidx[r]][fidx[c]];
-    if (project) psd_project(nf, Hf.data());
-    for (int r = 0; r < nf; ++r) {
-      int kr = fidx[r] / 3, cr = fidx[r] % 3;
-      int gr = 3 * gi[kr] + cr;
-      double gv = G.kappa * b.g[fidx[r]];
-      grad[gr] += gv;
-      fc[cr] -= gv;
-      for (int c = 0; c < nf; ++c) {
-        int kc = fidx[c] / 3, cc = fidx[c] % 3;
-        add(gr, 3 * gi[kc] + cc, Hf[r * nf + c]);
+  // per-pair contributions on the gel's points (computed in parallel, added in pair order)
+  struct PairTerm {
+    bool on = false;
+    int nf = 0, fidx[12], gi[4];
+    double g[12], H[144];
+  };
+  auto add_terms = [&](const std::vector<PairTerm>& terms) {
+    for (const PairTerm& q : terms) {
+      if (!q.on) continue;
+      for (int r = 0; r < q.nf; ++r) {
+        int kr = q.fidx[r] / 3, cr = q.fidx[r] % 3;
+        int gr = 3 * q.gi[kr] + cr;
+        grad[gr] += q.g[r];
+        fc[cr] -= q.g[r];
+        for (int c = 0; c < q.nf; ++c) {
+          int kc = q.fidx[c] / 3, cc = q.fidx[c] % 3;
+          add(gr, 3 * q.gi[kc] + cc, q.H[r * q.nf + c]);
+        }
       }
     }
+  };
+  std::vector<PairRef> pairs = candidate_pairs(G, x, x, IW, IW, G.dhat);
+  {
+    const int np = (int)pairs.size();
+    std::vector<PairTerm> terms(np);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < np; ++k) {
+      const PairRef& pr = pairs[k];
+      PairTerm& q = terms[k];
+      double P[4][3];
+      pair_points(G, x, IW, pr, P, q.gi);
+      int kind = kind_of(pr);
+      DType ty = classify(kind, P);
+      double D = d2_of_type(ty, P);
+      if (!(D < G.dhat * G.dhat) || !(D > 0.0)) continue;
+      q.on = true;
+      AD<12> Pv[4][3];
+      for (int j = 0; j < 4; ++j)
+        for (int c = 0; c < 3; ++c) Pv[j][c] = ad_var<12>(P[j][c], 3 * j + c);
+      AD<12> b = pair_barrier<AD<12>>(kind, ty, Pv, G.dhat, pair_eps_x(G, pr));
+      // free sub-block: the gel's points only
+      for (int j = 0; j < 4; ++j)
+        if (q.gi[j] >= 0)
+          for (int c = 0; c < 3; ++c) q.fidx[q.nf++] = 3 * j + c;
+      for (int r = 0; r < q.nf; ++r)
+        for (int c = 0; c < q.nf; ++c) q.H[r * q.nf + c] = G.kappa * b.h[q.fidx[r]][q.fidx[c]];
+      if (project) psd_project(q.nf, q.H);
+      for (int r = 0; r < q.nf; ++r) q.g[r] = G.kappa * b.g[q.fidx[r]];
+    }
+    add_terms(terms);
   }
   // lagged friction: convex in u, so its Hessian is PSD as it stands (projected all the same)
-  for (const FricPair& f : G.fric) {
-    double P[4][3];
-    int gi[4];
-    pair_points(G, x, IW, f.pr, P, gi);
-    AD<12> Pv[4][3];
-    for (int k = 0; k < 4; ++k)
-      for (int c = 0; c < 3; ++c) Pv[k][c] = ad_var<12>(P[k][c], 3 * k + c);
-    AD<12> D = fric_energy<AD<12>>(f, Pv, G.fric_mu, G.fric_eh);
-    int fidx[12], nf = 0;
-    for (int k = 0; k < 4; ++k)
-      if (gi[k] >= 0)
-        for (int c = 0; c < 3; ++c) fidx[nf++] = 3 * k + c;
-    std::vector<double> Hf(nf * nf);
-    for (int r = 0; r < nf; ++r)
-      for (int c = 0; c < nf; ++c) Hf[r * nf + c] = D.h[fidx[r]][fidx[c]];
-    if (project) psd_project(nf, Hf.data());
-    for (int r = 0; r < nf; ++r) {
-      int kr = fidx[r] / 3, cr = fidx[r] % 3;
-      int gr = 3 * gi[kr] + cr;
-      grad[gr] += D.g[fidx[r]];
-      fc[cr] -= D.g[fidx[r]];
-      for (int c = 0; c < nf; ++c) {
-        int kc = fidx[c] / 3, cc = fidx[c] % 3;
-        add(gr, 3 * gi[kc] + cc, Hf[r * nf + c]);
-      }
+  {
+    const int nfr = (int)G.fric.size();
+    std::vector<PairTerm> terms(nfr);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < nfr; ++k) {
+      const FricPair& f = G.fric[k];
+      PairTerm& q = terms[k];
+      double P[4][3];
+      pair_points(G, x, IW, f.pr, P, q.gi);
+      q.on = true;
+      AD<12> Pv[4][3];
+      for (int j = 0; j < 4; ++j)
+        for (int c = 0; c < 3; ++c) Pv[j][c] = ad_var<12>(P[j][c], 3 * j + c);
+      AD<12> D = fric_energy<AD<12>>(f, Pv, G.fric_mu, G.fric_eh);
+      for (int j = 0; j < 4; ++j)
+        if (q.gi[j] >= 0)
+          for (int c = 0; c < 3; ++c) q.fidx[q.nf++] = 3 * j + c;
+      for (int r = 0; r < q.nf; ++r)
+        for (int c = 0; c < q.nf; ++c) q.H[r * q.nf + c] = D.h[q.fidx[r]][q.fidx[c]];
+      if (project) psd_project(q.nf, q.H);
+      for (int r = 0; r < q.nf; ++r) q.g[r] = D.g[q.fidx[r]];
     }
+    add_terms(terms);
   }
 }
 
@@ -1088,32 +1136,62 @@ struct CSR {
   std::vector<double> va;
 };
 
+// CSR of the summed triplets.  The triplets of each row are gathered in the order they were
+// generated, ordered by column with a stable sort, and the entries of one (row, column) position
+// are summed in generation order.
 CSR to_csr(int n, std::vector<Triplet>& t) {
-  std::sort(t.begin(), t.end(), [](const Triplet& a, const Triplet& b) {
-    return a.r != b.r ? a.r < b.r : a.c < b.c;
-  });
   CSR A;
   A.n = n;
-  A.rp.assign(n + 1, 0);
-  for (size_t k = 0; k < t.size();) {
-    size_t m = k;
-    double s = 0.0;
-    while (m < t.size() && t[m].r == t[k].r && t[m].c == t[k].c) s += t[m++].v;
-    A.ci.push_back(t[k].c);
-    A.va.push_back(s);
-    A.rp[t[k].r + 1]++;
-    k = m;
+  std::vector<size_t> start(n + 1, 0);
+  for (const Triplet& e : t) start[e.r + 1]++;
+  for (int i = 0; i < n; ++i) start[i + 1] += start[i];
+  std::vector<size_t> fill(start.begin(), start.end() - 1);
+  std::vector<std::pair<int, double>> byrow(t.size());
+  for (const Triplet& e : t) byrow[fill[e.r]++] = {e.c, e.v};
+  std::vector<int> nnz(n, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int i = 0; i < n; ++i) {
+    auto b = byrow.begin() + start[i], e = byrow.begin() + start[i + 1];
+    std::stable_sort(b, e, [](const std::pair<int, double>& u, const std::pair<int, double>& w) {
+      return u.first < w.first;
+    });
+    for (auto k = b; k != e; ++k)
+      if (k == b || k->first != (k - 1)->first) nnz[i]++;
   }
-  for (int i = 0; i < n; ++i) A.rp[i + 1] += A.rp[i];
+  A.rp.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) A.rp[i + 1] = A.rp[i] + nnz[i];
+  A.ci.resize(A.rp[n]);
+  A.va.resize(A.rp[n]);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int i = 0; i < n; ++i) {
+    int o = A.rp[i];
+    for (size_t k = start[i]; k < start[i + 1];) {
+      size_t m = k;
+      double s = 0.0;
+      while (m < start[i + 1] && byrow[m].first == byrow[k].first) s += byrow[m++].second;
+      A.ci[o] = byrow[k].first;
+      A.va[o] = s;
+      ++o;
+      k = m;
+    }
+  }
   return A;
 }
 
 void spmv(const CSR& A, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A.n; ++i) {
     double s = 0.0;
     for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) s += A.va[k] * x[A.ci[k]];
     y[i] = s;
   }
+}
+
+// sum_i a_i b_i in index order
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
 }
 
 // Jacobi-preconditioned CG for A x = b, x0 = 0, stop at |r| <= tol |b|.  Returns iterations or -1.
@@ -1124,30 +1202,28 @@ int pcg(const CSR& A, const std::vector<double>& b, std::vector<double>& x, doub
   for (int i = 0; i < n; ++i)
     for (int k = A.rp[i]; k < A.rp[i + 1]; ++k)
       if (A.ci[k] == i) dinv[i] = 1.0 / A.va[k];
-  double bb = 0.0;
-  for (int i = 0; i < n; ++i) bb += b[i] * b[i];
+  double bb = dot(b, b);
   if (bb == 0.0) return 0;
   for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
   p = z;
-  double rz = 0.0;
-  for (int i = 0; i < n; ++i) rz += r[i] * z[i];
+  double rz = dot(r, z);
   for (int it = 1; it <= maxit; ++it) {
     spmv(A, p.data(), q.data());
-    double pq = 0.0;
-    for (int i = 0; i < n; ++i) pq += p[i] * q[i];
+    double pq = dot(p, q);
     double alpha = rz / pq;
-    double rr = 0.0;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
       x[i] += alpha * p[i];
       r[i] -= alpha * q[i];
-      rr += r[i] * r[i];
     }
+    double rr = dot(r, r);
     if (rr <= tol * tol * bb) return it;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
-    double rz2 = 0.0;
-    for (int i = 0; i < n; ++i) rz2 += r[i] * z[i];
+    double rz2 = dot(r, z);
     double beta = rz2 / rz;
     rz = rz2;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
   }
   return -1;
@@ -1160,20 +1236,25 @@ int min_toi(const Gel& G, const double* x0, const double* dx, const double* I0, 
   for (int i = 0; i < 3 * G.N; ++i) x1[i] = x0[i] + dx[i];
   for (int i = 0; i < 3 * G.M; ++i) I1[i] = I0[i] + dI[i];
   std::vector<PairRef> pairs = candidate_pairs(G, x0, x1.data(), I0, I1.data(), G.dhat);
-  double best = 1.0;
-  for (const PairRef& pr : pairs) {
+  const int np = (int)pairs.size();
+  std::vector<int> res(np);
+  std::vector<double> toi(np);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int q = 0; q < np; ++q) {
     double P[4][3], dP[4][3];
     int gi[4];
-    pair_points(G, x0, I0, pr, P, gi);
+    pair_points(G, x0, I0, pairs[q], P, gi);
     double Pd[4][3];
     int gd[4];
-    pair_points(G, dx, dI, pr, Pd, gd);
+    pair_points(G, dx, dI, pairs[q], Pd, gd);
     for (int k = 0; k < 4; ++k)
       for (int c = 0; c < 3; ++c) dP[k][c] = Pd[k][c];
-    double t;
-    int r = accd(kind_of(pr), P, dP, 0.1, 1.0, G.accd_max, &t);
-    if (r == 2) return ERR_CCD_MAXIT;
-    if (r == 1) best = std::min(best, t);
+    res[q] = accd(kind_of(pairs[q]), P, dP, 0.1, 1.0, G.accd_max, &toi[q]);
+  }
+  double best = 1.0;
+  for (int q = 0; q < np; ++q) {
+    if (res[q] == 2) return ERR_CCD_MAXIT;
+    if (res[q] == 1) best = std::min(best, toi[q]);
   }
   *out = best;
   return OK;
@@ -1287,27 +1368,34 @@ bool placement_ok(const Gel& G, const double* I0, const double* I1, int* err) {
   *err = s;
   if (s != OK) return false;
   std::vector<PairRef> pairs = candidate_pairs(G, G.x.data(), G.x.data(), I0, I1, G.dhat);
-  bool hit = false;
-  for (const PairRef& pr : pairs) {  // same pairs the sweep examined: any hit means t < 1
+  const int np = (int)pairs.size();
+  std::vector<int> res(np);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int q = 0; q < np; ++q) {  // same pairs the sweep examined: any hit means t < 1
     double P[4][3], dP[4][3], Pd[4][3];
     int gi[4], gd[4];
-    pair_points(G, G.x.data(), I0, pr, P, gi);
-    pair_points(G, zx.data(), dI.data(), pr, Pd, gd);
+    pair_points(G, G.x.data(), I0, pairs[q], P, gi);
+    pair_points(G, zx.data(), dI.data(), pairs[q], Pd, gd);
     for (int k = 0; k < 4; ++k)
       for (int c = 0; c < 3; ++c) dP[k][c] = Pd[k][c];
     double tt;
-    int r = accd(kind_of(pr), P, dP, 0.1, 1.0, G.accd_max, &tt);
-    if (r == 1) hit = true;
+    res[q] = accd(kind_of(pairs[q]), P, dP, 0.1, 1.0, G.accd_max, &tt);
   }
-  if (hit) return false;
+  for (int q = 0; q < np; ++q)
+    if (res[q] == 1) return false;
   // after placement every pair must be strictly separated
   std::vector<PairRef> after = candidate_pairs(G, G.x.data(), G.x.data(), I1, I1, G.dhat);
-  for (const PairRef& pr : after) {
+  const int na = (int)after.size();
+  std::vector<char> sep(na);
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < na; ++q) {
     double P[4][3];
     int gi[4];
-    pair_points(G, G.x.data(), I1, pr, P, gi);
-    if (!(pair_d2(kind_of(pr), P) > 0.0)) return false;
+    pair_points(G, G.x.data(), I1, after[q], P, gi);
+    sep[q] = pair_d2(kind_of(after[q]), P) > 0.0;
   }
+  for (int q = 0; q < na; ++q)
+    if (!sep[q]) return false;
   return true;
 }
 
@@ -1835,6 +1923,22 @@ int or_friction_pair(int kind, const double* Plag, const double* Pnow, double dh
   for (int i = 0; i < 12; ++i)
     for (int j = 0; j < 12; ++j) H[12 * i + j] = D.h[i][j];
   return 1;
+}
+
+// Threads of the parallel loops (n <= 0: all available); results do not depend on it.
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
+int or_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 void or_eigh(int n, const double* A, double* w, double* V) {

@@ -35,7 +35,8 @@ class tx_params(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
                 ("ls_max_halvings", ctypes.c_int32), ("accd_max_iter", ctypes.c_int32),
                 ("max_split_depth", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("refine_max", ctypes.c_int32), ("pcg_cta_slices", ctypes.c_int32)]
+                ("refine_max", ctypes.c_int32), ("pcg_cta_slices", ctypes.c_int32),
+                ("pcg_plan", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class tx_gel_desc(ctypes.Structure):
@@ -67,7 +68,8 @@ class tx_profile(ctypes.Structure):
                 ("names", ctypes.c_char_p * PROFILE_MAX), ("ms", ctypes.c_double * PROFILE_MAX),
                 ("launches", ctypes.c_int64 * PROFILE_MAX), ("flops", ctypes.c_double * PROFILE_MAX),
                 ("bytes", ctypes.c_double * PROFILE_MAX), ("pcg_iters", ctypes.c_int64),
-                ("newton_iters", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("newton_iters", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("pcg_resident_launches", ctypes.c_int64), ("pcg_streaming_launches", ctypes.c_int64)]
 
     def as_dict(self):
         phases = {}
@@ -75,7 +77,9 @@ class tx_profile(ctypes.Structure):
             phases[self.names[k].decode()] = dict(ms=self.ms[k], launches=int(self.launches[k]),
                                                   flops=self.flops[k], bytes=self.bytes[k])
         return dict(phases=phases, pcg_iters=int(self.pcg_iters), newton_iters=int(self.newton_iters),
-                    kernel_launches=int(self.kernel_launches))
+                    kernel_launches=int(self.kernel_launches),
+                    pcg_resident_launches=int(self.pcg_resident_launches),
+                    pcg_streaming_launches=int(self.pcg_streaming_launches))
 
 
 class TxError(RuntimeError):
@@ -95,6 +99,8 @@ _SIGS = [
     ("tx_params_default", None, [ctypes.POINTER(tx_params)]),
     ("tx_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tx_last_error", ctypes.c_char_p, []),
+    ("tx_debug_inject", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    ("tx_peak_fma", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, c_dp, c_dp, ctypes.c_void_p]),
     ("tx_gel_create", ctypes.c_int, [ctypes.POINTER(tx_gel_desc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("tx_gel_step", ctypes.c_int, [ctypes.c_void_p, c_dp, ctypes.c_double]),
     ("tx_gel_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_dp,
@@ -231,6 +237,24 @@ class GelDesc:
 
 
 # ------------------------------------------------------------------ C entry points
+TX_INJECT_ALLOC_FAIL = 1
+TX_INJECT_WAIT_TIMEOUT = 2
+
+
+def tx_debug_inject(kind, count):
+    """Fault-injection test hook (host-side allocation failure, or device waits that give up)."""
+    _check(load().tx_debug_inject(int(kind), int(count)), "tx_debug_inject")
+
+
+def tx_peak_fma(bits=64, iters=20000, stream=None):
+    """(flops, ms) of one FMA-peak launch (FP64: bits = 64, FP32: bits = 32)."""
+    f = ctypes.c_double(0.0)
+    t = ctypes.c_double(0.0)
+    _check(load().tx_peak_fma(int(bits), int(iters), ctypes.byref(f), ctypes.byref(t), _stream(stream)),
+           "tx_peak_fma")
+    return f.value, t.value
+
+
 def tx_gel_create(desc: GelDesc, stream=None):
     h = ctypes.c_void_p()
     _check(load().tx_gel_create(ctypes.byref(desc.c), _stream(stream), ctypes.byref(h)), "tx_gel_create")

@@ -42,32 +42,6 @@ __device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane,
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
-// Barrier of the nc CTAs of one group (all co-resident: cooperative launch).  Arrival is a
-// release add on the group's counter, the wait an acquire poll bounded by a spin limit; a wait
-// that gives up sets *err and the CTA returns false (the host reports a device timeout).
-__device__ __forceinline__ bool group_barrier(unsigned* cnt, int nc, unsigned& epoch, int* err, int* s_fail) {
-  __syncthreads();
-  epoch += 1;
-  if (nc > 1 && threadIdx.x == 0) {
-    const unsigned target = epoch * (unsigned)nc;
-    __threadfence();
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
-    unsigned spins = 0, cur;
-    while (true) {
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(cnt) : "memory");
-      if (cur >= target) break;
-      if (++spins > (1u << 22)) {
-        atomicExch(err, 1);
-        *s_fail = 1;
-        break;
-      }
-      __nanosleep(20);
-    }
-  }
-  __syncthreads();
-  return *s_fail == 0;
-}
-
 // Per-CTA view of its group (gels [g0, g0 + ng), CTAs [c0, c0 + nc)).  A group of several CTAs
 // holds a single gel; a group of one CTA may hold several small gels.
 struct PcgCta {
@@ -91,6 +65,34 @@ __device__ __forceinline__ PcgCta pcg_cta(const Dev& d, const PcgPlan& plan) {
   c.bar = d.bar + gr;
   c.epoch = 0;
   return c;
+}
+
+// Barrier of the nc CTAs of one group (all co-resident: cooperative launch).  Arrival is a
+// release add on the group's counter, the wait an acquire poll bounded by d.wait_limit polls; a
+// wait that gives up sets *err and the CTA returns false (the host reports a device timeout).
+// d.wait_extra (0 in normal operation; set only by the library's fault-injection test hook) adds
+// arrivals that never come, so that every wait runs into its limit.
+__device__ __forceinline__ bool group_barrier(PcgCta& c, const Dev& d, int* s_fail) {
+  __syncthreads();
+  c.epoch += 1;
+  if ((c.nc > 1 || d.wait_extra) && threadIdx.x == 0) {
+    const unsigned target = c.epoch * (unsigned)c.nc + d.wait_extra;
+    __threadfence();
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(c.bar) : "memory");
+    unsigned spins = 0, cur;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(c.bar) : "memory");
+      if (cur >= target) break;
+      if (++spins > d.wait_limit) {
+        atomicExch(d.err, 1);
+        *s_fail = 1;
+        break;
+      }
+      __nanosleep(20);
+    }
+  }
+  __syncthreads();
+  return *s_fail == 0;
 }
 
 // Group totals of quantities [k0, k1) from the per-slice partials dsm[(s - s0) * 4 + k]: every
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double*
     }
   }
   if (c.nc > 1) {
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, s_fail)) return false;
+    if (!group_barrier(c, d, s_fail)) return false;
     for (int t = wid; t < nk; t += (int)(blockDim.x >> 5)) {
       const int k = k0 + t;
       double v = 0.0;
@@ -136,7 +138,7 @@ __device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double*
 __device__ __forceinline__ void pcg_epilogue(const Dev& d, const PcgPlan& plan, PcgCta& c, double* dsm,
                                              double (*tot)[4], const int* gact, int* s_fail) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, s_fail)) return;  // p complete, exchange slots free
+  if (!group_barrier(c, d, s_fail)) return;  // p complete, exchange slots free
   for (int s = c.s0 + wid; s < c.s1; s += (int)(blockDim.x >> 5)) {
     const int j = plan.slice_gel[s] - c.g0;
     double gp = 0.0, m = 0.0;

@@ -5,6 +5,7 @@
 // One persistent cooperative kernel runs every iteration; grid-wide dot products are per-CTA
 // partials that every CTA sums in the same order after a bounded grid barrier, so all CTAs take
 // identical decisions and the result does not depend on timing.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -186,25 +187,69 @@ constexpr int NOALLOC_MAX_CTAS = 1024;
 constexpr size_t NOALLOC_DOUBLES = (size_t)21 * NOALLOC_MAX_ROWS + 2 * NOALLOC_MAX_CTAS + 4;
 static __device__ __align__(256) double g_pcg_scratch[NOALLOC_DOUBLES];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static double* g_scratch_dev[NOALLOC_MAX_DEVICES] = {nullptr};
+// Device addresses of the scratch array, one per CUDA context that used it.  The symbol's
+// host-side name is only a stand-in, so its address is looked up (cudaGetSymbolAddress, with the
+// context current) the first time a context calls; the cache is keyed by the context's unique
+// id, so a context created after a device reset (where the module, and the array, may have moved)
+// looks the address up again instead of using a stale one.
+constexpr int NOALLOC_MAX_CONTEXTS = 64;
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+static ScratchEntry g_scratch_ctx[NOALLOC_MAX_CONTEXTS];
+static int g_scratch_n = 0;
 static std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device.  The symbol's host-side name is
-// only a stand-in, so the address is looked up once per device (with that device current).
-static cudaError_t scratch_on_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_dev[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_pcg_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_dev[dev] = static_cast<double*>(ptr);
+// unique id of the current context (driver entry points taken through the runtime); false if
+// there is none yet or the driver does not offer it
+static bool current_context_id(unsigned long long* id) {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrentFn>(f0);
+      get_id = reinterpret_cast<GetIdFn>(f1);
+    }
+    cudaGetLastError();
   }
-  *out = g_scratch_dev[dev];
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the current context.
+static cudaError_t scratch_in_current_context(double** out) {
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (have_id)
+    for (int k = 0; k < g_scratch_n; ++k)
+      if (g_scratch_ctx[k].ctx_id == id) {
+        *out = g_scratch_ctx[k].ptr;
+        return cudaSuccess;
+      }
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_pcg_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(ptr);
+  if (have_id) {  // remember it (the oldest entry makes room when the table is full)
+    if (g_scratch_n == NOALLOC_MAX_CONTEXTS) {
+      for (int k = 1; k < NOALLOC_MAX_CONTEXTS; ++k) g_scratch_ctx[k - 1] = g_scratch_ctx[k];
+      g_scratch_n -= 1;
+    }
+    g_scratch_ctx[g_scratch_n++] = {id, *out};
+  }
   return cudaSuccess;
 }
 
@@ -287,7 +332,7 @@ extern "C" tx_status tx_bsr_pcg_noalloc(int32_t n, const int32_t* row_ptr, const
     return TX_ERR_CUDA;
   if (nsm > NOALLOC_MAX_CTAS) return TX_ERR_ARG;
   double* buf = nullptr;
-  if (scratch_on_current_device(&buf) != cudaSuccess) return TX_ERR_CUDA;
+  if (scratch_in_current_context(&buf) != cudaSuccess) return TX_ERR_CUDA;
   const size_t vec = (size_t)3 * n;
   BsrPcgArgs a;
   a.n = n;

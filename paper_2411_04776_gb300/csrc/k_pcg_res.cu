@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
     }
   }
   res_post(d, c, dsm, 0, 3, 0, tot);
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
   {
     ResPrefetch pf;
     res_prefetch(d, c, 0, 3, 0, pf);
@@ -262,17 +262,21 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
     rhoj[q] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
   }
   __syncthreads();
+  // a non-finite entry of the previous direction anywhere in the gel makes its sums non-finite
+  // and rho = 0: the solve then starts from zero without touching that direction
   if (mine) {
     const double rho = rhoj[j];
-    x0 = rho * xp0; x1 = rho * xp1; x2 = rho * xp2;
-    r0 = fma(-rho, a0, r0); r1 = fma(-rho, a1, r1); r2 = fma(-rho, a2, r2);
+    if (rho != 0.0) {
+      x0 = rho * xp0; x1 = rho * xp1; x2 = rho * xp2;
+      r0 = fma(-rho, a0, r0); r1 = fma(-rho, a1, r1); r2 = fma(-rho, a2, r2);
+    }
     u0 = fma(M[2], r2, fma(M[1], r1, M[0] * r0));
     u1 = fma(M[5], r2, fma(M[4], r1, M[3] * r0));
     u2 = fma(M[8], r2, fma(M[7], r1, M[6] * r0));
     d.u[row] = make_double4_32a(u0, u1, u2, 0.0);
   }
   // u complete before the SpMV; every CTA has read the start's sums before any reuses their slots
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
   // ---- w = A u, m = M^-1 w; dot products of iteration 0
   if (has) {
     double ga = 0.0, de = 0.0, rr = 0.0;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
     }
   }
   res_post(d, c, dsm, 0, 3, 0, tot);
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
   for (int i = 0;; ++i) {
     const int par = i & 1;
     double n0 = 0, n1 = 0, n2 = 0;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
       }
     }
     res_post(d, c, dsm, 0, 3, par ^ 1, tot);
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
   }
   if (mine) d.p[row] = make_double4_32a(x0, x1, x2, 0.0);
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
     }
   }
   res_post(d, c, dsm, 0, 3, 0, tot);
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
   {
     ResPrefetch pf;
     res_prefetch(d, c, 0, 3, 0, pf);
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
     rhoj[q] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
   }
   __syncthreads();
-  if (mine) {
+  if (mine && rhoj[j] != 0.0) {  // rho = 0 (no usable previous direction): start from zero
     const double rho = rhoj[j];
     P0 = rho * xp0; P1 = rho * xp1; P2 = rho * xp2;
     R0 = fma(-rho, a0, R0); R1 = fma(-rho, a1, R1); R2 = fma(-rho, a2, R2);
@@ -450,7 +454,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
     if (lane == 0) dsm[4 * wid + 2] = rr;
   }
   res_post(d, c, dsm, 2, 3, 1, tot);
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
   {
     ResPrefetch pf;
     res_prefetch(d, c, 2, 3, 1, pf);
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       u2 = fmaf(M[8], r2, fmaf(M[7], r1, M[6] * r0));
       d.u32[row] = make_float4(u0, u1, u2, 0.f);
     }
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     if (has) {
       double ga = 0.0, de = 0.0, rr = 0.0;
       if (in) {
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       }
     }
     res_post_f(d, c, dsm, 0, 3, 0, tot);
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     // ---- inner pipelined CG in FP32
     for (int i = 0;; ++i) {
       const int par = i & 1;
@@ -582,7 +586,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
         }
       }
       res_post_f(d, c, dsm, 0, 3, par ^ 1, tot);
-      if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+      if (!group_barrier(c, d, &s_fail)) return;
     }
     // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p (FP32 values, FP64 arithmetic)
     const bool rn = has && run[j];
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       P2 += (double)x2;
       d.p[row] = make_double4_32a(P0, P1, P2, 0.0);
     }
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     if (has) {
       double rr = 0.0;
       if (rn) {
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
       if (lane == 0) dsm[4 * wid + 2] = rr;
     }
     res_post(d, c, dsm, 2, 3, 0, tot);
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     {
       ResPrefetch pf;
       res_prefetch(d, c, 2, 3, 0, pf);

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     bbj[j] = tot[j][3];
     thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
   }
-  if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;  // u complete before the SpMV
+  if (!group_barrier(c, d, &s_fail)) return;  // u complete before the SpMV
   for (int k = 1;; ++k) {
     // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
     for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
       d.r[r] = rv;
       d.u[r] = mul3(d.Minv + 9 * r, rv);
     }
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
   }
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       d.s32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
     }
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     // ---- inner FP32 CG (Chronopoulos-Gear), same structure as the FP64 kernel
     for (int k = 1;; ++k) {
       for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
         d.r32[r] = rv;
         d.u32[r] = mul3f(d.Minv32 + 9 * r, rv);
       }
-      if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+      if (!group_barrier(c, d, &s_fail)) return;
     }
     // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p
     for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       p.z += (double)x.z;
       d.p[r] = p;
     }
-    if (!group_barrier(c.bar, c.nc, c.epoch, d.err, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
     for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
       double rr = 0.0;
       if (run[plan.slice_gel[s] - c.g0]) {

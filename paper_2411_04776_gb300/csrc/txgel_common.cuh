@@ -185,6 +185,8 @@ struct Dev {
   int* c1_n;
   double4_32a* cgrad;  // contact gradient per row: accumulated by the contact kernels, added by the gather
   int* err;
+  unsigned wait_limit;  // polls a bounded device-side wait makes before it gives up (sets *err)
+  unsigned wait_extra;  // fault-injection test hook: arrivals a group barrier waits for that never come (0)
 };
 
 // Partition of the slices of the gels being solved over the CTAs of the persistent PCG kernels

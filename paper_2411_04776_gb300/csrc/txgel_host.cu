@@ -176,7 +176,7 @@ tx_status check_desc(const tx_gel_desc* d) {
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
-      p.pcg_cta_slices < -1)
+      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 1 || p.reserved0 != 0)
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
     if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
@@ -339,15 +339,36 @@ uint64_t fnv(const void* p, size_t n, uint64_t h) {
   return h;
 }
 
+// ---------------------------------------------------------------- fault injection (test hook)
+// Host-side only: an allocation made to fail before it reaches the CUDA runtime, and bounded
+// device waits told to wait for an arrival that never comes.  Nothing faults the device.
+std::atomic<int> g_inject_alloc{0};  // > 0: the allocation this many allocations from now fails
+std::atomic<int> g_inject_wait{0};   // Newton iterations whose PCG barriers wait for a missing arrival
+constexpr unsigned WAIT_LIMIT = 1u << 22;        // polls of a bounded device wait (~0.1-1 s)
+constexpr unsigned WAIT_LIMIT_INJECTED = 1u << 12;  // the same when a timeout is being injected
+
+bool injected_alloc_failure() {
+  int k = g_inject_alloc.load();
+  while (k > 0) {
+    if (g_inject_alloc.compare_exchange_weak(k, k - 1)) return k == 1;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- device allocation
 struct DevMem {
   std::vector<void*> ptrs;
   size_t bytes = 0;
+  bool failed = false;  // some get() returned nullptr
   template <class T>
   T* get(size_t n) {
     if (n == 0) n = 1;
     void* p = nullptr;
-    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+    if (injected_alloc_failure() || cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      failed = true;
+      return nullptr;
+    }
     ptrs.push_back(p);
     bytes += n * sizeof(T);
     return static_cast<T*>(p);
@@ -356,8 +377,15 @@ struct DevMem {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
     bytes = 0;
+    failed = false;
   }
 };
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
 
 struct Task {
   double pa[7], pb[7];
@@ -392,6 +420,7 @@ struct Prof {
   double flops[PR_N] = {};
   double bytes[PR_N] = {};
   long long pcg_iters = 0, newton_iters = 0;
+  long long pcg_res = 0, pcg_stream = 0;  // PCG launches per kernel family
   struct Pending {
     cudaEvent_t a, b;
     int phase;
@@ -467,6 +496,7 @@ struct tx_batch {
     double us[8] = {};
     int best = -1;
   };
+  bool force_stream = false;  // some gel asked for the streaming PCG kernels (tx_params.pcg_plan = 1)
   bool tune_on = false;
   std::map<long long, Tune> tune;
   long long tune_key = -1;  // class of the current round (-1: not timing)
@@ -575,25 +605,34 @@ tx_status upload_info(tx_batch* b) {
 }
 
 // (Re)allocate the candidate-pair segments with the capacities in gi[].pcap.
+// The new segments are allocated before the old ones are freed: if the device is out of memory the
+// handle keeps its previous segments and capacities (TX_ERR_OOM), never a null segment.
 tx_status alloc_pairs(tx_batch* b) {
   CK(cudaStreamSynchronize(b->st));
-  b->pair_mem.release();
+  std::vector<GelInfo> old = b->gi;
   int total = 0;
   for (int g = 0; g < b->n; ++g) {
     b->gi[g].pbase = total;
     total += b->gi[g].pcap;
   }
-  b->d.pairs = b->pair_mem.get<int4>(total);
-  b->d.pslot_gel = b->pair_mem.get<int>(total);
-  b->d.cwork = b->pair_mem.get<int>(total);
-  b->d.crec_cap = std::min(total, CREC_PER_GEL * b->n + CREC_BASE);
-  b->d.crec = reinterpret_cast<PairBarrier*>(b->pair_mem.get<double>((size_t)b->d.crec_cap * pair_record_doubles()));
-  b->d.chv = b->pair_mem.get<double>((size_t)b->d.crec_cap * CH_STRIDE);
-  b->d.chbp = b->pair_mem.get<int>((size_t)b->d.crec_cap * CH_BP);
-  b->d.c1rec = b->pair_mem.get<C1Rec>(total);
-  if (!b->d.pairs || !b->d.pslot_gel || !b->d.cwork || !b->d.crec || !b->d.chv || !b->d.chbp ||
-      !b->d.c1rec)
+  DevMem nm;
+  Dev nd = b->d;
+  nd.pairs = nm.get<int4>(total);
+  nd.pslot_gel = nm.get<int>(total);
+  nd.cwork = nm.get<int>(total);
+  nd.crec_cap = std::min(total, CREC_PER_GEL * b->n + CREC_BASE);
+  nd.crec = reinterpret_cast<PairBarrier*>(nm.get<double>((size_t)nd.crec_cap * pair_record_doubles()));
+  nd.chv = nm.get<double>((size_t)nd.crec_cap * CH_STRIDE);
+  nd.chbp = nm.get<int>((size_t)nd.crec_cap * CH_BP);
+  nd.c1rec = nm.get<C1Rec>(total);
+  if (nm.failed) {
+    nm.release();
+    b->gi = old;
     return TX_ERR_OOM;
+  }
+  b->pair_mem.release();
+  b->pair_mem = nm;
+  b->d = nd;
   b->d.npslots = total;
   std::vector<int> slot(total);
   for (int g = 0; g < b->n; ++g)
@@ -604,15 +643,23 @@ tx_status alloc_pairs(tx_batch* b) {
 
 tx_status alloc_hash(tx_batch* b) {
   CK(cudaStreamSynchronize(b->st));
-  b->hash_mem.release();
+  std::vector<GelInfo> old = b->gi;
   int total = 0;
   for (int g = 0; g < b->n; ++g)
     for (int t = 0; t < NTAB; ++t) {
       b->gi[g].he0[t] = total;
       total += b->gi[g].hcap[t];
     }
-  b->d.hent = b->hash_mem.get<int2>(total);
-  if (!b->d.hent) return TX_ERR_OOM;
+  DevMem nm;
+  int2* hent = nm.get<int2>(total);
+  if (nm.failed) {
+    nm.release();
+    b->gi = old;
+    return TX_ERR_OOM;
+  }
+  b->hash_mem.release();
+  b->hash_mem = nm;
+  b->d.hent = hent;
   return upload_info(b);
 }
 
@@ -873,6 +920,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   for (int g = 0; g < n; ++g) {
     spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
     if (b->mesh[g].prm.pcg_cta_slices < 0) b->tune_on = true;
+    if (b->mesh[g].prm.pcg_plan == 1) b->force_stream = true;
   }
   if (spc_min <= 0) spc_min = b->mixed ? PCG_SLICES_MIXED : PCG_SLICES_FP64;
   b->pcg_spc_min = spc_min;
@@ -979,11 +1027,13 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   b->en_ticket = M.get<unsigned>(n);
   b->scan_tmp = M.get<int>((nq + 1023) / 1024 + 2);
   int* sg_buf = M.get<int>(nslices);
-  if (!d.gi || !d.x || !d.tscr || !d.ctr || !b->scan_tmp || !sg_buf || (b->mixed ? !d.vals32 : !d.vals)) {
+  if (M.failed) {
     M.release();
     delete b;
     return TX_ERR_OOM;
   }
+  d.wait_limit = WAIT_LIMIT;
+  d.wait_extra = 0;
   b->plan.slice_gel = sg_buf;
   b->plan.max_slices = 1;
   b->plan.ngroups = 0;
@@ -998,13 +1048,19 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     d.r32 = (float4*)M.get<float4>(rows);
     d.x32 = (float4*)M.get<float4>(rows);
   }
-  cudaHostAlloc((void**)&b->gc_h, sizeof(GelCtl) * n, cudaHostAllocDefault);
-  cudaHostAlloc((void**)&b->gv_h, sizeof(GelVar) * n, cudaHostAllocDefault);
-  if (!b->gc_h || !b->gv_h) {
+  host_alloc((void**)&b->gc_h, sizeof(GelCtl) * n);
+  host_alloc((void**)&b->gv_h, sizeof(GelVar) * n);
+  auto fail_create = [&](tx_status st) {
+    b->pair_mem.release();
+    b->hash_mem.release();
     M.release();
+    if (b->gc_h) cudaFreeHost(b->gc_h);
+    if (b->gv_h) cudaFreeHost(b->gv_h);
+    cudaGetLastError();
     delete b;
-    return TX_ERR_OOM;
-  }
+    return st;
+  };
+  if (M.failed || !b->gc_h || !b->gv_h) return fail_create(TX_ERR_OOM);
   std::memset(b->gc_h, 0, sizeof(GelCtl) * n);
   auto up = [&](void* dst, const void* src, size_t bytes) {
     return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -1057,20 +1113,12 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   if (e == cudaSuccess) e = cudaMemset(d.tscr, 0, sizeof(double) * TS * (size_t)std::max(tets, 1));
   if (e != cudaSuccess) {
     g_err = cudaGetErrorString(e);
-    M.release();
-    delete b;
-    return TX_ERR_CUDA;
+    return fail_create(TX_ERR_CUDA);
   }
   tx_status s = alloc_pairs(b);
   if (s == TX_OK) s = alloc_hash(b);
   if (s == TX_OK && cudaDeviceSynchronize() != cudaSuccess) s = TX_ERR_CUDA;
-  if (s != TX_OK) {
-    b->pair_mem.release();
-    b->hash_mem.release();
-    M.release();
-    delete b;
-    return s;
-  }
+  if (s != TX_OK) return fail_create(s);
   b->run.resize(n);
   b->nnzb_real.assign(n, 0.0);
   b->nfree.assign(n, 0.0);
@@ -1123,6 +1171,8 @@ tx_status rollback(tx_batch* b, const std::vector<int>& gels) {
     const GelInfo& G = b->gi[g];
     CK(cudaMemcpyAsync(b->d.x + G.v0, b->x0 + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
     CK(cudaMemcpyAsync(b->d.v + G.v0, b->v0 + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
+    // the failed solve's direction must not seed the next solve's Galerkin start
+    CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
     std::memcpy(b->run[g].pose, b->run[g].pose_req, sizeof(double) * 7);
   }
   return TX_OK;
@@ -1243,14 +1293,13 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
       for (int g : retry) finish_request(b, g, TX_ERR_OOM);
       return TX_OK;
     }
-    if (regrow_pairs) {
-      s = alloc_pairs(b);
-      if (s != TX_OK) return s;
+    if (regrow_pairs) s = alloc_pairs(b);
+    if (s == TX_OK && regrow_hash) s = alloc_hash(b);
+    if (s == TX_ERR_OOM) {  // the gels that needed more room fail their request; the rest go on
+      for (int g : retry) finish_request(b, g, TX_ERR_OOM);
+      return rollback(b, retry);
     }
-    if (regrow_hash) {
-      s = alloc_hash(b);
-      if (s != TX_OK) return s;
-    }
+    if (s != TX_OK) return s;
     return do_begin(b, retry, retries + 1);
   }
   return TX_OK;
@@ -1439,7 +1488,8 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
     const int occ_res = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
     // a multi-CTA group reduces three quantities at once, one warp each: two slice warps and the
     // control warp at least
-    res = occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC && (max_nc == 1 || max_slices >= 2);
+    res = !b->force_stream && occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC &&
+          (max_nc == 1 || max_slices >= 2);
     const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
     if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
     if (attempt > 400) {
@@ -1724,8 +1774,24 @@ tx_status do_newton(tx_batch* b) {
   s = prepare_pcg_plan(b, set);
   if (s != TX_OK) return s;
   const int accd_max = newton_accd_max(b);
+  // fault-injection test hook: this iteration's PCG barriers wait for an arrival that never comes
+  // (with a short limit), so every wait gives up and the step reports a device timeout
+  struct WaitGuard {
+    Dev& d;
+    ~WaitGuard() {
+      d.wait_extra = 0;
+      d.wait_limit = WAIT_LIMIT;
+    }
+  } wait_guard{d};
+  for (int k = g_inject_wait.load(); k > 0; k = g_inject_wait.load())
+    if (g_inject_wait.compare_exchange_weak(k, k - 1)) {
+      d.wait_extra = 1;
+      d.wait_limit = WAIT_LIMIT_INJECTED;
+      break;
+    }
   s = run_newton_launches(b, set, pcg_max, refine, accd_max);
   if (s != TX_OK) return s;
+  for (int k = 0; k < b->nparts; ++k) (b->parts[k].res ? b->prof.pcg_res : b->prof.pcg_stream) += 1;
   s = post_pcg_finish(b);
   if (s != TX_OK) return s;
   tune_record(b, set);
@@ -1748,6 +1814,12 @@ tx_status do_newton(tx_batch* b) {
     if (over.empty()) break;
     for (int g : over) b->gi[g].pcap = std::max(2 * b->gi[g].pcap, b->gv_h[g].npair + b->gv_h[g].npair / 2 + 64);
     s = alloc_pairs(b);
+    if (s == TX_ERR_OOM) {
+      for (int g : over) finish_request(b, g, TX_ERR_OOM);
+      s = rollback(b, over);
+      if (s != TX_OK) return s;
+      break;
+    }
     if (s != TX_OK) return s;
     for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = PH_PARK;
     for (int g : over) b->gc_h[g].phase = PH_NEWTON;
@@ -1790,6 +1862,7 @@ tx_status do_newton(tx_batch* b) {
   }
   for (int g : set) {
     Run& R = b->run[g];
+    if (!R.in_request) continue;  // already finished (out of memory while growing its pair segment)
     const GelVar& v = b->gv_h[g];
     R.acc.pcg_iters += v.pcg_it;
     R.acc.refine_rounds += v.rounds;
@@ -1995,6 +2068,19 @@ const char* tx_status_str(tx_status s) {
 
 const char* tx_last_error(void) { return g_err.c_str(); }
 
+tx_status tx_debug_inject(int32_t kind, int32_t count) {
+  if (count < 0) return TX_ERR_ARG;
+  if (kind == TX_INJECT_ALLOC_FAIL) {
+    g_inject_alloc.store(count);
+    return TX_OK;
+  }
+  if (kind == TX_INJECT_WAIT_TIMEOUT) {
+    g_inject_wait.store(count);
+    return TX_OK;
+  }
+  return TX_ERR_ARG;
+}
+
 tx_status tx_batch_create(const tx_gel_desc* descs, int32_t n, void* stream, tx_batch** out) {
   if (!out) return TX_ERR_ARG;
   *out = nullptr;
@@ -2097,6 +2183,10 @@ tx_status tx_batch_set_state(tx_batch* b, int32_t g, const double* x, const doub
   if (x) s = copy_rows_in(b, g, b->d.x, x);
   if (s == TX_OK && v) s = copy_rows_in(b, g, b->d.v, v);
   if (s != TX_OK) return s;
+  // a new state: no previous Newton direction (the next solve starts from zero)
+  const GelInfo& G = b->gi[g];
+  CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
+  CK(cudaStreamSynchronize(b->st));
   if (pose) std::memcpy(b->run[g].pose, pose, sizeof(double) * 7);
   return TX_OK;
 }
@@ -2106,6 +2196,7 @@ tx_status tx_batch_reset(tx_batch* b, int32_t g) {
   const GelInfo& G = b->gi[g];
   CK(cudaMemcpyAsync(b->d.x + G.v0, b->d.X + G.v0, sizeof(double4_32a) * G.ns * SLICE, cudaMemcpyDeviceToDevice, b->st));
   CK(cudaMemsetAsync(b->d.v + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
+  CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));  // no previous direction
   CK(cudaStreamSynchronize(b->st));
   std::memcpy(b->run[g].pose, b->mesh[g].pose0, sizeof(double) * 7);
   b->run[g].last = tx_step_stats{};
@@ -2261,6 +2352,8 @@ tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out) {
     }
     out->pcg_iters = b->prof.pcg_iters;
     out->newton_iters = b->prof.newton_iters;
+    out->pcg_resident_launches = b->prof.pcg_res;
+    out->pcg_streaming_launches = b->prof.pcg_stream;
     out->kernel_launches = g_launch_count.load() - g_launch_mark;
   }
   g_launch_mark = g_launch_count.load();

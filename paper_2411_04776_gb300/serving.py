@@ -9,6 +9,11 @@ Newton iteration at a time together with every other admitted request (tx_batch_
 request that arrives while others are on the GPU joins at the next Newton-iteration boundary;
 finished requests leave the batch and free their budget immediately.
 
+Admission takes the oldest waiting requests first.  A request too large for the budget left over
+may be passed by younger requests that fit, but only `max_bypass` times: after that no younger
+request is admitted ahead of it until it fits, so a large gel cannot starve behind a stream of
+small ones.
+
 All numerical work runs in the CUDA library; this module is the host scheduling loop.
 """
 from __future__ import annotations
@@ -31,6 +36,7 @@ class Request:
     admitted: float = float("nan")
     done: float = float("nan")
     status: int = -1
+    bypassed: int = 0  # younger requests admitted while this one waited at the head of its queue
 
 
 def poisson_arrivals(n_envs: int, rate: float, duration: float, seed: int):
@@ -48,8 +54,10 @@ def poisson_arrivals(n_envs: int, rate: float, duration: float, seed: int):
 class GelServer:
     """Resident gels + admission by device footprint + continuous batching."""
 
-    def __init__(self, workloads, budget_bytes: float, precision=B.TX_PREC_MIXED, stream=None, **params):
+    def __init__(self, workloads, budget_bytes: float, precision=B.TX_PREC_MIXED, stream=None, max_bypass=8,
+                 **params):
         self.wls = list(workloads)
+        self.max_bypass = int(max_bypass)
         self.descs = [B.GelDesc.from_workload(w, precision=precision, **params) for w in self.wls]
         self.footprint = np.array([B.tx_gel_footprint_bytes(d) for d in self.descs], dtype=np.float64)
         self.budget = float(budget_bytes)
@@ -87,10 +95,16 @@ class GelServer:
         heads = [(q[0].arrival, e) for e, q in enumerate(self.queues) if q and e not in self.inflight]
         heads.sort()
         ids, poses, dts = [], [], []
+        waiting = []  # older heads that did not fit
         for _, e in heads:
             fp = self.footprint[e]
             if self.inflight_bytes + fp > self.budget:
+                waiting.append(self.queues[e][0])
+                if waiting[-1].bypassed >= self.max_bypass:
+                    break  # it has been passed often enough: keep the rest of the budget for it
                 continue
+            for w in waiting:
+                w.bypassed += 1
             req = self.queues[e].popleft()
             wl = self.wls[e]
             k = req.step % len(wl.poses)
@@ -157,10 +171,17 @@ class GelServer:
 
 
 def latency_summary(reqs):
-    lat = np.array([r.done - r.arrival for r in reqs if r.status == 0])
-    svc = np.array([r.done - r.admitted for r in reqs if r.status == 0])
-    if len(lat) == 0:
-        return {}
-    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
-            "service_p99_ms": float(np.percentile(svc, 99) * 1e3)}
+    """Request latency (arrival to completion) and service time (admission to completion)
+    percentiles over every completed request -- failed requests, often the slowest, included --
+    and, beside them, over the successful ones only, with the failure count."""
+    out = {"completed": len(reqs), "failed": sum(1 for r in reqs if r.status != 0)}
+    for tag, sel in (("", lambda r: True), ("ok_", lambda r: r.status == 0)):
+        lat = np.array([r.done - r.arrival for r in reqs if sel(r)])
+        svc = np.array([r.done - r.admitted for r in reqs if sel(r)])
+        if len(lat) == 0:
+            continue
+        out[tag + "p50_ms"] = float(np.percentile(lat, 50) * 1e3)
+        out[tag + "p99_ms"] = float(np.percentile(lat, 99) * 1e3)
+        out[tag + "service_p50_ms"] = float(np.percentile(svc, 50) * 1e3)
+        out[tag + "service_p99_ms"] = float(np.percentile(svc, 99) * 1e3)
+    return out

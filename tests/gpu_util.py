@@ -26,3 +26,16 @@ def smooth_state(wl, seed, amp=2e-5):
     x = X + disp
     xt = X + 0.5 * disp
     return x, xt, wl.dt
+
+
+GOLDEN_C1 = "c1_prism_oracle.npz"
+
+
+def load_golden_c1():
+    """FP64 oracle snapshots of the GelSight-Mini gel on the benchmark trajectory
+    (tests/golden/make_oracle_snapshots.py): displacements at the snapshot steps, contact forces,
+    substeps and active pairs per step."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", GOLDEN_C1)
+    z = np.load(path)
+    return {k: z[k] for k in z.files}

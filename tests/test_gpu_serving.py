@@ -12,11 +12,12 @@ from paper_2411_04776_gb300 import workloads as W  # noqa: E402
 from tests.gpu_util import PARITY_NEWTON_TOL, POS_TOL  # noqa: E402
 
 
-def test_serving_results_equal_alone_under_budget():
+@pytest.mark.parametrize("precision", [B.TX_PREC_FP64, B.TX_PREC_MIXED], ids=["fp64", "mixed"])
+def test_serving_results_equal_alone_under_budget(precision):
     wls = [W.small_gel_sphere(s) for s in range(4)] + [W.mini_gel(7, grid=W.GRID_MID, depth=0.5e-3)]
-    fp = [B.tx_gel_footprint_bytes(B.GelDesc.from_workload(w)) for w in wls]
+    fp = [B.tx_gel_footprint_bytes(B.GelDesc.from_workload(w, precision=precision)) for w in wls]
     budget = sorted(fp)[-1] + sorted(fp)[-2] + 1  # at most the two largest gels in flight
-    srv = S.GelServer(wls, budget, precision=B.TX_PREC_FP64, newton_tol=PARITY_NEWTON_TOL)
+    srv = S.GelServer(wls, budget, precision=precision, newton_tol=PARITY_NEWTON_TOL)
     # staggered arrivals: new requests join while others are mid-Newton
     schedule = [[0, 1, 2, 3, 4], [], [0], [1], [], [2, 4], [3], [0], [], [1, 2], [4], [3], [0, 1]]
     done = srv.run_schedule(schedule)
@@ -28,7 +29,7 @@ def test_serving_results_equal_alone_under_budget():
     assert overlaps > 0
     for e, w in enumerate(wls):
         n_steps = int(srv.cursor[e])
-        alone = B.Gel.from_workload(w, newton_tol=PARITY_NEWTON_TOL)
+        alone = B.Gel.from_workload(w, newton_tol=PARITY_NEWTON_TOL, precision=precision)
         for s in range(n_steps):
             assert alone.step(w.poses[s], w.dt) == 0
         xa = alone.state()[0]

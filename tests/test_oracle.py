@@ -732,3 +732,22 @@ def test_height_map_at_vertices_is_the_vertex_height():
     for k in np.nonzero(t)[0]:
         i, j = int(round(X[k, 0] / 0.002)), int(round(X[k, 1] / 0.002))
         assert abs(hm[j, i] - x[k, 2]) <= 1e-15
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's parallel loops only write per-element results and every sum is taken serially
+    in index order: one thread and all threads give bitwise the same trajectory."""
+    wl = W.small_gel_sphere(4)
+    runs = []
+    for threads in (1, 0):
+        O.set_threads(threads)
+        og = O.OracleGel.from_workload(wl, newton_tol=1e-7)
+        xs = []
+        for s in range(6):  # the sphere starts d_hat above the gel: contact from the first step
+            info = og.step(wl.poses[s], wl.dt)
+            assert info["status"] == 0
+            xs.append(og.state()[0].copy())
+        runs.append((np.array(xs), info["active_pairs"]))
+    O.set_threads(0)
+    assert runs[0][1] > 0
+    assert np.array_equal(runs[0][0], runs[1][0])
