@@ -100,6 +100,10 @@ def _declare(L):
     L.or_markers.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, dp, dp, ip]
     L.or_height_map.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, dp]
+    L.or_stationary_rule.restype = ctypes.c_int
+    L.or_stationary_rule.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_last_stationary.restype = ctypes.c_int
+    L.or_last_stationary.argtypes = [ctypes.c_void_p]
     L.or_set_threads.argtypes = [ctypes.c_int]
     L.or_get_threads.restype = ctypes.c_int
     L.or_friction_pair.restype = ctypes.c_int
@@ -172,7 +176,8 @@ class OracleGel:
                           fst.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         info = dict(status=s, newton_iters=int(stats[0]), pcg_iters=int(stats[1]),
                     ls_halvings=int(stats[2]), substeps=int(stats[3]), active_pairs=int(stats[4]),
-                    energy=float(fst[0]), min_distance=float(fst[1]))
+                    energy=float(fst[0]), min_distance=float(fst[1]),
+                    stationary=int(lib().or_last_stationary(self._h)))
         return info
 
     def step_attached(self, pose, case_pose, dt):
@@ -333,6 +338,12 @@ def friction_pair(kind, Plag, Pnow, dhat, kappa, eps_x, mu, eh):
     a = lib().or_friction_pair(int(kind), Pl, Pn, dhat, kappa, eps_x, mu, eh, ctypes.byref(e), _d(g)[1],
                                _d(H)[1], ctypes.byref(lam))
     return a, e.value, g, H.reshape(12, 12), lam.value
+
+
+def stationary_rule(gp, E):
+    """True if a failed line search with model decrease -gp at energy E ends the solve as
+    converged (stationary to FP64 energy resolution), False if the step fails."""
+    return bool(lib().or_stationary_rule(float(gp), float(E)))
 
 
 def psd_project(A):

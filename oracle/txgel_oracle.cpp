@@ -688,6 +688,7 @@ struct Gel {
   double fc[3] = {0, 0, 0};
   // stats of the last step
   int st_newton = 0, st_pcg = 0, st_ls = 0, st_substeps = 0, st_pairs = 0;
+  int st_stationary = 0;  // solves of the last step ended by the stationarity rule (READING R8b)
   double st_energy = 0, st_min_d = INF;
 };
 
@@ -1261,6 +1262,11 @@ int min_toi(const Gel& G, const double* x0, const double* dx, const double* I0, 
 }
 
 // ---------------- Newton solve of one (sub)step ----------------
+// READING R8b: after a line search that found no decrease down to 1e-12 alpha_0, the iterate counts
+// as converged when the model decrease -g.p of the direction is at most 1e-10 |E| (below what FP64
+// evaluations of E can resolve), otherwise the step fails.
+bool stationary_to_resolution(double gp, double E) { return -gp <= 1e-10 * std::fabs(E); }
+
 int newton_iterate(Gel& G, double h, const double* IW) {
   int n3 = 3 * G.N;
   std::vector<double> xn = G.x, xt(n3);
@@ -1323,10 +1329,11 @@ int newton_iterate(Gel& G, double h, const double* IW) {
       double gp = 0.0;
       for (int i = 0; i < n3; ++i)
         if (dof[i] >= 0) gp += grad[i] * p[i];
-      if (-gp <= 1e-10 * std::fabs(E)) {
+      if (stationary_to_resolution(gp, E)) {
         G.st_energy = E;
         G.st_pairs = ep.active;
         G.st_min_d = ep.min_d;
+        G.st_stationary++;
         return OK;
       }
       return ERR_LINESEARCH;
@@ -1593,7 +1600,7 @@ int or_step(void* g, const double* pose, double dt, int* stats, double* fstats) 
 // vertices driven with their frame to case_pose (their rest positions carried by it)
 int or_step_attached(void* g, const double* pose, const double* case_pose, double dt, int* stats, double* fstats) {
   Gel& G = *static_cast<Gel*>(g);
-  G.st_newton = G.st_pcg = G.st_ls = G.st_substeps = G.st_pairs = 0;
+  G.st_newton = G.st_pcg = G.st_ls = G.st_substeps = G.st_pairs = G.st_stationary = 0;
   G.st_energy = 0;
   G.st_min_d = INF;
   std::vector<double> x0 = G.x, v0 = G.v;
@@ -1924,6 +1931,14 @@ int or_friction_pair(int kind, const double* Plag, const double* Pnow, double dh
     for (int j = 0; j < 12; ++j) H[12 * i + j] = D.h[i][j];
   return 1;
 }
+
+// The stationarity rule on its own: 1 if a failed line search with model decrease -gp at energy E
+// ends the solve as converged, 0 if the step fails (READING R8b).
+int or_stationary_rule(double gp, double E) { return stationary_to_resolution(gp, E) ? 1 : 0; }
+
+// Solves of the last step that ended by the stationarity rule (READING R8b: the line search
+// found no resolvable decrease and -g.p <= 1e-10 |E|).
+int or_last_stationary(void* g) { return static_cast<Gel*>(g)->st_stationary; }
 
 // Threads of the parallel loops (n <= 0: all available); results do not depend on it.
 void or_set_threads(int n) {

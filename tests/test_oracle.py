@@ -751,3 +751,153 @@ def test_oracle_threads_do_not_change_results():
     O.set_threads(0)
     assert runs[0][1] > 0
     assert np.array_equal(runs[0][0], runs[1][0])
+
+
+# ---- pins of the barrier value, the candidate rule and the stationarity rule -------------------
+
+def north_star_barrier(d, dhat):
+    """b(d) = -(d - dhat)^2 ln(d / dhat) for 0 < d < dhat, 0 beyond (the task's barrier)."""
+    return -(d - dhat) ** 2 * math.log(d / dhat) if d < dhat else 0.0
+
+
+def barrier_geometries(d):
+    """Hand-built point-triangle and edge-edge configurations whose distance is d by construction,
+    one per closest-feature kind: point-face, point-edge, point-vertex, edge-edge (interior
+    points of both) and edge-edge (an endpoint against the other edge's interior)."""
+    tri = np.array([[0.0, 0.0, 0.0], [1e-3, 0.0, 0.0], [0.0, 1e-3, 0.0]])
+    u = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)  # in-plane outward normal of the edge t1-t2
+    mid = 0.5 * (tri[1] + tri[2])
+    out = {
+        "PT face": (0, np.vstack([[2e-4, 2e-4, d], tri])),
+        "PT edge": (0, np.vstack([mid + 0.6 * d * u + 0.8 * d * np.array([0.0, 0.0, 1.0]), tri])),
+        "PT vertex": (0, np.vstack([[-0.5 * d, -0.5 * d, -d / math.sqrt(2.0)], tri])),
+        "EE interior": (1, np.array([[-5e-4, 0.0, 0.0], [5e-4, 0.0, 0.0], [0.0, -5e-4, d], [0.0, 5e-4, d]])),
+        "EE endpoint": (1, np.array([[-5e-4, 0.0, 0.0], [5e-4, 0.0, 0.0], [0.0, 0.6 * d, 0.8 * d],
+                                     [0.0, 0.6 * d + 1e-3, 0.8 * d]])),
+    }
+    return out
+
+
+@pytest.mark.parametrize("d", [1e-7, 3e-6, 2e-5, 6e-5, 9.5e-5, 1.2e-4])
+def test_barrier_value_at_known_distances(d):
+    dhat = 1e-4
+    for name, (kind, P) in barrier_geometries(d).items():
+        d2, _ = O.distance2(kind, P)
+        assert abs(math.sqrt(d2) - d) <= 1e-12 * d, name
+        eps_x = 1e-3 * np.sum((P[1] - P[0]) ** 2) * np.sum((P[3] - P[2]) ** 2) if kind == 1 else 0.0
+        s, b, _, _ = O.pair_barrier(kind, P, dhat, eps_x)
+        want = north_star_barrier(d, dhat)
+        assert abs(b - want) <= 1e-9 * abs(want) + 1e-300, (name, b, want)
+        assert (s == 1) == (d >= dhat), name
+
+
+def _quat_R(q):
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _boundary(tets):
+    """Boundary triangles (faces of exactly one tet), their vertices and edges."""
+    f = np.concatenate([tets[:, [1, 2, 3]], tets[:, [0, 2, 3]], tets[:, [0, 1, 3]], tets[:, [0, 1, 2]]])
+    key = np.sort(f, axis=1)
+    uniq, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    tris = uniq[cnt == 1]
+    e = np.sort(np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [0, 2]]]), axis=1)
+    return np.unique(tris.ravel()), tris, np.unique(e, axis=0)
+
+
+def _point_segment(p, a, b):
+    ab = b - a
+    t = np.clip(np.einsum("...i,...i", p - a, ab) / np.einsum("...i,...i", ab, ab), 0.0, 1.0)
+    return np.linalg.norm(p - (a + t[..., None] * ab), axis=-1)
+
+
+def _point_triangle(p, a, b, c):
+    """Distance point-triangle: plane distance when the projection falls inside the triangle,
+    otherwise the nearest of the three edges."""
+    n = np.cross(b - a, c - a)
+    nn = np.einsum("...i,...i", n, n)
+    w = p - a
+    dist = np.einsum("...i,...i", w, n)
+    q = p - (dist / nn)[..., None] * n
+    inside = np.ones(q.shape[:-1], dtype=bool)
+    for u, v in ((a, b), (b, c), (c, a)):
+        inside &= np.einsum("...i,...i", np.cross(v - u, q - u), n) >= 0.0
+    plane = np.abs(dist) / np.sqrt(nn)
+    edges = np.minimum(np.minimum(_point_segment(p, a, b), _point_segment(p, b, c)), _point_segment(p, c, a))
+    return np.where(inside, plane, edges)
+
+
+def _segment_segment(a0, a1, b0, b1):
+    """Distance between segments: the line-line closest points when both fall inside the
+    segments, otherwise the nearest endpoint-to-segment distance."""
+    u, v, w0 = a1 - a0, b1 - b0, a0 - b0
+    A, B, C = (np.einsum("...i,...i", u, u), np.einsum("...i,...i", u, v), np.einsum("...i,...i", v, v))
+    D, E = np.einsum("...i,...i", u, w0), np.einsum("...i,...i", v, w0)
+    den = A * C - B * B
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = (B * E - C * D) / den
+        t = (A * E - B * D) / den
+    ok = (den > 1e-14 * A * C) & (s > 0) & (s < 1) & (t > 0) & (t < 1)
+    s, t = np.where(ok, s, 0.0), np.where(ok, t, 0.0)
+    pl = np.linalg.norm(w0 + s[..., None] * u - t[..., None] * v, axis=-1)
+    ends = np.minimum.reduce([_point_segment(a0, b0, b1), _point_segment(a1, b0, b1),
+                              _point_segment(b0, a0, a1), _point_segment(b1, a0, a1)])
+    return np.where(ok, np.minimum(pl, ends), ends)
+
+
+def _near(alo, ahi, blo, bhi, pad):
+    return np.all((alo - pad <= bhi) & (blo - pad <= ahi), axis=-1)
+
+
+@pytest.mark.parametrize("case", ["sphere", "prism"])
+def test_candidate_rule_and_active_set_against_all_pairs(case):
+    """Every primitive pair (gel surface vertex / indenter triangle, indenter vertex / gel surface
+    triangle, gel surface edge / indenter edge) is scanned with plain numpy: the pairs whose
+    bounding boxes come within d_hat on every axis (R20) must be exactly the oracle's candidates,
+    and the pairs closer than d_hat exactly its active pairs."""
+    if case == "sphere":
+        wl, steps = W.small_gel_sphere(0), 12
+    else:
+        wl, steps = W.mini_gel(3, grid=W.GRID_SMALL, kind="prism", depth=0.6e-3, n_press=8, slide=0.0,
+                               n_slide=0), 6
+    og = O.OracleGel.from_workload(wl)
+    for s in range(steps):
+        assert og.step(wl.poses[s], wl.dt)["status"] == 0
+    x, _, _, pose = og.state()
+    oc = og.pair_counts(x, pose)
+    IW = wl.indenter.verts @ _quat_R(pose[:4]).T + pose[4:]
+    sv, st, se = _boundary(wl.gel.tets)
+    itris = wl.indenter.tris
+    ie = np.unique(np.sort(np.concatenate([itris[:, [0, 1]], itris[:, [1, 2]], itris[:, [0, 2]]]), axis=1), axis=0)
+    dhat = wl.dhat
+    P = x[sv][:, None, :]
+    T = IW[itris][None, :, :, :]
+    cand_pt = _near(P, P, T.min(axis=2), T.max(axis=2), dhat)
+    d_pt = _point_triangle(P, T[:, :, 0], T[:, :, 1], T[:, :, 2])
+    Q = IW[:, None, :]
+    G = x[st][None, :, :, :]
+    cand_tp = _near(G.min(axis=2), G.max(axis=2), Q, Q, dhat)
+    d_tp = _point_triangle(Q, G[:, :, 0], G[:, :, 1], G[:, :, 2])
+    Ea = x[se][:, None, :, :]
+    Eb = IW[ie][None, :, :, :]
+    cand_ee = _near(Ea.min(axis=2), Ea.max(axis=2), Eb.min(axis=2), Eb.max(axis=2), dhat)
+    d_ee = _segment_segment(Ea[:, :, 0], Ea[:, :, 1], Eb[:, :, 0], Eb[:, :, 1])
+    mine = [int(cand_pt.sum()), int(cand_tp.sum()), int(cand_ee.sum()),
+            int((d_pt < dhat).sum()), int((d_tp < dhat).sum()), int((d_ee < dhat).sum())]
+    assert sum(mine[3:]) > 0 and (case == "sphere" or mine[5] > 0)
+    assert list(oc) == mine, (list(oc), mine)
+
+
+def test_stationarity_rule_both_sides():
+    """READING R8b: a line search that finds no decrease ends the solve as converged only when the
+    model decrease -g.p is at most 1e-10 |E|; a larger one is a failed step."""
+    for E in (3.7e-6, -2.0, 1.0):
+        tol = 1e-10 * abs(E)
+        assert O.stationary_rule(-0.5 * tol, E)
+        assert O.stationary_rule(-tol, E)
+        assert O.stationary_rule(0.0, E)
+        assert not O.stationary_rule(-2.0 * tol, E)
+        assert not O.stationary_rule(-1e3 * tol, E)
