@@ -142,6 +142,20 @@ tx_status tx_gel_create(const tx_gel_desc* desc, void* stream, tx_gel** out);
  * short arc in rotation) from its current pose to `pose`.  Blocks until the step has finished. */
 tx_status tx_gel_step(tx_gel* g, const double pose[7], double dt);
 
+/* TacEx Sec. "General GIPC Simulation Pipeline" (GIPC attachments): each step first sets the
+ * attachment targets from the sensor-case pose, then solves.  Like tx_gel_step, with the gel's
+ * attached (Dirichlet) vertices also moving, with their frame, from the current case pose to
+ * `case_pose`: at the end of the step each sits at its rest position carried by case_pose (a pose
+ * (qw, qx, qy, qz, tx, ty, tz) of the frame the rest mesh is given in; the identity at create and
+ * after a reset).  The attached vertices are placed before the indenter placement check; a split
+ * step halves the case motion with the indenter's; their velocity is their displacement over the
+ * step.  Blocks until the step has finished; on error the state, the indenter pose and the case
+ * pose stay at the step's start. */
+tx_status tx_gel_step_attached(tx_gel* g, const double pose[7], const double case_pose[7], double dt);
+
+/* The current case pose of an attachment-driven gel (identity if none was ever given). */
+tx_status tx_gel_case_pose(const tx_gel* g, double case_pose[7]);
+
 /* Reads the state: x, v (n_verts x 3, may be NULL), contact force (3, may be NULL) and the last
  * step's statistics (may be NULL).  If device_ptrs != 0, x and v are device pointers and the copy
  * is enqueued on the gel's stream (ordered after the last step); otherwise host pointers and the
@@ -181,6 +195,10 @@ int32_t tx_batch_size(const tx_batch* b);
 
 /* Steps every gel once (poses: n x 7, dts: n) and blocks until all finished.  statuses: n. */
 tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_status* statuses);
+/* tx_batch_step with every gel attachment-driven as in tx_gel_step_attached (case_poses: n x 7;
+ * NULL: a plain tx_batch_step). */
+tx_status tx_batch_step_attached(tx_batch* b, const double* poses, const double* case_poses, const double* dts,
+                                 tx_status* statuses);
 
 /* Continuous batching.  submit() queues one step request for each listed gel (a gel may hold
  * at most one request in flight: TX_ERR_ARG otherwise); the request is admitted at the next

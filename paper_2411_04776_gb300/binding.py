@@ -103,6 +103,8 @@ _SIGS = [
     ("tx_peak_fma", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, c_dp, c_dp, ctypes.c_void_p]),
     ("tx_gel_create", ctypes.c_int, [ctypes.POINTER(tx_gel_desc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("tx_gel_step", ctypes.c_int, [ctypes.c_void_p, c_dp, ctypes.c_double]),
+    ("tx_gel_step_attached", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, ctypes.c_double]),
+    ("tx_gel_case_pose", ctypes.c_int, [ctypes.c_void_p, c_dp]),
     ("tx_gel_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_dp,
                                     ctypes.POINTER(tx_step_stats), ctypes.c_int32]),
     ("tx_gel_get_state", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_dp]),
@@ -117,6 +119,7 @@ _SIGS = [
     ("tx_batch_destroy", None, [ctypes.c_void_p]),
     ("tx_batch_size", ctypes.c_int32, [ctypes.c_void_p]),
     ("tx_batch_step", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_ip]),
+    ("tx_batch_step_attached", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_dp, c_ip]),
     ("tx_batch_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_ip, c_dp, c_dp]),
     ("tx_batch_advance", ctypes.c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip]),
     ("tx_batch_pending", ctypes.c_int32, [ctypes.c_void_p]),
@@ -266,6 +269,18 @@ def tx_gel_step(g, pose, dt) -> int:
     return load().tx_gel_step(g, pp, float(dt))
 
 
+def tx_gel_step_attached(g, pose, case_pose, dt) -> int:
+    pose, pp = _d(pose)
+    case_pose, cp = _d(case_pose)
+    return load().tx_gel_step_attached(g, pp, cp, float(dt))
+
+
+def tx_gel_case_pose(g):
+    out = np.zeros(7)
+    _check(load().tx_gel_case_pose(g, _d(out)[1]), "tx_gel_case_pose")
+    return out
+
+
 def tx_gel_state(g, n_verts, device_out=None):
     """Returns (x, v, contact force, stats).  With device_out=(x_t, v_t) (torch CUDA tensors of
     shape (n, 3), float64) the copy lands there on the gel's stream."""
@@ -353,6 +368,15 @@ def tx_batch_step(b, poses, dts):
     dts, dp = _d(dts)
     st = np.zeros(len(dts), dtype=np.int32)
     s = load().tx_batch_step(b, pp, dp, st.ctypes.data_as(c_ip))
+    return s, st
+
+
+def tx_batch_step_attached(b, poses, case_poses, dts):
+    poses, pp = _d(poses)
+    case_poses, cp = _d(case_poses)
+    dts, dp = _d(dts)
+    st = np.zeros(len(dts), dtype=np.int32)
+    s = load().tx_batch_step_attached(b, pp, cp, dp, st.ctypes.data_as(c_ip))
     return s, st
 
 
@@ -493,6 +517,12 @@ class Gel:
     def step(self, pose, dt):
         s = tx_gel_step(self.h, pose, dt)
         return s
+
+    def step_attached(self, pose, case_pose, dt):
+        return tx_gel_step_attached(self.h, pose, case_pose, dt)
+
+    def case_pose(self):
+        return tx_gel_case_pose(self.h)
 
     def state(self):
         return tx_gel_state(self.h, self.n)

@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
   extern __shared__ double dsm[];  // [slices of this CTA][4]
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ double rhoj[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
   __shared__ int s_fail, s_any;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -238,28 +239,64 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     run[j] = gact[j];
   }
   __syncthreads();
-  // ---- init: r = -grad, x = 0, u = M^-1 r, pp = s = 0; partial |b|^2
+  // ---- Galerkin start: x0 = rho p_prev, the minimiser of the quadratic model along the gel's
+  // previous Newton direction (in d.p; rho = b.p_prev / p_prev.A p_prev, 0 without a usable one);
+  // a = A p_prev goes to d.w.  Partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3).
   for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    double bb = 0.0;
+    double bp = 0.0, pw = 0.0, bb = 0.0;
     if (gact[plan.slice_gel[s] - c.g0]) {
       const int r = 32 * s + lane;
       const double4_32a gr = d.grad[r];
       const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-      const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-      d.r[r] = b;
-      d.p[r] = z;
-      d.pp[r] = z;
-      d.s[r] = z;
-      d.u[r] = mul3(d.Minv + 9 * r, b);
+      const bool fx = d.fixed[r] != 0;
+      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row64(d, s, lane, d.p);
+      d.w[r] = a;
+      bp = dot4(b, pv);
+      pw = dot4(pv, a);
       bb = dot4(b, b);
     }
+    bp = warp_sum(bp);
+    pw = warp_sum(pw);
     bb = warp_sum(bb);
-    if (lane == 0) dsm[(s - c.s0) * 4 + 3] = bb;
+    if (lane == 0) {
+      dsm[(s - c.s0) * 4 + 0] = bp;
+      dsm[(s - c.s0) * 4 + 1] = pw;
+      dsm[(s - c.s0) * 4 + 2] = 0.0;
+      dsm[(s - c.s0) * 4 + 3] = bb;
+    }
   }
-  if (!group_sum(d, c, dsm, 3, 4, tot, &s_fail)) return;
+  // (the group sum's barrier also ends every CTA's SpMV on d.p before d.p is overwritten below)
+  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;
   for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
     bbj[j] = tot[j][3];
     thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[j][1], rho = tot[j][0] / pw;
+    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;  // a non-finite p_prev anywhere gives 0
+  }
+  __syncthreads();
+  // ---- x = rho p_prev, r = b - rho a, u = M^-1 r, pp = s = 0
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    const int j = plan.slice_gel[s] - c.g0;
+    if (!gact[j]) continue;
+    const int r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    const double rho = rhoj[j];
+    if (rho != 0.0 && !d.fixed[r]) {
+      const double4_32a pv = d.p[r], a = d.w[r];
+      x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
+      b.x = fma(-rho, a.x, b.x);
+      b.y = fma(-rho, a.y, b.y);
+      b.z = fma(-rho, a.z, b.z);
+    }
+    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    d.r[r] = b;
+    d.p[r] = x;
+    d.pp[r] = z;
+    d.s[r] = z;
+    d.u[r] = mul3(d.Minv + 9 * r, b);
   }
   if (!group_barrier(c, d, &s_fail)) return;  // u complete before the SpMV
   for (int k = 1;; ++k) {
@@ -402,6 +439,7 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
   extern __shared__ double dsm[];
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
+  __shared__ double rhoj[PCG_MAXG];
   __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
   __shared__ int s_fail, s_any;
@@ -414,29 +452,65 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
     itj[j] = 0;
   }
   __syncthreads();
-  // ---- init: r64 = b = -grad, p = 0; partials |b|^2 (k = 3) and |r|^2 (k = 2)
+  // ---- Galerkin start along the previous Newton direction (as in k_pcg64; a = A32 p_prev with
+  // FP64 arithmetic, into d.w): partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3)
   for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    double bb = 0.0;
+    double bp = 0.0, pw = 0.0, bb = 0.0;
     if (gact[plan.slice_gel[s] - c.g0]) {
       const int r = 32 * s + lane;
       const double4_32a gr = d.grad[r];
       const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-      d.r[r] = b;
-      d.p[r] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      const bool fx = d.fixed[r] != 0;
+      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row_res(d, s, lane, d.p);
+      d.w[r] = a;
+      bp = dot4(b, pv);
+      pw = dot4(pv, a);
       bb = dot4(b, b);
     }
+    bp = warp_sum(bp);
+    pw = warp_sum(pw);
     bb = warp_sum(bb);
     if (lane == 0) {
+      dsm[(s - c.s0) * 4 + 0] = bp;
+      dsm[(s - c.s0) * 4 + 1] = pw;
+      dsm[(s - c.s0) * 4 + 2] = 0.0;
       dsm[(s - c.s0) * 4 + 3] = bb;
-      dsm[(s - c.s0) * 4 + 2] = bb;
     }
   }
-  if (!group_sum(d, c, dsm, 2, 4, tot, &s_fail)) return;
+  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;  // its barrier ends every SpMV on d.p
   for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
     bbj[j] = tot[j][3];
     thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[j][1], rho = tot[j][0] / pw;
+    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
   }
   __syncthreads();
+  // ---- p = rho p_prev, r64 = b - rho a; partial |r|^2 (k = 2)
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    double rr = 0.0;
+    const int j = plan.slice_gel[s] - c.g0;
+    if (gact[j]) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      const double rho = rhoj[j];
+      if (rho != 0.0 && !d.fixed[r]) {
+        const double4_32a pv = d.p[r], a = d.w[r];
+        x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
+        b.x = fma(-rho, a.x, b.x);
+        b.y = fma(-rho, a.y, b.y);
+        b.z = fma(-rho, a.z, b.z);
+      }
+      d.r[r] = b;
+      d.p[r] = x;
+      rr = dot4(b, b);
+    }
+    rr = warp_sum(rr);
+    if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
+  }
+  if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
   for (int round = 0;; ++round) {
     // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
     if (threadIdx.x == 0) s_any = 0;
@@ -590,7 +664,28 @@ int pcg_max_ctas_per_sm(int max_slices) {
 }
 
 // ---------------------------------------------------------------- per-row / per-gel steps
-// step begin: x_n = x, xt = x + h v + h^2 g on free rows (xt = x on fixed rows)
+// rest position X carried by the pose (R, t)
+__device__ __forceinline__ double4_32a carry(const double* R, const double* t, const double4_32a X) {
+  return make_double4_32a(fma(R[2], X.z, fma(R[1], X.y, R[0] * X.x)) + t[0],
+                          fma(R[5], X.z, fma(R[4], X.y, R[3] * X.x)) + t[1],
+                          fma(R[8], X.z, fma(R[7], X.y, R[6] * X.x)) + t[2], 0.0);
+}
+
+// attachment-driven (sub)step: the attached (Dirichlet) vertices of the gel move to their rest
+// positions carried by the case pose at the end of the (sub)step (TacEx, Sec. "General GIPC
+// Simulation Pipeline": the attachment targets are set from the sensor-case pose, then the solver
+// runs); done before the indenter placement check, which sees the moved gel
+__global__ void k_place_attached(Dev d, int phase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  const int g = d.vgel[r];
+  const GelCtl& c = d.gc[g];
+  if (c.phase != phase || !c.attached || !d.fixed[r] || r - d.gi[g].v0 >= d.gi[g].nv) return;
+  d.x[r] = carry(c.Rc, c.tc, d.X[r]);
+}
+
+// step begin: x_n = x, xt = x + h v + h^2 g on free rows (xt = x on fixed rows; an attached vertex
+// moved by its case has x_n = its position at the case pose of the step's start)
 __global__ void k_predictor(Dev d, int phase) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrows) return;
@@ -598,7 +693,8 @@ __global__ void k_predictor(Dev d, int phase) {
   if (d.gc[g].phase != phase) return;
   const GelCtl& c = d.gc[g];
   const double4_32a x = d.x[r], v = d.v[r];
-  d.xn[r] = x;
+  const bool moved = c.attached && d.fixed[r] && r - d.gi[g].v0 < d.gi[g].nv;
+  d.xn[r] = moved ? carry(c.Rcp, c.tcp, d.X[r]) : x;
   double4_32a xt = x;
   if (!d.fixed[r]) {
     const double h = c.h;
@@ -727,6 +823,10 @@ void launch_rows(int which, const Dev& d, int phase, cudaStream_t st) {
   }
   if (which == 3) {
     k_restore<<<nb, 256, 0, st>>>(d, phase);
+    count_launch(1);
+  }
+  if (which == 4) {
+    k_place_attached<<<nb, 256, 0, st>>>(d, phase);
     count_launch(1);
   }
 }

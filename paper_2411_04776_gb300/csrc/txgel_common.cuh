@@ -65,6 +65,13 @@ struct GelCtl {  // per gel, written by the host before the launches of an itera
   double grav[3];
   double R[9], t[3];         // indenter pose at the end of the (sub)step
   double Rp[9], tp[3];       // indenter pose at its start
+  // attachment-driven step (attached != 0): the Dirichlet (attached) vertices follow the sensor
+  // case, at their rest positions carried by the case pose -- (Rc, tc) at the end of the
+  // (sub)step, (Rcp, tcp) at its start
+  int attached;
+  int pad2_;
+  double Rc[9], tc[3];
+  double Rcp[9], tcp[3];
 };
 
 struct GelVar {  // per gel, written by the device

@@ -389,9 +389,11 @@ cudaError_t host_alloc(void** p, size_t bytes) {
 
 struct Task {
   double pa[7], pb[7];
+  double ca[7], cb[7];  // case pose at the start / end (attachment-driven steps only)
   double dt;
   int depth;
   bool first;
+  bool attached;
 };
 
 struct Run {
@@ -404,6 +406,8 @@ struct Run {
   tx_step_stats last{};     // last finished request
   double pose[7];           // indenter pose at the end of the last finished substep
   double pose_req[7];       // pose at the start of the request (for rollback)
+  double case_pose[7] = {1, 0, 0, 0, 0, 0, 0};  // pose of the attached vertices' frame (the sensor case)
+  double case_req[7] = {1, 0, 0, 0, 0, 0, 0};   // ... at the start of the request (for rollback)
 };
 
 }  // namespace
@@ -1152,6 +1156,15 @@ void fill_ctl(tx_batch* b, int g, int phase, const Task& t) {
     c.t[k] = t.pb[4 + k];
     c.tp[k] = t.pa[4 + k];
   }
+  c.attached = t.attached ? 1 : 0;
+  if (t.attached) {
+    quat_R(t.cb, c.Rc);
+    quat_R(t.ca, c.Rcp);
+    for (int k = 0; k < 3; ++k) {
+      c.tc[k] = t.cb[4 + k];
+      c.tcp[k] = t.ca[4 + k];
+    }
+  }
 }
 
 void finish_request(tx_batch* b, int g, tx_status s) {
@@ -1174,6 +1187,7 @@ tx_status rollback(tx_batch* b, const std::vector<int>& gels) {
     // the failed solve's direction must not seed the next solve's Galerkin start
     CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
     std::memcpy(b->run[g].pose, b->run[g].pose_req, sizeof(double) * 7);
+    std::memcpy(b->run[g].case_pose, b->run[g].case_req, sizeof(double) * 7);
   }
   return TX_OK;
 }
@@ -1198,6 +1212,7 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
   if (s != TX_OK) return s;
   prof_open(b, PR_BEGIN);
   launch_gel_op(d, PH_BEGIN, 3, st);
+  launch_rows(4, d, PH_BEGIN, st);  // attached vertices to the case pose of the substep's end
   launch_indenter_pose(d, PH_BEGIN, d.niv_total, st);
   launch_hash_build(d, PH_BEGIN, 1, st);
   launch_query(d, PH_BEGIN, 4, st);
@@ -1207,7 +1222,7 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
   const int accd_max = b->mesh[set[0]].prm.accd_max_iter;
   launch_accd(d, PH_BEGIN, 1, accd_max, st);
   launch_min_dist(d, PH_BEGIN, st);
-  prof_close(b, 12);
+  prof_close(b, 13);
   CK(cudaGetLastError());
   s = download_var(b);
   if (s != TX_OK) return s;
@@ -1252,6 +1267,11 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
       pose_mid(t.pa, t.pb, mid);
       std::memcpy(a.pb, mid, sizeof(mid));
       std::memcpy(c.pa, mid, sizeof(mid));
+      if (t.attached) {  // the case motion is halved with the indenter's
+        pose_mid(t.ca, t.cb, mid);
+        std::memcpy(a.cb, mid, sizeof(mid));
+        std::memcpy(c.ca, mid, sizeof(mid));
+      }
       a.dt = c.dt = 0.5 * t.dt;
       a.depth = c.depth = t.depth + 1;
       c.first = false;
@@ -1403,6 +1423,7 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
     R.acc.min_distance = bitsd_host(v.dmin_bits);
     for (int c = 0; c < 3; ++c) R.acc.contact_force[c] = v.fc[c];
     std::memcpy(R.pose, t.pb, sizeof(double) * 7);
+    if (t.attached) std::memcpy(R.case_pose, t.cb, sizeof(double) * 7);
     R.phase = PH_IDLE;
     if (R.stack.empty()) finish_request(b, g, TX_OK);
   }
@@ -1425,7 +1446,7 @@ tx_status ensure_plan_parts(tx_batch* b, int np) {
   int2* rng = b->plan_mem.get<int2>(C * cap);
   int* cg = b->plan_mem.get<int>(C * cap);
   int4* gr = b->plan_mem.get<int4>(G * cap);
-  if (!rng || !cg || !gr) return TX_ERR_OOM;
+  if (b->plan_mem.failed) return TX_ERR_OOM;
   b->parts.resize(cap);
   for (int k = 0; k < cap; ++k) {
     PcgPlan& P = b->parts[k].plan;
@@ -1831,17 +1852,13 @@ tx_status do_newton(tx_batch* b) {
   }
   std::vector<int> fin, fail;
   if (b->prof.on) {
-    // the resident solvers' Galerkin start: one SpMV (FP64 arithmetic), three dot products and two
-    // updates per solve
-    bool warm = b->nparts > 0;
-    for (int k = 0; k < b->nparts; ++k) warm = warm && b->parts[k].res;
+    // the solvers' Galerkin start: one SpMV (FP64 arithmetic), three dot products and two updates
+    // per solve
     for (int g : set) {
       const double it = b->gv_h[g].pcg_it;
       const GelInfo& G = b->gi[g];
-      if (warm) {
-        b->prof.flops[PR_PCG] += 18.0 * b->nnzb_real[g] + 30.0 * b->nfree[g];
-        b->prof.bytes[PR_PCG] += (b->mixed ? 40.0 : 76.0) * b->nnzb_real[g] + 96.0 * G.nv;
-      }
+      b->prof.flops[PR_PCG] += 18.0 * b->nnzb_real[g] + 30.0 * b->nfree[g];
+      b->prof.bytes[PR_PCG] += (b->mixed ? 40.0 : 76.0) * b->nnzb_real[g] + 96.0 * G.nv;
       // per PCG iteration and row: SpMV 18 flops per 3x3 block, preconditioner 18, four
       // axpys 24, three dot products 18; mixed precision adds one FP64 residual SpMV per round
       const double rounds = b->mixed ? b->gv_h[g].rounds : 0.0;
@@ -1898,22 +1915,30 @@ tx_status advance(tx_batch* b) {
   return do_newton(b);
 }
 
-tx_status submit_one(tx_batch* b, int g, const double pose[7], double dt) {
-  if (g < 0 || g >= b->n || !pose || !(dt > 0.0) || !std::isfinite(dt)) return TX_ERR_ARG;
+bool valid_pose(const double p[7]) {
   double qn = 0.0;
   for (int k = 0; k < 7; ++k)
-    if (!std::isfinite(pose[k])) return TX_ERR_ARG;
-  for (int k = 0; k < 4; ++k) qn += pose[k] * pose[k];
-  if (!(qn > 0.0)) return TX_ERR_ARG;
+    if (!std::isfinite(p[k])) return false;
+  for (int k = 0; k < 4; ++k) qn += p[k] * p[k];
+  return qn > 0.0;
+}
+
+tx_status submit_one(tx_batch* b, int g, const double pose[7], double dt, const double* case_pose = nullptr) {
+  if (g < 0 || g >= b->n || !pose || !(dt > 0.0) || !std::isfinite(dt)) return TX_ERR_ARG;
+  if (!valid_pose(pose) || (case_pose && !valid_pose(case_pose))) return TX_ERR_ARG;
   Run& R = b->run[g];
   if (R.in_request) return TX_ERR_ARG;
   R.in_request = true;
   R.acc = tx_step_stats{};
   R.newton_sub = 0;
   std::memcpy(R.pose_req, R.pose, sizeof(double) * 7);
+  std::memcpy(R.case_req, R.case_pose, sizeof(double) * 7);
   Task t;
   std::memcpy(t.pa, R.pose, sizeof(double) * 7);
   std::memcpy(t.pb, pose, sizeof(double) * 7);
+  t.attached = case_pose != nullptr;
+  std::memcpy(t.ca, R.case_pose, sizeof(double) * 7);
+  std::memcpy(t.cb, case_pose ? case_pose : R.case_pose, sizeof(double) * 7);
   t.dt = dt;
   t.depth = 0;
   t.first = true;
@@ -1951,10 +1976,11 @@ tx_status eval_setup(tx_batch* b, int g, const double* x, const double* xt, doub
   if (s == TX_OK) s = copy_rows_in(b, g, d.xt, xt);
   if (s != TX_OK) return s;
   for (int k = 0; k < b->n; ++k) b->gc_h[k].phase = PH_IDLE;
-  Task t;
+  Task t{};
   std::memcpy(t.pa, pose, sizeof(double) * 7);
   std::memcpy(t.pb, pose, sizeof(double) * 7);
   t.dt = h;
+  t.attached = false;
   fill_ctl(b, g, PH_EVAL, t);
   s = upload_ctl(b);
   if (s != TX_OK) return s;
@@ -2124,12 +2150,13 @@ int32_t tx_batch_pending(const tx_batch* b) {
   return c;
 }
 
-tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_status* statuses) {
+tx_status tx_batch_step_attached(tx_batch* b, const double* poses, const double* case_poses, const double* dts,
+                                 tx_status* statuses) {
   if (!b || !poses || !dts) return TX_ERR_ARG;
   for (int g = 0; g < b->n; ++g)
     if (b->run[g].in_request) return TX_ERR_ARG;
   for (int g = 0; g < b->n; ++g) {
-    tx_status s = submit_one(b, g, poses + 7 * g, dts[g]);
+    tx_status s = submit_one(b, g, poses + 7 * g, dts[g], case_poses ? case_poses + 7 * g : nullptr);
     if (s != TX_OK) {
       for (int k = 0; k < g; ++k) {
         b->run[k].in_request = false;
@@ -2150,6 +2177,10 @@ tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_
     if (s != TX_OK && worst == TX_OK) worst = s;
   }
   return worst;
+}
+
+tx_status tx_batch_step(tx_batch* b, const double* poses, const double* dts, tx_status* statuses) {
+  return tx_batch_step_attached(b, poses, nullptr, dts, statuses);
 }
 
 tx_status tx_batch_state(const tx_batch* bc, int32_t g, double* x, double* v, double f_contact[3],
@@ -2199,6 +2230,8 @@ tx_status tx_batch_reset(tx_batch* b, int32_t g) {
   CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));  // no previous direction
   CK(cudaStreamSynchronize(b->st));
   std::memcpy(b->run[g].pose, b->mesh[g].pose0, sizeof(double) * 7);
+  const double ident[7] = {1, 0, 0, 0, 0, 0, 0};
+  std::memcpy(b->run[g].case_pose, ident, sizeof(ident));  // the attached vertices are back at rest
   b->run[g].last = tx_step_stats{};
   return TX_OK;
 }
@@ -2225,6 +2258,19 @@ tx_status tx_gel_step(tx_gel* g, const double pose[7], double dt) {
   tx_status st = TX_OK;
   tx_status s = tx_batch_step(g->b, pose, &dt, &st);
   return s != TX_OK ? s : st;
+}
+
+tx_status tx_gel_step_attached(tx_gel* g, const double pose[7], const double case_pose[7], double dt) {
+  if (!g || !pose || !case_pose) return TX_ERR_ARG;
+  tx_status st = TX_OK;
+  tx_status s = tx_batch_step_attached(g->b, pose, case_pose, &dt, &st);
+  return s != TX_OK ? s : st;
+}
+
+tx_status tx_gel_case_pose(const tx_gel* g, double case_pose[7]) {
+  if (!g || !case_pose) return TX_ERR_ARG;
+  std::memcpy(case_pose, g->b->run[0].case_pose, sizeof(double) * 7);
+  return TX_OK;
 }
 
 tx_status tx_gel_state(const tx_gel* g, double* x, double* v, double f_contact[3], tx_step_stats* stats,

@@ -1,18 +1,23 @@
-"""Writes tests/golden/c1_prism_oracle.npz: FP64 oracle snapshots of the GelSight-Mini gel
-(41x51x9 grid, 18,819 vertices, 96,000 tets) pressed by the seeded triangular prism of the
-benchmark workload (workloads.mini_gel(seed=0): 1.0 mm over 60 steps, then a 2 mm slide).
+"""Writes FP64 oracle snapshots of the GelSight-Mini gel (41x51x9 grid, 18,819 vertices, 96,000
+tets) for the GPU parity tests:
+
+* c1_prism_window_oracle.npz -- the benchmark's own trajectory (workloads.mini_gel(seed=0): the
+  seeded triangular prism pressed 1.0 mm over 60 steps), steps 0..24: the benchmark's timed
+  window (steps 5..24) is deep-press contact with ~300-900 active pairs;
+* c1_prism_fastpress_oracle.npz -- the same gel and prism pressed 1.0 mm over 12 steps (92 um per
+  step), steps 0..5: the indenter move of every step has to be split (R7), deep contact.
 
 Only the CPU oracle (oracle/) computes these values; the CUDA library is never involved.  The
-oracle runs the first STEPS steps of that trajectory at the parity Newton tolerance and stores,
-at the steps listed in SNAP, the displacement of every vertex from its rest position (float32:
-the rounding, below 1e-10 m for displacements under 1.5 mm, is far inside the 4 nm parity
-gate), the contact force, and for every step the number of substeps (step splitting of the
-kinematic indenter) and of active contact pairs.  Run from the repository root:
+oracle runs at the parity Newton tolerance and stores, at the listed steps, the displacement of
+every vertex from its rest position (float32: the rounding, below 1e-10 m for displacements under
+1.5 mm, is far inside the 4 nm parity gate) and the contact force, and for every step the number
+of substeps, Newton iterations and active contact pairs.  Each file is rewritten after every
+stored step, so an interrupted run keeps what it has.  Run from the repository root:
 
-    python tests/golden/make_oracle_snapshots.py
+    python tests/golden/make_oracle_snapshots.py [window|fastpress]
 
-(about half an hour on 8 cores; the oracle's parallel loops give bitwise the same result for
-any thread count)."""
+(the window takes about half an hour on 8 cores; the oracle's parallel loops give bitwise the same
+result for any thread count)."""
 import os
 import sys
 import time
@@ -27,34 +32,44 @@ from oracle import oracle as O  # noqa: E402
 from paper_2411_04776_gb300 import workloads as W  # noqa: E402
 
 NEWTON_TOL = 1e-7   # the parity tolerance of the GPU tests (tests/gpu_util.PARITY_NEWTON_TOL)
-STEPS = 30          # covers the benchmark's timed window (steps 5..24) and the split steps after it
-SNAP = (4, 9, 14, 19, 24, 27, 28, 29)
-OUT = os.path.join(HERE, "c1_prism_oracle.npz")
+NEWTON_MAX = 400    # deep contact at this tolerance takes up to ~130 iterations per step
+
+CASES = {
+    "window": dict(file="c1_prism_window_oracle.npz", make=lambda: W.mini_gel(seed=0), steps=25,
+                   snap=(4, 9, 14, 19, 24)),
+    "fastpress": dict(file="c1_prism_fastpress_oracle.npz",
+                      make=lambda: W.mini_gel(seed=0, depth=1.0e-3, n_press=12, slide=0.0, n_slide=0),
+                      steps=6, snap=(0, 1, 2, 3, 4, 5)),
+}
 
 
-def main():
-    O.set_threads(0)
-    wl = W.mini_gel(seed=0)
-    og = O.OracleGel.from_workload(wl, newton_tol=NEWTON_TOL)
+def run(name):
+    case = CASES[name]
+    out = os.path.join(HERE, case["file"])
+    wl = case["make"]()
+    og = O.OracleGel.from_workload(wl, newton_tol=NEWTON_TOL, newton_max=NEWTON_MAX)
     X = wl.gel.verts
-    disp, force, substeps, active, newton = [], [], [], [], []
+    disp, force, snaps, substeps, active, newton = [], [], [], [], [], []
     t0 = time.perf_counter()
-    for s in range(STEPS):
+    for s in range(case["steps"]):
         info = og.step(wl.poses[s], wl.dt)
         assert info["status"] == 0, (s, info)
         substeps.append(info["substeps"])
         active.append(info["active_pairs"])
         newton.append(info["newton_iters"])
         x, _, fc, _ = og.state()
-        if s in SNAP:
+        if s in case["snap"]:
             disp.append((x - X).astype(np.float32))
             force.append(fc.copy())
-        print(f"step {s}: {info}  ({time.perf_counter() - t0:.0f} s)", flush=True)
-    np.savez_compressed(OUT, workload=np.array(wl.name), newton_tol=NEWTON_TOL, snap_steps=np.array(SNAP),
-                        disp=np.stack(disp), contact_force=np.stack(force), substeps=np.array(substeps),
-                        active_pairs=np.array(active), newton_iters=np.array(newton))
-    print("wrote", OUT)
+            snaps.append(s)
+            np.savez_compressed(out, workload=np.array(wl.name), newton_tol=NEWTON_TOL, newton_max=NEWTON_MAX,
+                                snap_steps=np.array(snaps), disp=np.stack(disp), contact_force=np.stack(force),
+                                substeps=np.array(substeps), active_pairs=np.array(active),
+                                newton_iters=np.array(newton))
+        print(f"{name} step {s}: {info}  ({time.perf_counter() - t0:.0f} s)", flush=True)
+    print("wrote", out)
 
 
 if __name__ == "__main__":
-    main()
+    for n in (sys.argv[1:] or list(CASES)):
+        run(n)

@@ -28,14 +28,22 @@ def smooth_state(wl, seed, amp=2e-5):
     return x, xt, wl.dt
 
 
-GOLDEN_C1 = "c1_prism_oracle.npz"
+GOLDEN = {"window": "c1_prism_window_oracle.npz", "fastpress": "c1_prism_fastpress_oracle.npz"}
 
 
-def load_golden_c1():
-    """FP64 oracle snapshots of the GelSight-Mini gel on the benchmark trajectory
-    (tests/golden/make_oracle_snapshots.py): displacements at the snapshot steps, contact forces,
-    substeps and active pairs per step."""
+def load_golden(case):
+    """FP64 oracle snapshots of the GelSight-Mini gel (tests/golden/make_oracle_snapshots.py):
+    displacements and contact forces at the snapshot steps, substeps, Newton iterations and
+    active pairs per step.  "window": the benchmark trajectory, steps 0..24; "fastpress": the
+    same prism pressed 1.0 mm over 12 steps, steps 0..5 (every step split)."""
     import os
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", GOLDEN_C1)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", GOLDEN[case])
     z = np.load(path)
     return {k: z[k] for k in z.files}
+
+
+def golden_workload(case):
+    from paper_2411_04776_gb300 import workloads as W
+    if case == "window":
+        return W.mini_gel(seed=0)
+    return W.mini_gel(seed=0, depth=1.0e-3, n_press=12, slide=0.0, n_slide=0)
