@@ -84,6 +84,15 @@ typedef struct tx_params {
                                measurements of that family).  A handle uses the streaming kernels
                                if any of its gels asks for them.                                */
   int32_t reserved0;        /* must be 0                                                       */
+  double friction;          /* IPC lagged friction coefficient mu_f between gel and indenter
+                               (0: frictionless, the default).  Pairs in contact at the start of a
+                               (sub)step fix their closest points, tangent plane and normal force
+                               lambda = kappa |b'(d)|; the step then adds
+                               D = mu_f lambda f0(|tangential relative displacement|), f0 the
+                               smoothed Coulomb law of IPC (TacEx App. A: IPC models static and
+                               dynamic friction)                                               */
+  double friction_eps_v;    /* velocity below which friction acts as a stiff spring (static
+                               friction) [m/s] (default 1e-3)                                  */
 } tx_params;
 
 void tx_params_default(tx_params* p);

@@ -703,6 +703,219 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d, int mode)
   }
 }
 
+// ---------------------------------------------------------------- lagged friction
+// IPC's lagged friction (Li et al. 2020, Sec. 5; TacEx App. A notes that IPC models static and
+// dynamic friction).  For a pair in contact at the start of the (sub)step,
+//   D(x) = mu_f lam f0(|u|),   u = T^T sum_k w_k (P_k - Plag_k)  (tangential relative displacement),
+// with the weights w, the tangent basis T and the normal force lam = kappa m |b'(d)| held at their
+// values at the start, and the smoothed Coulomb law of IPC with e = eps_v h:
+//   f0(y) = y for y >= e,   f0(y) = -y^3 / (3 e^2) + y^2 / e + e / 3 below.
+// In u: grad f0 = phi u, Hessian = phi I + psi u u^T, with phi = f0'(y) / y and
+// psi = (f0''(y) - phi) / y^2: for y >= e phi = 1 / y, psi = -1 / y^3; below, phi = 2 / e - y / e^2,
+// psi = -1 / (e^2 y) (its u u^T term vanishes with y).  Its eigenvalues, phi across u and f0'' >= 0
+// along it, are non-negative: D is convex in x and needs no projection.
+
+// f0(y), phi, psi at |u| = y
+__device__ __forceinline__ void coulomb_f0(double y, double e, double* f0, double* phi, double* psi) {
+  if (y >= e) {
+    *f0 = y;
+    *phi = 1.0 / y;
+    *psi = -1.0 / (y * y * y);
+    return;
+  }
+  const double ie = 1.0 / e;
+  *f0 = y * y * (ie - y * ie * ie / 3.0) + e / 3.0;
+  *phi = ie * (2.0 - y * ie);
+  *psi = y > 0.0 ? -ie * ie / y : 0.0;
+}
+
+// Lagged data of each candidate pair of a gel starting a (sub)step: gel at x_n (attached vertices
+// already placed), indenter at its pose at the substep's start.  The records cover the gel's
+// candidate list of that moment (the swept list of the placement check, a superset of the pairs
+// within d_hat); pairs not in contact are marked inactive.
+__global__ void __launch_bounds__(128) k_fric_setup(Dev d, int phase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.npslots) return;
+  const int g = d.pslot_gel[i];
+  const GelInfo& G = d.gi[g];
+  if (d.gc[g].phase != phase || !(G.mu_f > 0.0)) return;
+  const int k = i - G.pbase, np = min(d.gv[g].npair, G.pcap);
+  if (k == 0) d.gv[g].nfric = np;
+  if (k >= np) return;
+  FricRec& f = d.fric[i];
+  const int4 pr = d.pairs[i];
+  f.pr = pr;
+  f.active = 0;
+  double P[4][3];
+  int rows[4];
+  pair_points(d, pr, 0.0, true, P, rows);
+  DType ty;
+  const double D = pair_d2(pr.x == PAIR_EE ? 1 : 0, P, &ty);
+  if (!(D > 0.0) || !(D < G.dhat * G.dhat)) return;
+  double b, bD, bDD;
+  barrier_D(D, G.dhat, &b, &bD, &bDD);
+  double mol = 1.0;  // edge-edge mollifier at the lagged state scales the normal force
+  if (pr.x == PAIR_EE) {
+    double ea[3], eb[3], n[3];
+    sub3(P[1], P[0], ea);
+    sub3(P[3], P[2], eb);
+    cross3(ea, eb, n);
+    const double ex = pair_eps_x(d, pr), q = dot3(n, n) / ex;
+    if (q < 1.0) mol = q * (2.0 - q);
+  }
+  f.lam = G.kappa * mol * fabs(2.0 * sqrt(D) * bD);  // |b'(d)| = |2 d dB/dD|
+  double w[4] = {0.0, 0.0, 0.0, 0.0}, nrm[3];
+  const int* id = ty.i;
+  if (ty.f == DF_PP) {
+    w[id[0]] = 1.0;
+    w[id[1]] = -1.0;
+    sub3(P[id[0]], P[id[1]], nrm);
+  } else if (ty.f == DF_PE) {
+    double e[3], r[3];
+    sub3(P[id[2]], P[id[1]], e);
+    sub3(P[id[0]], P[id[1]], r);
+    const double t = dot3(r, e) / dot3(e, e);
+    w[id[0]] = 1.0;
+    w[id[1]] = t - 1.0;
+    w[id[2]] = -t;
+    for (int c = 0; c < 3; ++c) nrm[c] = r[c] - t * e[c];
+  } else if (ty.f == DF_PT) {  // the face's barycentric coordinates of the projected point
+    double e1[3], e2[3], r[3];
+    sub3(P[2], P[1], e1);
+    sub3(P[3], P[1], e2);
+    sub3(P[0], P[1], r);
+    const double a = dot3(e1, e1), bb = dot3(e1, e2), c = dot3(e2, e2), p = dot3(e1, r), q = dot3(e2, r);
+    const double den = a * c - bb * bb, l1 = (c * p - bb * q) / den, l2 = (a * q - bb * p) / den;
+    w[0] = 1.0;
+    w[1] = l1 + l2 - 1.0;
+    w[2] = -l1;
+    w[3] = -l2;
+    cross3(e1, e2, nrm);
+  } else {  // line-line: the closest points' parameters on both edges
+    double u[3], v[3], r[3];
+    sub3(P[1], P[0], u);
+    sub3(P[3], P[2], v);
+    sub3(P[0], P[2], r);
+    const double a = dot3(u, u), bb = dot3(u, v), c = dot3(v, v), p = dot3(u, r), q = dot3(v, r);
+    const double den = a * c - bb * bb, sa = (bb * q - c * p) / den, tb = (a * q - bb * p) / den;
+    w[0] = 1.0 - sa;
+    w[1] = sa;
+    w[2] = tb - 1.0;
+    w[3] = -tb;
+    cross3(u, v, nrm);
+  }
+  const double nn = sqrt(dot3(nrm, nrm));
+  for (int c = 0; c < 3; ++c) nrm[c] /= nn;
+  // tangent basis: the coordinate axis least aligned with the normal, made orthogonal to it, and
+  // normal x that
+  int ax = 0;
+  if (fabs(nrm[1]) < fabs(nrm[ax])) ax = 1;
+  if (fabs(nrm[2]) < fabs(nrm[ax])) ax = 2;
+  double t1[3] = {-nrm[ax] * nrm[0], -nrm[ax] * nrm[1], -nrm[ax] * nrm[2]}, t2[3];
+  t1[ax] += 1.0;
+  const double n1 = sqrt(dot3(t1, t1));
+  for (int c = 0; c < 3; ++c) t1[c] /= n1;
+  cross3(nrm, t1, t2);
+  for (int c = 0; c < 3; ++c) {
+    f.T[2 * c] = t1[c];
+    f.T[2 * c + 1] = t2[c];
+  }
+  for (int q = 0; q < 4; ++q) {
+    f.w[q] = w[q];
+    for (int c = 0; c < 3; ++c) f.Plag[3 * q + c] = P[q][c];
+  }
+  f.active = 1;
+}
+
+// the friction record of slot i, if its gel is in `phase` and it was in contact at the start
+__device__ __forceinline__ bool fric_slot(const Dev& d, int i, int phase, const FricRec*& f) {
+  const int g = d.pslot_gel[i];
+  if (d.gc[g].phase != phase || phase == PH_EVAL || !(d.gi[g].mu_f > 0.0)) return false;
+  if (i - d.gi[g].pbase >= d.gv[g].nfric) return false;
+  f = d.fric + i;
+  return f->active != 0;
+}
+
+// u = T^T sum_k w_k (P_k - Plag_k) at the pair's points P (gel at x + alpha p, indenter at its
+// current pose)
+__device__ __forceinline__ void fric_u(const FricRec& f, const double P[4][3], double u[2]) {
+  double dl[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < 4; ++q)
+    for (int c = 0; c < 3; ++c) dl[c] = fma(f.w[q], P[q][c] - f.Plag[3 * q + c], dl[c]);
+  u[0] = dl[0] * f.T[0] + dl[1] * f.T[2] + dl[2] * f.T[4];
+  u[1] = dl[0] * f.T[1] + dl[1] * f.T[3] + dl[2] * f.T[5];
+}
+
+// friction energy of a record at x + alpha p
+__device__ __forceinline__ double fric_energy(const Dev& d, const FricRec& f, int g, double alpha) {
+  double P[4][3], u[2], f0, phi, psi;
+  int rows[4];
+  pair_points(d, f.pr, alpha, false, P, rows);
+  fric_u(f, P, u);
+  coulomb_f0(sqrt(u[0] * u[0] + u[1] * u[1]), d.gi[g].eps_v * d.gc[g].h, &f0, &phi, &psi);
+  return d.gi[g].mu_f * f.lam * f0;
+}
+
+// Friction terms of the Newton iteration, one thread per record.  Mode 0 (with the contact
+// gradient): dD/dP_k = mu_f lam w_k T (phi u) into the contact gradient of the free gel rows and
+// the contact force.  Mode 1 (after the gather wrote the matrix): the blocks
+// d2D/dP_k dP_l = mu_f lam w_k w_l T (phi I + psi u u^T) T^T between free gel rows.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_fric(Dev d, int phase, int mode) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.npslots) return;
+  const FricRec* fp;
+  if (!fric_slot(d, i, phase, fp)) return;
+  const FricRec& f = *fp;
+  const int g = d.pslot_gel[i];
+  double P[4][3], u[2], f0, phi, psi;
+  int rows[4];
+  pair_points(d, f.pr, 0.0, false, P, rows);
+  fric_u(f, P, u);
+  coulomb_f0(sqrt(u[0] * u[0] + u[1] * u[1]), d.gi[g].eps_v * d.gc[g].h, &f0, &phi, &psi);
+  const double c = d.gi[g].mu_f * f.lam;
+  if (mode == 0) {
+    double gt[3];  // c T (phi u)
+    for (int k = 0; k < 3; ++k) gt[k] = c * phi * (f.T[2 * k] * u[0] + f.T[2 * k + 1] * u[1]);
+    for (int q = 0; q < 4; ++q) {
+      const int r = rows[q];
+      if (r < 0 || f.w[q] == 0.0) continue;
+      const double gx = f.w[q] * gt[0], gy = f.w[q] * gt[1], gz = f.w[q] * gt[2];
+      atomicAdd(&d.gv[g].fc[0], -gx);
+      atomicAdd(&d.gv[g].fc[1], -gy);
+      atomicAdd(&d.gv[g].fc[2], -gz);
+      if (d.fixed[r]) continue;
+      atomicAdd(&d.cgrad[r].x, gx);
+      atomicAdd(&d.cgrad[r].y, gy);
+      atomicAdd(&d.cgrad[r].z, gz);
+    }
+    return;
+  }
+  // H_delta = c T M T^T, M = phi I + psi u u^T (2 x 2)
+  const double m00 = phi + psi * u[0] * u[0], m01 = psi * u[0] * u[1], m11 = phi + psi * u[1] * u[1];
+  double H[9];
+  for (int a = 0; a < 3; ++a) {
+    const double ta0 = f.T[2 * a], ta1 = f.T[2 * a + 1];
+    const double r0 = ta0 * m00 + ta1 * m01, r1 = ta0 * m01 + ta1 * m11;
+    for (int b = 0; b < 3; ++b) H[3 * a + b] = c * (r0 * f.T[2 * b] + r1 * f.T[2 * b + 1]);
+  }
+  for (int qa = 0; qa < 4; ++qa) {
+    const int ra = rows[qa];
+    if (ra < 0 || f.w[qa] == 0.0 || d.fixed[ra]) continue;
+    for (int qb = 0; qb < 4; ++qb) {
+      const int rb = rows[qb];
+      if (rb < 0 || f.w[qb] == 0.0 || d.fixed[rb]) continue;
+      const int bp = find_block(d, ra, rb);
+      if (bp < 0) {
+        atomicOr(&d.gv[g].flags, 16);
+        continue;
+      }
+      const double ww = f.w[qa] * f.w[qb];
+      for (int e = 0; e < 9; ++e) add_val<MIXED>(d, bp, e, ww * H[e]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- ACCD and distances
 // mode 0: Newton step (gel moves by p, indenter fixed at cur); mode 1: indenter sweep prev -> cur
 // with the gel fixed at x.
@@ -795,7 +1008,7 @@ __global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* p
       }
       acc += d.mass[r] * (ex * ex + ey * ey + ez * ez) * ih2;
     }
-  } else {
+  } else if (pc.y == 2) {
     const int np = min(v.npair, G.pcap);
     for (int i = pc.z * EN_T + threadIdx.x; i < np; i += pc.w * EN_T) {
       const int4 pr = d.pairs[G.pbase + i];
@@ -803,6 +1016,11 @@ __global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* p
       int rows[4];
       pair_points(d, pr, alpha, false, P, rows);
       acc += G.kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+    }
+  } else if (phase != PH_EVAL) {  // lagged friction records of the running (sub)step
+    for (int i = pc.z * EN_T + threadIdx.x; i < v.nfric; i += pc.w * EN_T) {
+      const FricRec& f = d.fric[G.pbase + i];
+      if (f.active) acc += fric_energy(d, f, g, alpha);
     }
   }
   acc = block_sum<EN_T>(acc, sm);
@@ -985,6 +1203,19 @@ void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st) {
     k_contact_hess<true><<<nc, 32 * CW_WARPS, 0, st>>>(d, 1);
   else
     k_contact_hess<false><<<nc, 32 * CW_WARPS, 0, st>>>(d, 1);
+  count_launch(1);
+}
+void launch_fric_setup(const Dev& d, int phase, cudaStream_t st) {
+  if (d.npslots <= 0 || !d.fric) return;
+  k_fric_setup<<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase);
+  count_launch(1);
+}
+void launch_fric(const Dev& d, int phase, int mode, bool mixed, cudaStream_t st) {
+  if (d.npslots <= 0 || !d.fric) return;
+  if (mixed)
+    k_fric<true><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode);
+  else
+    k_fric<false><<<nblk(d.npslots, 128), 128, 0, st>>>(d, phase, mode);
   count_launch(1);
 }
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st) {

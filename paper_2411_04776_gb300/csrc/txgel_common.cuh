@@ -38,7 +38,8 @@ constexpr int PAIR_EE = 2;     // gel surface edge     vs indenter edge
 constexpr double ACCD_S = 0.1; // ACCD: the gap may shrink to this fraction per sweep
 
 // phases of a gel inside a batch
-enum Phase : int { PH_IDLE = 0, PH_BEGIN = 1, PH_NEWTON = 2 };
+enum Phase : int { PH_IDLE = 0, PH_BEGIN = 1, PH_NEWTON = 2, PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6,
+                   PH_PARK = 7, PH_FAIL = 8 };
 
 struct GelInfo {  // per gel, read-only after create
   int v0, nv;     // rows
@@ -54,6 +55,7 @@ struct GelInfo {  // per gel, read-only after create
   int fixed_count;
   double mu, lam, kappa, dhat, cell, bbox_diag, newton_tol;
   double org[3];             // hash grid origin
+  double mu_f, eps_v;        // IPC lagged friction: coefficient (0: frictionless), velocity threshold
 };
 
 struct GelCtl {  // per gel, written by the host before the launches of an iteration
@@ -98,9 +100,25 @@ struct GelVar {  // per gel, written by the device
   int active_pairs;
   double ibox_lo[3], ibox_hi[3];  // indenter bounding box of the current hash build
   int flags;                 // 1 hash overflow, 2 ACCD cap, 4 inverted tet, 8 ACCD hit, 16 pattern miss
+  int nfric;                 // friction records of the running (sub)step (slots of its pair segment)
+  int pad3_;
 };
 
 struct PairBarrier;  // barrier setup of one contact pair (dev_pairwarp.cuh)
+
+// Lagged friction data of one contact pair, taken at the start of the (sub)step (IPC, Li et al.
+// 2020, Sec. 5): the pair (as in the candidate list), whether it was in contact then, the
+// closest-point weights w (relative displacement of the closest points = sum_k w_k (P_k - Plag_k)),
+// the orthonormal tangent basis T (two columns, row-major 3 x 2) and the lagged normal force lam.
+struct FricRec {
+  int4 pr;
+  int active;
+  int pad_;
+  double w[4];
+  double T[6];
+  double lam;
+  double Plag[12];
+};
 
 // Barrier block of a pair with one free gel point: its diagonal block position and kappa d2b/dx2
 struct C1Rec {
@@ -189,6 +207,7 @@ struct Dev {
   double* chv;     // the projected kappa-scaled Hessians of those crec_cap pairs (CH_STRIDE each)
   int* chbp;       // their ns and block positions (CH_BP each)
   C1Rec* c1rec;    // single-free-point barrier blocks (appended; one per pair slot at most)
+  FricRec* fric;   // lagged friction records, one per pair slot at the (sub)step start (null: none)
   int* c1_n;
   double4_32a* cgrad;  // contact gradient per row: accumulated by the contact kernels, added by the gather
   int* err;

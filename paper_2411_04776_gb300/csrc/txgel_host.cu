@@ -44,6 +44,8 @@ void launch_contact_compute(const Dev& d, int phase, bool mixed, cudaStream_t st
 void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
 void launch_min_dist(const Dev& d, int phase, cudaStream_t st);
+void launch_fric_setup(const Dev& d, int phase, cudaStream_t st);
+void launch_fric(const Dev& d, int phase, int mode, bool mixed, cudaStream_t st);
 void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
                        const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st);
 void launch_eval_accd(int n, const int* kind, const double* P, const double* dP, double s, double tc,
@@ -85,8 +87,6 @@ void txg::set_last_error(const char* msg) { g_err = msg; }
 
 namespace {
 
-// phases beyond the ones the kernels name
-enum : int { PH_START = 3, PH_SAVE = 4, PH_FINAL = 5, PH_EVAL = 6, PH_PARK = 7, PH_FAIL = 8 };
 constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
 // default slices (32 rows) per PCG CTA: FP64 spreads a gel over many SMs (the FP64 pipe bounds
 // the SpMV); FP32 keeps groups small so that their barriers are cheap
@@ -101,6 +101,7 @@ constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernel
 constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
 constexpr int PIECE_HOST = 512;
 constexpr int PAIR_PIECES = 16;  // energy pieces over a gel's candidate pairs (a few thousand: one each per thread)
+constexpr int FRIC_PIECES = 4;   // energy pieces over a gel's friction records
 
 #define CK(call)                                                          \
   do {                                                                    \
@@ -176,7 +177,8 @@ tx_status check_desc(const tx_gel_desc* d) {
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
-      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 1 || p.reserved0 != 0)
+      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 1 || p.reserved0 != 0 || !(p.friction >= 0.0) ||
+      !(p.friction_eps_v > 0.0))
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
     if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
@@ -501,6 +503,7 @@ struct tx_batch {
     int best = -1;
   };
   bool force_stream = false;  // some gel asked for the streaming PCG kernels (tx_params.pcg_plan = 1)
+  bool friction = false;      // some gel has lagged friction (tx_params.friction > 0)
   bool tune_on = false;
   std::map<long long, Tune> tune;
   long long tune_key = -1;  // class of the current round (-1: not timing)
@@ -629,10 +632,18 @@ tx_status alloc_pairs(tx_batch* b) {
   nd.chv = nm.get<double>((size_t)nd.crec_cap * CH_STRIDE);
   nd.chbp = nm.get<int>((size_t)nd.crec_cap * CH_BP);
   nd.c1rec = nm.get<C1Rec>(total);
+  nd.fric = b->friction ? nm.get<FricRec>(total) : nullptr;
   if (nm.failed) {
     nm.release();
     b->gi = old;
     return TX_ERR_OOM;
+  }
+  if (b->friction && b->d.fric) {  // the lagged friction records of running substeps move along
+    for (int g = 0; g < b->n; ++g)
+      if (old[g].pcap > 0)
+        CK(cudaMemcpyAsync(nd.fric + b->gi[g].pbase, b->d.fric + old[g].pbase,
+                           sizeof(FricRec) * std::min(old[g].pcap, b->gi[g].pcap), cudaMemcpyDeviceToDevice, b->st));
+    CK(cudaStreamSynchronize(b->st));
   }
   b->pair_mem.release();
   b->pair_mem = nm;
@@ -778,6 +789,9 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     G.cell = m.cell;
     G.bbox_diag = m.bbox;
     G.newton_tol = m.prm.newton_tol;
+    G.mu_f = m.prm.friction;
+    G.eps_v = m.prm.friction_eps_v;
+    if (G.mu_f > 0.0) b->friction = true;
     for (int c = 0; c < 3; ++c) G.org[c] = m.org[c];
     int fc = 0;
     for (auto f : m.fixed) fc += f;
@@ -944,6 +958,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     for (int r = G.v0; r < G.v0 + G.nv; r += PIECE_HOST)
       b->pieces_h.push_back(make_int4(g, 1, r, std::min(r + PIECE_HOST, G.v0 + G.nv)));
     for (int k = 0; k < PAIR_PIECES; ++k) b->pieces_h.push_back(make_int4(g, 2, k, PAIR_PIECES));
+    if (G.mu_f > 0.0)  // lagged friction records
+      for (int k = 0; k < FRIC_PIECES; ++k) b->pieces_h.push_back(make_int4(g, 3, k, FRIC_PIECES));
   }
   b->gel_piece_h.push_back((int)b->pieces_h.size());
   b->npieces = (int)b->pieces_h.size();
@@ -1291,9 +1307,10 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
     if (s != TX_OK) return s;
     prof_open(b, PR_BEGIN);
     launch_rows(0, d, PH_START, st);         // x_n, predictor
+    if (b->friction) launch_fric_setup(d, PH_START, st);  // lagged friction at the substep start
     launch_hash_build(d, PH_START, 0, st);   // static tables at the target pose
     launch_energy(d, PH_START, b->pieces, b->npieces, b->gel_piece, b->part_e, b->en_ticket, 0, st);
-    prof_close(b, 4);
+    prof_close(b, b->friction ? 5 : 4);
     CK(cudaGetLastError());
     for (int g : start) {
       Run& R = b->run[g];
@@ -1622,7 +1639,8 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
   }
   prof_open(b, PR_CONTACT, cs);
   launch_contact_compute(d, PH_NEWTON, b->mixed, cs);
-  prof_close(b, 2, cs);
+  if (b->friction) launch_fric(d, PH_NEWTON, 0, b->mixed, cs);  // friction gradient and force
+  prof_close(b, b->friction ? 3 : 2, cs);
   if (cs != st) CK(cudaEventRecord(b->ev_join, cs));
   prof_open(b, PR_TET);
   launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
@@ -1631,7 +1649,8 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
   prof_open(b, PR_GATHER);
   launch_gather(d, PH_NEWTON, b->nbp, b->mixed, st);
   launch_contact_merge(d, b->mixed, st);
-  prof_close(b, 2);
+  if (b->friction) launch_fric(d, PH_NEWTON, 1, b->mixed, st);  // friction blocks into the matrix
+  prof_close(b, b->friction ? 3 : 2);
   prof_open(b, PR_PRECOND);
   launch_precond(d, PH_NEWTON, b->mixed, st);
   prof_close(b, 1);
@@ -2073,6 +2092,8 @@ void tx_params_default(tx_params* p) {
   p->precision = TX_PREC_FP64;
   p->refine_max = 3;
   p->pcg_cta_slices = 0;
+  p->friction = 0.0;
+  p->friction_eps_v = 1e-3;
 }
 
 const char* tx_status_str(tx_status s) {
