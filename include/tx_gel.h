@@ -226,6 +226,30 @@ tx_status tx_batch_set_state(tx_batch* b, int32_t gel, const double* x, const do
                              const double pose[7]);
 tx_status tx_batch_reset(tx_batch* b, int32_t gel);
 
+/* ---------------- gel-surface readout ----------------
+ * For the tactile simulation that consumes the physics state (TacEx, Sec. "Tactile Simulation":
+ * height maps of the gel surface feed the optical simulation; App. "Marker Simulation": markers
+ * tied to faces of the tet mesh follow the vertex positions of their facet).  The top surface is
+ * the set of boundary triangles whose rest outward normal points up (+z).  Both calls read the
+ * gel's current state (not while a request of the gel is in flight: TX_ERR_ARG), run on the
+ * device and return when the host arrays are filled.
+ *
+ * Markers: n markers at rest points rest_xy (n x 2, [m]) of the top surface; each lies in a top
+ * triangle of the rest mesh (the first in the surface order whose xy barycentric coordinates are
+ * all >= -1e-12) and is carried by them to the current positions: out (n x 3); found[i] = 0 (and
+ * out zero) for a point off the top surface. */
+tx_status tx_gel_markers(tx_gel* g, int32_t n, const double* rest_xy, double* out, int32_t* found);
+tx_status tx_batch_markers(tx_batch* b, int32_t gel, int32_t n, const double* rest_xy, double* out, int32_t* found);
+
+/* Height map of the deformed top surface seen from above: out (ny x nx, row j = y) at pixel
+ * centres (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy) holds the largest z [m] of the top triangles
+ * covering the centre in the xy projection (barycentric coordinates >= -1e-12), NaN where none
+ * does.  Rasterised by a CUDA kernel (no graphics API); nx * ny <= 2^26. */
+tx_status tx_gel_height_map(tx_gel* g, int32_t nx, int32_t ny, double x0, double y0, double dx, double dy,
+                            double* out);
+tx_status tx_batch_height_map(tx_batch* b, int32_t gel, int32_t nx, int32_t ny, double x0, double y0, double dx,
+                              double dy, double* out);
+
 /* ---------------- per-phase device timing ----------------
  * With profiling enabled the library brackets each phase of the step with CUDA events on the
  * handle's stream and accumulates, per phase, the device time, the number of kernel launches and

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libtxgel.so")
-UNITS = ["k_elastic.cu", "k_contact.cu", "k_solve.cu", "k_pcg_res.cu", "k_bsr_pcg.cu", "k_peak.cu", "txgel_host.cu"]
+UNITS = ["k_elastic.cu", "k_contact.cu", "k_solve.cu", "k_pcg_res.cu", "k_bsr_pcg.cu", "k_peak.cu", "k_readout.cu", "txgel_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -121,6 +121,12 @@ _SIGS = [
     ("tx_batch_size", ctypes.c_int32, [ctypes.c_void_p]),
     ("tx_batch_step", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_ip]),
     ("tx_batch_step_attached", ctypes.c_int, [ctypes.c_void_p, c_dp, c_dp, c_dp, c_ip]),
+    ("tx_gel_markers", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_dp, c_dp, c_ip]),
+    ("tx_batch_markers", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, c_dp, c_dp, c_ip]),
+    ("tx_gel_height_map", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, c_dp]),
+    ("tx_batch_height_map", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_dp]),
     ("tx_batch_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_ip, c_dp, c_dp]),
     ("tx_batch_advance", ctypes.c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip]),
     ("tx_batch_pending", ctypes.c_int32, [ctypes.c_void_p]),
@@ -279,6 +285,23 @@ def tx_gel_step_attached(g, pose, case_pose, dt) -> int:
 def tx_gel_case_pose(g):
     out = np.zeros(7)
     _check(load().tx_gel_case_pose(g, _d(out)[1]), "tx_gel_case_pose")
+    return out
+
+
+def tx_gel_markers(g, rest_xy):
+    """Markers at rest points (n x 2) of the top surface carried to the current state: (n x 3, found)."""
+    rest_xy, rp = _d(rest_xy)
+    n = len(rest_xy)
+    out = np.zeros((n, 3))
+    found = np.zeros(n, dtype=np.int32)
+    _check(load().tx_gel_markers(g, n, rp, _d(out)[1], found.ctypes.data_as(c_ip)), "tx_gel_markers")
+    return out, found.astype(bool)
+
+
+def tx_gel_height_map(g, nx, ny, x0, y0, dx, dy):
+    out = np.zeros((ny, nx))
+    _check(load().tx_gel_height_map(g, int(nx), int(ny), float(x0), float(y0), float(dx), float(dy), _d(out)[1]),
+           "tx_gel_height_map")
     return out
 
 
@@ -524,6 +547,12 @@ class Gel:
 
     def case_pose(self):
         return tx_gel_case_pose(self.h)
+
+    def markers(self, rest_xy):
+        return tx_gel_markers(self.h, rest_xy)
+
+    def height_map(self, nx, ny, x0, y0, dx, dy):
+        return tx_gel_height_map(self.h, nx, ny, x0, y0, dx, dy)
 
     def state(self):
         return tx_gel_state(self.h, self.n)

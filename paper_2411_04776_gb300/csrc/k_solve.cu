@@ -797,8 +797,9 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
     v.flags = 0;
     v.ls_total = 0;
     v.active_pairs = 0;
-  } else if (op == 4) {
+  } else if (op == 4) {  // the final state's distance minimum and active-pair count follow
     v.dmin_bits = dbits(CUDART_INF);
+    v.active_pairs = 0;
   } else if (op == 5) {
     if (v.ls_state == 1) v.ls_state = 3;  // the accepted step has been applied
   } else if (op == 6) {

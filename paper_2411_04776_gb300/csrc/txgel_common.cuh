@@ -56,6 +56,7 @@ struct GelInfo {  // per gel, read-only after create
   double mu, lam, kappa, dhat, cell, bbox_diag, newton_tol;
   double org[3];             // hash grid origin
   double mu_f, eps_v;        // IPC lagged friction: coefficient (0: frictionless), velocity threshold
+  int top0, ntop;            // top-surface triangles (rest outward normal up) in Dev::top
 };
 
 struct GelCtl {  // per gel, written by the host before the launches of an iteration
@@ -208,6 +209,7 @@ struct Dev {
   int* chbp;       // their ns and block positions (CH_BP each)
   C1Rec* c1rec;    // single-free-point barrier blocks (appended; one per pair slot at most)
   FricRec* fric;   // lagged friction records, one per pair slot at the (sub)step start (null: none)
+  int4* top;       // top-surface triangles of every gel (rows a, b, c), the readout's surface
   int* c1_n;
   double4_32a* cgrad;  // contact gradient per row: accumulated by the contact kernels, added by the gather
   int* err;

@@ -45,6 +45,9 @@ void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
 void launch_min_dist(const Dev& d, int phase, cudaStream_t st);
 void launch_fric_setup(const Dev& d, int phase, cudaStream_t st);
+void launch_markers(const Dev& d, int g, int n, const double* rest_xy, double* out, int* found, cudaStream_t st);
+void launch_height_map(const Dev& d, int g, int ntop, int nx, int ny, double x0, double y0, double dx, double dy,
+                       unsigned long long* img, double* out, cudaStream_t st);
 void launch_fric(const Dev& d, int phase, int mode, bool mixed, cudaStream_t st);
 void launch_eval_pairs(int n, const int* kind, const double* P, double dhat, const double* eps_x,
                        const int* free_mask, double* b, double* g, double* H, int* dtype, cudaStream_t st);
@@ -454,6 +457,8 @@ struct tx_batch {
   Dev d{};
   DevMem mem;
   DevMem pair_mem;          // pairs + slot map (regrown on overflow)
+  DevMem readout_mem;       // scratch of the surface readout (grown on demand)
+  size_t readout_bytes = 0;
   DevMem hash_mem;          // hash entries (regrown on overflow)
   int nbp = 0;
   // PCG
@@ -870,6 +875,21 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
           ctr[fillp[bp]++] = ((b->gi[g].t0 + t) << 4) | (a << 2) | c;
         }
   }
+  // ---- top surface (readout): boundary triangles whose rest outward normal points up
+  std::vector<int4> top4;
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    GelInfo& G = b->gi[g];
+    G.top0 = (int)top4.size();
+    for (const auto& t : m.st) {
+      const double* A = &m.X[3 * t[0]];
+      const double* Bv = &m.X[3 * t[1]];
+      const double* C = &m.X[3 * t[2]];
+      const double nz = (Bv[0] - A[0]) * (C[1] - A[1]) - (Bv[1] - A[1]) * (C[0] - A[0]);
+      if (nz > 0.0) top4.push_back(make_int4(G.v0 + t[0], G.v0 + t[1], G.v0 + t[2], g));
+    }
+    G.ntop = (int)top4.size() - G.top0;
+  }
   // ---- host arrays of the concatenated gels
   std::vector<double4_32a> X(rows);
   std::vector<int4> tet4(std::max(tets, 1));
@@ -1039,6 +1059,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.qnear = M.get<int>(nq + 1);
   d.qnear_n = M.get<int>(4);
   d.err = M.get<int>(4);
+  d.top = M.get<int4>(std::max<size_t>(top4.size(), 1));
   d.cwork_n = M.get<int>(4);
   d.c1_n = M.get<int>(4);
   b->pieces = M.get<int4>(b->npieces);
@@ -1121,6 +1142,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U(d.iv_gel, iv_gel.data(), sizeof(int) * niv);
   U(d.it_gel, it_gel.data(), sizeof(int) * nit);
   U(d.ie_gel, ie_gel.data(), sizeof(int) * nie);
+  U(d.top, top4.data(), sizeof(int4) * top4.size());
   U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
   U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
@@ -2066,6 +2088,7 @@ void destroy_batch(tx_batch* b) {
   b->pair_mem.release();
   b->hash_mem.release();
   b->plan_mem.release();
+  b->readout_mem.release();
   if (b->gc_h) cudaFreeHost(b->gc_h);
   if (b->gv_h) cudaFreeHost(b->gv_h);
   delete b;
@@ -2286,6 +2309,67 @@ tx_status tx_gel_step_attached(tx_gel* g, const double pose[7], const double cas
   tx_status st = TX_OK;
   tx_status s = tx_batch_step_attached(g->b, pose, case_pose, &dt, &st);
   return s != TX_OK ? s : st;
+}
+
+// device scratch of the readout calls, grown on demand (the handle keeps it)
+void* readout_scratch(tx_batch* b, size_t bytes) {
+  if (bytes <= b->readout_bytes) return b->readout_mem.ptrs.empty() ? nullptr : b->readout_mem.ptrs[0];
+  cudaStreamSynchronize(b->st);
+  b->readout_mem.release();
+  const size_t want = std::max(bytes, 2 * b->readout_bytes);
+  unsigned char* p = b->readout_mem.get<unsigned char>(want);
+  b->readout_bytes = p ? want : 0;
+  return p;
+}
+
+tx_status tx_batch_markers(tx_batch* b, int32_t gel, int32_t n, const double* rest_xy, double* out, int32_t* found) {
+  if (!b || gel < 0 || gel >= b->n || n < 0 || (n > 0 && (!rest_xy || !out || !found))) return TX_ERR_ARG;
+  if (b->run[gel].in_request) return TX_ERR_ARG;
+  if (n == 0) return TX_OK;
+  const size_t nb = (size_t)n;
+  unsigned char* p = static_cast<unsigned char*>(readout_scratch(b, nb * (2 + 3) * sizeof(double) + nb * sizeof(int)));
+  if (!p) return TX_ERR_OOM;
+  double* dxy = reinterpret_cast<double*>(p);
+  double* dout = dxy + 2 * nb;
+  int* dfound = reinterpret_cast<int*>(dout + 3 * nb);
+  CK(cudaMemcpyAsync(dxy, rest_xy, sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, b->st));
+  launch_markers(b->d, gel, n, dxy, dout, dfound, b->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, dout, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, b->st));
+  CK(cudaMemcpyAsync(found, dfound, sizeof(int) * nb, cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+
+tx_status tx_batch_height_map(tx_batch* b, int32_t gel, int32_t nx, int32_t ny, double x0, double y0, double dx,
+                              double dy, double* out) {
+  if (!b || gel < 0 || gel >= b->n || nx < 1 || ny < 1 || (size_t)nx * (size_t)ny > ((size_t)1 << 26) || !out ||
+      !std::isfinite(x0) || !std::isfinite(y0) || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) ||
+      !std::isfinite(dy))
+    return TX_ERR_ARG;
+  if (b->run[gel].in_request) return TX_ERR_ARG;
+  const size_t np = (size_t)nx * (size_t)ny;
+  unsigned char* p = static_cast<unsigned char*>(readout_scratch(b, np * (sizeof(unsigned long long) + sizeof(double))));
+  if (!p) return TX_ERR_OOM;
+  unsigned long long* img = reinterpret_cast<unsigned long long*>(p);
+  double* dout = reinterpret_cast<double*>(img + np);
+  CK(cudaMemsetAsync(img, 0, sizeof(unsigned long long) * np, b->st));
+  launch_height_map(b->d, gel, b->gi[gel].ntop, nx, ny, x0, y0, dx, dy, img, dout, b->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, dout, sizeof(double) * np, cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  return TX_OK;
+}
+
+tx_status tx_gel_markers(tx_gel* g, int32_t n, const double* rest_xy, double* out, int32_t* found) {
+  if (!g) return TX_ERR_ARG;
+  return tx_batch_markers(g->b, 0, n, rest_xy, out, found);
+}
+
+tx_status tx_gel_height_map(tx_gel* g, int32_t nx, int32_t ny, double x0, double y0, double dx, double dy,
+                            double* out) {
+  if (!g) return TX_ERR_ARG;
+  return tx_batch_height_map(g->b, 0, nx, ny, x0, y0, dx, dy, out);
 }
 
 tx_status tx_gel_case_pose(const tx_gel* g, double case_pose[7]) {

@@ -35,7 +35,7 @@ def load_golden(case):
     """FP64 oracle snapshots of the GelSight-Mini gel (tests/golden/make_oracle_snapshots.py):
     displacements and contact forces at the snapshot steps, substeps, Newton iterations and
     active pairs per step.  "window": the benchmark trajectory, steps 0..24; "fastpress": the
-    same prism pressed 1.0 mm over 12 steps, steps 0..5 (every step split)."""
+    same prism pressed 1.0 mm over 12 steps, steps 0 and 1 (each split in two)."""
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", GOLDEN[case])
     z = np.load(path)

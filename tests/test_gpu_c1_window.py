@@ -4,8 +4,8 @@ the benchmark times (one gel, the resident PCG kernels), against stored FP64 ora
 
 * "window": the benchmark's own trajectory (the seeded prism pressed 1.0 mm over 60 steps), steps
   0..24 -- the timed window (steps 5..24) is deep-press contact, 300 to 900 active pairs;
-* "fastpress": the same prism pressed 1.0 mm over 12 steps, steps 0..5 -- every step's indenter
-  move has to be split (R7), with deep contact.
+* "fastpress": the same prism pressed 1.0 mm over 12 steps, steps 0 and 1 -- each step's indenter
+  move has to be split (R7), with ~300 active pairs.
 
 Every vertex is compared at every stored step, the substep count of every step and the contact
 force.  The mixed-precision run of the same steps reports its error step by step against the same
