@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: total request rate [1/s]")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM admission budget")
+    ap.add_argument("--rate-sweep", default="", help="serve: further offered rates, comma separated")
+    ap.add_argument("--plain-sample", type=int, default=32,
+                    help="serve: gels of the plain FP64 one-at-a-time comparison (0: skip)")
     ap.add_argument("--n-gels", type=int, default=0, help="gels per batch (batch workloads)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=0)
@@ -403,7 +406,12 @@ def cpu_baseline(args, budget=30.0):
 
 def run_serve(args):
     """Continuous-batching server over resident gels (config 4): Poisson step requests from the
-    environments, admission by HBM footprint, one Newton iteration per round for all admitted."""
+    environments, admission by HBM footprint, one Newton iteration per round for all admitted.
+    The offered rate args.rate is the headline; --rate-sweep adds lower rates (same server; before
+    each rate the environments are reset and take the warm-up steps again, so every rate serves
+    the same trajectory window) to find the highest rate the server sustains (served rate >= 95 %
+    of the offered one).  Beside it, the plain FP64 path stepping a sample of the same
+    gels one at a time."""
     import torch
     from paper_2411_04776_gb300 import binding as B
     from paper_2411_04776_gb300 import serving as S
@@ -416,27 +424,48 @@ def run_serve(args):
     t_create = time.perf_counter() - t0
     # warm-up: every environment takes its first steps
     srv.run_schedule([list(range(srv.n))] * max(1, args.warmup))
-    srv.completed.clear()
-    arrivals = S.poisson_arrivals(srv.n, args.rate, args.duration, args.seed + 1)
-    with ClockSampler(0) as clk:
-        t0 = time.perf_counter()
-        done = srv.serve(arrivals, drain=True)
-        wall = time.perf_counter() - t0
-    ok = [r for r in done if r.status == 0]
-    lat = S.latency_summary(done)
-    line = {"metric": "gel Newton-converged steps/sec", "value": len(ok) / wall, "unit": "steps/s", "n_gpus": 1,
-            "steps": len(ok), "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(len(ok), 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+    rates = [args.rate] + [float(r) for r in args.rate_sweep.split(",") if r.strip()]
+    runs = []
+    for k, rate in enumerate(rates):
+        if k > 0:  # every rate starts from the same state: the environments back at the warm-up's end
+            for e in range(srv.n):
+                B.tx_batch_reset(srv.handle, e)
+            srv.cursor[:] = 0
+            srv.run_schedule([list(range(srv.n))] * max(1, args.warmup))
+        srv.completed.clear()
+        srv.max_inflight, srv.max_inflight_bytes = 0, 0.0
+        arrivals = S.poisson_arrivals(srv.n, rate, args.duration, args.seed + 1 + k)
+        with ClockSampler(0) as clk:
+            t1 = time.perf_counter()
+            done = list(srv.serve(arrivals, drain=True))
+            wall = time.perf_counter() - t1
+        ok = [r for r in done if r.status == 0]
+        served = len(ok) / wall
+        runs.append({"rate": rate, "requests": len(arrivals), "value": served, "unit": "steps/s",
+                     "wall_s": wall, "sustained": served >= 0.95 * len(arrivals) / args.duration,
+                     "latency_ms": S.latency_summary(done), "failed": len(done) - len(ok),
+                     "failed_requests": [[r.env, r.step % len(wls[r.env].poses), B.STATUS_NAMES.get(r.status, r.status)]
+                                         for r in done if r.status != 0][:16],
+                     "max_inflight": srv.max_inflight, "max_inflight_gb": srv.max_inflight_bytes / 1e9,
+                     "clocks": clk.summary()})
+    srv.close()
+    plain = plain_fp64_sequential(wls[:args.plain_sample], 4, max(1, args.warmup))[0] if args.plain_sample else None
+    head = runs[0]
+    sustained = [r["rate"] for r in runs if r["sustained"]]
+    line = {"metric": "gel Newton-converged steps/sec", "value": head["value"], "unit": "steps/s", "n_gpus": 1,
+            "steps": int(round(head["value"] * head["wall_s"])), "warmup": args.warmup,
+            "ms_per_step": 1e3 / max(head["value"], 1e-9), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
             "config": dict(workload_config(wls, "serve", args.precision), rate=args.rate, duration=args.duration,
                            budget_gb=args.budget_gb),
-            "latency_ms": lat, "requests": len(arrivals), "failed": len(done) - len(ok),
-            "failed_status": sorted({B.STATUS_NAMES.get(r.status, r.status) for r in done if r.status != 0}),
-            "failed_requests": [[r.env, r.step % len(wls[r.env].poses), B.STATUS_NAMES.get(r.status, r.status)]
-                                for r in done if r.status != 0][:32],
-            "max_inflight": srv.max_inflight, "max_inflight_gb": srv.max_inflight_bytes / 1e9,
-            "resident_gb": float(srv.footprint.sum() / 1e9), "create_s": t_create, "clocks": clk.summary()}
-    srv.close()
+            "latency_ms": head["latency_ms"], "requests": head["requests"], "failed": head["failed"],
+            "failed_requests": head["failed_requests"], "max_inflight": head["max_inflight"],
+            "max_inflight_gb": head["max_inflight_gb"], "resident_gb": float(srv.footprint.sum() / 1e9),
+            "create_s": t_create, "rate_sweep": runs[1:],
+            "max_sustained_rate": max(sustained) if sustained else None,
+            "plain_fp64_one_at_a_time": plain,
+            "vs_plain_fp64": (head["value"] / plain["value"]) if plain else None,
+            "clocks": head["clocks"]}
     print(json.dumps(line))
 
 
