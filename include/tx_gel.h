@@ -142,13 +142,21 @@ const char* tx_last_error(void);
 
 /* ---------------- single gel ---------------- */
 
-/* Validates and copies the description, precomputes rest data (Dm^-1, volumes, lumped masses,
- * surface, BSR pattern), allocates device memory and uploads.  Returns TX_ERR_MESH_INVERTED if a
- * rest tet has det(Dm) <= 0, TX_ERR_ARG on bad sizes/indices. */
+/* TacEx Sec. "General GIPC Simulation Pipeline" (set-up: a simulated object becomes a GIPC object
+ * from its tetrahedral mesh before the first step).  Validates and copies the description,
+ * precomputes rest data (Dm^-1, volumes, lumped masses, surface, BSR pattern), allocates device
+ * memory and uploads.  The handle owns everything it allocates until tx_gel_destroy.  Returns
+ * TX_ERR_MESH_INVERTED if a rest tet has det(Dm) <= 0, TX_ERR_ARG on bad sizes/indices or
+ * parameters, TX_ERR_OOM (nothing left allocated) if device or pinned host memory runs out. */
 tx_status tx_gel_create(const tx_gel_desc* desc, void* stream, tx_gel** out);
 
-/* Advances one time step of length dt with the indenter moving (linearly in position, along the
- * short arc in rotation) from its current pose to `pose`.  Blocks until the step has finished. */
+/* TacEx Sec. "General GIPC Simulation Pipeline": one GIPC step -- the kinematic target (here the
+ * indenter pose) is set, then the solver moves the free gel vertices (the incremental-potential
+ * minimisation above; App. A "Choice of the Simulation Methods": intersection- and inversion-
+ * free).  Advances one time step of length dt with the indenter moving (linearly in position,
+ * along the short arc in rotation) from its current pose to `pose`; a move whose sweep would hit
+ * the gel is split into half steps.  Blocks until the step has finished; on error the state stays
+ * at the step's start. */
 tx_status tx_gel_step(tx_gel* g, const double pose[7], double dt);
 
 /* TacEx Sec. "General GIPC Simulation Pipeline" (GIPC attachments): each step first sets the
@@ -165,10 +173,12 @@ tx_status tx_gel_step_attached(tx_gel* g, const double pose[7], const double cas
 /* The current case pose of an attachment-driven gel (identity if none was ever given). */
 tx_status tx_gel_case_pose(const tx_gel* g, double case_pose[7]);
 
-/* Reads the state: x, v (n_verts x 3, may be NULL), contact force (3, may be NULL) and the last
- * step's statistics (may be NULL).  If device_ptrs != 0, x and v are device pointers and the copy
- * is enqueued on the gel's stream (ordered after the last step); otherwise host pointers and the
- * call returns after the copy. */
+/* TacEx Sec. "General GIPC Simulation Pipeline": after each step the vertex positions update the
+ * rendered gel mesh and their mean is the object position.  Reads the state: x, v (n_verts x 3,
+ * may be NULL), contact force (3, may be NULL) and the last step's statistics (may be NULL; its
+ * mean_position is that mean).  If device_ptrs != 0, x and v are device pointers and the copy is
+ * enqueued on the gel's stream (ordered after the last step); otherwise host pointers and the
+ * call returns after the copy.  The caller owns the output arrays. */
 tx_status tx_gel_state(const tx_gel* g, double* x, double* v, double f_contact[3],
                        tx_step_stats* stats, int32_t device_ptrs);
 

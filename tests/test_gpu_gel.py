@@ -165,3 +165,26 @@ def test_error_paths():
     x, v, _, _ = gel.state()
     assert np.array_equal(x, wl.gel.verts)  # transactional
     assert gel.step(wl.poses[0], wl.dt) == 0
+
+
+def test_autotuned_split_keeps_the_minimiser():
+    """The opt-in PCG work-split autotuner (pcg_cta_slices = -1) tries other CTA splits on live
+    Newton rounds; the split changes only the order of the PCG's sums, so the stepped states stay
+    within the parity gate of the default split."""
+    wls = [W.small_gel_sphere(s) for s in range(3)] + [W.mini_gel(7, grid=W.GRID_MID, depth=0.5e-3)]
+    tuned = B.tx_batch_create([B.GelDesc.from_workload(w, newton_tol=PARITY_NEWTON_TOL, pcg_cta_slices=-1)
+                               for w in wls])
+    plain = B.tx_batch_create([B.GelDesc.from_workload(w, newton_tol=PARITY_NEWTON_TOL) for w in wls])
+    try:
+        for s in range(12):
+            poses = np.stack([w.poses[s] for w in wls])
+            dts = np.array([w.dt for w in wls])
+            for h in (tuned, plain):
+                st, sts = B.tx_batch_step(h, poses, dts)
+                assert st == 0 and np.all(sts == 0)
+        for g, w in enumerate(wls):
+            d = np.abs(B.tx_batch_state(tuned, g, len(w.gel.verts))[0] - B.tx_batch_state(plain, g, len(w.gel.verts))[0])
+            assert d.max() <= POS_TOL, (g, d.max())
+    finally:
+        B.tx_batch_destroy(tuned)
+        B.tx_batch_destroy(plain)
