@@ -146,7 +146,7 @@ def fp64_peak_tflops(sm_mhz):
 
 
 def measure_fma_peaks(dev, target_ms=150.0):
-    """FP64 and FP32 FMA-pipe peaks measured on this device now (tx_peak_fma: every SM, eight
+    """FP64 and FP32 FMA-pipe peaks measured on this device now (tx_peak_fma: every SM, four
     independent FMA chains per thread, CUDA-event timed), with the SM clock sampled while they
     run.  Each is the best of three launches sized to about target_ms."""
     from paper_2411_04776_gb300 import binding as B
@@ -161,7 +161,7 @@ def measure_fma_peaks(dev, target_ms=150.0):
                 best = max(best, f / (ms * 1e-3) / 1e12)
             out[f"fp{bits}_tflops"] = best
     out["clocks"] = clk.summary()
-    out["how"] = "tx_peak_fma: 8 independent FMA chains per thread over every SM, best of 3 CUDA-event-timed launches"
+    out["how"] = "tx_peak_fma: 4 independent FMA chains per thread over every SM, best of 3 CUDA-event-timed launches"
     return out
 
 

@@ -288,7 +288,7 @@ tx_status tx_gel_profile(tx_gel* g, int32_t enable, tx_profile* out);
 
 /* ---------------- measurement ----------------
  * Peak rate of the plain (non-tensor) FMA pipe in FP64 (bits = 64) or FP32 (bits = 32): one launch
- * over every SM in which each thread runs eight independent chains of `iters` FMAs, timed with
+ * over every SM in which each thread runs four independent chains of `iters` FMAs, timed with
  * CUDA events on `stream` (the call waits for it).  *flops = 2 x the FMAs executed, *ms = the
  * launch's event time; flops / ms is the roofline denominator of the FP64-bound solver kernels.
  * No counterpart in the paper: it measures the device the solver runs on. */

@@ -11,26 +11,42 @@
 namespace txg {
 
 constexpr int RES_MAXW = 8;    // warps (slices) per CTA
+// FP64: two warps per slice (an owner and a helper splitting its SpMV blocks) while a CTA holds at
+// most RES_SPLIT_MAXS slices.  A warp issues an FP64 FMA only about every 67 cycles, and with one
+// warp per sub-partition every bubble in its stream (operand loads, dependencies) idles the
+// sub-partition's FP64 pipe; a second warp fills them.
+constexpr int RES_SPLIT_MAXS = 4;
+constexpr int RES_SPLIT_W = 2 * RES_SPLIT_MAXS + 1;  // warps per CTA: owners, helpers, control
 constexpr int RES_MAXNC = 256; // CTAs of one group (exchange slots a lane prefetches: 8)
 
-// warp-owned image of slice s in shared memory: values [k][9][32], column indices [k][32]
+// warp-owned image of slice s in shared memory: values [k][9][32], column indices [k][32].  Both
+// are contiguous in the sliced BSR (a slice starts at a multiple of 32 positions, so at a 16-byte
+// boundary of the 256-byte aligned arrays) with the same layout, so the warp copies them as
+// 16-byte pieces with cp.async: every piece in flight at once, none through registers.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
+// tid / nthr: this thread's index among the nthr threads that copy the image together; each
+// waits for its own pieces, and a barrier over those threads must follow before the image is read
 template <typename V>
-__device__ __forceinline__ int res_load(const Dev& d, int s, const V* gval, V* sv, int* sc, int lane) {
+__device__ __forceinline__ int res_load(const Dev& d, int s, const V* gval, V* sv, int* sc, int tid, int nthr) {
   const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
-  for (int k = 0; k < w; ++k) {
-    sc[32 * k + lane] = d.colidx[o + 32 * k + lane];
-    const V* src = gval + (size_t)9 * (o + 32 * k) + lane;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) sv[288 * k + 32 * e + lane] = src[32 * e];
-  }
+  const char* vsrc = reinterpret_cast<const char*>(gval + (size_t)9 * o);
+  char* vdst = reinterpret_cast<char*>(sv);
+  const int nv = w * 288 * (int)sizeof(V) / 16;
+  for (int i = tid; i < nv; i += nthr) cp_async16(vdst + 16 * i, vsrc + 16 * i);
+  const char* csrc = reinterpret_cast<const char*>(d.colidx + o);
+  char* cdst = reinterpret_cast<char*>(sc);
+  for (int i = tid; i < 8 * w; i += nthr) cp_async16(cdst + 16 * i, csrc + 16 * i);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   return w;
 }
 
+// one block of the lane's row: a += A_k uc (values from the slice image in shared memory)
 template <typename V, typename U, typename A>
-__device__ __forceinline__ void res_block(const V* sv, const int* sc, int k, int lane, const U* u, A& a0, A& a1,
-                                          A& a2) {
-  const int c = sc[32 * k + lane];
-  const U uc = u[c];
+__device__ __forceinline__ void res_block(const V* sv, int k, int lane, const U uc, A& a0, A& a1, A& a2) {
   const V* v = sv + 288 * k + lane;
   a0 = fma((A)v[0], (A)uc.x, a0);
   a1 = fma((A)v[96], (A)uc.x, a1);
@@ -43,22 +59,76 @@ __device__ __forceinline__ void res_block(const V* sv, const int* sc, int k, int
   a2 = fma((A)v[256], (A)uc.z, a2);
 }
 
-// y = A u for the lane's row: values from shared memory, u gathered from global memory; even and
-// odd blocks accumulate separately (six independent FMA chains), then add
+// y = A u for the lane's row: values from shared memory, u gathered from global memory (L2)
+// RES_PF blocks ahead of the block being multiplied (a register ring), so that the gathers'
+// latency hides behind the FP64 work of the blocks before them; even and odd blocks accumulate
+// separately (six independent FMA chains), then add
+constexpr int RES_PF = 4;  // even: a ring slot keeps the parity of its blocks
 template <typename V, typename U, typename A>
 __device__ __forceinline__ void res_spmv(const V* sv, const int* sc, int w, int lane, const U* u, A& y0, A& y1,
                                          A& y2) {
   A a0 = A(0), a1 = A(0), a2 = A(0), b0 = A(0), b1 = A(0), b2 = A(0);
-  int k = 0;
-#pragma unroll 4
-  for (; k + 1 < w; k += 2) {
-    res_block(sv, sc, k, lane, u, a0, a1, a2);
-    res_block(sv, sc, k + 1, lane, u, b0, b1, b2);
+  U ring[RES_PF];
+#pragma unroll
+  for (int t = 0; t < RES_PF; ++t)
+    if (t < w) ring[t] = u[sc[32 * t + lane]];
+  for (int k0 = 0; k0 < w; k0 += RES_PF) {
+#pragma unroll
+    for (int t = 0; t < RES_PF; ++t) {
+      const int k = k0 + t;
+      if (k < w) {
+        const U uc = ring[t];
+        if (k + RES_PF < w) ring[t] = u[sc[32 * (k + RES_PF) + lane]];
+        if (t & 1)
+          res_block(sv, k, lane, uc, b0, b1, b2);
+        else
+          res_block(sv, k, lane, uc, a0, a1, a2);
+      }
+    }
   }
-  if (k < w) res_block(sv, sc, k, lane, u, a0, a1, a2);
   y0 = a0 + b0;
   y1 = a1 + b1;
   y2 = a2 + b2;
+}
+
+// The blocks k = k0, k0 + 2, ... of the lane's row: the share of one of the two warps of a slice
+// (split FP64 kernel); its even and odd blocks accumulate separately (six FMA chains), then add.
+__device__ __forceinline__ void res_spmv_half(const double* sv, const int* sc, int w, int k0, int lane,
+                                              const double4_32a* u, double& y0, double& y1, double& y2) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
+  int k = k0;
+#pragma unroll 2
+  for (; k + 2 < w; k += 4) {
+    res_block(sv, k, lane, u[sc[32 * k + lane]], a0, a1, a2);
+    res_block(sv, k + 2, lane, u[sc[32 * (k + 2) + lane]], b0, b1, b2);
+  }
+  if (k < w) res_block(sv, k, lane, u[sc[32 * k + lane]], a0, a1, a2);
+  y0 = a0 + b0;
+  y1 = a1 + b1;
+  y2 = a2 + b2;
+}
+
+// Warp sums of three per-lane FP64 values with 6 adds per lane instead of three butterflies'
+// 15 (the FP64 pipe is the scarce unit): at the first level lanes 0-15 carry (a, b) and lanes
+// 16-31 (c, -), at the second each lane keeps one of its two, and three butterfly levels finish
+// it.  Afterwards lanes 0-7 hold the sum of a, lanes 8-15 that of b, lanes 16-23 that of c.
+// Fixed order: bitwise the same in every warp and run.
+__device__ __forceinline__ double warp_sum3(double a, double b, double c, int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  double k0 = h16 ? c : a, k1 = h16 ? 0.0 : b;
+  const double g0 = h16 ? a : c, g1 = h16 ? b : 0.0;
+  k0 += __shfl_xor_sync(0xffffffffu, g0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, g1, 16);
+  double v = h8 ? k1 : k0;
+  v += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// the three sums of warp_sum3 into dsm[base + 0..2]
+__device__ __forceinline__ void put_sum3(double* dsm, int base, double v, int lane) {
+  if ((lane & 7) == 0 && lane < 24) dsm[base + (lane >> 3)] = v;
 }
 
 // CG scalars with two levels of division: beta = ga / ga_prev and t = ga / al_prev are independent
@@ -74,14 +144,18 @@ __device__ __forceinline__ void cg_scalars(int k, double ga, double de, double g
   }
 }
 
-// shared memory: [dsm: 4 per slice][values: warps x wmax x 288][columns: warps x wmax x 32]
+// shared memory: [dsm: 4 per slice][split kernel: helper partials, 96 per slice]
+// [values: slices x wmax x 288][columns: slices x wmax x 32]; sw: the warp's slice in the CTA
+// (the control warp's points past the images and is never used)
 template <typename V>
-__device__ __forceinline__ void res_smem(double* dyn, int max_slices, int wmax, double*& dsm, V*& sv, int*& sc) {
-  const int nw = max_slices, wid = threadIdx.x >> 5;  // slice warps; the control warp has no slice
+__device__ __forceinline__ void res_smem(double* dyn, int max_slices, int wmax, int sw, bool split, double*& dsm,
+                                         double*& hs, V*& sv, int*& sc) {
+  const int nw = max_slices;
   dsm = dyn;
-  V* vbase = reinterpret_cast<V*>(dyn + 4 * max_slices);
-  sv = vbase + (size_t)wid * wmax * 288;
-  sc = reinterpret_cast<int*>(vbase + (size_t)nw * wmax * 288) + (size_t)wid * wmax * 32;
+  hs = dyn + 4 * nw;
+  V* vbase = reinterpret_cast<V*>(dyn + 4 * nw + (split ? 96 * nw : 0));
+  sv = vbase + (size_t)sw * wmax * 288;
+  sc = reinterpret_cast<int*>(vbase + (size_t)nw * wmax * 288) + (size_t)sw * wmax * 32;
 }
 
 // Split group sums of the pipelined kernels (one group barrier between post and collect).
@@ -98,9 +172,12 @@ __device__ __forceinline__ void res_post(const Dev& d, const PcgCta& c, const do
     const int j = t / nk, k = k0 + t % nk;
     const GelInfo& G = d.gi[c.g0 + j];
     const int a = max(c.s0, G.s0), b = min(c.s1, G.s0 + G.ns);
+    // a CTA owns at most RES_MAXW - 1 slices: lane 0 adds their partials in slice order
     double v = 0.0;
-    for (int s = a + lane; s < b; s += 32) v += dsm[(s - c.s0) * 4 + k];
-    v = warp_sum(v);
+    if (lane == 0 && a < b) {
+      v = dsm[(a - c.s0) * 4 + k];
+      for (int s = a + 1; s < b; ++s) v += dsm[(s - c.s0) * 4 + k];
+    }
     if (lane == 0) {
       if (c.nc == 1)
         tot[j][k] = v;
@@ -190,29 +267,36 @@ __device__ __forceinline__ void ctl_collect(const Dev& d, const PcgCta& c, int k
 // k_solve.cu: |r| <= eta |b| or maxit iterations.  One extra (control) warp per CTA collects the
 // group totals and takes the per-gel decisions while the slice warps run the SpMV, so neither is
 // on the critical path; run flags are double-buffered (the slice warps read this iteration's,
-// the control warp writes the next one's).
-__global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase, PcgPlan plan, int maxit,
-                                                             int wmax) {
-  extern __shared__ double dyn[];
+// the control warp writes the next one's).  SPLIT = 2: each slice has an owner warp (its rows'
+// vectors, the update) and a helper warp; the two take alternate blocks of every SpMV and the
+// helper hands its partial products over in shared memory.
+template <int SPLIT>
+__global__ void __launch_bounds__(SPLIT == 2 ? 32 * RES_SPLIT_W : 32 * RES_MAXW, 1)
+    k_pcg64_res(Dev d, int phase, PcgPlan plan, int maxit, int wmax) {
+  extern __shared__ __align__(16) double dyn[];
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ double rhoj[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[2][PCG_MAXG];
   __shared__ int s_fail, s_any;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nsw = plan.max_slices, ctl = SPLIT * nsw;
+  const bool helper = SPLIT == 2 && wid >= nsw && wid < ctl;
+  const int sw = helper ? wid - nsw : wid;  // the warp's slice in the CTA
   PcgCta c = pcg_cta(d, plan);
   double* dsm;
+  double* hs;
   double* sv;
   int* sc;
-  res_smem<double>(dyn, plan.max_slices, wmax, dsm, sv, sc);
+  res_smem<double>(dyn, nsw, wmax, sw, SPLIT == 2, dsm, hs, sv, sc);
   if (threadIdx.x == 0) s_fail = 0;
   for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
     gact[q] = d.gc[c.g0 + q].phase == phase ? 1 : 0;
     run[0][q] = gact[q];
   }
   __syncthreads();
-  const int s = c.s0 + wid, row = 32 * s + lane;
-  const bool has = s < c.s1;
+  const int s = c.s0 + sw, row = 32 * s + lane;
+  const bool has = s < c.s1;  // owners and helpers of the CTA's slices
+  double* hsw = hs + 96 * sw + lane;  // split: the helper's partial products of the lane's row
   const int j = has ? plan.slice_gel[s] - c.g0 : 0;
   const bool mine = has && gact[j];
   const bool fixed = mine && d.fixed[row];
@@ -228,25 +312,37 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   // one); the linear Newton contraction makes it a good start, and the A-norm error cannot grow
   double xp0 = 0.0, xp1 = 0.0, xp2 = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (mine) {
-    w = res_load<double>(d, s, d.vals, sv, sc, lane);
-    for (int e = 0; e < 9; ++e) M[e] = d.Minv[9 * row + e];
-    const double4_32a gr = d.grad[row];
-    r0 = -gr.x; r1 = -gr.y; r2 = -gr.z;
-    if (!fixed) {
-      const double4_32a pv = d.p[row];
-      xp0 = pv.x; xp1 = pv.y; xp2 = pv.z;
-      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.p, a0, a1, a2);
+    w = res_load<double>(d, s, d.vals, sv, sc, lane + (helper ? 32 : 0), 32 * SPLIT);
+    if (!helper) {
+      for (int e = 0; e < 9; ++e) M[e] = d.Minv[9 * row + e];
+      const double4_32a gr = d.grad[row];
+      r0 = -gr.x; r1 = -gr.y; r2 = -gr.z;
+      if (!fixed) {
+        const double4_32a pv = d.p[row];
+        xp0 = pv.x; xp1 = pv.y; xp2 = pv.z;
+      }
     }
   }
-  if (has) {
-    const double bp = warp_sum(fma(r2, xp2, fma(r1, xp1, r0 * xp0)));
-    const double pw = warp_sum(fma(a2, xp2, fma(a1, xp1, a0 * xp0)));
-    const double bb = warp_sum(fma(r2, r2, fma(r1, r1, r0 * r0)));
-    if (lane == 0) {
-      dsm[4 * wid + 0] = bp;
-      dsm[4 * wid + 1] = pw;
-      dsm[4 * wid + 2] = bb;
+  __syncthreads();  // slice images complete
+  if (mine && !fixed) {
+    if (SPLIT == 2)
+      res_spmv_half(sv, sc, w, helper ? 1 : 0, lane, d.p, a0, a1, a2);
+    else
+      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.p, a0, a1, a2);
+  }
+  if (SPLIT == 2) {
+    if (helper && mine && !fixed) {
+      hsw[0] = a0; hsw[32] = a1; hsw[64] = a2;
     }
+    __syncthreads();
+    if (!helper && mine && !fixed) {
+      a0 += hsw[0]; a1 += hsw[32]; a2 += hsw[64];
+    }
+  }
+  if (has && !helper) {
+    const double v = warp_sum3(fma(r2, xp2, fma(r1, xp1, r0 * xp0)), fma(a2, xp2, fma(a1, xp1, a0 * xp0)),
+                               fma(r2, r2, fma(r1, r1, r0 * r0)), lane);
+    put_sum3(dsm, 4 * sw, v, lane);
   }
   res_post(d, c, dsm, 0, 3, 0, tot);
   if (!group_barrier(c, d, &s_fail)) return;
@@ -264,7 +360,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   __syncthreads();
   // a non-finite entry of the previous direction anywhere in the gel makes its sums non-finite
   // and rho = 0: the solve then starts from zero without touching that direction
-  if (mine) {
+  if (mine && !helper) {
     const double rho = rhoj[j];
     if (rho != 0.0) {
       x0 = rho * xp0; x1 = rho * xp1; x2 = rho * xp2;
@@ -278,10 +374,24 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
   // u complete before the SpMV; every CTA has read the start's sums before any reuses their slots
   if (!group_barrier(c, d, &s_fail)) return;
   // ---- w = A u, m = M^-1 w; dot products of iteration 0
-  if (has) {
+  if (mine) {
+    if (SPLIT == 2)
+      res_spmv_half(sv, sc, w, helper ? 1 : 0, lane, d.u, w0, w1, w2);
+    else
+      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.u, w0, w1, w2);
+  }
+  if (SPLIT == 2) {
+    if (helper && mine) {
+      hsw[0] = w0; hsw[32] = w1; hsw[64] = w2;
+    }
+    __syncthreads();
+    if (!helper && mine) {
+      w0 += hsw[0]; w1 += hsw[32]; w2 += hsw[64];
+    }
+  }
+  if (has && !helper) {
     double ga = 0.0, de = 0.0, rr = 0.0;
     if (mine) {
-      res_spmv<double, double4_32a, double>(sv, sc, w, lane, d.u, w0, w1, w2);
       if (fixed) w0 = w1 = w2 = 0.0;
       m0 = fma(M[2], w2, fma(M[1], w1, M[0] * w0));
       m1 = fma(M[5], w2, fma(M[4], w1, M[3] * w0));
@@ -291,14 +401,7 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
       de = fma(w2, u2, fma(w1, u1, w0 * u0));
       rr = fma(r2, r2, fma(r1, r1, r0 * r0));
     }
-    ga = warp_sum(ga);
-    de = warp_sum(de);
-    rr = warp_sum(rr);
-    if (lane == 0) {
-      dsm[4 * wid + 0] = ga;
-      dsm[4 * wid + 1] = de;
-      dsm[4 * wid + 2] = rr;
-    }
+    put_sum3(dsm, 4 * sw, warp_sum3(ga, de, rr, lane), lane);
   }
   res_post(d, c, dsm, 0, 3, 0, tot);
   if (!group_barrier(c, d, &s_fail)) return;
@@ -333,14 +436,24 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
       any = __any_sync(0xffffffffu, any);
       if (lane == 0) s_any = any;
     } else if (has && run[par][j]) {
-      res_spmv<double, double4_32a, double>(sv, sc, w, lane, mbuf[par], n0, n1, n2);
-      if (fixed) n0 = n1 = n2 = 0.0;
+      if (SPLIT == 2) {
+        res_spmv_half(sv, sc, w, helper ? 1 : 0, lane, mbuf[par], n0, n1, n2);
+        if (helper) {
+          hsw[0] = n0; hsw[32] = n1; hsw[64] = n2;
+        }
+      } else {
+        res_spmv<double, double4_32a, double>(sv, sc, w, lane, mbuf[par], n0, n1, n2);
+      }
     }
     __syncthreads();
     if (!s_any) break;
-    if (has) {
+    if (has && !helper) {
       double ga = 0.0, de = 0.0, rr = 0.0;
-      if (run[par ^ 1][j]) {
+      if (run[par ^ 1][j]) {  // implies run[par][j]: this iteration's SpMV ran
+        if (SPLIT == 2) {
+          n0 += hsw[0]; n1 += hsw[32]; n2 += hsw[64];
+        }
+        if (fixed) n0 = n1 = n2 = 0.0;
         const double be = bej[j], al = alj[j];
         z0 = fma(be, z0, n0); z1 = fma(be, z1, n1); z2 = fma(be, z2, n2);
         q0 = fma(be, q0, m0); q1 = fma(be, q1, m1); q2 = fma(be, q2, m2);
@@ -358,25 +471,18 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg64_res(Dev d, int phase
         de = fma(w2, u2, fma(w1, u1, w0 * u0));
         rr = fma(r2, r2, fma(r1, r1, r0 * r0));
       }
-      ga = warp_sum(ga);
-      de = warp_sum(de);
-      rr = warp_sum(rr);
-      if (lane == 0) {
-        dsm[4 * wid + 0] = ga;
-        dsm[4 * wid + 1] = de;
-        dsm[4 * wid + 2] = rr;
-      }
+      put_sum3(dsm, 4 * sw, warp_sum3(ga, de, rr, lane), lane);
     }
     res_post(d, c, dsm, 0, 3, par ^ 1, tot);
     if (!group_barrier(c, d, &s_fail)) return;
   }
-  if (mine) d.p[row] = make_double4_32a(x0, x1, x2, 0.0);
+  if (mine && !helper) d.p[row] = make_double4_32a(x0, x1, x2, 0.0);
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
 __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int phase, PcgPlan plan,
                                                                  int maxit, int refine_max, int wmax) {
-  extern __shared__ double dyn[];
+  extern __shared__ __align__(16) double dyn[];
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], rhoj[PCG_MAXG];
   __shared__ float alj[PCG_MAXG], bej[PCG_MAXG], gprf[PCG_MAXG], aprf[PCG_MAXG];
@@ -385,9 +491,10 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ctl = plan.max_slices;
   PcgCta c = pcg_cta(d, plan);
   double* dsm;
+  double* hs;
   float* sv;
   int* sc;
-  res_smem<float>(dyn, plan.max_slices, wmax, dsm, sv, sc);
+  res_smem<float>(dyn, plan.max_slices, wmax, wid, false, dsm, hs, sv, sc);
   if (threadIdx.x == 0) s_fail = 0;
   for (int q = threadIdx.x; q < c.ng; q += blockDim.x) {
     gact[q] = d.gc[c.g0 + q].phase == phase ? 1 : 0;
@@ -409,7 +516,8 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
   // Newton direction (FP64 arithmetic on the FP32 matrix, as the residual refinement)
   double xp0 = 0.0, xp1 = 0.0, xp2 = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (mine) {
-    w = res_load<float>(d, s, d.vals32, sv, sc, lane);
+    w = res_load<float>(d, s, d.vals32, sv, sc, lane, 32);
+    __syncwarp();
     for (int e = 0; e < 9; ++e) M[e] = d.Minv32[9 * row + e];
     const double4_32a gr = d.grad[row];
     g0 = gr.x; g1 = gr.y; g2 = gr.z;
@@ -623,24 +731,36 @@ __global__ void __launch_bounds__(32 * RES_MAXW, 1) k_pcg_mixed_res(Dev d, int p
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
 }
 
+// the FP64 kernel takes two warps per slice while a CTA holds at most RES_SPLIT_MAXS slices
+static bool res_split(bool mixed, int max_slices) { return !mixed && max_slices <= RES_SPLIT_MAXS; }
+
+static const void* res_kernel(bool mixed, int max_slices) {
+  if (mixed) return (const void*)k_pcg_mixed_res;
+  return res_split(false, max_slices) ? (const void*)k_pcg64_res<2> : (const void*)k_pcg64_res<1>;
+}
+
+static int res_threads(bool mixed, int max_slices) {
+  return 32 * ((res_split(mixed, max_slices) ? 2 : 1) * max_slices + 1);
+}
+
 // dynamic shared memory of the resident kernels
 size_t pcg_res_smem(bool mixed, int max_slices, int wmax) {
   const size_t nw = (size_t)max_slices;
-  return sizeof(double) * 4 * max_slices + nw * wmax * 288 * (mixed ? sizeof(float) : sizeof(double)) +
-         nw * wmax * 32 * sizeof(int);
+  return sizeof(double) * (4 + (res_split(mixed, max_slices) ? 96 : 0)) * nw +
+         nw * wmax * 288 * (mixed ? sizeof(float) : sizeof(double)) + nw * wmax * 32 * sizeof(int);
 }
 
 // co-resident CTAs per SM of the resident kernel (0 if it cannot be launched so)
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax) {
   if (max_slices + 1 > RES_MAXW) return 0;
   const size_t smem = pcg_res_smem(mixed, max_slices, wmax);
-  const void* fn = mixed ? (const void*)k_pcg_mixed_res : (const void*)k_pcg64_res;
+  const void* fn = res_kernel(mixed, max_slices);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * (max_slices + 1), smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, res_threads(mixed, max_slices), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -659,8 +779,8 @@ cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nct
                                        smem, st);
   }
   void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&wmax};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg64_res, dim3(nctas), dim3(32 * (plan.max_slices + 1)), args, smem,
-                                     st);
+  return cudaLaunchCooperativeKernel(res_kernel(false, plan.max_slices), dim3(nctas),
+                                     dim3(res_threads(false, plan.max_slices)), args, smem, st);
 }
 
 }  // namespace txg
