@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--features", action="store_true",
+                    help="mini: also time friction, the attachment-driven step and the surface readout")
     ap.add_argument("--reference-budget", type=float, default=200.0, help="seconds of timed oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
@@ -563,12 +565,92 @@ def main():
             line["batched_mixed"] = batched_mixed(args)
         except Exception as e:  # noqa: BLE001
             line["batched_mixed"] = {"error": f"{type(e).__name__}: {e}"}
+    if world == 1 and args.workload == "mini" and args.features:
+        try:
+            line["features"] = features_companion(args)
+        except Exception as e:  # noqa: BLE001
+            line["features"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args)
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
     print(json.dumps(line))
+
+
+def features_companion(args):
+    """Companion measurement of the further couplings on the GelSight-Mini gel (41x51x9, the
+    benchmark's trajectory, FP64): the same step window (warm-up steps untimed, then CUDA-event
+    timed steps with L2 flushed before each) for the plain step, with IPC lagged friction
+    (mu 0.5, eps_v 1e-3 m/s), and attachment-driven (the case carries the bottom face 2 um per
+    step along x while the indenter presses); and the gel-surface readout through the C ABI (a
+    9 x 7 marker grid and a 320 x 240 height map of the top surface, host arrays returned) after
+    every timed plain step, timed on the host clock around each call."""
+    import torch
+    from paper_2411_04776_gb300 import binding as B
+    from paper_2411_04776_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    wl = W.mini_gel(args.seed)
+    K, Wm = args.steps, args.warmup
+    X = wl.gel.verts
+    lo, hi = X.min(axis=0), X.max(axis=0)
+    gx, gy = np.meshgrid(np.linspace(lo[0], hi[0], 9)[1:-1], np.linspace(lo[1], hi[1], 11)[1:-1], indexing="ij")
+    markers = np.column_stack([gx.ravel(), gy.ravel()])  # 7 x 9 = 63 rest points inside the top face
+    nx, ny = 320, 240
+    grid = dict(nx=nx, ny=ny, x0=float(lo[0]), y0=float(lo[1]), dx=float(hi[0] - lo[0]) / nx,
+                dy=float(hi[1] - lo[1]) / ny)
+
+    def case(s):
+        return W.pose((2e-6 * (s + 1), 0.0, 0.0))
+
+    def run(kind):
+        kw = dict(friction=0.5, friction_eps_v=1e-3) if kind == "friction" else {}
+        gel = B.Gel.from_workload(wl, stream=stream, **kw)
+
+        def step(s):
+            if kind == "attached":
+                return gel.step_attached(wl.poses[s], case(s), wl.dt)
+            return gel.step(wl.poses[s], wl.dt)
+        for s in range(Wm):
+            assert step(s) == 0, (kind, s)
+        ms, newton, pcg, rd_m, rd_h = [], 0, 0, [], []
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step(Wm + i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert st == 0, (kind, Wm + i, st)
+            ms.append(e0.elapsed_time(e1))
+            stt = gel.stats()
+            newton += stt["newton_iters"]
+            pcg += stt["pcg_iters"]
+            if kind == "plain":
+                t0 = time.perf_counter()
+                _, found = gel.markers(markers)
+                t1 = time.perf_counter()
+                hm = gel.height_map(**grid)
+                t2 = time.perf_counter()
+                assert found.all() and np.isfinite(hm).mean() > 0.9
+                rd_m.append(t1 - t0)
+                rd_h.append(t2 - t1)
+        fc = np.array(gel.stats()["contact_force"])
+        gel.close()
+        ms = np.array(ms)
+        out = {"value": K / (ms.sum() / 1e3), "unit": "steps/s", "p50_ms": float(np.percentile(ms, 50)),
+               "newton_iters_per_step": newton / K, "pcg_iters_per_step": pcg / K,
+               "final_contact_force_N": fc.tolist()}
+        if kind == "plain":
+            out["readout"] = {"markers": len(markers), "markers_us_per_call": 1e6 * float(np.median(rd_m)),
+                              "height_map_px": nx * ny, "height_map_us_per_call": 1e6 * float(np.median(rd_h)),
+                              "timing": "host clock around the C-ABI call (device work, copy to host)"}
+        return out
+    res = {"workload": NAMES["mini"], "steps": K, "warmup": Wm, "precision": "fp64"}
+    for kind in ("plain", "friction", "attached"):
+        res[kind] = run(kind)
+    return res
 
 
 def plain_fp64_sequential(wls, steps, warmup):

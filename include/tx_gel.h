@@ -247,7 +247,8 @@ tx_status tx_batch_reset(tx_batch* b, int32_t gel);
  * Markers: n markers at rest points rest_xy (n x 2, [m]) of the top surface; each lies in a top
  * triangle of the rest mesh (the first in the surface order whose xy barycentric coordinates are
  * all >= -1e-12) and is carried by them to the current positions: out (n x 3); found[i] = 0 (and
- * out zero) for a point off the top surface. */
+ * out zero) for a point off the top surface.  n times the gel's top triangles must not exceed
+ * 2^38 (TX_ERR_ARG). */
 tx_status tx_gel_markers(tx_gel* g, int32_t n, const double* rest_xy, double* out, int32_t* found);
 tx_status tx_batch_markers(tx_batch* b, int32_t gel, int32_t n, const double* rest_xy, double* out, int32_t* found);
 

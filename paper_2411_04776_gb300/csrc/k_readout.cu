@@ -5,7 +5,9 @@
 // points up (+z).  Both readouts work on the current positions x of one gel:
 //   * markers: a marker placed at a rest point (mx, my) of the top surface lies in a top triangle
 //     of the rest mesh (its xy barycentric coordinates l, all >= -1e-12; the first such triangle
-//     in the top list); it is carried to sum_k l_k x_k;
+//     in the top list); it is carried to sum_k l_k x_k.  The search runs one thread per (marker,
+//     top triangle) pair and keeps the smallest containing index with atomicMin; a thread per
+//     marker then evaluates the position;
 //   * height map: pixel (i, j) at (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy) reads the largest z of
 //     the deformed top triangles that cover it in the xy projection (barycentric coordinates
 //     >= -1e-12), NaN where none does -- the top surface seen from above, rasterised by CUDA
@@ -30,24 +32,33 @@ __device__ __forceinline__ bool bary_xy(const double4_32a a, const double4_32a b
   return l[0] >= -1e-12 && l[1] >= -1e-12 && l[2] >= -1e-12;
 }
 
-__global__ void k_markers(Dev d, int g, int n, const double* rest_xy, double* out, int* found) {
+// tri[i]: smallest index (within the gel's top list) of a top triangle containing marker i, or
+// left at its initial value (INT_MAX: none)
+__global__ void k_marker_find(Dev d, int g, int n, int ntop, const double* rest_xy, int* tri) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)n * (size_t)ntop) return;
+  const int i = (int)(q / (size_t)ntop), k = (int)(q % (size_t)ntop);
+  const int4 t = d.top[d.gi[g].top0 + k];
+  double l[3];
+  if (bary_xy(d.X[t.x], d.X[t.y], d.X[t.z], rest_xy[2 * i], rest_xy[2 * i + 1], l)) atomicMin(tri + i, k);
+}
+
+__global__ void k_markers(Dev d, int g, int n, const double* rest_xy, const int* tri, double* out, int* found) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const GelInfo& G = d.gi[g];
-  const double mx = rest_xy[2 * i], my = rest_xy[2 * i + 1];
+  const int k = tri[i];
   found[i] = 0;
   out[3 * i] = out[3 * i + 1] = out[3 * i + 2] = 0.0;
-  for (int k = G.top0; k < G.top0 + G.ntop; ++k) {
-    const int4 t = d.top[k];
-    double l[3];
-    if (!bary_xy(d.X[t.x], d.X[t.y], d.X[t.z], mx, my, l)) continue;
-    const double4_32a a = d.x[t.x], b = d.x[t.y], c = d.x[t.z];
-    out[3 * i] = l[0] * a.x + l[1] * b.x + l[2] * c.x;
-    out[3 * i + 1] = l[0] * a.y + l[1] * b.y + l[2] * c.y;
-    out[3 * i + 2] = l[0] * a.z + l[1] * b.z + l[2] * c.z;
-    found[i] = 1;
-    return;
-  }
+  if (k < 0 || k >= G.ntop) return;
+  const int4 t = d.top[G.top0 + k];
+  double l[3];
+  bary_xy(d.X[t.x], d.X[t.y], d.X[t.z], rest_xy[2 * i], rest_xy[2 * i + 1], l);
+  const double4_32a a = d.x[t.x], b = d.x[t.y], c = d.x[t.z];
+  out[3 * i] = l[0] * a.x + l[1] * b.x + l[2] * c.x;
+  out[3 * i + 1] = l[0] * a.y + l[1] * b.y + l[2] * c.y;
+  out[3 * i + 2] = l[0] * a.z + l[1] * b.z + l[2] * c.z;
+  found[i] = 1;
 }
 
 // order-preserving map of doubles to unsigned 64-bit (0 is below every encoded value: "none")
@@ -91,9 +102,17 @@ __global__ void k_decode_heights(int n, const unsigned long long* img, double* o
   out[p] = k == 0ull ? CUDART_NAN : z_of_key(k);
 }
 
-void launch_markers(const Dev& d, int g, int n, const double* rest_xy, double* out, int* found, cudaStream_t st) {
+// tri: n ints of device scratch; ntop: the gel's top triangles
+void launch_markers(const Dev& d, int g, int n, int ntop, const double* rest_xy, int* tri, double* out, int* found,
+                    cudaStream_t st) {
   if (n <= 0) return;
-  k_markers<<<nblk_r(n, 128), 128, 0, st>>>(d, g, n, rest_xy, out, found);
+  cudaMemsetAsync(tri, 0x7f, sizeof(int) * (size_t)n, st);  // 0x7f7f7f7f: no triangle yet
+  const size_t pairs = (size_t)n * (size_t)ntop;
+  if (pairs > 0) {
+    k_marker_find<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(d, g, n, ntop, rest_xy, tri);
+    count_launch(1);
+  }
+  k_markers<<<nblk_r(n, 128), 128, 0, st>>>(d, g, n, rest_xy, tri, out, found);
   count_launch(1);
 }
 

@@ -45,7 +45,8 @@ void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
 void launch_min_dist(const Dev& d, int phase, cudaStream_t st);
 void launch_fric_setup(const Dev& d, int phase, cudaStream_t st);
-void launch_markers(const Dev& d, int g, int n, const double* rest_xy, double* out, int* found, cudaStream_t st);
+void launch_markers(const Dev& d, int g, int n, int ntop, const double* rest_xy, int* tri, double* out, int* found,
+                    cudaStream_t st);
 void launch_height_map(const Dev& d, int g, int ntop, int nx, int ny, double x0, double y0, double dx, double dy,
                        unsigned long long* img, double* out, cudaStream_t st);
 void launch_fric(const Dev& d, int phase, int mode, bool mixed, cudaStream_t st);
@@ -2327,13 +2328,15 @@ tx_status tx_batch_markers(tx_batch* b, int32_t gel, int32_t n, const double* re
   if (b->run[gel].in_request) return TX_ERR_ARG;
   if (n == 0) return TX_OK;
   const size_t nb = (size_t)n;
-  unsigned char* p = static_cast<unsigned char*>(readout_scratch(b, nb * (2 + 3) * sizeof(double) + nb * sizeof(int)));
+  if (nb * (size_t)b->gi[gel].ntop > ((size_t)1 << 38)) return TX_ERR_ARG;  // (marker, triangle) pairs of the search
+  unsigned char* p = static_cast<unsigned char*>(readout_scratch(b, nb * (2 + 3) * sizeof(double) + 2 * nb * sizeof(int)));
   if (!p) return TX_ERR_OOM;
   double* dxy = reinterpret_cast<double*>(p);
   double* dout = dxy + 2 * nb;
   int* dfound = reinterpret_cast<int*>(dout + 3 * nb);
+  int* dtri = dfound + nb;
   CK(cudaMemcpyAsync(dxy, rest_xy, sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, b->st));
-  launch_markers(b->d, gel, n, dxy, dout, dfound, b->st);
+  launch_markers(b->d, gel, n, b->gi[gel].ntop, dxy, dtri, dout, dfound, b->st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, dout, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, b->st));
   CK(cudaMemcpyAsync(found, dfound, sizeof(int) * nb, cudaMemcpyDeviceToHost, b->st));
