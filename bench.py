@@ -341,7 +341,7 @@ def roofline(prof, clocks, precision, kernel, fma=None):
 def pcg_kernel_name(precision, n_gels):
     if n_gels == 1:
         return "k_pcg64_res" if precision == "fp64" else "k_pcg_mixed_res"
-    return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
+    return "k_pcg64_pool" if precision == "fp64" else "k_pcg_mixed_pool"
 
 
 def source_hash(files):

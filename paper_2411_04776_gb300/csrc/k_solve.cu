@@ -4,10 +4,12 @@
 //   * gather: every 3x3 block of the sliced BSR sums its per-tet contributions in a fixed order
 //     (plus M/h^2 on the diagonal); diagonal blocks also gather the gradient
 //     g = M (x - xt) / h^2 + sum_t V_t P_t D_a.  Dirichlet rows get g = 0.
-//   * PCG: one persistent cooperative kernel per Newton iteration runs every PCG iteration of
-//     every gel of the batch (Chronopoulos-Gear single-reduction CG: two grid barriers per
-//     iteration; dot products as per-slice partials summed per gel in a fixed order by every CTA
-//     that needs them, so all CTAs take identical decisions and results are reproducible).
+//   * PCG (batches too large for the resident kernels of k_pcg_res.cu): one persistent cooperative
+//     kernel per Newton iteration runs every PCG iteration of every gel of the batch
+//     (Chronopoulos-Gear single-reduction CG) over a pool of one CTA per SM that splits the slices
+//     of the gels still iterating evenly at every phase; dot products are per-slice partials that
+//     each gel's owner warp adds in a fixed order, so results are reproducible and a gel's sums do
+//     not depend on the other gels.
 //   * energy: E(x + alpha p) per gel = inertia + elastic + barrier, as per-piece partial sums
 //     (pieces never straddle gels) reduced per gel in a fixed order; the reduction kernel also
 //     takes the line-search decision (accept on E <= E_cur, else halve alpha).
@@ -221,75 +223,211 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   count_launch(1);
 }
 
-// One projected-Newton direction per gel of the gels in `phase`: block-Jacobi preconditioned CG
-// on H p = -g (Chronopoulos-Gear: one reduction phase per iteration), FP64, stops per gel when
-// |r| <= eta |g| or after maxit iterations.
-__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, int maxit) {
-  extern __shared__ double dsm[];  // [slices of this CTA][4]
-  __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
-  __shared__ double rhoj[PCG_MAXG];
-  __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
-  __shared__ int s_fail, s_any;
+// ---------------------------------------------------------------- pooled streaming PCG
+// Every CTA of the launch belongs to one group (the pool).  At each phase the slices of the gels
+// still taking part are split evenly over the CTAs: a prefix sum over the gels' slice counts, the
+// same in every CTA.  So a gel that converges early leaves no SM idle while the others iterate
+// (with a fixed group of CTAs per gel, the whole launch waits for the slowest gel).  Per-slice
+// partial sums go to d.pslice; after a pool barrier the owner warp of each gel (in CTA j mod the
+// grid, so that the owners' work spreads over the SMs) adds its gel's partials in slice order, takes the gel's decisions and
+// publishes them in d.pool, and a second barrier makes them visible to every CTA.  Same
+// arithmetic, scalars and stopping rules as the per-group kernels; the sums are deterministic.
+
+constexpr int POOL_T = 1024;  // one CTA per SM: the pool barrier has one arrival per SM
+constexpr int POOL_W = POOL_T / 32;
+
+__device__ __forceinline__ bool pool_flag(const Dev& d, int g, int mode, int phase) {
+  if (mode == 0) return d.gc[g].phase == phase;
+  return mode == 1 ? d.pool[g].run != 0 : d.pool[g].inner != 0;
+}
+
+// pre[j] (j = 0..ng): slices of the gels g0 .. g0 + j - 1 whose flag `mode` is set (0: in the
+// solve's phase, 1: run, 2: inner); returns pre[ng].  Block-wide, identical in every CTA.
+__device__ int pool_prefix(const Dev& d, const PoolPlan& pl, int mode, int phase, int* pre) {
+  __shared__ int wtot[POOL_W];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  PcgCta c = pcg_cta(d, plan);
-  if (threadIdx.x == 0) s_fail = 0;
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
-    run[j] = gact[j];
+  const int per = (pl.ng + POOL_T - 1) / POOL_T, j0 = min((int)threadIdx.x * per, pl.ng), j1 = min(j0 + per, pl.ng);
+  int loc = 0;
+  for (int j = j0; j < j1; ++j) {
+    pre[j] = pool_flag(d, pl.g0 + j, mode, phase) ? d.gi[pl.g0 + j].ns : 0;
+    loc += pre[j];
+  }
+  int inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wtot[wid] = inc;
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < POOL_W; ++w) {
+    if (w < wid) base += wtot[w];
+    total += wtot[w];
+  }
+  int ex = base + inc - loc;
+  for (int j = j0; j < j1; ++j) {
+    const int n = pre[j];
+    pre[j] = ex;
+    ex += n;
+  }
+  if (threadIdx.x == 0) pre[pl.ng] = total;
+  __syncthreads();
+  return total;
+}
+
+// the CTA's share [a0, a1) of the S active slices
+__device__ __forceinline__ void pool_share(int S, int& a0, int& a1) {
+  a0 = (int)((long long)blockIdx.x * S / gridDim.x);
+  a1 = (int)((long long)(blockIdx.x + 1) * S / gridDim.x);
+}
+
+// gel index j (relative to g0) of active slice a: pre[j] <= a < pre[j + 1]
+__device__ __forceinline__ int pool_gel_at(const int* pre, int ng, int a) {
+  int lo = 0, hi = ng;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= a)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// The CTA's share of the S active slices as a list in shared memory: lst[i] = (slice, gel) for
+// the i-th of them (all threads, one entry each); returns its length.  cap: the list's room.
+__device__ int pool_list(const Dev& d, const PoolPlan& pl, const int* pre, int S, int2* lst, int cap) {
+  int a0, a1;
+  pool_share(S, a0, a1);
+  const int n = min(a1 - a0, cap);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int a = a0 + i, j = pool_gel_at(pre, pl.ng, a), g = pl.g0 + j;
+    lst[i] = make_int2(d.gi[g].s0 + (a - pre[j]), g);
   }
   __syncthreads();
-  // ---- Galerkin start: x0 = rho p_prev, the minimiser of the quadratic model along the gel's
-  // previous Newton direction (in d.p; rho = b.p_prev / p_prev.A p_prev, 0 without a usable one);
-  // a = A p_prev goes to d.w.  Partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3).
-  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    double bp = 0.0, pw = 0.0, bb = 0.0;
-    if (gact[plan.slice_gel[s] - c.g0]) {
-      const int r = 32 * s + lane;
-      const double4_32a gr = d.grad[r];
-      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-      const bool fx = d.fixed[r] != 0;
-      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
-      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row64(d, s, lane, d.p);
-      d.w[r] = a;
-      bp = dot4(b, pv);
-      pw = dot4(pv, a);
-      bb = dot4(b, b);
-    }
-    bp = warp_sum(bp);
-    pw = warp_sum(pw);
-    bb = warp_sum(bb);
+  return n;
+}
+
+// the owner warp's sums of partials k in [k0, k1) over gel g's slices, in slice order per lane
+// and a fixed warp tree (every lane gets them)
+__device__ __forceinline__ void pool_total(const Dev& d, int g, int k0, int k1, double* t) {
+  const int lane = threadIdx.x & 31;
+  const GelInfo& G = d.gi[g];
+  for (int k = k0; k < k1; ++k) {
+    double v = 0.0;
+    for (int s = G.s0 + lane; s < G.s0 + G.ns; s += 32) v += d.pslice[4 * (size_t)s + k];
+    t[k] = warp_sum(v);
+  }
+}
+
+__device__ __forceinline__ PcgCta pool_cta(const Dev& d, const PoolPlan& pl) {
+  PcgCta c;
+  c.s0 = c.s1 = 0;
+  c.c0 = 0;
+  c.nc = gridDim.x;
+  c.g0 = pl.g0;
+  c.ng = pl.ng;
+  c.bar = d.bar;
+  c.epoch = 0;
+  return c;
+}
+
+// g . p and ||p||_inf of the new direction per gel of the solve (the line search's model slope)
+__device__ bool pool_epilogue(const Dev& d, const PoolPlan& pl, PcgCta& c, int phase, int* pre, int2* lst,
+                              int* s_fail) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = wid * gridDim.x + blockIdx.x, nw = gridDim.x * POOL_W;  // owners spread over the CTAs first
+  const int nl = pool_list(d, pl, pre, pool_prefix(d, pl, 0, phase, pre), lst, pl.cap);
+  for (int i = wid; i < nl; i += POOL_W) {
+    const int s = lst[i].x, g = lst[i].y;
+    const double4_32a x = d.p[32 * s + lane];
+    double gp = dot4(d.grad[32 * s + lane], x);
+    double m = fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z)));
+    gp = warp_sum(gp);
+    m = warp_max(m);
     if (lane == 0) {
-      dsm[(s - c.s0) * 4 + 0] = bp;
-      dsm[(s - c.s0) * 4 + 1] = pw;
-      dsm[(s - c.s0) * 4 + 2] = 0.0;
-      dsm[(s - c.s0) * 4 + 3] = bb;
+      d.pslice[4 * (size_t)s + 3] = gp;
+      atomic_max_pos(&d.gv[g].pnorm_bits, m);
     }
   }
-  // (the group sum's barrier also ends every CTA's SpMV on d.p before d.p is overwritten below)
-  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-    bbj[j] = tot[j][3];
-    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
-    const double pw = tot[j][1], rho = tot[j][0] / pw;
-    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;  // a non-finite p_prev anywhere gives 0
+  if (!group_barrier(c, d, s_fail)) return false;
+  for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+    const int g = pl.g0 + j;
+    if (d.gc[g].phase != phase) continue;
+    double t[4];
+    pool_total(d, g, 3, 4, t);
+    if (lane == 0) d.gv[g].gtp = t[3];
   }
-  __syncthreads();
-  // ---- x = rho p_prev, r = b - rho a, u = M^-1 r, pp = s = 0
-  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    const int j = plan.slice_gel[s] - c.g0;
-    if (!gact[j]) continue;
-    const int r = 32 * s + lane;
+  return true;
+}
+
+// FP64 pooled PCG: block-Jacobi preconditioned CG on H p = -g (Chronopoulos-Gear: one reduction
+// phase per iteration), started from x0 = rho p_prev, the minimiser of the quadratic model along
+// the gel's previous Newton direction; stops per gel when |r| <= eta |g| or after maxit iterations
+__global__ void __launch_bounds__(POOL_T, 1) k_pcg64_pool(Dev d, int phase, PoolPlan pl, int maxit) {
+  extern __shared__ int pre[];  // ng + 1, then the CTA's slice list
+  int2* lst = reinterpret_cast<int2*>(pre + ((pl.ng + 2) & ~1));
+  __shared__ int s_fail;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = wid * gridDim.x + blockIdx.x, nw = gridDim.x * POOL_W;  // owners spread over the CTAs first
+  PcgCta c = pool_cta(d, pl);
+  if (threadIdx.x == 0) s_fail = 0;
+  // ---- Galerkin start: a = A p_prev into d.w; partials b.p_prev (0), p_prev.a (1),
+  // |b|^2 (3)
+  int S = pool_prefix(d, pl, 0, phase, pre);
+  int nl = pool_list(d, pl, pre, S, lst, pl.cap);
+  for (int i = wid; i < nl; i += POOL_W) {
+    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    const bool fx = d.fixed[r] != 0;
+    const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+    const double4_32a av = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row64(d, s, lane, d.p);
+    d.w[r] = av;
+    const double bp = warp_sum(dot4(b, pv)), pw = warp_sum(dot4(pv, av)), bb = warp_sum(dot4(b, b));
+    if (lane == 0) {
+      d.pslice[4 * (size_t)s + 0] = bp;
+      d.pslice[4 * (size_t)s + 1] = pw;
+      d.pslice[4 * (size_t)s + 3] = bb;
+    }
+  }
+  if (!group_barrier(c, d, &s_fail)) return;  // also ends every SpMV on d.p before it is overwritten
+  for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+    const int g = pl.g0 + j;
+    PoolGel& P = d.pool[g];
+    if (d.gc[g].phase != phase) {
+      if (lane == 0) P.act = P.run = P.inner = 0;
+      continue;
+    }
+    double t[4];
+    pool_total(d, g, 0, 2, t);
+    pool_total(d, g, 3, 4, t);
+    if (lane == 0) {
+      P.act = P.run = 1;
+      P.inner = 0;
+      P.it = 0;
+      P.bb = t[3];
+      P.th = d.gv[g].eta2 * t[3];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+      const double rho = t[0] / t[1];
+      P.rho = (t[1] > 0.0 && isfinite(rho)) ? rho : 0.0;  // a non-finite p_prev anywhere gives 0
+    }
+  }
+  if (!group_barrier(c, d, &s_fail)) return;
+  // ---- x = rho p_prev, r = b - rho a, u = M^-1 r, pp = s = 0 (same share as above)
+  for (int i = wid; i < nl; i += POOL_W) {
+    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
     const double4_32a gr = d.grad[r];
     double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
     double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    const double rho = rhoj[j];
+    const double rho = d.pool[g].rho;
     if (rho != 0.0 && !d.fixed[r]) {
-      const double4_32a pv = d.p[r], a = d.w[r];
+      const double4_32a pv = d.p[r], av = d.w[r];
       x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
-      b.x = fma(-rho, a.x, b.x);
-      b.y = fma(-rho, a.y, b.y);
-      b.z = fma(-rho, a.z, b.z);
+      b.x = fma(-rho, av.x, b.x);
+      b.y = fma(-rho, av.y, b.y);
+      b.z = fma(-rho, av.z, b.z);
     }
     const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     d.r[r] = b;
@@ -299,62 +437,57 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     d.u[r] = mul3(d.Minv + 9 * r, b);
   }
   if (!group_barrier(c, d, &s_fail)) return;  // u complete before the SpMV
+  S = pool_prefix(d, pl, 1, phase, pre);
+  nl = pool_list(d, pl, pre, S, lst, pl.cap);
   for (int k = 1;; ++k) {
     // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
-    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-      double ga = 0.0, de = 0.0, rr = 0.0;
-      if (run[plan.slice_gel[s] - c.g0]) {
-        const int r = 32 * s + lane;
-        double4_32a w = spmv_row64(d, s, lane, d.u);
-        if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-        d.w[r] = w;
-        const double4_32a rv = d.r[r], uv = d.u[r];
-        ga = dot4(rv, uv);
-        de = dot4(w, uv);
-        rr = dot4(rv, rv);
-      }
-      ga = warp_sum(ga);
-      de = warp_sum(de);
-      rr = warp_sum(rr);
+    for (int i = wid; i < nl; i += POOL_W) {
+      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      double4_32a w = spmv_row64(d, s, lane, d.u);
+      if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      d.w[r] = w;
+      const double4_32a rv = d.r[r], uv = d.u[r];
+      const double ga = warp_sum(dot4(rv, uv)), de = warp_sum(dot4(w, uv)), rr = warp_sum(dot4(rv, rv));
       if (lane == 0) {
-        dsm[(s - c.s0) * 4 + 0] = ga;
-        dsm[(s - c.s0) * 4 + 1] = de;
-        dsm[(s - c.s0) * 4 + 2] = rr;
+        d.pslice[4 * (size_t)s + 0] = ga;
+        d.pslice[4 * (size_t)s + 1] = de;
+        d.pslice[4 * (size_t)s + 2] = rr;
       }
     }
-    if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
-    // ---- per-gel scalars and convergence (identical in every CTA of the group)
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-      if (!run[j]) continue;
-      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
-      if (!(rr > thj[j]) || k > maxit) {
-        run[j] = 0;
-        if (blockIdx.x == c.c0) {
-          d.gv[c.g0 + j].pcg_it = k - 1;
-          d.gv[c.g0 + j].bb = bbj[j];
-          d.gv[c.g0 + j].res2 = bbj[j] > 0.0 ? rr / bbj[j] : 0.0;
-          d.gv[c.g0 + j].pcg_done = 1;
+    if (!group_barrier(c, d, &s_fail)) return;
+    // ---- per-gel scalars and convergence, by the gel's owner warp
+    for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+      const int g = pl.g0 + j;
+      PoolGel& P = d.pool[g];
+      if (!P.run) continue;
+      double t[4];
+      pool_total(d, g, 0, 3, t);
+      if (lane == 0) {
+        const double ga = t[0], de = t[1], rr = t[2];
+        if (!(rr > P.th) || k > maxit) {
+          P.run = 0;
+          d.gv[g].pcg_it = k - 1;
+          d.gv[g].bb = P.bb;
+          d.gv[g].res2 = P.bb > 0.0 ? rr / P.bb : 0.0;
+          d.gv[g].pcg_done = 1;
+        } else {
+          const double beta = k == 1 ? 0.0 : ga / P.gprev;
+          const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / P.aprev);
+          P.gprev = ga;
+          P.aprev = alpha;
+          P.al = alpha;
+          P.be = beta;
         }
-        continue;
       }
-      s_any = 1;
-      const double beta = k == 1 ? 0.0 : ga / gprev[j];
-      const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
-      gprev[j] = ga;
-      aprev[j] = alpha;
-      alj[j] = alpha;
-      bej[j] = beta;
     }
-    __syncthreads();
-    if (!s_any) break;
+    if (!group_barrier(c, d, &s_fail)) return;
+    S = pool_prefix(d, pl, 1, phase, pre);
+    nl = pool_list(d, pl, pre, S, lst, pl.cap);
+    if (S == 0) break;
     // ---- vector updates
-    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-      const int j = plan.slice_gel[s] - c.g0;
-      if (!run[j]) continue;
-      const double beta = bej[j], alpha = alj[j];
-      const int r = 32 * s + lane;
+    for (int i = wid; i < nl; i += POOL_W) {
+      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const double beta = d.pool[g].be, alpha = d.pool[g].al;
       const double4_32a u = d.u[r], w = d.w[r];
       double4_32a pp = d.pp[r], sv = d.s[r], x = d.p[r], rv = d.r[r];
       pp.x = fma(beta, pp.x, u.x); pp.y = fma(beta, pp.y, u.y); pp.z = fma(beta, pp.z, u.z);
@@ -369,16 +502,7 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     }
     if (!group_barrier(c, d, &s_fail)) return;
   }
-  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
-}
-
-cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st) {
-  Dev dd = d;
-  PcgPlan pp = plan;
-  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit};
-  count_launch(1);
-  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
-  return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, smem, st);
+  pool_epilogue(d, pl, c, phase, pre, lst, &s_fail);
 }
 
 // ---------------------------------------------------------------- mixed-precision PCG
@@ -434,112 +558,110 @@ __device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lan
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
-__global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPlan plan, int maxit,
-                                                     int refine_max) {
-  extern __shared__ double dsm[];
-  __shared__ double tot[PCG_MAXG][4];
-  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
-  __shared__ double rhoj[PCG_MAXG];
-  __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
-  __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
-  __shared__ int s_fail, s_any;
+// the owner's decision at the start of a refinement round from the gel's FP64 residual rr: the
+// solve ends (rounds done = round) or the round's FP32 inner solve starts with its target
+__device__ __forceinline__ void pool_round_start(const Dev& d, int g, double rr, int round, int refine_max) {
+  PoolGel& P = d.pool[g];
+  P.rr = rr;
+  if (!(rr > P.th) || round >= refine_max) {
+    P.run = 0;
+    P.inner = 0;
+    d.gv[g].res2 = P.bb > 0.0 ? rr / P.bb : 0.0;
+    d.gv[g].pcg_done = 1;
+    d.gv[g].rounds = round;
+    d.gv[g].bb = P.bb;
+    d.gv[g].pcg_it = P.it;
+  } else {
+    P.inner = 1;
+    P.tol = fmax(P.th / rr, 1e-11);  // reach eta |b| in one round if FP32 allows, else the FP32 floor
+  }
+}
+
+// mixed-precision pooled PCG: FP64 residual refinement rounds around an FP32 inner CG (above)
+__global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, PoolPlan pl, int maxit,
+                                                         int refine_max) {
+  extern __shared__ int pre[];  // ng + 1, then the CTA's slice list
+  int2* lst = reinterpret_cast<int2*>(pre + ((pl.ng + 2) & ~1));
+  __shared__ int s_fail;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  PcgCta c = pcg_cta(d, plan);
+  const int gw = wid * gridDim.x + blockIdx.x, nw = gridDim.x * POOL_W;  // owners spread over the CTAs first
+  PcgCta c = pool_cta(d, pl);
   if (threadIdx.x == 0) s_fail = 0;
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
-    run[j] = gact[j];
-    itj[j] = 0;
-  }
-  __syncthreads();
-  // ---- Galerkin start along the previous Newton direction (as in k_pcg64; a = A32 p_prev with
-  // FP64 arithmetic, into d.w): partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3)
-  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    double bp = 0.0, pw = 0.0, bb = 0.0;
-    if (gact[plan.slice_gel[s] - c.g0]) {
-      const int r = 32 * s + lane;
-      const double4_32a gr = d.grad[r];
-      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-      const bool fx = d.fixed[r] != 0;
-      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
-      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row_res(d, s, lane, d.p);
-      d.w[r] = a;
-      bp = dot4(b, pv);
-      pw = dot4(pv, a);
-      bb = dot4(b, b);
-    }
-    bp = warp_sum(bp);
-    pw = warp_sum(pw);
-    bb = warp_sum(bb);
+  // ---- Galerkin start (FP64 arithmetic on the FP32 matrix): a = A32 p_prev into d.w
+  int S = pool_prefix(d, pl, 0, phase, pre);
+  int nl = pool_list(d, pl, pre, S, lst, pl.cap);
+  for (int i = wid; i < nl; i += POOL_W) {
+    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    const bool fx = d.fixed[r] != 0;
+    const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+    const double4_32a av = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row_res(d, s, lane, d.p);
+    d.w[r] = av;
+    const double bp = warp_sum(dot4(b, pv)), pw = warp_sum(dot4(pv, av)), bb = warp_sum(dot4(b, b));
     if (lane == 0) {
-      dsm[(s - c.s0) * 4 + 0] = bp;
-      dsm[(s - c.s0) * 4 + 1] = pw;
-      dsm[(s - c.s0) * 4 + 2] = 0.0;
-      dsm[(s - c.s0) * 4 + 3] = bb;
+      d.pslice[4 * (size_t)s + 0] = bp;
+      d.pslice[4 * (size_t)s + 1] = pw;
+      d.pslice[4 * (size_t)s + 3] = bb;
     }
   }
-  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;  // its barrier ends every SpMV on d.p
-  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-    bbj[j] = tot[j][3];
-    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
-    const double pw = tot[j][1], rho = tot[j][0] / pw;
-    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
-  }
-  __syncthreads();
-  // ---- p = rho p_prev, r64 = b - rho a; partial |r|^2 (k = 2)
-  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-    double rr = 0.0;
-    const int j = plan.slice_gel[s] - c.g0;
-    if (gact[j]) {
-      const int r = 32 * s + lane;
-      const double4_32a gr = d.grad[r];
-      double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
-      double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-      const double rho = rhoj[j];
-      if (rho != 0.0 && !d.fixed[r]) {
-        const double4_32a pv = d.p[r], a = d.w[r];
-        x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
-        b.x = fma(-rho, a.x, b.x);
-        b.y = fma(-rho, a.y, b.y);
-        b.z = fma(-rho, a.z, b.z);
-      }
-      d.r[r] = b;
-      d.p[r] = x;
-      rr = dot4(b, b);
+  if (!group_barrier(c, d, &s_fail)) return;
+  for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+    const int g = pl.g0 + j;
+    PoolGel& P = d.pool[g];
+    if (d.gc[g].phase != phase) {
+      if (lane == 0) P.act = P.run = P.inner = 0;
+      continue;
     }
-    rr = warp_sum(rr);
-    if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
+    double t[4];
+    pool_total(d, g, 0, 2, t);
+    pool_total(d, g, 3, 4, t);
+    if (lane == 0) {
+      P.act = P.run = 1;
+      P.inner = 0;
+      P.it = 0;
+      P.bb = t[3];
+      P.th = d.gv[g].eta2 * t[3];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+      const double rho = t[0] / t[1];
+      P.rho = (t[1] > 0.0 && isfinite(rho)) ? rho : 0.0;
+    }
   }
-  if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
+  if (!group_barrier(c, d, &s_fail)) return;
+  // ---- p = rho p_prev, r64 = b - rho a; partial |r|^2 (2)
+  for (int i = wid; i < nl; i += POOL_W) {
+    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    const double rho = d.pool[g].rho;
+    if (rho != 0.0 && !d.fixed[r]) {
+      const double4_32a pv = d.p[r], av = d.w[r];
+      x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
+      b.x = fma(-rho, av.x, b.x);
+      b.y = fma(-rho, av.y, b.y);
+      b.z = fma(-rho, av.z, b.z);
+    }
+    d.r[r] = b;
+    d.p[r] = x;
+    const double rr = warp_sum(dot4(b, b));
+    if (lane == 0) d.pslice[4 * (size_t)s + 2] = rr;
+  }
+  if (!group_barrier(c, d, &s_fail)) return;
+  for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+    const int g = pl.g0 + j;
+    if (!d.pool[g].run) continue;
+    double t[4];
+    pool_total(d, g, 2, 3, t);
+    if (lane == 0) pool_round_start(d, g, t[2], 0, refine_max);
+  }
+  if (!group_barrier(c, d, &s_fail)) return;
   for (int round = 0;; ++round) {
-    // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-      inner[j] = 0;
-      if (!run[j]) continue;
-      const double rr = tot[j][2], bb = bbj[j];
-      if (!(rr > thj[j]) || round >= refine_max) {
-        run[j] = 0;
-        if (blockIdx.x == c.c0) {
-          d.gv[c.g0 + j].res2 = bb > 0.0 ? rr / bb : 0.0;
-          d.gv[c.g0 + j].pcg_done = 1;
-          d.gv[c.g0 + j].rounds = round;
-          d.gv[c.g0 + j].bb = bb;
-          d.gv[c.g0 + j].pcg_it = itj[j];
-        }
-        continue;
-      }
-      s_any = 1;
-      inner[j] = 1;
-      // inner target: reach eta |b| in one round if FP32 allows, else the FP32 floor
-      tolj[j] = fmax(thj[j] / rr, 1e-11);
-    }
-    __syncthreads();
-    if (!s_any) break;
-    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-      if (!inner[plan.slice_gel[s] - c.g0]) continue;
-      const int r = 32 * s + lane;
+    S = pool_prefix(d, pl, 2, phase, pre);
+    nl = pool_list(d, pl, pre, S, lst, pl.cap);
+    if (S == 0) break;  // no gel starts a round: every solve has ended
+    // ---- inner init: r32 = r64, x32 = pp32 = s32 = 0, u32 = M^-1 r32
+    for (int i = wid; i < nl; i += POOL_W) {
+      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
       const double4_32a rv = d.r[r];
       const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
       d.r32[r] = r32;
@@ -549,56 +671,53 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
     }
     if (!group_barrier(c, d, &s_fail)) return;
-    // ---- inner FP32 CG (Chronopoulos-Gear), same structure as the FP64 kernel
+    // ---- inner FP32 CG (Chronopoulos-Gear)
     for (int k = 1;; ++k) {
-      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-        double ga = 0.0, de = 0.0, rr = 0.0;
-        if (inner[plan.slice_gel[s] - c.g0]) {
-          const int r = 32 * s + lane;
-          float4 w = spmv_row32(d, s, lane, d.u32);
-          if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
-          d.w32[r] = w;
-          const float4 rv = d.r32[r], uv = d.u32[r];
-          // FP32 warp sums: the inner solve's dot products are FP32 quantities (GB300 runs FP64
-          // adds at 1/64 of the FP32 rate); slices and CTAs are then added in FP64
-          ga = warp_sum(dot4f(rv, uv));
-          de = warp_sum(dot4f(w, uv));
-          rr = warp_sum(dot4f(rv, rv));
-        }
+      for (int i = wid; i < nl; i += POOL_W) {
+        const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+        float4 w = spmv_row32(d, s, lane, d.u32);
+        if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.w32[r] = w;
+        const float4 rv = d.r32[r], uv = d.u32[r];
+        // FP32 warp sums (FP32 quantities of the inner solve); the owner adds the slices in FP64
+        const float ga = warp_sum(dot4f(rv, uv)), de = warp_sum(dot4f(w, uv)), rr = warp_sum(dot4f(rv, rv));
         if (lane == 0) {
-          dsm[(s - c.s0) * 4 + 0] = ga;
-          dsm[(s - c.s0) * 4 + 1] = de;
-          dsm[(s - c.s0) * 4 + 2] = rr;
+          d.pslice[4 * (size_t)s + 0] = ga;
+          d.pslice[4 * (size_t)s + 1] = de;
+          d.pslice[4 * (size_t)s + 2] = rr;
         }
       }
-      if (!group_sum<float>(d, c, dsm, 0, 3, tot, &s_fail)) return;
-      if (threadIdx.x == 0) s_any = 0;
-      __syncthreads();
-      for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
-        if (!inner[j]) continue;
-        const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
-        // converged once |r32|^2 <= tol |r32 at the round start|^2 (FP32 accuracy floor 1e-11)
-        if (k == 1) rr0j[j] = rr;
-        if (!(rr > tolj[j] * rr0j[j]) || k > maxit) {
-          inner[j] = 0;
-          itj[j] += k - 1;
-          continue;
+      if (!group_barrier(c, d, &s_fail)) return;
+      for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+        const int g = pl.g0 + j;
+        PoolGel& P = d.pool[g];
+        if (!P.inner) continue;
+        double t[4];
+        pool_total(d, g, 0, 3, t);
+        if (lane == 0) {
+          const double ga = t[0], de = t[1], rr = t[2];
+          // converged once |r32|^2 <= tol |r32 at the round start|^2 (FP32 accuracy floor 1e-11)
+          if (k == 1) P.rr0 = rr;
+          if (!(rr > P.tol * P.rr0) || k > maxit) {
+            P.inner = 0;
+            P.it += k - 1;
+          } else {
+            const double beta = k == 1 ? 0.0 : ga / P.gprev;
+            const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / P.aprev);
+            P.gprev = ga;
+            P.aprev = alpha;
+            P.al = alpha;
+            P.be = beta;
+          }
         }
-        s_any = 1;
-        const double beta = k == 1 ? 0.0 : ga / gprev[j];
-        const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
-        gprev[j] = ga;
-        aprev[j] = alpha;
-        alj[j] = (float)alpha;
-        bej[j] = (float)beta;
       }
-      __syncthreads();
-      if (!s_any) break;
-      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-        const int j = plan.slice_gel[s] - c.g0;
-        if (!inner[j]) continue;
-        const float fb = bej[j], fa = alj[j];
-        const int r = 32 * s + lane;
+      if (!group_barrier(c, d, &s_fail)) return;
+      S = pool_prefix(d, pl, 2, phase, pre);
+      nl = pool_list(d, pl, pre, S, lst, pl.cap);
+      if (S == 0) break;
+      for (int i = wid; i < nl; i += POOL_W) {
+        const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+        const float fb = (float)d.pool[g].be, fa = (float)d.pool[g].al;
         const float4 u = d.u32[r], w = d.w32[r];
         float4 pp = d.pp32[r], sv = d.s32[r], x = d.x32[r], rv = d.r32[r];
         pp.x = fmaf(fb, pp.x, u.x); pp.y = fmaf(fb, pp.y, u.y); pp.z = fmaf(fb, pp.z, u.z);
@@ -613,10 +732,11 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       }
       if (!group_barrier(c, d, &s_fail)) return;
     }
-    // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p
-    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-      if (!run[plan.slice_gel[s] - c.g0]) continue;
-      const int r = 32 * s + lane;
+    // ---- p += x32 (FP64) for the gels still in their rounds
+    S = pool_prefix(d, pl, 1, phase, pre);
+    nl = pool_list(d, pl, pre, S, lst, pl.cap);
+    for (int i = wid; i < nl; i += POOL_W) {
+      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
       const float4 x = d.x32[r];
       double4_32a p = d.p[r];
       p.x += (double)x.x;
@@ -625,41 +745,68 @@ __global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPla
       d.p[r] = p;
     }
     if (!group_barrier(c, d, &s_fail)) return;
-    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
-      double rr = 0.0;
-      if (run[plan.slice_gel[s] - c.g0]) {
-        const int r = 32 * s + lane;
-        double4_32a ap = spmv_row_res(d, s, lane, d.p);
-        const double4_32a gr = d.grad[r];
-        double4_32a rv = make_double4_32a(-gr.x - ap.x, -gr.y - ap.y, -gr.z - ap.z, 0.0);
-        if (d.fixed[r]) rv = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-        d.r[r] = rv;
-        rr = dot4(rv, rv);
-      }
-      rr = warp_sum(rr);
-      if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
+    // ---- the FP64 residual r64 = b - A p; partial |r|^2 (2)
+    for (int i = wid; i < nl; i += POOL_W) {
+      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const double4_32a ap = spmv_row_res(d, s, lane, d.p);
+      const double4_32a gr = d.grad[r];
+      double4_32a rv = make_double4_32a(-gr.x - ap.x, -gr.y - ap.y, -gr.z - ap.z, 0.0);
+      if (d.fixed[r]) rv = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      d.r[r] = rv;
+      const double rr = warp_sum(dot4(rv, rv));
+      if (lane == 0) d.pslice[4 * (size_t)s + 2] = rr;
     }
-    if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
+    if (!group_barrier(c, d, &s_fail)) return;
+    for (int j = gw; j < pl.ng; j += nw) {  // owner: CTA j mod grid, then warp
+      const int g = pl.g0 + j;
+      if (!d.pool[g].run) continue;
+      double t[4];
+      pool_total(d, g, 2, 3, t);
+      if (lane == 0) pool_round_start(d, g, t[2], round + 1, refine_max);
+    }
+    if (!group_barrier(c, d, &s_fail)) return;
   }
-  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
+  pool_epilogue(d, pl, c, phase, pre, lst, &s_fail);
 }
 
-cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
-                             cudaStream_t st) {
+// dynamic shared memory of the pooled kernels: the gel prefix (ng + 1 ints, padded to 8 bytes),
+// then the CTA's slice list (cap entries)
+size_t pcg_pool_smem(const PoolPlan& pl) {
+  return sizeof(int) * (size_t)((pl.ng + 2) & ~1) + sizeof(int2) * (size_t)pl.cap;
+}
+
+cudaError_t launch_pcg_pool(const Dev& d, int phase, const PoolPlan& pl, int nctas, bool mixed, int maxit,
+                            int refine_max, cudaStream_t st) {
   Dev dd = d;
-  PcgPlan pp = plan;
-  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&refine_max};
+  PoolPlan pp = pl;
+  const size_t smem = pcg_pool_smem(pl);
   count_launch(1);
-  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed, dim3(nctas), dim3(PCG_T), args, smem, st);
+  if (mixed) {
+    void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&refine_max};
+    return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed_pool, dim3(nctas), dim3(POOL_T), args, smem, st);
+  }
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg64_pool, dim3(nctas), dim3(POOL_T), args, smem, st);
 }
 
-// co-resident CTAs per SM of the persistent solvers (both must fit a cooperative launch)
-int pcg_max_ctas_per_sm(int max_slices) {
+// co-resident CTAs per SM of the pooled solvers for the plan (both must fit a cooperative launch)
+int pcg_pool_ctas_per_sm(const PoolPlan& pl) {
   int a = 0, b = 0;
-  const size_t smem = (size_t)max_slices * 4 * sizeof(double);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg64, PCG_T, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_mixed, PCG_T, smem);
+  const size_t smem = pcg_pool_smem(pl);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute((const void*)k_pcg64_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_pcg_mixed_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg64_pool, POOL_T, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_mixed_pool, POOL_T, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return a < b ? a : b;
 }
 

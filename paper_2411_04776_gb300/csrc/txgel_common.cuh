@@ -105,6 +105,20 @@ struct GelVar {  // per gel, written by the device
   int pad3_;
 };
 
+// Per-gel record of the pooled streaming PCG (k_solve.cu): written by the gel's owner warp after
+// a pool barrier, read by every CTA after the next one
+struct PoolGel {
+  double al, be;          // CG step and direction update of the current iteration
+  double gprev, aprev;    // the previous iteration's gamma and alpha (owner only)
+  double bb, th;          // |b|^2 of the right-hand side and the stopping threshold eta^2 |b|^2
+  double rho;             // Galerkin start along the previous direction
+  double rr, rr0, tol;    // mixed: |r|^2 (FP64 residual / FP32 inner), its round-start value, the inner target
+  int act;                // in this solve
+  int run;                // solve not finished (FP64: CG running; mixed: refinement rounds running)
+  int inner;              // mixed: FP32 inner CG of the current round running
+  int it;                 // CG iterations so far
+};
+
 struct PairBarrier;  // barrier setup of one contact pair (dev_pairwarp.cuh)
 
 // Lagged friction data of one contact pair, taken at the start of the (sub)step (IPC, Li et al.
@@ -168,6 +182,8 @@ struct Dev {
   float4 *u32, *w32, *pp32, *s32, *r32, *x32;
   double* part;    // PCG: per-CTA partial sums exchanged inside a group, [2 sets][4][nctas]
   unsigned* bar;   // PCG: one barrier counter per group
+  double* pslice;  // pooled PCG: per-slice partial sums [slice][4]
+  PoolGel* pool;   // pooled PCG: per-gel records
   // surface primitives (global)
   int* sv;
   int4* st;
@@ -222,6 +238,12 @@ struct Dev {
 // with many slices forms a group alone, spread over several CTAs; runs of small gels are packed
 // into a group of one CTA.  The CTAs of a group synchronise through a barrier counter of their
 // own, so a group never waits for another one.
+// Pooled streaming PCG launch: the gels [g0, g0 + ng) (those in the solve's phase take part)
+struct PoolPlan {
+  int g0, ng;
+  int cap;  // room of a CTA's slice list (at least its share of the gels' slices)
+};
+
 struct PcgPlan {
   const int2* cta_rng;   // per CTA: its slices [x, y)
   const int* cta_grp;    // per CTA: its group

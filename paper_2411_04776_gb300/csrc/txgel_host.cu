@@ -57,10 +57,9 @@ void launch_eval_accd(int n, const int* kind, const double* P, const double* dP,
 void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st);
 void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st);
 void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st);
-cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st);
-cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
-                             cudaStream_t st);
-int pcg_max_ctas_per_sm(int max_slices);
+cudaError_t launch_pcg_pool(const Dev& d, int phase, const PoolPlan& pl, int nctas, bool mixed, int maxit,
+                            int refine_max, cudaStream_t st);
+int pcg_pool_ctas_per_sm(const PoolPlan& pl);
 size_t pair_record_doubles();
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
 cudaError_t launch_pcg_res(const Dev& d, int phase, const PcgPlan& plan, int nctas, bool mixed, int maxit,
@@ -102,6 +101,7 @@ constexpr int TUNE_SPC[TUNE_N] = {4, 2, 3, 6, 8};  // candidate slices per CTA (
 constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
 constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
+constexpr int PCG_RES_MAXS = 7;     // slices per CTA the resident PCG kernels handle (a warp each)
 constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
 constexpr int PIECE_HOST = 512;
 constexpr int PAIR_PIECES = 16;  // energy pieces over a gel's candidate pairs (a few thousand: one each per thread)
@@ -480,6 +480,8 @@ struct tx_batch {
     PcgPlan plan{};
     int nctas = 0;
     bool res = false;
+    PoolPlan pool{};     // streaming parts: the pooled kernels' gel range and CTAs
+    int pool_nctas = 0;
   };
   std::vector<PlanPart> parts;
   int nparts = 0;
@@ -1033,6 +1035,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
   d.part = M.get<double>(8 * (size_t)cta_cap);
+  d.pslice = M.get<double>(4 * (size_t)nslices);
+  d.pool = M.get<PoolGel>(n);
   d.bar = M.get<unsigned>(n);
   d.sv = M.get<int>(nsv);
   d.st = M.get<int4>(nst);
@@ -1551,8 +1555,8 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
     // control warp at least
     res = !b->force_stream && occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC &&
           (max_nc == 1 || max_slices >= 2);
-    const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
-    if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
+    // without a resident plan within a slice per warp the pooled kernels take the set
+    if (res || b->force_stream || max_slices > PCG_RES_MAXS) break;
     if (attempt > 400) {
       set_last_error("PCG partition does not fit the device");
       return TX_ERR_ARG;
@@ -1561,14 +1565,34 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
   }
   const int nctas = (int)rng.size();
   cudaStream_t st = b->st;
-  // pageable sources: the copies take the data when enqueued, the vectors can be reused at once
-  CK(cudaMemcpyAsync((void*)part.plan.cta_rng, rng.data(), sizeof(int2) * nctas, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync((void*)part.plan.cta_grp, cgrp.data(), sizeof(int) * nctas, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync((void*)part.plan.grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
+  // pageable sources: the copies take the data when enqueued, the vectors can be reused at once.
+  // (the pooled kernels need no CTA plan)
+  if (res) {
+    if (nctas > b->pcg_cta_cap) {
+      set_last_error("PCG partition does not fit the device");
+      return TX_ERR_ARG;
+    }
+    CK(cudaMemcpyAsync((void*)part.plan.cta_rng, rng.data(), sizeof(int2) * nctas, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void*)part.plan.cta_grp, cgrp.data(), sizeof(int) * nctas, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void*)part.plan.grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
+  }
   part.plan.max_slices = max_slices;
   part.plan.ngroups = (int)grp.size();
   part.nctas = nctas;
   part.res = res;
+  if (!res) {  // streaming: the pooled kernels over the set's gel range, every SM
+    part.pool.g0 = set.front();
+    part.pool.ng = set.back() - set.front() + 1;
+    long long tot = 0;  // slices of the gel range: bounds every CTA's share
+    for (int g = part.pool.g0; g < part.pool.g0 + part.pool.ng; ++g) tot += b->gi[g].ns;
+    part.pool.cap = (int)(tot / nsm) + 2;  // one CTA per SM (checked below)
+    const int occp = pcg_pool_ctas_per_sm(part.pool);
+    if (occp < 1) {
+      set_last_error("pooled PCG does not fit the device");
+      return TX_ERR_ARG;
+    }
+    part.pool_nctas = nsm;
+  }
   return TX_OK;
 }
 
@@ -1686,12 +1710,12 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
       if (P.res)
         CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, true, pcg_max, refine, b->pcg_wmax, st));
       else
-        CK(launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, pcg_max, refine, st));
+        CK(launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, true, pcg_max, refine, st));
     } else {
       if (P.res)
         CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, pcg_max, 0, b->pcg_wmax, st));
       else
-        CK(launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, pcg_max, st));
+        CK(launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, false, pcg_max, 0, st));
     }
   }
   prof_close(b, b->nparts);

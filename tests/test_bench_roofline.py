@@ -28,7 +28,7 @@ def test_fp64_roofline_is_flops_over_launch_time():
 
 
 def test_mixed_roofline_is_bytes_over_launch_time_against_measured_copy():
-    r = bench.roofline(_prof(4.0, 8, 0.0, 8.0e9), {}, "mixed", "k_pcg_mixed")
+    r = bench.roofline(_prof(4.0, 8, 0.0, 8.0e9), {}, "mixed", "k_pcg_mixed_pool")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 2000.0) < 1e-9  # 1e9 B per launch in 0.5 ms
     pk = bench.measured_peaks().get("hbm_gbs")

@@ -1,9 +1,10 @@
-"""Parity of the streaming PCG kernels (k_pcg64 in FP64, k_pcg_mixed in mixed precision: the
-matrix streamed from HBM every iteration, the kernels the large batched configurations run) on a
-batch of gels of uneven size, one from each of the three grids: every gel against the FP64 oracle
-and against the same gel stepped alone (which takes the resident kernels).  The streaming family
-is selected with tx_params.pcg_plan = 1; the test checks through the profile counters that no
-resident launch ran."""
+"""Parity of the pooled streaming PCG kernels (k_pcg64_pool in FP64, k_pcg_mixed_pool in mixed
+precision: the matrix streamed from HBM every iteration, the kernels the large batched
+configurations run) on a batch of gels of uneven size, one from each of the three grids, so that
+the small gels finish their solves while the large one still iterates and the pool re-splits the
+remaining slices: every gel against the FP64 oracle and against the same gel stepped alone (which
+takes the resident kernels).  The streaming family is selected with tx_params.pcg_plan = 1; the
+test checks through the profile counters that no resident launch ran."""
 import numpy as np
 import pytest
 
