@@ -339,9 +339,13 @@ def roofline(prof, clocks, precision, kernel, fma=None):
 
 
 def pcg_kernel_name(precision, n_gels):
+    """The PCG kernel the library's automatic plan runs for n_gels gels: resident for one gel,
+    the pooled streaming form from 32 gels on, the per-gel-group streaming form between."""
     if n_gels == 1:
         return "k_pcg64_res" if precision == "fp64" else "k_pcg_mixed_res"
-    return "k_pcg64_pool" if precision == "fp64" else "k_pcg_mixed_pool"
+    if n_gels >= 32:
+        return "k_pcg64_pool" if precision == "fp64" else "k_pcg_mixed_pool"
+    return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
 
 
 def source_hash(files):
@@ -552,7 +556,8 @@ def main():
         "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
         "gpu_launches": r["prof"]["kernel_launches"],
         "pcg_launches": {"resident": r["prof"]["pcg_resident_launches"],
-                         "streaming": r["prof"]["pcg_streaming_launches"]},
+                         "streaming": r["prof"]["pcg_streaming_launches"],
+                         "pooled": r["prof"]["pcg_pool_launches"]},
         "fma_peaks": fma,
         "iteration_histogram": iteration_histogram(r["stats"]),
         "clocks": r["clocks"],
@@ -729,7 +734,8 @@ def batched_mixed(args):
                              "roofline": roofline(r64["prof"], r64["clocks"], "fp64", pcg_kernel_name("fp64", ng),
                                                   args.fma_peaks),
                              "pcg_launches": {"resident": r64["prof"]["pcg_resident_launches"],
-                                              "streaming": r64["prof"]["pcg_streaming_launches"]}},
+                                              "streaming": r64["prof"]["pcg_streaming_launches"],
+                                              "pooled": r64["prof"]["pcg_pool_launches"]}},
             "plain_fp64_same_steps": plain,
             "vs_plain_fp64": value / plain["value"],
             "batching_gain_fp64": value64 / plain["value"],
@@ -737,7 +743,8 @@ def batched_mixed(args):
             "accuracy_vs_plain_fp64": state_difference(r["finals"], plain_finals),
             "accuracy_batched_fp64_vs_plain_fp64": state_difference(r64["finals"], plain_finals),
             "roofline": roofline(prof, r["clocks"], "mixed", pcg_kernel_name("mixed", ng)),
-            "pcg_launches": {"resident": prof["pcg_resident_launches"], "streaming": prof["pcg_streaming_launches"]},
+            "pcg_launches": {"resident": prof["pcg_resident_launches"], "streaming": prof["pcg_streaming_launches"],
+                             "pooled": prof["pcg_pool_launches"]},
             "phases_ms": {k: round(v["ms"], 3) for k, v in prof["phases"].items()},
             "gpu_launches": prof["kernel_launches"], "clocks": r["clocks"]}
 

@@ -80,9 +80,12 @@ typedef struct tx_params {
                                PCG's sums, so tuned runs are not bitwise reproducible)          */
   int32_t pcg_plan;         /* PCG kernel family: 0 automatic (the resident kernels, which keep the
                                matrix in shared memory, whenever the gels fit them; otherwise the
-                               streaming kernels); 1 always the streaming kernels (tests and
-                               measurements of that family).  A handle uses the streaming kernels
-                               if any of its gels asks for them.                                */
+                               streaming kernels, which stream it from HBM: per-gel CTA groups
+                               below 32 gels being solved, the pool of one CTA per SM that
+                               re-splits the gels still iterating from 32 on); 1 always the
+                               per-gel-group streaming kernels; 2 always the pooled streaming
+                               kernels (1 and 2: tests and measurements of one family).  A handle
+                               takes the largest value any of its gels asks for.               */
   int32_t reserved0;        /* must be 0                                                       */
   double friction;          /* IPC lagged friction coefficient mu_f between gel and indenter
                                (0: frictionless, the default).  Pairs in contact at the start of a
@@ -281,7 +284,9 @@ typedef struct tx_profile {
   int64_t kernel_launches;          /* every kernel this library launched (all handles)          */
   int64_t pcg_resident_launches;    /* PCG launches of the resident kernels (matrix in shared
                                        memory; counted whether or not profiling is on)            */
-  int64_t pcg_streaming_launches;   /* PCG launches of the streaming kernels (matrix from HBM)   */
+  int64_t pcg_streaming_launches;   /* PCG launches of the streaming kernels (matrix from HBM),
+                                       both forms                                                */
+  int64_t pcg_pool_launches;        /* of which launches of the pooled form                      */
 } tx_profile;
 
 tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out);

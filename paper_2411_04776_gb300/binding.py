@@ -70,7 +70,8 @@ class tx_profile(ctypes.Structure):
                 ("launches", ctypes.c_int64 * PROFILE_MAX), ("flops", ctypes.c_double * PROFILE_MAX),
                 ("bytes", ctypes.c_double * PROFILE_MAX), ("pcg_iters", ctypes.c_int64),
                 ("newton_iters", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("pcg_resident_launches", ctypes.c_int64), ("pcg_streaming_launches", ctypes.c_int64)]
+                ("pcg_resident_launches", ctypes.c_int64), ("pcg_streaming_launches", ctypes.c_int64),
+                ("pcg_pool_launches", ctypes.c_int64)]
 
     def as_dict(self):
         phases = {}
@@ -80,7 +81,8 @@ class tx_profile(ctypes.Structure):
         return dict(phases=phases, pcg_iters=int(self.pcg_iters), newton_iters=int(self.newton_iters),
                     kernel_launches=int(self.kernel_launches),
                     pcg_resident_launches=int(self.pcg_resident_launches),
-                    pcg_streaming_launches=int(self.pcg_streaming_launches))
+                    pcg_streaming_launches=int(self.pcg_streaming_launches),
+                    pcg_pool_launches=int(self.pcg_pool_launches))
 
 
 class TxError(RuntimeError):

@@ -6,10 +6,11 @@
 //     g = M (x - xt) / h^2 + sum_t V_t P_t D_a.  Dirichlet rows get g = 0.
 //   * PCG (batches too large for the resident kernels of k_pcg_res.cu): one persistent cooperative
 //     kernel per Newton iteration runs every PCG iteration of every gel of the batch
-//     (Chronopoulos-Gear single-reduction CG) over a pool of one CTA per SM that splits the slices
-//     of the gels still iterating evenly at every phase; dot products are per-slice partials that
-//     each gel's owner warp adds in a fixed order, so results are reproducible and a gel's sums do
-//     not depend on the other gels.
+//     (Chronopoulos-Gear single-reduction CG), in one of two forms.  Per-gel CTA groups: each gel
+//     (or run of small gels) has its own CTAs and group barrier; best for a few gels.  Pooled:
+//     one CTA per SM splits the slices of the gels still iterating evenly at every phase, so no SM
+//     idles while the slowest gel finishes; best for many gels.  Dot products are per-slice (or
+//     per-CTA) partials added in a fixed order: results are reproducible.
 //   * energy: E(x + alpha p) per gel = inertia + elastic + barrier, as per-piece partial sums
 //     (pieces never straddle gels) reduced per gel in a fixed order; the reduction kernel also
 //     takes the line-search decision (accept on E <= E_cur, else halve alpha).
@@ -223,6 +224,166 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
   count_launch(1);
 }
 
+// One projected-Newton direction per gel of the gels in `phase`: block-Jacobi preconditioned CG
+// on H p = -g (Chronopoulos-Gear: one reduction phase per iteration), FP64, stops per gel when
+// |r| <= eta |g| or after maxit iterations.
+__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, int maxit) {
+  extern __shared__ double dsm[];  // [slices of this CTA][4]
+  __shared__ double tot[PCG_MAXG][4];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ double rhoj[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
+  __shared__ int s_fail, s_any;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  PcgCta c = pcg_cta(d, plan);
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
+    run[j] = gact[j];
+  }
+  __syncthreads();
+  // ---- Galerkin start: x0 = rho p_prev, the minimiser of the quadratic model along the gel's
+  // previous Newton direction (in d.p; rho = b.p_prev / p_prev.A p_prev, 0 without a usable one);
+  // a = A p_prev goes to d.w.  Partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3).
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    double bp = 0.0, pw = 0.0, bb = 0.0;
+    if (gact[plan.slice_gel[s] - c.g0]) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      const bool fx = d.fixed[r] != 0;
+      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row64(d, s, lane, d.p);
+      d.w[r] = a;
+      bp = dot4(b, pv);
+      pw = dot4(pv, a);
+      bb = dot4(b, b);
+    }
+    bp = warp_sum(bp);
+    pw = warp_sum(pw);
+    bb = warp_sum(bb);
+    if (lane == 0) {
+      dsm[(s - c.s0) * 4 + 0] = bp;
+      dsm[(s - c.s0) * 4 + 1] = pw;
+      dsm[(s - c.s0) * 4 + 2] = 0.0;
+      dsm[(s - c.s0) * 4 + 3] = bb;
+    }
+  }
+  // (the group sum's barrier also ends every CTA's SpMV on d.p before d.p is overwritten below)
+  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    bbj[j] = tot[j][3];
+    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[j][1], rho = tot[j][0] / pw;
+    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;  // a non-finite p_prev anywhere gives 0
+  }
+  __syncthreads();
+  // ---- x = rho p_prev, r = b - rho a, u = M^-1 r, pp = s = 0
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    const int j = plan.slice_gel[s] - c.g0;
+    if (!gact[j]) continue;
+    const int r = 32 * s + lane;
+    const double4_32a gr = d.grad[r];
+    double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+    double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    const double rho = rhoj[j];
+    if (rho != 0.0 && !d.fixed[r]) {
+      const double4_32a pv = d.p[r], a = d.w[r];
+      x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
+      b.x = fma(-rho, a.x, b.x);
+      b.y = fma(-rho, a.y, b.y);
+      b.z = fma(-rho, a.z, b.z);
+    }
+    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    d.r[r] = b;
+    d.p[r] = x;
+    d.pp[r] = z;
+    d.s[r] = z;
+    d.u[r] = mul3(d.Minv + 9 * r, b);
+  }
+  if (!group_barrier(c, d, &s_fail)) return;  // u complete before the SpMV
+  for (int k = 1;; ++k) {
+    // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      double ga = 0.0, de = 0.0, rr = 0.0;
+      if (run[plan.slice_gel[s] - c.g0]) {
+        const int r = 32 * s + lane;
+        double4_32a w = spmv_row64(d, s, lane, d.u);
+        if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.w[r] = w;
+        const double4_32a rv = d.r[r], uv = d.u[r];
+        ga = dot4(rv, uv);
+        de = dot4(w, uv);
+        rr = dot4(rv, rv);
+      }
+      ga = warp_sum(ga);
+      de = warp_sum(de);
+      rr = warp_sum(rr);
+      if (lane == 0) {
+        dsm[(s - c.s0) * 4 + 0] = ga;
+        dsm[(s - c.s0) * 4 + 1] = de;
+        dsm[(s - c.s0) * 4 + 2] = rr;
+      }
+    }
+    if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
+    // ---- per-gel scalars and convergence (identical in every CTA of the group)
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+      if (!run[j]) continue;
+      const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
+      if (!(rr > thj[j]) || k > maxit) {
+        run[j] = 0;
+        if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + j].pcg_it = k - 1;
+          d.gv[c.g0 + j].bb = bbj[j];
+          d.gv[c.g0 + j].res2 = bbj[j] > 0.0 ? rr / bbj[j] : 0.0;
+          d.gv[c.g0 + j].pcg_done = 1;
+        }
+        continue;
+      }
+      s_any = 1;
+      const double beta = k == 1 ? 0.0 : ga / gprev[j];
+      const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
+      gprev[j] = ga;
+      aprev[j] = alpha;
+      alj[j] = alpha;
+      bej[j] = beta;
+    }
+    __syncthreads();
+    if (!s_any) break;
+    // ---- vector updates
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      const int j = plan.slice_gel[s] - c.g0;
+      if (!run[j]) continue;
+      const double beta = bej[j], alpha = alj[j];
+      const int r = 32 * s + lane;
+      const double4_32a u = d.u[r], w = d.w[r];
+      double4_32a pp = d.pp[r], sv = d.s[r], x = d.p[r], rv = d.r[r];
+      pp.x = fma(beta, pp.x, u.x); pp.y = fma(beta, pp.y, u.y); pp.z = fma(beta, pp.z, u.z);
+      sv.x = fma(beta, sv.x, w.x); sv.y = fma(beta, sv.y, w.y); sv.z = fma(beta, sv.z, w.z);
+      x.x = fma(alpha, pp.x, x.x); x.y = fma(alpha, pp.y, x.y); x.z = fma(alpha, pp.z, x.z);
+      rv.x = fma(-alpha, sv.x, rv.x); rv.y = fma(-alpha, sv.y, rv.y); rv.z = fma(-alpha, sv.z, rv.z);
+      d.pp[r] = pp;
+      d.s[r] = sv;
+      d.p[r] = x;
+      d.r[r] = rv;
+      d.u[r] = mul3(d.Minv + 9 * r, rv);
+    }
+    if (!group_barrier(c, d, &s_fail)) return;
+  }
+  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
+}
+
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st) {
+  Dev dd = d;
+  PcgPlan pp = plan;
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit};
+  count_launch(1);
+  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg64, dim3(nctas), dim3(PCG_T), args, smem, st);
+}
+
 // ---------------------------------------------------------------- pooled streaming PCG
 // Every CTA of the launch belongs to one group (the pool).  At each phase the slices of the gels
 // still taking part are split evenly over the CTAs: a prefix sum over the gels' slice counts, the
@@ -379,7 +540,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg64_pool(Dev d, int phase, Pool
   int S = pool_prefix(d, pl, 0, phase, pre);
   int nl = pool_list(d, pl, pre, S, lst, pl.cap);
   for (int i = wid; i < nl; i += POOL_W) {
-    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+    const int s = lst[i].x, r = 32 * s + lane;
     const double4_32a gr = d.grad[r];
     const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
     const bool fx = d.fixed[r] != 0;
@@ -442,7 +603,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg64_pool(Dev d, int phase, Pool
   for (int k = 1;; ++k) {
     // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
     for (int i = wid; i < nl; i += POOL_W) {
-      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const int s = lst[i].x, r = 32 * s + lane;
       double4_32a w = spmv_row64(d, s, lane, d.u);
       if (d.fixed[r]) w = make_double4_32a(0.0, 0.0, 0.0, 0.0);
       d.w[r] = w;
@@ -558,6 +719,235 @@ __device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lan
   return make_double4_32a(a0, a1, a2, 0.0);
 }
 
+__global__ void __launch_bounds__(PCG_T, 3) k_pcg_mixed(Dev d, int phase, PcgPlan plan, int maxit,
+                                                     int refine_max) {
+  extern __shared__ double dsm[];
+  __shared__ double tot[PCG_MAXG][4];
+  __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], tolj[PCG_MAXG], rr0j[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG];
+  __shared__ double rhoj[PCG_MAXG];
+  __shared__ float alj[PCG_MAXG], bej[PCG_MAXG];
+  __shared__ int gact[PCG_MAXG], run[PCG_MAXG], inner[PCG_MAXG], itj[PCG_MAXG];
+  __shared__ int s_fail, s_any;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  PcgCta c = pcg_cta(d, plan);
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
+    run[j] = gact[j];
+    itj[j] = 0;
+  }
+  __syncthreads();
+  // ---- Galerkin start along the previous Newton direction (as in k_pcg64; a = A32 p_prev with
+  // FP64 arithmetic, into d.w): partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3)
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    double bp = 0.0, pw = 0.0, bb = 0.0;
+    if (gact[plan.slice_gel[s] - c.g0]) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      const bool fx = d.fixed[r] != 0;
+      const double4_32a pv = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : d.p[r];
+      const double4_32a a = fx ? make_double4_32a(0.0, 0.0, 0.0, 0.0) : spmv_row_res(d, s, lane, d.p);
+      d.w[r] = a;
+      bp = dot4(b, pv);
+      pw = dot4(pv, a);
+      bb = dot4(b, b);
+    }
+    bp = warp_sum(bp);
+    pw = warp_sum(pw);
+    bb = warp_sum(bb);
+    if (lane == 0) {
+      dsm[(s - c.s0) * 4 + 0] = bp;
+      dsm[(s - c.s0) * 4 + 1] = pw;
+      dsm[(s - c.s0) * 4 + 2] = 0.0;
+      dsm[(s - c.s0) * 4 + 3] = bb;
+    }
+  }
+  if (!group_sum(d, c, dsm, 0, 4, tot, &s_fail)) return;  // its barrier ends every SpMV on d.p
+  for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+    bbj[j] = tot[j][3];
+    thj[j] = d.gv[c.g0 + j].eta2 * bbj[j];  // stop at |r|^2 <= eta^2 |b|^2 (the gel's forcing term)
+    const double pw = tot[j][1], rho = tot[j][0] / pw;
+    rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;
+  }
+  __syncthreads();
+  // ---- p = rho p_prev, r64 = b - rho a; partial |r|^2 (k = 2)
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    double rr = 0.0;
+    const int j = plan.slice_gel[s] - c.g0;
+    if (gact[j]) {
+      const int r = 32 * s + lane;
+      const double4_32a gr = d.grad[r];
+      double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
+      double4_32a x = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      const double rho = rhoj[j];
+      if (rho != 0.0 && !d.fixed[r]) {
+        const double4_32a pv = d.p[r], a = d.w[r];
+        x = make_double4_32a(rho * pv.x, rho * pv.y, rho * pv.z, 0.0);
+        b.x = fma(-rho, a.x, b.x);
+        b.y = fma(-rho, a.y, b.y);
+        b.z = fma(-rho, a.z, b.z);
+      }
+      d.r[r] = b;
+      d.p[r] = x;
+      rr = dot4(b, b);
+    }
+    rr = warp_sum(rr);
+    if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
+  }
+  if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
+  for (int round = 0;; ++round) {
+    // ---- round start: outer convergence on the FP64 residual; inner init r32 = r64, x32 = 0
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+      inner[j] = 0;
+      if (!run[j]) continue;
+      const double rr = tot[j][2], bb = bbj[j];
+      if (!(rr > thj[j]) || round >= refine_max) {
+        run[j] = 0;
+        if (blockIdx.x == c.c0) {
+          d.gv[c.g0 + j].res2 = bb > 0.0 ? rr / bb : 0.0;
+          d.gv[c.g0 + j].pcg_done = 1;
+          d.gv[c.g0 + j].rounds = round;
+          d.gv[c.g0 + j].bb = bb;
+          d.gv[c.g0 + j].pcg_it = itj[j];
+        }
+        continue;
+      }
+      s_any = 1;
+      inner[j] = 1;
+      // inner target: reach eta |b| in one round if FP32 allows, else the FP32 floor
+      tolj[j] = fmax(thj[j] / rr, 1e-11);
+    }
+    __syncthreads();
+    if (!s_any) break;
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      if (!inner[plan.slice_gel[s] - c.g0]) continue;
+      const int r = 32 * s + lane;
+      const double4_32a rv = d.r[r];
+      const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
+      d.r32[r] = r32;
+      d.x32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.pp32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.s32[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.u32[r] = mul3f(d.Minv32 + 9 * r, r32);
+    }
+    if (!group_barrier(c, d, &s_fail)) return;
+    // ---- inner FP32 CG (Chronopoulos-Gear), same structure as the FP64 kernel
+    for (int k = 1;; ++k) {
+      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+        double ga = 0.0, de = 0.0, rr = 0.0;
+        if (inner[plan.slice_gel[s] - c.g0]) {
+          const int r = 32 * s + lane;
+          float4 w = spmv_row32(d, s, lane, d.u32);
+          if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
+          d.w32[r] = w;
+          const float4 rv = d.r32[r], uv = d.u32[r];
+          // FP32 warp sums: the inner solve's dot products are FP32 quantities (GB300 runs FP64
+          // adds at 1/64 of the FP32 rate); slices and CTAs are then added in FP64
+          ga = warp_sum(dot4f(rv, uv));
+          de = warp_sum(dot4f(w, uv));
+          rr = warp_sum(dot4f(rv, rv));
+        }
+        if (lane == 0) {
+          dsm[(s - c.s0) * 4 + 0] = ga;
+          dsm[(s - c.s0) * 4 + 1] = de;
+          dsm[(s - c.s0) * 4 + 2] = rr;
+        }
+      }
+      if (!group_sum<float>(d, c, dsm, 0, 3, tot, &s_fail)) return;
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
+        if (!inner[j]) continue;
+        const double ga = tot[j][0], de = tot[j][1], rr = tot[j][2];
+        // converged once |r32|^2 <= tol |r32 at the round start|^2 (FP32 accuracy floor 1e-11)
+        if (k == 1) rr0j[j] = rr;
+        if (!(rr > tolj[j] * rr0j[j]) || k > maxit) {
+          inner[j] = 0;
+          itj[j] += k - 1;
+          continue;
+        }
+        s_any = 1;
+        const double beta = k == 1 ? 0.0 : ga / gprev[j];
+        const double alpha = k == 1 ? ga / de : ga / (de - beta * ga / aprev[j]);
+        gprev[j] = ga;
+        aprev[j] = alpha;
+        alj[j] = (float)alpha;
+        bej[j] = (float)beta;
+      }
+      __syncthreads();
+      if (!s_any) break;
+      for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+        const int j = plan.slice_gel[s] - c.g0;
+        if (!inner[j]) continue;
+        const float fb = bej[j], fa = alj[j];
+        const int r = 32 * s + lane;
+        const float4 u = d.u32[r], w = d.w32[r];
+        float4 pp = d.pp32[r], sv = d.s32[r], x = d.x32[r], rv = d.r32[r];
+        pp.x = fmaf(fb, pp.x, u.x); pp.y = fmaf(fb, pp.y, u.y); pp.z = fmaf(fb, pp.z, u.z);
+        sv.x = fmaf(fb, sv.x, w.x); sv.y = fmaf(fb, sv.y, w.y); sv.z = fmaf(fb, sv.z, w.z);
+        x.x = fmaf(fa, pp.x, x.x); x.y = fmaf(fa, pp.y, x.y); x.z = fmaf(fa, pp.z, x.z);
+        rv.x = fmaf(-fa, sv.x, rv.x); rv.y = fmaf(-fa, sv.y, rv.y); rv.z = fmaf(-fa, sv.z, rv.z);
+        d.pp32[r] = pp;
+        d.s32[r] = sv;
+        d.x32[r] = x;
+        d.r32[r] = rv;
+        d.u32[r] = mul3f(d.Minv32 + 9 * r, rv);
+      }
+      if (!group_barrier(c, d, &s_fail)) return;
+    }
+    // ---- p += x32 (FP64), then the FP64 residual r64 = b - A p
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      if (!run[plan.slice_gel[s] - c.g0]) continue;
+      const int r = 32 * s + lane;
+      const float4 x = d.x32[r];
+      double4_32a p = d.p[r];
+      p.x += (double)x.x;
+      p.y += (double)x.y;
+      p.z += (double)x.z;
+      d.p[r] = p;
+    }
+    if (!group_barrier(c, d, &s_fail)) return;
+    for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+      double rr = 0.0;
+      if (run[plan.slice_gel[s] - c.g0]) {
+        const int r = 32 * s + lane;
+        double4_32a ap = spmv_row_res(d, s, lane, d.p);
+        const double4_32a gr = d.grad[r];
+        double4_32a rv = make_double4_32a(-gr.x - ap.x, -gr.y - ap.y, -gr.z - ap.z, 0.0);
+        if (d.fixed[r]) rv = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.r[r] = rv;
+        rr = dot4(rv, rv);
+      }
+      rr = warp_sum(rr);
+      if (lane == 0) dsm[(s - c.s0) * 4 + 2] = rr;
+    }
+    if (!group_sum(d, c, dsm, 2, 3, tot, &s_fail)) return;
+  }
+  pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
+}
+
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
+                             cudaStream_t st) {
+  Dev dd = d;
+  PcgPlan pp = plan;
+  void* args[] = {(void*)&dd, (void*)&phase, (void*)&pp, (void*)&maxit, (void*)&refine_max};
+  count_launch(1);
+  const size_t smem = (size_t)plan.max_slices * 4 * sizeof(double);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_mixed, dim3(nctas), dim3(PCG_T), args, smem, st);
+}
+
+// co-resident CTAs per SM of the persistent solvers (both must fit a cooperative launch)
+int pcg_max_ctas_per_sm(int max_slices) {
+  int a = 0, b = 0;
+  const size_t smem = (size_t)max_slices * 4 * sizeof(double);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg64, PCG_T, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_mixed, PCG_T, smem);
+  return a < b ? a : b;
+}
+
 // the owner's decision at the start of a refinement round from the gel's FP64 residual rr: the
 // solve ends (rounds done = round) or the round's FP32 inner solve starts with its target
 __device__ __forceinline__ void pool_round_start(const Dev& d, int g, double rr, int round, int refine_max) {
@@ -591,7 +981,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, 
   int S = pool_prefix(d, pl, 0, phase, pre);
   int nl = pool_list(d, pl, pre, S, lst, pl.cap);
   for (int i = wid; i < nl; i += POOL_W) {
-    const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+    const int s = lst[i].x, r = 32 * s + lane;
     const double4_32a gr = d.grad[r];
     const double4_32a b = make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0);
     const bool fx = d.fixed[r] != 0;
@@ -661,7 +1051,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, 
     if (S == 0) break;  // no gel starts a round: every solve has ended
     // ---- inner init: r32 = r64, x32 = pp32 = s32 = 0, u32 = M^-1 r32
     for (int i = wid; i < nl; i += POOL_W) {
-      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const int s = lst[i].x, r = 32 * s + lane;
       const double4_32a rv = d.r[r];
       const float4 r32 = make_float4((float)rv.x, (float)rv.y, (float)rv.z, 0.f);
       d.r32[r] = r32;
@@ -674,7 +1064,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, 
     // ---- inner FP32 CG (Chronopoulos-Gear)
     for (int k = 1;; ++k) {
       for (int i = wid; i < nl; i += POOL_W) {
-        const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+        const int s = lst[i].x, r = 32 * s + lane;
         float4 w = spmv_row32(d, s, lane, d.u32);
         if (d.fixed[r]) w = make_float4(0.f, 0.f, 0.f, 0.f);
         d.w32[r] = w;
@@ -736,7 +1126,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, 
     S = pool_prefix(d, pl, 1, phase, pre);
     nl = pool_list(d, pl, pre, S, lst, pl.cap);
     for (int i = wid; i < nl; i += POOL_W) {
-      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const int s = lst[i].x, r = 32 * s + lane;
       const float4 x = d.x32[r];
       double4_32a p = d.p[r];
       p.x += (double)x.x;
@@ -747,7 +1137,7 @@ __global__ void __launch_bounds__(POOL_T, 1) k_pcg_mixed_pool(Dev d, int phase, 
     if (!group_barrier(c, d, &s_fail)) return;
     // ---- the FP64 residual r64 = b - A p; partial |r|^2 (2)
     for (int i = wid; i < nl; i += POOL_W) {
-      const int s = lst[i].x, g = lst[i].y, r = 32 * s + lane;
+      const int s = lst[i].x, r = 32 * s + lane;
       const double4_32a ap = spmv_row_res(d, s, lane, d.p);
       const double4_32a gr = d.grad[r];
       double4_32a rv = make_double4_32a(-gr.x - ap.x, -gr.y - ap.y, -gr.z - ap.z, 0.0);

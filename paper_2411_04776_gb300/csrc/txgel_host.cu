@@ -59,6 +59,10 @@ void launch_gather(const Dev& d, int phase, int nbp, bool mixed, cudaStream_t st
 void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st);
 cudaError_t launch_pcg_pool(const Dev& d, int phase, const PoolPlan& pl, int nctas, bool mixed, int maxit,
                             int refine_max, cudaStream_t st);
+cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st);
+cudaError_t launch_pcg_mixed(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, int refine_max,
+                             cudaStream_t st);
+int pcg_max_ctas_per_sm(int max_slices);
 int pcg_pool_ctas_per_sm(const PoolPlan& pl);
 size_t pair_record_doubles();
 int pcg_res_ctas_per_sm(bool mixed, int max_slices, int wmax);
@@ -101,7 +105,9 @@ constexpr int TUNE_SPC[TUNE_N] = {4, 2, 3, 6, 8};  // candidate slices per CTA (
 constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
 constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
-constexpr int PCG_RES_MAXS = 7;     // slices per CTA the resident PCG kernels handle (a warp each)
+constexpr int PCG_POOL_MIN_GELS = 32;  // automatic plan: pooled streaming kernels from this many gels
+                                      // being solved on (per-gel CTA groups below: measured faster
+                                      // up to 16 gels, slower from 64)
 constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
 constexpr int PIECE_HOST = 512;
 constexpr int PAIR_PIECES = 16;  // energy pieces over a gel's candidate pairs (a few thousand: one each per thread)
@@ -181,7 +187,7 @@ tx_status check_desc(const tx_gel_desc* d) {
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
-      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 1 || p.reserved0 != 0 || !(p.friction >= 0.0) ||
+      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 2 || p.reserved0 != 0 || !(p.friction >= 0.0) ||
       !(p.friction_eps_v > 0.0))
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
@@ -430,7 +436,7 @@ struct Prof {
   double flops[PR_N] = {};
   double bytes[PR_N] = {};
   long long pcg_iters = 0, newton_iters = 0;
-  long long pcg_res = 0, pcg_stream = 0;  // PCG launches per kernel family
+  long long pcg_res = 0, pcg_stream = 0, pcg_pool = 0;  // PCG launches per kernel family
   struct Pending {
     cudaEvent_t a, b;
     int phase;
@@ -480,7 +486,8 @@ struct tx_batch {
     PcgPlan plan{};
     int nctas = 0;
     bool res = false;
-    PoolPlan pool{};     // streaming parts: the pooled kernels' gel range and CTAs
+    bool pool_on = false;  // streaming in the pooled form
+    PoolPlan pool{};       // its gel range and CTAs
     int pool_nctas = 0;
   };
   std::vector<PlanPart> parts;
@@ -510,7 +517,8 @@ struct tx_batch {
     double us[8] = {};
     int best = -1;
   };
-  bool force_stream = false;  // some gel asked for the streaming PCG kernels (tx_params.pcg_plan = 1)
+  int plan_mode = 0;  // the largest tx_params.pcg_plan of the gels: 0 automatic, 1 per-gel-group
+                      // streaming, 2 pooled streaming
   bool friction = false;      // some gel has lagged friction (tx_params.friction > 0)
   bool tune_on = false;
   std::map<long long, Tune> tune;
@@ -961,7 +969,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   for (int g = 0; g < n; ++g) {
     spc_min = std::max(spc_min, b->mesh[g].prm.pcg_cta_slices);
     if (b->mesh[g].prm.pcg_cta_slices < 0) b->tune_on = true;
-    if (b->mesh[g].prm.pcg_plan == 1) b->force_stream = true;
+    b->plan_mode = std::max(b->plan_mode, (int)b->mesh[g].prm.pcg_plan);
   }
   if (spc_min <= 0) spc_min = b->mixed ? PCG_SLICES_MIXED : PCG_SLICES_FP64;
   b->pcg_spc_min = spc_min;
@@ -1553,10 +1561,10 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
     const int occ_res = pcg_res_ctas_per_sm(b->mixed, max_slices, b->pcg_wmax);
     // a multi-CTA group reduces three quantities at once, one warp each: two slice warps and the
     // control warp at least
-    res = !b->force_stream && occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC &&
+    res = b->plan_mode == 0 && occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC &&
           (max_nc == 1 || max_slices >= 2);
-    // without a resident plan within a slice per warp the pooled kernels take the set
-    if (res || b->force_stream || max_slices > PCG_RES_MAXS) break;
+    const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
+    if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
     if (attempt > 400) {
       set_last_error("PCG partition does not fit the device");
       return TX_ERR_ARG;
@@ -1567,7 +1575,9 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
   cudaStream_t st = b->st;
   // pageable sources: the copies take the data when enqueued, the vectors can be reused at once.
   // (the pooled kernels need no CTA plan)
-  if (res) {
+  // the pooled form (streaming, many gels or asked for) needs no CTA plan
+  part.pool_on = !res && (b->plan_mode == 2 || (b->plan_mode == 0 && (int)set.size() >= PCG_POOL_MIN_GELS));
+  if (!part.pool_on) {
     if (nctas > b->pcg_cta_cap) {
       set_last_error("PCG partition does not fit the device");
       return TX_ERR_ARG;
@@ -1580,7 +1590,7 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
   part.plan.ngroups = (int)grp.size();
   part.nctas = nctas;
   part.res = res;
-  if (!res) {  // streaming: the pooled kernels over the set's gel range, every SM
+  if (part.pool_on) {  // the pooled kernels over the set's gel range, one CTA per SM
     part.pool.g0 = set.front();
     part.pool.ng = set.back() - set.front() + 1;
     long long tot = 0;  // slices of the gel range: bounds every CTA's share
@@ -1710,12 +1720,14 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
       if (P.res)
         CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, true, pcg_max, refine, b->pcg_wmax, st));
       else
-        CK(launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, true, pcg_max, refine, st));
+        CK(P.pool_on ? launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, true, pcg_max, refine, st)
+                     : launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, pcg_max, refine, st));
     } else {
       if (P.res)
         CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, pcg_max, 0, b->pcg_wmax, st));
       else
-        CK(launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, false, pcg_max, 0, st));
+        CK(P.pool_on ? launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, false, pcg_max, 0, st)
+                     : launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, pcg_max, st));
     }
   }
   prof_close(b, b->nparts);
@@ -1878,7 +1890,10 @@ tx_status do_newton(tx_batch* b) {
     }
   s = run_newton_launches(b, set, pcg_max, refine, accd_max);
   if (s != TX_OK) return s;
-  for (int k = 0; k < b->nparts; ++k) (b->parts[k].res ? b->prof.pcg_res : b->prof.pcg_stream) += 1;
+  for (int k = 0; k < b->nparts; ++k) {
+    (b->parts[k].res ? b->prof.pcg_res : b->prof.pcg_stream) += 1;
+    if (b->parts[k].pool_on) b->prof.pcg_pool += 1;
+  }
   s = post_pcg_finish(b);
   if (s != TX_OK) return s;
   tune_record(b, set);
@@ -2532,6 +2547,7 @@ tx_status tx_batch_profile(tx_batch* b, int32_t enable, tx_profile* out) {
     out->newton_iters = b->prof.newton_iters;
     out->pcg_resident_launches = b->prof.pcg_res;
     out->pcg_streaming_launches = b->prof.pcg_stream;
+    out->pcg_pool_launches = b->prof.pcg_pool;
     out->kernel_launches = g_launch_count.load() - g_launch_mark;
   }
   g_launch_mark = g_launch_count.load();

@@ -38,14 +38,15 @@ def test_struct_layout_matches_c(tmp_path):
     from paper_2411_04776_gb300 import binding as B
     c = tmp_path / "sz.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tx_gel.h"\n'
-                 'int main(){printf("%zu %zu %zu %zu %zu %zu\\n",sizeof(tx_params),sizeof(tx_gel_desc),'
+                 'int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n",sizeof(tx_params),sizeof(tx_gel_desc),'
                  'sizeof(tx_step_stats),offsetof(tx_gel_desc,params),offsetof(tx_gel_desc,ind_pose),'
-                 'offsetof(tx_step_stats,energy));}\n')
+                 'offsetof(tx_step_stats,energy),sizeof(tx_profile),offsetof(tx_profile,pcg_pool_launches));}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(B.tx_params), ctypes.sizeof(B.tx_gel_desc), ctypes.sizeof(B.tx_step_stats),
-            B.tx_gel_desc.params.offset, B.tx_gel_desc.ind_pose.offset, B.tx_step_stats.energy.offset]
+            B.tx_gel_desc.params.offset, B.tx_gel_desc.ind_pose.offset, B.tx_step_stats.energy.offset,
+            ctypes.sizeof(B.tx_profile), B.tx_profile.pcg_pool_launches.offset]
     assert got == want
 
 

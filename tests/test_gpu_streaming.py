@@ -1,10 +1,11 @@
-"""Parity of the pooled streaming PCG kernels (k_pcg64_pool in FP64, k_pcg_mixed_pool in mixed
-precision: the matrix streamed from HBM every iteration, the kernels the large batched
-configurations run) on a batch of gels of uneven size, one from each of the three grids, so that
-the small gels finish their solves while the large one still iterates and the pool re-splits the
-remaining slices: every gel against the FP64 oracle and against the same gel stepped alone (which
-takes the resident kernels).  The streaming family is selected with tx_params.pcg_plan = 1; the
-test checks through the profile counters that no resident launch ran."""
+"""Parity of the streaming PCG kernels (the matrix streamed from HBM every iteration, the kernels
+the large batched configurations run) in both forms: per-gel CTA groups (k_pcg64 in FP64,
+k_pcg_mixed in mixed precision; tx_params.pcg_plan = 1) and the pool of one CTA per SM
+(k_pcg64_pool, k_pcg_mixed_pool; pcg_plan = 2), on a batch of gels of uneven size, one from each of
+the three grids, so that the small gels finish their solves while the large one still iterates
+(the pool re-splits the remaining slices): every gel against the FP64 oracle and against the same
+gel stepped alone (which takes the resident kernels).  The profile counters show that only the
+asked-for form ran."""
 import numpy as np
 import pytest
 
@@ -75,19 +76,22 @@ def run_alone(w, precision):
     return out
 
 
+@pytest.mark.parametrize("plan", [1, 2], ids=["groups", "pool"])
 @pytest.mark.parametrize("precision", [B.TX_PREC_FP64, B.TX_PREC_MIXED], ids=["fp64", "mixed"])
-def test_streaming_batch_matches_oracle_and_alone(reference, precision):
+def test_streaming_batch_matches_oracle_and_alone(reference, precision, plan):
     wls, ref = reference
-    out, prof = run_batch(wls, precision, plan=1)
+    out, prof = run_batch(wls, precision, plan=plan)
     assert prof["pcg_streaming_launches"] > 0 and prof["pcg_resident_launches"] == 0, prof
+    # plan 1: the per-gel CTA groups only; plan 2: the pool only
+    assert prof["pcg_pool_launches"] == (prof["pcg_streaming_launches"] if plan == 2 else 0), prof
     worst = np.zeros(3)
     for s in range(STEPS):
         for g in (0, 1):
             worst[g] = max(worst[g], np.abs(out[s][g] - ref[g][s]).max())
         if s in ref[2]:
             worst[2] = max(worst[2], np.abs(out[s][2] - ref[2][s]).max())
-    print("streaming PCG (%s) vs oracle, max vertex error per gel [m]: %s"
-          % ("fp64" if precision == B.TX_PREC_FP64 else "mixed", worst))
+    print("streaming PCG (%s, %s) vs oracle, max vertex error per gel [m]: %s"
+          % ("fp64" if precision == B.TX_PREC_FP64 else "mixed", "pool" if plan == 2 else "groups", worst))
     assert np.all(worst <= POS_TOL), worst
     for g, w in enumerate(wls):
         alone = run_alone(w, precision)
