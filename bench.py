@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--reference-budget", type=float, default=200.0, help="seconds of timed oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
+    ap.add_argument("--pcg-plan", type=int, default=0, choices=[0, 1, 2],
+                    help="PCG kernel family (tx_params.pcg_plan): 0 automatic, 1 per-gel-group streaming, 2 pooled")
     ap.add_argument("--pcg-cta-slices", type=int, default=0,
                     help="PCG work split: 32-row slices per CTA at least (0: library default, -1: autotune; "
                          "the autotuner measured no gain on the default workloads)")
@@ -183,6 +185,8 @@ def run_gpu(args, rank, world, e2e=True):
     T = min(len(w.poses) for w in wls)
     assert Wm + K <= T, f"the trajectories have {T} steps"
     kw = {k: getattr(args, k) for k in ("pcg_rel_tol", "pcg_rel_tol_far") if getattr(args, k) is not None}
+    if getattr(args, "pcg_plan", 0):
+        kw["pcg_plan"] = args.pcg_plan
     descs = [B.GelDesc.from_workload(w, precision=prec, pcg_cta_slices=args.pcg_cta_slices, **kw) for w in wls]
     single = len(wls) == 1
     if single:
