@@ -96,6 +96,14 @@ typedef struct tx_params {
                                dynamic friction)                                               */
   double friction_eps_v;    /* velocity below which friction acts as a stiff spring (static
                                friction) [m/s] (default 1e-3)                                  */
+  double kappa_adapt_max;   /* adaptive barrier stiffness (IPC's kappa update, applied between
+                               steps: the indenter is placed before each solve, so pairs close in
+                               between steps): 0 keeps kappa fixed (the default); else, after a
+                               step whose final smallest pair distance is below kappa_adapt_dmin
+                               and below that of the step before, kappa doubles for the next
+                               steps, up to kappa_adapt_max times its initial value (>= 1).
+                               Reset and set_state return kappa to its initial value           */
+  double kappa_adapt_dmin;  /* that distance threshold [m] (> 0 when kappa_adapt_max > 0)     */
 } tx_params;
 
 void tx_params_default(tx_params* p);
@@ -134,6 +142,7 @@ typedef struct tx_step_stats {
   double min_distance;      /* smallest candidate-pair distance at the final state [m]          */
   double contact_force[3];  /* force of the indenter on the gel, -kappa sum grad b [N]           */
   double mean_position[3];  /* mean of the gel vertex positions (TacEx "object position") [m]    */
+  double kappa;             /* barrier stiffness for the next step [N/m] (tx_params.kappa_adapt_max) */
 } tx_step_stats;
 
 typedef struct tx_gel tx_gel;     /* opaque single-gel handle                                  */

@@ -104,6 +104,12 @@ def _declare(L):
     L.or_stationary_rule.argtypes = [ctypes.c_double, ctypes.c_double]
     L.or_last_stationary.restype = ctypes.c_int
     L.or_last_stationary.argtypes = [ctypes.c_void_p]
+    L.or_last_kappa_doublings.restype = ctypes.c_int
+    L.or_last_kappa_doublings.argtypes = [ctypes.c_void_p]
+    L.or_kappa.restype = ctypes.c_double
+    L.or_kappa.argtypes = [ctypes.c_void_p]
+    L.or_set_kappa_adapt.restype = None
+    L.or_set_kappa_adapt.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
     L.or_set_threads.argtypes = [ctypes.c_int]
     L.or_get_threads.restype = ctypes.c_int
     L.or_friction_pair.restype = ctypes.c_int
@@ -134,7 +140,7 @@ class OracleGel:
     def __init__(self, verts, tets, dirichlet, material, ind_verts, ind_tris, pose0, dhat=1e-4,
                  kappa=0.0, newton_tol=1e-5, pcg_tol=1e-10, gravity=(0.0, 0.0, 0.0),
                  newton_max=200, pcg_max=200000, ls_max=80, accd_max=1000000, split_depth=4,
-                 friction=0.0, eps_v=1e-3):
+                 friction=0.0, eps_v=1e-3, kappa_adapt_max=0.0, kappa_adapt_dmin=0.0):
         L = lib()
         self.N = int(len(verts))
         self.M = int(len(ind_verts))
@@ -155,6 +161,8 @@ class OracleGel:
             raise OracleError(st.value)
         if friction > 0.0:  # IPC lagged friction (coefficient, velocity threshold [m/s])
             L.or_set_friction(self._h, float(friction), float(eps_v))
+        if kappa_adapt_max > 0.0:  # adaptive kappa: cap (multiple of kappa0), threshold distance [m]
+            L.or_set_kappa_adapt(self._h, float(kappa_adapt_max), float(kappa_adapt_dmin))
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -177,7 +185,9 @@ class OracleGel:
         info = dict(status=s, newton_iters=int(stats[0]), pcg_iters=int(stats[1]),
                     ls_halvings=int(stats[2]), substeps=int(stats[3]), active_pairs=int(stats[4]),
                     energy=float(fst[0]), min_distance=float(fst[1]),
-                    stationary=int(lib().or_last_stationary(self._h)))
+                    stationary=int(lib().or_last_stationary(self._h)),
+                    kappa_doublings=int(lib().or_last_kappa_doublings(self._h)),
+                    kappa=float(lib().or_kappa(self._h)))
         return info
 
     def step_attached(self, pose, case_pose, dt):

@@ -681,6 +681,11 @@ struct Gel {
   double fric_mu = 0.0, fric_epsv = 1e-3;  // friction coefficient (0: none), velocity threshold [m/s]
   std::vector<struct FricPair> fric;        // lagged friction pairs of the running (sub)step
   double fric_eh = 0.0;                     // eps_v h of the running (sub)step
+  // adaptive barrier stiffness (READING R5b): kappa is part of the state; after a step whose final
+  // closest pair is nearer than kappa_dmin and nearer than at the end of the step before, kappa
+  // doubles (up to kappa_cap) for the steps that follow; reset and set_state return to kappa0
+  // (kappa_cap = 0: kappa stays kappa0)
+  double kappa0 = 0.0, kappa_cap = 0.0, kappa_dmin = 0.0, dmin_last = INF;
   // state
   std::vector<double> x, v;
   double pose[7] = {1, 0, 0, 0, 0, 0, 0};
@@ -689,6 +694,7 @@ struct Gel {
   // stats of the last step
   int st_newton = 0, st_pcg = 0, st_ls = 0, st_substeps = 0, st_pairs = 0;
   int st_stationary = 0;  // solves of the last step ended by the stationarity rule (READING R8b)
+  int st_kappa_doublings = 0;  // doublings of kappa after the last step (READING R5b)
   double st_energy = 0, st_min_d = INF;
 };
 
@@ -1565,6 +1571,7 @@ void* or_create(int N, const double* X, int T, const int* tets, const uint8_t* d
   }
   G->dhat = fparams[0];
   G->kappa = fparams[1] > 0 ? fparams[1] : E * (edges.empty() ? 0.0 : lsum / edges.size());
+  G->kappa0 = G->kappa;
   G->newton_tol = fparams[2];
   G->pcg_tol = fparams[3];
   for (int c = 0; c < 3; ++c) G->grav[c] = fparams[4 + c];
@@ -1601,6 +1608,7 @@ int or_step(void* g, const double* pose, double dt, int* stats, double* fstats) 
 int or_step_attached(void* g, const double* pose, const double* case_pose, double dt, int* stats, double* fstats) {
   Gel& G = *static_cast<Gel*>(g);
   G.st_newton = G.st_pcg = G.st_ls = G.st_substeps = G.st_pairs = G.st_stationary = 0;
+  G.st_kappa_doublings = 0;
   G.st_energy = 0;
   G.st_min_d = INF;
   std::vector<double> x0 = G.x, v0 = G.v;
@@ -1614,6 +1622,17 @@ int or_step_attached(void* g, const double* pose, const double* case_pose, doubl
     std::memcpy(G.pose, p0, sizeof(p0));
   } else if (case_pose) {
     std::memcpy(G.case_pose, case_pose, sizeof(G.case_pose));
+  }
+  if (s == OK) {
+    // READING R5b (IPC's adaptive barrier stiffness at step granularity: the kinematic indenter is
+    // placed before the solve, so pairs close in between steps, not across Newton iterates): a
+    // final closest pair nearer than kappa_dmin that came nearer than at the end of the step before
+    // doubles kappa for the next steps
+    if (G.kappa_cap > 0.0 && G.st_min_d < G.kappa_dmin && G.st_min_d < G.dmin_last && G.kappa < G.kappa_cap) {
+      G.kappa = std::min(2.0 * G.kappa, G.kappa_cap);
+      G.st_kappa_doublings = 1;
+    }
+    G.dmin_last = G.st_min_d;
   }
   if (stats) {
     stats[0] = G.st_newton;
@@ -1639,6 +1658,8 @@ void or_get_state(void* g, double* x, double* v, double* fc, double* pose) {
 
 void or_set_state(void* g, const double* x, const double* v, const double* pose) {
   Gel& G = *static_cast<Gel*>(g);
+  G.kappa = G.kappa0;  // READING R5b
+  G.dmin_last = INF;
   if (x) G.x.assign(x, x + 3 * G.N);
   if (v) G.v.assign(v, v + 3 * G.N);
   if (pose) std::memcpy(G.pose, pose, sizeof(G.pose));
@@ -1646,6 +1667,8 @@ void or_set_state(void* g, const double* x, const double* v, const double* pose)
 
 void or_reset(void* g) {
   Gel& G = *static_cast<Gel*>(g);
+  G.kappa = G.kappa0;  // READING R5b
+  G.dmin_last = INF;
   G.x = G.X;
   G.v.assign(3 * G.N, 0.0);
   const double id[7] = {1, 0, 0, 0, 0, 0, 0};
@@ -1939,6 +1962,14 @@ int or_stationary_rule(double gp, double E) { return stationary_to_resolution(gp
 // Solves of the last step that ended by the stationarity rule (READING R8b: the line search
 // found no resolvable decrease and -g.p <= 1e-10 |E|).
 int or_last_stationary(void* g) { return static_cast<Gel*>(g)->st_stationary; }
+int or_last_kappa_doublings(void* g) { return static_cast<Gel*>(g)->st_kappa_doublings; }
+double or_kappa(void* g) { return static_cast<Gel*>(g)->kappa; }
+// READING R5b: adaptive kappa with cap = scale * kappa0 (scale <= 0: off) and threshold dmin [m]
+void or_set_kappa_adapt(void* g, double scale, double dmin) {
+  Gel& G = *static_cast<Gel*>(g);
+  G.kappa_cap = scale > 0.0 ? scale * G.kappa0 : 0.0;
+  G.kappa_dmin = dmin;
+}
 
 // Threads of the parallel loops (n <= 0: all available); results do not depend on it.
 void or_set_threads(int n) {

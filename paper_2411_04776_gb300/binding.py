@@ -37,7 +37,8 @@ class tx_params(ctypes.Structure):
                 ("max_split_depth", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("pcg_cta_slices", ctypes.c_int32),
                 ("pcg_plan", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("friction", ctypes.c_double), ("friction_eps_v", ctypes.c_double)]
+                ("friction", ctypes.c_double), ("friction_eps_v", ctypes.c_double),
+                ("kappa_adapt_max", ctypes.c_double), ("kappa_adapt_dmin", ctypes.c_double)]
 
 
 class tx_gel_desc(ctypes.Structure):
@@ -54,7 +55,8 @@ class tx_step_stats(ctypes.Structure):
                 ("active_pairs", ctypes.c_int32), ("candidate_pairs", ctypes.c_int32),
                 ("refine_rounds", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("energy", ctypes.c_double), ("min_distance", ctypes.c_double),
-                ("contact_force", ctypes.c_double * 3), ("mean_position", ctypes.c_double * 3)]
+                ("contact_force", ctypes.c_double * 3), ("mean_position", ctypes.c_double * 3),
+                ("kappa", ctypes.c_double)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k in ("contact_force", "mean_position") else getattr(self, k))

@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
   PairBarrier pb;
   if (!pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), pb)) return;
   atomicAdd(&d.gv[g].active_pairs, 1);
-  const double kap = G.kappa;
+  const double kap = d.gc[g].kappa;  // the step's barrier stiffness (host-set, adaptive)
   int slots[4], ns = 0;
   for (int k = 0; k < 4; ++k)
     if (rows[k] >= 0 && (pb.involved >> k) & 1) slots[ns++] = k;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d, int mode)
     }
     if (mode == 0 && tm.id == 0) d.chbp[(size_t)k * CH_BP] = ns;
     __syncwarp();
-    const double kap = d.gi[g].kappa;
+    const double kap = d.gc[g].kappa;
     for (int e = tm.id; e < nf * nf; e += 32) {
       const int r = e / nf, c = e - r * nf;
       const double v = kap * w.pj.H[r * m + c];
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(128) k_fric_setup(Dev d, int phase) {
     const double ex = pair_eps_x(d, pr), q = dot3(n, n) / ex;
     if (q < 1.0) mol = q * (2.0 - q);
   }
-  f.lam = G.kappa * mol * fabs(2.0 * sqrt(D) * bD);  // |b'(d)| = |2 d dB/dD|
+  f.lam = d.gc[g].kappa * mol * fabs(2.0 * sqrt(D) * bD);  // |b'(d)| = |2 d dB/dD|
   double w[4] = {0.0, 0.0, 0.0, 0.0}, nrm[3];
   const int* id = ty.i;
   if (ty.f == DF_PP) {
@@ -1015,7 +1015,7 @@ __global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* p
       double P[4][3], dist;
       int rows[4];
       pair_points(d, pr, alpha, false, P, rows);
-      acc += G.kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+      acc += d.gc[g].kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
     }
   } else if (phase != PH_EVAL) {  // lagged friction records of the running (sub)step
     for (int i = pc.z * EN_T + threadIdx.x; i < v.nfric; i += pc.w * EN_T) {

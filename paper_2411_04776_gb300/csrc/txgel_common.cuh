@@ -75,6 +75,7 @@ struct GelCtl {  // per gel, written by the host before the launches of an itera
   int pad2_;
   double Rc[9], tc[3];
   double Rcp[9], tcp[3];
+  double kappa;              // barrier stiffness of the step (the host's adaptive rule)
 };
 
 struct GelVar {  // per gel, written by the device

@@ -188,7 +188,8 @@ tx_status check_desc(const tx_gel_desc* d) {
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
       p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 2 || p.reserved0 != 0 || !(p.friction >= 0.0) ||
-      !(p.friction_eps_v > 0.0))
+      !(p.friction_eps_v > 0.0) || !(p.kappa_adapt_max == 0.0 || (p.kappa_adapt_max >= 1.0 && std::isfinite(p.kappa_adapt_max))) ||
+      (p.kappa_adapt_max > 0.0 && !(p.kappa_adapt_dmin > 0.0 && std::isfinite(p.kappa_adapt_dmin))))
     return TX_ERR_ARG;
   for (int k = 0; k < 4 * d->n_tets; ++k)
     if (d->tets[k] < 0 || d->tets[k] >= d->n_verts) return TX_ERR_ARG;
@@ -420,6 +421,10 @@ struct Run {
   double pose_req[7];       // pose at the start of the request (for rollback)
   double case_pose[7] = {1, 0, 0, 0, 0, 0, 0};  // pose of the attached vertices' frame (the sensor case)
   double case_req[7] = {1, 0, 0, 0, 0, 0, 0};   // ... at the start of the request (for rollback)
+  // barrier stiffness of the next step and the final smallest pair distance of the last step
+  // (tx_params.kappa_adapt_max: doubled after a step that ended nearer than kappa_adapt_dmin and
+  // nearer than the step before)
+  double kappa = 0.0, dmin_last = 1e300;
 };
 
 }  // namespace
@@ -1175,6 +1180,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   if (s == TX_OK && cudaDeviceSynchronize() != cudaSuccess) s = TX_ERR_CUDA;
   if (s != TX_OK) return fail_create(s);
   b->run.resize(n);
+  for (int g = 0; g < n; ++g) b->run[g].kappa = b->gc_h[g].kappa = b->mesh[g].kappa;
   b->nnzb_real.assign(n, 0.0);
   b->nfree.assign(n, 0.0);
   for (int g = 0; g < n; ++g) {
@@ -1195,6 +1201,7 @@ void fill_ctl(tx_batch* b, int g, int phase, const Task& t) {
   GelCtl& c = b->gc_h[g];
   const Mesh& m = b->mesh[g];
   c.phase = phase;
+  c.kappa = b->run[g].kappa;
   c.h = t.dt;
   c.tol_p = m.prm.newton_tol * m.bbox * t.dt;
   const double far = std::max(m.prm.pcg_rel_tol_far, m.prm.pcg_rel_tol);
@@ -1221,6 +1228,7 @@ void fill_ctl(tx_batch* b, int g, int phase, const Task& t) {
 void finish_request(tx_batch* b, int g, tx_status s) {
   Run& R = b->run[g];
   R.acc.status = s;
+  R.acc.kappa = R.kappa;
   R.last = R.acc;
   R.in_request = false;
   R.stack.clear();
@@ -1477,7 +1485,18 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
     std::memcpy(R.pose, t.pb, sizeof(double) * 7);
     if (t.attached) std::memcpy(R.case_pose, t.cb, sizeof(double) * 7);
     R.phase = PH_IDLE;
-    if (R.stack.empty()) finish_request(b, g, TX_OK);
+    if (R.stack.empty()) {
+      // adaptive barrier stiffness (IPC's kappa update at step granularity: the indenter is placed
+      // before each solve, so pairs close in between steps): a step that ended nearer than
+      // kappa_adapt_dmin, and nearer than the step before, doubles kappa for the next steps
+      const tx_params& P = b->mesh[g].prm;
+      if (P.kappa_adapt_max > 0.0) {
+        const double dfin = R.acc.min_distance, cap = P.kappa_adapt_max * b->mesh[g].kappa;
+        if (dfin < P.kappa_adapt_dmin && dfin < R.dmin_last && R.kappa < cap) R.kappa = std::min(2.0 * R.kappa, cap);
+        R.dmin_last = dfin;
+      }
+      finish_request(b, g, TX_OK);
+    }
   }
   for (int g = 0; g < b->n; ++g) b->gc_h[g].phase = b->run[g].phase == PH_NEWTON ? PH_NEWTON : PH_IDLE;
   return upload_ctl(b);
@@ -2157,6 +2176,8 @@ void tx_params_default(tx_params* p) {
   p->pcg_cta_slices = 0;
   p->friction = 0.0;
   p->friction_eps_v = 1e-3;
+  p->kappa_adapt_max = 0.0;
+  p->kappa_adapt_dmin = 0.0;
 }
 
 const char* tx_status_str(tx_status s) {
@@ -2303,6 +2324,8 @@ tx_status tx_batch_set_state(tx_batch* b, int32_t g, const double* x, const doub
   CK(cudaMemsetAsync(b->d.p + G.v0, 0, sizeof(double4_32a) * G.ns * SLICE, b->st));
   CK(cudaStreamSynchronize(b->st));
   if (pose) std::memcpy(b->run[g].pose, pose, sizeof(double) * 7);
+  b->run[g].kappa = b->mesh[g].kappa;  // a new state: the initial barrier stiffness
+  b->run[g].dmin_last = 1e300;
   return TX_OK;
 }
 
@@ -2317,6 +2340,8 @@ tx_status tx_batch_reset(tx_batch* b, int32_t g) {
   const double ident[7] = {1, 0, 0, 0, 0, 0, 0};
   std::memcpy(b->run[g].case_pose, ident, sizeof(ident));  // the attached vertices are back at rest
   b->run[g].last = tx_step_stats{};
+  b->run[g].kappa = b->mesh[g].kappa;
+  b->run[g].dmin_last = 1e300;
   return TX_OK;
 }
 

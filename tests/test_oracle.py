@@ -901,3 +901,40 @@ def test_stationarity_rule_both_sides():
         assert O.stationary_rule(0.0, E)
         assert not O.stationary_rule(-2.0 * tol, E)
         assert not O.stationary_rule(-1e3 * tol, E)
+
+
+# ---------------- adaptive barrier stiffness (READING R5b) ----------------
+def _weak_barrier_run(adapt, steps):
+    """The sphere press of the 10x13x4 gel with kappa at 1 % of the fixed rule (the indenter's
+    next placement eventually meets a gel surface the weak barrier let come too close)."""
+    wl = W.small_gel_sphere(1)
+    k0 = O.OracleGel.from_workload(wl).info()["kappa"] * 0.01
+    og = O.OracleGel.from_workload(wl, kappa=k0, kappa_adapt_max=adapt, kappa_adapt_dmin=1e-5)
+    infos = []
+    for s in range(steps):
+        infos.append(og.step(wl.poses[s], wl.dt))
+        if infos[-1]["status"] != 0:
+            break
+    return og, k0, infos
+
+
+def test_adaptive_kappa_carries_a_press_a_weak_fixed_barrier_cannot():
+    O.set_threads(2)
+    _, k0, fixed = _weak_barrier_run(0.0, 6)
+    assert [i["status"] for i in fixed] == [0, 0, 0, 0, 4], fixed[-1]  # TX_ERR_INFEASIBLE at step 4
+    assert all(i["kappa"] == k0 and i["kappa_doublings"] == 0 for i in fixed)
+    og, k0, ad = _weak_barrier_run(100.0, 8)
+    assert all(i["status"] == 0 for i in ad), ad[-1]
+    # kappa = k0 2^n, at most 100 k0, and it doubled after a step exactly when that step ended nearer
+    # than 10 um and nearer than the step before (the first step has no predecessor)
+    prev_d, kap = math.inf, k0
+    for i in ad:
+        want = i["min_distance"] < 1e-5 and i["min_distance"] < prev_d and kap < 100.0 * k0
+        assert i["kappa_doublings"] == int(want), i
+        kap = min(2.0 * kap, 100.0 * k0) if want else kap
+        assert abs(i["kappa"] - kap) <= 1e-12 * kap, (i["kappa"], kap)
+        prev_d = i["min_distance"]
+    assert sum(i["kappa_doublings"] for i in ad) >= 3
+    og.reset()  # reset returns kappa to its initial value
+    wl = W.small_gel_sphere(1)
+    assert og.step(wl.poses[0], wl.dt)["kappa"] == k0
