@@ -65,11 +65,11 @@ def run_batch(wls, precision, plan):
     return out, prof
 
 
-def run_alone(w, precision):
+def run_alone(w, precision, steps=STEPS):
     gel = B.Gel.from_workload(w, newton_tol=PARITY_NEWTON_TOL, precision=precision, newton_max_iter=400,
                               stream=torch.cuda.current_stream())
     out = []
-    for s in range(STEPS):
+    for s in range(steps):
         assert gel.step(w.poses[s], w.dt) == 0
         out.append(gel.state()[0])
     gel.close()
@@ -97,3 +97,34 @@ def test_streaming_batch_matches_oracle_and_alone(reference, precision, plan):
         alone = run_alone(w, precision)
         d = max(np.abs(alone[s] - out[s][g]).max() for s in range(STEPS))
         assert d <= POS_TOL, (g, d)
+
+
+def test_automatic_plan_pools_a_large_batch_and_each_gel_matches_alone():
+    """32 gels of the 21x26x5 grid, each with its own seeded indenter: too many slices for the
+    resident kernels and enough gels for the automatic plan to take the pool; every gel of the
+    batch against the same gel stepped alone (resident kernels)."""
+    wls = [W.mini_gel(seed=s, grid=W.GRID_MID, depth=0.5e-3, n_press=20, slide=0.0, n_slide=0) for s in range(32)]
+    steps = 8
+    descs = [B.GelDesc.from_workload(w, newton_tol=PARITY_NEWTON_TOL, newton_max_iter=400) for w in wls]
+    b = B.tx_batch_create(descs, stream=torch.cuda.current_stream())
+    B.tx_batch_profile(b, True)
+    out = []
+    try:
+        for s in range(steps):
+            st, sts = B.tx_batch_step(b, np.stack([w.poses[s] for w in wls]), np.array([w.dt for w in wls]))
+            assert st == 0 and np.all(sts == 0), sts
+        out = [B.tx_batch_state(b, g, len(w.gel.verts))[0] for g, w in enumerate(wls)]
+        contact = [B.tx_batch_state(b, g, len(w.gel.verts))[3].active_pairs for g, w in enumerate(wls)]
+        prof = B.tx_batch_profile(b, False)
+    finally:
+        B.tx_batch_destroy(b)
+    # the pool while 32 gels iterate; Newton rounds of fewer gels (the others converged) may take the
+    # per-gel groups or the resident kernels
+    assert prof["pcg_pool_launches"] > 0 and prof["pcg_pool_launches"] <= prof["pcg_streaming_launches"], prof
+    assert sum(c > 0 for c in contact) >= 8, contact  # the gels are in contact by then
+    worst = 0.0
+    for g in range(0, 32, 4):  # every fourth gel alone (the others ran in the same launches)
+        alone = run_alone(wls[g], B.TX_PREC_FP64, steps)
+        worst = max(worst, float(np.abs(alone[steps - 1] - out[g]).max()))
+    print("pooled batch of 32 gels vs alone: max vertex difference %.3e m" % worst)
+    assert worst <= POS_TOL, worst
