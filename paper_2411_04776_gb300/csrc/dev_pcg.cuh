@@ -28,16 +28,17 @@ __device__ __forceinline__ double4_32a spmv_row64(const Dev& d, int s, int lane,
     const int bp = o + 32 * k + lane;
     const int c = __ldg(d.colidx + bp);
     const double4_32a uc = u[c];
-    const double* v = d.vals + (size_t)9 * (o + 32 * k) + lane;
+    double v[9];
+    load_block64(d.vals + (size_t)9 * (o + 32 * k), lane, v);
     a0 = fma(v[0], uc.x, a0);
-    a1 = fma(v[96], uc.x, a1);
-    a2 = fma(v[192], uc.x, a2);
-    a0 = fma(v[32], uc.y, a0);
-    a1 = fma(v[128], uc.y, a1);
-    a2 = fma(v[224], uc.y, a2);
-    a0 = fma(v[64], uc.z, a0);
-    a1 = fma(v[160], uc.z, a1);
-    a2 = fma(v[256], uc.z, a2);
+    a1 = fma(v[3], uc.x, a1);
+    a2 = fma(v[6], uc.x, a2);
+    a0 = fma(v[1], uc.y, a0);
+    a1 = fma(v[4], uc.y, a1);
+    a2 = fma(v[7], uc.y, a2);
+    a0 = fma(v[2], uc.z, a0);
+    a1 = fma(v[5], uc.z, a1);
+    a2 = fma(v[8], uc.z, a2);
   }
   return make_double4_32a(a0, a1, a2, 0.0);
 }

@@ -532,9 +532,6 @@ __device__ __forceinline__ int find_block(const Dev& d, int row, int col) {
   }
   return -1;
 }
-__device__ __forceinline__ size_t val_addr(int bp, int e) {
-  return (size_t)9 * (bp & ~31) + 32 * e + (bp & 31);
-}
 
 // Contact assembly, part 1: one thread per candidate slot.  Active pairs (d < dhat) add their
 // barrier gradient and the contact force; a pair whose value depends on a single gel point adds
@@ -611,9 +608,9 @@ struct ContactWS {
 template <bool MIXED>
 __device__ __forceinline__ void add_val(const Dev& d, int bp, int e, double v) {
   if (MIXED)
-    atomicAdd(&d.vals32[val_addr(bp, e)], (float)v);
+    atomicAdd(&d.vals32[val_addr32(bp, e)], (float)v);
   else
-    atomicAdd(&d.vals[val_addr(bp, e)], v);
+    atomicAdd(&d.vals[val_addr64(bp, e)], v);
 }
 
 template <bool MIXED>

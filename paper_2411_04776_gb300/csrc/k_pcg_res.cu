@@ -44,19 +44,24 @@ __device__ __forceinline__ int res_load(const Dev& d, int s, const V* gval, V* s
   return w;
 }
 
-// one block of the lane's row: a += A_k uc (values from the slice image in shared memory)
+// one block of the lane's row: a += A_k uc (values from the slice image in shared memory, in the
+// sliced BSR's value layout: pairs of FP64 or quads of FP32 per 16-byte load)
 template <typename V, typename U, typename A>
 __device__ __forceinline__ void res_block(const V* sv, int k, int lane, const U uc, A& a0, A& a1, A& a2) {
-  const V* v = sv + 288 * k + lane;
+  V v[9];
+  if constexpr (sizeof(V) == 8)
+    load_block64(reinterpret_cast<const double*>(sv) + 288 * k, lane, reinterpret_cast<double*>(v));
+  else
+    load_block32(reinterpret_cast<const float*>(sv) + 288 * k, lane, reinterpret_cast<float*>(v));
   a0 = fma((A)v[0], (A)uc.x, a0);
-  a1 = fma((A)v[96], (A)uc.x, a1);
-  a2 = fma((A)v[192], (A)uc.x, a2);
-  a0 = fma((A)v[32], (A)uc.y, a0);
-  a1 = fma((A)v[128], (A)uc.y, a1);
-  a2 = fma((A)v[224], (A)uc.y, a2);
-  a0 = fma((A)v[64], (A)uc.z, a0);
-  a1 = fma((A)v[160], (A)uc.z, a1);
-  a2 = fma((A)v[256], (A)uc.z, a2);
+  a1 = fma((A)v[3], (A)uc.x, a1);
+  a2 = fma((A)v[6], (A)uc.x, a2);
+  a0 = fma((A)v[1], (A)uc.y, a0);
+  a1 = fma((A)v[4], (A)uc.y, a1);
+  a2 = fma((A)v[7], (A)uc.y, a2);
+  a0 = fma((A)v[2], (A)uc.z, a0);
+  a1 = fma((A)v[5], (A)uc.z, a1);
+  a2 = fma((A)v[8], (A)uc.z, a2);
 }
 
 // y = A u for the lane's row: values from shared memory, u gathered from global memory (L2)

@@ -89,7 +89,6 @@ void launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- gather (assembly)
-__device__ __forceinline__ size_t vaddr(int bp, int e) { return (size_t)9 * (bp & ~31) + 32 * e + (bp & 31); }
 
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
@@ -165,12 +164,20 @@ __global__ void __launch_bounds__(256) k_gather(Dev d, int phase, int nbp) {
     d.grad[r] = go;
   }
   (void)c;
+  // the block in the slice's value layout (val_addr64 / val_addr32): 16-byte stores of its pairs
+  // (FP64) or quads (FP32), then the ninth element
+  const int l = bp & 31;
+  if (MIXED) {
+    float* b = d.vals32 + (size_t)9 * (bp & ~31);
+    *reinterpret_cast<float4*>(b + 4 * l) = make_float4((float)h[0], (float)h[1], (float)h[2], (float)h[3]);
+    *reinterpret_cast<float4*>(b + 128 + 4 * l) = make_float4((float)h[4], (float)h[5], (float)h[6], (float)h[7]);
+    b[256 + l] = (float)h[8];
+  } else {
+    double* b = d.vals + (size_t)9 * (bp & ~31);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    if (MIXED)
-      d.vals32[vaddr(bp, e)] = (float)h[e];
-    else
-      d.vals[vaddr(bp, e)] = h[e];
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<double2*>(b + 64 * q + 2 * l) = make_double2((double)h[2 * q], (double)h[2 * q + 1]);
+    b[256 + l] = (double)h[8];
   }
 }
 
@@ -191,7 +198,7 @@ __global__ void k_precond(Dev d, int phase) {
   if (d.gc[g].phase != phase) return;
   double A[9], R[9];
   const int bp = d.diag_pos[r];
-  for (int e = 0; e < 9; ++e) A[e] = MIXED ? (double)d.vals32[vaddr(bp, e)] : d.vals[vaddr(bp, e)];
+  for (int e = 0; e < 9; ++e) A[e] = MIXED ? (double)d.vals32[val_addr32(bp, e)] : d.vals[val_addr64(bp, e)];
   if (d.fixed[r]) {
     for (int e = 0; e < 9; ++e) R[e] = 0.0;
   } else {
@@ -682,16 +689,17 @@ __device__ __forceinline__ float4 spmv_row32(const Dev& d, int s, int lane, cons
     const int bp = o + 32 * k + lane;
     const int c = __ldg(d.colidx + bp);
     const float4 uc = u[c];
-    const float* v = d.vals32 + (size_t)9 * (o + 32 * k) + lane;
+    float v[9];
+    load_block32(d.vals32 + (size_t)9 * (o + 32 * k), lane, v);
     a0 = fmaf(v[0], uc.x, a0);
-    a1 = fmaf(v[96], uc.x, a1);
-    a2 = fmaf(v[192], uc.x, a2);
-    a0 = fmaf(v[32], uc.y, a0);
-    a1 = fmaf(v[128], uc.y, a1);
-    a2 = fmaf(v[224], uc.y, a2);
-    a0 = fmaf(v[64], uc.z, a0);
-    a1 = fmaf(v[160], uc.z, a1);
-    a2 = fmaf(v[256], uc.z, a2);
+    a1 = fmaf(v[3], uc.x, a1);
+    a2 = fmaf(v[6], uc.x, a2);
+    a0 = fmaf(v[1], uc.y, a0);
+    a1 = fmaf(v[4], uc.y, a1);
+    a2 = fmaf(v[7], uc.y, a2);
+    a0 = fmaf(v[2], uc.z, a0);
+    a1 = fmaf(v[5], uc.z, a1);
+    a2 = fmaf(v[8], uc.z, a2);
   }
   return make_float4(a0, a1, a2, 0.f);
 }
@@ -705,16 +713,17 @@ __device__ __forceinline__ double4_32a spmv_row_res(const Dev& d, int s, int lan
     const int bp = o + 32 * k + lane;
     const int c = __ldg(d.colidx + bp);
     const double4_32a xc = x[c];
-    const float* v = d.vals32 + (size_t)9 * (o + 32 * k) + lane;
+    float v[9];
+    load_block32(d.vals32 + (size_t)9 * (o + 32 * k), lane, v);
     a0 = fma((double)v[0], xc.x, a0);
-    a1 = fma((double)v[96], xc.x, a1);
-    a2 = fma((double)v[192], xc.x, a2);
-    a0 = fma((double)v[32], xc.y, a0);
-    a1 = fma((double)v[128], xc.y, a1);
-    a2 = fma((double)v[224], xc.y, a2);
-    a0 = fma((double)v[64], xc.z, a0);
-    a1 = fma((double)v[160], xc.z, a1);
-    a2 = fma((double)v[256], xc.z, a2);
+    a1 = fma((double)v[3], xc.x, a1);
+    a2 = fma((double)v[6], xc.x, a2);
+    a0 = fma((double)v[1], xc.y, a0);
+    a1 = fma((double)v[4], xc.y, a1);
+    a2 = fma((double)v[7], xc.y, a2);
+    a0 = fma((double)v[2], xc.z, a0);
+    a1 = fma((double)v[5], xc.z, a1);
+    a2 = fma((double)v[8], xc.z, a2);
   }
   return make_double4_32a(a0, a1, a2, 0.0);
 }

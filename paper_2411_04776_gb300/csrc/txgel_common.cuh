@@ -254,6 +254,37 @@ struct PcgPlan {
   int ngroups;
 };
 
+// Value layout of the sliced BSR.  The 32 block positions of one column k of a slice share 288
+// consecutive values; element e (row-major 3x3) of the block at lane l = bp mod 32 sits at
+//   FP64: e < 8: 64 (e / 2) + 2 l + e % 2 (pairs: one 16-byte load reads two), e = 8: 256 + l;
+//   FP32: e < 8: 128 (e / 4) + 4 l + e % 4 (quads: one 16-byte load reads four), e = 8: 256 + l,
+// so a lane reads its block with 5 (FP64) or 3 (FP32) loads instead of 9.
+__host__ __device__ __forceinline__ size_t val_addr64(int bp, int e) {
+  const int l = bp & 31;
+  return (size_t)9 * (bp & ~31) + (e < 8 ? 64 * (e >> 1) + 2 * l + (e & 1) : 256 + l);
+}
+__host__ __device__ __forceinline__ size_t val_addr32(int bp, int e) {
+  const int l = bp & 31;
+  return (size_t)9 * (bp & ~31) + (e < 8 ? 128 * (e >> 2) + 4 * l + (e & 3) : 256 + l);
+}
+
+// one lane's block from its slice column image (column base b: 288 values, the layout above);
+// returns the row-major elements
+__device__ __forceinline__ void load_block64(const double* b, int lane, double e[9]) {
+  const double2 p0 = *reinterpret_cast<const double2*>(b + 2 * lane);
+  const double2 p1 = *reinterpret_cast<const double2*>(b + 64 + 2 * lane);
+  const double2 p2 = *reinterpret_cast<const double2*>(b + 128 + 2 * lane);
+  const double2 p3 = *reinterpret_cast<const double2*>(b + 192 + 2 * lane);
+  e[0] = p0.x; e[1] = p0.y; e[2] = p1.x; e[3] = p1.y; e[4] = p2.x;
+  e[5] = p2.y; e[6] = p3.x; e[7] = p3.y; e[8] = b[256 + lane];
+}
+__device__ __forceinline__ void load_block32(const float* b, int lane, float e[9]) {
+  const float4 q0 = *reinterpret_cast<const float4*>(b + 4 * lane);
+  const float4 q1 = *reinterpret_cast<const float4*>(b + 128 + 4 * lane);
+  e[0] = q0.x; e[1] = q0.y; e[2] = q0.z; e[3] = q0.w;
+  e[4] = q1.x; e[5] = q1.y; e[6] = q1.z; e[7] = q1.w; e[8] = b[256 + lane];
+}
+
 // host-side count of kernel launches (every launcher adds the kernels it enqueued)
 void count_launch(int k);
 
