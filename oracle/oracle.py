@@ -93,6 +93,8 @@ def _declare(L):
     L.or_pcg_csr.restype = ctypes.c_int
     L.or_pcg_csr.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_double, ctypes.c_int]
     L.or_pair_counts.argtypes = [ctypes.c_void_p, dp, dp, ip]
+    L.or_components.restype = ctypes.c_int
+    L.or_components.argtypes = [ctypes.c_void_p, ip]
     L.or_set_friction.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
     L.or_step_attached.restype = ctypes.c_int
     L.or_step_attached.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ip, dp]
@@ -282,11 +284,19 @@ class OracleGel:
         return g.reshape(-1, 3), fc, (r[:n].copy(), c[:n].copy(), v[:n].copy())
 
     def pair_counts(self, x, pose):
-        c = np.zeros(6, dtype=np.int32)
+        """Candidate pairs of each type (PT, TP, EE, SPT, SEE), then the active ones (d < d_hat)."""
+        c = np.zeros(10, dtype=np.int32)
         x, xp = _d(x)
         pose, pp = _d(pose)
         lib().or_pair_counts(self._h, xp, pp, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         return c
+
+    def components(self):
+        """(number of connected components of the tet mesh, component of each vertex)."""
+        n = lib().or_components(self._h, None)
+        comp = np.zeros(self.N, dtype=np.int32)
+        lib().or_components(self._h, comp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return n, comp
 
 
 # ---- unit-level helpers ----

@@ -671,6 +671,10 @@ struct Gel {
   std::vector<double> mass;  // N
   std::vector<int> sverts, stris, sedges;
   std::vector<double> sedge_len2;
+  // connected components of the tet mesh (READING R25: a second deformable body, f4): vertex
+  // component, and the component of each surface vertex / triangle / edge
+  int ncomp = 1;
+  std::vector<int> comp, sv_comp, st_comp, se_comp;
   std::vector<double> IV;  // indenter verts in its own frame, 3M
   std::vector<int> itris, iedges;
   std::vector<double> iedge_len2;
@@ -731,6 +735,9 @@ void pose_mid(const double a[7], const double b[7], double m[7]) {
 //   PT  (type 0): gel surface vertex  vs indenter triangle   P = [gv, it0, it1, it2], gel slot 0
 //   TP  (type 1): indenter vertex     vs gel surface triangle P = [iv, gt0, gt1, gt2], gel 1..3
 //   EE  (type 2): gel surface edge    vs indenter edge        P = [ga0, ga1, ib0, ib1], gel 0..1
+// and, between two deformable bodies (surface primitives of different mesh components):
+//   SPT (type 3): surface vertex      vs surface triangle     P = [sv, st0, st1, st2], all mesh
+//   SEE (type 4): surface edge        vs surface edge         P = [sa0, sa1, sb0, sb1], all mesh
 struct PairRef {
   int type, g, k;
 };
@@ -753,15 +760,24 @@ void pair_points(const Gel& G, const double* x, const double* IW, const PairRef&
   } else if (pr.type == 1) {
     put(0, IW, pr.k, false);
     for (int c = 0; c < 3; ++c) put(1 + c, x, G.stris[3 * pr.g + c], true);
-  } else {
+  } else if (pr.type == 2) {
     put(0, x, G.sedges[2 * pr.g], true);
     put(1, x, G.sedges[2 * pr.g + 1], true);
     put(2, IW, G.iedges[2 * pr.k], false);
     put(3, IW, G.iedges[2 * pr.k + 1], false);
+  } else if (pr.type == 3) {
+    put(0, x, G.sverts[pr.g], true);
+    for (int c = 0; c < 3; ++c) put(1 + c, x, G.stris[3 * pr.k + c], true);
+  } else {
+    put(0, x, G.sedges[2 * pr.g], true);
+    put(1, x, G.sedges[2 * pr.g + 1], true);
+    put(2, x, G.sedges[2 * pr.k], true);
+    put(3, x, G.sedges[2 * pr.k + 1], true);
   }
 }
 
 double pair_eps_x(const Gel& G, const PairRef& pr) {
+  if (pr.type == 4) return 1e-3 * G.sedge_len2[pr.g] * G.sedge_len2[pr.k];
   return pr.type == 2 ? 1e-3 * G.sedge_len2[pr.g] * G.iedge_len2[pr.k] : 0.0;
 }
 
@@ -807,10 +823,32 @@ std::vector<PairRef> candidate_pairs(const Gel& G, const double* x0, const doubl
   scan(0, (int)G.sverts.size(), 1, G.sverts.data(), itb);
   scan(1, (int)(G.stris.size() / 3), 3, G.stris.data(), ivb);
   scan(2, (int)(G.sedges.size() / 2), 2, G.sedges.data(), iedb);
+  if (G.ncomp > 1) {  // READING R25: the surfaces of different components against each other
+    const int nsv = (int)G.sverts.size(), nst = (int)(G.stris.size() / 3), nse = (int)(G.sedges.size() / 2);
+    std::vector<Box> stb(nst), seb(nse);
+    for (int k = 0; k < nst; ++k) stb[k] = gbox(&G.stris[3 * k], 3);
+    for (int k = 0; k < nse; ++k) seb[k] = gbox(&G.sedges[2 * k], 2);
+    std::vector<std::vector<int>> hv(nsv), he(nse);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < nsv; ++g) {  // every vertex against the triangles of the other bodies
+      const Box b = gbox(&G.sverts[g], 1);
+      for (int k = 0; k < nst; ++k)
+        if (G.st_comp[k] != G.sv_comp[g] && near_boxes(b, stb[k], pad)) hv[g].push_back(k);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int g = 0; g < nse; ++g)  // each pair of edges of different bodies once (g < k)
+      for (int k = g + 1; k < nse; ++k)
+        if (G.se_comp[k] != G.se_comp[g] && near_boxes(seb[g], seb[k], pad)) he[g].push_back(k);
+    for (int g = 0; g < nsv; ++g)
+      for (int k : hv[g]) out.push_back({3, g, k});
+    for (int g = 0; g < nse; ++g)
+      for (int k : he[g]) out.push_back({4, g, k});
+  }
   return out;
 }
 
-int kind_of(const PairRef& pr) { return pr.type == 2 ? K_EE : K_PT; }
+int kind_of(const PairRef& pr) { return (pr.type == 2 || pr.type == 4) ? K_EE : K_PT; }
+bool soft_soft(const PairRef& pr) { return pr.type >= 3; }
 
 // ---------------- lagged friction ----------------
 struct FricPair {
@@ -1061,7 +1099,7 @@ void assemble(const Gel& G, const double* x, const double* xt, double h, const d
   }
   // per-pair contributions on the gel's points (computed in parallel, added in pair order)
   struct PairTerm {
-    bool on = false;
+    bool on = false, ss = false;  // ss: between two deformable bodies (not in the indenter force)
     int nf = 0, fidx[12], gi[4];
     double g[12], H[144];
   };
@@ -1072,7 +1110,7 @@ void assemble(const Gel& G, const double* x, const double* xt, double h, const d
         int kr = q.fidx[r] / 3, cr = q.fidx[r] % 3;
         int gr = 3 * q.gi[kr] + cr;
         grad[gr] += q.g[r];
-        fc[cr] -= q.g[r];
+        if (!q.ss) fc[cr] -= q.g[r];
         for (int c = 0; c < q.nf; ++c) {
           int kc = q.fidx[c] / 3, cc = q.fidx[c] % 3;
           add(gr, 3 * q.gi[kc] + cc, q.H[r * q.nf + c]);
@@ -1095,6 +1133,7 @@ void assemble(const Gel& G, const double* x, const double* xt, double h, const d
       double D = d2_of_type(ty, P);
       if (!(D < G.dhat * G.dhat) || !(D > 0.0)) continue;
       q.on = true;
+      q.ss = soft_soft(pr);
       AD<12> Pv[4][3];
       for (int j = 0; j < 4; ++j)
         for (int c = 0; c < 3; ++c) Pv[j][c] = ad_var<12>(P[j][c], 3 * j + c);
@@ -1359,6 +1398,7 @@ int newton_solve(Gel& G, double h, const double* I0, const double* IW) {
   if (G.fric_mu > 0.0) {
     G.fric_eh = G.fric_epsv * h;
     for (const PairRef& pr : candidate_pairs(G, G.x.data(), G.x.data(), I0, I0, G.dhat)) {
+      if (soft_soft(pr)) continue;  // READING R25: friction against the rigid indenter only
       double P[4][3];
       int gi[4];
       pair_points(G, G.x.data(), I0, pr, P, gi);
@@ -1550,6 +1590,37 @@ void* or_create(int N, const double* X, int T, const int* tets, const uint8_t* d
     }
     G->sedge_len2.push_back(l2);
     lsum += std::sqrt(l2);
+  }
+  // connected components: vertices joined by a tet (union-find, each root the smallest index);
+  // numbered in the order of their smallest vertex, so the body of the first vertex in a tet is
+  // component 0 (the gelpad)
+  {
+    std::vector<int> up(N);
+    for (int i = 0; i < N; ++i) up[i] = i;
+    auto root = [&](int i) {
+      while (up[i] != i) i = up[i] = up[up[i]];
+      return i;
+    };
+    for (int t = 0; t < T; ++t)
+      for (int a = 1; a < 4; ++a) {
+        const int r0 = root(tets[4 * t]), r1 = root(tets[4 * t + a]);
+        if (r0 != r1) up[std::max(r0, r1)] = std::min(r0, r1);
+      }
+    std::vector<int> id(N, -1);
+    std::vector<char> used(N, 0);
+    for (int k = 0; k < 4 * T; ++k) used[tets[k]] = 1;
+    G->comp.assign(N, 0);
+    G->ncomp = 0;
+    for (int i = 0; i < N; ++i) {
+      if (!used[i]) continue;  // in no tet: on no surface, never in a pair (left in component 0)
+      const int r = root(i);
+      if (id[r] < 0) id[r] = G->ncomp++;
+      G->comp[i] = id[r];
+    }
+    G->ncomp = std::max(G->ncomp, 1);
+    for (int v : G->sverts) G->sv_comp.push_back(G->comp[v]);
+    for (size_t k = 0; k < G->stris.size() / 3; ++k) G->st_comp.push_back(G->comp[G->stris[3 * k]]);
+    for (size_t k = 0; k < G->sedges.size() / 2; ++k) G->se_comp.push_back(G->comp[G->sedges[2 * k]]);
   }
   G->IV.assign(IV, IV + 3 * M);
   G->itris.assign(itris, itris + 3 * K);
@@ -1869,6 +1940,7 @@ static bool xy_bary(const double* P, int a, int b, int c, double px, double py, 
 static std::vector<int> top_tris(const Gel& G) {
   std::vector<int> out;
   for (size_t k = 0; k < G.stris.size() / 3; ++k) {
+    if (G.st_comp[k] != 0) continue;  // the gelpad: component 0
     const int a = G.stris[3 * k], b = G.stris[3 * k + 1], c = G.stris[3 * k + 2];
     double e1[3], e2[3], n[3];
     sub3(&G.X[3 * b], &G.X[3 * a], e1);
@@ -2008,21 +2080,28 @@ int or_pcg_csr(int n, const int* rp, const int* ci, const double* va, const doub
   return it;
 }
 
-// Number of candidate pairs (PT, TP, EE) for the gel at x and the indenter at `pose`, and the
-// number of those within dhat (active).
+// Number of candidate pairs of each type (PT, TP, EE, SPT, SEE) for the gel at x and the
+// indenter at `pose`, then the number of those within dhat (active): counts[0..4], counts[5..9].
 void or_pair_counts(void* g, const double* x, const double* pose, int* counts) {
   Gel& G = *static_cast<Gel*>(g);
   std::vector<double> IW(3 * G.M);
   pose_apply(pose, G.IV.data(), G.M, IW.data());
   std::vector<PairRef> pairs = candidate_pairs(G, x, x, IW.data(), IW.data(), G.dhat);
-  for (int i = 0; i < 6; ++i) counts[i] = 0;
+  for (int i = 0; i < 10; ++i) counts[i] = 0;
   for (const PairRef& pr : pairs) {
     counts[pr.type]++;
     double P[4][3];
     int gi[4];
     pair_points(G, x, IW.data(), pr, P, gi);
-    if (pair_d2(kind_of(pr), P) < G.dhat * G.dhat) counts[3 + pr.type]++;
+    if (pair_d2(kind_of(pr), P) < G.dhat * G.dhat) counts[5 + pr.type]++;
   }
+}
+
+// Number of connected components of the tet mesh, and the component of each vertex (comp[N]).
+int or_components(void* g, int* comp) {
+  const Gel& G = *static_cast<Gel*>(g);
+  if (comp) std::copy(G.comp.begin(), G.comp.end(), comp);
+  return G.ncomp;
 }
 
 }  // extern "C"

@@ -349,6 +349,63 @@ def hertz_block(h0: float = 0.06e-3, ratio: float = 1.3, half: float = 3.0e-3, t
                     dhat=dhat)
 
 
+def ball_mesh(n: int, radius: float, center) -> GelMesh:
+    """Soft ball: an n*n*n vertex grid over the cube [-1, 1]^3 (6 Kuhn tets per cube) carried onto
+    the ball by the concentric map p -> p |p|_inf / |p|_2 (the cube's faces onto the sphere), scaled
+    by `radius` and moved to `center`; no vertex held.  n = 10, 20, 23 give 1000, 8000, 12167
+    vertices and 4374, 41154, 63888 tets, next to the three soft-ball resolutions of Table 3."""
+    verts, tets, _ = _tensor_grid_arrays(*(np.linspace(-1.0, 1.0, int(n)),) * 3)
+    inf = np.abs(verts).max(axis=1)
+    two = np.linalg.norm(verts, axis=1)
+    scale = np.divide(inf, two, out=np.zeros_like(inf), where=two > 0)
+    verts = verts * scale[:, None] * float(radius) + np.asarray(center, dtype=np.float64)
+    e1, e2, e3 = (verts[tets[:, k]] - verts[tets[:, 0]] for k in (1, 2, 3))
+    vol = np.einsum("ij,ij->i", np.cross(e1, e2), e3) / 6.0
+    assert vol.min() > 0.0, "ball map inverted a tet"
+    return GelMesh(verts, tets.astype(np.int32), np.zeros(len(verts), dtype=np.uint8))
+
+
+def flat_plate(side: float, n: int) -> Indenter:
+    """Square plate of `side` in the indenter frame's z = 0 plane (facing down), an n*n vertex grid,
+    two triangles per cell."""
+    t = np.linspace(-0.5 * side, 0.5 * side, n)
+    yy, xx = np.meshgrid(t, t, indexing="ij")
+    verts = np.stack([xx.ravel(), yy.ravel(), np.zeros(n * n)], axis=1)
+    j, i = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    a = (i + n * j).ravel()
+    tris = np.concatenate([np.stack([a, a + n, a + 1], 1), np.stack([a + 1, a + n, a + n + 1], 1)])
+    return Indenter(verts, tris.astype(np.int32), "plate")
+
+
+def join_meshes(a: GelMesh, b: GelMesh) -> GelMesh:
+    """One tet mesh holding both bodies (b's vertices after a's): two connected components."""
+    return GelMesh(np.concatenate([a.verts, b.verts]), np.concatenate([a.tets, b.tets + len(a.verts)]).astype(np.int32),
+                   np.concatenate([a.dirichlet, b.dirichlet]))
+
+
+def gel_ball(ball_n: int = 20, grid=GRID_MINI, radius: float = 4.0e-3, depth: float = 1.0e-3, n_press: int = 60,
+             slide: float = 2.0e-3, n_slide: int = 60, seed: int = 0) -> Workload:
+    """Soft ball between the gel and a rigid plate (the soft-ball scene of Table 3, the ball a
+    deformable body of the gel's material): the ball (`ball_mesh`) rests 2 d_hat above the gel's top
+    face, its centre offset by a seeded +-1 mm in x-y; a 12 mm plate (`flat_plate`) starts d_hat above
+    the ball, closes both gaps and squeezes `depth` over n_press steps, then slides along +x (no
+    friction: over the ball)."""
+    rng = np.random.default_rng(seed)
+    (nx, ny, nz), size = grid
+    gel = gel_grid(nx, ny, nz, size)
+    off = rng.uniform(-0.001, 0.001, size=2)
+    c = np.array([0.5 * size[0] + off[0], 0.5 * size[1] + off[1], gel.top + 2 * DHAT + radius])
+    ball = ball_mesh(ball_n, radius, c)
+    ind = flat_plate(0.012, 13)
+    start = np.array([c[0], c[1], float(ball.verts[:, 2].max()) + DHAT])
+    travel = 3 * DHAT + depth
+    poses = [pose(start - np.array([0.0, 0.0, travel * s / n_press])) for s in range(1, n_press + 1)]
+    bottom = start - np.array([0.0, 0.0, travel])
+    poses += [pose(bottom + np.array([slide * s / n_slide, 0.0, 0.0])) for s in range(1, n_slide + 1)]
+    name = f"gel{nx}x{ny}x{nz}_softball{len(ball.verts)}v_r{radius*1e3:.1f}mm_plate_press{depth*1e3:.1f}mm"
+    return Workload(name, join_meshes(gel, ball), ind, pose(start), np.asarray(poses), DT)
+
+
 def mixed_batch(n_gels: int = 256, seed0: int = 0, n_press: int = 60, n_slide: int = 60):
     """Batch of gels with resolutions drawn uniformly from the three grids, each with its own
     seeded indenter, trajectory and depth uniform in [0.2, 1.2] mm."""

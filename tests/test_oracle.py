@@ -885,10 +885,136 @@ def test_candidate_rule_and_active_set_against_all_pairs(case):
     Eb = IW[ie][None, :, :, :]
     cand_ee = _near(Ea.min(axis=2), Ea.max(axis=2), Eb.min(axis=2), Eb.max(axis=2), dhat)
     d_ee = _segment_segment(Ea[:, :, 0], Ea[:, :, 1], Eb[:, :, 0], Eb[:, :, 1])
-    mine = [int(cand_pt.sum()), int(cand_tp.sum()), int(cand_ee.sum()),
-            int((d_pt < dhat).sum()), int((d_tp < dhat).sum()), int((d_ee < dhat).sum())]
-    assert sum(mine[3:]) > 0 and (case == "sphere" or mine[5] > 0)
+    mine = [int(cand_pt.sum()), int(cand_tp.sum()), int(cand_ee.sum()), 0, 0,
+            int((d_pt < dhat).sum()), int((d_tp < dhat).sum()), int((d_ee < dhat).sum()), 0, 0]
+    assert sum(mine[5:]) > 0 and (case == "sphere" or mine[7] > 0)
     assert list(oc) == mine, (list(oc), mine)
+
+
+def test_soft_soft_candidates_and_active_set_against_all_pairs():
+    """A soft ball squeezed between the gel and a plate (two mesh components): every surface
+    vertex against every surface triangle of the other body, and every pair of surface edges of
+    different bodies, scanned with plain numpy (components from scipy's graph routine, not the
+    oracle's union-find): the box rule (R20) picks exactly the oracle's SPT and SEE candidates, the
+    distance below d_hat exactly its active ones; the rigid pairs are still counted as before."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    wl = W.gel_ball(6, grid=W.GRID_SMALL, n_press=10, n_slide=0, depth=0.6e-3)
+    og = O.OracleGel.from_workload(wl)
+    for s in range(4):
+        assert og.step(wl.poses[s], wl.dt)["status"] == 0
+    x, _, _, pose = og.state()
+    oc = og.pair_counts(x, pose)
+    tets = wl.gel.tets
+    n = len(x)
+    rows = np.repeat(tets[:, :1], 3, axis=1).ravel()
+    adj = sp.coo_matrix((np.ones(len(rows)), (rows, tets[:, 1:].ravel())), shape=(n, n))
+    ncomp, comp = connected_components(adj, directed=False)
+    assert ncomp == 2 and og.components()[0] == 2
+    assert np.array_equal(og.components()[1] == og.components()[1][0], comp == comp[0])
+    sv, st, se = _boundary(tets)
+    dhat = wl.dhat
+    P = x[sv][:, None, :]
+    T = x[st][None, :, :, :]
+    other = comp[sv][:, None] != comp[st[:, 0]][None, :]
+    cand_spt = _near(P, P, T.min(axis=2), T.max(axis=2), dhat) & other
+    i, k = np.nonzero(cand_spt)
+    d_spt = _point_triangle(x[sv[i]], x[st[k, 0]], x[st[k, 1]], x[st[k, 2]])
+    E = x[se]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    cand_see = _near(lo[:, None], hi[:, None], lo[None], hi[None], dhat)
+    cand_see &= comp[se[:, 0]][:, None] != comp[se[:, 0]][None, :]
+    cand_see = np.triu(cand_see, 1)
+    a, b = np.nonzero(cand_see)
+    d_see = _segment_segment(x[se[a, 0]], x[se[a, 1]], x[se[b, 0]], x[se[b, 1]])
+    mine_ss = [len(i), len(a), int((d_spt < dhat).sum()), int((d_see < dhat).sum())]
+    assert mine_ss[2] > 0 and mine_ss[3] > 0, mine_ss  # the ball touches the gel by step 4
+    assert [oc[3], oc[4], oc[8], oc[9]] == mine_ss, (list(oc), mine_ss)
+    assert oc[5] + oc[6] + oc[7] > 0  # and the plate touches the ball
+
+
+def _ball_into(v0, steps, kappa, tol):
+    """READING R25 pin: a soft ball falling (gravity, initial velocity v0) onto (a) the gel held
+    fixed in the same mesh (soft-soft pairs) and (b) the ball alone onto a rigid indenter made of
+    the gel's surface at rest (rigid pairs), both with the same absolute Newton tolerance; returns
+    the ball's positions of each step in both and the most active pairs of each rigid type in (b)."""
+    gel = W.gel_grid(*W.GRID_SMALL[0], W.GRID_SMALL[1])
+    c = (0.009, 0.012, gel.top + 2 * W.DHAT + 3e-3)
+    ball = W.ball_mesh(6, 3e-3, c)
+    far = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])  # the plate of (a), out of reach
+    plate = W.flat_plate(0.004, 3)
+    nb = len(ball.verts)
+    gel.dirichlet[:] = 1
+    both = W.join_meshes(gel, ball)
+
+    def diag(v):
+        return float(np.linalg.norm(v.max(axis=0) - v.min(axis=0)))
+
+    kw = dict(dhat=W.DHAT, kappa=kappa, gravity=(0.0, 0.0, -9.81), newton_max=2000)
+    a = O.OracleGel(both.verts, both.tets, both.dirichlet, (E_, NU_, RHO_), plate.verts, plate.tris, far,
+                    newton_tol=tol, **kw)
+    sv, st, _ = _boundary(gel.tets)
+    remap = np.full(len(gel.verts), -1)
+    remap[sv] = np.arange(len(sv))
+    ident = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    b = O.OracleGel(ball.verts, ball.tets, ball.dirichlet, (E_, NU_, RHO_), gel.verts[sv], remap[st], ident,
+                    newton_tol=tol * diag(both.verts) / diag(ball.verts), **kw)
+    v = np.tile(v0, (nb, 1))
+    a.set_state(both.verts, np.concatenate([np.zeros_like(gel.verts), v]), far)
+    b.set_state(ball.verts, v, ident)
+    xa, xb, most = [], [], np.zeros(3, dtype=int)
+    for s in range(steps):
+        ra, rb = a.step(far, W.DT), b.step(ident, W.DT)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert ra["active_pairs"] == rb["active_pairs"]
+        most = np.maximum(most, b.pair_counts(b.state()[0], ident)[5:8])
+        xa.append(a.state()[0][len(gel.verts):])
+        xb.append(b.state()[0])
+    return np.array(xa), np.array(xb), most
+
+
+def test_soft_soft_contact_against_a_held_body_is_rigid_contact():
+    """Contact between two deformable bodies uses the same barrier on the same primitive
+    distances as contact with a rigid body (Sec. 2's GIPC pipeline, soft-to-soft): a ball dropped
+    on a gel whose vertices are all held must move as the ball alone dropped on a rigid obstacle
+    whose surface is the gel's surface, to the Newton tolerance.  Every rigid pair type is active
+    in the second scene, so a missing soft-soft direction (gel vertex vs ball triangle, ball vertex
+    vs gel triangle), a missing edge-edge type or another mollifier changes the trajectory."""
+    xa, xb, most = _ball_into(np.array([0.01, 0.0, -0.05]), 6, 500.0, 1e-7)
+    assert np.all(most > 0), most
+    err = np.abs(xa - xb).max()
+    assert err < 1e-9, err
+
+
+def test_soft_soft_contact_conserves_momentum():
+    """Two free balls (no held vertex, no gravity) thrown at each other: the elastic and the
+    soft-soft barrier forces are internal (each pair's gradient sums to zero over its four points),
+    so implicit Euler keeps the total momentum sum m_i v_i (to the Newton tolerance)."""
+    b1 = W.ball_mesh(5, 3e-3, (0.0, 0.0, 0.0))
+    b2 = W.ball_mesh(5, 3e-3, (0.0015, 0.0, 6e-3 + 3 * W.DHAT))
+    both = W.join_meshes(b1, b2)
+    far = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    plate = W.flat_plate(0.004, 3)
+    og = O.OracleGel(both.verts, both.tets, both.dirichlet, (E_, NU_, RHO_), plate.verts, plate.tris, far,
+                     dhat=W.DHAT, kappa=500.0, newton_tol=3e-7, newton_max=2000)
+    n1 = len(b1.verts)
+    v = np.zeros_like(both.verts)
+    v[:n1] = (0.0, 0.0, 0.05)
+    v[n1:] = (0.0, 0.0, -0.05)
+    og.set_state(both.verts, v, far)
+    m = og.mass()
+    p0 = (m[:, None] * v).sum(axis=0)
+    act, worst = 0, 0.0
+    for s in range(5):
+        r = og.step(far, W.DT)
+        assert r["status"] == 0
+        act = max(act, r["active_pairs"])
+        vs = og.state()[1]
+        dp = np.abs((m[:, None] * vs).sum(axis=0) - p0).max()
+        worst = max(worst, dp / (0.5 * m.sum() * 0.05))  # against one ball's momentum
+    print("soft-soft collision: relative momentum change %.2e, most active pairs %d" % (worst, act))
+    assert act > 10, act
+    assert worst < 1e-12, worst
 
 
 def test_stationarity_rule_both_sides():
