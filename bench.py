@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--features", action="store_true",
                     help="mini: also time friction, the attachment-driven step and the surface readout")
+    ap.add_argument("--softball", default="",
+                    help="mini: also time the soft-ball scenes (gel + deformable ball + rigid plate) at these ball "
+                         "grid sizes, comma separated (10, 20, 23: the three ball resolutions of Table 3)")
     ap.add_argument("--reference-budget", type=float, default=200.0, help="seconds of timed oracle work")
     ap.add_argument("--batched-gels", type=int, default=64,
                     help="default run: gels of the batched mixed-precision companion measurement (0: skip)")
@@ -579,6 +582,11 @@ def main():
             line["features"] = features_companion(args)
         except Exception as e:  # noqa: BLE001
             line["features"] = {"error": f"{type(e).__name__}: {e}"}
+    if world == 1 and args.workload == "mini" and args.softball:
+        try:
+            line["softball"] = softball_companion(args)
+        except Exception as e:  # noqa: BLE001
+            line["softball"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args)
@@ -659,6 +667,58 @@ def features_companion(args):
     res = {"workload": NAMES["mini"], "steps": K, "warmup": Wm, "precision": "fp64"}
     for kind in ("plain", "friction", "attached"):
         res[kind] = run(kind)
+    return res
+
+
+# GIPC's time per frame of the soft-ball scene at three ball resolutions (Table 3: vertices, tets, ms),
+# measured by the paper on its own machine: context for the same-sized scenes here, not a target
+TABLE3_GIPC = {10: (1029, 3717, 24.95), 20: (7900, 40370, 110.47), 23: (12509, 66563, 221.61)}
+
+
+def softball_companion(args):
+    """Companion measurement of soft-to-soft contact: the GelSight-Mini gel (41x51x9) with a soft
+    ball of radius 4 mm on it (an n^3 ball grid, the gel's material) squeezed by a rigid 12 mm plate
+    (`workloads.gel_ball`), FP64: warm-up steps untimed, then CUDA-event timed steps with L2 flushed
+    before each; per ball size the mean time per step (frame), its Newton and PCG iterations, and
+    the soft-soft pair assemblies whose cross-body blocks found no spare matrix position."""
+    import torch
+    from paper_2411_04776_gb300 import binding as B
+    from paper_2411_04776_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, Wm = args.steps, args.warmup
+    res = {"steps": K, "warmup": Wm, "precision": "fp64", "sizes": []}
+    for n in (int(v) for v in args.softball.split(",") if v.strip()):
+        wl = W.gel_ball(n, seed=args.seed)
+        gel = B.Gel.from_workload(wl, stream=stream, newton_max_iter=1000)
+        for s in range(Wm):
+            assert gel.step(wl.poses[s], wl.dt) == 0, (n, s)
+        ms, newton, pcg, cut, act = [], 0, 0, 0, 0
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gel.step(wl.poses[Wm + i], wl.dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert st == 0, (n, Wm + i, st)
+            ms.append(e0.elapsed_time(e1))
+            stt = gel.stats()
+            newton += stt["newton_iters"]
+            pcg += stt["pcg_iters"]
+            cut += stt["soft_pairs_cut"]
+            act = max(act, stt["active_pairs"])
+        gel.close()
+        ms = np.array(ms)
+        nb = n ** 3
+        row = {"workload": wl.name, "ball_verts": nb, "ball_tets": 6 * (n - 1) ** 3, "mesh_verts": len(wl.gel.verts),
+               "ms_per_step": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)),
+               "newton_iters_per_step": newton / K, "pcg_iters_per_step": pcg / K, "most_active_pairs": act,
+               "soft_pairs_cut": cut}
+        if n in TABLE3_GIPC:
+            v, t, g = TABLE3_GIPC[n]
+            row["table3_gipc"] = {"ball_verts": v, "ball_tets": t, "ms_per_frame": g}
+        res["sizes"].append(row)
     return res
 
 

@@ -110,7 +110,14 @@ void tx_params_default(tx_params* p);
 
 /* One gel + indenter scene.  The gel is a tet mesh (rest positions, positively oriented tets,
  * Dirichlet mask: 1 = vertex held at its rest position).  The indenter is a rigid triangle mesh
- * given in its own frame, placed in the world by a pose (qw, qx, qy, qz, tx, ty, tz). */
+ * given in its own frame, placed in the world by a pose (qw, qx, qy, qz, tx, ty, tz).
+ * The tet mesh may hold up to 4 deformable bodies (its connected components through the tets,
+ * numbered in the order of their first vertex; all of one material): their surfaces then also
+ * touch each other through the same barrier (GIPC's soft-to-soft contact, TacEx Sec. 2: every
+ * surface vertex against every surface triangle of another body, every two surface edges of
+ * different bodies), without friction and without counting in contact_force.  Body 0 is the
+ * gelpad: the marker and height-map readouts use its top surface only.  More than 4 bodies is
+ * TX_ERR_ARG. */
 typedef struct tx_gel_desc {
   int32_t n_verts;
   const double* verts;       /* n_verts x 3 rest positions [m]                                  */
@@ -143,6 +150,10 @@ typedef struct tx_step_stats {
   double contact_force[3];  /* force of the indenter on the gel, -kappa sum grad b [N]           */
   double mean_position[3];  /* mean of the gel vertex positions (TacEx "object position") [m]    */
   double kappa;             /* barrier stiffness for the next step [N/m] (tx_params.kappa_adapt_max) */
+  int32_t soft_pairs_cut;   /* several bodies: Newton assemblies of a soft-soft pair whose blocks
+                               between the two bodies found no spare matrix position and were left
+                               out (the matrix stays PSD; the solve only converges more slowly)  */
+  int32_t reserved1;
 } tx_step_stats;
 
 typedef struct tx_gel tx_gel;     /* opaque single-gel handle                                  */

@@ -56,7 +56,7 @@ class tx_step_stats(ctypes.Structure):
                 ("refine_rounds", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("energy", ctypes.c_double), ("min_distance", ctypes.c_double),
                 ("contact_force", ctypes.c_double * 3), ("mean_position", ctypes.c_double * 3),
-                ("kappa", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("soft_pairs_cut", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k in ("contact_force", "mean_position") else getattr(self, k))

@@ -229,13 +229,25 @@ __device__ __forceinline__ void pair_points(const Dev& d, const int4& pr, double
     gel(1, t.x);
     gel(2, t.y);
     gel(3, t.z);
-  } else {
+  } else if (pr.x == PAIR_EE) {
     const int2 e = d.se[pr.y];
     gel(0, e.x);
     gel(1, e.y);
     const int2 f = d.ie[pr.z];
     indv(2, f.x);
     indv(3, f.y);
+  } else if (pr.x == PAIR_SPT) {  // both primitives on the gel's mesh
+    gel(0, d.sv[pr.y]);
+    const int4 t = d.st[pr.z];
+    gel(1, t.x);
+    gel(2, t.y);
+    gel(3, t.z);
+  } else {
+    const int2 e = d.se[pr.y], f = d.se[pr.z];
+    gel(0, e.x);
+    gel(1, e.y);
+    gel(2, f.x);
+    gel(3, f.y);
   }
 }
 
@@ -250,15 +262,29 @@ __device__ __forceinline__ void pair_rows(const Dev& d, const int4& pr, int rows
     rows[1] = t.x;
     rows[2] = t.y;
     rows[3] = t.z;
-  } else {
+  } else if (pr.x == PAIR_EE) {
     const int2 e = d.se[pr.y];
     rows[0] = e.x;
     rows[1] = e.y;
     rows[2] = rows[3] = -1;
+  } else if (pr.x == PAIR_SPT) {
+    const int4 t = d.st[pr.z];
+    rows[0] = d.sv[pr.y];
+    rows[1] = t.x;
+    rows[2] = t.y;
+    rows[3] = t.z;
+  } else {
+    const int2 e = d.se[pr.y], f = d.se[pr.z];
+    rows[0] = e.x;
+    rows[1] = e.y;
+    rows[2] = f.x;
+    rows[3] = f.y;
   }
 }
 
+// IPC's edge-edge mollifier threshold eps_x = 1e-3 |e_a|^2 |e_b|^2 from the rest lengths
 __device__ __forceinline__ double pair_eps_x(const Dev& d, const int4& pr) {
+  if (pr.x == PAIR_SEE) return 1e-3 * d.se_len2[pr.y] * d.se_len2[pr.z];
   return pr.x == PAIR_EE ? 1e-3 * d.se_len2[pr.y] * d.ie_len2[pr.z] : 0.0;
 }
 

@@ -512,6 +512,152 @@ __global__ void k_pair_ranges(Dev d, int phase, int skip_conv) {
   if (n > G.pcap) atomicOr(&d.gv[g].flags, 32);
 }
 
+// ---------------------------------------------------------------- soft-soft candidates
+// A gel whose mesh has several connected components (bodies) also pairs the surfaces of its
+// different bodies: every surface vertex with every surface triangle of another body, and every
+// two surface edges of different bodies (each unordered pair once), by the box rule of the
+// indenter pairs (primitive boxes -- swept by p in Newton mode -- within d_hat on every axis).
+// Three launches: the bodies' boxes (a CTA per soft-soft gel), the surface primitives near the box
+// of another body (listed), then every listed pair tested by brute force and appended after the
+// gel's indenter pairs.  mode bit 1: boxes swept by p; bit 3: skip gels whose Newton converged.
+constexpr int SS_T = 256;
+
+__device__ __forceinline__ bool ss_active(const Dev& d, int g, int phase, int mode) {
+  return d.gc[g].phase == phase && !((mode & 8) && d.gv[g].converged);
+}
+
+__global__ void __launch_bounds__(SS_T) k_ss_boxes(Dev d, int phase, int mode) {
+  __shared__ double sm[SS_T / 32][SS_MAXC * 6];
+  const int j = blockIdx.x, g = d.ss_gel[j];
+  if (!ss_active(d, g, phase, mode)) return;
+  const GelInfo& G = d.gi[g];
+  double bx[SS_MAXC * 6];  // per component: lo[3], then -hi[3] (all reduced by min)
+#pragma unroll
+  for (int e = 0; e < SS_MAXC * 6; ++e) bx[e] = CUDART_INF;
+  for (int k = threadIdx.x; k < G.nsv; k += SS_T) {
+    const int c = d.vcomp[d.sv[G.sv0 + k]];
+    const Box b = gel_box(d, PAIR_PT, G.sv0 + k, (mode & 2) != 0);
+#pragma unroll
+    for (int q = 0; q < SS_MAXC; ++q)
+      if (q == c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          bx[6 * q + a] = fmin(bx[6 * q + a], b.lo[a]);
+          bx[6 * q + 3 + a] = fmin(bx[6 * q + 3 + a], -b.hi[a]);
+        }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < SS_MAXC * 6; ++e) {
+    double v = bx[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sm[wid][e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < SS_MAXC * 6) {
+    double v = CUDART_INF;
+    for (int w = 0; w < SS_T / 32; ++w) v = fmin(v, sm[w][threadIdx.x]);
+    const int a = threadIdx.x % 6;
+    d.ss_box[(size_t)j * SS_MAXC * 6 + threadIdx.x] = a < 3 ? v : -v;
+  }
+  if (threadIdx.x < 3) d.ss_cnt[3 * j + threadIdx.x] = 0;
+}
+
+// type (PAIR_PT / PAIR_TP / PAIR_EE as the kind of surface primitive), global index, sub-list and
+// first row of query q of gel G
+__device__ __forceinline__ void ss_prim(const Dev& d, const GelInfo& G, int q, int& type, int& gk, int& t, int& r) {
+  if (q < G.nsv) {
+    type = PAIR_PT; gk = G.sv0 + q; t = 0; r = d.sv[gk];
+  } else if (q < G.nsv + G.nst) {
+    type = PAIR_TP; gk = G.st0 + q - G.nsv; t = 1; r = d.st[gk].x;
+  } else {
+    type = PAIR_EE; gk = G.se0 + q - G.nsv - G.nst; t = 2; r = d.se[gk].x;
+  }
+}
+
+__global__ void __launch_bounds__(SS_T) k_ss_filter(Dev d, int phase, int mode) {
+  const int j = blockIdx.y, g = d.ss_gel[j];
+  if (!ss_active(d, g, phase, mode)) return;
+  const GelInfo& G = d.gi[g];
+  const double* cb = d.ss_box + (size_t)j * SS_MAXC * 6;
+  const int nc = min(G.ncomp, SS_MAXC);
+  for (int q = blockIdx.x * SS_T + threadIdx.x; q < G.nq; q += gridDim.x * SS_T) {
+    int type, gk, t, r;
+    ss_prim(d, G, q, type, gk, t, r);
+    const int c = d.vcomp[r];
+    const Box b = gel_box(d, type, gk, (mode & 2) != 0);
+    bool near = false;
+    for (int o = 0; o < nc; ++o) {
+      if (o == c) continue;
+      Box ob;
+      for (int a = 0; a < 3; ++a) {
+        ob.lo[a] = cb[6 * o + a];
+        ob.hi[a] = cb[6 * o + 3 + a];
+      }
+      near = near || near_boxes(b, ob, G.dhat);
+    }
+    if (near) {
+      const int base = t == 0 ? 0 : (t == 1 ? G.nsv : G.nsv + G.nst);
+      d.ss_list[G.q0 + base + atomicAdd(&d.ss_cnt[3 * j + t], 1)] = gk;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SS_T) k_ss_pairs(Dev d, int phase, int mode) {
+  const int j = blockIdx.y, g = d.ss_gel[j];
+  if (!ss_active(d, g, phase, mode)) return;
+  const GelInfo& G = d.gi[g];
+  const bool sw = (mode & 2) != 0;
+  const int nv = d.ss_cnt[3 * j], nt = d.ss_cnt[3 * j + 1], ne = d.ss_cnt[3 * j + 2];
+  const int* lv = d.ss_list + G.q0;
+  const int* lt = lv + G.nsv;
+  const int* le = lt + G.nst;
+  const long long n1 = (long long)nv * nt, n = n1 + (long long)ne * ne;
+  for (long long w = (long long)blockIdx.x * SS_T + threadIdx.x; w < n; w += (long long)gridDim.x * SS_T) {
+    int type, a, b, ra, rb;
+    Box ba, bb;
+    if (w < n1) {  // surface vertex vs surface triangle
+      type = PAIR_SPT;
+      a = lv[w / nt];
+      b = lt[w % nt];
+      ra = d.sv[a];
+      rb = d.st[b].x;
+      if (d.vcomp[ra] == d.vcomp[rb]) continue;
+      ba = gel_box(d, PAIR_PT, a, sw);
+      bb = gel_box(d, PAIR_TP, b, sw);
+    } else {  // two surface edges, the first earlier in the list
+      const long long u = w - n1;
+      const int i = (int)(u / ne), k = (int)(u % ne);
+      if (k <= i) continue;
+      type = PAIR_SEE;
+      a = le[i];
+      b = le[k];
+      ra = d.se[a].x;
+      rb = d.se[b].x;
+      if (d.vcomp[ra] == d.vcomp[rb]) continue;
+      ba = gel_box(d, PAIR_EE, a, sw);
+      bb = gel_box(d, PAIR_EE, b, sw);
+    }
+    if (!near_boxes(ba, bb, G.dhat)) continue;
+    const int pos = atomicAdd(&d.gv[g].npair, 1);
+    if (pos < G.pcap)
+      d.pairs[G.pbase + pos] = make_int4(type, a, b, g);
+    else
+      atomicOr(&d.gv[g].flags, 32);  // the host grows the segment and redoes the search
+  }
+}
+
+// the soft-soft candidates of the soft-soft gels in `phase`; returns the launches made
+int launch_ss_pairs(const Dev& d, int phase, int mode, cudaStream_t st) {
+  if (d.n_ss <= 0) return 0;
+  k_ss_boxes<<<d.n_ss, SS_T, 0, st>>>(d, phase, mode);
+  k_ss_filter<<<dim3(std::max(1, std::min(64, (d.ss_maxq + SS_T - 1) / SS_T)), d.n_ss), SS_T, 0, st>>>(d, phase, mode);
+  k_ss_pairs<<<dim3(std::max(8, 592 / d.n_ss), d.n_ss), SS_T, 0, st>>>(d, phase, mode);
+  count_launch(3);
+  return 3;
+}
+
 // the pair in slot i, if its gel is in `phase` (and, optionally, not converged)
 __device__ __forceinline__ bool pair_slot(const Dev& d, int i, int phase, bool skip_conv, int4& pr) {
   const int g = d.pslot_gel[i];
@@ -533,6 +679,49 @@ __device__ __forceinline__ int find_block(const Dev& d, int row, int col) {
   return -1;
 }
 
+// Block (row, col) of a soft-soft pair between two bodies: not in the mesh pattern, so it takes a
+// free slot of the row (a padding position: column = the row itself, past the diagonal, value 0
+// after the gather) by a compare-and-swap of its column, listed for the reset before the next
+// assembly.  Every claimer of a row walks its slots in the same order and takes the first free
+// one, and a failed swap shows the column that won it, so a block gets one slot however many
+// pairs claim it at once (a slot never becomes free again before the reset).  -1: no free slot.
+__device__ __forceinline__ int claim_block(const Dev& d, int row, int col) {
+  const int s = row >> 5, lane = row & 31;
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5, dg = d.diag_pos[row];
+  for (int k = 0; k < w; ++k) {
+    const int bp = o + 32 * k + lane;
+    const int c = d.colidx[bp];
+    if (c == col) return bp;
+    if (c != row || bp == dg) continue;
+    const int old = atomicCAS(&d.colidx[bp], row, col);
+    if (old == col) return bp;  // another pair claimed this block here first
+    if (old != row) continue;   // another block took the slot
+    const int q = atomicAdd(d.ss_nclaim, 1);
+    if (q < d.ss_claim_cap) {
+      d.ss_claim[q] = bp;
+      return bp;
+    }
+    return -1;  // not reached: the list holds every padding slot of the soft-soft gels
+  }
+  return -1;
+}
+
+// Reset of the claimed slots (one CTA; before the contact assembly of every Newton iteration)
+__global__ void k_ss_reset(Dev d) {
+  const int n = min(*d.ss_nclaim, d.ss_claim_cap);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int bp = d.ss_claim[k];
+    d.colidx[bp] = d.bp_row[bp];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *d.ss_nclaim = 0;
+}
+
+void launch_ss_reset(const Dev& d, cudaStream_t st) {
+  k_ss_reset<<<1, 512, 0, st>>>(d);
+  count_launch(1);
+}
+
 // Contact assembly, part 1: one thread per candidate slot.  Active pairs (d < dhat) add their
 // barrier gradient and the contact force; a pair whose value depends on a single gel point adds
 // its projected block in closed form (the Hessian of b(d(P)) in the one free point is
@@ -551,18 +740,19 @@ __global__ void __launch_bounds__(128) k_contact_pairs(Dev d, int phase) {
   int rows[4];
   pair_points(d, pr, 0.0, false, P, rows);
   PairBarrier pb;
-  if (!pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), pb)) return;
+  if (!pair_barrier_setup(pair_kind(pr.x), P, G.dhat, pair_eps_x(d, pr), pb)) return;
   atomicAdd(&d.gv[g].active_pairs, 1);
   const double kap = d.gc[g].kappa;  // the step's barrier stiffness (host-set, adaptive)
   int slots[4], ns = 0;
   for (int k = 0; k < 4; ++k)
     if (rows[k] >= 0 && (pb.involved >> k) & 1) slots[ns++] = k;
+  const bool rigid = pr.x < PAIR_SPT;  // soft-soft forces are internal: not in the indenter force
   for (int a = 0; a < ns; ++a) {
     const int ra = rows[slots[a]];
     double gr[3];
     for (int c = 0; c < 3; ++c) {
       gr[c] = kap * pair_grad_entry(pb, 3 * slots[a] + c);
-      atomicAdd(&d.gv[g].fc[c], -gr[c]);
+      if (rigid) atomicAdd(&d.gv[g].fc[c], -gr[c]);
     }
     if (d.fixed[ra]) continue;
     atomicAdd(&d.cgrad[ra].x, gr[0]);
@@ -654,7 +844,7 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d, int mode)
       int rows[4];
       if (k >= d.crec_cap) {
         pair_points(d, pr, 0.0, false, w.P, rows);
-        pair_barrier_setup(pr.x == PAIR_EE ? 1 : 0, w.P, G.dhat, pair_eps_x(d, pr), w.pb);
+        pair_barrier_setup(pair_kind(pr.x), w.P, G.dhat, pair_eps_x(d, pr), w.pb);
       } else {
         pair_rows(d, pr, rows);
       }
@@ -672,14 +862,28 @@ __global__ void __launch_bounds__(32 * CW_WARPS) k_contact_hess(Dev d, int mode)
     team_pair_block(w.pb, w.fd, nf, m, w.pj.T, w.pj.H, tm);
     team_psd_project(w.pj, nf, tm);
     const int g = w.g;
+    // a soft-soft pair's blocks between its two bodies claim free slots; if one finds none, all of
+    // them are left out (the pair's block-diagonal part, its principal submatrices on each body,
+    // is PSD on its own, so the matrix stays PSD and the direction a descent one)
+    bool cross = false, miss = false;
+    int bp = -1;
     if (tm.id < ns * ns) {
       const int a = tm.id / ns, c = tm.id - a * ns;
       const int ra = w.rows[w.slots[a]], rc = w.rows[w.slots[c]];
-      int bp = -1;
       if (!d.fixed[ra] && !d.fixed[rc]) {
-        bp = find_block(d, ra, rc);
-        if (bp < 0) atomicOr(&d.gv[g].flags, 16);
+        cross = d.gi[g].ncomp > 1 && d.vcomp[ra] != d.vcomp[rc];
+        bp = cross ? claim_block(d, ra, rc) : find_block(d, ra, rc);
+        if (bp < 0) {
+          if (cross) miss = true;
+          else atomicOr(&d.gv[g].flags, 16);
+        }
       }
+    }
+    if (__any_sync(0xffffffffu, miss)) {
+      if (cross) bp = -1;
+      if (tm.id == 0) atomicAdd(&d.gv[g].ss_cut, 1);
+    }
+    if (tm.id < ns * ns) {
       w.bp[tm.id] = bp;
       if (mode == 0) d.chbp[(size_t)k * CH_BP + 1 + tm.id] = bp;
     }
@@ -743,11 +947,12 @@ __global__ void __launch_bounds__(128) k_fric_setup(Dev d, int phase) {
   const int4 pr = d.pairs[i];
   f.pr = pr;
   f.active = 0;
+  if (pr.x >= PAIR_SPT) return;  // friction acts against the rigid indenter only
   double P[4][3];
   int rows[4];
   pair_points(d, pr, 0.0, true, P, rows);
   DType ty;
-  const double D = pair_d2(pr.x == PAIR_EE ? 1 : 0, P, &ty);
+  const double D = pair_d2(pair_kind(pr.x), P, &ty);
   if (!(D > 0.0) || !(D < G.dhat * G.dhat)) return;
   double b, bD, bDD;
   barrier_D(D, G.dhat, &b, &bD, &bDD);
@@ -942,7 +1147,7 @@ __global__ void __launch_bounds__(128) k_accd(Dev d, int phase, int mode, int ma
       for (int c = 0; c < 3; ++c) dP[k][c] = Q[k][c] - P[k][c];
   }
   double toi = 1.0;
-  const int r = accd_pair(pr.x == PAIR_EE ? 1 : 0, P, dP, ACCD_S, 1.0, maxit, &toi);
+  const int r = accd_pair(pair_kind(pr.x), P, dP, ACCD_S, 1.0, maxit, &toi);
   if (r == 1) {
     atomic_min_pos(&d.gv[g].toi_bits, toi);
     atomicOr(&d.gv[g].flags, 8);
@@ -962,7 +1167,7 @@ __global__ void k_min_dist(Dev d, int phase) {
   int rows[4];
   pair_points(d, pr, 0.0, false, P, rows);
   DType ty;
-  const double D = pair_d2(pr.x == PAIR_EE ? 1 : 0, P, &ty);
+  const double D = pair_d2(pair_kind(pr.x), P, &ty);
   atomic_min_pos(&d.gv[g].dmin_bits, sqrt(fmax(D, 0.0)));
   if (D < d.gi[g].dhat * d.gi[g].dhat) atomicAdd(&d.gv[g].active_pairs, 1);
 }
@@ -1012,7 +1217,7 @@ __global__ void __launch_bounds__(EN_T) k_energy(Dev d, int phase, const int4* p
       double P[4][3], dist;
       int rows[4];
       pair_points(d, pr, alpha, false, P, rows);
-      acc += d.gc[g].kappa * pair_energy(pr.x == PAIR_EE ? 1 : 0, P, G.dhat, pair_eps_x(d, pr), &dist);
+      acc += d.gc[g].kappa * pair_energy(pair_kind(pr.x), P, G.dhat, pair_eps_x(d, pr), &dist);
     }
   } else if (phase != PH_EVAL) {  // lagged friction records of the running (sub)step
     for (int i = pc.z * EN_T + threadIdx.x; i < v.nfric; i += pc.w * EN_T) {

@@ -1342,6 +1342,7 @@ __global__ void k_gel_op(Dev d, int phase, int op) {
     v.dmin_bits = dbits(CUDART_INF);
     v.flags = 0;
     v.ls_total = 0;
+    v.ss_cut = 0;
     v.active_pairs = 0;
   } else if (op == 4) {  // the final state's distance minimum and active-pair count follow
     v.dmin_bits = dbits(CUDART_INF);

@@ -35,6 +35,12 @@ constexpr int NTAB = 3;        // hash tables per gel: indenter tris, indenter v
 constexpr int PAIR_PT = 0;     // gel surface vertex   vs indenter triangle
 constexpr int PAIR_TP = 1;     // indenter vertex      vs gel surface triangle
 constexpr int PAIR_EE = 2;     // gel surface edge     vs indenter edge
+// between two deformable bodies of one mesh (surface primitives of different connected components)
+constexpr int PAIR_SPT = 3;    // surface vertex       vs surface triangle
+constexpr int PAIR_SEE = 4;    // surface edge         vs surface edge
+// distance kind of a pair type: 1 edge-edge (mollified), 0 point-triangle
+__host__ __device__ constexpr int pair_kind(int type) { return (type == PAIR_EE || type == PAIR_SEE) ? 1 : 0; }
+constexpr int SS_MAXC = 4;     // connected components of a mesh that take part in soft-soft contact
 constexpr double ACCD_S = 0.1; // ACCD: the gap may shrink to this fraction per sweep
 
 // phases of a gel inside a batch
@@ -57,6 +63,8 @@ struct GelInfo {  // per gel, read-only after create
   double org[3];             // hash grid origin
   double mu_f, eps_v;        // IPC lagged friction: coefficient (0: frictionless), velocity threshold
   int top0, ntop;            // top-surface triangles (rest outward normal up) in Dev::top
+  int ncomp;                 // connected components of the tet mesh (> 1: soft-soft contact)
+  int ss;                    // its index in the soft-soft gel list (-1: one body)
 };
 
 struct GelCtl {  // per gel, written by the host before the launches of an iteration
@@ -103,7 +111,7 @@ struct GelVar {  // per gel, written by the device
   double ibox_lo[3], ibox_hi[3];  // indenter bounding box of the current hash build
   int flags;                 // 1 hash overflow, 2 ACCD cap, 4 inverted tet, 8 ACCD hit, 16 pattern miss
   int nfric;                 // friction records of the running (sub)step (slots of its pair segment)
-  int pad3_;
+  int ss_cut;                // soft-soft pairs whose cross-body blocks found no free slot (this substep)
 };
 
 // Per-gel record of the pooled streaming PCG (k_solve.cu): written by the gel's owner warp after
@@ -227,6 +235,17 @@ struct Dev {
   C1Rec* c1rec;    // single-free-point barrier blocks (appended; one per pair slot at most)
   FricRec* fric;   // lagged friction records, one per pair slot at the (sub)step start (null: none)
   int4* top;       // top-surface triangles of every gel (rows a, b, c), the readout's surface
+  // soft-soft contact (gels whose mesh has several connected components)
+  int8_t* vcomp;   // per row: its connected component within its gel's mesh
+  int n_ss;        // soft-soft gels, and the most surface primitives (queries) of one of them
+  int ss_maxq;
+  int* ss_gel;     // the soft-soft gels, and per soft-soft gel: component boxes (SS_MAXC x 6) ...
+  double* ss_box;
+  int* ss_cnt;     // ... and the counts of its listed vertices, triangles, edges (3 each)
+  int* ss_list;    // listed primitives near another component (global query ids, the gel's query range)
+  int* ss_claim;   // block positions whose column a cross-body block took (reset every Newton iteration)
+  int* ss_nclaim;
+  int ss_claim_cap;
   int* c1_n;
   double4_32a* cgrad;  // contact gradient per row: accumulated by the contact kernels, added by the gather
   int* err;

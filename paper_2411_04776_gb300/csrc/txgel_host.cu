@@ -40,6 +40,8 @@ void launch_indenter_pose(const Dev& d, int phase, int n_ind_verts, cudaStream_t
 void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st);
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st);
 void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st);
+int launch_ss_pairs(const Dev& d, int phase, int mode, cudaStream_t st);
+void launch_ss_reset(const Dev& d, cudaStream_t st);
 void launch_contact_compute(const Dev& d, int phase, bool mixed, cudaStream_t st);
 void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
 void launch_accd(const Dev& d, int phase, int mode, int maxit, cudaStream_t st);
@@ -106,6 +108,10 @@ constexpr int CREC_PER_GEL = 512;
 constexpr int CREC_BASE = 8192;
 constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernels handle
 constexpr int PCG_POOL_MIN_GELS = 32;  // automatic plan: pooled streaming kernels from this many gels
+// soft-soft contact: spare block positions of a surface row near another body, and "near": within
+// this fraction of that body's rest bounding-box diagonal (plus d_hat) of its rest box
+constexpr int SS_SLOTS = 24;
+constexpr double SS_NEAR = 0.25;
                                       // being solved on (per-gel CTA groups below: measured faster
                                       // up to 16 gels, slower from 64)
 constexpr int PCG_CTAS_PER_SM_CAP = 8;  // plan arrays are sized for this many CTAs per SM
@@ -171,6 +177,8 @@ struct Mesh {
   std::vector<std::array<int, 2>> ie;
   std::vector<double> ie_len2;
   std::vector<std::vector<int>> adj;  // sorted neighbour lists (incl. self)
+  std::vector<int8_t> comp;           // connected component of each vertex (vertex 0: component 0)
+  int ncomp = 1;
   double mu = 0, lam = 0, kappa = 0, bbox = 0, cell = 0, org[3] = {0, 0, 0};
   double mean_se = 0, lo[3] = {0, 0, 0};
   tx_params prm{};
@@ -295,6 +303,29 @@ tx_status build_gel_part(const tx_gel_desc* d, Mesh& m) {
   for (auto& l : m.adj) {
     std::sort(l.begin(), l.end());
     l.erase(std::unique(l.begin(), l.end()), l.end());
+  }
+  // connected components through the tets, numbered in the order of their first vertex; a mesh of
+  // several bodies takes part in soft-soft contact, up to SS_MAXC of them
+  m.comp.assign(m.nv, -1);
+  m.ncomp = 0;
+  std::vector<int> stack;
+  for (int i = 0; i < m.nv; ++i)
+    if (m.adj[i].size() == 1) m.comp[i] = 0;  // in no tet: on no surface, never in a pair
+  for (int i = 0; i < m.nv; ++i) {
+    if (m.comp[i] >= 0) continue;
+    if (m.ncomp == SS_MAXC) return TX_ERR_ARG;
+    m.comp[i] = (int8_t)m.ncomp;
+    stack.assign(1, i);
+    while (!stack.empty()) {
+      const int v = stack.back();
+      stack.pop_back();
+      for (int u : m.adj[v])
+        if (m.comp[u] < 0) {
+          m.comp[u] = (int8_t)m.ncomp;
+          stack.push_back(u);
+        }
+    }
+    ++m.ncomp;
   }
   return TX_OK;
 }
@@ -464,6 +495,7 @@ struct tx_batch {
   std::vector<Mesh> mesh;
   std::vector<GelInfo> gi;
   std::vector<Run> run;
+  std::vector<int> ss_gel_h;  // the gels whose mesh holds several bodies (soft-soft contact)
   GelCtl* gc_h = nullptr;   // pinned
   GelVar* gv_h = nullptr;   // pinned
   Dev d{};
@@ -817,19 +849,56 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     int fc = 0;
     for (auto f : m.fixed) fc += f;
     G.fixed_count = fc;
+    G.ncomp = m.ncomp;
+    G.ss = -1;
+    if (m.ncomp > 1) {
+      G.ss = (int)b->ss_gel_h.size();
+      b->ss_gel_h.push_back(g);
+    }
   }
   b->total_rows = rows;
   const int nslices = rows / SLICE;
-  // ---- sliced BSR pattern
+  // ---- sliced BSR pattern.  A mesh of several bodies gives the free surface rows that lie, at
+  // rest, near the box of another body SS_SLOTS spare positions for the blocks of soft-soft
+  // pairs (claimed during the assembly); other rows keep only the padding of their slice.
   std::vector<int> slice_off(nslices + 1, 0);
   for (int g = 0; g < n; ++g) {
     const Mesh& m = b->mesh[g];
     const GelInfo& G = b->gi[g];
+    std::vector<int> need(m.nv);
+    for (int i = 0; i < m.nv; ++i) need[i] = (int)m.adj[i].size();
+    if (m.ncomp > 1) {
+      double lo[SS_MAXC][3], hi[SS_MAXC][3];
+      for (int c = 0; c < SS_MAXC; ++c)
+        for (int a = 0; a < 3; ++a) {
+          lo[c][a] = INFINITY;
+          hi[c][a] = -INFINITY;
+        }
+      for (int i = 0; i < m.nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+          lo[m.comp[i]][a] = std::min(lo[m.comp[i]][a], m.X[3 * i + a]);
+          hi[m.comp[i]][a] = std::max(hi[m.comp[i]][a], m.X[3 * i + a]);
+        }
+      for (int i : m.sv) {
+        if (m.fixed[i]) continue;
+        bool near = false;
+        for (int c = 0; c < m.ncomp && !near; ++c) {
+          if (c == m.comp[i]) continue;
+          double diag2 = 0.0;
+          for (int a = 0; a < 3; ++a) diag2 += (hi[c][a] - lo[c][a]) * (hi[c][a] - lo[c][a]);
+          const double pad = SS_NEAR * std::sqrt(diag2) + m.prm.dhat;
+          near = true;
+          for (int a = 0; a < 3; ++a)
+            if (m.X[3 * i + a] < lo[c][a] - pad || m.X[3 * i + a] > hi[c][a] + pad) near = false;
+        }
+        if (near) need[i] += SS_SLOTS;
+      }
+    }
     for (int s = 0; s < G.ns; ++s) {
       int w = 1;
       for (int l = 0; l < SLICE; ++l) {
         const int i = s * SLICE + l;
-        if (i < m.nv) w = std::max(w, (int)m.adj[i].size());
+        if (i < m.nv) w = std::max(w, need[i]);
       }
       slice_off[G.s0 + s + 1] = w * SLICE;
     }
@@ -867,6 +936,19 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
       }
     }
   }
+  // soft-soft gels: every padding position of their rows may be claimed once per assembly
+  std::vector<int8_t> vcomp(rows, 0);
+  long long claim_cap = 0;
+  for (int g = 0; g < n; ++g) {
+    const Mesh& m = b->mesh[g];
+    const GelInfo& G = b->gi[g];
+    for (int l = 0; l < m.nv; ++l) vcomp[G.v0 + l] = m.comp[l];
+    if (m.ncomp > 1)
+      for (int l = 0; l < m.nv; ++l) {
+        const int r = G.v0 + l, s = r / SLICE;
+        claim_cap += (slice_off[s + 1] - slice_off[s]) / SLICE - (long long)m.adj[l].size();
+      }
+  }
   auto bp_of = [&](int g, int li, int lj) {
     const Mesh& m = b->mesh[g];
     const auto& a = m.adj[li];
@@ -898,6 +980,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     GelInfo& G = b->gi[g];
     G.top0 = (int)top4.size();
     for (const auto& t : m.st) {
+      if (m.comp[t[0]] != 0) continue;  // the gelpad: component 0 (a mesh may hold other bodies)
       const double* A = &m.X[3 * t[0]];
       const double* Bv = &m.X[3 * t[1]];
       const double* C = &m.X[3 * t[2]];
@@ -1080,6 +1163,17 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.top = M.get<int4>(std::max<size_t>(top4.size(), 1));
   d.cwork_n = M.get<int>(4);
   d.c1_n = M.get<int>(4);
+  d.vcomp = M.get<int8_t>(rows);
+  d.n_ss = (int)b->ss_gel_h.size();
+  d.ss_maxq = 0;
+  for (int g : b->ss_gel_h) d.ss_maxq = std::max(d.ss_maxq, b->gi[g].nq);
+  d.ss_gel = M.get<int>(std::max(d.n_ss, 1));
+  d.ss_box = M.get<double>((size_t)std::max(d.n_ss, 1) * SS_MAXC * 6);
+  d.ss_cnt = M.get<int>(3 * (size_t)std::max(d.n_ss, 1));
+  d.ss_list = M.get<int>(std::max(nq, 1));
+  d.ss_claim_cap = (int)std::min<long long>(std::max<long long>(claim_cap, 1), 1LL << 30);
+  d.ss_claim = M.get<int>(d.ss_claim_cap);
+  d.ss_nclaim = M.get<int>(4);
   b->pieces = M.get<int4>(b->npieces);
   b->gel_piece = M.get<int>(n + 1);
   b->part_e = M.get<double>(b->npieces);
@@ -1161,6 +1255,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   U(d.it_gel, it_gel.data(), sizeof(int) * nit);
   U(d.ie_gel, ie_gel.data(), sizeof(int) * nie);
   U(d.top, top4.data(), sizeof(int4) * top4.size());
+  U(d.vcomp, vcomp.data(), rows);
+  U(d.ss_gel, b->ss_gel_h.data(), sizeof(int) * b->ss_gel_h.size());
   U(b->pieces, b->pieces_h.data(), sizeof(int4) * b->npieces);
   U(b->gel_piece, b->gel_piece_h.data(), sizeof(int) * (n + 1));
   U((void*)b->plan.slice_gel, slice_gel.data(), sizeof(int) * nslices);
@@ -1169,6 +1265,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   if (e == cudaSuccess) e = cudaMemset(d.p, 0, sizeof(double4_32a) * rows);
   if (e == cudaSuccess) e = cudaMemset(d.gv, 0, sizeof(GelVar) * n);
   if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(d.ss_nclaim, 0, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(d.qcount, 0, sizeof(int) * (nq + 1));
   if (e == cudaSuccess) e = cudaMemset(d.tscr, 0, sizeof(double) * TS * (size_t)std::max(tets, 1));
   if (e != cudaSuccess) {
@@ -1278,10 +1375,11 @@ tx_status do_begin(tx_batch* b, std::vector<int> set, int retries = 0) {
   launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
   launch_query(d, PH_BEGIN, 1 | 4, st);
   launch_pair_ranges(d, PH_BEGIN, 0, st);
+  const int nss = launch_ss_pairs(d, PH_BEGIN, 0, st);
   const int accd_max = b->mesh[set[0]].prm.accd_max_iter;
   launch_accd(d, PH_BEGIN, 1, accd_max, st);
   launch_min_dist(d, PH_BEGIN, st);
-  prof_close(b, 13);
+  prof_close(b, 13 + nss);
   CK(cudaGetLastError());
   s = download_var(b);
   if (s != TX_OK) return s;
@@ -1401,7 +1499,8 @@ void post_pcg_launch(tx_batch* b, int accd_max) {
   launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, st);
   launch_query(d, PH_NEWTON, 1 | 2 | 8, st);
   launch_pair_ranges(d, PH_NEWTON, 1, st);
-  prof_close(b, 7);
+  const int nss = launch_ss_pairs(d, PH_NEWTON, 2 | 8, st);
+  prof_close(b, 7 + nss);
   prof_open(b, PR_ACCD);
   launch_accd(d, PH_NEWTON, 0, accd_max, st);
   launch_gel_op(d, PH_NEWTON, 2, st);
@@ -1477,6 +1576,7 @@ tx_status finalize_substeps(tx_batch* b, const std::vector<int>& fin) {
     R.stack.pop_back();
     R.acc.newton_iters += R.newton_sub;
     R.acc.ls_halvings += v.ls_total;
+    R.acc.soft_pairs_cut += v.ss_cut;
     R.acc.energy = v.E_cur;
     R.acc.active_pairs = v.active_pairs;
     R.acc.candidate_pairs = v.npair;
@@ -1714,9 +1814,10 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
     cs = b->st2;
   }
   prof_open(b, PR_CONTACT, cs);
+  if (d.n_ss > 0) launch_ss_reset(d, cs);  // the cross-body blocks of the last assembly give their slots back
   launch_contact_compute(d, PH_NEWTON, b->mixed, cs);
   if (b->friction) launch_fric(d, PH_NEWTON, 0, b->mixed, cs);  // friction gradient and force
-  prof_close(b, b->friction ? 3 : 2, cs);
+  prof_close(b, (b->friction ? 3 : 2) + (d.n_ss > 0 ? 1 : 0), cs);
   if (cs != st) CK(cudaEventRecord(b->ev_join, cs));
   prof_open(b, PR_TET);
   launch_tet_assemble(d, PH_NEWTON, b->mixed, st);
@@ -2091,6 +2192,7 @@ tx_status eval_setup(tx_batch* b, int g, const double* x, const double* xt, doub
   launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, b->st);
   launch_query(d, PH_EVAL, 1, b->st);
   launch_pair_ranges(d, PH_EVAL, 0, b->st);
+  launch_ss_pairs(d, PH_EVAL, 0, b->st);
   CK(cudaGetLastError());
   s = download_var(b);
   if (s != TX_OK) return s;
@@ -2107,6 +2209,7 @@ tx_status eval_setup(tx_batch* b, int g, const double* x, const double* xt, doub
     launch_scan(d.qcount, d.qoff, d.nq, b->scan_tmp, b->st);
     launch_query(d, PH_EVAL, 1, b->st);
     launch_pair_ranges(d, PH_EVAL, 0, b->st);
+    launch_ss_pairs(d, PH_EVAL, 0, b->st);
   }
   return TX_OK;
 }
@@ -2540,6 +2643,7 @@ tx_status tx_gel_gradient(tx_gel* gl, const double* x, const double* xt, double 
   if (s != TX_OK) return s;
   Dev& d = b->d;
   launch_gel_op(d, PH_EVAL, 0, b->st);
+  if (d.n_ss > 0) launch_ss_reset(d, b->st);
   launch_contact_compute(d, PH_EVAL, b->mixed, b->st);
   launch_tet_assemble(d, PH_EVAL, b->mixed, b->st);
   launch_gather(d, PH_EVAL, b->nbp, b->mixed, b->st);

@@ -1,0 +1,177 @@
+"""Soft-to-soft contact (a mesh of two bodies: the gelpad and a soft ball, pressed by a rigid plate)
+through the C ABI: every step against the FP64 oracle (positions, active pairs, the plate's force
+on the mesh, no pair left out of the matrix); the energy, gradient and active pairs at a squeezed
+state; a ball dropped on a gel whose vertices are all held against the same ball dropped on a
+rigid copy of that gel's surface (both on the GPU: soft-soft pairs against rigid pairs); and the
+readouts, which see the gelpad's top surface only."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2411_04776_gb300 import binding as B  # noqa: E402
+from paper_2411_04776_gb300 import workloads as W  # noqa: E402
+from tests.gpu_util import PARITY_NEWTON_TOL, POS_TOL  # noqa: E402
+
+STEPS = 6
+
+
+def ball_scene():
+    return W.gel_ball(6, grid=W.GRID_SMALL, n_press=10, n_slide=4, depth=0.6e-3)
+
+
+@pytest.fixture(scope="module")
+def reference():
+    O.set_threads(0)
+    wl = ball_scene()
+    og = O.OracleGel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max=400)
+    assert og.components()[0] == 2
+    out = []
+    for s in range(STEPS):
+        info = og.step(wl.poses[s], wl.dt)
+        assert info["status"] == 0, info
+        x, _, fc, _ = og.state()
+        out.append((x.copy(), fc.copy(), info))
+    return wl, out
+
+
+def test_soft_ball_matches_oracle(reference):
+    """FP64 (mixed precision is not offered for a free body: its FP32 inner solves cannot resolve
+    the ball's rigid modes, held only by its mass, and the first step already ends elsewhere)."""
+    wl, ref = reference
+    precision = B.TX_PREC_FP64
+    gel = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max_iter=400, precision=precision,
+                              stream=torch.cuda.current_stream())
+    worst, ss_active, cut, errs = 0.0, 0, 0, []
+    try:
+        for s in range(STEPS):
+            assert gel.step(wl.poses[s], wl.dt) == 0
+            x, _, fc, st = gel.state()
+            xo, fo, info = ref[s]
+            assert st.active_pairs == info["active_pairs"], (s, st.active_pairs, info["active_pairs"])
+            cut += st.soft_pairs_cut
+            errs.append(float(np.abs(x - xo).max()))
+            worst = max(worst, errs[-1])
+            # the plate's force: the barrier's stiffness near d = 50 um turns the position gate into
+            # this relative bound
+            assert np.abs(np.asarray(fc) - fo).max() <= 2e-3 * max(1e-3, np.abs(fo).max()), (s, fc, fo)
+            ss_active = max(ss_active, info["active_pairs"])
+    finally:
+        gel.close()
+    print("soft ball (%s) vs oracle: max vertex error per step %s m, most active pairs %d, pair assemblies cut %d"
+          % ("fp64" if precision == B.TX_PREC_FP64 else "mixed", ["%.2e" % e for e in errs], ss_active, cut))
+    assert worst <= POS_TOL, worst
+    assert cut == 0, cut  # every cross-body block found a spare position
+
+
+def test_soft_ball_energy_and_gradient_match_oracle(reference):
+    """At the oracle's state after the squeeze (soft-soft pairs within d_hat): the GPU's energy
+    parts, active-pair count (indenter and soft-soft pairs together) and gradient of the step's
+    incremental potential, evaluated at that state, against the oracle's."""
+    wl, ref = reference
+    og = O.OracleGel.from_workload(wl)
+    xo = ref[-1][0]
+    pose = wl.poses[STEPS - 1]
+    counts = og.pair_counts(xo, pose)
+    assert counts[8] > 0 and counts[9] > 0, counts  # soft-soft pairs in contact
+    xt = xo + 1e-6  # any predictor
+    eo, po = og.energy(xo, xt, wl.dt, pose)
+    go, fo = og.gradient(xo, xt, wl.dt, pose)
+    gel = B.Gel.from_workload(wl)
+    try:
+        eg, pg = gel.energy(xo, xt, wl.dt, pose)
+        gg, fg = gel.gradient(xo, xt, wl.dt, pose)
+    finally:
+        gel.close()
+    assert pg["active"] == po["active"] == int(counts[5:].sum()), (pg, po, counts)
+    assert abs(pg["barrier"] - po["barrier"]) <= 1e-11 * abs(po["barrier"]), (pg, po)
+    assert abs(eg - eo) <= 1e-11 * abs(eo), (eg, eo)
+    free = wl.gel.dirichlet == 0
+    scale = np.abs(go[free]).max()
+    assert np.abs(gg[free] - go[free]).max() <= 1e-9 * scale, np.abs(gg[free] - go[free]).max() / scale
+    assert np.abs(np.asarray(fg) - fo).max() <= 1e-9 * max(np.abs(fo).max(), 1e-12), (fg, fo)
+
+
+def _held_gel_scene():
+    gel = W.gel_grid(*W.GRID_SMALL[0], W.GRID_SMALL[1])
+    c = (0.009, 0.012, gel.top + 2 * W.DHAT + 3e-3)
+    ball = W.ball_mesh(6, 3e-3, c)
+    gel.dirichlet[:] = 1
+    return gel, ball
+
+
+def test_ball_on_held_gel_equals_ball_on_rigid_copy():
+    """GPU against GPU: a ball dropped (gravity, initial velocity) on a gel whose vertices are all
+    held moves as the ball alone dropped on a rigid indenter made of that gel's surface at rest,
+    to the Newton tolerance (soft-soft pairs against the rigid pair path)."""
+    gel, ball = _held_gel_scene()
+    both = W.join_meshes(gel, ball)
+    far = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    plate = W.flat_plate(0.004, 3)
+    f = np.concatenate([gel.tets[:, [1, 2, 3]], gel.tets[:, [0, 2, 3]], gel.tets[:, [0, 1, 3]], gel.tets[:, [0, 1, 2]]])
+    key, cnt = np.unique(np.sort(f, axis=1), axis=0, return_counts=True)
+    st = key[cnt == 1]
+    sv = np.unique(st)
+    remap = np.full(len(gel.verts), -1)
+    remap[sv] = np.arange(len(sv))
+    ident = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+
+    def diag(v):
+        return float(np.linalg.norm(v.max(axis=0) - v.min(axis=0)))
+
+    kw = dict(dhat=W.DHAT, kappa=500.0, gravity=(0.0, 0.0, -9.81), newton_max_iter=2000,
+              stream=torch.cuda.current_stream())
+    tol = 1e-7
+    a = B.Gel(B.GelDesc(both.verts, both.tets, both.dirichlet, (W.YOUNG, W.POISSON, W.DENSITY), plate.verts,
+                        plate.tris, far, newton_tol=tol, **{k: v for k, v in kw.items() if k != "stream"}),
+              kw["stream"])
+    b = B.Gel(B.GelDesc(ball.verts, ball.tets, ball.dirichlet, (W.YOUNG, W.POISSON, W.DENSITY), gel.verts[sv],
+                        remap[st].astype(np.int32), ident, newton_tol=tol * diag(both.verts) / diag(ball.verts),
+                        **{k: v for k, v in kw.items() if k != "stream"}), kw["stream"])
+    v = np.tile([0.01, 0.0, -0.05], (len(ball.verts), 1))
+    a.set_state(both.verts, np.concatenate([np.zeros_like(gel.verts), v]), far)
+    b.set_state(ball.verts, v, ident)
+    err, act = 0.0, 0
+    try:
+        for s in range(6):
+            assert a.step(far, W.DT) == 0 and b.step(ident, W.DT) == 0
+            sa, sb = a.stats(), b.stats()
+            assert sa["active_pairs"] == sb["active_pairs"], (s, sa, sb)
+            act = max(act, sa["active_pairs"])
+            err = max(err, float(np.abs(a.state()[0][len(gel.verts):] - b.state()[0]).max()))
+    finally:
+        a.close()
+        b.close()
+    print("ball on a held gel vs on its rigid copy (GPU): max difference %.3e m, most active pairs %d" % (err, act))
+    assert act > 20, act
+    assert err < 1e-9, err
+
+
+def test_readout_sees_the_gelpad_only(reference):
+    """Markers and the height map of the two-body mesh use the gelpad's top surface (body 0): the
+    ball above it never shows, and both readouts equal the oracle's of the same state."""
+    wl, ref = reference
+    xo = ref[-1][0]
+    og = O.OracleGel.from_workload(wl)
+    gel = B.Gel.from_workload(wl)
+    try:
+        gel.set_state(xo, np.zeros_like(xo), wl.poses[STEPS - 1])
+        rng = np.random.default_rng(3)
+        m = np.column_stack([rng.uniform(0.0, 0.018, 80), rng.uniform(0.0, 0.024, 80)])
+        pg, fg = gel.markers(m)
+        po, fo = og.markers(xo, m)
+        assert np.array_equal(fg, fo) and fg.all()
+        assert np.abs(pg - po).max() <= 1e-15
+        grid = dict(nx=64, ny=80, x0=-0.5e-3, y0=-0.6e-3, dx=0.3e-3, dy=0.315e-3)
+        hg = gel.height_map(**grid)
+        ho = og.height_map(xo, grid["nx"], grid["ny"], grid["x0"], grid["y0"], grid["dx"], grid["dy"])
+    finally:
+        gel.close()
+    assert np.array_equal(np.isnan(hg), np.isnan(ho))
+    ok = ~np.isnan(ho)
+    assert np.abs(hg[ok] - ho[ok]).max() <= 1e-15
+    # the gel bulges by microns around the ball; the ball itself (from 2 d_hat above the top face
+    # up) never shows
+    assert np.nanmax(hg) < W.gel_grid(*W.GRID_SMALL[0], W.GRID_SMALL[1]).top + W.DHAT
