@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="mini", choices=["mini", "small", "batch_mini", "batch_mixed", "serve"])
+    ap.add_argument("--workload", default="mini", choices=["mini", "small", "batch_mini", "batch_mixed", "serve", "softball"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: total request rate [1/s]")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM admission budget")
@@ -84,13 +84,16 @@ def make_workload(kind, seed, n_gels=0):
         return [W.mini_gel(seed + g) for g in range(n_gels or 64)]
     if kind in ("batch_mixed", "serve"):  # config 2 / 4: resolutions drawn from the three grids
         return W.mixed_batch(n_gels or (1024 if kind == "serve" else 256), seed0=seed)
+    if kind == "softball":  # soft-to-soft contact: the gel, a 20^3 soft ball, a rigid plate
+        return [W.gel_ball(20, seed=seed)]
     return [W.mini_gel(seed)]
 
 
 NAMES = {"mini": "GelSight-Mini gel 41x51x9 (config 1)", "small": "small gel 10x13x4 (config 0)",
          "batch_mini": "batch of GelSight-Mini gels 41x51x9 (config 3 geometry)",
          "batch_mixed": "batch of gels with mixed resolutions (config 2)",
-         "serve": "serving: RL envs with mixed-resolution gels, Poisson step requests (config 4)"}
+         "serve": "serving: RL envs with mixed-resolution gels, Poisson step requests (config 4)",
+         "softball": "GelSight-Mini gel 41x51x9 + soft ball 20^3 (8000 verts) + rigid plate (soft-to-soft contact)"}
 
 
 def workload_config(wls, kind, precision):
@@ -355,6 +358,14 @@ def pcg_kernel_name(precision, n_gels):
     return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
 
 
+def ran_pcg_kernel(prof, precision, n_gels):
+    """pcg_kernel_name, unless the profile shows that a single gel's solves took the streaming
+    kernels (its slices did not fit the resident kernels' shared memory)."""
+    if n_gels == 1 and prof.get("pcg_resident_launches", 1) == 0 and prof.get("pcg_streaming_launches", 0) > 0:
+        return "k_pcg64" if precision == "fp64" else "k_pcg_mixed"
+    return pcg_kernel_name(precision, n_gels)
+
+
 def source_hash(files):
     """Hash of the CUDA sources a kernel is built from (the ncu counters in profiles/traffic.json
     are used only while these are unchanged)."""
@@ -559,7 +570,7 @@ def main():
                        "max": float(step_ms.max())},
         "newton_iters_per_step": prof["newton_iters"] / (ng * K),
         "pcg_iters_per_step": prof["pcg_iters"] / (ng * K),
-        "roofline": roofline(r["prof"], r["clocks"], args.precision, pcg_kernel_name(args.precision, ng), fma),
+        "roofline": roofline(r["prof"], r["clocks"], args.precision, ran_pcg_kernel(r["prof"], args.precision, ng), fma),
         "phases_ms": {k: round(v["ms"], 3) for k, v in r["prof"]["phases"].items()},
         "gpu_launches": r["prof"]["kernel_launches"],
         "pcg_launches": {"resident": r["prof"]["pcg_resident_launches"],
