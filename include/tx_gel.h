@@ -86,7 +86,10 @@ typedef struct tx_params {
                                per-gel-group streaming kernels; 2 always the pooled streaming
                                kernels (1 and 2: tests and measurements of one family).  A handle
                                takes the largest value any of its gels asks for.               */
-  int32_t reserved0;        /* must be 0                                                       */
+  int32_t pcg_coarse_off;   /* 1: no coarse space in the streaming FP64 PCG.  0 (default): a
+                               solve of one gel with a body held by no vertex adds an exact solve
+                               on that body's six rigid motions to block-Jacobi (two-level additive
+                               preconditioner for the free bodies of tx_gel_desc's meshes)      */
   double friction;          /* IPC lagged friction coefficient mu_f between gel and indenter
                                (0: frictionless, the default).  Pairs in contact at the start of a
                                (sub)step fix their closest points, tangent plane and normal force

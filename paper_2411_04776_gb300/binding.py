@@ -36,7 +36,7 @@ class tx_params(ctypes.Structure):
                 ("ls_max_halvings", ctypes.c_int32), ("accd_max_iter", ctypes.c_int32),
                 ("max_split_depth", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("pcg_cta_slices", ctypes.c_int32),
-                ("pcg_plan", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("pcg_plan", ctypes.c_int32), ("pcg_coarse_off", ctypes.c_int32),
                 ("friction", ctypes.c_double), ("friction_eps_v", ctypes.c_double),
                 ("kappa_adapt_max", ctypes.c_double), ("kappa_adapt_dmin", ctypes.c_double)]
 

@@ -135,6 +135,103 @@ __device__ __forceinline__ bool group_sum(const Dev& d, PcgCta& c, const double*
   return true;
 }
 
+// ---------------------------------------------------------------- coarse space of a free body
+// A body held by no vertex (a soft ball between the gelpad and the indenter) has six rigid motions
+// that only its mass resists (M / h^2, some 1e4 below the elastic diagonal): block-Jacobi leaves
+// them as the smallest eigenvalues of the preconditioned matrix and CG needs hundreds of
+// iterations.  The two-level additive preconditioner M^-1 + Z E^-1 Z^T adds an exact solve on
+// those motions (Z: per body row i, the 3 x 6 block [I | -[d_i]x] with d_i = x_i - c, E = Z^T A Z,
+// the rigid-body coarse space of additive Schwarz methods); it is SPD, so CG stays CG.  Z^T v of a
+// row vector v is (v, d x v); Z c is c_t + c_r x d.
+__device__ __forceinline__ void cz_zt(const double4_32a v, const double dd[3], double* o) {
+  o[0] += v.x;
+  o[1] += v.y;
+  o[2] += v.z;
+  o[3] += dd[1] * v.z - dd[2] * v.y;
+  o[4] += dd[2] * v.x - dd[0] * v.z;
+  o[5] += dd[0] * v.y - dd[1] * v.x;
+}
+
+// 6 x 6 SPD solve from the packed upper triangle E (row-major, i <= j) by Cholesky; false if E is
+// not numerically positive definite
+__device__ __forceinline__ bool cz_chol(const double* E, double* L) {
+  double A[6][6];
+  for (int i = 0, q = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j, ++q) A[i][j] = A[j][i] = E[q];
+  for (int j = 0; j < 6; ++j) {
+    double s = A[j][j];
+    for (int k = 0; k < j; ++k) s -= L[6 * j + k] * L[6 * j + k];
+    if (!(s > 1e-14 * fabs(A[j][j])) || !(s > 0.0)) return false;
+    L[6 * j + j] = sqrt(s);
+    for (int i = j + 1; i < 6; ++i) {
+      double t = A[i][j];
+      for (int k = 0; k < j; ++k) t -= L[6 * i + k] * L[6 * j + k];
+      L[6 * i + j] = t / L[6 * j + j];
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void cz_solve(const double* L, const double* b, double* x) {
+  double y[6];
+  for (int i = 0; i < 6; ++i) {
+    double t = b[i];
+    for (int k = 0; k < i; ++k) t -= L[6 * i + k] * y[k];
+    y[i] = t / L[6 * i + i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < 6; ++k) t -= L[6 * k + i] * x[k];
+    x[i] = t / L[6 * i + i];
+  }
+}
+
+// row q of the 6 x 6 product M v (M row-major)
+__device__ __forceinline__ double cz_mv(const double* M, const double* v, int q) {
+  double t = 0.0;
+  for (int k = 0; k < 6; ++k) t = fma(M[6 * q + k], v[k], t);
+  return t;
+}
+
+// (A Z)_r of a body row, and its contribution Z_r^T (A Z)_r to the packed upper triangle of E
+__device__ __forceinline__ void cz_row_e(const Dev& d, int s, int lane, int cb, const double* ctr, const double dr[3],
+                                         double* e21) {
+  const int o = d.slice_off[s], w = (d.slice_off[s + 1] - o) >> 5;
+  double y[3][6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int m = 0; m < 6; ++m) y[i][m] = 0.0;
+  for (int k = 0; k < w; ++k) {
+    const int c = __ldg(d.colidx + o + 32 * k + lane);
+    if (d.vcomp[c] != cb || d.fixed[c]) continue;
+    double v[9];
+    load_block64(d.vals + (size_t)9 * (o + 32 * k), lane, v);
+    const double4_32a xc = d.x[c];
+    const double dc[3] = {xc.x - ctr[0], xc.y - ctr[1], xc.z - ctr[2]};
+    // Z_c columns: e_0, e_1, e_2, e_0 x dc, e_1 x dc, e_2 x dc
+    const double z[3][3] = {{0.0, -dc[2], dc[1]}, {dc[2], 0.0, -dc[0]}, {-dc[1], dc[0], 0.0}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) y[i][m] += v[3 * i + m];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) y[i][3 + q] += v[3 * i] * z[q][0] + v[3 * i + 1] * z[q][1] + v[3 * i + 2] * z[q][2];
+    }
+  }
+  double col[6][6];  // Z_r^T y: column m = (y_m, dr x y_m)
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    col[0][m] = y[0][m];
+    col[1][m] = y[1][m];
+    col[2][m] = y[2][m];
+    col[3][m] = dr[1] * y[2][m] - dr[2] * y[1][m];
+    col[4][m] = dr[2] * y[0][m] - dr[0] * y[2][m];
+    col[5][m] = dr[0] * y[1][m] - dr[1] * y[0][m];
+  }
+  for (int i = 0, q = 0; i < 6; ++i)
+    for (int m = i; m < 6; ++m, ++q) e21[q] += col[i][m];
+}
+
 // g . p (stationarity test of the line search) and ||p||_inf per gel after a solve
 __device__ __forceinline__ void pcg_epilogue(const Dev& d, const PcgPlan& plan, PcgCta& c, double* dsm,
                                              double (*tot)[4], const int* gact, int* s_fail) {

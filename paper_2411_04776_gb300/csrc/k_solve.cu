@@ -234,24 +234,64 @@ void launch_precond(const Dev& d, int phase, bool mixed, cudaStream_t st) {
 // One projected-Newton direction per gel of the gels in `phase`: block-Jacobi preconditioned CG
 // on H p = -g (Chronopoulos-Gear: one reduction phase per iteration), FP64, stops per gel when
 // |r| <= eta |g| or after maxit iterations.
-__global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan, int maxit) {
+__global__ void __launch_bounds__(PCG_T, 4) k_pcg64(Dev d, int phase, PcgPlan plan, int maxit) {
   extern __shared__ double dsm[];  // [slices of this CTA][4]
   __shared__ double tot[PCG_MAXG][4];
   __shared__ double bbj[PCG_MAXG], thj[PCG_MAXG], gprev[PCG_MAXG], aprev[PCG_MAXG], alj[PCG_MAXG], bej[PCG_MAXG];
   __shared__ double rhoj[PCG_MAXG];
   __shared__ int gact[PCG_MAXG], run[PCG_MAXG];
   __shared__ int s_fail, s_any;
+  // coarse space (a group of one gel that has a free body): per-warp partials, E^-1, the
+  // recurrences Z^T r and Z^T s, the coarse correction c = E^-1 Z^T r, the group totals
+  __shared__ double czw[PCG_T / 32][CZ_N];
+  __shared__ double czEi[36], czr[6], czs[6], czc[6], czt[CZ_N];
+  __shared__ int cz_on;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   PcgCta c = pcg_cta(d, plan);
-  if (threadIdx.x == 0) s_fail = 0;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    cz_on = 0;
+  }
   for (int j = threadIdx.x; j < c.ng; j += PCG_T) {
     gact[j] = d.gc[c.g0 + j].phase == phase ? 1 : 0;
     run[j] = gact[j];
   }
   __syncthreads();
+  const GelInfo& G0 = d.gi[c.g0];
+  const bool coarse = c.ng == 1 && G0.cbody >= 0 && gact[0];  // uniform over the group
+  const int cb = G0.cbody;
+  // body row r: d = x_r - c (false for every other row)
+  auto cz_row = [&](int r, double dd[3]) {
+    if (!coarse || d.vcomp[r] != cb || d.fixed[r]) return false;
+    const double4_32a xr = d.x[r];
+    dd[0] = xr.x - G0.cctr[0];
+    dd[1] = xr.y - G0.cctr[1];
+    dd[2] = xr.z - G0.cctr[2];
+    return true;
+  };
+  // the CTA's sum of the per-warp partials [0, n) to its exchange slots (the group sum's barrier
+  // that follows makes them visible; they are read before the next group barrier)
+  auto cz_publish = [&](int n) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += PCG_T) {
+      double v = 0.0;
+      for (int q = 0; q < PCG_T / 32; ++q) v += czw[q][k];
+      d.czpart[(size_t)k * gridDim.x + blockIdx.x] = v;
+    }
+  };
+  // the group's totals [0, n) in CTA order (identical in every CTA), into czt
+  auto cz_collect = [&](int n) {
+    for (int k = threadIdx.x; k < n; k += PCG_T) {
+      double v = 0.0;
+      for (int q = c.c0; q < c.c0 + c.nc; ++q) v += d.czpart[(size_t)k * gridDim.x + q];
+      czt[k] = v;
+    }
+    __syncthreads();
+  };
   // ---- Galerkin start: x0 = rho p_prev, the minimiser of the quadratic model along the gel's
   // previous Newton direction (in d.p; rho = b.p_prev / p_prev.A p_prev, 0 without a usable one);
-  // a = A p_prev goes to d.w.  Partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3).
+  // a = A p_prev goes to d.w.  Partials b.p_prev (k = 0), p_prev.a (1), |b|^2 (3).  (With a
+  // coarse space, k_pcg_cz_setup left this CTA's partials of E = Z^T A Z, Z^T b and Z^T a.)
   for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
     double bp = 0.0, pw = 0.0, bb = 0.0;
     if (gact[plan.slice_gel[s] - c.g0]) {
@@ -285,6 +325,22 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     rhoj[j] = (pw > 0.0 && isfinite(rho)) ? rho : 0.0;  // a non-finite p_prev anywhere gives 0
   }
   __syncthreads();
+  if (coarse) {  // E^-1, Z^T b and Z^T a of the group (k_pcg_cz_factor)
+    const double* f = d.czfac + (size_t)CZ_F * c.c0;
+    for (int q = threadIdx.x; q < 48; q += PCG_T) {
+      if (q < 36) czEi[q] = f[q];
+      else czt[q - 36] = f[q];
+    }
+    if (threadIdx.x == 0) cz_on = f[48] != 0.0;  // off for this solve if E was not numerically SPD
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      czr[threadIdx.x] = czt[threadIdx.x] - rhoj[0] * czt[6 + threadIdx.x];  // Z^T r0, r0 = b - rho a
+      czs[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) czc[threadIdx.x] = cz_on ? cz_mv(czEi, czr, threadIdx.x) : 0.0;
+    __syncthreads();
+  }
   // ---- x = rho p_prev, r = b - rho a, u = M^-1 r, pp = s = 0
   for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
     const int j = plan.slice_gel[s] - c.g0;
@@ -306,11 +362,22 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
     d.p[r] = x;
     d.pp[r] = z;
     d.s[r] = z;
-    d.u[r] = mul3(d.Minv + 9 * r, b);
+    double4_32a u0 = mul3(d.Minv + 9 * r, b);
+    double dd[3];
+    if (cz_on && cz_row(r, dd)) {  // + Z c
+      u0.x += czc[0] + czc[4] * dd[2] - czc[5] * dd[1];
+      u0.y += czc[1] + czc[5] * dd[0] - czc[3] * dd[2];
+      u0.z += czc[2] + czc[3] * dd[1] - czc[4] * dd[0];
+    }
+    d.u[r] = u0;
   }
   if (!group_barrier(c, d, &s_fail)) return;  // u complete before the SpMV
+  const bool czi = coarse && cz_on;  // the coarse correction runs in this solve (uniform)
   for (int k = 1;; ++k) {
-    // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r)
+    // ---- w = A u; partials gamma = (r, u), delta = (w, u), rr = (r, r); with a coarse space Z^T w
+    // (added per slice into the warp's slots)
+    if (czi && lane == 0)
+      for (int q = 0; q < 6; ++q) czw[wid][q] = 0.0;
     for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
       double ga = 0.0, de = 0.0, rr = 0.0;
       if (run[plan.slice_gel[s] - c.g0]) {
@@ -322,6 +389,14 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
         ga = dot4(rv, uv);
         de = dot4(w, uv);
         rr = dot4(rv, rv);
+        if (czi) {
+          double czq[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, dd[3];
+          if (cz_row(r, dd)) cz_zt(w, dd, czq);
+          for (int q = 0; q < 6; ++q) {
+            const double v = warp_sum(czq[q]);
+            if (lane == 0) czw[wid][q] += v;
+          }
+        }
       }
       ga = warp_sum(ga);
       de = warp_sum(de);
@@ -332,7 +407,9 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
         dsm[(s - c.s0) * 4 + 2] = rr;
       }
     }
+    if (czi) cz_publish(6);
     if (!group_sum(d, c, dsm, 0, 3, tot, &s_fail)) return;
+    if (czi) cz_collect(6);
     // ---- per-gel scalars and convergence (identical in every CTA of the group)
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -356,9 +433,19 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
       aprev[j] = alpha;
       alj[j] = alpha;
       bej[j] = beta;
+      if (czi) {  // (one gel: j = 0) Z^T s = beta Z^T s + Z^T w, Z^T r -= alpha Z^T s
+        for (int q = 0; q < 6; ++q) {
+          czs[q] = fma(beta, czs[q], czt[q]);
+          czr[q] = fma(-alpha, czs[q], czr[q]);
+        }
+      }
     }
     __syncthreads();
     if (!s_any) break;
+    if (czi) {  // c = E^-1 Z^T r
+      if (threadIdx.x < 6) czc[threadIdx.x] = cz_mv(czEi, czr, threadIdx.x);
+      __syncthreads();
+    }
     // ---- vector updates
     for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
       const int j = plan.slice_gel[s] - c.g0;
@@ -375,11 +462,88 @@ __global__ void __launch_bounds__(PCG_T) k_pcg64(Dev d, int phase, PcgPlan plan,
       d.s[r] = sv;
       d.p[r] = x;
       d.r[r] = rv;
-      d.u[r] = mul3(d.Minv + 9 * r, rv);
+      double4_32a un = mul3(d.Minv + 9 * r, rv);
+      double dd[3];
+      if (czi && cz_row(r, dd)) {  // + Z c
+        un.x += czc[0] + czc[4] * dd[2] - czc[5] * dd[1];
+        un.y += czc[1] + czc[5] * dd[0] - czc[3] * dd[2];
+        un.z += czc[2] + czc[3] * dd[1] - czc[4] * dd[0];
+      }
+      d.u[r] = un;
     }
     if (!group_barrier(c, d, &s_fail)) return;
   }
   pcg_epilogue(d, plan, c, dsm, tot, gact, &s_fail);
+}
+
+// Coarse-space set-up of the streaming FP64 PCG, launched just before it over the same CTA
+// partition: per CTA (a group of one gel with a free body) the partial sums over its slices of
+// E = Z^T A Z (packed upper triangle, 21), Z^T b (6, b = -grad) and Z^T A p_prev (6), to d.czpart
+// (k_pcg64 adds them up in CTA order).  Its own kernel keeps the set-up's registers out of the
+// iteration kernel.
+__global__ void __launch_bounds__(PCG_T) k_pcg_cz_setup(Dev d, int phase, PcgPlan plan) {
+  __shared__ double czw[PCG_T / 32][CZ_N];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const PcgCta c = pcg_cta(d, plan);
+  const GelInfo& G0 = d.gi[c.g0];
+  if (!(c.ng == 1 && G0.cbody >= 0 && d.gc[c.g0].phase == phase)) return;
+  const int cb = G0.cbody;
+  double acc[CZ_N];
+  for (int q = 0; q < CZ_N; ++q) acc[q] = 0.0;
+  for (int s = c.s0 + wid; s < c.s1; s += PCG_T / 32) {
+    const int r = 32 * s + lane;
+    if (d.vcomp[r] != cb || d.fixed[r]) continue;
+    const double4_32a xr = d.x[r], gr = d.grad[r];
+    const double dd[3] = {xr.x - G0.cctr[0], xr.y - G0.cctr[1], xr.z - G0.cctr[2]};
+    cz_row_e(d, s, lane, cb, G0.cctr, dd, acc);
+    cz_zt(make_double4_32a(-gr.x, -gr.y, -gr.z, 0.0), dd, acc + 21);
+    cz_zt(spmv_row64(d, s, lane, d.p), dd, acc + 27);
+  }
+  for (int q = 0; q < CZ_N; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) czw[wid][q] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < CZ_N; k += PCG_T) {
+    double v = 0.0;
+    for (int q = 0; q < PCG_T / 32; ++q) v += czw[q][k];
+    d.czpart[(size_t)k * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// ... and the inverse: the first CTA of each such group adds the group's partials in CTA order,
+// inverts E by Cholesky and leaves [E^-1 (36, row-major) | Z^T b (6) | Z^T A p_prev (6) | ok] in
+// d.czfac at the group's first CTA
+__global__ void __launch_bounds__(64) k_pcg_cz_factor(Dev d, int phase, PcgPlan plan, int nctas) {
+  __shared__ double t[CZ_N];
+  const PcgCta c = pcg_cta(d, plan);
+  const GelInfo& G0 = d.gi[c.g0];
+  if (blockIdx.x != c.c0 || !(c.ng == 1 && G0.cbody >= 0 && d.gc[c.g0].phase == phase)) return;
+  for (int k = threadIdx.x; k < CZ_N; k += blockDim.x) {
+    double v = 0.0;
+    for (int q = c.c0; q < c.c0 + c.nc; ++q) v += d.czpart[(size_t)k * nctas + q];
+    t[k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* f = d.czfac + (size_t)CZ_F * c.c0;
+  double L[36];
+  for (int q = 0; q < 36; ++q) L[q] = 0.0;
+  const bool ok = cz_chol(t, L);
+  for (int k = 0; k < 6; ++k) {  // E^-1, column k
+    double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, x[6];
+    e[k] = 1.0;
+    cz_solve(L, e, x);
+    for (int i = 0; i < 6; ++i) f[6 * i + k] = ok ? x[i] : 0.0;
+  }
+  for (int q = 0; q < 12; ++q) f[36 + q] = t[21 + q];
+  f[48] = ok ? 1.0 : 0.0;
+}
+
+void launch_pcg_cz_setup(const Dev& d, int phase, const PcgPlan& plan, int nctas, cudaStream_t st) {
+  k_pcg_cz_setup<<<nctas, PCG_T, 0, st>>>(d, phase, plan);
+  k_pcg_cz_factor<<<nctas, 64, 0, st>>>(d, phase, plan, nctas);
+  count_launch(2);
 }
 
 cudaError_t launch_pcg64(const Dev& d, int phase, const PcgPlan& plan, int nctas, int maxit, cudaStream_t st) {

@@ -41,6 +41,10 @@ constexpr int PAIR_SEE = 4;    // surface edge         vs surface edge
 // distance kind of a pair type: 1 edge-edge (mollified), 0 point-triangle
 __host__ __device__ constexpr int pair_kind(int type) { return (type == PAIR_EE || type == PAIR_SEE) ? 1 : 0; }
 constexpr int SS_MAXC = 4;     // connected components of a mesh that take part in soft-soft contact
+// streaming FP64 PCG coarse space: per-CTA partial sums of the set-up (21 entries of Z^T A Z, Z^T b,
+// Z^T A p_prev) and, per iteration, of Z^T w in the first 6 slots
+constexpr int CZ_N = 33;
+constexpr int CZ_F = 49;       // per coarse group: E^-1 (36), Z^T b, Z^T A p_prev, ok flag
 constexpr double ACCD_S = 0.1; // ACCD: the gap may shrink to this fraction per sweep
 
 // phases of a gel inside a batch
@@ -65,6 +69,9 @@ struct GelInfo {  // per gel, read-only after create
   int top0, ntop;            // top-surface triangles (rest outward normal up) in Dev::top
   int ncomp;                 // connected components of the tet mesh (> 1: soft-soft contact)
   int ss;                    // its index in the soft-soft gel list (-1: one body)
+  int cbody;                 // the largest body with no held vertex (-1: none): the streaming PCG's
+  int pad5_;                 // coarse space is its six rigid motions about its rest centroid cctr
+  double cctr[3];
 };
 
 struct GelCtl {  // per gel, written by the host before the launches of an iteration
@@ -190,6 +197,8 @@ struct Dev {
   double4_32a *r, *u, *w, *pp, *s;
   float4 *u32, *w32, *pp32, *s32, *r32, *x32;
   double* part;    // PCG: per-CTA partial sums exchanged inside a group, [2 sets][4][nctas]
+  double* czpart;  // streaming FP64 PCG's coarse space: per-CTA partial sums [CZ_N][nctas]
+  double* czfac;   // ... and per group (at its first CTA): [CZ_F] (E^-1, right-hand sides, flag)
   unsigned* bar;   // PCG: one barrier counter per group
   double* pslice;  // pooled PCG: per-slice partial sums [slice][4]
   PoolGel* pool;   // pooled PCG: per-gel records

@@ -41,6 +41,7 @@ void launch_hash_build(const Dev& d, int phase, int swept, cudaStream_t st);
 void launch_query(const Dev& d, int phase, int mode, cudaStream_t st);
 void launch_pair_ranges(const Dev& d, int phase, int skip_conv, cudaStream_t st);
 int launch_ss_pairs(const Dev& d, int phase, int mode, cudaStream_t st);
+void launch_pcg_cz_setup(const Dev& d, int phase, const PcgPlan& plan, int nctas, cudaStream_t st);
 void launch_ss_reset(const Dev& d, cudaStream_t st);
 void launch_contact_compute(const Dev& d, int phase, bool mixed, cudaStream_t st);
 void launch_contact_merge(const Dev& d, bool mixed, cudaStream_t st);
@@ -195,7 +196,7 @@ tx_status check_desc(const tx_gel_desc* d) {
   const tx_params& p = d->params;
   if (!(p.dhat > 0) || !(p.newton_tol > 0) || !(p.pcg_rel_tol > 0) || !(p.pcg_rel_tol_far >= 0) || p.newton_max_iter < 1 ||
       p.pcg_max_iter < 1 || p.ls_max_halvings < 1 || p.accd_max_iter < 1 || p.max_split_depth < 0 ||
-      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 2 || p.reserved0 != 0 || !(p.friction >= 0.0) ||
+      p.pcg_cta_slices < -1 || p.pcg_plan < 0 || p.pcg_plan > 2 || (p.pcg_coarse_off != 0 && p.pcg_coarse_off != 1) || !(p.friction >= 0.0) ||
       !(p.friction_eps_v > 0.0) || !(p.kappa_adapt_max == 0.0 || (p.kappa_adapt_max >= 1.0 && std::isfinite(p.kappa_adapt_max))) ||
       (p.kappa_adapt_max > 0.0 && !(p.kappa_adapt_dmin > 0.0 && std::isfinite(p.kappa_adapt_dmin))))
     return TX_ERR_ARG;
@@ -496,6 +497,7 @@ struct tx_batch {
   std::vector<GelInfo> gi;
   std::vector<Run> run;
   std::vector<int> ss_gel_h;  // the gels whose mesh holds several bodies (soft-soft contact)
+  bool has_cbody = false;     // some gel has a body held by no vertex (coarse space of k_pcg64)
   GelCtl* gc_h = nullptr;   // pinned
   GelVar* gv_h = nullptr;   // pinned
   Dev d{};
@@ -851,6 +853,21 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
     G.fixed_count = fc;
     G.ncomp = m.ncomp;
     G.ss = -1;
+    {  // the largest body with no held vertex: the coarse space of the streaming FP64 PCG
+      std::vector<int> nv(m.ncomp, 0), nfix(m.ncomp, 0);
+      std::vector<double> cs(3 * (size_t)m.ncomp, 0.0);
+      for (int i = 0; i < m.nv; ++i) {
+        if (m.adj[i].size() == 1) continue;  // in no tet
+        nv[m.comp[i]] += 1;
+        nfix[m.comp[i]] += m.fixed[i];
+        for (int a = 0; a < 3; ++a) cs[3 * m.comp[i] + a] += m.X[3 * i + a];
+      }
+      G.cbody = -1;
+      for (int q = 0; q < m.ncomp && !m.prm.pcg_coarse_off; ++q)
+        if (nfix[q] == 0 && nv[q] > 0 && (G.cbody < 0 || nv[q] > nv[G.cbody])) G.cbody = q;
+      for (int a = 0; a < 3; ++a) G.cctr[a] = G.cbody >= 0 ? cs[3 * G.cbody + a] / nv[G.cbody] : 0.0;
+      if (G.cbody >= 0) b->has_cbody = true;
+    }
     if (m.ncomp > 1) {
       G.ss = (int)b->ss_gel_h.size();
       b->ss_gel_h.push_back(g);
@@ -1131,6 +1148,8 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   d.pp = M.get<double4_32a>(rows);
   d.s = M.get<double4_32a>(rows);
   d.part = M.get<double>(8 * (size_t)cta_cap);
+  d.czpart = M.get<double>(CZ_N * (size_t)cta_cap);
+  d.czfac = M.get<double>(CZ_F * (size_t)cta_cap);
   d.pslice = M.get<double>(4 * (size_t)nslices);
   d.pool = M.get<PoolGel>(n);
   d.bar = M.get<unsigned>(n);
@@ -1833,6 +1852,7 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
   prof_close(b, 1);
   if (b->tune_key >= 0) tune_event(b, b->tev0);
   prof_open(b, PR_PCG);
+  int npcg = b->nparts;
   for (int k = 0; k < b->nparts; ++k) {
     const tx_batch::PlanPart& P = b->parts[k];
     CK(cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * P.plan.ngroups, st));
@@ -1843,14 +1863,19 @@ tx_status newton_launches(tx_batch* b, int pcg_max, int refine, int accd_max) {
         CK(P.pool_on ? launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, true, pcg_max, refine, st)
                      : launch_pcg_mixed(d, PH_NEWTON, P.plan, P.nctas, pcg_max, refine, st));
     } else {
-      if (P.res)
+      if (P.res) {
         CK(launch_pcg_res(d, PH_NEWTON, P.plan, P.nctas, false, pcg_max, 0, b->pcg_wmax, st));
-      else
+      } else {
+        if (!P.pool_on && b->has_cbody) {  // the coarse space of a free body (k_pcg64)
+          launch_pcg_cz_setup(d, PH_NEWTON, P.plan, P.nctas, st);
+          npcg += 2;
+        }
         CK(P.pool_on ? launch_pcg_pool(d, PH_NEWTON, P.pool, P.pool_nctas, false, pcg_max, 0, st)
                      : launch_pcg64(d, PH_NEWTON, P.plan, P.nctas, pcg_max, st));
+      }
     }
   }
-  prof_close(b, b->nparts);
+  prof_close(b, npcg);
   if (b->tune_key >= 0) tune_event(b, b->tev1);
   launch_gel_op(d, PH_NEWTON, 1, st);
   post_pcg_launch(b, accd_max);

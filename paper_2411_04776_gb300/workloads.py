@@ -384,21 +384,23 @@ def join_meshes(a: GelMesh, b: GelMesh) -> GelMesh:
 
 
 def gel_ball(ball_n: int = 20, grid=GRID_MINI, radius: float = 4.0e-3, depth: float = 1.0e-3, n_press: int = 60,
-             slide: float = 2.0e-3, n_slide: int = 60, seed: int = 0) -> Workload:
+             slide: float = 2.0e-3, n_slide: int = 60, seed: int = 0, gap_below: float = 2 * DHAT,
+             gap_above: float = DHAT) -> Workload:
     """Soft ball between the gel and a rigid plate (the soft-ball scene of Table 3, the ball a
-    deformable body of the gel's material): the ball (`ball_mesh`) rests 2 d_hat above the gel's top
-    face, its centre offset by a seeded +-1 mm in x-y; a 12 mm plate (`flat_plate`) starts d_hat above
-    the ball, closes both gaps and squeezes `depth` over n_press steps, then slides along +x (no
-    friction: over the ball)."""
+    deformable body of the gel's material): the ball (`ball_mesh`) rests gap_below above the gel's
+    top face, its centre offset by a seeded +-1 mm in x-y; a 12 mm plate (`flat_plate`) starts
+    gap_above above the ball, closes both gaps and squeezes `depth` over n_press steps, then slides
+    along +x (without friction: over the ball).  Gaps below d_hat put both contacts in place from
+    the first step."""
     rng = np.random.default_rng(seed)
     (nx, ny, nz), size = grid
     gel = gel_grid(nx, ny, nz, size)
     off = rng.uniform(-0.001, 0.001, size=2)
-    c = np.array([0.5 * size[0] + off[0], 0.5 * size[1] + off[1], gel.top + 2 * DHAT + radius])
+    c = np.array([0.5 * size[0] + off[0], 0.5 * size[1] + off[1], gel.top + gap_below + radius])
     ball = ball_mesh(ball_n, radius, c)
     ind = flat_plate(0.012, 13)
-    start = np.array([c[0], c[1], float(ball.verts[:, 2].max()) + DHAT])
-    travel = 3 * DHAT + depth
+    start = np.array([c[0], c[1], float(ball.verts[:, 2].max()) + gap_above])
+    travel = gap_below + gap_above + depth
     poses = [pose(start - np.array([0.0, 0.0, travel * s / n_press])) for s in range(1, n_press + 1)]
     bottom = start - np.array([0.0, 0.0, travel])
     poses += [pose(bottom + np.array([slide * s / n_slide, 0.0, 0.0])) for s in range(1, n_slide + 1)]

@@ -16,17 +16,27 @@ from paper_2411_04776_gb300 import workloads as W  # noqa: E402
 from tests.gpu_util import PARITY_NEWTON_TOL, POS_TOL  # noqa: E402
 
 STEPS = 6
+# No friction: with IPC friction on the plate-ball pairs and none on the ball-gel pairs (R25) the
+# squeezed ball's sideways motion is nearly free once the plate slides over it, and the state a
+# solve converges to depends on its path (the GPU's inexact Newton with its Galerkin start against
+# the oracle's exact solves: 38 um apart after the second step; from the same start state, the same
+# point to 5e-12 m)
+MU = 0.0
 
 
 def ball_scene():
-    return W.gel_ball(6, grid=W.GRID_SMALL, n_press=10, n_slide=4, depth=0.6e-3)
+    """Both contacts in place from the first step (gaps of d_hat / 2), a slow squeeze: a ball that
+    the plate first knocks loose flies free and is caught again, and where it lands then depends on
+    rounding (tens of microns, every outcome converged) — not a parity case."""
+    return W.gel_ball(6, grid=W.GRID_SMALL, n_press=20, n_slide=4, depth=0.6e-3, gap_below=0.5 * W.DHAT,
+                      gap_above=0.5 * W.DHAT)
 
 
 @pytest.fixture(scope="module")
 def reference():
     O.set_threads(0)
     wl = ball_scene()
-    og = O.OracleGel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max=400)
+    og = O.OracleGel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max=400, friction=MU)
     assert og.components()[0] == 2
     out = []
     for s in range(STEPS):
@@ -37,14 +47,21 @@ def reference():
     return wl, out
 
 
-def test_soft_ball_matches_oracle(reference):
-    """FP64 (mixed precision is not offered for a free body: its FP32 inner solves cannot resolve
-    the ball's rigid modes, held only by its mass, and the first step already ends elsewhere)."""
+@pytest.mark.parametrize("plan,coarse_off", [(0, 0), (1, 0), (1, 1)],
+                         ids=["resident", "streaming", "streaming-no-coarse"])
+def test_soft_ball_matches_oracle(reference, plan, coarse_off):
+    """FP64, with the automatic plan (the resident PCG) and with the streaming PCG, whose coarse
+    space over the ball's six rigid motions then runs.  (Mixed precision is not offered for a free
+    body: its FP32 inner solves cannot resolve the ball's rigid modes, held only by its mass, and
+    the first step already ends elsewhere.)"""
     wl, ref = reference
     precision = B.TX_PREC_FP64
     gel = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max_iter=400, precision=precision,
+                              pcg_plan=plan, pcg_coarse_off=coarse_off, friction=MU,
                               stream=torch.cuda.current_stream())
-    worst, ss_active, cut, errs, acts, fdev = 0.0, 0, 0, [], [], []
+    B.tx_gel_profile(gel.h, True)
+    worst, ss_active, cut, errs, acts, fdev, subs = 0.0, 0, 0, [], [], [], []
+    pcg = newton = 0
     try:
         for s in range(STEPS):
             assert gel.step(wl.poses[s], wl.dt) == 0
@@ -52,6 +69,7 @@ def test_soft_ball_matches_oracle(reference):
             xo, fo, info = ref[s]
             # pairs whose distance ends within rounding of d_hat may count on one side only
             acts.append((st.active_pairs, info["active_pairs"]))
+            subs.append((st.substeps, info["substeps"], st.newton_iters, info["newton_iters"]))
             cut += st.soft_pairs_cut
             errs.append(float(np.abs(x - xo).max()))
             worst = max(worst, errs[-1])
@@ -62,11 +80,18 @@ def test_soft_ball_matches_oracle(reference):
             fcv = np.asarray(fc)
             fdev.append((abs(fcv[2] - fo[2]) / fn, float(np.abs(fcv[:2] - fo[:2]).max()) / fn))
             ss_active = max(ss_active, info["active_pairs"])
+            pcg += st.pcg_iters
+            newton += st.newton_iters
+        prof = B.tx_gel_profile(gel.h, False)
     finally:
         gel.close()
-    print("soft ball (%s) vs oracle: max vertex error per step %s m, active pairs (GPU, oracle) %s, pair "
-          "assemblies cut %d" % ("fp64" if precision == B.TX_PREC_FP64 else "mixed", ["%.2e" % e for e in errs],
-                                 acts, cut))
+    print("soft ball (fp64, %s PCG) vs oracle: max vertex error per step %s m, active pairs (GPU, oracle) %s, "
+          "pair assemblies cut %d, %d Newton and %d PCG iterations"
+          % (("streaming" + (" without coarse space" if coarse_off else "")) if plan else "resident",
+             ["%.2e" % e for e in errs], acts, cut, newton, pcg))
+    print("  substeps and Newton iterations per step (GPU, oracle):", subs)
+    if plan == 1:
+        assert prof["pcg_streaming_launches"] > 0 and prof["pcg_resident_launches"] == 0, prof
     assert worst <= POS_TOL, worst
     assert all(abs(a - b) <= max(3, b // 10) for a, b in acts), acts
     assert all(n <= 2e-3 and t <= 2e-2 for n, t in fdev), fdev
@@ -97,7 +122,12 @@ def test_soft_ball_energy_and_gradient_match_oracle(reference):
     assert abs(eg - eo) <= 1e-11 * abs(eo), (eg, eo)
     free = wl.gel.dirichlet == 0
     scale = np.abs(go[free]).max()
-    assert np.abs(gg[free] - go[free]).max() <= 1e-9 * scale, np.abs(gg[free] - go[free]).max() / scale
+    err = np.abs(gg - go) * free[:, None]
+    i = int(np.argmax(err.max(axis=1)))
+    print("soft ball gradient vs oracle: %.2e of its scale, worst at vertex %d" % (err.max() / scale, i))
+    # the flat contact patch holds nearly parallel edge pairs, whose line-line closest points lose
+    # digits (both sides: the energy still agrees to 1e-11)
+    assert err.max() <= 1e-7 * scale, err.max() / scale
     assert np.abs(np.asarray(fg) - fo).max() <= 1e-9 * max(np.abs(fo).max(), 1e-12), (fg, fo)
 
 
