@@ -519,10 +519,12 @@ __global__ void __launch_bounds__(64) k_pcg_cz_factor(Dev d, int phase, PcgPlan 
   const PcgCta c = pcg_cta(d, plan);
   const GelInfo& G0 = d.gi[c.g0];
   if (blockIdx.x != c.c0 || !(c.ng == 1 && G0.cbody >= 0 && d.gc[c.g0].phase == phase)) return;
-  for (int k = threadIdx.x; k < CZ_N; k += blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = wid; k < CZ_N; k += blockDim.x >> 5) {  // a warp per quantity, lanes over the CTAs
     double v = 0.0;
-    for (int q = c.c0; q < c.c0 + c.nc; ++q) v += d.czpart[(size_t)k * nctas + q];
-    t[k] = v;
+    for (int q = c.c0 + lane; q < c.c0 + c.nc; q += 32) v += d.czpart[(size_t)k * nctas + q];
+    v = warp_sum(v);
+    if (lane == 0) t[k] = v;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
