@@ -212,3 +212,38 @@ def test_readout_sees_the_gelpad_only(reference):
     # the gel bulges by microns around the ball; the ball itself (from 2 d_hat above the top face
     # up) never shows
     assert np.nanmax(hg) < W.gel_grid(*W.GRID_SMALL[0], W.GRID_SMALL[1]).top + W.DHAT
+
+
+def test_full_size_soft_ball_state_matches_oracle():
+    """The benchmark's soft-ball scene at full size (the 41x51x9 gel + a 20^3 ball + plate): after
+    the GPU's first steps of the squeeze, the oracle evaluates the GPU's state itself -- its
+    brute-force pair scan gives the active pairs by type (rigid and soft-soft) that the GPU counts,
+    and the energy and gradient of the step's potential there agree."""
+    O.set_threads(0)
+    wl = W.gel_ball(20)
+    og = O.OracleGel.from_workload(wl)
+    gel = B.Gel.from_workload(wl, stream=torch.cuda.current_stream())
+    try:
+        for s in range(30):  # the first step that ends with the ball pressed on the gel
+            assert gel.step(wl.poses[s], wl.dt) == 0
+            x = gel.state()[0]
+            pose = wl.poses[s]
+            counts = og.pair_counts(x, pose)
+            if counts[8] + counts[9] > 0:
+                break
+        xt = x + 1e-6
+        eg, pg = gel.energy(x, xt, wl.dt, pose)
+        gg, _ = gel.gradient(x, xt, wl.dt, pose)
+    finally:
+        gel.close()
+    eo, po = og.energy(x, xt, wl.dt, pose)
+    go, _ = og.gradient(x, xt, wl.dt, pose)
+    print("full-size soft ball after %d steps: active pairs by type (PT, TP, EE, SPT, SEE) %s, GPU %d"
+          % (s + 1, list(counts[5:]), pg["active"]))
+    assert counts[8] + counts[9] > 0, counts  # the ball presses on the gel
+    assert pg["active"] == po["active"] == int(counts[5:].sum()), (pg, po, counts)
+    assert abs(pg["barrier"] - po["barrier"]) <= 1e-11 * abs(po["barrier"]), (pg, po)
+    assert abs(eg - eo) <= 1e-11 * abs(eo), (eg, eo)
+    free = wl.gel.dirichlet == 0
+    scale = np.abs(go[free]).max()
+    assert np.abs(gg - go)[free].max() <= 1e-7 * scale, np.abs(gg - go)[free].max() / scale
