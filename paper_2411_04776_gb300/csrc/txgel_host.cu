@@ -111,7 +111,7 @@ constexpr int PCG_RES_MAXNC = 256;  // CTAs of one group the resident PCG kernel
 constexpr int PCG_POOL_MIN_GELS = 32;  // automatic plan: pooled streaming kernels from this many gels
 // soft-soft contact: spare block positions of a surface row near another body, and "near": within
 // this fraction of that body's rest bounding-box diagonal (plus d_hat) of its rest box
-constexpr int SS_SLOTS = 24;
+constexpr int SS_SLOTS = 12;
 constexpr double SS_NEAR = 0.25;
                                       // being solved on (per-gel CTA groups below: measured faster
                                       // up to 16 gels, slower from 64)
