@@ -120,7 +120,8 @@ void tx_params_default(tx_params* p);
  * surface vertex against every surface triangle of another body, every two surface edges of
  * different bodies), without friction and without counting in contact_force.  Body 0 is the
  * gelpad: the marker and height-map readouts use its top surface only.  More than 4 bodies is
- * TX_ERR_ARG. */
+ * TX_ERR_ARG, and so is mixed precision for a mesh with a body held by no vertex (its rigid
+ * motions, resisted by its mass alone, are beyond the FP32 inner solves: use FP64). */
 typedef struct tx_gel_desc {
   int32_t n_verts;
   const double* verts;       /* n_verts x 3 rest positions [m]                                  */

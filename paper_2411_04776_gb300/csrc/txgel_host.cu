@@ -792,6 +792,23 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
       delete b;
       return TX_ERR_ARG;
     }
+  // mixed precision needs every body held by a vertex: a free body's rigid motions, resisted by
+  // its mass alone, are beyond the FP32 inner solves (its solves stop at a wrong state)
+  for (int g = 0; g < n && b->mixed; ++g) {
+    const Mesh& m = b->mesh[g];
+    std::vector<char> used(m.ncomp, 0), held(m.ncomp, 0);
+    for (int i = 0; i < m.nv; ++i)
+      if (m.adj[i].size() > 1) {
+        used[m.comp[i]] = 1;
+        held[m.comp[i]] |= m.fixed[i];
+      }
+    for (int q = 0; q < m.ncomp; ++q)
+      if (used[q] && !held[q]) {
+        set_last_error("mixed precision needs every body of the mesh held by a vertex (a free body: use FP64)");
+        delete b;
+        return TX_ERR_ARG;
+      }
+  }
   // ---- offsets
   b->gi.resize(n);
   int rows = 0, tets = 0, nsv = 0, nst = 0, nse = 0, nq = 0, niv = 0, nit = 0, nie = 0, hb = 0, max_hnb = 1;

@@ -48,14 +48,12 @@ def reference():
 
 
 @pytest.mark.parametrize("plan,coarse_off", [(0, 0), (1, 0), (1, 1)],
-                         ids=["resident", "streaming", "streaming-no-coarse"])
+                         ids=["automatic", "streaming", "streaming-no-coarse"])
 def test_soft_ball_matches_oracle(reference, plan, coarse_off):
-    """FP64, with the automatic plan (the resident PCG) and with the streaming PCG, whose coarse
-    space over the ball's six rigid motions then runs.  (Mixed precision is not offered for a free
-    body: its FP32 inner solves cannot resolve the ball's rigid modes, held only by its mass, and
-    the first step already ends elsewhere.)"""
-    wl, ref = reference
+    """FP64, with the automatic plan and with the streaming PCG forced, with and without its
+    coarse space over the ball's six rigid motions."""
     precision = B.TX_PREC_FP64
+    wl, ref = reference
     gel = B.Gel.from_workload(wl, newton_tol=PARITY_NEWTON_TOL, newton_max_iter=400, precision=precision,
                               pcg_plan=plan, pcg_coarse_off=coarse_off, friction=MU,
                               stream=torch.cuda.current_stream())
@@ -85,9 +83,10 @@ def test_soft_ball_matches_oracle(reference, plan, coarse_off):
         prof = B.tx_gel_profile(gel.h, False)
     finally:
         gel.close()
-    print("soft ball (fp64, %s PCG) vs oracle: max vertex error per step %s m, active pairs (GPU, oracle) %s, "
+    print("soft ball (%s, %s PCG) vs oracle: max vertex error per step %s m, active pairs (GPU, oracle) %s, "
           "pair assemblies cut %d, %d Newton and %d PCG iterations"
-          % (("streaming" + (" without coarse space" if coarse_off else "")) if plan else "resident",
+          % ("fp64" if precision == B.TX_PREC_FP64 else "mixed",
+             ("streaming" + (" without coarse space" if coarse_off else "")) if plan else "automatic",
              ["%.2e" % e for e in errs], acts, cut, newton, pcg))
     print("  substeps and Newton iterations per step (GPU, oracle):", subs)
     if plan == 1:
@@ -96,6 +95,21 @@ def test_soft_ball_matches_oracle(reference, plan, coarse_off):
     assert all(abs(a - b) <= max(3, b // 10) for a, b in acts), acts
     assert all(n <= 2e-3 and t <= 2e-2 for n, t in fdev), fdev
     assert cut == 0, cut  # every cross-body block found a spare position
+
+
+def test_mixed_precision_refuses_a_free_body():
+    """Mixed precision is not offered for a mesh with a body held by no vertex (measured: its FP32
+    inner solves end the soft ball's first step 30 um from the oracle's state): TX_ERR_ARG with a
+    message; FP64, and mixed precision once the ball is held, are accepted."""
+    wl = ball_scene()
+    with pytest.raises(B.TxError) as e:
+        B.Gel.from_workload(wl, precision=B.TX_PREC_MIXED)
+    assert e.value.status == 1 and "free body" in B.load().tx_last_error().decode()  # TX_ERR_ARG
+    B.Gel.from_workload(wl).close()
+    held = wl.gel.dirichlet.copy()
+    held[-1] = 1  # one ball vertex held
+    B.Gel(B.GelDesc(wl.gel.verts, wl.gel.tets, held, wl.material, wl.indenter.verts, wl.indenter.tris, wl.pose0,
+                    dhat=wl.dhat, precision=B.TX_PREC_MIXED)).close()
 
 
 def test_soft_ball_energy_and_gradient_match_oracle(reference):
