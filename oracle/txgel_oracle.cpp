@@ -39,7 +39,11 @@
 //   * mass lumping m_i = rho * sum_{t ni i} V_t / 4;
 //   * kappa = 0 means kappa = E * (mean rest length of the gel surface edges);
 //   * contact primitives: gel surface vertices vs indenter triangles, indenter vertices vs gel
-//     surface triangles, gel surface edges vs indenter edges (no gel self-contact);
+//     surface triangles, gel surface edges vs indenter edges (no self-contact within a body);
+//     a tet mesh of several connected components (bodies) also pairs the surfaces of different
+//     bodies (surface vertex vs surface triangle, surface edge vs surface edge: GIPC's
+//     soft-to-soft contact), without friction and outside the indenter force; body 0 (the body
+//     of the first vertex in a tet) is the gelpad of the readouts;
 //   * distance classification: the closest feature pair (vertex/edge/face) of the primitive pair;
 //   * EE mollifier threshold eps_x = 1e-3 |a1-a0|^2 |b1-b0|^2 at rest;
 //   * ACCD: C-IPC's additive CCD with s = 0.1 (the gap may shrink to 10%), t_c = 1, thickness 0,
