@@ -1064,3 +1064,19 @@ def test_adaptive_kappa_carries_a_press_a_weak_fixed_barrier_cannot():
     og.reset()  # reset returns kappa to its initial value
     wl = W.small_gel_sphere(1)
     assert og.step(wl.poses[0], wl.dt)["kappa"] == k0
+
+
+@pytest.mark.parametrize("n,nv,nt", [(10, 1000, 4374), (20, 8000, 41154), (23, 12167, 63888)])
+def test_soft_ball_mesh_sizes_and_shape(n, nv, nt):
+    """The soft-ball meshes of the Table 3 comparison: the documented vertex and tet counts, every
+    tet positively oriented, and the cube's faces carried onto the sphere (every boundary vertex at
+    the radius, every vertex inside it)."""
+    r, c = 4e-3, np.array([0.01, 0.012, 0.006])
+    b = W.ball_mesh(n, r, c)
+    assert (len(b.verts), len(b.tets)) == (nv, nt)
+    e = [b.verts[b.tets[:, k]] - b.verts[b.tets[:, 0]] for k in (1, 2, 3)]
+    assert np.einsum("ij,ij->i", np.cross(e[0], e[1]), e[2]).min() > 0.0
+    sv, _, _ = _boundary(b.tets)
+    rad = np.linalg.norm(b.verts - c, axis=1)
+    assert np.abs(rad[sv] - r).max() <= 1e-15 * 10 and rad.max() <= r * (1 + 1e-14)
+    assert not b.dirichlet.any()
