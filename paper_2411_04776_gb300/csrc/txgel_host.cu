@@ -733,6 +733,41 @@ tx_status alloc_hash(tx_batch* b) {
   return upload_info(b);
 }
 
+// Block positions each row of a gel needs in its slice: its mesh neighbours (incl. itself), and
+// in a mesh of several bodies SS_SLOTS more for every free surface row that lies, at rest, near
+// the box of another body (room for the blocks of soft-soft pairs, claimed during the assembly)
+std::vector<int> row_block_needs(const Mesh& m) {
+  std::vector<int> need(m.nv);
+  for (int i = 0; i < m.nv; ++i) need[i] = (int)m.adj[i].size();
+  if (m.ncomp <= 1) return need;
+  double lo[SS_MAXC][3], hi[SS_MAXC][3];
+  for (int c = 0; c < SS_MAXC; ++c)
+    for (int a = 0; a < 3; ++a) {
+      lo[c][a] = INFINITY;
+      hi[c][a] = -INFINITY;
+    }
+  for (int i = 0; i < m.nv; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[m.comp[i]][a] = std::min(lo[m.comp[i]][a], m.X[3 * i + a]);
+      hi[m.comp[i]][a] = std::max(hi[m.comp[i]][a], m.X[3 * i + a]);
+    }
+  for (int i : m.sv) {
+    if (m.fixed[i]) continue;
+    bool near = false;
+    for (int c = 0; c < m.ncomp && !near; ++c) {
+      if (c == m.comp[i]) continue;
+      double diag2 = 0.0;
+      for (int a = 0; a < 3; ++a) diag2 += (hi[c][a] - lo[c][a]) * (hi[c][a] - lo[c][a]);
+      const double pad = SS_NEAR * std::sqrt(diag2) + m.prm.dhat;
+      near = true;
+      for (int a = 0; a < 3; ++a)
+        if (m.X[3 * i + a] < lo[c][a] - pad || m.X[3 * i + a] > hi[c][a] + pad) near = false;
+    }
+    if (near) need[i] += SS_SLOTS;
+  }
+  return need;
+}
+
 // ---------------------------------------------------------------- creation
 tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch** out) {
   if (!descs || n <= 0 || !out) return TX_ERR_ARG;
@@ -899,35 +934,7 @@ tx_status create_batch(const tx_gel_desc* descs, int n, void* stream, tx_batch**
   for (int g = 0; g < n; ++g) {
     const Mesh& m = b->mesh[g];
     const GelInfo& G = b->gi[g];
-    std::vector<int> need(m.nv);
-    for (int i = 0; i < m.nv; ++i) need[i] = (int)m.adj[i].size();
-    if (m.ncomp > 1) {
-      double lo[SS_MAXC][3], hi[SS_MAXC][3];
-      for (int c = 0; c < SS_MAXC; ++c)
-        for (int a = 0; a < 3; ++a) {
-          lo[c][a] = INFINITY;
-          hi[c][a] = -INFINITY;
-        }
-      for (int i = 0; i < m.nv; ++i)
-        for (int a = 0; a < 3; ++a) {
-          lo[m.comp[i]][a] = std::min(lo[m.comp[i]][a], m.X[3 * i + a]);
-          hi[m.comp[i]][a] = std::max(hi[m.comp[i]][a], m.X[3 * i + a]);
-        }
-      for (int i : m.sv) {
-        if (m.fixed[i]) continue;
-        bool near = false;
-        for (int c = 0; c < m.ncomp && !near; ++c) {
-          if (c == m.comp[i]) continue;
-          double diag2 = 0.0;
-          for (int a = 0; a < 3; ++a) diag2 += (hi[c][a] - lo[c][a]) * (hi[c][a] - lo[c][a]);
-          const double pad = SS_NEAR * std::sqrt(diag2) + m.prm.dhat;
-          near = true;
-          for (int a = 0; a < 3; ++a)
-            if (m.X[3 * i + a] < lo[c][a] - pad || m.X[3 * i + a] > hi[c][a] + pad) near = false;
-        }
-        if (near) need[i] += SS_SLOTS;
-      }
-    }
+    const std::vector<int> need = row_block_needs(m);
     for (int s = 0; s < G.ns; ++s) {
       int w = 1;
       for (int l = 0; l < SLICE; ++l) {
@@ -2626,21 +2633,23 @@ size_t tx_gel_footprint_bytes(const tx_gel_desc* desc) {
   if (build_mesh(desc, m) != TX_OK) return 0;
   const bool mixed = desc->params.precision == TX_PREC_MIXED;
   const size_t rows = (size_t)((m.nv + SLICE - 1) / SLICE) * SLICE;
+  const std::vector<int> need = row_block_needs(m);
   size_t nbp = 0;
   for (size_t s = 0; s < rows / SLICE; ++s) {
     size_t w = 1;
     for (int l = 0; l < SLICE; ++l) {
       const size_t i = s * SLICE + l;
-      if (i < (size_t)m.nv) w = std::max(w, m.adj[i].size());
+      if (i < (size_t)m.nv) w = std::max(w, (size_t)need[i]);
     }
     nbp += w * SLICE;
   }
   const size_t nt = m.nt, nq = m.sv.size() + m.st.size() + m.se.size();
-  size_t bytes = rows * (17 * sizeof(double4_32a) + 8 + 1 + 4 + 4 + 72);
+  size_t bytes = rows * (17 * sizeof(double4_32a) + 8 + 1 + 4 + 4 + 72 + 1);  // (+ body id)
   if (mixed) bytes += rows * (6 * sizeof(float4) + 36);
   bytes += nt * (16 + 72 + 8 + 4 + 64 + TS * 8 + (mixed ? TS32 * 4 : 0));
   bytes += nbp * (4 + 4 + 4 + (mixed ? 36 : 72));
-  bytes += nq * (4 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;
+  bytes += nq * (5 * 4) + (size_t)m.niv * 96 + (size_t)m.nit * 20 + m.ie.size() * 20;  // (+ soft-soft list)
+  if (m.ncomp > 1) bytes += nbp * 4;  // soft-soft claim list (at most every padding position)
   bytes += ((size_t)m.niv + m.nit + m.ie.size()) * 2 * sizeof(double4_32a);  // primitive boxes
   bytes += (size_t)initial_pcap(m) * (32 + sizeof(C1Rec)) +
            (size_t)CREC_PER_GEL * (pair_record_doubles() * 8 + CH_STRIDE * 8 + CH_BP * 4);
