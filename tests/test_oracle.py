@@ -1080,3 +1080,22 @@ def test_soft_ball_mesh_sizes_and_shape(n, nv, nt):
     rad = np.linalg.norm(b.verts - c, axis=1)
     assert np.abs(rad[sv] - r).max() <= 1e-15 * 10 and rad.max() <= r * (1 + 1e-14)
     assert not b.dirichlet.any()
+
+
+def test_body_numbering_and_a_vertex_in_no_tet():
+    """Bodies are the tet mesh's connected components, numbered in the order of their first vertex
+    in a tet; a vertex in no tet belongs to no body (it joins body 0 and is in no pair).  Here a
+    stray vertex comes first, then two balls: two bodies, the first ball is body 0 (the gelpad
+    slot of the readouts), and the stray vertex is counted in neither."""
+    b1 = W.ball_mesh(4, 2e-3, (0.0, 0.0, 0.0))
+    b2 = W.ball_mesh(4, 2e-3, (0.0, 0.0, 5e-3))
+    both = W.join_meshes(b1, b2)
+    verts = np.vstack([[[1.0, 1.0, 1.0]], both.verts])
+    tets = (both.tets + 1).astype(np.int32)
+    plate = W.flat_plate(0.004, 3)
+    far = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    og = O.OracleGel(verts, tets, np.zeros(len(verts), dtype=np.uint8), (E_, NU_, RHO_), plate.verts, plate.tris,
+                     far, dhat=W.DHAT, kappa=500.0)
+    n, comp = og.components()
+    assert n == 2
+    assert comp[0] == 0 and np.all(comp[1:1 + len(b1.verts)] == 0) and np.all(comp[1 + len(b1.verts):] == 1)
