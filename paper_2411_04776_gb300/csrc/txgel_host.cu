@@ -101,6 +101,7 @@ constexpr int PCG_MAXG_HOST = 64;  // must match PCG_MAXG in the PCG kernel
 // default slices (32 rows) per PCG CTA: FP64 spreads a gel over many SMs (the FP64 pipe bounds
 // the SpMV); FP32 keeps groups small so that their barriers are cheap
 constexpr int PCG_SLICES_FP64 = 4;
+constexpr int PCG_SLICES_FP64_LARGE = 6;  // one FP64 gel on the streaming kernels
 constexpr int PCG_SLICES_MIXED = 4;
 constexpr int TUNE_N = 5;
 constexpr int TUNE_SPC[TUNE_N] = {4, 2, 3, 6, 8};  // candidate slices per CTA (first: the default)
@@ -1726,7 +1727,17 @@ tx_status plan_part(tx_batch* b, const std::vector<int>& set, int spc0, tx_batch
     res = b->plan_mode == 0 && occ_res > 0 && nctas <= nsm * occ_res && max_nc <= PCG_RES_MAXNC &&
           (max_nc == 1 || max_slices >= 2);
     const int occ = std::max(1, pcg_max_ctas_per_sm(max_slices));
-    if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) break;
+    if (res || (nctas <= nsm * occ && nctas <= b->pcg_cta_cap)) {
+      // one FP64 gel too large for the resident kernels, at the default split: fewer, fuller CTAs
+      // (measured on the 41x51x9 gel + 20^3 soft ball, 26,819 rows: 93.4 / 73.6 / 74.2 / 109.1 ms
+      // per step at 4 / 6 / 8 / 12 slices per CTA)
+      if (!res && !b->mixed && set.size() == 1 && spc0 == PCG_SLICES_FP64 && spc < PCG_SLICES_FP64_LARGE &&
+          b->plan_mode != 2) {
+        spc = PCG_SLICES_FP64_LARGE;
+        continue;
+      }
+      break;
+    }
     if (attempt > 400) {
       set_last_error("PCG partition does not fit the device");
       return TX_ERR_ARG;
